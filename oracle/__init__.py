@@ -1,0 +1,238 @@
+"""CPU FP64 oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never calls it and
+shares no code with it (see ``oracle.c`` for what it computes and the paper
+passages each function follows).
+
+The C source is compiled on first use with the system C compiler into
+``oracle/_build/liboracle.so`` (plain ``-O2``, IEEE arithmetic).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# energy identifiers of the public interface
+SYMDIR, STVK, HINGE, SHELL, NH, MLP, AREA, ARAP = 1, 2, 3, 4, 5, 6, 7, 16
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            i64, i32, vp = C.c_int64, C.c_int, C.c_void_p
+            L.orc_hinges.restype = i64
+            L.orc_hinges.argtypes = [i64, i64, _ip, vp]
+            L.orc_pattern.restype = i64
+            L.orc_pattern.argtypes = [i64, i64, _ip, i64, vp, vp, vp]
+            L.orc_tri_rest.restype = None
+            L.orc_tri_rest.argtypes = [i64, _dp, _ip, _dp, _dp]
+            L.orc_hinge_rest.restype = None
+            L.orc_hinge_rest.argtypes = [i64, vp, _dp, vp, vp]
+            L.orc_assemble.restype = i64
+            L.orc_assemble.argtypes = [
+                i32, vp, i32, i32, i64, i32, i64, _ip, _dp, _dp, i64, vp, vp, vp, _dp, _ip, _ip,
+                vp, _dp, vp, vp, vp,
+            ]
+            L.orc_local.restype = i32
+            L.orc_local.argtypes = [i32, i32, vp, i32, _dp, i32, _dp, C.c_double, C.c_double,
+                                    C.c_double, _dp, _dp, _dp]
+            L.orc_hd_probe.restype = None
+            L.orc_hd_probe.argtypes = [i32, _dp, i32, _dp]
+            L.orc_arap_jacobian.restype = i64
+            L.orc_arap_jacobian.argtypes = [i64, _ip, _dp, _dp, _dp, _dp, _ip, _ip, _dp]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _params(p):
+    return None if p is None or len(p) == 0 else np.ascontiguousarray(p, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# connectivity and rest data
+# --------------------------------------------------------------------------
+def hinges(nV: int, F: np.ndarray) -> np.ndarray:
+    """Canonical hinges (nH, 4) int32: (e0, e1, a, b), e0 < e1, sorted."""
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    L = lib()
+    n = L.orc_hinges(nV, F.shape[0], F, None)
+    if n < 0:
+        raise ValueError("non-manifold or inconsistently oriented edge")
+    H = np.zeros((max(n, 1), 4), dtype=np.int32)
+    L.orc_hinges(nV, F.shape[0], F, _ptr(H))
+    return H[:n]
+
+
+def pattern(nV: int, F: np.ndarray, H: np.ndarray | None = None):
+    """Brute-force block pattern of the triangle (and hinge) stencils."""
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    nH = 0 if H is None else int(H.shape[0])
+    Hc = None if H is None else np.ascontiguousarray(H, dtype=np.int32)
+    L = lib()
+    nnzb = L.orc_pattern(nV, F.shape[0], F, nH, _ptr(Hc), None, None)
+    row_ptr = np.zeros(nV + 1, dtype=np.int32)
+    col = np.zeros(max(nnzb, 1), dtype=np.int32)
+    L.orc_pattern(nV, F.shape[0], F, nH, _ptr(Hc), _ptr(row_ptr), _ptr(col))
+    return row_ptr, col[:nnzb]
+
+
+def tri_rest(V: np.ndarray, F: np.ndarray):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    nT = F.shape[0]
+    Dinv = np.zeros((max(nT, 1), 4))
+    area = np.zeros(max(nT, 1))
+    lib().orc_tri_rest(nT, V, F, Dinv, area)
+    return Dinv[:nT], area[:nT]
+
+
+def hinge_rest(H: np.ndarray, V: np.ndarray):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    Hc = np.ascontiguousarray(H, dtype=np.int32)
+    n = Hc.shape[0]
+    tb = np.zeros(max(n, 1))
+    ab = np.zeros(max(n, 1))
+    lib().orc_hinge_rest(n, _ptr(Hc), V, _ptr(tb), _ptr(ab))
+    return tb[:n], ab[:n]
+
+
+class Problem:
+    """Connectivity, pattern and rest data of one (batched) mesh for one
+    energy, built by the oracle's own routines."""
+
+    def __init__(self, rest: np.ndarray, F: np.ndarray, energy: int, vdim: int, params=None):
+        self.rest = np.ascontiguousarray(rest, dtype=np.float64)
+        self.F = np.ascontiguousarray(F, dtype=np.int32)
+        self.nV = int(self.rest.shape[0])
+        self.nT = int(self.F.shape[0])
+        self.energy = energy
+        self.vdim = vdim
+        self.params = _params(params)
+        self.Dinv, self.area = tri_rest(self.rest, self.F)
+        if energy in (HINGE, SHELL):
+            self.H = hinges(self.nV, self.F)
+            self.thetabar, self.abar = hinge_rest(self.H, self.rest)
+        else:
+            self.H = np.zeros((0, 4), dtype=np.int32)
+            self.thetabar = np.zeros(0)
+            self.abar = np.zeros(0)
+        self.row_ptr, self.col = pattern(self.nV, self.F, self.H if energy in (HINGE, SHELL) else None)
+
+    @property
+    def nH(self) -> int:
+        return int(self.H.shape[0])
+
+    @property
+    def nnzb(self) -> int:
+        return int(self.col.shape[0])
+
+    def n_elements(self) -> int:
+        if self.energy == SHELL:
+            return self.nT + self.nH
+        if self.energy == HINGE:
+            return self.nH
+        return self.nT
+
+    def assemble(self, x: np.ndarray, route: int = 0, rows: np.ndarray | None = None,
+                 hessian: bool = True, per_element: bool = False):
+        """Energy, gradient (nV, vdim) and BSR values (nnzb, vdim, vdim).
+
+        rows: optional vertex ids; only those block rows (and gradient rows)
+        are assembled, from every element touching them."""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.nV, self.vdim)
+        vd = self.vdim
+        grad = np.zeros((self.nV, vd))
+        vals = np.zeros((self.nnzb, vd, vd)) if hessian else None
+        mask = None
+        if rows is not None:
+            mask = np.zeros(self.nV, dtype=np.uint8)
+            mask[np.asarray(rows)] = 1
+        e = np.zeros(1)
+        elem = np.zeros(max(self.n_elements(), 1)) if per_element else None
+        nerr = lib().orc_assemble(
+            self.energy, _ptr(self.params), 0 if self.params is None else len(self.params), route,
+            self.nV, vd, self.nT, self.F, self.Dinv, self.area, self.nH, _ptr(self.H),
+            _ptr(self.thetabar), _ptr(self.abar), x, self.row_ptr, self.col, _ptr(mask), e,
+            _ptr(grad), _ptr(vals), _ptr(elem))
+        if nerr < 0:
+            raise RuntimeError(f"oracle assembly error {nerr}")
+        out = {"energy": float(e[0]), "grad": grad, "vals": vals, "n_domain_err": int(nerr)}
+        if per_element:
+            out["elem_energy"] = elem[: self.n_elements()]
+        return out
+
+    def arap_jacobian(self, uv: np.ndarray):
+        """Residual r (4 nT), CSR Jacobian (row_ptr, col, val)."""
+        uv = np.ascontiguousarray(uv, dtype=np.float64).reshape(self.nV, 2)
+        nT = self.nT
+        r = np.zeros(4 * nT)
+        rp = np.zeros(4 * nT + 1, dtype=np.int32)
+        jc = np.zeros(24 * nT, dtype=np.int32)
+        jv = np.zeros(24 * nT)
+        nerr = lib().orc_arap_jacobian(nT, self.F, self.Dinv, self.area, uv, r, rp, jc, jv)
+        return {"r": r, "row_ptr": rp, "col": jc, "val": jv, "n_domain_err": int(nerr)}
+
+
+def local(energy: int, xl, vdim: int = 3, Dinv=None, area: float = 0.0, thetabar: float = 0.0,
+          abar: float = 0.0, params=None, route: int = 0):
+    """Local f, gradient (k), Hessian (k, k) of one element."""
+    xl = np.ascontiguousarray(xl, dtype=np.float64).ravel()
+    k = xl.shape[0]
+    f = np.zeros(1)
+    g = np.zeros(k)
+    H = np.zeros(k * k)
+    Dinv = np.ascontiguousarray(np.zeros(4) if Dinv is None else Dinv, dtype=np.float64).ravel()
+    p = _params(params)
+    err = lib().orc_local(energy, route, _ptr(p), 0 if p is None else len(p), xl, vdim, Dinv,
+                          float(area), float(thetabar), float(abar), f, g, H)
+    if err < 0:
+        raise ValueError(f"no route {route} for energy {energy}")
+    return {"f": float(f[0]), "g": g, "H": H.reshape(k, k), "err": int(err)}
+
+
+def hd_probe(op: int, *inputs):
+    n = len(inputs)
+    out = np.zeros(1 + n + n * n)
+    lib().orc_hd_probe(op, np.asarray(inputs, dtype=np.float64), n, out)
+    return out[0], out[1:1 + n], out[1 + n:].reshape(n, n)
+
+
+def bsr_to_dense(nV: int, vd: int, row_ptr, col, vals) -> np.ndarray:
+    """Dense (nV*vd)^2 matrix of a BSR matrix (tiny meshes only)."""
+    Hd = np.zeros((nV * vd, nV * vd))
+    for i in range(nV):
+        for p in range(row_ptr[i], row_ptr[i + 1]):
+            j = col[p]
+            Hd[i * vd:(i + 1) * vd, j * vd:(j + 1) * vd] += vals[p]
+    return Hd
