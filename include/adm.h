@@ -1,0 +1,192 @@
+/*
+ * adm.h -- C ABI of libadm: per-element forward-mode differentiation of
+ * energy terms on triangle meshes and assembly of the global gradient,
+ * block-sparse Hessian and sparse Jacobian, on one NVIDIA GB300 (sm_103a).
+ *
+ * The calls follow the problem statement of "Locality-Aware Automatic
+ * Differentiation on the GPU for Mesh-Based Computations" (Sec. 4.1):
+ *   F(x) = sum_j f_j(S_j x)                (Eq. 1)
+ *   g = sum_j S_j^T grad f_j,  H = sum_j S_j^T Hess f_j S_j   (Eq. 2)
+ *   J = sum_j P_j^T J_j S_j                (Eq. 3)
+ * with the block pattern of H (and the column pattern of J) fixed from the
+ * mesh connectivity at creation time (Sec. 6.1) and every local derivative
+ * computed by forward-mode AD in registers (Sec. 5.1, Sec. 6.2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - No exception crosses the ABI; every call returns an adm_status.
+ *  - Argument and mesh errors are detected on the host and returned
+ *    synchronously.  Errors found by the kernels (a folded triangle, a
+ *    degenerate hinge, a non-finite value) are latched in a device status
+ *    word and read with adm_get_status() after the caller has synchronised
+ *    the stream; the offending element contributes nothing.
+ *  - Evaluation calls are stream-ordered and asynchronous: they enqueue work
+ *    on the CUDA stream passed as `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream) and return without waiting.
+ *  - Ownership: the caller owns every buffer it passes (x, outputs); the
+ *    library owns the handle, the pattern arrays it returns, its rest data,
+ *    slot maps and work tables.  Pattern pointers stay valid until
+ *    adm_destroy().  Evaluation calls allocate no memory except where
+ *    stated (the first call of a CUDA graph, the host-buffer call).
+ *  - Outputs are fully overwritten (no accumulate-into contract).
+ *  - Layouts: x and the gradient are vertex-major, x[v * var_dim + d];
+ *    BSR values are nnzb blocks of var_dim x var_dim, row-major inside a
+ *    block, in the order of the pattern's col array; the pattern stores both
+ *    (i, j) and (j, i) (full symmetric storage, as the CSR of Sec. 6.1), and
+ *    columns ascend inside every block row.
+ *  - Precision: ADM_FP64 buffers are double, ADM_FP32 buffers are float;
+ *    energies and gradient norms are always double.
+ */
+#ifndef ADM_H
+#define ADM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adm_ctx *adm_handle; /* opaque, library-owned */
+
+typedef enum {
+    ADM_OK = 0,
+    ADM_ERR_ARG = -1,         /* bad argument (null pointer, size, enum)        */
+    ADM_ERR_MESH = -2,        /* bad mesh: index out of range, degenerate rest
+                                 triangle, edge with > 2 faces or inconsistent
+                                 orientation where a hinge term needs it       */
+    ADM_ERR_DOMAIN = -3,      /* a kernel met an element outside the energy's
+                                 domain (folded triangle, degenerate hinge)     */
+    ADM_ERR_CUDA = -4,        /* a CUDA runtime call failed                     */
+    ADM_ERR_TIMEOUT = -5,     /* a bounded device wait ran out                  */
+    ADM_ERR_OOM = -6,         /* device allocation failed                       */
+    ADM_ERR_UNSUPPORTED = -7  /* energy / precision / var_dim combination that
+                                 this build does not provide                    */
+} adm_status;
+
+/* Energy terms.  Stencils: triangle (3 vertices) or hinge = interior edge plus
+ * its two opposite vertices (4 vertices, Sec. 7.7). */
+typedef enum {
+    ADM_SYMDIR2D = 1,         /* area_t (|J|_F^2 + |J^-1|_F^2), UV map, var_dim 2 (Sec. 7.2) */
+    ADM_STVK_MEMBRANE = 2,    /* t A (mu |E|^2 + lambda/2 tr(E)^2), var_dim 3       */
+    ADM_HINGE_BENDING = 3,    /* k_b (A/3) (theta - theta')^2 h^2, var_dim 3 (Sec. 7.7) */
+    ADM_SHELL = 4,            /* ADM_STVK_MEMBRANE + ADM_HINGE_BENDING              */
+    ADM_NH_MEMBRANE = 5,      /* Neo-Hookean on the invariants of C (Sec. 7.7)      */
+    ADM_MLP_MEMBRANE = 6,     /* learned Neo-Hookean surrogate (adm_mlp_* calls)    */
+    ADM_AREA = 7,             /* 1/2 |(x_j - x_i) x (x_k - x_i)| (Sec. 7.6)         */
+    ADM_ARAP2D_RESIDUAL = 16  /* 4 residuals sqrt(A) vec(J - R(J)) per triangle,
+                                 var_dim 2 (vector-valued term, Eq. 3)              */
+} adm_energy;
+
+typedef enum { ADM_FP64 = 0, ADM_FP32 = 1 } adm_precision;
+
+/* Options for adm_set_option(). */
+typedef enum {
+    ADM_OPT_ASSEMBLER = 1,    /* 0 = tiled (shared-memory patches, default),
+                                 1 = per-element atomic scatter (the paper's
+                                 Sec. 5.5 scheme, kept as a reference path)    */
+    ADM_OPT_TILE_TRIS = 2,    /* triangles per tile of the tiled assembler      */
+    ADM_OPT_BLOCK_THREADS = 3 /* threads per block of the element kernels       */
+} adm_option;
+
+/* --- creation ---------------------------------------------------------- */
+
+/* One mesh.  V: nV x 3 rest positions (host, double); F: nF x 3 vertex
+ * indices (host, int32, counter-clockwise); var_dim: 3 for positions, 2 for
+ * a UV map.  Builds edges, hinges (canonical order: e0 < e1, face A holds
+ * e0->e1), rest data, the block patterns and the work tables, and uploads
+ * them to the current device.  Synchronous.  Errors: ADM_ERR_ARG,
+ * ADM_ERR_MESH, ADM_ERR_OOM, ADM_ERR_CUDA.  On error *out is NULL. */
+adm_status adm_create(const double *V, int64_t nV, const int32_t *F, int64_t nF,
+                      int32_t var_dim, adm_handle *out);
+
+/* A batch of n_mesh independent meshes concatenated: mesh m owns vertices
+ * [v_off[m], v_off[m+1]) and faces [f_off[m], f_off[m+1]); F holds global
+ * (batch-wide) vertex indices.  v_off, f_off: n_mesh + 1 entries (host). */
+adm_status adm_create_batch(const double *V, const int64_t *v_off, const int32_t *F,
+                            const int64_t *f_off, int32_t n_mesh, int32_t var_dim,
+                            adm_handle *out);
+
+/* Material parameters of an energy (host array, copied).  Membranes
+ * (ADM_STVK_MEMBRANE, ADM_NH_MEMBRANE, ADM_MLP_MEMBRANE): {E, nu, thickness};
+ * ADM_HINGE_BENDING: {k_b, h}; ADM_SHELL: {E, nu, thickness, k_b, h}.
+ * Missing trailing values keep their defaults E = 1e5, nu = 0.3,
+ * thickness = 1e-3, h = 1, k_b = E t^3 / (12 (1 - nu^2)).  Lame parameters
+ * are the plane-stress ones, mu = E / (2 (1 + nu)), lambda = E nu / (1 - nu^2). */
+adm_status adm_set_params(adm_handle h, adm_energy energy, const double *p, int32_t np);
+
+adm_status adm_set_option(adm_handle h, adm_option option, int64_t value);
+
+/* --- patterns ------------------------------------------------------------ */
+
+/* Block-sparse (BSR) pattern of the Hessian of `energy`: *block = var_dim,
+ * *n_rows = number of vertices, *nnzb = number of blocks, and device
+ * pointers to row_ptr (n_rows + 1, int32) and col (nnzb, int32).  Builds the
+ * pattern on first use (synchronous, allocates).  Any output may be NULL. */
+adm_status adm_pattern(adm_handle h, adm_energy energy, int32_t *block, int64_t *n_rows,
+                       int64_t *nnzb, const int32_t **row_ptr_dev, const int32_t **col_dev);
+
+/* CSR pattern of the residual Jacobian of a vector-valued energy
+ * (ADM_ARAP2D_RESIDUAL): rows 4t + r (triangle t, residual r), columns
+ * v * 2 + d sorted ascending, 6 per row.  Device pointers; any output may
+ * be NULL. */
+adm_status adm_jac_pattern(adm_handle h, adm_energy energy, int64_t *n_rows, int64_t *n_cols,
+                           int64_t *nnz, const int32_t **row_ptr_dev, const int32_t **col_dev);
+
+/* Canonical hinge list (device, nH x 4 int32: e0, e1, a, b) and the slot map
+ * of `energy`: for every element in canonical order (triangles in input
+ * order, then hinges) and every ordered local vertex pair (a, b), the index
+ * of block (v_a, v_b) in the BSR pattern (device int32, n_elem x nv x nv). */
+adm_status adm_hinges(adm_handle h, const int32_t **hinges_dev, int64_t *n_hinges);
+adm_status adm_slot_map(adm_handle h, adm_energy energy, const int32_t **slots_dev,
+                        int64_t *n_entries);
+
+/* --- evaluation -------------------------------------------------------- */
+
+/* Energy, gradient and Hessian of one energy at x (device, n_rows * var_dim
+ * of the precision's type).  energy_dev: device double, receives F(x)
+ * summed over every mesh of the handle (nullable); grad_dev: device,
+ * n_rows * var_dim (nullable); bsr_vals_dev: device, nnzb * var_dim^2
+ * (nullable).  With both grad_dev and bsr_vals_dev NULL the call runs the
+ * passive (value-only) mode; with bsr_vals_dev NULL the gradient-only mode.
+ * Errors: ADM_ERR_ARG, ADM_ERR_UNSUPPORTED, ADM_ERR_CUDA (launch). */
+adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
+                    double *energy_dev, void *grad_dev, void *bsr_vals_dev, void *stream);
+
+/* Batched form: per-mesh energies (device, n_mesh doubles, nullable) and
+ * per-mesh gradient 2-norms in FP64 (device, n_mesh doubles, nullable),
+ * plus the batch gradient and Hessian as in adm_eval. */
+adm_status adm_eval_batch(adm_handle h, adm_energy energy, adm_precision prec,
+                          const void *x_dev, double *energy_per_mesh_dev, double *gnorm_dev,
+                          void *grad_dev, void *bsr_vals_dev, void *stream);
+
+/* Same work as adm_eval_batch with HOST buffers: copies x host->device,
+ * evaluates, copies the requested outputs device->host, and returns after
+ * the copies completed (synchronous).  Uses library-owned device staging
+ * buffers (allocated on first use) and the library's own stream.  Host
+ * buffers may be pageable; pinned buffers make the copies faster. */
+adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision prec,
+                               const void *x_host, double *energy_per_mesh_host,
+                               double *gnorm_host, void *grad_host, void *bsr_vals_host);
+
+/* Residual r (device, 4 nT), CSR Jacobian values (device, 24 nT, in the
+ * order of adm_jac_pattern) and the Gauss-Newton matrix J^T J assembled into
+ * the 2 x 2 BSR pattern of the triangle stencil (device, nullable). */
+adm_status adm_eval_jacobian(adm_handle h, adm_energy energy, adm_precision prec,
+                             const void *x_dev, void *r_dev, void *jac_vals_dev,
+                             void *jtj_bsr_vals_dev, void *stream);
+
+/* Device status word of the last evaluation on this handle: ADM_OK,
+ * ADM_ERR_DOMAIN or ADM_ERR_TIMEOUT.  Call after synchronising the stream of
+ * that evaluation; this call itself blocks until the status is read. */
+adm_status adm_get_status(adm_handle h);
+
+const char *adm_strerror(adm_status s);
+
+/* Frees every device and host allocation of the handle (synchronous). */
+void adm_destroy(adm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADM_H */

@@ -1,0 +1,214 @@
+"""Python binding of libadm (C ABI in include/adm.h).
+
+Argument marshalling only: every step of the differentiation and assembly
+runs in the library's sm_103a kernels.  Device memory and streams come from
+PyTorch; buffers are passed to the library as raw pointers.
+
+The shared library is built in-tree by ``__graft_entry__.build()`` (or
+``paper_2509_00406_gb300._build.build()``).  If it is missing, ``lib()``
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "_build", "libadm.so")
+HEADER = os.path.join(ROOT, "include", "adm.h")
+
+# adm_energy
+SYMDIR2D, STVK_MEMBRANE, HINGE_BENDING, SHELL, NH_MEMBRANE, MLP_MEMBRANE, AREA = 1, 2, 3, 4, 5, 6, 7
+ARAP2D_RESIDUAL = 16
+# adm_precision
+FP64, FP32 = 0, 1
+# adm_option
+OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS = 1, 2, 3
+
+STATUS = {0: "ADM_OK", -1: "ADM_ERR_ARG", -2: "ADM_ERR_MESH", -3: "ADM_ERR_DOMAIN",
+          -4: "ADM_ERR_CUDA", -5: "ADM_ERR_TIMEOUT", -6: "ADM_ERR_OOM", -7: "ADM_ERR_UNSUPPORTED"}
+
+_lib = None
+
+
+class AdmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/adm.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(adm_[a-z_0-9]+)\s*\(", txt)))
+
+
+def lib():
+    """Load libadm.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    i32, i64, vp, dp = C.c_int32, C.c_int64, C.c_void_p, C.POINTER(C.c_double)
+    pp = C.POINTER(C.c_void_p)
+    sig = {
+        "adm_create": (i32, [vp, i64, vp, i64, i32, pp]),
+        "adm_create_batch": (i32, [vp, vp, vp, vp, i32, i32, pp]),
+        "adm_set_params": (i32, [vp, i32, vp, i32]),
+        "adm_set_option": (i32, [vp, i32, i64]),
+        "adm_pattern": (i32, [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), pp, pp]),
+        "adm_jac_pattern": (i32, [vp, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), pp, pp]),
+        "adm_hinges": (i32, [vp, pp, C.POINTER(i64)]),
+        "adm_slot_map": (i32, [vp, i32, pp, C.POINTER(i64)]),
+        "adm_eval": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
+        "adm_eval_batch": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
+        "adm_eval_batch_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
+        "adm_eval_jacobian": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
+        "adm_get_status": (i32, [vp]),
+        "adm_strerror": (C.c_char_p, [i32]),
+        "adm_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise AdmError(status, where)
+
+
+def _ptr(t):
+    """Raw pointer of a torch tensor / numpy array / None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return C.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(C.c_void_p)
+
+
+class _DevView:
+    """__cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True),
+                                         "version": 3}
+
+
+def _dev_copy(ptr, n: int, typestr: str = "<i4"):
+    import torch
+    if n == 0:
+        return torch.zeros(0, dtype=torch.int32, device="cuda")
+    return torch.as_tensor(_DevView(int(ptr), int(n), typestr), device="cuda").clone()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Mesh:
+    """A libadm handle over one mesh or a batch of meshes."""
+
+    def __init__(self, rest, faces, var_dim: int = 3, v_off=None, f_off=None):
+        L = lib()
+        rest = np.ascontiguousarray(rest, dtype=np.float64)
+        faces = np.ascontiguousarray(faces, dtype=np.int32)
+        self.var_dim = int(var_dim)
+        self.nV = int(rest.shape[0])
+        self.nT = int(faces.shape[0])
+        h = C.c_void_p()
+        if v_off is None:
+            _check(L.adm_create(_ptr(rest), self.nV, _ptr(faces), self.nT, self.var_dim, C.byref(h)),
+                   "adm_create")
+            self.n_mesh = 1
+        else:
+            vo = np.ascontiguousarray(v_off, dtype=np.int64)
+            fo = np.ascontiguousarray(f_off, dtype=np.int64)
+            self.n_mesh = int(vo.shape[0] - 1)
+            _check(L.adm_create_batch(_ptr(rest), _ptr(vo), _ptr(faces), _ptr(fo), self.n_mesh,
+                                      self.var_dim, C.byref(h)), "adm_create_batch")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().adm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration ---------------------------------------------------
+    def set_params(self, energy: int, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        _check(lib().adm_set_params(self._h, energy, _ptr(p), int(p.shape[0])), "adm_set_params")
+
+    def set_option(self, option: int, value: int):
+        _check(lib().adm_set_option(self._h, option, int(value)), "adm_set_option")
+
+    # -- patterns --------------------------------------------------------
+    def pattern(self, energy: int):
+        """(block, n_rows, nnzb, row_ptr, col) with row_ptr/col as int32 cuda tensors."""
+        b, nr, nz = C.c_int32(), C.c_int64(), C.c_int64()
+        rp, col = C.c_void_p(), C.c_void_p()
+        _check(lib().adm_pattern(self._h, energy, C.byref(b), C.byref(nr), C.byref(nz), C.byref(rp),
+                                 C.byref(col)), "adm_pattern")
+        return (b.value, nr.value, nz.value, _dev_copy(rp.value, nr.value + 1),
+                _dev_copy(col.value, nz.value))
+
+    def jac_pattern(self, energy: int = ARAP2D_RESIDUAL):
+        nr, nc, nz = C.c_int64(), C.c_int64(), C.c_int64()
+        rp, col = C.c_void_p(), C.c_void_p()
+        _check(lib().adm_jac_pattern(self._h, energy, C.byref(nr), C.byref(nc), C.byref(nz), C.byref(rp),
+                                     C.byref(col)), "adm_jac_pattern")
+        return nr.value, nc.value, nz.value, _dev_copy(rp.value, nr.value + 1), _dev_copy(col.value, nz.value)
+
+    def hinges(self):
+        p, n = C.c_void_p(), C.c_int64()
+        _check(lib().adm_hinges(self._h, C.byref(p), C.byref(n)), "adm_hinges")
+        return _dev_copy(p.value, 4 * n.value).reshape(-1, 4)
+
+    def slot_map(self, energy: int):
+        p, n = C.c_void_p(), C.c_int64()
+        _check(lib().adm_slot_map(self._h, energy, C.byref(p), C.byref(n)), "adm_slot_map")
+        return _dev_copy(p.value, n.value)
+
+    # -- evaluation --------------------------------------------------------
+    def eval(self, energy: int, prec: int, x, energy_out=None, grad=None, bsr=None, stream=None):
+        _check(lib().adm_eval(self._h, energy, prec, _ptr(x), _ptr(energy_out), _ptr(grad), _ptr(bsr),
+                              _stream(stream)), "adm_eval")
+
+    def eval_batch(self, energy: int, prec: int, x, energy_per_mesh=None, gnorm=None, grad=None,
+                   bsr=None, stream=None):
+        _check(lib().adm_eval_batch(self._h, energy, prec, _ptr(x), _ptr(energy_per_mesh), _ptr(gnorm),
+                                    _ptr(grad), _ptr(bsr), _stream(stream)), "adm_eval_batch")
+
+    def eval_batch_host(self, energy: int, prec: int, x_host, energy_per_mesh=None, gnorm=None,
+                        grad=None, bsr=None):
+        _check(lib().adm_eval_batch_host(self._h, energy, prec, _ptr(x_host), _ptr(energy_per_mesh),
+                                         _ptr(gnorm), _ptr(grad), _ptr(bsr)), "adm_eval_batch_host")
+
+    def eval_jacobian(self, energy: int, prec: int, x, r, jac_vals=None, jtj=None, stream=None):
+        _check(lib().adm_eval_jacobian(self._h, energy, prec, _ptr(x), _ptr(r), _ptr(jac_vals), _ptr(jtj),
+                                       _stream(stream)), "adm_eval_jacobian")
+
+    def status(self) -> int:
+        return int(lib().adm_get_status(self._h))
+
+
+def strerror(status: int) -> str:
+    return lib().adm_strerror(status).decode()

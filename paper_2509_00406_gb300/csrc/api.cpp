@@ -1,0 +1,505 @@
+// api.cpp -- the C ABI of libadm (declared in include/adm.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace adm;
+
+namespace {
+
+constexpr int kElemThreads = 128;  // must match the kernels' block size
+constexpr int kChunk = 8192;        // gradient entries per norm chunk
+
+template <typename P>
+adm_status dev_alloc(adm_ctx *h, P **out, size_t bytes)
+{
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return ADM_ERR_OOM;
+    }
+    h->owned.push_back(p);
+    *out = (P *)p;
+    return ADM_OK;
+}
+
+template <typename P>
+adm_status upload(adm_ctx *h, P **out, const void *src, size_t bytes)
+{
+    adm_status s = dev_alloc(h, out, bytes);
+    if (s != ADM_OK) return s;
+    if (bytes && cudaMemcpy(*out, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return ADM_ERR_CUDA;
+    return ADM_OK;
+}
+
+void dev_free(adm_ctx *h, void *p)
+{
+    if (!p) return;
+    auto it = std::find(h->owned.begin(), h->owned.end(), p);
+    if (it != h->owned.end()) h->owned.erase(it);
+    cudaFree(p);
+}
+
+// SoA rest arrays in both precisions
+adm_status upload_rest(adm_ctx *h, void **dst, const std::vector<std::vector<double>> &fields, int64_t n)
+{
+    std::vector<double> d(fields.size() * n);
+    std::vector<float> f(fields.size() * n);
+    for (size_t k = 0; k < fields.size(); ++k)
+        for (int64_t i = 0; i < n; ++i) {
+            d[k * n + i] = fields[k][i];
+            f[k * n + i] = (float)fields[k][i];
+        }
+    adm_status s = upload(h, &dst[ADM_FP64], d.data(), d.size() * sizeof(double));
+    if (s != ADM_OK) return s;
+    return upload(h, &dst[ADM_FP32], f.data(), f.size() * sizeof(float));
+}
+
+// element blocks of `threads` elements that never straddle a mesh
+adm_status build_blocks(adm_ctx *h, BlockTable &bt, const std::vector<int64_t> &elem_off, int threads)
+{
+    std::vector<int32_t> b, e;
+    bt.mesh_block_off.assign(elem_off.size(), 0);
+    for (size_t k = 0; k + 1 < elem_off.size(); ++k) {
+        for (int64_t s = elem_off[k]; s < elem_off[k + 1]; s += threads) {
+            b.push_back((int32_t)s);
+            e.push_back((int32_t)std::min<int64_t>(s + threads, elem_off[k + 1]));
+        }
+        bt.mesh_block_off[k + 1] = (int32_t)b.size();
+    }
+    bt.n_blocks = (int32_t)b.size();
+    bt.threads = threads;
+    adm_status s;
+    if ((s = upload(h, &bt.d_begin, b.data(), b.size() * 4)) != ADM_OK) return s;
+    if ((s = upload(h, &bt.d_end, e.data(), e.size() * 4)) != ADM_OK) return s;
+    if ((s = upload(h, &bt.d_mesh_block_off, bt.mesh_block_off.data(), bt.mesh_block_off.size() * 4)) != ADM_OK)
+        return s;
+    bt.built = true;
+    return ADM_OK;
+}
+
+adm_status ensure_epart(adm_ctx *h)
+{
+    size_t need = (size_t)h->tri_blocks.n_blocks + (size_t)h->hinge_blocks.n_blocks + 1;
+    if (need <= h->epart_cap) return ADM_OK;
+    dev_free(h, h->d_epart);
+    h->d_epart = nullptr;
+    adm_status s = dev_alloc(h, &h->d_epart, need * sizeof(double));
+    if (s == ADM_OK) h->epart_cap = need;
+    return s;
+}
+
+adm_status build_pattern(adm_ctx *h, int kind)
+{
+    Pattern &P = h->pat[kind];
+    if (P.built) return ADM_OK;
+    std::vector<int32_t> ts, hs;
+    mesh_build_pattern(h->m, kind == PAT_SHELL, P.row_ptr, P.col);
+    P.nnzb = (int64_t)P.col.size();
+    mesh_build_slots(h->m, P.row_ptr, P.col, kind == PAT_SHELL, ts, hs);
+    adm_status s;
+    if ((s = upload(h, &P.d_row_ptr, P.row_ptr.data(), P.row_ptr.size() * 4)) != ADM_OK) return s;
+    if ((s = upload(h, &P.d_col, P.col.data(), P.col.size() * 4)) != ADM_OK) return s;
+    if ((s = upload(h, &P.d_tri_slots, ts.data(), ts.size() * 4)) != ADM_OK) return s;
+    if (kind == PAT_SHELL)
+        if ((s = upload(h, &P.d_hinge_slots, hs.data(), hs.size() * 4)) != ADM_OK) return s;
+    P.built = true;
+    return ADM_OK;
+}
+
+// hinges, their rest data, block table and the shell pattern
+adm_status ensure_shell(adm_ctx *h)
+{
+    if (h->pat[PAT_SHELL].built) return ADM_OK;
+    if (h->m.vdim != 3) return ADM_ERR_UNSUPPORTED;
+    adm_status s = mesh_build_hinges(h->m);
+    if (s != ADM_OK) return s;
+    const int64_t nH = h->m.nH();
+    if (!h->d_H && (s = upload(h, &h->d_H, h->m.H.data(), h->m.H.size() * 4)) != ADM_OK) return s;
+    std::vector<double> abar3(nH);
+    for (int64_t i = 0; i < nH; ++i) abar3[i] = h->m.h_abar[i] / 3.0;
+    if ((s = upload_rest(h, h->d_hinge_rest, {h->m.h_thetabar, abar3}, nH)) != ADM_OK) return s;
+    if ((s = build_blocks(h, h->hinge_blocks, h->m.h_off, kElemThreads)) != ADM_OK) return s;
+    if ((s = ensure_epart(h)) != ADM_OK) return s;
+    return build_pattern(h, PAT_SHELL);
+}
+
+bool energy_ok(int energy, int vdim)
+{
+    switch (energy) {
+    case ADM_SYMDIR2D:
+    case ADM_ARAP2D_RESIDUAL: return vdim == 2;
+    case ADM_STVK_MEMBRANE:
+    case ADM_HINGE_BENDING:
+    case ADM_SHELL:
+    case ADM_NH_MEMBRANE:
+    case ADM_AREA: return vdim == 3;
+    default: return false;
+    }
+}
+
+bool needs_hinges(int energy) { return energy == ADM_HINGE_BENDING || energy == ADM_SHELL; }
+
+adm_status prepare(adm_ctx *h, int energy)
+{
+    if (!energy_ok(energy, h->m.vdim)) return ADM_ERR_UNSUPPORTED;
+    if (needs_hinges(energy)) return ensure_shell(h);
+    return build_pattern(h, PAT_TRI);
+}
+
+cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+extern "C" {
+
+adm_status adm_create(const double *V, int64_t nV, const int32_t *F, int64_t nF, int32_t var_dim,
+                      adm_handle *out)
+{
+    int64_t v_off[2] = {0, nV}, f_off[2] = {0, nF};
+    return adm_create_batch(V, v_off, F, f_off, 1, var_dim, out);
+}
+
+adm_status adm_create_batch(const double *V, const int64_t *v_off, const int32_t *F,
+                            const int64_t *f_off, int32_t n_mesh, int32_t var_dim, adm_handle *out)
+{
+    if (!out) return ADM_ERR_ARG;
+    *out = nullptr;
+    if (!V || !v_off || !F || !f_off || n_mesh <= 0 || (var_dim != 2 && var_dim != 3)) return ADM_ERR_ARG;
+    adm_ctx *h = new (std::nothrow) adm_ctx();
+    if (!h) return ADM_ERR_OOM;
+    HostMesh &m = h->m;
+    m.n_mesh = n_mesh;
+    m.vdim = var_dim;
+    m.v_off.assign(v_off, v_off + n_mesh + 1);
+    m.f_off.assign(f_off, f_off + n_mesh + 1);
+    m.nV = m.v_off[n_mesh];
+    m.nT = m.f_off[n_mesh];
+    adm_status s = ADM_OK;
+    if (m.nV <= 0 || m.nT <= 0) s = ADM_ERR_ARG;
+    if (s == ADM_OK) {
+        m.V.assign(V, V + 3 * m.nV);
+        m.F.assign(F, F + 3 * m.nT);
+        s = mesh_validate(m);
+    }
+    if (s == ADM_OK) {
+        mesh_rest_triangles(m);
+        for (int64_t t = 0; t < m.nT; ++t)
+            if (!(m.tri_area[t] > 0.0) || !std::isfinite(m.tri_Dinv[4 * t + 1])) {
+                s = ADM_ERR_MESH;
+                break;
+            }
+    }
+    if (s == ADM_OK && cudaGetDevice(&h->device) != cudaSuccess) s = ADM_ERR_CUDA;
+    if (s == ADM_OK) s = dev_alloc(h, &h->d_status, sizeof(int));
+    if (s == ADM_OK && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) s = ADM_ERR_CUDA;
+    if (s == ADM_OK) s = upload(h, &h->d_F, m.F.data(), m.F.size() * 4);
+    if (s == ADM_OK) {
+        std::vector<std::vector<double>> fields(5, std::vector<double>(m.nT));
+        for (int64_t t = 0; t < m.nT; ++t) {
+            for (int k = 0; k < 4; ++k) fields[k][t] = m.tri_Dinv[4 * t + k];
+            fields[4][t] = m.tri_area[t];
+        }
+        s = upload_rest(h, h->d_tri_rest, fields, m.nT);
+    }
+    if (s == ADM_OK) s = build_blocks(h, h->tri_blocks, m.f_off, kElemThreads);
+    if (s == ADM_OK) s = ensure_epart(h);
+    if (s == ADM_OK) {
+        // gradient-norm chunks
+        std::vector<int32_t> cb, ce, co(1, 0);
+        for (int k = 0; k < n_mesh; ++k) {
+            int64_t a = m.v_off[k] * var_dim, b = m.v_off[k + 1] * var_dim;
+            for (int64_t c = a; c < b; c += kChunk) {
+                cb.push_back((int32_t)c);
+                ce.push_back((int32_t)std::min<int64_t>(c + kChunk, b));
+            }
+            co.push_back((int32_t)cb.size());
+        }
+        h->chunks.n_chunks = (int32_t)cb.size();
+        s = upload(h, &h->chunks.d_begin, cb.data(), cb.size() * 4);
+        if (s == ADM_OK) s = upload(h, &h->chunks.d_end, ce.data(), ce.size() * 4);
+        if (s == ADM_OK) s = upload(h, &h->chunks.d_mesh_chunk_off, co.data(), co.size() * 4);
+        if (s == ADM_OK) s = dev_alloc(h, &h->d_gpart, cb.size() * sizeof(double));
+        h->chunks.built = true;
+    }
+    if (s == ADM_OK) s = build_pattern(h, PAT_TRI);
+    if (s != ADM_OK) {
+        adm_destroy(h);
+        return s;
+    }
+    *out = h;
+    return ADM_OK;
+}
+
+adm_status adm_set_params(adm_handle h, adm_energy energy, const double *p, int32_t np)
+{
+    if (!h || np < 0 || (np > 0 && !p)) return ADM_ERR_ARG;
+    EnergyParams q;
+    if (energy == ADM_HINGE_BENDING) {
+        if (np > 2) return ADM_ERR_ARG;
+        if (np > 0) q.kb = p[0];
+        if (np > 1) q.h = p[1];
+    } else if (energy == ADM_SHELL || energy == ADM_STVK_MEMBRANE || energy == ADM_NH_MEMBRANE ||
+               energy == ADM_MLP_MEMBRANE) {
+        if (np > (energy == ADM_SHELL ? 5 : 3)) return ADM_ERR_ARG;
+        if (np > 0) q.E = p[0];
+        if (np > 1) q.nu = p[1];
+        if (np > 2) q.t = p[2];
+        if (np > 3) q.kb = p[3];
+        if (np > 4) q.h = p[4];
+    } else if (np != 0) {
+        return ADM_ERR_ARG;
+    }
+    h->params[energy] = q;
+    return ADM_OK;
+}
+
+adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
+{
+    if (!h) return ADM_ERR_ARG;
+    switch (option) {
+    case ADM_OPT_ASSEMBLER:
+        if (value != 1) return ADM_ERR_UNSUPPORTED;
+        h->assembler = (int)value;
+        return ADM_OK;
+    case ADM_OPT_TILE_TRIS:
+        if (value < 32 || value > 4096) return ADM_ERR_ARG;
+        h->tile_tris = (int)value;
+        return ADM_OK;
+    case ADM_OPT_BLOCK_THREADS:
+        if (value != kElemThreads) return ADM_ERR_UNSUPPORTED;
+        return ADM_OK;
+    default: return ADM_ERR_ARG;
+    }
+}
+
+adm_status adm_pattern(adm_handle h, adm_energy energy, int32_t *block, int64_t *n_rows, int64_t *nnzb,
+                       const int32_t **row_ptr_dev, const int32_t **col_dev)
+{
+    if (!h) return ADM_ERR_ARG;
+    if (energy == ADM_ARAP2D_RESIDUAL) energy = ADM_SYMDIR2D;  // J^T J lives on the triangle pattern
+    adm_status s = prepare(h, energy);
+    if (s != ADM_OK) return s;
+    const Pattern &P = h->pat[needs_hinges(energy) ? PAT_SHELL : PAT_TRI];
+    if (block) *block = h->m.vdim;
+    if (n_rows) *n_rows = h->m.nV;
+    if (nnzb) *nnzb = P.nnzb;
+    if (row_ptr_dev) *row_ptr_dev = P.d_row_ptr;
+    if (col_dev) *col_dev = P.d_col;
+    return ADM_OK;
+}
+
+adm_status adm_jac_pattern(adm_handle h, adm_energy energy, int64_t *n_rows, int64_t *n_cols, int64_t *nnz,
+                           const int32_t **row_ptr_dev, const int32_t **col_dev)
+{
+    if (!h) return ADM_ERR_ARG;
+    if (energy != ADM_ARAP2D_RESIDUAL || h->m.vdim != 2) return ADM_ERR_UNSUPPORTED;
+    const HostMesh &m = h->m;
+    if (!h->d_jac_row_ptr) {
+        std::vector<int32_t> rp(4 * m.nT + 1), col(24 * m.nT);
+        for (int64_t r = 0; r <= 4 * m.nT; ++r) rp[r] = (int32_t)(6 * r);
+        for (int64_t t = 0; t < m.nT; ++t) {
+            int32_t v[3] = {m.F[3 * t], m.F[3 * t + 1], m.F[3 * t + 2]};
+            std::sort(v, v + 3);
+            for (int i = 0; i < 4; ++i)
+                for (int a = 0; a < 3; ++a)
+                    for (int d = 0; d < 2; ++d) col[24 * t + 6 * i + 2 * a + d] = 2 * v[a] + d;
+        }
+        adm_status s = upload(h, &h->d_jac_row_ptr, rp.data(), rp.size() * 4);
+        if (s == ADM_OK) s = upload(h, &h->d_jac_col, col.data(), col.size() * 4);
+        if (s != ADM_OK) return s;
+    }
+    if (n_rows) *n_rows = 4 * m.nT;
+    if (n_cols) *n_cols = 2 * m.nV;
+    if (nnz) *nnz = 24 * m.nT;
+    if (row_ptr_dev) *row_ptr_dev = h->d_jac_row_ptr;
+    if (col_dev) *col_dev = h->d_jac_col;
+    return ADM_OK;
+}
+
+adm_status adm_hinges(adm_handle h, const int32_t **hinges_dev, int64_t *n_hinges)
+{
+    if (!h) return ADM_ERR_ARG;
+    adm_status s = ensure_shell(h);
+    if (s != ADM_OK) return s;
+    if (hinges_dev) *hinges_dev = h->d_H;
+    if (n_hinges) *n_hinges = h->m.nH();
+    return ADM_OK;
+}
+
+adm_status adm_slot_map(adm_handle h, adm_energy energy, const int32_t **slots_dev, int64_t *n_entries)
+{
+    if (!h) return ADM_ERR_ARG;
+    adm_status s = prepare(h, energy);
+    if (s != ADM_OK) return s;
+    const bool hin = needs_hinges(energy);
+    Pattern &P = h->pat[hin ? PAT_SHELL : PAT_TRI];
+    const bool tri = energy != ADM_HINGE_BENDING;
+    const int64_t nt = tri ? 9 * h->m.nT : 0, nh = hin ? 16 * h->m.nH() : 0;
+    if (!P.d_all_slots || P.n_all_slots != nt + nh) {
+        dev_free(h, P.d_all_slots);
+        P.d_all_slots = nullptr;
+        if ((s = dev_alloc(h, &P.d_all_slots, (nt + nh) * 4)) != ADM_OK) return s;
+        if (nt && cudaMemcpy(P.d_all_slots, P.d_tri_slots, nt * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+            return ADM_ERR_CUDA;
+        if (nh && cudaMemcpy(P.d_all_slots + nt, P.d_hinge_slots, nh * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+            return ADM_ERR_CUDA;
+        P.n_all_slots = nt + nh;
+    }
+    if (slots_dev) *slots_dev = P.d_all_slots;
+    if (n_entries) *n_entries = nt + nh;
+    return ADM_OK;
+}
+
+adm_status adm_eval_batch(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
+                          double *energy_per_mesh_dev, double *gnorm_dev, void *grad_dev, void *bsr_vals_dev,
+                          void *stream)
+{
+    if (!h || !x_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
+    if (gnorm_dev && !grad_dev) return ADM_ERR_ARG;
+    if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE) return ADM_ERR_UNSUPPORTED;
+    adm_status s = prepare(h, energy);
+    if (s != ADM_OK) return s;
+    EvalArgs a;
+    a.energy = energy;
+    a.prec = prec;
+    a.vdim = h->m.vdim;
+    a.x = x_dev;
+    a.grad = grad_dev;
+    a.bsr = bsr_vals_dev;
+    a.energy_total = nullptr;
+    a.energy_per_mesh = energy_per_mesh_dev;
+    a.gnorm_per_mesh = gnorm_dev;
+    a.stream = as_stream(stream);
+    return launch_eval(h, a);
+}
+
+adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev, double *energy_dev,
+                    void *grad_dev, void *bsr_vals_dev, void *stream)
+{
+    if (!h || !x_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
+    if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE) return ADM_ERR_UNSUPPORTED;
+    adm_status s = prepare(h, energy);
+    if (s != ADM_OK) return s;
+    EvalArgs a;
+    a.energy = energy;
+    a.prec = prec;
+    a.vdim = h->m.vdim;
+    a.x = x_dev;
+    a.grad = grad_dev;
+    a.bsr = bsr_vals_dev;
+    a.energy_total = energy_dev;
+    a.energy_per_mesh = nullptr;
+    a.gnorm_per_mesh = nullptr;
+    a.stream = as_stream(stream);
+    return launch_eval(h, a);
+}
+
+adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision prec, const void *x_host,
+                               double *energy_per_mesh_host, double *gnorm_host, void *grad_host,
+                               void *bsr_vals_host)
+{
+    if (!h || !x_host || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
+    adm_status s = prepare(h, energy);
+    if (s != ADM_OK) return s;
+    const HostMesh &m = h->m;
+    const size_t es = prec == ADM_FP32 ? 4 : 8;
+    const size_t xb = es * m.nV * m.vdim;
+    const int64_t nnzb = h->pat[needs_hinges(energy) ? PAT_SHELL : PAT_TRI].nnzb;
+    const size_t bb = es * nnzb * m.vdim * m.vdim;
+    if (!h->own_stream && cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    auto grow = [&](void **p, size_t &cap, size_t need) -> adm_status {
+        if (need <= cap) return ADM_OK;
+        dev_free(h, *p);
+        *p = nullptr;
+        cap = 0;
+        adm_status r = dev_alloc(h, p, need);
+        if (r == ADM_OK) cap = need;
+        return r;
+    };
+    if ((s = grow(&h->d_stage_x, h->stage_x_bytes, xb)) != ADM_OK) return s;
+    bool need_grad = grad_host || gnorm_host;
+    if (need_grad && (s = grow(&h->d_stage_grad, h->stage_grad_bytes, xb)) != ADM_OK) return s;
+    if (bsr_vals_host && (s = grow(&h->d_stage_bsr, h->stage_bsr_bytes, bb)) != ADM_OK) return s;
+    if (!h->d_stage_e) {
+        if ((s = dev_alloc(h, &h->d_stage_e, m.n_mesh * sizeof(double))) != ADM_OK) return s;
+        if ((s = dev_alloc(h, &h->d_stage_gn, m.n_mesh * sizeof(double))) != ADM_OK) return s;
+    }
+    cudaStream_t st = h->own_stream;
+    if (cudaMemcpyAsync(h->d_stage_x, x_host, xb, cudaMemcpyHostToDevice, st) != cudaSuccess) return ADM_ERR_CUDA;
+    s = adm_eval_batch(h, energy, prec, h->d_stage_x, h->d_stage_e, gnorm_host ? h->d_stage_gn : nullptr,
+                       need_grad ? h->d_stage_grad : nullptr, bsr_vals_host ? h->d_stage_bsr : nullptr, st);
+    if (s != ADM_OK) return s;
+    if (energy_per_mesh_host &&
+        cudaMemcpyAsync(energy_per_mesh_host, h->d_stage_e, m.n_mesh * sizeof(double), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    if (gnorm_host && cudaMemcpyAsync(gnorm_host, h->d_stage_gn, m.n_mesh * sizeof(double),
+                                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    if (grad_host && cudaMemcpyAsync(grad_host, h->d_stage_grad, xb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    if (bsr_vals_host &&
+        cudaMemcpyAsync(bsr_vals_host, h->d_stage_bsr, bb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+adm_status adm_eval_jacobian(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev, void *r_dev,
+                             void *jac_vals_dev, void *jtj_bsr_vals_dev, void *stream)
+{
+    if (!h || !x_dev || !r_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
+    if (energy != ADM_ARAP2D_RESIDUAL || h->m.vdim != 2) return ADM_ERR_UNSUPPORTED;
+    adm_status s = build_pattern(h, PAT_TRI);
+    if (s != ADM_OK) return s;
+    return launch_jacobian(h, prec, x_dev, r_dev, jac_vals_dev, jtj_bsr_vals_dev, as_stream(stream));
+}
+
+adm_status adm_get_status(adm_handle h)
+{
+    if (!h) return ADM_ERR_ARG;
+    int st = 0;
+    if (cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ADM_ERR_CUDA;
+    if (st & ST_TIMEOUT) return ADM_ERR_TIMEOUT;
+    if (st & ST_DOMAIN) return ADM_ERR_DOMAIN;
+    return ADM_OK;
+}
+
+const char *adm_strerror(adm_status s)
+{
+    switch (s) {
+    case ADM_OK: return "ok";
+    case ADM_ERR_ARG: return "invalid argument";
+    case ADM_ERR_MESH: return "invalid mesh (index range, degenerate rest triangle, non-manifold or "
+                              "inconsistently oriented edge)";
+    case ADM_ERR_DOMAIN: return "element outside the energy's domain (folded triangle, degenerate hinge, "
+                                "non-finite value)";
+    case ADM_ERR_CUDA: return "CUDA runtime error";
+    case ADM_ERR_TIMEOUT: return "bounded device wait ran out";
+    case ADM_ERR_OOM: return "device allocation failed";
+    case ADM_ERR_UNSUPPORTED: return "unsupported energy / precision / var_dim combination";
+    }
+    return "unknown status";
+}
+
+void adm_destroy(adm_handle h)
+{
+    if (!h) return;
+    if (h->own_stream) {
+        cudaStreamSynchronize(h->own_stream);
+        cudaStreamDestroy(h->own_stream);
+    }
+    for (void *p : h->owned) cudaFree(p);
+    delete h;
+}
+
+}  // extern "C"

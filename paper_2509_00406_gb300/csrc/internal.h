@@ -1,0 +1,159 @@
+// internal.h -- host-side structures shared by the C ABI, the mesh builder and
+// the kernel launchers of libadm.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "adm.h"
+
+namespace adm {
+
+// stencil sets that own a block pattern
+enum PatternKind { PAT_TRI = 0, PAT_SHELL = 1, PAT_COUNT = 2 };
+
+// device status bits (latched by kernels with atomicOr)
+enum StatusBits { ST_DOMAIN = 1, ST_TIMEOUT = 2 };
+
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// mesh as given by the caller plus everything derived from it on the host
+struct HostMesh {
+    int64_t nV = 0, nT = 0;
+    int vdim = 3;
+    int n_mesh = 1;
+    std::vector<double> V;          // nV * 3 rest positions
+    std::vector<int32_t> F;         // nT * 3
+    std::vector<int64_t> v_off;     // n_mesh + 1
+    std::vector<int64_t> f_off;     // n_mesh + 1
+    // hinges (built on demand): canonical (e0, e1, a, b), e0 < e1, sorted
+    bool hinges_built = false;
+    int hinge_error = 0;
+    std::vector<int32_t> H;         // nH * 4
+    std::vector<int32_t> H_face;    // face A of every hinge
+    std::vector<int64_t> h_off;     // n_mesh + 1 hinge offsets
+    // rest data (double)
+    std::vector<double> tri_Dinv;   // nT * 4, row-major
+    std::vector<double> tri_area;   // nT
+    std::vector<double> h_thetabar; // nH
+    std::vector<double> h_abar;     // nH, mean rest area of the two faces
+    int64_t nH() const { return (int64_t)H.size() / 4; }
+};
+
+struct Pattern {
+    bool built = false;
+    std::vector<int32_t> row_ptr, col;
+    int32_t *d_row_ptr = nullptr, *d_col = nullptr;
+    int64_t nnzb = 0;
+    // slot maps: global block of (v_a, v_b) per element, row-major a * nv + b
+    int32_t *d_tri_slots = nullptr;    // nT * 9
+    int32_t *d_hinge_slots = nullptr;  // nH * 16 (shell pattern only)
+    int32_t *d_all_slots = nullptr;    // concatenation exported by adm_slot_map
+    int64_t n_all_slots = 0;
+};
+
+// element work split into blocks that never straddle two meshes
+struct BlockTable {
+    bool built = false;
+    int threads = 0;
+    int32_t n_blocks = 0;
+    int32_t *d_begin = nullptr;      // n_blocks, first element
+    int32_t *d_end = nullptr;        // n_blocks, one past last
+    std::vector<int32_t> mesh_block_off;  // n_mesh + 1 (host)
+    int32_t *d_mesh_block_off = nullptr;  // device copy
+};
+
+// per-mesh chunks of the gradient used by the FP64 norm reduction
+struct ChunkTable {
+    bool built = false;
+    int32_t n_chunks = 0;
+    int32_t *d_begin = nullptr, *d_end = nullptr;   // in scalar entries
+    int32_t *d_mesh_chunk_off = nullptr;            // n_mesh + 1
+};
+
+struct EnergyParams {
+    double E = 1.0e5, nu = 0.3, t = 1.0e-3, kb = -1.0, h = 1.0;
+    double mu() const { return E / (2.0 * (1.0 + nu)); }
+    double lambda() const { return E * nu / (1.0 - nu * nu); }
+    double kbend() const { return kb >= 0.0 ? kb : E * t * t * t / (12.0 * (1.0 - nu * nu)); }
+};
+
+struct Graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace adm
+
+struct adm_ctx {
+    int device = 0;
+    adm::HostMesh m;
+    // device copies of connectivity
+    int32_t *d_F = nullptr;
+    int32_t *d_H = nullptr;
+    // rest data per precision, SoA: triangles 5 fields (d00,d01,d10,d11,area),
+    // hinges 2 fields (thetabar, abar / 3)
+    void *d_tri_rest[2] = {nullptr, nullptr};
+    void *d_hinge_rest[2] = {nullptr, nullptr};
+    adm::Pattern pat[adm::PAT_COUNT];
+    // ARAP Jacobian column pattern
+    int32_t *d_jac_row_ptr = nullptr, *d_jac_col = nullptr;
+    // element block tables (keyed by threads per block)
+    adm::BlockTable tri_blocks, hinge_blocks;
+    adm::ChunkTable chunks;
+    // scratch for reductions
+    double *d_epart = nullptr;      // energy partial per element block
+    size_t epart_cap = 0;
+    double *d_gpart = nullptr;      // sum of squares partial per gradient chunk
+    double *d_mesh_energy = nullptr;  // n_mesh
+    int *d_status = nullptr;
+    std::map<int, adm::EnergyParams> params;
+    // options
+    int assembler = 1;
+    int tile_tris = 256;
+    int block_threads = 128;
+    // host-buffer path
+    void *d_stage_x = nullptr, *d_stage_grad = nullptr, *d_stage_bsr = nullptr;
+    double *d_stage_e = nullptr, *d_stage_gn = nullptr;
+    size_t stage_x_bytes = 0, stage_grad_bytes = 0, stage_bsr_bytes = 0;
+    cudaStream_t own_stream = nullptr;
+    std::vector<void *> owned;  // every device allocation, freed by destroy
+};
+
+namespace adm {
+
+// mesh.cpp
+adm_status mesh_validate(const HostMesh &m);
+void mesh_rest_triangles(HostMesh &m);
+adm_status mesh_build_hinges(HostMesh &m);
+void mesh_build_pattern(const HostMesh &m, bool with_hinges, std::vector<int32_t> &row_ptr,
+                        std::vector<int32_t> &col);
+void mesh_build_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr,
+                      const std::vector<int32_t> &col, bool hinges, std::vector<int32_t> &tri_slots,
+                      std::vector<int32_t> &hinge_slots);
+
+// kernels.cu
+struct EvalArgs {
+    int energy;          // adm_energy
+    int prec;            // adm_precision
+    int vdim;
+    const void *x;
+    void *grad;          // nullable
+    void *bsr;           // nullable
+    double *energy_total;      // nullable, device
+    double *energy_per_mesh;   // nullable, device
+    double *gnorm_per_mesh;    // nullable, device
+    cudaStream_t stream;
+};
+adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
+adm_status launch_jacobian(adm_ctx *h, int prec, const void *x, void *r, void *jv, void *jtj,
+                           cudaStream_t stream);
+
+}  // namespace adm

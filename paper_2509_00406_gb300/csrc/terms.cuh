@@ -1,0 +1,274 @@
+// terms.cuh -- per-element energy terms written on the forward-mode engine.
+//
+// Every term returns the element's value f, gradient g[K] and packed upper
+// Hessian H[K(K+1)/2] over its local DOFs (vertex-major, k = a * VD + d), the
+// dense local derivatives of Sec. 5.1 that Eq. 2 assembles.  A term is split
+// as f = psi(q(x)): q are a few polynomial invariants of the element's edge
+// vectors (sparse SHDs over the K DOFs), psi a density over them (a dense SHD
+// over M <= 5 seeds); compose() applies the second-order chain rule.
+//
+// Triangle membranes use q = (C11, C22, C12), C = F^T F the right
+// Cauchy-Green tensor of the 3x2 deformation gradient F = [x1-x0, x2-x0] Dm^-1
+// (Dm the rest edges in the triangle's local frame).  The symmetric Dirichlet
+// term uses the same q with the 2x2 UV Jacobian J (|J|^2 = tr C,
+// det(J)^2 = det C).  The hinge uses q = (e.e, e.u, e.v, u.v, det[e,u,v]) with
+// e = x1 - x0, u = xa - x0, v = xb - x1, for which the signed dihedral angle
+// is theta = atan2(-|e| det, (e.v)(e.u) - (e.e)(u.v)).
+#pragma once
+
+#include "ad.cuh"
+
+namespace adm {
+
+// ------------------------------------------------------------ densities --
+// StVK: t A (mu |E|^2 + lambda/2 tr(E)^2), E = (C - I)/2
+template <typename T>
+struct PsiStVK {
+    T mu, lam, s;  // s = thickness * rest area
+    template <class A, class B, class C>
+    ADM_HD auto operator()(const A &c11, const B &c22, const C &c12) const
+    {
+        auto e11 = (c11 - T(1)) * T(0.5);
+        auto e22 = (c22 - T(1)) * T(0.5);
+        auto tr = e11 + e22;
+        auto n2 = sq(e11) + sq(e22) + sq(c12) * T(0.5);  // 2 (c12 / 2)^2
+        return (n2 * mu + sq(tr) * (T(0.5) * lam)) * s;
+    }
+};
+
+// Neo-Hookean on the invariants of C3 = diag(C, 1):
+// I1 = tr C + 1, I3 = det C, psi = mu/2 (I1 - 3) - mu ln J + lambda/2 (ln J)^2
+template <typename T>
+struct PsiNH {
+    T mu, lam, s;
+    template <class A, class B, class C>
+    ADM_HD auto operator()(const A &c11, const B &c22, const C &c12) const
+    {
+        auto i3 = c11 * c22 - sq(c12);
+        auto L = log(i3);  // 2 ln J
+        return ((c11 + c22 - T(2)) * (T(0.5) * mu) - L * (T(0.5) * mu) + sq(L) * (T(0.125) * lam)) * s;
+    }
+};
+
+// symmetric Dirichlet: A (|J|^2 + |J^-1|^2) = A tr C (1 + 1/det C)
+template <typename T>
+struct PsiSymDir {
+    T s;  // rest area
+    template <class A, class B, class C>
+    ADM_HD auto operator()(const A &c11, const B &c22, const C &c12) const
+    {
+        auto tr = c11 + c22;
+        auto det = c11 * c22 - sq(c12);
+        return (tr + tr * recip(det)) * s;
+    }
+};
+
+// area from the Gram invariants of the edges: 1/2 sqrt(|u|^2 |w|^2 - (u.w)^2)
+template <typename T>
+struct PsiArea {
+    template <class A, class B, class C>
+    ADM_HD auto operator()(const A &uu, const B &ww, const C &uw) const
+    {
+        return sqrt(uu * ww - sq(uw)) * T(0.5);
+    }
+};
+
+// --------------------------------------------------------------- output --
+template <typename T, int K>
+struct Local {
+    T f;
+    T g[K];
+    T H[K * (K + 1) / 2];
+};
+
+template <typename T, int K, class R>
+ADM_HD void store_local(const R &r, Local<T, K> &out)
+{
+    out.f = r.v;
+#pragma unroll
+    for (int i = 0; i < K; ++i) out.g[i] = gbit(R::gm, i) ? r.g[i] : T(0);
+#pragma unroll
+    for (int k = 0; k < K * (K + 1) / 2; ++k) out.H[k] = hbit(R::hl, R::hh, k) ? r.h[k] : T(0);
+}
+
+// ------------------------------------------------------ triangle, VD = 3 --
+// C = F^T F of F = [x1-x0, x2-x0] Dinv;  Dinv row-major (d00, d01, d10, d11)
+template <typename T, class Psi>
+ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Local<T, 9> &out)
+{
+    auto X0 = seed<T, 9, 0>(x[0]);
+    auto X1 = seed<T, 9, 1>(x[1]);
+    auto X2 = seed<T, 9, 2>(x[2]);
+    auto X3 = seed<T, 9, 3>(x[3]);
+    auto X4 = seed<T, 9, 4>(x[4]);
+    auto X5 = seed<T, 9, 5>(x[5]);
+    auto X6 = seed<T, 9, 6>(x[6]);
+    auto X7 = seed<T, 9, 7>(x[7]);
+    auto X8 = seed<T, 9, 8>(x[8]);
+    auto u0 = X3 - X0;  // x1 - x0
+    auto u1 = X4 - X1;
+    auto u2 = X5 - X2;
+    auto w0 = X6 - X0;  // x2 - x0
+    auto w1 = X7 - X1;
+    auto w2 = X8 - X2;
+    auto a0 = u0 * D[0] + w0 * D[2];               // first column of F
+    auto a1 = u1 * D[0] + w1 * D[2];
+    auto a2 = u2 * D[0] + w2 * D[2];
+    auto b0 = u0 * D[1] + w0 * D[3];               // second column of F
+    auto b1 = u1 * D[1] + w1 * D[3];
+    auto b2 = u2 * D[1] + w2 * D[3];
+    auto c11 = sq(a0) + sq(a1) + sq(a2);
+    auto c22 = sq(b0) + sq(b1) + sq(b2);
+    auto c12 = a0 * b0 + a1 * b1 + a2 * b2;
+    auto p = psi(seed<T, 3, 0>(c11.v), seed<T, 3, 1>(c22.v), seed<T, 3, 2>(c12.v));
+    store_local(compose(p, c11, c22, c12), out);
+}
+
+// area term (test energy of Sec. 7.6)
+template <typename T>
+ADM_HD void area_local(const T (&x)[9], Local<T, 9> &out)
+{
+    auto X0 = seed<T, 9, 0>(x[0]);
+    auto X1 = seed<T, 9, 1>(x[1]);
+    auto X2 = seed<T, 9, 2>(x[2]);
+    auto X3 = seed<T, 9, 3>(x[3]);
+    auto X4 = seed<T, 9, 4>(x[4]);
+    auto X5 = seed<T, 9, 5>(x[5]);
+    auto X6 = seed<T, 9, 6>(x[6]);
+    auto X7 = seed<T, 9, 7>(x[7]);
+    auto X8 = seed<T, 9, 8>(x[8]);
+    auto u0 = X3 - X0;
+    auto u1 = X4 - X1;
+    auto u2 = X5 - X2;
+    auto w0 = X6 - X0;
+    auto w1 = X7 - X1;
+    auto w2 = X8 - X2;
+    auto uu = sq(u0) + sq(u1) + sq(u2);
+    auto ww = sq(w0) + sq(w1) + sq(w2);
+    auto uw = u0 * w0 + u1 * w1 + u2 * w2;
+    auto p = PsiArea<T>{}(seed<T, 3, 0>(uu.v), seed<T, 3, 1>(ww.v), seed<T, 3, 2>(uw.v));
+    store_local(compose(p, uu, ww, uw), out);
+}
+
+// ------------------------------------------------------ triangle, VD = 2 --
+// C = J^T J of the UV Jacobian J = [b-a, c-a] Dinv; returns det J (value)
+template <typename T, class Psi>
+ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> &out)
+{
+    auto X0 = seed<T, 6, 0>(x[0]);
+    auto X1 = seed<T, 6, 1>(x[1]);
+    auto X2 = seed<T, 6, 2>(x[2]);
+    auto X3 = seed<T, 6, 3>(x[3]);
+    auto X4 = seed<T, 6, 4>(x[4]);
+    auto X5 = seed<T, 6, 5>(x[5]);
+    auto u0 = X2 - X0;  // b - a
+    auto u1 = X3 - X1;
+    auto w0 = X4 - X0;  // c - a
+    auto w1 = X5 - X1;
+    auto j00 = u0 * D[0] + w0 * D[2];
+    auto j10 = u1 * D[0] + w1 * D[2];
+    auto j01 = u0 * D[1] + w0 * D[3];
+    auto j11 = u1 * D[1] + w1 * D[3];
+    auto c11 = sq(j00) + sq(j10);
+    auto c22 = sq(j01) + sq(j11);
+    auto c12 = j00 * j01 + j10 * j11;
+    auto p = psi(seed<T, 3, 0>(c11.v), seed<T, 3, 1>(c22.v), seed<T, 3, 2>(c12.v));
+    store_local(compose(p, c11, c22, c12), out);
+    return j00.v * j11.v - j01.v * j10.v;
+}
+
+// ----------------------------------------------------------------- hinge --
+// hinge (x0, x1, xa, xb), face A = (x0, x1, xa), face B = (x1, x0, xb);
+// psi = w (theta - thetabar)^2.  Returns false for a degenerate hinge.
+template <typename T>
+ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out)
+{
+    auto X0 = seed<T, 12, 0>(x[0]);
+    auto X1 = seed<T, 12, 1>(x[1]);
+    auto X2 = seed<T, 12, 2>(x[2]);
+    auto X3 = seed<T, 12, 3>(x[3]);
+    auto X4 = seed<T, 12, 4>(x[4]);
+    auto X5 = seed<T, 12, 5>(x[5]);
+    auto X6 = seed<T, 12, 6>(x[6]);
+    auto X7 = seed<T, 12, 7>(x[7]);
+    auto X8 = seed<T, 12, 8>(x[8]);
+    auto X9 = seed<T, 12, 9>(x[9]);
+    auto X10 = seed<T, 12, 10>(x[10]);
+    auto X11 = seed<T, 12, 11>(x[11]);
+    auto e0 = X3 - X0;    // x1 - x0
+    auto e1 = X4 - X1;
+    auto e2 = X5 - X2;
+    auto u0 = X6 - X0;    // xa - x0
+    auto u1 = X7 - X1;
+    auto u2 = X8 - X2;
+    auto v0 = X9 - X3;  // xb - x1
+    auto v1 = X10 - X4;
+    auto v2 = X11 - X5;
+    auto ee = sq(e0) + sq(e1) + sq(e2);
+    auto eu = e0 * u0 + e1 * u1 + e2 * u2;
+    auto ev = e0 * v0 + e1 * v1 + e2 * v2;
+    auto uv = u0 * v0 + u1 * v1 + u2 * v2;
+    auto det = e0 * (u1 * v2 - u2 * v1) + e1 * (u2 * v0 - u0 * v2) + e2 * (u0 * v1 - u1 * v0);
+    auto EE = seed<T, 5, 0>(ee.v);
+    auto EU = seed<T, 5, 1>(eu.v);
+    auto EV = seed<T, 5, 2>(ev.v);
+    auto UV = seed<T, 5, 3>(uv.v);
+    auto DD = seed<T, 5, 4>(det.v);
+    auto ys = -(sqrt(EE) * DD);
+    auto xc = EV * EU - EE * UV;
+    if (!(xc.v != T(0) || ys.v != T(0))) return false;
+    auto th = atan2(ys, xc);
+    auto p = sq(th - thetabar) * w;
+    store_local(compose(p, ee, eu, ev, uv, det), out);
+    return true;
+}
+
+// --------------------------------------------- ARAP-style residual (Eq. 3) --
+// r = sqrt(A) vec_rowmajor(J - R(J)), R the closest rotation: with
+// p = J00 + J11, q = J10 - J01, n = |(p, q)|, R = [[p, -q], [q, p]] / n.
+// Out: r[4], Jr[4][6] over the local DOFs (vertex-major).
+template <typename T>
+ADM_HD bool arap_local(const T (&x)[6], const T (&D)[4], T sqrt_area, T (&r)[4], T (&Jr)[4][6])
+{
+    auto X0 = dseed<T, 6, 0>(x[0]);
+    auto X1 = dseed<T, 6, 1>(x[1]);
+    auto X2 = dseed<T, 6, 2>(x[2]);
+    auto X3 = dseed<T, 6, 3>(x[3]);
+    auto X4 = dseed<T, 6, 4>(x[4]);
+    auto X5 = dseed<T, 6, 5>(x[5]);
+    auto u0 = X2 - X0;
+    auto u1 = X3 - X1;
+    auto w0 = X4 - X0;
+    auto w1 = X5 - X1;
+    auto j00 = u0 * D[0] + w0 * D[2];
+    auto j10 = u1 * D[0] + w1 * D[2];
+    auto j01 = u0 * D[1] + w0 * D[3];
+    auto j11 = u1 * D[1] + w1 * D[3];
+    auto p = j00 + j11;
+    auto q = j10 - j01;
+    T n2 = p.v * p.v + q.v * q.v;
+    if (!(n2 > T(0))) return false;
+    T in = T(1) / Fn<T>::sqrt_(n2);
+    T in3 = in * in * in;
+    // c = p/n, s = q/n:  dc = (q^2 dp - p q dq)/n^3, ds = (p^2 dq - p q dp)/n^3
+    auto c = dchain2(p, q, p.v * in, q.v * q.v * in3, -p.v * q.v * in3);
+    auto s = dchain2(p, q, q.v * in, -p.v * q.v * in3, p.v * p.v * in3);
+    auto r0 = (j00 - c) * sqrt_area;
+    auto r1 = (j01 + s) * sqrt_area;
+    auto r2 = (j10 - s) * sqrt_area;
+    auto r3 = (j11 - c) * sqrt_area;
+    r[0] = r0.v;
+    r[1] = r1.v;
+    r[2] = r2.v;
+    r[3] = r3.v;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        Jr[0][i] = gbit(decltype(r0)::gm, i) ? r0.g[i] : T(0);
+        Jr[1][i] = gbit(decltype(r1)::gm, i) ? r1.g[i] : T(0);
+        Jr[2][i] = gbit(decltype(r2)::gm, i) ? r2.g[i] : T(0);
+        Jr[3][i] = gbit(decltype(r3)::gm, i) ? r3.g[i] : T(0);
+    }
+    return true;
+}
+
+}  // namespace adm
