@@ -85,8 +85,24 @@ typedef enum {
                                  1 = per-element atomic scatter (the paper's
                                  Sec. 5.5 scheme, kept as a reference path)    */
     ADM_OPT_TILE_TRIS = 2,    /* triangles per tile of the tiled assembler      */
-    ADM_OPT_BLOCK_THREADS = 3 /* threads per block of the element kernels       */
+    ADM_OPT_BLOCK_THREADS = 3,/* threads per block of the element kernels       */
+    ADM_OPT_PROFILE = 4       /* > 0: record CUDA events around every kernel of
+                                 each evaluation, on the evaluation's stream,
+                                 keeping the last `value` evaluations (a ring);
+                                 0: off (default).  Creates events, allocates no
+                                 device memory. */
 } adm_option;
+
+/* Kernel stages reported by adm_profile_read(). */
+typedef enum {
+    ADM_STAGE_ZERO = 0,       /* zero-fill of outputs (memset)                  */
+    ADM_STAGE_TRIANGLES = 1,  /* triangle-term kernel                           */
+    ADM_STAGE_HINGES = 2,     /* hinge-term kernel                              */
+    ADM_STAGE_GNORM = 3,      /* FP64 gradient-norm partials                    */
+    ADM_STAGE_FINALIZE = 4,   /* per-mesh FP64 energy / norm reduction          */
+    ADM_STAGE_TILED = 5,      /* fused tiled element + assembly kernel          */
+    ADM_N_STAGES = 6
+} adm_stage;
 
 /* --- creation ---------------------------------------------------------- */
 
@@ -159,11 +175,13 @@ adm_status adm_eval_batch(adm_handle h, adm_energy energy, adm_precision prec,
                           const void *x_dev, double *energy_per_mesh_dev, double *gnorm_dev,
                           void *grad_dev, void *bsr_vals_dev, void *stream);
 
-/* Same work as adm_eval_batch with HOST buffers: copies x host->device,
- * evaluates, copies the requested outputs device->host, and returns after
- * the copies completed (synchronous).  Uses library-owned device staging
- * buffers (allocated on first use) and the library's own stream.  Host
- * buffers may be pageable; pinned buffers make the copies faster. */
+/* The full derivative pass of adm_eval_batch (energy, gradient, Hessian)
+ * with HOST buffers: copies x host->device, evaluates into library-owned
+ * device staging buffers, copies back those outputs whose host pointer is
+ * not NULL, and returns after the copies completed (synchronous).  Outputs
+ * not copied back stay in the staging buffers (for a solver on the device).
+ * Staging buffers are allocated on first use; the call uses the library's
+ * own stream.  Pinned host buffers make the copies faster. */
 adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision prec,
                                const void *x_host, double *energy_per_mesh_host,
                                double *gnorm_host, void *grad_host, void *bsr_vals_host);
@@ -174,6 +192,13 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
 adm_status adm_eval_jacobian(adm_handle h, adm_energy energy, adm_precision prec,
                              const void *x_dev, void *r_dev, void *jac_vals_dev,
                              void *jtj_bsr_vals_dev, void *stream);
+
+/* Average device time (ms) per launch of every stage over the evaluations
+ * recorded since profiling was enabled or last read (at most the ring size),
+ * and the number of launches of each stage (n_launches may be NULL).  Waits
+ * for the recorded events, then clears the ring.  n_stages <= ADM_N_STAGES.
+ * ADM_ERR_ARG when profiling is off. */
+adm_status adm_profile_read(adm_handle h, float *avg_ms, int32_t *n_launches, int32_t n_stages);
 
 /* Device status word of the last evaluation on this handle: ADM_OK,
  * ADM_ERR_DOMAIN or ADM_ERR_TIMEOUT.  Call after synchronising the stream of

@@ -27,7 +27,9 @@ ARAP2D_RESIDUAL = 16
 # adm_precision
 FP64, FP32 = 0, 1
 # adm_option
-OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS = 1, 2, 3
+OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE = 1, 2, 3, 4
+# adm_stage
+STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled"]
 
 STATUS = {0: "ADM_OK", -1: "ADM_ERR_ARG", -2: "ADM_ERR_MESH", -3: "ADM_ERR_DOMAIN",
           -4: "ADM_ERR_CUDA", -5: "ADM_ERR_TIMEOUT", -6: "ADM_ERR_OOM", -7: "ADM_ERR_UNSUPPORTED"}
@@ -71,6 +73,7 @@ def lib():
         "adm_eval_batch_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_eval_jacobian": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_get_status": (i32, [vp]),
+        "adm_profile_read": (i32, [vp, C.POINTER(C.c_float), C.POINTER(i32), i32]),
         "adm_strerror": (C.c_char_p, [i32]),
         "adm_destroy": (None, [vp]),
     }
@@ -100,7 +103,7 @@ class _DevView:
     """__cuda_array_interface__ view of library-owned device memory."""
 
     def __init__(self, ptr: int, n: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
                                          "version": 3}
 
 
@@ -205,6 +208,14 @@ class Mesh:
     def eval_jacobian(self, energy: int, prec: int, x, r, jac_vals=None, jtj=None, stream=None):
         _check(lib().adm_eval_jacobian(self._h, energy, prec, _ptr(x), _ptr(r), _ptr(jac_vals), _ptr(jtj),
                                        _stream(stream)), "adm_eval_jacobian")
+
+    def profile_read(self) -> dict:
+        """{stage: (average ms per launch, launches)} since the last read."""
+        n = len(STAGES)
+        ms = (C.c_float * n)()
+        cnt = (C.c_int32 * n)()
+        _check(lib().adm_profile_read(self._h, ms, cnt, n), "adm_profile_read")
+        return {STAGES[k]: (float(ms[k]), int(cnt[k])) for k in range(n)}
 
     def status(self) -> int:
         return int(lib().adm_get_status(self._h))

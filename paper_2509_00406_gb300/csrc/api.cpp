@@ -277,6 +277,21 @@ adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
     case ADM_OPT_BLOCK_THREADS:
         if (value != kElemThreads) return ADM_ERR_UNSUPPORTED;
         return ADM_OK;
+    case ADM_OPT_PROFILE: {
+        if (value < 0 || value > 4096) return ADM_ERR_ARG;
+        for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+        h->prof_ev.clear();
+        h->prof_ran.clear();
+        h->prof_ring = 0;
+        h->prof_next = h->prof_count = 0;
+        if (value == 0) return ADM_OK;
+        h->prof_ev.resize((size_t)value * ADM_N_STAGES * 2);
+        h->prof_ran.assign((size_t)value * ADM_N_STAGES, 0);
+        for (auto &e : h->prof_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return ADM_ERR_CUDA;
+        h->prof_ring = (int)value;
+        return ADM_OK;
+    }
     default: return ADM_ERR_ARG;
     }
 }
@@ -427,17 +442,16 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
         return r;
     };
     if ((s = grow(&h->d_stage_x, h->stage_x_bytes, xb)) != ADM_OK) return s;
-    bool need_grad = grad_host || gnorm_host;
-    if (need_grad && (s = grow(&h->d_stage_grad, h->stage_grad_bytes, xb)) != ADM_OK) return s;
-    if (bsr_vals_host && (s = grow(&h->d_stage_bsr, h->stage_bsr_bytes, bb)) != ADM_OK) return s;
+    if ((s = grow(&h->d_stage_grad, h->stage_grad_bytes, xb)) != ADM_OK) return s;
+    if ((s = grow(&h->d_stage_bsr, h->stage_bsr_bytes, bb)) != ADM_OK) return s;
     if (!h->d_stage_e) {
         if ((s = dev_alloc(h, &h->d_stage_e, m.n_mesh * sizeof(double))) != ADM_OK) return s;
         if ((s = dev_alloc(h, &h->d_stage_gn, m.n_mesh * sizeof(double))) != ADM_OK) return s;
     }
     cudaStream_t st = h->own_stream;
     if (cudaMemcpyAsync(h->d_stage_x, x_host, xb, cudaMemcpyHostToDevice, st) != cudaSuccess) return ADM_ERR_CUDA;
-    s = adm_eval_batch(h, energy, prec, h->d_stage_x, h->d_stage_e, gnorm_host ? h->d_stage_gn : nullptr,
-                       need_grad ? h->d_stage_grad : nullptr, bsr_vals_host ? h->d_stage_bsr : nullptr, st);
+    s = adm_eval_batch(h, energy, prec, h->d_stage_x, h->d_stage_e, h->d_stage_gn, h->d_stage_grad,
+                       h->d_stage_bsr, st);
     if (s != ADM_OK) return s;
     if (energy_per_mesh_host &&
         cudaMemcpyAsync(energy_per_mesh_host, h->d_stage_e, m.n_mesh * sizeof(double), cudaMemcpyDeviceToHost,
@@ -462,6 +476,32 @@ adm_status adm_eval_jacobian(adm_handle h, adm_energy energy, adm_precision prec
     adm_status s = build_pattern(h, PAT_TRI);
     if (s != ADM_OK) return s;
     return launch_jacobian(h, prec, x_dev, r_dev, jac_vals_dev, jtj_bsr_vals_dev, as_stream(stream));
+}
+
+adm_status adm_profile_read(adm_handle h, float *avg_ms, int32_t *n_launches, int32_t n_stages)
+{
+    if (!h || !avg_ms || n_stages < 0 || n_stages > ADM_N_STAGES || h->prof_ring <= 0) return ADM_ERR_ARG;
+    double sum[ADM_N_STAGES] = {0};
+    int cnt[ADM_N_STAGES] = {0};
+    for (int i = 0; i < h->prof_count; ++i) {
+        int slot = (h->prof_next - 1 - i + h->prof_ring) % h->prof_ring;
+        for (int k = 0; k < ADM_N_STAGES; ++k) {
+            if (!h->prof_ran[slot * ADM_N_STAGES + k]) continue;
+            cudaEvent_t e0 = h->prof_ev[(slot * ADM_N_STAGES + k) * 2], e1 = h->prof_ev[(slot * ADM_N_STAGES + k) * 2 + 1];
+            float ms = 0.0f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                return ADM_ERR_CUDA;
+            sum[k] += ms;
+            cnt[k]++;
+        }
+    }
+    for (int k = 0; k < n_stages; ++k) {
+        avg_ms[k] = cnt[k] ? (float)(sum[k] / cnt[k]) : 0.0f;
+        if (n_launches) n_launches[k] = cnt[k];
+    }
+    h->prof_count = 0;
+    h->prof_next = 0;
+    return ADM_OK;
 }
 
 adm_status adm_get_status(adm_handle h)
@@ -498,6 +538,7 @@ void adm_destroy(adm_handle h)
         cudaStreamSynchronize(h->own_stream);
         cudaStreamDestroy(h->own_stream);
     }
+    for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     for (void *p : h->owned) cudaFree(p);
     delete h;
 }

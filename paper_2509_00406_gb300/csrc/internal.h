@@ -124,6 +124,10 @@ struct adm_ctx {
     double *d_stage_e = nullptr, *d_stage_gn = nullptr;
     size_t stage_x_bytes = 0, stage_grad_bytes = 0, stage_bsr_bytes = 0;
     cudaStream_t own_stream = nullptr;
+    // kernel timing ring: per evaluation and stage, a start and an end event
+    int prof_ring = 0, prof_next = 0, prof_count = 0;
+    std::vector<cudaEvent_t> prof_ev;          // ring * ADM_N_STAGES * 2
+    std::vector<unsigned char> prof_ran;       // ring * ADM_N_STAGES
     std::vector<void *> owned;  // every device allocation, freed by destroy
 };
 
@@ -153,6 +157,15 @@ struct EvalArgs {
     cudaStream_t stream;
 };
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
+// brackets one stage of one evaluation with events when profiling is on
+struct StageTimer {
+    adm_ctx *h;
+    cudaStream_t s;
+    int slot;
+    StageTimer(adm_ctx *h_, cudaStream_t s_);
+    void begin(int stage);
+    void end(int stage);
+};
 adm_status launch_jacobian(adm_ctx *h, int prec, const void *x, void *r, void *jv, void *jtj,
                            cudaStream_t stream);
 

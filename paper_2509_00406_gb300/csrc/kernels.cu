@@ -8,6 +8,7 @@
 // energy (Eq. 1) and of the gradient norm.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -323,6 +324,26 @@ static void launch_hinge(int mode, dim3 grid, cudaStream_t s, const ElemArgs<T> 
 constexpr int kThreads = 128;
 constexpr int kRedThreads = 256;
 
+StageTimer::StageTimer(adm_ctx *h_, cudaStream_t s_) : h(h_), s(s_), slot(-1)
+{
+    if (h->prof_ring <= 0) return;
+    slot = h->prof_next;
+    h->prof_next = (h->prof_next + 1) % h->prof_ring;
+    h->prof_count = std::min(h->prof_count + 1, h->prof_ring);
+    for (int k = 0; k < ADM_N_STAGES; ++k) h->prof_ran[slot * ADM_N_STAGES + k] = 0;
+}
+void StageTimer::begin(int stage)
+{
+    if (slot < 0) return;
+    cudaEventRecord(h->prof_ev[(slot * ADM_N_STAGES + stage) * 2 + 0], s);
+}
+void StageTimer::end(int stage)
+{
+    if (slot < 0) return;
+    cudaEventRecord(h->prof_ev[(slot * ADM_N_STAGES + stage) * 2 + 1], s);
+    h->prof_ran[slot * ADM_N_STAGES + stage] = 1;
+}
+
 template <typename T>
 static adm_status eval_typed(adm_ctx *h, const EvalArgs &a)
 {
@@ -332,11 +353,14 @@ static adm_status eval_typed(adm_ctx *h, const EvalArgs &a)
     const Pattern &P = h->pat[pk];
     const int mode = a.bsr ? MODE_HESS : (a.grad ? MODE_GRAD : MODE_VALUE);
     cudaStream_t s = a.stream;
+    StageTimer tm(h, s);
+    tm.begin(ADM_STAGE_ZERO);
     if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
     if (a.grad && cudaMemsetAsync(a.grad, 0, sizeof(T) * m.nV * vd, s) != cudaSuccess)
         return ADM_ERR_CUDA;
     if (a.bsr && cudaMemsetAsync(a.bsr, 0, sizeof(T) * P.nnzb * vd * vd, s) != cudaSuccess)
         return ADM_ERR_CUDA;
+    tm.end(ADM_STAGE_ZERO);
     const int prec = a.prec;
     const TermConsts<T> c = consts<T>(h, a.energy);
     const bool tri = has_tris(a.energy), hin = has_hinges(a.energy);
@@ -354,7 +378,9 @@ static adm_status eval_typed(adm_ctx *h, const EvalArgs &a)
         A.epart = h->d_epart;
         A.status = h->d_status;
         A.c = c;
+        tm.begin(ADM_STAGE_TRIANGLES);
         launch_tri<T, kThreads>(a.energy, mode, dim3(h->tri_blocks.n_blocks), s, A);
+        tm.end(ADM_STAGE_TRIANGLES);
     }
     if (hin) {
         ElemArgs<T> A;
@@ -370,19 +396,26 @@ static adm_status eval_typed(adm_ctx *h, const EvalArgs &a)
         A.epart = h->d_epart + (tri ? h->tri_blocks.n_blocks : 0);
         A.status = h->d_status;
         A.c = c;
-        if (h->hinge_blocks.n_blocks > 0)
+        if (h->hinge_blocks.n_blocks > 0) {
+            tm.begin(ADM_STAGE_HINGES);
             launch_hinge<T, kThreads>(mode, dim3(h->hinge_blocks.n_blocks), s, A);
+            tm.end(ADM_STAGE_HINGES);
+        }
     }
     if (cudaGetLastError() != cudaSuccess) return ADM_ERR_CUDA;
     if (a.gnorm_per_mesh) {
+        tm.begin(ADM_STAGE_GNORM);
         k_sumsq<T, kRedThreads><<<h->chunks.n_chunks, kRedThreads, 0, s>>>(
             (const T *)a.grad, h->chunks.d_begin, h->chunks.d_end, h->d_gpart);
+        tm.end(ADM_STAGE_GNORM);
     }
+    tm.begin(ADM_STAGE_FINALIZE);
     k_finalize<1024><<<1, 1024, 0, s>>>(
         m.n_mesh, h->d_epart, tri ? h->tri_blocks.d_mesh_block_off : nullptr,
         hin ? h->hinge_blocks.d_mesh_block_off : nullptr, tri ? h->tri_blocks.n_blocks : 0,
         h->d_gpart, h->chunks.d_mesh_chunk_off, a.energy_per_mesh, a.gnorm_per_mesh,
         a.energy_total);
+    tm.end(ADM_STAGE_FINALIZE);
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
