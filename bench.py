@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the derivative pass on one GB300 (or N, one process each).
+
+Workload (default): the batched elastic shell -- 700 icospheres (levels
+4/5/6 in the fixed 668/28/4 mix, 2,162,040 vertices, 4,321,280 triangles,
+6,481,920 hinges), StVK membrane + dihedral hinge bending, FP32 local
+forward-mode AD with FP64 energy and gradient-norm reductions.  One step is
+one call of the library's batched evaluation: per-mesh energies, per-mesh
+gradient norms, the gradient and the 3x3 BSR Hessian of every mesh.
+
+Metric: elements/s (triangles + hinges differentiated and assembled per
+second, whole job).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (the slow, plain implementation
+used by the tests) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "elements/s for grad+BSR Hessian assembly"
+UNIT = "elements/s"
+SHELL_PARAMS = [1.0e5, 0.3, 1.0e-3]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--assembler", type=int, default=-1, help="-1: library default")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- workload --
+def workload(rank: int):
+    levels = synth.shell_batch_levels("paper")
+    mesh = synth.shell_batch(levels, sigma=1e-3, seed=4 + rank)
+    return levels, mesh
+
+
+def counts(mesh):
+    """Element and pattern counts of a batch of closed meshes (every edge is a
+    hinge): E = 3T/2 per mesh, nnzb = V + 4E."""
+    nT = mesh.nT
+    nE = 3 * nT // 2
+    return {"n_vertices": mesh.nV, "n_triangles": nT, "n_hinges": nE, "nnzb": mesh.nV + 4 * nE}
+
+
+def algorithmic_bytes(c, stage: str) -> int:
+    """Bytes the method must move once (FP32): x 12 B/V, faces 12 B/T,
+    hinges 16 B/H, triangle rest data (Dm^-1, area) 20 B/T, hinge rest data
+    (rest angle, weight) 8 B/H, gradient 12 B/V, BSR 36 B per block.
+    Per stage: the triangle kernel reads its own inputs and x and writes the
+    gradient and the triangle-stencil blocks (V + 2E); the hinge kernel reads
+    its inputs and x and writes the gradient and every block; a fused pass
+    moves everything once."""
+    V, T, H, nnzb = c["n_vertices"], c["n_triangles"], c["n_hinges"], c["nnzb"]
+    if stage == "triangles":
+        return 12 * V + 32 * T + 12 * V + 36 * (V + 2 * H)
+    if stage == "hinges":
+        return 12 * V + 24 * H + 12 * V + 36 * nnzb
+    return 12 * V + 32 * T + 24 * H + 12 * V + 36 * nnzb
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except Exception:
+        return 6800.0, "profiling-recipe fallback 6.8 TB/s (of fallback)"
+
+
+# -------------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.out = None
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            txt, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            txt = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in txt.strip().splitlines():
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle --
+def oracle_sample(levels, mesh, n_mesh: int):
+    """Oracle problem and FP32-rounded x of the first n_mesh meshes."""
+    import oracle
+
+    vo, fo = mesh.v_off, mesh.f_off
+    rest = mesh.rest[: vo[n_mesh]]
+    faces = mesh.faces[: fo[n_mesh]]
+    x = mesh.x[: vo[n_mesh]].astype(np.float32).astype(np.float64)
+    P = oracle.Problem(rest, faces, oracle.SHELL, 3, params=SHELL_PARAMS)
+    return P, x
+
+
+def meshes_for_elements(mesh, target: int) -> int:
+    el = 0
+    for k in range(mesh.n_mesh):
+        nt = int(mesh.f_off[k + 1] - mesh.f_off[k])
+        el += nt + 3 * nt // 2
+        if el >= target:
+            return k + 1
+    return mesh.n_mesh
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    levels, mesh = workload(0)
+    c = counts(mesh)
+    # calibrate on one mesh, then size each step so that K + W steps take
+    # about two minutes
+    P1, x1 = oracle_sample(levels, mesh, 1)
+    t0 = time.perf_counter()
+    P1.assemble(x1)
+    rate = (P1.nT + P1.nH) / (time.perf_counter() - t0)
+    per_step_s = max(0.2, 120.0 / max(1, args.steps + args.warmup))
+    n = meshes_for_elements(mesh, int(rate * per_step_s))
+    P, x = oracle_sample(levels, mesh, n)
+    n_el = P.nT + P.nH
+    for _ in range(args.warmup):
+        P.assemble(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.assemble(x)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n_el / dt
+    sample = f"first {n} of 700 meshes ({n_el} elements) per step, hyper-dual route, 1 thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(c, None),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(c, assembler):
+    return {
+        "workload": "shell_batch: 700 icospheres, levels 4/5/6 = 668/28/4, StVK membrane + dihedral hinges",
+        "n_mesh": 700, **c,
+        "energy": "StVK membrane (E=1e5, nu=0.3, t=1e-3) + hinge bending (k_b = E t^3/(12(1-nu^2)), h=1)",
+        "precision": "fp32 local forward-mode AD, fp64 per-mesh energy and gradient norm",
+        "assembler": assembler,
+        "l2": "no flush: working set (inputs, slot maps, BSR output) > 1 GB >> 129 MB L2",
+        "parallelism": "replicas (one independent batch per GPU)",
+    }
+
+
+# ------------------------------------------------------------------ our arm --
+def run_ours(args, rank: int, world: int, local: int):
+    import torch
+
+    import __graft_entry__
+    import paper_2509_00406_gb300 as adm
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    levels, mesh = workload(rank)
+    c = counts(mesh)
+    m = adm.Mesh(mesh.rest, mesh.faces, 3, v_off=mesh.v_off, f_off=mesh.f_off)
+    m.set_params(adm.SHELL, SHELL_PARAMS)
+    if args.assembler >= 0:
+        m.set_option(adm.OPT_ASSEMBLER, args.assembler)
+    _, nV, nnzb, _, _ = m.pattern(adm.SHELL)
+    assert nnzb == c["nnzb"] and nV == c["n_vertices"]
+    n_el = c["n_triangles"] + c["n_hinges"]
+    x = torch.from_numpy(mesh.x.astype(np.float32)).cuda()
+    e = torch.zeros(mesh.n_mesh, dtype=torch.float64, device="cuda")
+    gn = torch.zeros(mesh.n_mesh, dtype=torch.float64, device="cuda")
+    g = torch.zeros(nV * 3, dtype=torch.float32, device="cuda")
+    H = torch.zeros(nnzb * 9, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        m.eval_batch(adm.SHELL, adm.FP32, x, e, gn, g, H, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    assert m.status() == 0, adm.STATUS.get(m.status())
+
+    m.set_option(adm.OPT_PROFILE, min(args.steps, 4096))
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = m.profile_read()
+    m.set_option(adm.OPT_PROFILE, 0)
+    if dist:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * n_el / (ms_step * 1e-3)
+
+    # dominant kernel and its roofline
+    kern = {k: v for k, v in prof.items() if k != "zero" and v[1] > 0}
+    dom = max(kern, key=lambda k: kern[k][0] * kern[k][1])
+    dom_ms = kern[dom][0]
+    launches_per_step = sum(v[1] for v in kern.values()) / args.steps
+    peak, peak_src = measured_peaks()
+    ab = algorithmic_bytes(c, dom)
+    achieved = ab / (dom_ms * 1e-3) / 1e9
+    pass_bytes = algorithmic_bytes(c, "pass")
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        from paper_2509_00406_gb300 import _build
+
+        tj = json.load(open(tfile))
+        ent = tj.get(dom)
+        if ent and ent.get("source_digest") == _build._digest():
+            traffic = ent["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    xh = torch.from_numpy(mesh.x.astype(np.float32)).pin_memory()
+    eh = torch.zeros(mesh.n_mesh, dtype=torch.float64).pin_memory()
+    gnh = torch.zeros(mesh.n_mesh, dtype=torch.float64).pin_memory()
+    m.eval_batch_host(adm.SHELL, adm.FP32, xh.numpy(), eh.numpy(), gnh.numpy())
+    k_e2e = max(3, min(args.steps, 50))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        m.eval_batch_host(adm.SHELL, adm.FP32, xh.numpy(), eh.numpy(), gnh.numpy())
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
+           "d2h_bytes_per_step": int(2 * mesh.n_mesh * 8),
+           "note": "adm_eval_batch_host: x in, per-mesh energy + gradient norm out; gradient and "
+                   "Hessian stay in device staging buffers"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(c, "per-element atomic scatter"),
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": ab,
+                     "avg_ms": dom_ms, "peak_source": peak_src},
+        "pass": {"algorithmic_bytes": pass_bytes, "achieved_gbs": pass_bytes / (ms_step * 1e-3) / 1e9,
+                 "frac_of_hbm": pass_bytes / (ms_step * 1e-3) / 1e9 / peak,
+                 "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}},
+        "e2e": e2e,
+        "clocks": clk,
+    }
+
+    # CPU baseline and FP32-vs-FP64 error on the same sample (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = meshes_for_elements(mesh, 550_000)
+        P, xs = oracle_sample(levels, mesh, n)
+        t0 = time.perf_counter()
+        ref = P.assemble(xs)
+        dt = time.perf_counter() - t0
+        n_s = P.nT + P.nH
+        line["cpu_baseline"] = {"value": n_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {n} of 700 meshes ({n_s} elements), hyper-dual route, "
+                                          f"1 thread, {dt:.1f} s"}
+        Hs = H[: P.nnzb * 9].cpu().numpy().reshape(-1, 3, 3).astype(np.float64)
+        gs = g[: P.nV * 3].cpu().numpy().reshape(-1, 3).astype(np.float64)
+        es = e[:n].sum().item()
+        line["error_vs_fp64_oracle"] = {
+            "hessian_rel_fro": float(np.linalg.norm(Hs - ref["vals"]) / np.linalg.norm(ref["vals"])),
+            "gradient_rel": float(np.linalg.norm(gs - ref["grad"]) / np.linalg.norm(ref["grad"])),
+            "energy_rel": float(abs(es - ref["energy"]) / abs(ref["energy"])),
+            "sample": f"first {n} meshes", "tolerance": 2e-5}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    m.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()
