@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--assembler", type=int, default=-1, help="-1: library default")
+    ap.add_argument("--tile-tris", type=int, default=0, help="0: library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -227,6 +228,10 @@ def run_ours(args, rank: int, world: int, local: int):
     m.set_params(adm.SHELL, SHELL_PARAMS)
     if args.assembler >= 0:
         m.set_option(adm.OPT_ASSEMBLER, args.assembler)
+    if args.tile_tris > 0:
+        m.set_option(adm.OPT_TILE_TRIS, args.tile_tris)
+    assembler = "per-element atomic scatter" if args.assembler == 1 else \
+        f"tiled shared-memory (tile_tris={args.tile_tris if args.tile_tris > 0 else 512})"
     _, nV, nnzb, _, _ = m.pattern(adm.SHELL)
     assert nnzb == c["nnzb"] and nV == c["n_vertices"]
     n_el = c["n_triangles"] + c["n_hinges"]
@@ -276,6 +281,8 @@ def run_ours(args, rank: int, world: int, local: int):
     dom = max(kern, key=lambda k: kern[k][0] * kern[k][1])
     dom_ms = kern[dom][0]
     launches_per_step = sum(v[1] for v in kern.values()) / args.steps
+    if args.assembler != 1:
+        launches_per_step += prof["zero"][1] / args.steps   # k_zero_shared
     peak, peak_src = measured_peaks()
     ab = algorithmic_bytes(c, dom)
     achieved = ab / (dom_ms * 1e-3) / 1e9
@@ -317,7 +324,7 @@ def run_ours(args, rank: int, world: int, local: int):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(c, "per-element atomic scatter"),
+        "config": config_dict(c, assembler),
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": ab,

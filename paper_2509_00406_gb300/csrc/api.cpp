@@ -132,6 +132,59 @@ adm_status ensure_shell(adm_ctx *h)
     return build_pattern(h, PAT_SHELL);
 }
 
+// tiles of the tiled assembler for one pattern kind, with rest data in tile order
+adm_status ensure_tiles(adm_ctx *h, int kind)
+{
+    TileSet &ts = h->tiles[kind];
+    if (ts.built) return ADM_OK;
+    adm_status s = build_pattern(h, kind);
+    if (s != ADM_OK) return s;
+    s = tiles_build(h->m, h->pat[kind], kind == PAT_SHELL, h->tile_tris, ts);
+    if (s != ADM_OK) {
+        ts = TileSet();
+        return s;
+    }
+    const HostMesh &m = h->m;
+    auto up = [&](auto **dst, const auto &v) { return upload(h, dst, v.data(), v.size() * sizeof(v[0])); };
+    if ((s = up(&ts.d_hdr, ts.hdr)) != ADM_OK) return s;
+    if ((s = up(&ts.d_tri_loc, ts.tri_loc)) != ADM_OK) return s;
+    if ((s = up(&ts.d_hinge_loc, ts.hinge_loc)) != ADM_OK) return s;
+    if ((s = up(&ts.d_foot, ts.foot)) != ADM_OK) return s;
+    if ((s = up(&ts.d_row_start, ts.row_start)) != ADM_OK) return s;
+    if ((s = up(&ts.d_code_off, ts.code_off)) != ADM_OK) return s;
+    if ((s = up(&ts.d_codes, ts.codes)) != ADM_OK) return s;
+    if ((s = up(&ts.d_zero_blocks, ts.zero_blocks)) != ADM_OK) return s;
+    if ((s = up(&ts.d_zero_verts, ts.zero_verts)) != ADM_OK) return s;
+    if ((s = up(&ts.d_mesh_tile_off, ts.mesh_tile_off)) != ADM_OK) return s;
+    {
+        std::vector<std::vector<double>> f(5, std::vector<double>(m.nT));
+        for (int64_t i = 0; i < m.nT; ++i) {
+            const int64_t t = ts.tri_perm[i];
+            for (int k = 0; k < 4; ++k) f[k][i] = m.tri_Dinv[4 * t + k];
+            f[4][i] = m.tri_area[t];
+        }
+        if ((s = upload_rest(h, ts.d_tri_rest, f, m.nT)) != ADM_OK) return s;
+    }
+    if (kind == PAT_SHELL) {
+        const int64_t nH = m.nH();
+        std::vector<std::vector<double>> f(2, std::vector<double>(nH));
+        for (int64_t i = 0; i < nH; ++i) {
+            const int64_t e = ts.hinge_perm[i];
+            f[0][i] = m.h_thetabar[e];
+            f[1][i] = m.h_abar[e] / 3.0;
+        }
+        if ((s = upload_rest(h, ts.d_hinge_rest, f, nH)) != ADM_OK) return s;
+    }
+    if ((size_t)ts.n_tiles + 1 > h->epart_cap) {
+        dev_free(h, h->d_epart);
+        h->d_epart = nullptr;
+        if ((s = dev_alloc(h, &h->d_epart, ((size_t)ts.n_tiles + 1) * sizeof(double))) != ADM_OK) return s;
+        h->epart_cap = (size_t)ts.n_tiles + 1;
+    }
+    ts.built = true;
+    return ADM_OK;
+}
+
 bool energy_ok(int energy, int vdim)
 {
     switch (energy) {
@@ -151,8 +204,9 @@ bool needs_hinges(int energy) { return energy == ADM_HINGE_BENDING || energy == 
 adm_status prepare(adm_ctx *h, int energy)
 {
     if (!energy_ok(energy, h->m.vdim)) return ADM_ERR_UNSUPPORTED;
-    if (needs_hinges(energy)) return ensure_shell(h);
-    return build_pattern(h, PAT_TRI);
+    adm_status s = needs_hinges(energy) ? ensure_shell(h) : build_pattern(h, PAT_TRI);
+    if (s != ADM_OK || h->assembler != 0 || energy == ADM_ARAP2D_RESIDUAL) return s;
+    return ensure_tiles(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
 }
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
@@ -267,11 +321,13 @@ adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
     if (!h) return ADM_ERR_ARG;
     switch (option) {
     case ADM_OPT_ASSEMBLER:
-        if (value != 1) return ADM_ERR_UNSUPPORTED;
+        if (value != 0 && value != 1) return ADM_ERR_ARG;
         h->assembler = (int)value;
         return ADM_OK;
     case ADM_OPT_TILE_TRIS:
         if (value < 32 || value > 4096) return ADM_ERR_ARG;
+        if (value != h->tile_tris)
+            for (auto &ts : h->tiles) ts.built = false;  // rebuilt on next use
         h->tile_tris = (int)value;
         return ADM_OK;
     case ADM_OPT_BLOCK_THREADS:

@@ -1,0 +1,104 @@
+// device_common.cuh -- definitions shared by the kernel translation units of
+// libadm (one per assembler and precision, so that they compile in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+#include "terms.cuh"
+
+namespace adm {
+
+constexpr int kThreads = 128;      // per-element kernels
+constexpr int kRedThreads = 256;   // reductions
+constexpr int kTileThreads = 256;  // tiled kernel
+
+enum Mode { MODE_VALUE = 0, MODE_GRAD = 1, MODE_HESS = 2 };
+
+template <typename T>
+struct TermConsts {
+    T mu, lam, thick, kbh2;
+};
+
+// deterministic block sum of one double per thread (fixed tree order)
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red[THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < THREADS / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+// ----------------------------------------------------- term evaluation --
+template <int ENERGY>
+struct TriTraits {
+    static constexpr int VD = ENERGY == ADM_SYMDIR2D ? 2 : 3;
+    static constexpr int K = 3 * VD;
+};
+
+// local f, g, H of one triangle term; false outside the energy's domain
+template <typename T, int ENERGY>
+__device__ __forceinline__ bool tri_term(const T (&x)[TriTraits<ENERGY>::K], const T (&D)[4], T area,
+                                         const TermConsts<T> &c, Local<T, TriTraits<ENERGY>::K> &L)
+{
+    bool ok = true;
+    if constexpr (ENERGY == ADM_SYMDIR2D) {
+        T det = uv_local(x, D, PsiSymDir<T>{area}, L);
+        ok = det > T(0);
+    } else if constexpr (ENERGY == ADM_STVK_MEMBRANE || ENERGY == ADM_SHELL) {
+        membrane_local(x, D, PsiStVK<T>{c.mu, c.lam, c.thick * area}, L);
+    } else if constexpr (ENERGY == ADM_NH_MEMBRANE) {
+        membrane_local(x, D, PsiNH<T>{c.mu, c.lam, c.thick * area}, L);
+    } else if constexpr (ENERGY == ADM_AREA) {
+        area_local(x, L);
+    }
+    return ok && isfinite(L.f);
+}
+
+inline bool has_tris(int energy)
+{
+    return energy == ADM_SYMDIR2D || energy == ADM_STVK_MEMBRANE || energy == ADM_SHELL ||
+           energy == ADM_NH_MEMBRANE || energy == ADM_AREA;
+}
+inline bool has_hinges(int energy) { return energy == ADM_HINGE_BENDING || energy == ADM_SHELL; }
+
+template <typename T>
+inline TermConsts<T> consts(const adm_ctx *h, int energy)
+{
+    EnergyParams p;
+    auto it = h->params.find(energy);
+    if (it != h->params.end()) p = it->second;
+    TermConsts<T> c;
+    c.mu = (T)p.mu();
+    c.lam = (T)p.lambda();
+    c.thick = (T)p.t;
+    c.kbh2 = (T)(p.kbend() * p.h * p.h);
+    return c;
+}
+
+
+// per-assembler evaluations (explicitly instantiated for float and double)
+template <typename T>
+adm_status eval_atomic(adm_ctx *h, const EvalArgs &a);
+template <typename T>
+adm_status eval_tiled(adm_ctx *h, const EvalArgs &a);
+
+// FP64 per-mesh energy (from element-block or tile partials) and gradient
+// norm, enqueued after an assembler (reduce.cu)
+adm_status launch_reduce(adm_ctx *h, const EvalArgs &a, const int32_t *tri_off, const int32_t *hinge_off,
+                         int32_t hinge_base, StageTimer &tm);
+
+}  // namespace adm

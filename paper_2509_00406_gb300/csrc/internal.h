@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <array>
 #include <map>
 #include <string>
 #include <vector>
@@ -78,6 +79,33 @@ struct ChunkTable {
     int32_t *d_mesh_chunk_off = nullptr;            // n_mesh + 1
 };
 
+// shared-memory tiles of the tiled assembler (tiles.cpp)
+struct TileSet {
+    bool built = false;
+    int tile_tris = 0;
+    int32_t n_tiles = 0;
+    int64_t max_smem_units = 0;          // 12 per footprint vertex + 9 per pair (VD = 3)
+    int64_t max_smem_units2 = 0;         // 7 per footprint vertex + 4 per pair (VD = 2)
+    std::vector<int32_t> hdr;            // 8 per tile: tri begin/count, hinge begin/count,
+                                         // footprint begin/count, pairs, code begin
+    std::vector<uint16_t> tri_loc;       // 6 per triangle (tile order): 3 local ids, 3 pair slots
+    std::vector<uint16_t> hinge_loc;     // 10 per hinge (tile order): 4 local ids, 6 pair slots
+    std::vector<int32_t> tri_perm, hinge_perm;  // tile order -> canonical element index
+    std::vector<int32_t> foot;           // footprint vertex (global id)
+    std::vector<int32_t> row_start;      // BSR block of its row start; bit 31: gradient row shared
+    std::vector<int32_t> code_off;       // per footprint row + one sentinel per tile
+    std::vector<uint16_t> codes;         // per block of every footprint row
+    std::vector<int32_t> zero_blocks;    // shared blocks, zeroed before a pass
+    std::vector<int32_t> zero_verts;     // shared gradient rows
+    std::vector<int32_t> mesh_tile_off;  // n_mesh + 1
+    // device copies
+    int32_t *d_hdr = nullptr, *d_foot = nullptr, *d_row_start = nullptr, *d_code_off = nullptr;
+    uint16_t *d_tri_loc = nullptr, *d_hinge_loc = nullptr, *d_codes = nullptr;
+    int32_t *d_zero_blocks = nullptr, *d_zero_verts = nullptr, *d_mesh_tile_off = nullptr;
+    void *d_tri_rest[2] = {nullptr, nullptr};    // rest data permuted to tile order
+    void *d_hinge_rest[2] = {nullptr, nullptr};
+};
+
 struct EnergyParams {
     double E = 1.0e5, nu = 0.3, t = 1.0e-3, kb = -1.0, h = 1.0;
     double mu() const { return E / (2.0 * (1.0 + nu)); }
@@ -103,6 +131,7 @@ struct adm_ctx {
     void *d_tri_rest[2] = {nullptr, nullptr};
     void *d_hinge_rest[2] = {nullptr, nullptr};
     adm::Pattern pat[adm::PAT_COUNT];
+    adm::TileSet tiles[adm::PAT_COUNT];
     // ARAP Jacobian column pattern
     int32_t *d_jac_row_ptr = nullptr, *d_jac_col = nullptr;
     // element block tables (keyed by threads per block)
@@ -116,8 +145,8 @@ struct adm_ctx {
     int *d_status = nullptr;
     std::map<int, adm::EnergyParams> params;
     // options
-    int assembler = 1;
-    int tile_tris = 256;
+    int assembler = 0;
+    int tile_tris = 512;
     int block_threads = 128;
     // host-buffer path
     void *d_stage_x = nullptr, *d_stage_grad = nullptr, *d_stage_bsr = nullptr;
@@ -142,6 +171,9 @@ void mesh_build_pattern(const HostMesh &m, bool with_hinges, std::vector<int32_t
 void mesh_build_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr,
                       const std::vector<int32_t> &col, bool hinges, std::vector<int32_t> &tri_slots,
                       std::vector<int32_t> &hinge_slots);
+
+// tiles.cpp
+adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_tris, TileSet &ts);
 
 // kernels.cu
 struct EvalArgs {

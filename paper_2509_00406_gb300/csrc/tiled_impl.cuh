@@ -1,0 +1,271 @@
+// tiled_impl.cuh -- the tiled assembler: one block per tile of triangles and
+// hinges, shared-memory staging and accumulation, row-contiguous BSR stores.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace adm {
+
+// ----------------------------------------------------------- tiled pass --
+// One block per tile: stage the footprint positions in shared memory, run
+// every triangle and hinge term of the tile, accumulate gradient rows,
+// diagonal blocks (upper 6) and pair blocks (9, oriented lower -> higher
+// local id) with shared-memory atomics, then write every footprint row of the
+// BSR with row-contiguous stores (plain for blocks only this tile touches,
+// global atomic adds into pre-zeroed shared blocks).
+template <typename T>
+struct TiledArgs {
+    const int32_t *hdr;
+    const uint16_t *tri_loc, *hinge_loc, *codes;
+    const int32_t *foot, *row_start, *code_off;
+    const T *tri_rest, *hinge_rest;   // SoA in tile order
+    int64_t nT, nH;                   // SoA strides
+    const T *x;
+    T *grad, *bsr;
+    double *epart;
+    int *status;
+    TermConsts<T> c;
+};
+
+template <typename T, int VD, int NV, int NP, int K>
+__device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint16_t (&lid)[NV],
+                                                const uint16_t (&slot)[NP], const int (&pr)[NP][2], T *gacc,
+                                                T *dacc, T *pacc, int mode)
+{
+    constexpr int ND = VD * (VD + 1) / 2, NB = VD * VD;
+    auto H = [&](int i, int j) { return L.H[i <= j ? hix(i, j) : hix(j, i)]; };
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int d = 0; d < VD; ++d) atomicAdd(gacc + lid[a] * VD + d, L.g[a * VD + d]);
+    if (mode < MODE_HESS) return;
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int s = 0; s < VD; ++s)
+#pragma unroll
+            for (int r = 0; r <= s; ++r) atomicAdd(dacc + lid[a] * ND + hix(r, s), H(a * VD + r, a * VD + s));
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int a = pr[p][0], b = pr[p][1];
+        const bool fwd = lid[a] < lid[b];
+        T *dst = pacc + slot[p] * NB;
+#pragma unroll
+        for (int r = 0; r < VD; ++r)
+#pragma unroll
+            for (int s = 0; s < VD; ++s)
+                atomicAdd(dst + r * VD + s, fwd ? H(a * VD + r, b * VD + s) : H(b * VD + r, a * VD + s));
+    }
+}
+
+template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tiled(TiledArgs<T> A)
+{
+    constexpr int VD = TriTraits<ENERGY>::VD;
+    constexpr int K = 3 * VD;
+    constexpr int ND = VD * (VD + 1) / 2, NB = VD * VD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int t = blockIdx.x;
+    const int32_t *hd = A.hdr + 8 * t;
+    const int32_t tri_begin = hd[0], n_tri = hd[1], hinge_begin = hd[2], n_hinge = hd[3];
+    const int32_t foot_begin = hd[4], nf = hd[5], np = hd[6];
+    T *xs = sm;
+    T *gacc = xs + VD * nf;
+    T *dacc = gacc + VD * nf;
+    T *pacc = dacc + ND * nf;
+    for (int i = threadIdx.x; i < nf; i += THREADS) {
+        const int64_t v = A.foot[foot_begin + i];
+#pragma unroll
+        for (int d = 0; d < VD; ++d) xs[VD * i + d] = A.x[v * VD + d];
+    }
+    for (int i = threadIdx.x; i < (VD + ND) * nf + NB * np; i += THREADS) gacc[i] = T(0);
+    __syncthreads();
+    double fe = 0.0;
+    if constexpr (TRIS) {
+        static constexpr int TP[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (int i = threadIdx.x; i < n_tri; i += THREADS) {
+            const int64_t e = (int64_t)tri_begin + i;
+            uint16_t lid[3], slot[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                lid[a] = A.tri_loc[6 * e + a];
+                slot[a] = A.tri_loc[6 * e + 3 + a];
+            }
+            T x[K];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int d = 0; d < VD; ++d) x[a * VD + d] = xs[lid[a] * VD + d];
+            T D[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nT + e];
+            const T area = A.tri_rest[4 * A.nT + e];
+            Local<T, K> L;
+            if (!tri_term<T, ENERGY>(x, D, area, A.c, L)) {
+                atomicOr(A.status, ST_DOMAIN);
+                continue;
+            }
+            fe += (double)L.f;
+            if (MODE >= MODE_GRAD) tile_accumulate<T, VD, 3, 3, K>(L, lid, slot, TP, gacc, dacc, pacc, MODE);
+        }
+    }
+    if constexpr (HINGES) {
+        static constexpr int HP[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+        for (int i = threadIdx.x; i < n_hinge; i += THREADS) {
+            const int64_t e = (int64_t)hinge_begin + i;
+            uint16_t lid[4], slot[6];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) lid[a] = A.hinge_loc[10 * e + a];
+#pragma unroll
+            for (int p = 0; p < 6; ++p) slot[p] = A.hinge_loc[10 * e + 4 + p];
+            T x[12];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) x[a * 3 + d] = xs[lid[a] * 3 + d];
+            const T thetabar = A.hinge_rest[e];
+            const T w = A.c.kbh2 * A.hinge_rest[A.nH + e];
+            Local<T, 12> L;
+            if (!(hinge_local(x, thetabar, w, L) && isfinite(L.f))) {
+                atomicOr(A.status, ST_DOMAIN);
+                continue;
+            }
+            fe += (double)L.f;
+            if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 4, 6, 12>(L, lid, slot, HP, gacc, dacc, pacc, MODE);
+        }
+    }
+    __syncthreads();
+    if (MODE >= MODE_GRAD && A.grad) {
+        for (int i = threadIdx.x; i < nf; i += THREADS) {
+            const int32_t rs = A.row_start[foot_begin + i];
+            const int64_t v = A.foot[foot_begin + i];
+#pragma unroll
+            for (int d = 0; d < VD; ++d) {
+                const T val = gacc[VD * i + d];
+                if (rs < 0) atomicAdd(A.grad + v * VD + d, val);
+                else A.grad[v * VD + d] = val;
+            }
+        }
+    }
+    if (MODE >= MODE_HESS) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int r = warp; r < nf; r += THREADS / 32) {
+            const int64_t rs = A.row_start[foot_begin + r] & 0x7fffffff;
+            const int32_t c0 = A.code_off[foot_begin + t + r], c1 = A.code_off[foot_begin + t + r + 1];
+            for (int idx = lane; idx < (c1 - c0) * NB; idx += 32) {
+                const int e = idx / NB, k = idx - e * NB;
+                const uint32_t code = A.codes[c0 + e];
+                const uint32_t kind = code >> 14;
+                if (kind == 0) continue;
+                const int rr = k / VD, ss = k - rr * VD;
+                const int slot = (int)(code & 0x1fffu);
+                T val;
+                if (kind == 1) val = dacc[r * ND + (rr <= ss ? hix(rr, ss) : hix(ss, rr))];
+                else if (kind == 2) val = pacc[slot * NB + rr * VD + ss];
+                else val = pacc[slot * NB + ss * VD + rr];
+                T *dst = A.bsr + (rs + e) * NB + k;
+                if (code & 0x2000u) atomicAdd(dst, val);
+                else *dst = val;
+            }
+        }
+    }
+    const double sum = block_sum<THREADS>(fe);
+    if (threadIdx.x == 0) A.epart[t] = sum;
+}
+
+// zero the blocks and gradient rows that several tiles add into
+template <typename T, int VD>
+__global__ void k_zero_shared(const int32_t *blocks, int64_t nb, const int32_t *verts, int64_t nv, T *bsr,
+                              T *grad)
+{
+    constexpr int NB = VD * VD;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bsr)
+        for (int64_t i = i0; i < nb * NB; i += stride) bsr[(int64_t)blocks[i / NB] * NB + i % NB] = T(0);
+    if (grad)
+        for (int64_t i = i0; i < nv * VD; i += stride) grad[(int64_t)verts[i / VD] * VD + i % VD] = T(0);
+}
+
+template <typename T, int ENERGY, bool TRIS, bool HINGES>
+static void launch_tiled_modes(int mode, int n_tiles, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
+{
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<n_tiles, kTileThreads, smem, s>>>(A);
+    };
+    if (mode == MODE_VALUE) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_VALUE, kTileThreads>);
+    else if (mode == MODE_GRAD) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_GRAD, kTileThreads>);
+    else go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_HESS, kTileThreads>);
+}
+
+template <typename T>
+static void launch_tiled(int energy, int mode, int n_tiles, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
+{
+    switch (energy) {
+    case ADM_SYMDIR2D: launch_tiled_modes<T, ADM_SYMDIR2D, true, false>(mode, n_tiles, smem, s, A); break;
+    case ADM_STVK_MEMBRANE: launch_tiled_modes<T, ADM_STVK_MEMBRANE, true, false>(mode, n_tiles, smem, s, A); break;
+    case ADM_NH_MEMBRANE: launch_tiled_modes<T, ADM_NH_MEMBRANE, true, false>(mode, n_tiles, smem, s, A); break;
+    case ADM_AREA: launch_tiled_modes<T, ADM_AREA, true, false>(mode, n_tiles, smem, s, A); break;
+    case ADM_SHELL: launch_tiled_modes<T, ADM_SHELL, true, true>(mode, n_tiles, smem, s, A); break;
+    case ADM_HINGE_BENDING:
+        launch_tiled_modes<T, ADM_STVK_MEMBRANE, false, true>(mode, n_tiles, smem, s, A);
+        break;
+    default: break;
+    }
+}
+
+template <typename T>
+adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
+{
+    const HostMesh &m = h->m;
+    const int vd = m.vdim;
+    const bool hin = has_hinges(a.energy);
+    const TileSet &ts = h->tiles[hin ? PAT_SHELL : PAT_TRI];
+    const int mode = a.bsr ? MODE_HESS : (a.grad ? MODE_GRAD : MODE_VALUE);
+    const size_t smem = (size_t)(vd == 3 ? ts.max_smem_units : ts.max_smem_units2) * sizeof(T);
+    if (smem > 227 * 1024) return ADM_ERR_UNSUPPORTED;
+    cudaStream_t s = a.stream;
+    StageTimer tm(h, s);
+    tm.begin(ADM_STAGE_ZERO);
+    if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
+    const int64_t nzb = a.bsr ? (int64_t)ts.zero_blocks.size() : 0;
+    const int64_t nzv = a.grad ? (int64_t)ts.zero_verts.size() : 0;
+    if (nzb + nzv > 0) {
+        const int64_t work = std::max(nzb * vd * vd, nzv * vd);
+        const int blocks = (int)std::min<int64_t>((work + 255) / 256, 152 * 8);
+        if (vd == 3)
+            k_zero_shared<T, 3><<<blocks, 256, 0, s>>>(ts.d_zero_blocks, nzb, ts.d_zero_verts, nzv,
+                                                        (T *)a.bsr, (T *)a.grad);
+        else
+            k_zero_shared<T, 2><<<blocks, 256, 0, s>>>(ts.d_zero_blocks, nzb, ts.d_zero_verts, nzv,
+                                                        (T *)a.bsr, (T *)a.grad);
+    }
+    tm.end(ADM_STAGE_ZERO);
+    TiledArgs<T> A;
+    A.hdr = ts.d_hdr;
+    A.tri_loc = ts.d_tri_loc;
+    A.hinge_loc = ts.d_hinge_loc;
+    A.codes = ts.d_codes;
+    A.foot = ts.d_foot;
+    A.row_start = ts.d_row_start;
+    A.code_off = ts.d_code_off;
+    A.tri_rest = (const T *)ts.d_tri_rest[a.prec];
+    A.hinge_rest = (const T *)ts.d_hinge_rest[a.prec];
+    A.nT = m.nT;
+    A.nH = hin ? m.nH() : 0;
+    A.x = (const T *)a.x;
+    A.grad = (T *)a.grad;
+    A.bsr = (T *)a.bsr;
+    A.epart = h->d_epart;
+    A.status = h->d_status;
+    A.c = consts<T>(h, a.energy);
+    tm.begin(ADM_STAGE_TILED);
+    launch_tiled<T>(a.energy, mode, ts.n_tiles, smem, s, A);
+    tm.end(ADM_STAGE_TILED);
+    if (cudaGetLastError() != cudaSuccess) return ADM_ERR_CUDA;
+    return launch_reduce(h, a, ts.d_mesh_tile_off, nullptr, 0, tm);
+}
+
+}  // namespace adm

@@ -14,6 +14,8 @@
 // pass and written with global atomic additions; all others are written once
 // with plain stores.
 #include <algorithm>
+#include <array>
+#include <map>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -135,7 +137,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     ts.hinge_loc.resize(nH * 10);
     ts.tri_perm.resize(nT);
     ts.hinge_perm.resize(nH);
-    int64_t max_smem_units = 0;
+    int64_t max_smem_units = 0, max_smem_units2 = 0;
     std::vector<int32_t> foot;
     std::vector<int32_t> lid(m.nV, -1);
     std::map<std::pair<int32_t, int32_t>, int32_t> pair_slot;
@@ -232,11 +234,13 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         // shared-memory accumulator units: x (3) + grad (3) + diag (6) per
         // footprint vertex, 9 per pair
         max_smem_units = std::max<int64_t>(max_smem_units, 12 * (int64_t)foot.size() + 9 * (int64_t)pair_slot.size());
+        max_smem_units2 = std::max<int64_t>(max_smem_units2, 7 * (int64_t)foot.size() + 4 * (int64_t)pair_slot.size());
         for (int32_t v : foot) lid[v] = -1;
     }
     // code_off has one sentinel per tile: index of footprint row r of tile t is
     // foot_begin + r + t (the t sentinels before it)
     ts.max_smem_units = max_smem_units;
+    ts.max_smem_units2 = max_smem_units2;
     // ---- shared outputs zeroed before every pass
     for (int64_t b = 0; b < P.nnzb; ++b)
         if (blk_owner[b] == -2) ts.zero_blocks.push_back((int32_t)b);

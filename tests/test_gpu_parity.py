@@ -60,9 +60,12 @@ def gpu_eval(m: adm.Mesh, energy, prec, x, hess=True, grad=True, batch=False):
     return out
 
 
-def check(energy, prec, rest, faces, x, vd, params=None, tol=None):
+def check(energy, prec, rest, faces, x, vd, params=None, tol=None, assembler=0, tile_tris=None):
     tol = TOL[prec] if tol is None else tol
     m = adm.Mesh(rest, faces, vd)
+    m.set_option(adm.OPT_ASSEMBLER, assembler)
+    if tile_tris is not None:
+        m.set_option(adm.OPT_TILE_TRIS, tile_tris)
     if params is not None:
         m.set_params(energy, params)
     xr = np.asarray(x, dtype=NP[prec])
@@ -81,10 +84,14 @@ def check(energy, prec, rest, faces, x, vd, params=None, tol=None):
 
 
 # ---------------------------------------------------------------- C1 -------
+ASSEMBLERS = [0, 1]   # 0 tiled (default), 1 per-element atomic scatter
+
+
+@pytest.mark.parametrize("assembler", ASSEMBLERS)
 @pytest.mark.parametrize("prec", [adm.FP64, adm.FP32])
-def test_symdir_grid33(prec):
+def test_symdir_grid33(prec, assembler):
     g = synth.grid_uv()
-    check(adm.SYMDIR2D, prec, g.rest, g.faces, g.x, 2)
+    check(adm.SYMDIR2D, prec, g.rest, g.faces, g.x, 2, assembler=assembler)
 
 
 def test_symdir_identity_exact():
@@ -112,14 +119,31 @@ def test_symdir_folded_map_is_domain_error():
 SHELL_P = [1.0e5, 0.3, 1.0e-3]
 
 
+@pytest.mark.parametrize("assembler", ASSEMBLERS)
 @pytest.mark.parametrize("prec", [adm.FP64, adm.FP32])
 @pytest.mark.parametrize("energy", [adm.STVK_MEMBRANE, adm.HINGE_BENDING, adm.SHELL, adm.NH_MEMBRANE,
                                     adm.AREA])
-def test_shell_terms_icosphere3(energy, prec):
+def test_shell_terms_icosphere3(energy, prec, assembler):
     v, f = synth.icosphere(3)
     x = synth.perturb(v, 1e-2, 2)
     params = None if energy == adm.AREA else (SHELL_P if energy != adm.HINGE_BENDING else None)
-    check(energy, prec, v, f, x, 3, params=params)
+    check(energy, prec, v, f, x, 3, params=params, assembler=assembler)
+
+
+@pytest.mark.parametrize("tile_tris", [32, 100, 777, 4096])
+def test_tile_sizes_shell_fp64(tile_tris):
+    """Tiny tiles make most blocks shared between tiles (pre-zeroed, atomic
+    adds); huge tiles make one tile per mesh.  Every size gives the oracle's
+    result to FP64 rounding."""
+    v, f = synth.icosphere(4)
+    x = synth.perturb(v, 1e-2, 5)
+    check(adm.SHELL, adm.FP64, v, f, x, 3, params=SHELL_P, tile_tris=tile_tris)
+
+
+@pytest.mark.parametrize("tile_tris", [32, 512])
+def test_tile_sizes_symdir_fp64(tile_tris):
+    g = synth.grid_uv()
+    check(adm.SYMDIR2D, adm.FP64, g.rest, g.faces, g.x, 2, tile_tris=tile_tris)
 
 
 def test_hinge_list_bit_exact():
@@ -128,10 +152,13 @@ def test_hinge_list_bit_exact():
     assert np.array_equal(m.hinges().cpu().numpy(), oracle.hinges(v.shape[0], f))
 
 
-def test_open_mesh_hinges_and_pattern():
+@pytest.mark.parametrize("assembler", ASSEMBLERS)
+def test_open_mesh_hinges_and_pattern(assembler):
     d = synth.noisy_disk(2000)
     x = d.rest + synth.perturb(np.zeros_like(d.rest), 1e-3, 9)
-    check(adm.SHELL, adm.FP64, d.rest, d.faces, x, 3, params=[1.0e3, 0.3, 0.01, 0.5, 1.0])
+    check(adm.SHELL, adm.FP64, d.rest, d.faces, x, 3, params=[1.0e3, 0.3, 0.01, 0.5, 1.0],
+          assembler=assembler)
+    check(adm.HINGE_BENDING, adm.FP64, d.rest, d.faces, x, 3, params=[0.5, 1.0], assembler=assembler)
 
 
 def test_shell_level7_sampled_rows_fp32():
@@ -173,10 +200,12 @@ def test_value_and_gradient_modes_match_full(prec):
 
 
 # ------------------------------------------------------------ batch ---------
+@pytest.mark.parametrize("assembler", ASSEMBLERS)
 @pytest.mark.parametrize("prec", [adm.FP64, adm.FP32])
-def test_batch_per_mesh_energy_and_gnorm(prec):
+def test_batch_per_mesh_energy_and_gnorm(prec, assembler):
     b = synth.shell_batch([1, 3, 2, 4, 0, 3], sigma=1e-2, seed=11)
     m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_option(adm.OPT_ASSEMBLER, assembler)
     m.set_params(adm.SHELL, SHELL_P)
     xr = b.x.astype(NP[prec])
     out = gpu_eval(m, adm.SHELL, prec, xr, batch=True)
