@@ -74,16 +74,63 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     std::vector<int64_t> tile_tri_off(1, 0);
     std::vector<int32_t> tile_mesh;
     ts.mesh_tile_off.assign(m.n_mesh + 1, 0);
+    // face -> faces across its edges, to count the hinge footprint of a
+    // candidate tile (a hinge belongs to the tile of its face A)
+    std::vector<int32_t> hinges_of_face;
+    std::vector<int64_t> hof_off;
+    if (with_hinges) {
+        hof_off.assign(nT + 1, 0);
+        for (int64_t h = 0; h < m.nH(); ++h) hof_off[m.H_face[h] + 1]++;
+        for (int64_t t = 0; t < nT; ++t) hof_off[t + 1] += hof_off[t];
+        hinges_of_face.resize(m.nH());
+        std::vector<int64_t> pos(hof_off.begin(), hof_off.end() - 1);
+        for (int64_t h = 0; h < m.nH(); ++h) hinges_of_face[pos[m.H_face[h]]++] = (int32_t)h;
+    }
+    // shared-memory units (VD = 3) of the triangles order[a, b) plus their hinges
+    std::vector<int32_t> fv;
+    std::vector<std::pair<int32_t, int32_t>> pp;
+    auto units = [&](int64_t a, int64_t b) -> int64_t {
+        fv.clear();
+        pp.clear();
+        auto add = [&](const int32_t *q, int n) {
+            for (int i = 0; i < n; ++i) {
+                fv.push_back(q[i]);
+                for (int j = i + 1; j < n; ++j) pp.emplace_back(std::min(q[i], q[j]), std::max(q[i], q[j]));
+            }
+        };
+        for (int64_t i = a; i < b; ++i) {
+            add(&m.F[3 * (int64_t)order[i]], 3);
+            if (with_hinges)
+                for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k)
+                    add(&m.H[4 * (int64_t)hinges_of_face[k]], 4);
+        }
+        std::sort(fv.begin(), fv.end());
+        std::sort(pp.begin(), pp.end());
+        int64_t nf = std::unique(fv.begin(), fv.end()) - fv.begin();
+        int64_t np = std::unique(pp.begin(), pp.end()) - pp.begin();
+        return 12 * nf + 9 * np;
+    };
+    // tiles must fit the shared memory of the FP64 kernel; larger ones split
+    const int64_t budget = (227 * 1024) / 8;
     for (int k = 0; k < m.n_mesh; ++k) {
         int64_t a = m.f_off[k], b = m.f_off[k + 1];
         size_t base = order.size();
         morton_order(m, a, b, order);
         int64_t n = b - a;
         int64_t ntile = (n + tile_tris - 1) / tile_tris;
-        for (int64_t i = 0; i < ntile; ++i) {
-            // balanced split of the mesh's triangles over its tiles
-            int64_t e = (int64_t)base + (n * (i + 1)) / ntile;
-            tile_tri_off.push_back(e);
+        std::vector<std::pair<int64_t, int64_t>> stack;
+        for (int64_t i = ntile - 1; i >= 0; --i)  // balanced split, processed in order
+            stack.emplace_back((int64_t)base + (n * i) / ntile, (int64_t)base + (n * (i + 1)) / ntile);
+        while (!stack.empty()) {
+            auto [s0, s1] = stack.back();
+            stack.pop_back();
+            if (s1 - s0 > 1 && units(s0, s1) > budget) {
+                int64_t mid = (s0 + s1) / 2;
+                stack.emplace_back(mid, s1);
+                stack.emplace_back(s0, mid);
+                continue;
+            }
+            tile_tri_off.push_back(s1);
             tile_mesh.push_back(k);
         }
         ts.mesh_tile_off[k + 1] = (int32_t)tile_mesh.size();
