@@ -47,13 +47,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--assembler", type=int, default=-1, help="-1: library default")
     ap.add_argument("--tile-tris", type=int, default=0, help="0: library default")
+    ap.add_argument("--meshes", type=int, default=700, help="first N meshes of the batch (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------- workload --
-def workload(rank: int):
-    levels = synth.shell_batch_levels("paper")
+def workload(rank: int, n_mesh: int = 700):
+    levels = synth.shell_batch_levels("paper")[:n_mesh]
     mesh = synth.shell_batch(levels, sigma=1e-3, seed=4 + rank)
     return levels, mesh
 
@@ -195,10 +196,11 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(c, assembler):
+def config_dict(c, assembler, n_mesh=700):
     return {
-        "workload": "shell_batch: 700 icospheres, levels 4/5/6 = 668/28/4, StVK membrane + dihedral hinges",
-        "n_mesh": 700, **c,
+        "workload": "shell_batch: 700 icospheres, levels 4/5/6 = 668/28/4, StVK membrane + dihedral hinges"
+                    + ("" if n_mesh == 700 else f" (first {n_mesh} meshes)"),
+        "n_mesh": n_mesh, **c,
         "energy": "StVK membrane (E=1e5, nu=0.3, t=1e-3) + hinge bending (k_b = E t^3/(12(1-nu^2)), h=1)",
         "precision": "fp32 local forward-mode AD, fp64 per-mesh energy and gradient norm",
         "assembler": assembler,
@@ -222,7 +224,7 @@ def run_ours(args, rank: int, world: int, local: int):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    levels, mesh = workload(rank)
+    levels, mesh = workload(rank, args.meshes)
     c = counts(mesh)
     m = adm.Mesh(mesh.rest, mesh.faces, 3, v_off=mesh.v_off, f_off=mesh.f_off)
     m.set_params(adm.SHELL, SHELL_PARAMS)
@@ -324,7 +326,7 @@ def run_ours(args, rank: int, world: int, local: int):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(c, assembler),
+        "config": config_dict(c, assembler, args.meshes),
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": ab,

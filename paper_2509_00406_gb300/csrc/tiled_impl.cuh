@@ -58,8 +58,10 @@ __device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint
     }
 }
 
+// FP32 tiles are register-capped at two resident blocks per SM (128 registers
+// for 256 threads); FP64 keeps one block and the full register file
 template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_tiled(TiledArgs<T> A)
+__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(TiledArgs<T> A)
 {
     constexpr int VD = TriTraits<ENERGY>::VD;
     constexpr int K = 3 * VD;
