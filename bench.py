@@ -296,8 +296,10 @@ def run_ours(args, rank: int, world: int, local: int):
 
         tj = json.load(open(tfile))
         ent = tj.get(dom)
-        if ent and ent.get("source_digest") == _build._digest():
-            traffic = ent["dram_bytes_per_launch"]
+        if ent and ent.get("source_digest") == _build.kernel_digest():
+            # bytes of a full launch: the capture's bytes scaled by the
+            # algorithmic bytes of this workload over the captured workload's
+            traffic = int(ent["dram_bytes_per_launch"] * ab / ent["algorithmic_bytes"])
     except Exception:
         traffic = None
 

@@ -41,6 +41,22 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# sources of the tiled FP32 kernel; a change to any of them (or to the flags)
+# invalidates ncu counters recorded for that kernel
+TILED_KERNEL_SOURCES = ["ad.cuh", "terms.cuh", "device_common.cuh", "tiled_impl.cuh", "tiled_f32.cu"]
+
+
+def kernel_digest(files=None) -> str:
+    """Digest of the sources one kernel is compiled from, plus the flags."""
+    h = hashlib.sha256()
+    for name in (files or TILED_KERNEL_SOURCES):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    h.update(" ".join(ARCH + COMMON).encode())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     stamp = os.path.join(OUT, "stamp")
