@@ -200,6 +200,29 @@ adm_status adm_eval_jacobian(adm_handle h, adm_energy energy, adm_precision prec
  * ADM_ERR_ARG when profiling is off. */
 adm_status adm_profile_read(adm_handle h, float *avg_ms, int32_t *n_launches, int32_t n_stages);
 
+/* FP64 2-norm ||v||_2 of a device vector of n entries (float for ADM_FP32,
+ * double for ADM_FP64), written to *norm_dev (device double), enqueued on
+ * `stream`.  This is the gradient-norm reduction of adm_eval_batch as a call
+ * that allocates nothing and needs no handle; the paper has no counterpart.
+ * It is meant for callers that cannot call cudaMalloc where they need the
+ * norm: code running while its stream is captured into a CUDA graph,
+ * real-time loops whose device memory is fixed in advance, and hosts that
+ * own every device allocation through their own pool.
+ *  - Scratch: a static device array of 4096 FP64 partial sums (32 KiB) that
+ *    every GPU loading the library holds until the process exits; n may be at
+ *    most 4096 * 8192 = 33,554,432 entries, larger n returns ADM_ERR_ARG and
+ *    launches nothing.
+ *  - The first call on a device, with that device current, resolves the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's partials:
+ *    calls whose work overlaps on the GPU (different streams, no ordering)
+ *    race on it.  Calls ordered on one stream are safe; nothing needs
+ *    clearing between them.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called. */
+adm_status adm_grad_norm_noalloc(const void *v_dev, int64_t n, adm_precision prec, double *norm_dev,
+                                 void *stream);
+
 /* Device status word of the last evaluation on this handle: ADM_OK,
  * ADM_ERR_DOMAIN or ADM_ERR_TIMEOUT.  Call after synchronising the stream of
  * that evaluation; this call itself blocks until the status is read. */

@@ -74,6 +74,7 @@ def lib():
         "adm_eval_jacobian": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_get_status": (i32, [vp]),
         "adm_profile_read": (i32, [vp, C.POINTER(C.c_float), C.POINTER(i32), i32]),
+        "adm_grad_norm_noalloc": (i32, [vp, i64, i32, vp, vp]),
         "adm_strerror": (C.c_char_p, [i32]),
         "adm_destroy": (None, [vp]),
     }
@@ -219,6 +220,13 @@ class Mesh:
 
     def status(self) -> int:
         return int(lib().adm_get_status(self._h))
+
+
+def grad_norm_noalloc(v, prec: int, norm_out, stream=None):
+    """FP64 2-norm of a device vector into norm_out (device double); the call
+    allocates nothing (see adm_grad_norm_noalloc in include/adm.h)."""
+    _check(lib().adm_grad_norm_noalloc(_ptr(v), int(v.numel()), prec, _ptr(norm_out), _stream(stream)),
+           "adm_grad_norm_noalloc")
 
 
 def strerror(status: int) -> str:

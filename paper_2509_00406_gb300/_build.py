@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libadm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu",
+SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu", "noalloc.cu",
            "mesh.cpp", "tiles.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++20", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
