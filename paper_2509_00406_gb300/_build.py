@@ -14,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libadm.so")
+HOST_LIB = os.path.join(OUT, "libadm_host.so")
+HOST_SOURCES = ["host_check.cpp", "mesh.cpp", "tiles.cpp"]
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu", "noalloc.cu",
@@ -82,14 +84,41 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs],
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lpthread"],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
     os.replace(tmp, LIB)
+    build_host()
     with open(stamp, "w") as f:
         f.write(dig)
     return LIB
+
+
+def build_host() -> str:
+    """libadm_host.so: the creation-time builders (hinges, pattern, tiles)
+    compiled with the host C++ compiler alone, for GPU-free tests."""
+    os.makedirs(OUT, exist_ok=True)
+    h = hashlib.sha256()
+    for name in HOST_SOURCES + ["internal.h"]:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(INCLUDE, "adm.h"), "rb") as f:
+        h.update(f.read())
+    stamp = os.path.join(OUT, "host_stamp")
+    if os.path.exists(HOST_LIB) and os.path.exists(stamp) and open(stamp).read() == h.hexdigest():
+        return HOST_LIB
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(_nvcc())), "include")
+    tmp = HOST_LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++20", "-fPIC", "-shared", "-pthread", "-I", INCLUDE, "-I", CSRC, "-I", cuda_inc,
+           *[os.path.join(CSRC, f) for f in HOST_SOURCES], "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"host build failed:\n{r.stderr[-4000:]}")
+    os.replace(tmp, HOST_LIB)
+    with open(stamp, "w") as f:
+        f.write(h.hexdigest())
+    return HOST_LIB
 
 
 if __name__ == "__main__":

@@ -7,24 +7,27 @@
 // centroids (per mesh, never across meshes) plus the hinges whose face A is
 // one of them.  A tile stages the positions of its footprint vertices,
 // accumulates gradient and Hessian contributions of all its elements in
-// shared memory (diagonal blocks as 6 unique entries, one 3x3 block per
-// unordered vertex pair), and writes every BSR row of its footprint with
+// shared memory (diagonal blocks as their upper-triangle entries, one block
+// per unordered vertex pair), and writes every BSR row of its footprint with
 // row-contiguous stores.  Blocks and gradient rows that also receive
 // contributions from another tile are "shared": they are zeroed before the
 // pass and written with global atomic additions; all others are written once
-// with plain stores.
+// with plain stores.  Tiles are built in parallel on the host.
 #include <algorithm>
 #include <array>
-#include <map>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "internal.h"
 
 namespace adm {
 
-static uint32_t spread3(uint32_t v)
+namespace {
+
+uint32_t spread3(uint32_t v)
 {
     v &= 0x3ff;
     v = (v | (v << 16)) & 0x030000ff;
@@ -36,11 +39,11 @@ static uint32_t spread3(uint32_t v)
 
 // triangle order of one mesh: Morton code of the rest centroid in the mesh's
 // bounding box, ties by index
-static void morton_order(const HostMesh &m, int64_t t0, int64_t t1, std::vector<int32_t> &out)
+void morton_order(const HostMesh &m, int64_t t0, int64_t t1, int32_t *out)
 {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     std::vector<std::array<double, 3>> c(t1 - t0);
-    for (int64_t t = t0; t < t1; ++t) {
+    for (int64_t t = t0; t < t1; ++t)
         for (int d = 0; d < 3; ++d) {
             double s = 0.0;
             for (int k = 0; k < 3; ++k) s += m.V[3 * (int64_t)m.F[3 * t + k] + d];
@@ -48,7 +51,6 @@ static void morton_order(const HostMesh &m, int64_t t0, int64_t t1, std::vector<
             lo[d] = std::min(lo[d], c[t - t0][d]);
             hi[d] = std::max(hi[d], c[t - t0][d]);
         }
-    }
     std::vector<std::pair<uint32_t, int32_t>> key(t1 - t0);
     for (int64_t t = t0; t < t1; ++t) {
         uint32_t q[3];
@@ -60,237 +62,333 @@ static void morton_order(const HostMesh &m, int64_t t0, int64_t t1, std::vector<
         key[t - t0] = {spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2), (int32_t)t};
     }
     std::sort(key.begin(), key.end());
-    for (auto &k : key) out.push_back(k.second);
+    for (size_t i = 0; i < key.size(); ++i) out[i] = key[i].second;
 }
+
+unsigned worker_count() { return std::max(1u, std::min(16u, std::thread::hardware_concurrency())); }
+
+template <class F>
+void parallel_for(int64_t n, unsigned nt, F &&f)
+{
+    if (n < 64 || nt == 1) {
+        for (int64_t i = 0; i < n; ++i) f(i, 0u);
+        return;
+    }
+    std::atomic<int64_t> next(0);
+    std::vector<std::thread> th;
+    for (unsigned k = 0; k < nt; ++k)
+        th.emplace_back([&, k] {
+            for (int64_t i; (i = next.fetch_add(1)) < n;) f(i, k);
+        });
+    for (auto &t : th) t.join();
+}
+
+constexpr int TP[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+constexpr int HP[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+// per-thread scratch: vertex -> local id map and an open-addressing set of
+// local vertex pairs (keys lo << 16 | hi)
+struct Work {
+    std::vector<int32_t> lid;   // nV, -1 when unused
+    std::vector<uint32_t> hkey; // 0xffffffff = empty
+    std::vector<uint16_t> hval; // slot per key
+    std::vector<uint32_t> hused;
+    std::vector<int32_t> foot;
+    std::vector<uint32_t> pairs;
+    explicit Work(int64_t nV) : lid(nV, -1), hkey(1u << 16, 0xffffffffu), hval(1u << 16, 0) {}
+    static uint32_t hash(uint32_t k) { return (k * 2654435761u) >> 16; }
+    bool insert(uint32_t k)  // true if new
+    {
+        uint32_t h = hash(k);
+        while (hkey[h] != 0xffffffffu) {
+            if (hkey[h] == k) return false;
+            h = (h + 1) & 0xffffu;
+        }
+        hkey[h] = k;
+        hused.push_back(h);
+        return true;
+    }
+    uint16_t &value(uint32_t k)
+    {
+        uint32_t h = hash(k);
+        while (hkey[h] != k) h = (h + 1) & 0xffffu;
+        return hval[h];
+    }
+    void clear_pairs()
+    {
+        for (uint32_t h : hused) hkey[h] = 0xffffffffu;
+        hused.clear();
+        pairs.clear();
+    }
+};
+
+uint32_t pkey(uint32_t a, uint32_t b) { return a < b ? (a << 16 | b) : (b << 16 | a); }
+
+}  // namespace
 
 adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_tris, TileSet &ts)
 {
     const int64_t nT = m.nT, nH = with_hinges ? m.nH() : 0;
     ts = TileSet();
     ts.tile_tris = tile_tris;
-    // ---- triangle order and tiles (never across meshes)
-    std::vector<int32_t> order;
-    order.reserve(nT);
-    std::vector<int64_t> tile_tri_off(1, 0);
-    std::vector<int32_t> tile_mesh;
-    ts.mesh_tile_off.assign(m.n_mesh + 1, 0);
-    // face -> faces across its edges, to count the hinge footprint of a
-    // candidate tile (a hinge belongs to the tile of its face A)
-    std::vector<int32_t> hinges_of_face;
-    std::vector<int64_t> hof_off;
-    if (with_hinges) {
-        hof_off.assign(nT + 1, 0);
-        for (int64_t h = 0; h < m.nH(); ++h) hof_off[m.H_face[h] + 1]++;
-        for (int64_t t = 0; t < nT; ++t) hof_off[t + 1] += hof_off[t];
-        hinges_of_face.resize(m.nH());
+    // hinges by face A
+    std::vector<int64_t> hof_off(nT + 1, 0);
+    std::vector<int32_t> hinges_of_face(nH);
+    for (int64_t h = 0; h < nH; ++h) hof_off[m.H_face[h] + 1]++;
+    for (int64_t t = 0; t < nT; ++t) hof_off[t + 1] += hof_off[t];
+    {
         std::vector<int64_t> pos(hof_off.begin(), hof_off.end() - 1);
-        for (int64_t h = 0; h < m.nH(); ++h) hinges_of_face[pos[m.H_face[h]]++] = (int32_t)h;
+        for (int64_t h = 0; h < nH; ++h) hinges_of_face[pos[m.H_face[h]]++] = (int32_t)h;
     }
-    // shared-memory units (VD = 3) of the triangles order[a, b) plus their hinges
-    std::vector<int32_t> fv;
-    std::vector<std::pair<int32_t, int32_t>> pp;
-    auto units = [&](int64_t a, int64_t b) -> int64_t {
-        fv.clear();
-        pp.clear();
+    const unsigned nthr = worker_count();
+    std::vector<Work> work;
+    work.reserve(nthr);
+    for (unsigned k = 0; k < nthr; ++k) work.emplace_back(m.nV);
+
+    // shared-memory units (VD = 3) of the triangles order[a, b) and their hinges
+    std::vector<int32_t> order(nT);
+    auto units = [&](Work &w, int64_t a, int64_t b) -> int64_t {
+        w.foot.clear();
+        w.clear_pairs();
+        int64_t np = 0;
         auto add = [&](const int32_t *q, int n) {
-            for (int i = 0; i < n; ++i) {
-                fv.push_back(q[i]);
-                for (int j = i + 1; j < n; ++j) pp.emplace_back(std::min(q[i], q[j]), std::max(q[i], q[j]));
-            }
+            for (int i = 0; i < n; ++i)
+                if (w.lid[q[i]] < 0) {
+                    w.lid[q[i]] = (int32_t)w.foot.size();
+                    w.foot.push_back(q[i]);
+                }
+            for (int i = 0; i < n; ++i)
+                for (int j = i + 1; j < n; ++j) np += w.insert(pkey(w.lid[q[i]], w.lid[q[j]]));
         };
         for (int64_t i = a; i < b; ++i) {
             add(&m.F[3 * (int64_t)order[i]], 3);
-            if (with_hinges)
-                for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k)
-                    add(&m.H[4 * (int64_t)hinges_of_face[k]], 4);
+            for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k)
+                add(&m.H[4 * (int64_t)hinges_of_face[k]], 4);
         }
-        std::sort(fv.begin(), fv.end());
-        std::sort(pp.begin(), pp.end());
-        int64_t nf = std::unique(fv.begin(), fv.end()) - fv.begin();
-        int64_t np = std::unique(pp.begin(), pp.end()) - pp.begin();
-        return 12 * nf + 9 * np;
+        const int64_t u = 12 * (int64_t)w.foot.size() + 9 * np;
+        for (int32_t v : w.foot) w.lid[v] = -1;
+        w.clear_pairs();
+        return u;
     };
-    // tiles must fit the shared memory of the FP64 kernel; larger ones split
+
+    // ---- triangle order and tiles per mesh (never across meshes); tiles
+    // must fit the shared memory of the FP64 kernel, larger ones split
     const int64_t budget = (227 * 1024) / 8;
-    for (int k = 0; k < m.n_mesh; ++k) {
-        int64_t a = m.f_off[k], b = m.f_off[k + 1];
-        size_t base = order.size();
-        morton_order(m, a, b, order);
-        int64_t n = b - a;
-        int64_t ntile = (n + tile_tris - 1) / tile_tris;
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> mesh_tiles(m.n_mesh);
+    parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned th) {
+        const int64_t a = m.f_off[k], b = m.f_off[k + 1];
+        morton_order(m, a, b, order.data() + a);
+        const int64_t n = b - a;
+        const int64_t ntile = (n + tile_tris - 1) / tile_tris;
         std::vector<std::pair<int64_t, int64_t>> stack;
         for (int64_t i = ntile - 1; i >= 0; --i)  // balanced split, processed in order
-            stack.emplace_back((int64_t)base + (n * i) / ntile, (int64_t)base + (n * (i + 1)) / ntile);
+            stack.emplace_back(a + (n * i) / ntile, a + (n * (i + 1)) / ntile);
         while (!stack.empty()) {
             auto [s0, s1] = stack.back();
             stack.pop_back();
-            if (s1 - s0 > 1 && units(s0, s1) > budget) {
-                int64_t mid = (s0 + s1) / 2;
+            if (s1 - s0 > 1 && units(work[th], s0, s1) > budget) {
+                const int64_t mid = (s0 + s1) / 2;
                 stack.emplace_back(mid, s1);
                 stack.emplace_back(s0, mid);
                 continue;
             }
-            tile_tri_off.push_back(s1);
-            tile_mesh.push_back(k);
+            mesh_tiles[k].emplace_back(s0, s1);
         }
-        ts.mesh_tile_off[k + 1] = (int32_t)tile_mesh.size();
+    });
+    std::vector<int64_t> tile_tri_off(1, 0);
+    ts.mesh_tile_off.assign(m.n_mesh + 1, 0);
+    for (int k = 0; k < m.n_mesh; ++k) {
+        for (auto &r : mesh_tiles[k]) tile_tri_off.push_back(r.second);
+        ts.mesh_tile_off[k + 1] = (int32_t)(tile_tri_off.size() - 1);
     }
-    const int32_t n_tiles = (int32_t)tile_mesh.size();
+    const int32_t n_tiles = (int32_t)tile_tri_off.size() - 1;
     ts.n_tiles = n_tiles;
-    std::vector<int32_t> tri_tile(nT);
-    for (int32_t t = 0; t < n_tiles; ++t)
-        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) tri_tile[order[i]] = t;
-    // ---- hinges grouped by the tile of face A (canonical order inside a tile)
+    // hinges grouped by tile, in the order of their faces A inside the tile
     std::vector<int64_t> tile_hinge_off(n_tiles + 1, 0);
-    std::vector<int32_t> horder(nH);
-    for (int64_t h = 0; h < nH; ++h) tile_hinge_off[tri_tile[m.H_face[h]] + 1]++;
-    for (int32_t t = 0; t < n_tiles; ++t) tile_hinge_off[t + 1] += tile_hinge_off[t];
-    {
-        std::vector<int64_t> pos(tile_hinge_off.begin(), tile_hinge_off.end() - 1);
-        for (int64_t h = 0; h < nH; ++h) horder[pos[tri_tile[m.H_face[h]]]++] = (int32_t)h;
+    for (int32_t t = 0; t < n_tiles; ++t) {
+        int64_t c = 0;
+        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) c += hof_off[order[i] + 1] - hof_off[order[i]];
+        tile_hinge_off[t + 1] = tile_hinge_off[t] + c;
     }
-    // ---- global ownership of blocks and gradient rows: owner tile or -2 if shared
-    std::vector<int32_t> blk_owner(P.nnzb, -1), v_owner(m.nV, -1);
-    auto touch_block = [&](int32_t blk, int32_t t) {
-        int32_t &o = blk_owner[blk];
-        o = (o == -1 || o == t) ? t : -2;
-    };
-    auto touch_v = [&](int32_t v, int32_t t) {
-        int32_t &o = v_owner[v];
-        o = (o == -1 || o == t) ? t : -2;
-    };
-    auto block_of = [&](int32_t i, int32_t j) -> int32_t {
-        auto b = P.col.begin() + P.row_ptr[i], e = P.col.begin() + P.row_ptr[i + 1];
-        return (int32_t)(std::lower_bound(b, e, j) - P.col.begin());
-    };
-    for (int64_t t = 0; t < nT; ++t) {
-        const int32_t *f = &m.F[3 * t];
-        for (int a = 0; a < 3; ++a) {
-            touch_v(f[a], tri_tile[t]);
-            for (int b = 0; b < 3; ++b) touch_block(block_of(f[a], f[b]), tri_tile[t]);
-        }
-    }
-    for (int64_t h = 0; h < nH; ++h) {
-        const int32_t *q = &m.H[4 * h];
-        int32_t t = tri_tile[m.H_face[h]];
-        for (int a = 0; a < 4; ++a) {
-            touch_v(q[a], t);
-            for (int b = 0; b < 4; ++b) touch_block(block_of(q[a], q[b]), t);
-        }
-    }
-    // ---- per tile: footprint, pair slots, element local data, row codes
+
+    // ---- per tile: footprint (sorted global ids = local ids), pair slots
+    // (rank in (lo, hi) order), element local ids and slots
     ts.hdr.assign((size_t)n_tiles * 8, 0);
     ts.tri_loc.resize(nT * 6);
     ts.hinge_loc.resize(nH * 10);
     ts.tri_perm.resize(nT);
     ts.hinge_perm.resize(nH);
-    int64_t max_smem_units = 0, max_smem_units2 = 0;
-    std::vector<int32_t> foot;
-    std::vector<int32_t> lid(m.nV, -1);
-    std::map<std::pair<int32_t, int32_t>, int32_t> pair_slot;
-    for (int32_t t = 0; t < n_tiles; ++t) {
-        foot.clear();
-        pair_slot.clear();
-        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i)
-            for (int a = 0; a < 3; ++a) foot.push_back(m.F[3 * (int64_t)order[i] + a]);
-        for (int64_t i = tile_hinge_off[t]; i < tile_hinge_off[t + 1]; ++i)
-            for (int a = 0; a < 4; ++a) foot.push_back(m.H[4 * (int64_t)horder[i] + a]);
-        std::sort(foot.begin(), foot.end());
-        foot.erase(std::unique(foot.begin(), foot.end()), foot.end());
-        if (foot.size() > 65535) return ADM_ERR_UNSUPPORTED;
-        for (size_t r = 0; r < foot.size(); ++r) lid[foot[r]] = (int32_t)r;
-        auto slot = [&](int32_t la, int32_t lb) -> int32_t {
-            auto key = std::make_pair(std::min(la, lb), std::max(la, lb));
-            auto it = pair_slot.find(key);
-            if (it != pair_slot.end()) return it->second;
-            int32_t s = (int32_t)pair_slot.size();
-            pair_slot.emplace(key, s);
-            return s;
+    std::vector<std::vector<int32_t>> foots(n_tiles);
+    std::vector<std::vector<uint32_t>> pairs(n_tiles);
+    std::atomic<int> fail(0);
+    parallel_for(n_tiles, nthr, [&](int64_t t, unsigned th) {
+        Work &w = work[th];
+        std::vector<int32_t> &foot = foots[t];
+        auto visit = [&](const int32_t *q, int n) {
+            for (int i = 0; i < n; ++i)
+                if (w.lid[q[i]] < 0) {
+                    w.lid[q[i]] = 0;
+                    foot.push_back(q[i]);
+                }
         };
-        static const int TP[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-        static const int HP[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+        int64_t hi_idx = tile_hinge_off[t];
         for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) {
-            const int32_t *f = &m.F[3 * (int64_t)order[i]];
+            visit(&m.F[3 * (int64_t)order[i]], 3);
             ts.tri_perm[i] = order[i];
-            for (int a = 0; a < 3; ++a) ts.tri_loc[6 * i + a] = (uint16_t)lid[f[a]];
-            for (int p = 0; p < 3; ++p) ts.tri_loc[6 * i + 3 + p] = 0;  // filled after slot renumbering
+            for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k) {
+                const int32_t h = hinges_of_face[k];
+                visit(&m.H[4 * (int64_t)h], 4);
+                ts.hinge_perm[hi_idx++] = h;
+            }
+        }
+        std::sort(foot.begin(), foot.end());
+        if (foot.size() > 65535) fail = ADM_ERR_UNSUPPORTED;
+        for (size_t r = 0; r < foot.size(); ++r) w.lid[foot[r]] = (int32_t)r;
+        w.clear_pairs();
+        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) {
+            const int32_t *f = &m.F[3 * (int64_t)ts.tri_perm[i]];
+            for (int a = 0; a < 3; ++a) ts.tri_loc[6 * i + a] = (uint16_t)w.lid[f[a]];
+            for (int p = 0; p < 3; ++p) {
+                const uint32_t k = pkey(w.lid[f[TP[p][0]]], w.lid[f[TP[p][1]]]);
+                if (w.insert(k)) w.pairs.push_back(k);
+            }
         }
         for (int64_t i = tile_hinge_off[t]; i < tile_hinge_off[t + 1]; ++i) {
-            const int32_t *q = &m.H[4 * (int64_t)horder[i]];
-            ts.hinge_perm[i] = horder[i];
-            for (int a = 0; a < 4; ++a) ts.hinge_loc[10 * i + a] = (uint16_t)lid[q[a]];
+            const int32_t *q = &m.H[4 * (int64_t)ts.hinge_perm[i]];
+            for (int a = 0; a < 4; ++a) ts.hinge_loc[10 * i + a] = (uint16_t)w.lid[q[a]];
+            for (int p = 0; p < 6; ++p) {
+                const uint32_t k = pkey(w.lid[q[HP[p][0]]], w.lid[q[HP[p][1]]]);
+                if (w.insert(k)) w.pairs.push_back(k);
+            }
         }
-        // pair slots numbered in (lo, hi) order so that the accumulator walks
-        // rows in order
-        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i)
-            for (int p = 0; p < 3; ++p) slot(ts.tri_loc[6 * i + TP[p][0]], ts.tri_loc[6 * i + TP[p][1]]);
-        for (int64_t i = tile_hinge_off[t]; i < tile_hinge_off[t + 1]; ++i)
-            for (int p = 0; p < 6; ++p) slot(ts.hinge_loc[10 * i + HP[p][0]], ts.hinge_loc[10 * i + HP[p][1]]);
-        {
-            int32_t s = 0;
-            for (auto &kv : pair_slot) kv.second = s++;  // std::map iterates in (lo, hi) order
-        }
-        if (pair_slot.size() > 8191) return ADM_ERR_UNSUPPORTED;
+        std::sort(w.pairs.begin(), w.pairs.end());
+        if (w.pairs.size() > 8191) fail = ADM_ERR_UNSUPPORTED;
+        for (size_t s = 0; s < w.pairs.size(); ++s) w.value(w.pairs[s]) = (uint16_t)s;
         for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i)
             for (int p = 0; p < 3; ++p)
-                ts.tri_loc[6 * i + 3 + p] = (uint16_t)slot(ts.tri_loc[6 * i + TP[p][0]], ts.tri_loc[6 * i + TP[p][1]]);
+                ts.tri_loc[6 * i + 3 + p] = w.value(pkey(ts.tri_loc[6 * i + TP[p][0]], ts.tri_loc[6 * i + TP[p][1]]));
         for (int64_t i = tile_hinge_off[t]; i < tile_hinge_off[t + 1]; ++i)
             for (int p = 0; p < 6; ++p)
                 ts.hinge_loc[10 * i + 4 + p] =
-                    (uint16_t)slot(ts.hinge_loc[10 * i + HP[p][0]], ts.hinge_loc[10 * i + HP[p][1]]);
-        // row codes: for every footprint row, every block of its BSR row
-        const int32_t foot_begin = (int32_t)ts.foot.size();
-        const int32_t code_begin = (int32_t)ts.codes.size();
-        for (size_t r = 0; r < foot.size(); ++r) {
+                    w.value(pkey(ts.hinge_loc[10 * i + HP[p][0]], ts.hinge_loc[10 * i + HP[p][1]]));
+        pairs[t] = w.pairs;
+        w.clear_pairs();
+        for (int32_t v : foot) w.lid[v] = -1;
+    });
+    if (fail) return (adm_status)fail.load();
+
+    // ---- ownership: vertices touched by several tiles, and the vertex pairs
+    // added into by several tiles (only pairs of two such vertices can be)
+    std::vector<int32_t> v_owner(m.nV, -1);  // tile, or -2 if shared
+    for (int32_t t = 0; t < n_tiles; ++t)
+        for (int32_t v : foots[t]) v_owner[v] = (v_owner[v] == -1) ? t : -2;
+    std::vector<std::pair<uint64_t, int32_t>> bnd;
+    for (int32_t t = 0; t < n_tiles; ++t) {
+        const std::vector<int32_t> &foot = foots[t];
+        for (uint32_t k : pairs[t]) {
+            const int32_t a = foot[k >> 16], b = foot[k & 0xffff];
+            if (v_owner[a] == -2 && v_owner[b] == -2) bnd.emplace_back((uint64_t)a * (uint64_t)m.nV + b, t);
+        }
+    }
+    std::sort(bnd.begin(), bnd.end());
+    std::vector<uint64_t> shared_pairs;
+    for (size_t i = 0; i < bnd.size();) {
+        size_t j = i;
+        while (j < bnd.size() && bnd[j].first == bnd[i].first) ++j;
+        if (j - i > 1) shared_pairs.push_back(bnd[i].first);
+        i = j;
+    }
+    auto pair_shared = [&](int32_t a, int32_t b) {  // global ids, a < b
+        return std::binary_search(shared_pairs.begin(), shared_pairs.end(), (uint64_t)a * (uint64_t)m.nV + b);
+    };
+
+    // ---- row codes: the columns a tile touches in footprint row r are, in
+    // ascending order, the lower partners of r (pairs (c, r)), r itself and
+    // the upper partners (pairs (r, c)); walk them against the BSR row
+    std::vector<std::vector<uint16_t>> t_codes(n_tiles);
+    std::vector<std::vector<int32_t>> t_code_off(n_tiles), t_row_start(n_tiles), t_zero(n_tiles);
+    parallel_for(n_tiles, nthr, [&](int64_t t, unsigned) {
+        const std::vector<int32_t> &foot = foots[t];
+        const std::vector<uint32_t> &pp = pairs[t];
+        const int32_t nf = (int32_t)foot.size();
+        std::vector<int32_t> lo_off(nf + 1, 0), up_off(nf + 1, 0);
+        for (uint32_t k : pp) {
+            up_off[(k >> 16) + 1]++;
+            lo_off[(k & 0xffff) + 1]++;
+        }
+        for (int32_t r = 0; r < nf; ++r) {
+            up_off[r + 1] += up_off[r];
+            lo_off[r + 1] += lo_off[r];
+        }
+        // lower partners of every row, ascending (pp is sorted by lo)
+        std::vector<uint32_t> lower(pp.size());  // partner << 16 | slot
+        {
+            std::vector<int32_t> pos(lo_off.begin(), lo_off.end() - 1);
+            for (size_t s = 0; s < pp.size(); ++s) lower[pos[pp[s] & 0xffff]++] = (pp[s] >> 16) << 16 | (uint32_t)s;
+        }
+        std::vector<uint16_t> &codes = t_codes[t];
+        for (int32_t r = 0; r < nf; ++r) {
             const int32_t v = foot[r];
-            ts.foot.push_back(v);
-            uint32_t rs = (uint32_t)P.row_ptr[v];
-            if (v_owner[v] == -2) rs |= 0x80000000u;
-            ts.row_start.push_back((int32_t)rs);
-            ts.code_off.push_back((int32_t)ts.codes.size());
+            const bool v_sh = v_owner[v] == -2;
+            t_row_start[t].push_back((int32_t)((uint32_t)P.row_ptr[v] | (v_sh ? 0x80000000u : 0u)));
+            t_code_off[t].push_back((int32_t)codes.size());
+            int32_t li = lo_off[r], ui = up_off[r];
+            bool diag_done = false;
             for (int32_t b = P.row_ptr[v]; b < P.row_ptr[v + 1]; ++b) {
                 const int32_t c = P.col[b];
-                const int32_t lc = lid[c];
-                uint16_t code = 0;  // kind 0: not produced by this tile
-                if (lc >= 0 && blk_owner[b] != -1) {
-                    const bool mine = blk_owner[b] == t || blk_owner[b] == -2;
-                    if (lc == (int32_t)r) {
-                        code = (uint16_t)(1u << 14);  // diagonal, slot = row
-                    } else {
-                        auto it = pair_slot.find(std::make_pair(std::min<int32_t>(lc, (int32_t)r),
-                                                                std::max<int32_t>(lc, (int32_t)r)));
-                        if (it != pair_slot.end())
-                            code = (uint16_t)(((int32_t)r < lc ? 2u : 3u) << 14 | (uint32_t)it->second);
-                    }
-                    if (!mine) code = 0;
-                    if (code && blk_owner[b] == -2) code |= (uint16_t)(1u << 13);
+                uint16_t code = 0;  // kind 0: block not produced by this tile
+                if (li < lo_off[r + 1] && foot[lower[li] >> 16] == c) {
+                    code = (uint16_t)(3u << 14 | (lower[li] & 0xffffu));  // transposed pair (c, v)
+                    if (v_sh && v_owner[c] == -2 && pair_shared(c, v)) code |= (uint16_t)(1u << 13);
+                    ++li;
+                } else if (!diag_done && c == v) {
+                    code = (uint16_t)(1u << 14);  // diagonal
+                    if (v_sh) code |= (uint16_t)(1u << 13);
+                    diag_done = true;
+                } else if (ui < up_off[r + 1] && foot[pp[ui] & 0xffff] == c) {
+                    code = (uint16_t)(2u << 14 | (uint32_t)ui);  // pair (v, c)
+                    if (v_sh && v_owner[c] == -2 && pair_shared(v, c)) code |= (uint16_t)(1u << 13);
+                    ++ui;
                 }
-                ts.codes.push_back(code);
+                codes.push_back(code);
+                if (code & 0x2000) t_zero[t].push_back(b);
             }
+            if (li != lo_off[r + 1] || ui != up_off[r + 1] || !diag_done) fail = ADM_ERR_MESH;
         }
-        ts.code_off.push_back((int32_t)ts.codes.size());  // sentinel of the tile's last row
+    });
+    if (fail) return (adm_status)fail.load();
+
+    // ---- concatenate
+    int64_t max_smem_units = 0, max_smem_units2 = 0;
+    for (int32_t t = 0; t < n_tiles; ++t) {
+        const int32_t nf = (int32_t)foots[t].size(), np = (int32_t)pairs[t].size();
+        const int32_t foot_begin = (int32_t)ts.foot.size();
+        const int32_t code_begin = (int32_t)ts.codes.size();
+        ts.foot.insert(ts.foot.end(), foots[t].begin(), foots[t].end());
+        ts.row_start.insert(ts.row_start.end(), t_row_start[t].begin(), t_row_start[t].end());
+        for (int32_t c : t_code_off[t]) ts.code_off.push_back(c + code_begin);
+        ts.code_off.push_back(code_begin + (int32_t)t_codes[t].size());  // sentinel of the last row
+        ts.codes.insert(ts.codes.end(), t_codes[t].begin(), t_codes[t].end());
+        ts.zero_blocks.insert(ts.zero_blocks.end(), t_zero[t].begin(), t_zero[t].end());
         int32_t *hd = &ts.hdr[8 * (size_t)t];
         hd[0] = (int32_t)tile_tri_off[t];
         hd[1] = (int32_t)(tile_tri_off[t + 1] - tile_tri_off[t]);
         hd[2] = (int32_t)tile_hinge_off[t];
         hd[3] = (int32_t)(tile_hinge_off[t + 1] - tile_hinge_off[t]);
         hd[4] = foot_begin;
-        hd[5] = (int32_t)foot.size();
-        hd[6] = (int32_t)pair_slot.size();
+        hd[5] = nf;
+        hd[6] = np;
         hd[7] = code_begin;
-        // shared-memory accumulator units: x (3) + grad (3) + diag (6) per
-        // footprint vertex, 9 per pair
-        max_smem_units = std::max<int64_t>(max_smem_units, 12 * (int64_t)foot.size() + 9 * (int64_t)pair_slot.size());
-        max_smem_units2 = std::max<int64_t>(max_smem_units2, 7 * (int64_t)foot.size() + 4 * (int64_t)pair_slot.size());
-        for (int32_t v : foot) lid[v] = -1;
+        max_smem_units = std::max<int64_t>(max_smem_units, 12 * (int64_t)nf + 9 * (int64_t)np);
+        max_smem_units2 = std::max<int64_t>(max_smem_units2, 7 * (int64_t)nf + 4 * (int64_t)np);
     }
-    // code_off has one sentinel per tile: index of footprint row r of tile t is
-    // foot_begin + r + t (the t sentinels before it)
+    // code_off has one sentinel per tile: footprint row r of tile t is at
+    // index foot_begin + t + r
     ts.max_smem_units = max_smem_units;
     ts.max_smem_units2 = max_smem_units2;
-    // ---- shared outputs zeroed before every pass
-    for (int64_t b = 0; b < P.nnzb; ++b)
-        if (blk_owner[b] == -2) ts.zero_blocks.push_back((int32_t)b);
+    // shared outputs zeroed before every pass, each listed once
+    std::sort(ts.zero_blocks.begin(), ts.zero_blocks.end());
+    ts.zero_blocks.erase(std::unique(ts.zero_blocks.begin(), ts.zero_blocks.end()), ts.zero_blocks.end());
     for (int64_t v = 0; v < m.nV; ++v)
         if (v_owner[v] == -2) ts.zero_verts.push_back((int32_t)v);
     ts.built = true;
