@@ -28,6 +28,9 @@
  *    slot maps and work tables.  Pattern pointers stay valid until
  *    adm_destroy().  Evaluation calls allocate no memory except where
  *    stated (the first call of a CUDA graph, the host-buffer call).
+ *  - The first evaluation of an energy on a handle builds its tiles and
+ *    pattern on the host (synchronous, allocates); make it before capturing
+ *    a stream into a CUDA graph.
  *  - Outputs are fully overwritten (no accumulate-into contract).
  *  - Layouts: x and the gradient are vertex-major, x[v * var_dim + d];
  *    BSR values are nnzb blocks of var_dim x var_dim, row-major inside a
@@ -86,11 +89,21 @@ typedef enum {
                                  Sec. 5.5 scheme, kept as a reference path)    */
     ADM_OPT_TILE_TRIS = 2,    /* triangles per tile of the tiled assembler      */
     ADM_OPT_BLOCK_THREADS = 3,/* threads per block of the element kernels       */
-    ADM_OPT_PROFILE = 4       /* > 0: record CUDA events around every kernel of
+    ADM_OPT_PROFILE = 4,      /* > 0: record CUDA events around every kernel of
                                  each evaluation, on the evaluation's stream,
                                  keeping the last `value` evaluations (a ring);
                                  0: off (default).  Creates events, allocates no
                                  device memory. */
+    ADM_OPT_GRAPH = 5         /* 1: adm_eval / adm_eval_batch capture their
+                                 whole pass (zero-fill, element kernel,
+                                 reductions) into a CUDA graph on the first call
+                                 with a given (energy, precision, buffers) tuple
+                                 and replay it on later calls with the same
+                                 tuple (up to 8 tuples are kept); 0: direct
+                                 launches (default).  Capture happens on a
+                                 library stream, the replay on the caller's
+                                 stream.  Changing parameters or options drops
+                                 the captured graphs. */
 } adm_option;
 
 /* Kernel stages reported by adm_profile_read(). */
@@ -101,7 +114,8 @@ typedef enum {
     ADM_STAGE_GNORM = 3,      /* FP64 gradient-norm partials                    */
     ADM_STAGE_FINALIZE = 4,   /* per-mesh FP64 energy / norm reduction          */
     ADM_STAGE_TILED = 5,      /* fused tiled element + assembly kernel          */
-    ADM_N_STAGES = 6
+    ADM_STAGE_GRAPH = 6,      /* a whole captured pass replayed (ADM_OPT_GRAPH) */
+    ADM_N_STAGES = 7
 } adm_stage;
 
 /* --- creation ---------------------------------------------------------- */
@@ -185,6 +199,17 @@ adm_status adm_eval_batch(adm_handle h, adm_energy energy, adm_precision prec,
 adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision prec,
                                const void *x_host, double *energy_per_mesh_host,
                                double *gnorm_host, void *grad_host, void *bsr_vals_host);
+
+/* Autotuner of the tiled assembler (the batched evaluation's work split):
+ * times the full pass of `energy` at `prec` on x (device) for each candidate
+ * tile size {128, 192, 256, 384, 512, 768} triangles, keeps the fastest for
+ * this handle and returns it (and its time per pass in ms; either output may
+ * be NULL).  Synchronous; allocates temporary output buffers and rebuilds the
+ * tiles for every candidate (host work of a few seconds on a 2M-vertex
+ * batch).  Not part of the paper (Sec. 7 uses a fixed patch size of 512
+ * faces). */
+adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
+                        int32_t *best_tile_tris, float *best_ms);
 
 /* Residual r (device, 4 nT), CSR Jacobian values (device, 24 nT, in the
  * order of adm_jac_pattern) and the Gauss-Newton matrix J^T J assembled into

@@ -27,9 +27,9 @@ ARAP2D_RESIDUAL = 16
 # adm_precision
 FP64, FP32 = 0, 1
 # adm_option
-OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE = 1, 2, 3, 4
+OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE, OPT_GRAPH = 1, 2, 3, 4, 5
 # adm_stage
-STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled"]
+STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled", "graph"]
 
 STATUS = {0: "ADM_OK", -1: "ADM_ERR_ARG", -2: "ADM_ERR_MESH", -3: "ADM_ERR_DOMAIN",
           -4: "ADM_ERR_CUDA", -5: "ADM_ERR_TIMEOUT", -6: "ADM_ERR_OOM", -7: "ADM_ERR_UNSUPPORTED"}
@@ -75,6 +75,7 @@ def lib():
         "adm_get_status": (i32, [vp]),
         "adm_profile_read": (i32, [vp, C.POINTER(C.c_float), C.POINTER(i32), i32]),
         "adm_grad_norm_noalloc": (i32, [vp, i64, i32, vp, vp]),
+        "adm_autotune": (i32, [vp, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_float)]),
         "adm_strerror": (C.c_char_p, [i32]),
         "adm_destroy": (None, [vp]),
     }
@@ -209,6 +210,12 @@ class Mesh:
     def eval_jacobian(self, energy: int, prec: int, x, r, jac_vals=None, jtj=None, stream=None):
         _check(lib().adm_eval_jacobian(self._h, energy, prec, _ptr(x), _ptr(r), _ptr(jac_vals), _ptr(jtj),
                                        _stream(stream)), "adm_eval_jacobian")
+
+    def autotune(self, energy: int, prec: int, x):
+        """(best tile size, ms per pass) of the tiled assembler on x."""
+        best, ms = C.c_int32(), C.c_float()
+        _check(lib().adm_autotune(self._h, energy, prec, _ptr(x), C.byref(best), C.byref(ms)), "adm_autotune")
+        return best.value, ms.value
 
     def profile_read(self) -> dict:
         """{stage: (average ms per launch, launches)} since the last read."""

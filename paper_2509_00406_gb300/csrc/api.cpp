@@ -132,11 +132,25 @@ adm_status ensure_shell(adm_ctx *h)
     return build_pattern(h, PAT_SHELL);
 }
 
+// device arrays of a tile set (freed before a rebuild)
+void free_tiles(adm_ctx *h, TileSet &ts)
+{
+    void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_row_start, ts.d_code_off, ts.d_tri_loc, ts.d_hinge_loc,
+                    ts.d_codes, ts.d_zero_blocks, ts.d_zero_verts, ts.d_mesh_tile_off, ts.d_tri_rest[0],
+                    ts.d_tri_rest[1], ts.d_hinge_rest[0], ts.d_hinge_rest[1]};
+    for (void *p : ptrs) dev_free(h, p);
+    ts = TileSet();
+}
+
 // tiles of the tiled assembler for one pattern kind, with rest data in tile order
 adm_status ensure_tiles(adm_ctx *h, int kind)
 {
     TileSet &ts = h->tiles[kind];
     if (ts.built) return ADM_OK;
+    if (ts.d_hdr) {  // a rebuild: no pass may still read the old set
+        if (cudaDeviceSynchronize() != cudaSuccess) return ADM_ERR_CUDA;
+        free_tiles(h, ts);
+    }
     adm_status s = build_pattern(h, kind);
     if (s != ADM_OK) return s;
     s = tiles_build(h->m, h->pat[kind], kind == PAT_SHELL, h->tile_tris, ts);
@@ -210,6 +224,73 @@ adm_status prepare(adm_ctx *h, int energy)
 }
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+void drop_graphs(adm_ctx *h)
+{
+    for (auto &g : h->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    h->graphs.clear();
+}
+
+// direct launch, or capture once and replay (ADM_OPT_GRAPH)
+adm_status run_pass(adm_ctx *h, const EvalArgs &a)
+{
+    if (!h->use_graph) return launch_eval(h, a);
+    GraphEntry *hit = nullptr;
+    for (auto &g : h->graphs)
+        if (g.energy == a.energy && g.prec == a.prec && g.x == a.x && g.grad == a.grad && g.bsr == a.bsr &&
+            g.e_total == a.energy_total && g.e_mesh == a.energy_per_mesh && g.gnorm == a.gnorm_per_mesh)
+            hit = &g;
+    if (!hit) {
+        if (!h->capture_stream &&
+            cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return ADM_ERR_CUDA;
+        GraphEntry g;
+        g.energy = a.energy;
+        g.prec = a.prec;
+        g.x = a.x;
+        g.grad = a.grad;
+        g.bsr = a.bsr;
+        g.e_total = a.energy_total;
+        g.e_mesh = a.energy_per_mesh;
+        g.gnorm = a.gnorm_per_mesh;
+        EvalArgs c = a;
+        c.stream = h->capture_stream;
+        const int ring = h->prof_ring;
+        h->prof_ring = 0;  // no per-stage events inside a graph
+        if (cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            h->prof_ring = ring;
+            return ADM_ERR_CUDA;
+        }
+        adm_status s = launch_eval(h, c);
+        cudaError_t e = cudaStreamEndCapture(h->capture_stream, &g.graph);
+        h->prof_ring = ring;
+        if (s != ADM_OK || e != cudaSuccess) {
+            if (g.graph) cudaGraphDestroy(g.graph);
+            cudaGetLastError();
+            return s != ADM_OK ? s : ADM_ERR_CUDA;
+        }
+        if (cudaGraphInstantiate(&g.exec, g.graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(g.graph);
+            cudaGetLastError();
+            return ADM_ERR_CUDA;
+        }
+        if (h->graphs.size() >= 8) {
+            cudaGraphExecDestroy(h->graphs.front().exec);
+            cudaGraphDestroy(h->graphs.front().graph);
+            h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.push_back(g);
+        hit = &h->graphs.back();
+    }
+    StageTimer tm(h, a.stream);
+    tm.begin(ADM_STAGE_GRAPH);
+    if (cudaGraphLaunch(hit->exec, a.stream) != cudaSuccess) return ADM_ERR_CUDA;
+    tm.end(ADM_STAGE_GRAPH);
+    return ADM_OK;
+}
 
 }  // namespace
 
@@ -313,13 +394,19 @@ adm_status adm_set_params(adm_handle h, adm_energy energy, const double *p, int3
         return ADM_ERR_ARG;
     }
     h->params[energy] = q;
+    drop_graphs(h);
     return ADM_OK;
 }
 
 adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
 {
     if (!h) return ADM_ERR_ARG;
+    if (option != ADM_OPT_PROFILE) drop_graphs(h);
     switch (option) {
+    case ADM_OPT_GRAPH:
+        if (value != 0 && value != 1) return ADM_ERR_ARG;
+        h->use_graph = (int)value;
+        return ADM_OK;
     case ADM_OPT_ASSEMBLER:
         if (value != 0 && value != 1) return ADM_ERR_ARG;
         h->assembler = (int)value;
@@ -450,7 +537,7 @@ adm_status adm_eval_batch(adm_handle h, adm_energy energy, adm_precision prec, c
     a.energy_per_mesh = energy_per_mesh_dev;
     a.gnorm_per_mesh = gnorm_dev;
     a.stream = as_stream(stream);
-    return launch_eval(h, a);
+    return run_pass(h, a);
 }
 
 adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev, double *energy_dev,
@@ -471,7 +558,7 @@ adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const v
     a.energy_per_mesh = nullptr;
     a.gnorm_per_mesh = nullptr;
     a.stream = as_stream(stream);
-    return launch_eval(h, a);
+    return run_pass(h, a);
 }
 
 adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision prec, const void *x_host,
@@ -522,6 +609,80 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
         cudaMemcpyAsync(bsr_vals_host, h->d_stage_bsr, bb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return ADM_ERR_CUDA;
     return cudaStreamSynchronize(st) == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
+                        int32_t *best_tile_tris, float *best_ms)
+{
+    if (!h || !x_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
+    if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE || !energy_ok(energy, h->m.vdim))
+        return ADM_ERR_UNSUPPORTED;
+    const int saved_asm = h->assembler, saved_graph = h->use_graph, saved_ring = h->prof_ring;
+    h->assembler = 0;
+    h->use_graph = 0;
+    h->prof_ring = 0;
+    const int kind = needs_hinges(energy) ? PAT_SHELL : PAT_TRI;
+    adm_status s = needs_hinges(energy) ? ensure_shell(h) : build_pattern(h, PAT_TRI);
+    const size_t es = prec == ADM_FP32 ? 4 : 8;
+    const int vd = h->m.vdim;
+    void *g = nullptr, *H = nullptr;
+    double *e = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s == ADM_OK && (cudaMalloc(&g, es * h->m.nV * vd) != cudaSuccess ||
+                        cudaMalloc(&H, es * h->pat[kind].nnzb * vd * vd) != cudaSuccess ||
+                        cudaMalloc(&e, sizeof(double) * h->m.n_mesh) != cudaSuccess ||
+                        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        s = ADM_ERR_OOM;
+    static const int cand[] = {128, 192, 256, 384, 512, 768};
+    int best = -1;
+    float best_t = 1e30f;
+    for (int c : cand) {
+        if (s != ADM_OK) break;
+        h->tile_tris = c;
+        h->tiles[kind].built = false;
+        if ((s = ensure_tiles(h, kind)) != ADM_OK) break;
+        EvalArgs a;
+        a.energy = energy;
+        a.prec = prec;
+        a.vdim = vd;
+        a.x = x_dev;
+        a.grad = g;
+        a.bsr = H;
+        a.energy_total = nullptr;
+        a.energy_per_mesh = e;
+        a.gnorm_per_mesh = nullptr;
+        a.stream = st;
+        for (int w = 0; w < 2 && s == ADM_OK; ++w) s = launch_eval(h, a);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5 && s == ADM_OK; ++r) s = launch_eval(h, a);
+        cudaEventRecord(e1, st);
+        float ms = 0.0f;
+        if (s == ADM_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            s = ADM_ERR_CUDA;
+        if (s == ADM_OK && ms / 5 < best_t) {
+            best_t = ms / 5;
+            best = c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(g);
+    cudaFree(H);
+    cudaFree(e);
+    h->assembler = saved_asm;
+    h->use_graph = saved_graph;
+    h->prof_ring = saved_ring;
+    if (s != ADM_OK) return s;
+    h->tile_tris = best;
+    h->tiles[kind].built = false;
+    if ((s = ensure_tiles(h, kind)) != ADM_OK) return s;
+    h->tuned[{(int)energy, (int)prec}] = best;
+    if (best_tile_tris) *best_tile_tris = best;
+    if (best_ms) *best_ms = best_t;
+    return ADM_OK;
 }
 
 adm_status adm_eval_jacobian(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev, void *r_dev,
@@ -594,6 +755,8 @@ void adm_destroy(adm_handle h)
         cudaStreamSynchronize(h->own_stream);
         cudaStreamDestroy(h->own_stream);
     }
+    drop_graphs(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     for (void *p : h->owned) cudaFree(p);
     delete h;

@@ -113,7 +113,12 @@ struct EnergyParams {
     double kbend() const { return kb >= 0.0 ? kb : E * t * t * t / (12.0 * (1.0 - nu * nu)); }
 };
 
-struct Graph {
+// a captured evaluation pass and the arguments it was captured with
+struct GraphEntry {
+    int energy = 0, prec = 0;
+    const void *x = nullptr;
+    void *grad = nullptr, *bsr = nullptr;
+    double *e_total = nullptr, *e_mesh = nullptr, *gnorm = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -153,6 +158,12 @@ struct adm_ctx {
     double *d_stage_e = nullptr, *d_stage_gn = nullptr;
     size_t stage_x_bytes = 0, stage_grad_bytes = 0, stage_bsr_bytes = 0;
     cudaStream_t own_stream = nullptr;
+    // CUDA graphs of whole passes (ADM_OPT_GRAPH)
+    int use_graph = 0;
+    std::vector<adm::GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
+    // autotuned tile size per (energy, precision)
+    std::map<std::pair<int, int>, int> tuned;
     // kernel timing ring: per evaluation and stage, a start and an end event
     int prof_ring = 0, prof_next = 0, prof_count = 0;
     std::vector<cudaEvent_t> prof_ev;          // ring * ADM_N_STAGES * 2

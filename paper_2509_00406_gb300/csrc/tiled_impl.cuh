@@ -151,24 +151,45 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
         }
     }
     if (MODE >= MODE_HESS) {
+        // one warp per footprint row; the row's blocks are contiguous in the
+        // BSR.  Each lane decodes one block's code (smem source, layout,
+        // shared bit) once per chunk of 32 blocks; the floats of the chunk
+        // then stream out lane-contiguously with the decoded codes broadcast
+        // by shuffles.
+        constexpr uint64_t DTAB = VD == 3 ? 0x543421310ull : 0x2110ull;      // (r,s) -> packed upper
+        constexpr uint64_t TTAB = VD == 3 ? 0x852741630ull : 0x3120ull;      // (r,s) -> (s,r)
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int r = warp; r < nf; r += THREADS / 32) {
             const int64_t rs = A.row_start[foot_begin + r] & 0x7fffffff;
             const int32_t c0 = A.code_off[foot_begin + t + r], c1 = A.code_off[foot_begin + t + r + 1];
-            for (int idx = lane; idx < (c1 - c0) * NB; idx += 32) {
-                const int e = idx / NB, k = idx - e * NB;
-                const uint32_t code = A.codes[c0 + e];
-                const uint32_t kind = code >> 14;
-                if (kind == 0) continue;
-                const int rr = k / VD, ss = k - rr * VD;
-                const int slot = (int)(code & 0x1fffu);
-                T val;
-                if (kind == 1) val = dacc[r * ND + (rr <= ss ? hix(rr, ss) : hix(ss, rr))];
-                else if (kind == 2) val = pacc[slot * NB + rr * VD + ss];
-                else val = pacc[slot * NB + ss * VD + rr];
-                T *dst = A.bsr + (rs + e) * NB + k;
-                if (code & 0x2000u) atomicAdd(dst, val);
-                else *dst = val;
+            for (int cb = c0; cb < c1; cb += 32) {
+                const int nb = min(32, c1 - cb);
+                int pack = 0;  // smem base << 3 | shared << 2 | kind
+                if (lane < nb) {
+                    const uint32_t code = A.codes[cb + lane];
+                    const uint32_t kind = code >> 14;
+                    const int base = kind == 1 ? r * ND : (int)(code & 0x1fffu) * NB;
+                    pack = (int)kind | (int)((code >> 11) & 4u) | (base << 3);
+                }
+                T *out = A.bsr + (rs + (cb - c0)) * NB;
+                const T *pd = dacc, *pp = pacc;
+                const int n_it = (nb * NB + 31) >> 5;  // warp-uniform trip count
+                for (int it = 0; it < n_it; ++it) {
+                    const int idx = (it << 5) + lane;
+                    const bool valid = idx < nb * NB;
+                    const int e = valid ? idx / NB : 0;
+                    const int k = idx - e * NB;
+                    const int p = __shfl_sync(0xffffffffu, pack, e);  // all lanes take part
+                    const int kind = p & 3;
+                    if (!valid || kind == 0) continue;
+                    const int base = p >> 3;
+                    T val;
+                    if (kind == 1) val = pd[base + (int)((DTAB >> (4 * k)) & 0xf)];
+                    else if (kind == 2) val = pp[base + k];
+                    else val = pp[base + (int)((TTAB >> (4 * k)) & 0xf)];
+                    if (p & 4) atomicAdd(out + idx, val);
+                    else out[idx] = val;
+                }
             }
         }
     }

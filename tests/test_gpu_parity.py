@@ -268,3 +268,48 @@ def test_arap_jacobian_and_jtj(prec):
     Hd = oracle.bsr_to_dense(nV, 2, rp.cpu().numpy(), col.cpu().numpy(),
                              jtj.cpu().numpy().reshape(-1, 2, 2).astype(np.float64))
     assert rel(Hd, JtJ) <= tol
+
+
+# ------------------------------------------------- graphs and autotuning ---
+def test_graph_replay_matches_direct_launch():
+    b = synth.shell_batch([2, 3, 1], sigma=1e-2, seed=21)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    direct = gpu_eval(m, adm.SHELL, adm.FP64, b.x, batch=True)
+    m.set_option(adm.OPT_GRAPH, 1)
+    _, nV, nnzb, _, _ = m.pattern(adm.SHELL)
+    xd = torch.from_numpy(b.x.astype(np.float64)).cuda()
+    e = torch.zeros(b.n_mesh, dtype=torch.float64, device="cuda")
+    gn = torch.zeros(b.n_mesh, dtype=torch.float64, device="cuda")
+    g = torch.zeros(nV * 3, dtype=torch.float64, device="cuda")
+    H = torch.zeros(nnzb * 9, dtype=torch.float64, device="cuda")
+    for _ in range(3):                      # capture, then replays with the same buffers
+        H.fill_(float("nan"))
+        m.eval_batch(adm.SHELL, adm.FP64, xd, e, gn, g, H)
+        torch.cuda.synchronize()
+        assert m.status() == 0
+        assert rel(H.cpu().numpy().reshape(-1, 3, 3), direct["vals"]) <= 1e-13
+        assert np.allclose(e.cpu().numpy(), direct["energy"], rtol=1e-13)
+        assert np.allclose(gn.cpu().numpy(), direct["gnorm"], rtol=1e-13)
+    # new contents in the same buffer: the replay reads them
+    x2 = synth.perturb(b.rest, 2e-2, 99)
+    xd.copy_(torch.from_numpy(x2))
+    m.eval_batch(adm.SHELL, adm.FP64, xd, e, gn, g, H)
+    torch.cuda.synchronize()
+    m2 = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m2.set_params(adm.SHELL, SHELL_P)
+    ref = gpu_eval(m2, adm.SHELL, adm.FP64, x2, batch=True)
+    assert rel(H.cpu().numpy().reshape(-1, 3, 3), ref["vals"]) <= 1e-13
+
+
+def test_autotune_picks_a_candidate_and_stays_correct():
+    b = synth.shell_batch([3, 4, 3, 2], sigma=1e-2, seed=22)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    xd = torch.from_numpy(b.x.astype(np.float32)).cuda()
+    best, ms = m.autotune(adm.SHELL, adm.FP32, xd)
+    assert best in (128, 192, 256, 384, 512, 768) and ms > 0
+    out = gpu_eval(m, adm.SHELL, adm.FP32, b.x.astype(np.float32), batch=True)
+    P = oracle.Problem(b.rest, b.faces, oracle.SHELL, 3, params=SHELL_P)
+    ref = P.assemble(b.x.astype(np.float32).astype(np.float64))
+    assert rel(out["vals"], ref["vals"]) <= 2e-5
