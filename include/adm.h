@@ -115,7 +115,8 @@ typedef enum {
     ADM_STAGE_FINALIZE = 4,   /* per-mesh FP64 energy / norm reduction          */
     ADM_STAGE_TILED = 5,      /* fused tiled element + assembly kernel          */
     ADM_STAGE_GRAPH = 6,      /* a whole captured pass replayed (ADM_OPT_GRAPH) */
-    ADM_N_STAGES = 7
+    ADM_STAGE_MLP = 7,        /* per-triangle network table (learned membrane)  */
+    ADM_N_STAGES = 8
 } adm_stage;
 
 /* --- creation ---------------------------------------------------------- */
@@ -247,6 +248,56 @@ adm_status adm_profile_read(adm_handle h, float *avg_ms, int32_t *n_launches, in
  *  - No cudaMalloc, cudaFree or allocating library routine is called. */
 adm_status adm_grad_norm_noalloc(const void *v_dev, int64_t n, adm_precision prec, double *norm_dev,
                                  void *stream);
+
+/* --- learned membrane energy ------------------------------------------- */
+/* A per-triangle MLP surrogate of the Neo-Hookean membrane density on the
+ * invariants (I1, I2, I3) of C3 = diag(F^T F, 1): u = (I - m_I)/s_I,
+ * a1 = silu(W1 u + b1), a2 = silu(W2 a1 + b2), y = w3.a2 + b3,
+ * psi = s_psi y + m_psi, hidden width 64.  Not in the paper (it stands in for
+ * an analytic density of Sec. 7.7).  theta: ADM_MLP_NPARAM floats in the order
+ * W1 (64x3 row-major), b1 (64), W2 (64x64 row-major, row = output unit), b2
+ * (64), w3 (64), b3; the kernels use them rounded to BF16, contract on the
+ * tensor cores with FP32 accumulation.  norm: 8 floats
+ * {m_I1, m_I2, m_I3, s_I1, s_I2, s_I3, m_psi, s_psi}.  All pointers are
+ * device pointers; all calls are stream-ordered. */
+#define ADM_MLP_NPARAM 4481
+
+/* Network on n invariant samples I (n x 3): out (n x 10) = psi, dpsi/dI (3),
+ * upper Hessian in I (I1I1, I1I2, I2I2, I1I3, I2I3, I3I3), by forward mode
+ * through the network. */
+adm_status adm_mlp_eval(const float *theta, const float *norm, int64_t n, const float *I, float *out,
+                        void *stream);
+
+/* Bytes of the workspace adm_mlp_loss_grad needs (per-warp gradient partials). */
+size_t adm_mlp_workspace_size(void);
+
+/* Sobolev loss on standardised quantities,
+ *   L = mean (y - (psi - m_psi)/s_psi)^2
+ *     + beta mean sum_k (dy/du_k - dpsi/dI_k s_k / s_psi)^2,
+ * over n samples (I: n x 3, psi: n, dpsi: n x 3) and its gradient in theta
+ * (device, ADM_MLP_NPARAM floats); loss: device double (nullable).  The sum
+ * over samples is deterministic. */
+adm_status adm_mlp_loss_grad(const float *theta, const float *norm, int64_t n, const float *I,
+                             const float *psi, const float *dpsi, float beta, double *loss, float *grad,
+                             void *workspace, size_t workspace_bytes, void *stream);
+
+/* One Adam step on theta with moments m, v (all ADM_MLP_NPARAM floats);
+ * step counts from 1. */
+adm_status adm_mlp_adam(float *theta, float *m, float *v, const float *grad, int64_t step, float lr,
+                        float beta1, float beta2, float eps, void *stream);
+
+/* The analytic Neo-Hookean density (the ADM_NH_MEMBRANE density, plane-stress
+ * Lame parameters of E, nu) on n deformation samples F (n x 3 x 2 row-major):
+ * invariants I (n x 3), psi (n), dpsi/dI (n x 3). */
+adm_status adm_mlp_nh_targets(int64_t n, const float *F, double E, double nu, float *I, float *psi,
+                              float *dpsi, void *stream);
+
+/* Network used by ADM_MLP_MEMBRANE on this handle (copied; synchronous,
+ * allocates on first use).  ADM_MLP_MEMBRANE then evaluates
+ * f = thickness * A_rest * psi(I(C)) with FP32 local AD and the tiled
+ * assembler (a per-triangle network pass, stage ADM_STAGE_MLP, precedes the
+ * element kernel); FP64 and the atomic assembler return ADM_ERR_UNSUPPORTED. */
+adm_status adm_mlp_attach(adm_handle h, const float *theta, const float *norm);
 
 /* Device status word of the last evaluation on this handle: ADM_OK,
  * ADM_ERR_DOMAIN or ADM_ERR_TIMEOUT.  Call after synchronising the stream of

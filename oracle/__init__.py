@@ -65,6 +65,16 @@ def lib():
                                     C.c_double, _dp, _dp, _dp]
             L.orc_hd_probe.restype = None
             L.orc_hd_probe.argtypes = [i32, _dp, i32, _dp]
+            L.orc_invariants_from_F.restype = None
+            L.orc_invariants_from_F.argtypes = [i64, _dp, _dp]
+            L.orc_nh_targets.restype = None
+            L.orc_nh_targets.argtypes = [i64, _dp, vp, i32, _dp, _dp]
+            L.orc_mlp_eval.restype = None
+            L.orc_mlp_eval.argtypes = [_dp, _dp, i64, _dp, _dp]
+            L.orc_mlp_loss.restype = C.c_double
+            L.orc_mlp_loss.argtypes = [_dp, _dp, i64, _dp, _dp, _dp, C.c_double, vp]
+            L.orc_mlp_set.restype = None
+            L.orc_mlp_set.argtypes = [_dp, _dp]
             L.orc_arap_jacobian.restype = i64
             L.orc_arap_jacobian.argtypes = [i64, _ip, _dp, _dp, _dp, _dp, _ip, _ip, _dp]
             _lib = L
@@ -219,6 +229,51 @@ def local(energy: int, xl, vdim: int = 3, Dinv=None, area: float = 0.0, thetabar
     if err < 0:
         raise ValueError(f"no route {route} for energy {energy}")
     return {"f": float(f[0]), "g": g, "H": H.reshape(k, k), "err": int(err)}
+
+
+MLP_NPARAM = 4481
+
+
+def invariants_from_F(F):
+    """(I1, I2, I3) of C3 = diag(F^T F, 1) for F of shape (n, 3, 2)."""
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 6)
+    out = np.zeros((F.shape[0], 3))
+    lib().orc_invariants_from_F(F.shape[0], F, out)
+    return out
+
+
+def nh_targets(I, params=None):
+    """Neo-Hookean density and its gradient in the invariants."""
+    I = np.ascontiguousarray(I, dtype=np.float64).reshape(-1, 3)
+    psi = np.zeros(I.shape[0])
+    g = np.zeros((I.shape[0], 3))
+    p = _params(params)
+    lib().orc_nh_targets(I.shape[0], I, _ptr(p), 0 if p is None else len(p), psi, g)
+    return psi, g
+
+
+def mlp_eval(theta, norm, I):
+    """(n, 10): psi, dpsi/dI (3), upper Hessian (I1I1, I1I2, I2I2, I1I3, I2I3, I3I3)."""
+    I = np.ascontiguousarray(I, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((I.shape[0], 10))
+    lib().orc_mlp_eval(np.ascontiguousarray(theta, dtype=np.float64), np.ascontiguousarray(norm, dtype=np.float64),
+                       I.shape[0], I, out)
+    return out
+
+
+def mlp_set(theta, norm):
+    """Network of the MLP membrane mesh energy (energy id MLP)."""
+    lib().orc_mlp_set(np.ascontiguousarray(theta, dtype=np.float64), np.ascontiguousarray(norm, dtype=np.float64))
+
+
+def mlp_loss(theta, norm, I, psi_t, g_t, beta=1.0, grad=True):
+    """Sobolev loss and (optionally) its gradient in theta."""
+    I = np.ascontiguousarray(I, dtype=np.float64).reshape(-1, 3)
+    gbuf = np.zeros(MLP_NPARAM) if grad else None
+    L = lib().orc_mlp_loss(np.ascontiguousarray(theta, dtype=np.float64), np.ascontiguousarray(norm, dtype=np.float64),
+                           I.shape[0], I, np.ascontiguousarray(psi_t, dtype=np.float64),
+                           np.ascontiguousarray(g_t, dtype=np.float64).reshape(-1), float(beta), _ptr(gbuf))
+    return (L, gbuf) if grad else L
 
 
 def hd_probe(op: int, *inputs):

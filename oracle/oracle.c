@@ -799,6 +799,10 @@ static int touches(const asm_t *A, int nv, const int32_t *vid)
     return 0;
 }
 
+/* learned membrane energy (section 9): network parameters set by orc_mlp_set */
+static double g_mlp_theta[4481], g_mlp_norm[8];
+static int mlp_hd(const hd *x, const double *Dinv, double area, params_t q, hd *out);
+
 /* local derivatives of one triangle term; route 0 = hyper-dual, 1 = closed form */
 static int tri_local(int energy, int route, const double *xl, int vd, const double *Dinv,
                      double area, params_t q, double *f, double *g, double *H)
@@ -824,6 +828,7 @@ static int tri_local(int energy, int route, const double *xl, int vd, const doub
     case E_STVK: err = stvk_hd(xs, Dinv, area, q, &r); break;
     case E_NH: err = nh_hd(xs, Dinv, area, q, &r); break;
     case E_AREA: err = area_hd(xs, &r); break;
+    case E_MLP: err = mlp_hd(xs, Dinv, area, q, &r); break;
     default: return -2;
     }
     if (err) return err;
@@ -848,7 +853,7 @@ static int hinge_local(int route, const double *xl, double thetabar, double abar
 static int tri_term(int energy)
 {
     return energy == E_SYMDIR || energy == E_STVK || energy == E_SHELL || energy == E_NH ||
-           energy == E_AREA;
+           energy == E_AREA || energy == E_MLP;
 }
 
 /* Evaluate energy, gradient and BSR Hessian of one energy over a mesh.
@@ -996,4 +1001,226 @@ int64_t orc_arap_jacobian(int64_t nT, const int32_t *F, const double *tri_Dinv,
     }
     jrow_ptr[4 * nT] = (int32_t)(24 * nT);
     return nerr;
+}
+
+/* ======================================================================
+ * 9. Learned membrane energy (per-triangle MLP surrogate of the
+ *    Neo-Hookean density on the three invariants of C3 = diag(F^T F, 1)).
+ *    Parameters theta (4481): W1 (64x3, row j = hidden unit), b1 (64),
+ *    W2 (64x64, row i = output unit, column j = input unit), b2 (64),
+ *    w3 (64), b3.  norm (8): mean and scale of I1..I3, mean and scale of psi.
+ *    Network on standardised inputs u_k = (I_k - m_k)/s_k:
+ *      z1 = W1 u + b1, a1 = silu(z1), z2 = W2 a1 + b2, a2 = silu(z2),
+ *      y = w3 . a2 + b3,  psi = s_psi y + m_psi,  silu(z) = z / (1 + e^-z).
+ * ====================================================================== */
+#define MLP_H 64
+#define MLP_NP (MLP_H * 3 + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1)
+
+static void silu3(double z, double *s, double *s1, double *s2)
+{
+    double sg = 1.0 / (1.0 + exp(-z));
+    *s = z * sg;
+    *s1 = sg * (1.0 + z * (1.0 - sg));
+    *s2 = sg * (1.0 - sg) * (2.0 + z * (1.0 - 2.0 * sg));
+}
+
+static hd hd_silu(hd a)
+{
+    double s, s1, s2;
+    silu3(a.v, &s, &s1, &s2);
+    return hd_chain1(a, s, s1, s2);
+}
+
+/* invariants (I1, I2, I3) of C3 = diag(F^T F, 1) for n samples F (3x2 row-major) */
+void orc_invariants_from_F(int64_t n, const double *F, double *I)
+{
+    for (int64_t s = 0; s < n; ++s) {
+        const double *f = F + 6 * s;
+        double C[3][3] = {{0}};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int i = 0; i < 3; ++i) C[a][b] += f[2 * i + a] * f[2 * i + b];
+        C[2][2] = 1.0;
+        double tr = C[0][0] + C[1][1] + C[2][2], trsq = 0.0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) trsq += C[a][b] * C[b][a];
+        double det = C[0][0] * (C[1][1] * C[2][2] - C[1][2] * C[2][1]) -
+                     C[0][1] * (C[1][0] * C[2][2] - C[1][2] * C[2][0]) +
+                     C[0][2] * (C[1][0] * C[2][1] - C[1][1] * C[2][0]);
+        I[3 * s + 0] = tr;
+        I[3 * s + 1] = 0.5 * (tr * tr - trsq);
+        I[3 * s + 2] = det;
+    }
+}
+
+/* Neo-Hookean density psi(I) = mu/2 (I1 - 3) - mu ln J + lambda/2 (ln J)^2,
+ * J = sqrt(I3), and its gradient in I, by hyper-duals over (I1, I2, I3) */
+void orc_nh_targets(int64_t n, const double *I, const double *p, int np, double *psi, double *dpsi)
+{
+    params_t q = params_from(E_NH, p, np);
+    double mu = lame_mu(q), la = lame_lambda(q);
+    for (int64_t s = 0; s < n; ++s) {
+        hd i1 = hd_var(3, I[3 * s + 0], 0), i3 = hd_var(3, I[3 * s + 2], 2);
+        hd lnJ = hd_scale(hd_log(i3), 0.5);
+        hd r = hd_add(hd_sub(hd_scale(hd_addc(i1, -3.0), 0.5 * mu), hd_scale(lnJ, mu)),
+                      hd_scale(hd_sq(lnJ), 0.5 * la));
+        psi[s] = r.v;
+        for (int k = 0; k < 3; ++k) dpsi[3 * s + k] = r.g[k];
+    }
+}
+
+/* network on hyper-duals over the raw invariants: psi, dpsi/dI (3), and the
+ * upper Hessian (I1I1, I1I2, I2I2, I1I3, I2I3, I3I3) per sample */
+void orc_mlp_eval(const double *th, const double *norm, int64_t n, const double *I, double *out)
+{
+    const double *W1 = th, *b1 = W1 + MLP_H * 3, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
+                 *w3 = b2 + MLP_H, *b3 = w3 + MLP_H;
+    for (int64_t s = 0; s < n; ++s) {
+        hd u[3], a1[MLP_H];
+        for (int k = 0; k < 3; ++k)
+            u[k] = hd_scale(hd_addc(hd_var(3, I[3 * s + k], k), -norm[k]), 1.0 / norm[3 + k]);
+        for (int j = 0; j < MLP_H; ++j) {
+            hd z = hd_const(3, b1[j]);
+            for (int k = 0; k < 3; ++k) z = hd_add(z, hd_scale(u[k], W1[3 * j + k]));
+            a1[j] = hd_silu(z);
+        }
+        hd y = hd_const(3, b3[0]);
+        for (int i = 0; i < MLP_H; ++i) {
+            hd z = hd_const(3, b2[i]);
+            for (int j = 0; j < MLP_H; ++j) z = hd_add(z, hd_scale(a1[j], W2[MLP_H * i + j]));
+            y = hd_add(y, hd_scale(hd_silu(z), w3[i]));
+        }
+        y = hd_addc(hd_scale(y, norm[7]), norm[6]);
+        double *o = out + 10 * s;
+        o[0] = y.v;
+        for (int k = 0; k < 3; ++k) o[1 + k] = y.g[k];
+        o[4] = y.h[0][0];
+        o[5] = y.h[0][1];
+        o[6] = y.h[1][1];
+        o[7] = y.h[0][2];
+        o[8] = y.h[1][2];
+        o[9] = y.h[2][2];
+    }
+}
+
+/* Sobolev loss on standardised quantities,
+ *   L = mean_s (y_s - ty_s)^2 + beta mean_s sum_k (dy/du_k - tg_{s,k})^2,
+ * ty = (target psi - m_psi) / s_psi, tg_k = (target dpsi/dI_k) s_k / s_psi, and its gradient
+ * with respect to theta by reverse mode through the value-and-tangent
+ * forward pass (written out by hand; pinned by finite differences in the
+ * tests).  grad may be NULL. */
+double orc_mlp_loss(const double *th, const double *norm, int64_t n, const double *I, const double *psi_t,
+                    const double *g_t, double beta, double *grad)
+{
+    const double *W1 = th, *b1 = W1 + MLP_H * 3, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
+                 *w3 = b2 + MLP_H, *b3 = w3 + MLP_H;
+    double *gW1 = grad, *gb1 = grad ? gW1 + MLP_H * 3 : NULL, *gW2 = grad ? gb1 + MLP_H : NULL,
+           *gb2 = grad ? gW2 + MLP_H * MLP_H : NULL, *gw3 = grad ? gb2 + MLP_H : NULL,
+           *gb3 = grad ? gw3 + MLP_H : NULL;
+    if (grad) memset(grad, 0, sizeof(double) * MLP_NP);
+    double L = 0.0;
+    double u[3], z1[MLP_H], a1[MLP_H], s1p[MLP_H], s1pp[MLP_H], t1[3][MLP_H];
+    double z2[MLP_H], a2[MLP_H], s2p[MLP_H], s2pp[MLP_H], u2[3][MLP_H], t2[3][MLP_H];
+    for (int64_t s = 0; s < n; ++s) {
+        for (int k = 0; k < 3; ++k) u[k] = (I[3 * s + k] - norm[k]) / norm[3 + k];
+        for (int j = 0; j < MLP_H; ++j) {
+            z1[j] = b1[j];
+            for (int k = 0; k < 3; ++k) z1[j] += W1[3 * j + k] * u[k];
+            silu3(z1[j], &a1[j], &s1p[j], &s1pp[j]);
+            for (int k = 0; k < 3; ++k) t1[k][j] = s1p[j] * W1[3 * j + k];
+        }
+        double y = b3[0], dy[3] = {0, 0, 0};
+        for (int i = 0; i < MLP_H; ++i) {
+            z2[i] = b2[i];
+            for (int k = 0; k < 3; ++k) u2[k][i] = 0.0;
+            for (int j = 0; j < MLP_H; ++j) {
+                z2[i] += W2[MLP_H * i + j] * a1[j];
+                for (int k = 0; k < 3; ++k) u2[k][i] += W2[MLP_H * i + j] * t1[k][j];
+            }
+            silu3(z2[i], &a2[i], &s2p[i], &s2pp[i]);
+            y += w3[i] * a2[i];
+            for (int k = 0; k < 3; ++k) {
+                t2[k][i] = s2p[i] * u2[k][i];
+                dy[k] += w3[i] * t2[k][i];
+            }
+        }
+        double ty = (psi_t[s] - norm[6]) / norm[7];
+        double r0 = y - ty, rk[3];
+        L += r0 * r0;
+        for (int k = 0; k < 3; ++k) {
+            rk[k] = dy[k] - g_t[3 * s + k] * norm[3 + k] / norm[7];
+            L += beta * rk[k] * rk[k];
+        }
+        if (!grad) continue;
+        double dY = 2.0 * r0 / n, dDY[3];
+        for (int k = 0; k < 3; ++k) dDY[k] = 2.0 * beta * rk[k] / n;
+        gb3[0] += dY;
+        double dz2[MLP_H], du2[3][MLP_H];
+        for (int i = 0; i < MLP_H; ++i) {
+            gw3[i] += dY * a2[i];
+            for (int k = 0; k < 3; ++k) gw3[i] += dDY[k] * t2[k][i];
+            /* t2_k = s'(z2) u2_k, a2 = s(z2) */
+            dz2[i] = dY * w3[i] * s2p[i];
+            for (int k = 0; k < 3; ++k) {
+                dz2[i] += dDY[k] * w3[i] * s2pp[i] * u2[k][i];
+                du2[k][i] = dDY[k] * w3[i] * s2p[i];
+            }
+            gb2[i] += dz2[i];
+        }
+        for (int i = 0; i < MLP_H; ++i)
+            for (int j = 0; j < MLP_H; ++j) {
+                double g = dz2[i] * a1[j];
+                for (int k = 0; k < 3; ++k) g += du2[k][i] * t1[k][j];
+                gW2[MLP_H * i + j] += g;
+            }
+        for (int j = 0; j < MLP_H; ++j) {
+            double da1 = 0.0, dt1[3] = {0, 0, 0};
+            for (int i = 0; i < MLP_H; ++i) {
+                da1 += W2[MLP_H * i + j] * dz2[i];
+                for (int k = 0; k < 3; ++k) dt1[k] += W2[MLP_H * i + j] * du2[k][i];
+            }
+            /* t1_k = s'(z1) W1[j][k], a1 = s(z1), z1 = W1 u + b1 */
+            double dz1 = da1 * s1p[j];
+            for (int k = 0; k < 3; ++k) {
+                dz1 += dt1[k] * s1pp[j] * W1[3 * j + k];
+                gW1[3 * j + k] += dt1[k] * s1p[j];
+            }
+            gb1[j] += dz1;
+            for (int k = 0; k < 3; ++k) gW1[3 * j + k] += dz1 * u[k];
+        }
+    }
+    return L / n;
+}
+
+/* learned membrane as a mesh energy: f = t A psi(I(C)), the network run on
+ * hyper-dual numbers over the element's 9 DOFs (route 0) */
+void orc_mlp_set(const double *theta, const double *norm)
+{
+    memcpy(g_mlp_theta, theta, sizeof g_mlp_theta);
+    memcpy(g_mlp_norm, norm, sizeof g_mlp_norm);
+}
+
+static int mlp_hd(const hd *x, const double *Dinv, double area, params_t q, hd *out)
+{
+    hd I[3];
+    if (nh_invariants_hd(x, Dinv, I)) return 1;
+    const double *th = g_mlp_theta, *norm = g_mlp_norm;
+    const double *W1 = th, *b1 = W1 + MLP_H * 3, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
+                 *w3 = b2 + MLP_H, *b3 = w3 + MLP_H;
+    int k = x[0].k;
+    hd u[3], a1[MLP_H];
+    for (int c = 0; c < 3; ++c) u[c] = hd_scale(hd_addc(I[c], -norm[c]), 1.0 / norm[3 + c]);
+    for (int j = 0; j < MLP_H; ++j) {
+        hd z = hd_const(k, b1[j]);
+        for (int c = 0; c < 3; ++c) z = hd_add(z, hd_scale(u[c], W1[3 * j + c]));
+        a1[j] = hd_silu(z);
+    }
+    hd y = hd_const(k, b3[0]);
+    for (int i = 0; i < MLP_H; ++i) {
+        hd z = hd_const(k, b2[i]);
+        for (int j = 0; j < MLP_H; ++j) z = hd_add(z, hd_scale(a1[j], W2[MLP_H * i + j]));
+        y = hd_add(y, hd_scale(hd_silu(z), w3[i]));
+    }
+    *out = hd_scale(hd_addc(hd_scale(y, norm[7]), norm[6]), q.t * area);
+    return 0;
 }

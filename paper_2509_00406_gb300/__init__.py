@@ -29,7 +29,8 @@ FP64, FP32 = 0, 1
 # adm_option
 OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE, OPT_GRAPH = 1, 2, 3, 4, 5
 # adm_stage
-STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled", "graph"]
+STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled", "graph", "mlp"]
+MLP_NPARAM = 4481
 
 STATUS = {0: "ADM_OK", -1: "ADM_ERR_ARG", -2: "ADM_ERR_MESH", -3: "ADM_ERR_DOMAIN",
           -4: "ADM_ERR_CUDA", -5: "ADM_ERR_TIMEOUT", -6: "ADM_ERR_OOM", -7: "ADM_ERR_UNSUPPORTED"}
@@ -76,6 +77,12 @@ def lib():
         "adm_profile_read": (i32, [vp, C.POINTER(C.c_float), C.POINTER(i32), i32]),
         "adm_grad_norm_noalloc": (i32, [vp, i64, i32, vp, vp]),
         "adm_autotune": (i32, [vp, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_float)]),
+        "adm_mlp_eval": (i32, [vp, vp, i64, vp, vp, vp]),
+        "adm_mlp_workspace_size": (C.c_size_t, []),
+        "adm_mlp_loss_grad": (i32, [vp, vp, i64, vp, vp, vp, C.c_float, vp, vp, vp, C.c_size_t, vp]),
+        "adm_mlp_adam": (i32, [vp, vp, vp, vp, i64, C.c_float, C.c_float, C.c_float, C.c_float, vp]),
+        "adm_mlp_nh_targets": (i32, [i64, vp, C.c_double, C.c_double, vp, vp, vp, vp]),
+        "adm_mlp_attach": (i32, [vp, vp, vp]),
         "adm_strerror": (C.c_char_p, [i32]),
         "adm_destroy": (None, [vp]),
     }
@@ -217,6 +224,9 @@ class Mesh:
         _check(lib().adm_autotune(self._h, energy, prec, _ptr(x), C.byref(best), C.byref(ms)), "adm_autotune")
         return best.value, ms.value
 
+    def mlp_attach(self, theta, norm):
+        _check(lib().adm_mlp_attach(self._h, _ptr(theta), _ptr(norm)), "adm_mlp_attach")
+
     def profile_read(self) -> dict:
         """{stage: (average ms per launch, launches)} since the last read."""
         n = len(STAGES)
@@ -234,6 +244,36 @@ def grad_norm_noalloc(v, prec: int, norm_out, stream=None):
     allocates nothing (see adm_grad_norm_noalloc in include/adm.h)."""
     _check(lib().adm_grad_norm_noalloc(_ptr(v), int(v.numel()), prec, _ptr(norm_out), _stream(stream)),
            "adm_grad_norm_noalloc")
+
+
+class MLP:
+    """The learned membrane network's calls (device tensors in and out)."""
+
+    @staticmethod
+    def eval(theta, norm, I, out, stream=None):
+        _check(lib().adm_mlp_eval(_ptr(theta), _ptr(norm), I.shape[0], _ptr(I), _ptr(out), _stream(stream)),
+               "adm_mlp_eval")
+
+    @staticmethod
+    def workspace_size() -> int:
+        return int(lib().adm_mlp_workspace_size())
+
+    @staticmethod
+    def loss_grad(theta, norm, I, psi, dpsi, beta, loss, grad, workspace, stream=None):
+        _check(lib().adm_mlp_loss_grad(_ptr(theta), _ptr(norm), I.shape[0], _ptr(I), _ptr(psi), _ptr(dpsi),
+                                       float(beta), _ptr(loss), _ptr(grad), _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), _stream(stream)),
+               "adm_mlp_loss_grad")
+
+    @staticmethod
+    def adam(theta, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(lib().adm_mlp_adam(_ptr(theta), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr), float(beta1),
+                                  float(beta2), float(eps), _stream(stream)), "adm_mlp_adam")
+
+    @staticmethod
+    def nh_targets(F, E, nu, I, psi, dpsi, stream=None):
+        _check(lib().adm_mlp_nh_targets(F.shape[0], _ptr(F), float(E), float(nu), _ptr(I), _ptr(psi), _ptr(dpsi),
+                                        _stream(stream)), "adm_mlp_nh_targets")
 
 
 def strerror(status: int) -> str:

@@ -18,7 +18,7 @@ HOST_LIB = os.path.join(OUT, "libadm_host.so")
 HOST_SOURCES = ["host_check.cpp", "mesh.cpp", "tiles.cpp"]
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu", "noalloc.cu",
+SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu", "noalloc.cu", "mlp.cu",
            "mesh.cpp", "tiles.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++20", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,

@@ -135,7 +135,7 @@ adm_status ensure_shell(adm_ctx *h)
 // device arrays of a tile set (freed before a rebuild)
 void free_tiles(adm_ctx *h, TileSet &ts)
 {
-    void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_row_start, ts.d_code_off, ts.d_tri_loc, ts.d_hinge_loc,
+    void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_row_start, ts.d_code_off, ts.d_tri_loc, ts.d_hinge_loc, ts.d_tri_perm,
                     ts.d_codes, ts.d_zero_blocks, ts.d_zero_verts, ts.d_mesh_tile_off, ts.d_tri_rest[0],
                     ts.d_tri_rest[1], ts.d_hinge_rest[0], ts.d_hinge_rest[1]};
     for (void *p : ptrs) dev_free(h, p);
@@ -170,6 +170,7 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
     if ((s = up(&ts.d_zero_blocks, ts.zero_blocks)) != ADM_OK) return s;
     if ((s = up(&ts.d_zero_verts, ts.zero_verts)) != ADM_OK) return s;
     if ((s = up(&ts.d_mesh_tile_off, ts.mesh_tile_off)) != ADM_OK) return s;
+    if ((s = up(&ts.d_tri_perm, ts.tri_perm)) != ADM_OK) return s;
     {
         std::vector<std::vector<double>> f(5, std::vector<double>(m.nT));
         for (int64_t i = 0; i < m.nT; ++i) {
@@ -208,6 +209,7 @@ bool energy_ok(int energy, int vdim)
     case ADM_HINGE_BENDING:
     case ADM_SHELL:
     case ADM_NH_MEMBRANE:
+    case ADM_MLP_MEMBRANE:
     case ADM_AREA: return vdim == 3;
     default: return false;
     }
@@ -219,8 +221,12 @@ adm_status prepare(adm_ctx *h, int energy)
 {
     if (!energy_ok(energy, h->m.vdim)) return ADM_ERR_UNSUPPORTED;
     adm_status s = needs_hinges(energy) ? ensure_shell(h) : build_pattern(h, PAT_TRI);
+    if (energy == ADM_MLP_MEMBRANE && h->assembler != 0) return ADM_ERR_UNSUPPORTED;
     if (s != ADM_OK || h->assembler != 0 || energy == ADM_ARAP2D_RESIDUAL) return s;
-    return ensure_tiles(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
+    s = ensure_tiles(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
+    if (s == ADM_OK && energy == ADM_MLP_MEMBRANE && !h->d_mlp_table)
+        s = dev_alloc(h, &h->d_mlp_table, (size_t)h->m.nT * 10 * sizeof(float));
+    return s;
 }
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
@@ -523,7 +529,8 @@ adm_status adm_eval_batch(adm_handle h, adm_energy energy, adm_precision prec, c
 {
     if (!h || !x_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
     if (gnorm_dev && !grad_dev) return ADM_ERR_ARG;
-    if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE) return ADM_ERR_UNSUPPORTED;
+    if (energy == ADM_ARAP2D_RESIDUAL) return ADM_ERR_UNSUPPORTED;
+    if (energy == ADM_MLP_MEMBRANE && (prec != ADM_FP32 || !h->d_mlp_theta)) return ADM_ERR_UNSUPPORTED;
     adm_status s = prepare(h, energy);
     if (s != ADM_OK) return s;
     EvalArgs a;
@@ -544,7 +551,8 @@ adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const v
                     void *grad_dev, void *bsr_vals_dev, void *stream)
 {
     if (!h || !x_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
-    if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE) return ADM_ERR_UNSUPPORTED;
+    if (energy == ADM_ARAP2D_RESIDUAL) return ADM_ERR_UNSUPPORTED;
+    if (energy == ADM_MLP_MEMBRANE && (prec != ADM_FP32 || !h->d_mlp_theta)) return ADM_ERR_UNSUPPORTED;
     adm_status s = prepare(h, energy);
     if (s != ADM_OK) return s;
     EvalArgs a;
@@ -718,6 +726,55 @@ adm_status adm_profile_read(adm_handle h, float *avg_ms, int32_t *n_launches, in
     }
     h->prof_count = 0;
     h->prof_next = 0;
+    return ADM_OK;
+}
+
+adm_status adm_mlp_eval(const float *theta, const float *norm, int64_t n, const float *I, float *out, void *stream)
+{
+    if (!theta || !norm || n < 0 || (n > 0 && (!I || !out))) return ADM_ERR_ARG;
+    return mlp_eval_samples(theta, norm, n, I, out, as_stream(stream));
+}
+
+size_t adm_mlp_workspace_size(void) { return mlp_workspace_bytes(); }
+
+adm_status adm_mlp_loss_grad(const float *theta, const float *norm, int64_t n, const float *I, const float *psi,
+                             const float *dpsi, float beta, double *loss, float *grad, void *workspace,
+                             size_t workspace_bytes, void *stream)
+{
+    if (!theta || !norm || n <= 0 || !I || !psi || !dpsi || !grad || !workspace) return ADM_ERR_ARG;
+    return mlp_loss_grad(theta, norm, n, I, psi, dpsi, beta, loss, grad, workspace, workspace_bytes,
+                         as_stream(stream));
+}
+
+adm_status adm_mlp_adam(float *theta, float *m, float *v, const float *grad, int64_t step, float lr, float beta1,
+                        float beta2, float eps, void *stream)
+{
+    if (!theta || !m || !v || !grad || step < 1) return ADM_ERR_ARG;
+    return mlp_adam(theta, m, v, grad, step, lr, beta1, beta2, eps, as_stream(stream));
+}
+
+adm_status adm_mlp_nh_targets(int64_t n, const float *F, double E, double nu, float *I, float *psi, float *dpsi,
+                              void *stream)
+{
+    if (n < 0 || (n > 0 && (!F || !I || !psi || !dpsi))) return ADM_ERR_ARG;
+    EnergyParams p;
+    p.E = E;
+    p.nu = nu;
+    return mlp_nh_targets(n, F, p.mu(), p.lambda(), I, psi, dpsi, as_stream(stream));
+}
+
+adm_status adm_mlp_attach(adm_handle h, const float *theta, const float *norm)
+{
+    if (!h || !theta || !norm) return ADM_ERR_ARG;
+    adm_status s;
+    if (!h->d_mlp_theta) {
+        if ((s = dev_alloc(h, &h->d_mlp_theta, ADM_MLP_NPARAM * sizeof(float))) != ADM_OK) return s;
+        if ((s = dev_alloc(h, &h->d_mlp_norm, 8 * sizeof(float))) != ADM_OK) return s;
+    }
+    if (cudaMemcpy(h->d_mlp_theta, theta, ADM_MLP_NPARAM * sizeof(float), cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(h->d_mlp_norm, norm, 8 * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    drop_graphs(h);
     return ADM_OK;
 }
 

@@ -52,7 +52,8 @@ struct TriTraits {
 // local f, g, H of one triangle term; false outside the energy's domain
 template <typename T, int ENERGY>
 __device__ __forceinline__ bool tri_term(const T (&x)[TriTraits<ENERGY>::K], const T (&D)[4], T area,
-                                         const TermConsts<T> &c, Local<T, TriTraits<ENERGY>::K> &L)
+                                         const TermConsts<T> &c, Local<T, TriTraits<ENERGY>::K> &L,
+                                         const float *tab = nullptr)
 {
     bool ok = true;
     if constexpr (ENERGY == ADM_SYMDIR2D) {
@@ -64,6 +65,8 @@ __device__ __forceinline__ bool tri_term(const T (&x)[TriTraits<ENERGY>::K], con
         membrane_local(x, D, PsiNH<T>{c.mu, c.lam, c.thick * area}, L);
     } else if constexpr (ENERGY == ADM_AREA) {
         area_local(x, L);
+    } else if constexpr (ENERGY == ADM_MLP_MEMBRANE) {
+        membrane_local(x, D, PsiTable<T>{tab, c.thick * area}, L);
     }
     return ok && isfinite(L.f);
 }

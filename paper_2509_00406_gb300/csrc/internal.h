@@ -102,6 +102,7 @@ struct TileSet {
     int32_t *d_hdr = nullptr, *d_foot = nullptr, *d_row_start = nullptr, *d_code_off = nullptr;
     uint16_t *d_tri_loc = nullptr, *d_hinge_loc = nullptr, *d_codes = nullptr;
     int32_t *d_zero_blocks = nullptr, *d_zero_verts = nullptr, *d_mesh_tile_off = nullptr;
+    int32_t *d_tri_perm = nullptr;               // tile order -> canonical triangle (learned membrane)
     void *d_tri_rest[2] = {nullptr, nullptr};    // rest data permuted to tile order
     void *d_hinge_rest[2] = {nullptr, nullptr};
 };
@@ -162,6 +163,9 @@ struct adm_ctx {
     int use_graph = 0;
     std::vector<adm::GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
+    // learned membrane: network parameters (FP32 master, used BF16-rounded),
+    // input / output standardisation, per-triangle table
+    float *d_mlp_theta = nullptr, *d_mlp_norm = nullptr, *d_mlp_table = nullptr;
     // autotuned tile size per (energy, precision)
     std::map<std::pair<int, int>, int> tuned;
     // kernel timing ring: per evaluation and stage, a start and an end event
@@ -209,6 +213,21 @@ struct StageTimer {
     void begin(int stage);
     void end(int stage);
 };
+// learned membrane (mlp.cu)
+adm_status mlp_eval_samples(const float *th, const float *norm, int64_t n, const float *I, float *out,
+                            cudaStream_t s);
+size_t mlp_workspace_bytes();
+adm_status mlp_loss_grad(const float *th, const float *norm, int64_t n, const float *I, const float *psi,
+                         const float *g, float beta, double *loss, float *grad, void *ws, size_t ws_bytes,
+                         cudaStream_t s);
+adm_status mlp_adam(float *th, float *m, float *v, const float *grad, int64_t step, float lr, float b1, float b2,
+                    float eps, cudaStream_t s);
+adm_status mlp_nh_targets(int64_t n, const float *F, double mu, double lam, float *I, float *psi, float *dpsi,
+                          cudaStream_t s);
+adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *perm,
+                              const int32_t *Fv, const float *rest_tiled, const float *x, float *table,
+                              cudaStream_t s);
+
 adm_status launch_jacobian(adm_ctx *h, int prec, const void *x, void *r, void *jv, void *jtj,
                            cudaStream_t stream);
 

@@ -1,0 +1,698 @@
+// mlp.cu -- learned membrane energy: a per-triangle MLP surrogate of the
+// Neo-Hookean density on the invariants (I1, I2, I3) of C3 = diag(F^T F, 1).
+// Not part of the paper; it replaces the analytic density of a membrane term
+// (Sec. 7.7's Neo-Hookean) by a small network whose derivatives are taken by
+// the same forward mode as every other term.
+//
+// Network (parameters theta, 4481 FP32 master values, used BF16-rounded):
+//   u = (I - m_I) / s_I,  z1 = W1 u + b1,  a1 = silu(z1),
+//   z2 = W2 a1 + b2,      a2 = silu(z2),   y = w3 . a2 + b3,
+//   psi = s_psi y + m_psi;  W1 64x3, W2 64x64, silu(z) = z sigma(z).
+// Forward mode carries 10 channels per sample through the network: the value,
+// the 3 tangents along u and the 6 second-order terms.  The 64x64 contraction
+// of every channel runs on the tensor cores (mma.sync m16n8k16, BF16 inputs,
+// FP32 accumulation), one warp per 16 samples; everything elementwise is FP32.
+//
+// Training minimises the Sobolev loss on standardised quantities
+//   L = mean (y - ty)^2 + beta mean sum_k (dy/du_k - tg_k)^2
+// by reverse mode through the value + tangent forward pass; the backward
+// contractions (W2^T and the weight gradient) also run on the tensor cores.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "device_common.cuh"
+
+namespace adm {
+
+namespace {
+
+constexpr int H = 64;              // hidden width
+constexpr int LDW = H + 8;         // padded row of BF16 matrices in shared memory
+constexpr int NP = H * 3 + H + H * H + H + H + 1;  // 4481
+constexpr int WARPS = 4;           // warps per block of the MLP kernels
+
+struct MlpSmem {
+    __nv_bfloat16 W2[H * LDW];     // [i][j]: B operand of z2 = W2 a1
+    __nv_bfloat16 W2T[H * LDW];    // [j][i]: B operand of d a1 = d z2 W2
+    float W1[H * 3], b1[H], b2[H], w3[H], b3, norm[8];
+};
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16(x)); }
+
+// parameters of theta into shared memory, BF16-rounded (the network's weights)
+__device__ void load_params(MlpSmem &S, const float *th, const float *norm)
+{
+    const float *W1 = th, *b1 = W1 + H * 3, *W2 = b1 + H, *b2 = W2 + H * H, *w3 = b2 + H, *b3 = w3 + H;
+    for (int k = threadIdx.x; k < H * H; k += blockDim.x) {
+        const int i = k / H, j = k % H;
+        const __nv_bfloat16 w = __float2bfloat16(W2[k]);
+        S.W2[i * LDW + j] = w;
+        S.W2T[j * LDW + i] = w;
+    }
+    for (int k = threadIdx.x; k < H * 3; k += blockDim.x) S.W1[k] = bf16r(W1[k]);
+    for (int k = threadIdx.x; k < H; k += blockDim.x) {
+        S.b1[k] = bf16r(b1[k]);
+        S.b2[k] = bf16r(b2[k]);
+        S.w3[k] = bf16r(w3[k]);
+    }
+    if (threadIdx.x == 0) S.b3 = bf16r(b3[0]);
+    if (threadIdx.x < 8) S.norm[threadIdx.x] = norm[threadIdx.x];
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// acc (16 x 64, m16n8 accumulator layout, n-tile nn) += A (16 x 64) B where A
+// is given as per-lane fragments a[kk][4] and B through Bt[n][k] (row stride LDW)
+__device__ __forceinline__ void mma_16x64(float (&acc)[8][4], const uint32_t (&a)[4][4], const __nv_bfloat16 *Bt)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int nn = 0; nn < 8; ++nn) {
+            const uint32_t b0 = *reinterpret_cast<const uint32_t *>(Bt + (nn * 8 + g) * LDW + kk * 16 + 2 * t);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t *>(Bt + (nn * 8 + g) * LDW + kk * 16 + 2 * t + 8);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(acc[nn][0]), "+f"(acc[nn][1]), "+f"(acc[nn][2]), "+f"(acc[nn][3])
+                : "r"(a[kk][0]), "r"(a[kk][1]), "r"(a[kk][2]), "r"(a[kk][3]), "r"(b0), "r"(b1));
+        }
+}
+
+__device__ __forceinline__ void zero(float (&acc)[8][4])
+{
+#pragma unroll
+    for (int nn = 0; nn < 8; ++nn)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[nn][q] = 0.0f;
+}
+
+// A-fragment / accumulator index helpers.  Lane (g, t) owns rows g and g+8
+// (samples) and, for accumulator n-tile nn, columns 8 nn + 2 t + {0, 1};
+// the same (row, column) set forms the A fragments of k-tile kk = nn / 2.
+// Element e = nn * 4 + q: row g + 8 (q >> 1), column 8 nn + 2 t + (q & 1).
+__device__ __forceinline__ int elem_row(int e) { return ((threadIdx.x & 31) >> 2) + 8 * ((e & 3) >> 1); }
+__device__ __forceinline__ int elem_col(int e) { return 8 * (e >> 2) + 2 * (threadIdx.x & 3) + (e & 1); }
+
+__device__ __forceinline__ void silu_all(float z, float &sg, float &s, float &s1, float &s2)
+{
+    sg = 1.0f / (1.0f + expf(-z));
+    s = z * sg;
+    s1 = sg * (1.0f + z * (1.0f - sg));
+    s2 = sg * (1.0f - sg) * (2.0f + z * (1.0f - 2.0f * sg));
+}
+
+// A fragments of one channel from per-element values v[32] (element order e)
+__device__ __forceinline__ void to_frag(const float (&v)[32], uint32_t (&a)[4][4])
+{
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        // k-tile kk covers n-tiles 2 kk (cols 2t..) and 2 kk + 1 (cols 8 + 2t..)
+        const int e0 = (2 * kk) * 4, e1 = (2 * kk + 1) * 4;
+        a[kk][0] = pack_bf16(v[e0 + 0], v[e0 + 1]);  // row g,   cols 2t, 2t+1
+        a[kk][1] = pack_bf16(v[e0 + 2], v[e0 + 3]);  // row g+8
+        a[kk][2] = pack_bf16(v[e1 + 0], v[e1 + 1]);  // row g,   cols 2t+8, 2t+9
+        a[kk][3] = pack_bf16(v[e1 + 2], v[e1 + 3]);  // row g+8
+    }
+}
+
+// per-row sums across the 4 lanes of a quad (same g, t = 0..3)
+__device__ __forceinline__ float quad_sum(float v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    return v;
+}
+
+// Forward mode through the network for the 16 samples of a warp.
+// u[16][3]: standardised inputs (shared memory).  out[16][10] (shared):
+// y, dy/du_k (3), upper Hessian in u (uu00, uu01, uu11, uu02, uu12, uu22).
+// scratch: per-warp shared floats, 5 * 32 * 32.
+__device__ void warp_forward10(const MlpSmem &S, const float (*u)[3], float (*out)[10], float *scr)
+{
+    const int lane = threadIdx.x & 31;
+    // lane-strided slabs [e * 32 + lane]: z1 (1024), s'(z2) and s''(z2)
+    // (2 x 1024), d z2 / d u_k (3 x 1024)
+    float *sZ1 = scr, *sS2 = scr + 1024, *sD = scr + 3072;
+    float v[32];
+    // layer 1: z1 for the lane's (sample, unit) elements
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const int r = elem_row(e), j = elem_col(e);
+        const float z = S.b1[j] + S.W1[3 * j] * u[r][0] + S.W1[3 * j + 1] * u[r][1] + S.W1[3 * j + 2] * u[r][2];
+        sZ1[e * 32 + lane] = z;
+    }
+    float acc[8][4];
+    uint32_t a[4][4];
+    // channel order: value, tangents 0..2, second order (00, 01, 11, 02, 12, 22)
+#pragma unroll 1
+    for (int c = 0; c < 10; ++c) {
+        const int k = c == 0 ? -1 : (c < 4 ? c - 1 : (c == 4 || c == 5 || c == 7 ? 0 : (c == 6 || c == 8 ? 1 : 2)));
+        const int l = c < 4 ? -1 : (c == 4 ? 0 : (c == 5 || c == 6 ? 1 : 2));
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const float z = sZ1[e * 32 + lane];
+            float sg, s, s1, s2;
+            silu_all(z, sg, s, s1, s2);
+            const int j = elem_col(e);
+            v[e] = c == 0 ? s : (l < 0 ? s1 * S.W1[3 * j + k] : s2 * S.W1[3 * j + k] * S.W1[3 * j + l]);
+        }
+        to_frag(v, a);
+        zero(acc);
+        mma_16x64(acc, a, S.W2);
+        // layer 2 and output, per element of the accumulator
+        float p0 = 0.0f, p1 = 0.0f;  // rows g and g+8
+#pragma unroll
+        for (int nn = 0; nn < 8; ++nn)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = nn * 4 + q, i = elem_col(e);
+                float w;
+                if (c == 0) {
+                    const float z2 = acc[nn][q] + S.b2[i];
+                    float sg, s, s1, s2;
+                    silu_all(z2, sg, s, s1, s2);
+                    sS2[e * 32 + lane] = s1;                // s'(z2)
+                    sS2[(32 + e) * 32 + lane] = s2;         // s''(z2)
+                    w = S.w3[i] * s;
+                } else if (l < 0) {
+                    sD[(k * 32 + e) * 32 + lane] = acc[nn][q];  // d z2 / d u_k
+                    w = S.w3[i] * sS2[e * 32 + lane] * acc[nn][q];
+                } else {
+                    const float dk = sD[(k * 32 + e) * 32 + lane], dl = sD[(l * 32 + e) * 32 + lane];
+                    w = S.w3[i] * (sS2[(32 + e) * 32 + lane] * dk * dl + sS2[e * 32 + lane] * acc[nn][q]);
+                }
+                if (q < 2) p0 += w;
+                else p1 += w;
+            }
+        p0 = quad_sum(p0);
+        p1 = quad_sum(p1);
+        if ((lane & 3) == 0) {
+            out[lane >> 2][c] = p0 + (c == 0 ? S.b3 : 0.0f);
+            out[(lane >> 2) + 8][c] = p1 + (c == 0 ? S.b3 : 0.0f);
+        }
+    }
+    __syncwarp();
+}
+
+// scratch floats per warp of warp_forward10: z1 (1024), s'(z2) and s''(z2)
+// (2048), d z2 / d u_k (3 * 1024)
+constexpr int FWD_SCRATCH = 1024 + 2048 + 3 * 1024;
+
+// ---------------------------------------------------------------- kernels --
+// samples: invariants I (n x 3) -> psi, dpsi/dI (3), upper Hessian in I (6)
+__global__ void __launch_bounds__(WARPS * 32) k_mlp_eval(const float *th, const float *norm, int64_t n,
+                                                          const float *I, float *out)
+{
+    __shared__ MlpSmem S;
+    __shared__ float su[WARPS][16][3], so[WARPS][16][10];
+    extern __shared__ float scr_all[];
+    load_params(S, th, norm);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *scr = scr_all + w * FWD_SCRATCH;
+    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 16; base < n; base += (int64_t)gridDim.x * WARPS * 16) {
+        if (lane < 16) {
+            const int64_t s = base + lane;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                su[w][lane][k] = s < n ? (I[3 * s + k] - S.norm[k]) / S.norm[3 + k] : 0.0f;
+        }
+        __syncwarp();
+        warp_forward10(S, su[w], so[w], scr);
+        if (lane < 16 && base + lane < n) {
+            const int64_t s = base + lane;
+            const float sp = S.norm[7], si[3] = {S.norm[3], S.norm[4], S.norm[5]};
+            float *o = out + 10 * s;
+            o[0] = sp * so[w][lane][0] + S.norm[6];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) o[1 + k] = sp * so[w][lane][1 + k] / si[k];
+            const int HK[6] = {0, 0, 1, 0, 1, 2}, HL[6] = {0, 1, 1, 2, 2, 2};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) o[4 + q] = sp * so[w][lane][4 + q] / (si[HK[q]] * si[HL[q]]);
+        }
+        __syncwarp();
+    }
+}
+
+
+// ------------------------------------------------------------- training --
+constexpr int TWARPS = 2;  // warps per block of the training kernel
+
+struct TrainWarp {            // per-warp shared memory of the training kernel
+    float z1[1024], z2[1024], dz2[3][1024];      // lane-strided slabs
+    __nv_bfloat16 AT[H * LDW];                   // [i][(c, s)]: dz2^T | du2_k^T
+    __nv_bfloat16 BT[H * LDW];                   // [j][(c, s)]: a1^T | t1_k^T
+    float gW2[H * H];                            // gradient partials of this warp
+    float gW1[H * 3], gb1[H], gb2[H], gw3[H], gb3;
+    float u[16][3], ty[16], tg[16][3], dY[16], dDY[16][3], y[16], dy[16][3];
+    double loss;
+};
+
+// column sums over the 16 rows of a warp tile: lanes with the same t hold the
+// same columns; reduce across g (lane bits 2..4)
+__device__ __forceinline__ float col_sum(float v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    return v;
+}
+
+__global__ void __launch_bounds__(TWARPS * 32) k_mlp_grad(const float *th, const float *norm, int64_t n,
+                                                          const float *I, const float *psi_t, const float *g_t,
+                                                          float beta, float *part, double *part_loss)
+{
+    __shared__ MlpSmem S;
+    extern __shared__ __align__(16) unsigned char tw_raw[];
+    TrainWarp *TWs = reinterpret_cast<TrainWarp *>(tw_raw);
+    load_params(S, th, norm);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    TrainWarp &W = TWs[w];
+    for (int k = lane; k < H * H; k += 32) W.gW2[k] = 0.0f;
+    for (int k = lane; k < H * 3; k += 32) W.gW1[k] = 0.0f;
+    for (int k = lane; k < H; k += 32) W.gb1[k] = W.gb2[k] = W.gw3[k] = 0.0f;
+    if (lane == 0) {
+        W.gb3 = 0.0f;
+        W.loss = 0.0;
+    }
+    __syncthreads();
+    const float inv_n = 1.0f / (float)n;
+    float acc[8][4];
+    uint32_t a[4][4];
+    float v[32];
+    for (int64_t base = ((int64_t)blockIdx.x * TWARPS + w) * 16; base < n; base += (int64_t)gridDim.x * TWARPS * 16) {
+        if (lane < 16) {
+            const int64_t sidx = base + lane;
+            const bool ok = sidx < n;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                W.u[lane][k] = ok ? (I[3 * sidx + k] - S.norm[k]) / S.norm[3 + k] : 0.0f;
+                W.tg[lane][k] = ok ? g_t[3 * sidx + k] * S.norm[3 + k] / S.norm[7] : 0.0f;
+            }
+            W.ty[lane] = ok ? (psi_t[sidx] - S.norm[6]) / S.norm[7] : 0.0f;
+        }
+        __syncwarp();
+        // ---- forward: z1, value and tangent channels
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const int r = elem_row(e), j = elem_col(e);
+            W.z1[e * 32 + lane] = S.b1[j] + S.W1[3 * j] * W.u[r][0] + S.W1[3 * j + 1] * W.u[r][1] + S.W1[3 * j + 2] * W.u[r][2];
+        }
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                float sg, s0, s1, s2;
+                silu_all(W.z1[e * 32 + lane], sg, s0, s1, s2);
+                v[e] = c == 0 ? s0 : s1 * S.W1[3 * elem_col(e) + c - 1];
+            }
+            to_frag(v, a);
+            zero(acc);
+            mma_16x64(acc, a, S.W2);
+            float p0 = 0.0f, p1 = 0.0f;
+#pragma unroll
+            for (int nn = 0; nn < 8; ++nn)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = nn * 4 + q, i = elem_col(e);
+                    float wv;
+                    if (c == 0) {
+                        const float z2 = acc[nn][q] + S.b2[i];
+                        W.z2[e * 32 + lane] = z2;
+                        float sg, s0, s1, s2;
+                        silu_all(z2, sg, s0, s1, s2);
+                        wv = S.w3[i] * s0;
+                    } else {
+                        W.dz2[c - 1][e * 32 + lane] = acc[nn][q];
+                        float sg, s0, s1, s2;
+                        silu_all(W.z2[e * 32 + lane], sg, s0, s1, s2);
+                        wv = S.w3[i] * s1 * acc[nn][q];
+                    }
+                    if (q < 2) p0 += wv;
+                    else p1 += wv;
+                }
+            p0 = quad_sum(p0);
+            p1 = quad_sum(p1);
+            if (t == 0) {
+                if (c == 0) {
+                    W.y[g] = p0 + S.b3;
+                    W.y[g + 8] = p1 + S.b3;
+                } else {
+                    W.dy[g][c - 1] = p0;
+                    W.dy[g + 8][c - 1] = p1;
+                }
+            }
+        }
+        __syncwarp();
+        // ---- loss and output adjoints (rows beyond n contribute nothing)
+        if (lane < 16) {
+            const bool ok = base + lane < n;
+            const float r0 = W.y[lane] - W.ty[lane];
+            float l = r0 * r0;
+            W.dY[lane] = ok ? 2.0f * r0 * inv_n : 0.0f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float rk = W.dy[lane][k] - W.tg[lane][k];
+                l += beta * rk * rk;
+                W.dDY[lane][k] = ok ? 2.0f * beta * rk * inv_n : 0.0f;
+            }
+            double ls = ok ? (double)l : 0.0;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) ls += __shfl_down_sync(0x0000ffffu, ls, o, 16);
+            if (lane == 0) W.loss += ls;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            float sb3 = 0.0f;
+            for (int r = 0; r < 16; ++r) sb3 += W.dY[r];
+            W.gb3 += sb3;
+        }
+        // ---- layer 2 adjoints per element: dz2, du2_k; gradients of w3, b2
+        float dz2v[32], du2v[3][32];
+        {
+            float cw3[16], cb2[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) cw3[q] = cb2[q] = 0.0f;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int r = elem_row(e), i = elem_col(e);
+                float sg, s0, s1, s2;
+                silu_all(W.z2[e * 32 + lane], sg, s0, s1, s2);
+                float dz = W.dY[r] * S.w3[i] * s1;
+                float gw = W.dY[r] * s0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float d = W.dz2[k][e * 32 + lane];
+                    dz += W.dDY[r][k] * S.w3[i] * s2 * d;
+                    du2v[k][e] = W.dDY[r][k] * S.w3[i] * s1;
+                    gw += W.dDY[r][k] * s1 * d;
+                }
+                dz2v[e] = dz;
+                // column (e >> 2, e & 1) of the lane: q index = (e >> 2) * 2 + (e & 1)
+                cw3[(e >> 2) * 2 + (e & 1)] += gw;
+                cb2[(e >> 2) * 2 + (e & 1)] += dz;
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float sw = col_sum(cw3[q]), sb = col_sum(cb2[q]);
+                if (g == 0) {
+                    const int i = 8 * (q >> 1) + 2 * t + (q & 1);
+                    W.gw3[i] += sw;
+                    W.gb2[i] += sb;
+                }
+            }
+        }
+        // ---- stage operands of the W2 gradient: AT[i][(c,s)], BT[j][(c,s)]
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const int r = elem_row(e), col = elem_col(e);
+            float sg, s0, s1, s2;
+            silu_all(W.z1[e * 32 + lane], sg, s0, s1, s2);
+            W.AT[col * LDW + r] = __float2bfloat16(dz2v[e]);
+            W.BT[col * LDW + r] = __float2bfloat16(s0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                W.AT[col * LDW + 16 * (k + 1) + r] = __float2bfloat16(du2v[k][e]);
+                W.BT[col * LDW + 16 * (k + 1) + r] = __float2bfloat16(s1 * S.W1[3 * col + k]);
+            }
+        }
+        __syncwarp();
+        // ---- dW2[i][j] += sum_(c,s) AT[i][(c,s)] BT[j][(c,s)]  (4 m-tiles of i)
+#pragma unroll 1
+        for (int mi = 0; mi < 4; ++mi) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const __nv_bfloat16 *Ar = W.AT + (mi * 16) * LDW + kk * 16;
+                a[kk][0] = *reinterpret_cast<const uint32_t *>(Ar + g * LDW + 2 * t);
+                a[kk][1] = *reinterpret_cast<const uint32_t *>(Ar + (g + 8) * LDW + 2 * t);
+                a[kk][2] = *reinterpret_cast<const uint32_t *>(Ar + g * LDW + 2 * t + 8);
+                a[kk][3] = *reinterpret_cast<const uint32_t *>(Ar + (g + 8) * LDW + 2 * t + 8);
+            }
+            zero(acc);
+            mma_16x64(acc, a, W.BT);
+#pragma unroll
+            for (int nn = 0; nn < 8; ++nn)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = nn * 4 + q;
+                    const int i = mi * 16 + elem_row(e), j = elem_col(e);
+                    W.gW2[i * H + j] += acc[nn][q];  // each element owned by one lane
+                }
+        }
+        // ---- layer 1 adjoints: da1 = dz2 W2, dt1_k = du2_k W2
+        float dz1v[32];
+        to_frag(dz2v, a);
+        zero(acc);
+        mma_16x64(acc, a, S.W2T);
+#pragma unroll
+        for (int nn = 0; nn < 8; ++nn)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = nn * 4 + q;
+                float sg, s0, s1, s2;
+                silu_all(W.z1[e * 32 + lane], sg, s0, s1, s2);
+                dz1v[e] = acc[nn][q] * s1;
+            }
+        float cW1[3][16];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int q = 0; q < 16; ++q) cW1[k][q] = 0.0f;
+#pragma unroll 1
+        for (int k = 0; k < 3; ++k) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = du2v[k][e];
+            to_frag(v, a);
+            zero(acc);
+            mma_16x64(acc, a, S.W2T);
+#pragma unroll
+            for (int nn = 0; nn < 8; ++nn)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = nn * 4 + q, j = elem_col(e);
+                    float sg, s0, s1, s2;
+                    silu_all(W.z1[e * 32 + lane], sg, s0, s1, s2);
+                    dz1v[e] += acc[nn][q] * s2 * S.W1[3 * j + k];
+                    cW1[k][nn * 2 + (q & 1)] += acc[nn][q] * s1;   // dt1_k s'(z1)
+                }
+        }
+        float cb1[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) cb1[q] = 0.0f;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const int r = elem_row(e), qc = (e >> 2) * 2 + (e & 1);
+            cb1[qc] += dz1v[e];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cW1[k][qc] += dz1v[e] * W.u[r][k];
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float sb = col_sum(cb1[q]);
+            const float s0 = col_sum(cW1[0][q]), s1 = col_sum(cW1[1][q]), s2 = col_sum(cW1[2][q]);
+            if (g == 0) {
+                const int j = 8 * (q >> 1) + 2 * t + (q & 1);
+                W.gb1[j] += sb;
+                W.gW1[3 * j] += s0;
+                W.gW1[3 * j + 1] += s1;
+                W.gW1[3 * j + 2] += s2;
+            }
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    // this warp's partial gradient, in theta order
+    const int wid = blockIdx.x * TWARPS + w;
+    float *P = part + (int64_t)wid * NP;
+    for (int k = lane; k < H * 3; k += 32) P[k] = W.gW1[k];
+    for (int k = lane; k < H; k += 32) P[H * 3 + k] = W.gb1[k];
+    for (int k = lane; k < H * H; k += 32) P[H * 3 + H + k] = W.gW2[k];
+    for (int k = lane; k < H; k += 32) {
+        P[H * 3 + H + H * H + k] = W.gb2[k];
+        P[H * 3 + H + H * H + H + k] = W.gw3[k];
+    }
+    if (lane == 0) {
+        P[NP - 1] = W.gb3;
+        part_loss[wid] = W.loss / (double)n;
+    }
+}
+
+// grad[p] = sum over warps of part[w][p] (fixed order); loss likewise
+__global__ void k_mlp_reduce(const float *part, const double *part_loss, int n_warps, float *grad, double *loss)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < NP) {
+        float s = 0.0f;
+        for (int w = 0; w < n_warps; ++w) s += part[(int64_t)w * NP + p];
+        grad[p] = s;
+    }
+    if (p == 0 && loss) {
+        double l = 0.0;
+        for (int w = 0; w < n_warps; ++w) l += part_loss[w];
+        *loss = l;
+    }
+}
+
+// Adam on the FP32 master parameters
+__global__ void k_mlp_adam(float *th, float *m, float *v, const float *grad, int64_t step, float lr, float b1,
+                           float b2, float eps)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    const float gr = grad[p];
+    const float mm = b1 * m[p] + (1.0f - b1) * gr;
+    const float vv = b2 * v[p] + (1.0f - b2) * gr * gr;
+    m[p] = mm;
+    v[p] = vv;
+    const float mh = mm / (1.0f - powf(b1, (float)step)), vh = vv / (1.0f - powf(b2, (float)step));
+    th[p] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// invariants of C3 = diag(F^T F, 1) and the analytic Neo-Hookean density and
+// gradient in the invariants (the same density as the Neo-Hookean term)
+__global__ void k_nh_targets(int64_t n, const float *F, double mu, double lam, float *I, float *psi, float *dpsi)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double f[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) f[k] = F[6 * s + k];
+    const double c11 = f[0] * f[0] + f[2] * f[2] + f[4] * f[4];
+    const double c22 = f[1] * f[1] + f[3] * f[3] + f[5] * f[5];
+    const double c12 = f[0] * f[1] + f[2] * f[3] + f[4] * f[5];
+    const double i3 = c11 * c22 - c12 * c12, i1 = c11 + c22 + 1.0, i2 = i3 + c11 + c22;
+    const double lnJ = 0.5 * ::log(i3);
+    I[3 * s] = (float)i1;
+    I[3 * s + 1] = (float)i2;
+    I[3 * s + 2] = (float)i3;
+    psi[s] = (float)(0.5 * mu * (i1 - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ);
+    dpsi[3 * s] = (float)(0.5 * mu);
+    dpsi[3 * s + 1] = 0.0f;
+    dpsi[3 * s + 2] = (float)((-mu + lam * lnJ) / (2.0 * i3));
+}
+
+// per-triangle network table in tile order: psi, dpsi/dI, upper Hessian in I
+__global__ void __launch_bounds__(WARPS * 32) k_mlp_tri(const float *th, const float *norm, int64_t nT,
+                                                         const int32_t *perm, const int32_t *Fv,
+                                                         const float *rest, const float *x, float *table)
+{
+    __shared__ MlpSmem S;
+    __shared__ float su[WARPS][16][3], so[WARPS][16][10];
+    extern __shared__ float scr_all[];
+    load_params(S, th, norm);
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *scr = scr_all + w * FWD_SCRATCH;
+    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 16; base < nT; base += (int64_t)gridDim.x * WARPS * 16) {
+        if (lane < 16) {
+            const int64_t p = base + lane;
+            float uu[3] = {0.0f, 0.0f, 0.0f};
+            if (p < nT) {
+                const int64_t tri = perm[p];
+                float xv[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * (int64_t)Fv[3 * tri + c] + d];
+                const float D0 = rest[p], D1 = rest[nT + p], D2 = rest[2 * nT + p], D3 = rest[3 * nT + p];
+                float c11 = 0.0f, c22 = 0.0f, c12 = 0.0f;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float u1 = xv[3 + d] - xv[d], w1 = xv[6 + d] - xv[d];
+                    const float f1 = u1 * D0 + w1 * D2, f2 = u1 * D1 + w1 * D3;
+                    c11 += f1 * f1;
+                    c22 += f2 * f2;
+                    c12 += f1 * f2;
+                }
+                const float i3 = c11 * c22 - c12 * c12;
+                const float I3[3] = {c11 + c22 + 1.0f, i3 + c11 + c22, i3};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) uu[k] = (I3[k] - S.norm[k]) / S.norm[3 + k];
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) su[w][lane][k] = uu[k];
+        }
+        __syncwarp();
+        warp_forward10(S, su[w], so[w], scr);
+        if (lane < 16 && base + lane < nT) {
+            const int64_t p = base + lane;
+            const float sp = S.norm[7], si[3] = {S.norm[3], S.norm[4], S.norm[5]};
+            float *o = table + 10 * p;
+            o[0] = sp * so[w][lane][0] + S.norm[6];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) o[1 + k] = sp * so[w][lane][1 + k] / si[k];
+            const int HK[6] = {0, 0, 1, 0, 1, 2}, HL[6] = {0, 1, 1, 2, 2, 2};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) o[4 + q] = sp * so[w][lane][4 + q] / (si[HK[q]] * si[HL[q]]);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+// launchers used by api.cpp
+adm_status mlp_eval_samples(const float *th, const float *norm, int64_t n, const float *I, float *out,
+                            cudaStream_t s)
+{
+    const size_t dyn = (size_t)WARPS * FWD_SCRATCH * sizeof(float);
+    cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    const int64_t blocks = std::min<int64_t>((n + WARPS * 16 - 1) / (WARPS * 16), 152 * 8);
+    if (blocks > 0) k_mlp_eval<<<(unsigned)blocks, WARPS * 32, dyn, s>>>(th, norm, n, I, out);
+    return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+
+size_t mlp_workspace_bytes()
+{
+    return (size_t)152 * TWARPS * (NP * sizeof(float) + sizeof(double)) + 256;
+}
+
+adm_status mlp_loss_grad(const float *th, const float *norm, int64_t n, const float *I, const float *psi,
+                         const float *g, float beta, double *loss, float *grad, void *ws, size_t ws_bytes,
+                         cudaStream_t s)
+{
+    if (n <= 0 || ws_bytes < mlp_workspace_bytes()) return ADM_ERR_ARG;
+    const int blocks = 152;
+    float *part = (float *)ws;
+    double *part_loss = (double *)((char *)ws + (((size_t)blocks * TWARPS * NP * sizeof(float) + 255) & ~(size_t)255));
+    const size_t dyn = TWARPS * sizeof(TrainWarp);
+    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_mlp_grad<<<blocks, TWARPS * 32, dyn, s>>>(th, norm, n, I, psi, g, beta, part, part_loss);
+    k_mlp_reduce<<<(NP + 255) / 256, 256, 0, s>>>(part, part_loss, blocks * TWARPS, grad, loss);
+    return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+adm_status mlp_adam(float *th, float *m, float *v, const float *grad, int64_t step, float lr, float b1, float b2,
+                    float eps, cudaStream_t s)
+{
+    k_mlp_adam<<<(NP + 255) / 256, 256, 0, s>>>(th, m, v, grad, step, lr, b1, b2, eps);
+    return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+adm_status mlp_nh_targets(int64_t n, const float *F, double mu, double lam, float *I, float *psi, float *dpsi,
+                          cudaStream_t s)
+{
+    if (n > 0) k_nh_targets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, F, mu, lam, I, psi, dpsi);
+    return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *perm, const int32_t *Fv,
+                              const float *rest_tiled, const float *x, float *table, cudaStream_t s)
+{
+    const size_t dyn = (size_t)WARPS * FWD_SCRATCH * sizeof(float);
+    cudaFuncSetAttribute(k_mlp_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    const int64_t blocks = std::min<int64_t>((nT + WARPS * 16 - 1) / (WARPS * 16), 152 * 8);
+    if (blocks > 0) k_mlp_tri<<<(unsigned)blocks, WARPS * 32, dyn, s>>>(th, norm, nT, perm, Fv, rest_tiled, x, table);
+    return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+}  // namespace adm

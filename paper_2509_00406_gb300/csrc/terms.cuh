@@ -63,6 +63,30 @@ struct PsiSymDir {
     }
 };
 
+// learned membrane: the network's density tabulated per triangle in the
+// invariants (I1, I2, I3) of C3 = diag(C, 1) -- value, gradient, upper
+// Hessian (10 numbers) -- composed with I(C): I1 = c11 + c22 + 1,
+// I3 = c11 c22 - c12^2, I2 = I3 + c11 + c22; times thickness * rest area
+template <typename T>
+struct PsiTable {
+    const float *tab;
+    T s;
+    template <class A, class B, class C>
+    ADM_HD auto operator()(const A &c11, const B &c22, const C &c12) const
+    {
+        auto i3 = c11 * c22 - sq(c12);
+        auto i1 = c11 + c22 + T(1);
+        auto i2 = i3 + c11 + c22;
+        Dense<T, 3> p;
+        p.v = (T)tab[0];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p.g[k] = (T)tab[1 + k];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) p.h[q] = (T)tab[4 + q];
+        return compose(p, i1, i2, i3) * s;
+    }
+};
+
 // area from the Gram invariants of the edges: 1/2 sqrt(|u|^2 |w|^2 - (u.w)^2)
 template <typename T>
 struct PsiArea {

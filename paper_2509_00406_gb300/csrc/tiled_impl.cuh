@@ -25,6 +25,7 @@ struct TiledArgs {
     double *epart;
     int *status;
     TermConsts<T> c;
+    const float *mlp_table;           // learned membrane: 10 per triangle, tile order
 };
 
 template <typename T, int VD, int NV, int NP, int K>
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
             for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nT + e];
             const T area = A.tri_rest[4 * A.nT + e];
             Local<T, K> L;
-            if (!tri_term<T, ENERGY>(x, D, area, A.c, L)) {
+            if (!tri_term<T, ENERGY>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * e : nullptr)) {
                 atomicOr(A.status, ST_DOMAIN);
                 continue;
             }
@@ -231,6 +232,9 @@ static void launch_tiled(int energy, int mode, int n_tiles, size_t smem, cudaStr
     case ADM_STVK_MEMBRANE: launch_tiled_modes<T, ADM_STVK_MEMBRANE, true, false>(mode, n_tiles, smem, s, A); break;
     case ADM_NH_MEMBRANE: launch_tiled_modes<T, ADM_NH_MEMBRANE, true, false>(mode, n_tiles, smem, s, A); break;
     case ADM_AREA: launch_tiled_modes<T, ADM_AREA, true, false>(mode, n_tiles, smem, s, A); break;
+    case ADM_MLP_MEMBRANE:
+        if constexpr (sizeof(T) == 4) launch_tiled_modes<T, ADM_MLP_MEMBRANE, true, false>(mode, n_tiles, smem, s, A);
+        break;
     case ADM_SHELL: launch_tiled_modes<T, ADM_SHELL, true, true>(mode, n_tiles, smem, s, A); break;
     case ADM_HINGE_BENDING:
         launch_tiled_modes<T, ADM_STVK_MEMBRANE, false, true>(mode, n_tiles, smem, s, A);
@@ -284,6 +288,17 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     A.epart = h->d_epart;
     A.status = h->d_status;
     A.c = consts<T>(h, a.energy);
+    A.mlp_table = nullptr;
+    if (a.energy == ADM_MLP_MEMBRANE) {
+        if (sizeof(T) != 4 || !h->d_mlp_theta || !ts.d_tri_perm) return ADM_ERR_UNSUPPORTED;
+        tm.begin(ADM_STAGE_MLP);
+        adm_status st = mlp_triangle_table(h->d_mlp_theta, h->d_mlp_norm, m.nT, ts.d_tri_perm, h->d_F,
+                                           (const float *)ts.d_tri_rest[ADM_FP32], (const float *)a.x,
+                                           h->d_mlp_table, s);
+        tm.end(ADM_STAGE_MLP);
+        if (st != ADM_OK) return st;
+        A.mlp_table = h->d_mlp_table;
+    }
     tm.begin(ADM_STAGE_TILED);
     launch_tiled<T>(a.energy, mode, ts.n_tiles, smem, s, A);
     tm.end(ADM_STAGE_TILED);

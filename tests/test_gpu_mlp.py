@@ -1,0 +1,182 @@
+"""Learned membrane energy on the GPU: the BF16 tensor-core network against
+the FP64 oracle (forward mode through the network, the Sobolev-loss
+gradient, the analytic Neo-Hookean targets), training on oracle-generated
+samples, what the trained network gains over the method without it, and the
+ADM_MLP_MEMBRANE mesh energy against the oracle's hyper-dual evaluation of
+the same network.
+
+The network contracts BF16-rounded activations on the tensor cores (FP32
+accumulation), so agreement with the FP64 oracle is at the BF16 level:
+relative errors of a few 1e-3, bounded here by 3e-2."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from util import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import __graft_entry__  # noqa: E402
+import paper_2509_00406_gb300 as adm  # noqa: E402
+
+E, NU = 1.0e5, 0.3
+MU = E / (2 * (1 + NU))
+LAM = E * NU / (1 - NU * NU)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def bf16(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def init_theta(rng):
+    th = np.zeros(adm.MLP_NPARAM)
+    th[:192] = rng.normal(scale=0.6, size=192)
+    th[256:4352] = rng.normal(scale=1 / 8, size=4096)
+    th[4416:4480] = rng.normal(scale=1 / 8, size=64)
+    return th
+
+
+def samples(n, seed):
+    F = synth.membrane_samples(n, seed=seed)
+    I = oracle.invariants_from_F(F)
+    psi, g = oracle.nh_targets(I)
+    return F, I, psi, g
+
+
+def norm_of(I, psi):
+    return np.concatenate([I.mean(0), I.std(0), [psi.mean(), psi.std()]])
+
+
+def cuda32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_mlp_eval_matches_oracle():
+    rng = np.random.default_rng(0)
+    _, I, psi, _ = samples(1000, 11)
+    th = init_theta(rng)
+    norm = norm_of(I, psi)
+    out = torch.zeros((I.shape[0], 10), dtype=torch.float32, device="cuda")
+    adm.MLP.eval(cuda32(th), cuda32(norm), cuda32(I), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = oracle.mlp_eval(bf16(th), norm, I.astype(np.float32).astype(np.float64))
+    assert rel(got[:, 0], ref[:, 0]) < 3e-2
+    assert rel(got[:, 1:4], ref[:, 1:4]) < 3e-2
+    assert rel(got[:, 4:], ref[:, 4:]) < 3e-2
+
+
+def test_mlp_nh_targets_match_oracle():
+    F, I, psi, g = samples(500, 12)
+    Fd = cuda32(F.reshape(-1, 6))
+    Ig = torch.zeros((500, 3), device="cuda")
+    pg = torch.zeros(500, device="cuda")
+    gg = torch.zeros((500, 3), device="cuda")
+    adm.MLP.nh_targets(Fd, E, NU, Ig, pg, gg)
+    torch.cuda.synchronize()
+    I32 = oracle.invariants_from_F(F.astype(np.float32).astype(np.float64))
+    p32, g32 = oracle.nh_targets(I32)
+    assert rel(Ig.cpu().numpy(), I32) < 1e-6
+    assert rel(pg.cpu().numpy(), p32) < 1e-5
+    assert rel(gg.cpu().numpy(), g32) < 1e-5
+
+
+def test_mlp_loss_gradient_matches_oracle():
+    rng = np.random.default_rng(3)
+    _, I, psi, g = samples(2000, 13)
+    th = init_theta(rng)
+    norm = norm_of(I, psi)
+    ws = torch.zeros(adm.MLP.workspace_size() // 4 + 1, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(adm.MLP_NPARAM, dtype=torch.float32, device="cuda")
+    adm.MLP.loss_grad(cuda32(th), cuda32(norm), cuda32(I), cuda32(psi), cuda32(g), 0.5, loss, grad, ws)
+    torch.cuda.synchronize()
+    Lref, gref = oracle.mlp_loss(bf16(th), norm, I.astype(np.float32).astype(np.float64),
+                                 psi.astype(np.float32).astype(np.float64),
+                                 g.astype(np.float32).astype(np.float64), beta=0.5)
+    assert abs(loss.item() - Lref) <= 3e-2 * Lref
+    gg = grad.cpu().numpy()
+    for lo, hi in ((0, 192), (192, 256), (256, 4352), (4352, 4416), (4416, 4480), (4480, 4481)):
+        assert rel(gg[lo:hi], gref[lo:hi]) < 3e-2, (lo, hi, rel(gg[lo:hi], gref[lo:hi]))
+
+
+def train(I, psi, g, norm, steps=600, batch=8192, lr=3e-3, seed=0):
+    rng = np.random.default_rng(seed)
+    th = cuda32(init_theta(rng))
+    m = torch.zeros_like(th)
+    v = torch.zeros_like(th)
+    nd = cuda32(norm)
+    Id, pd, gd = cuda32(I), cuda32(psi), cuda32(g)
+    ws = torch.zeros(adm.MLP.workspace_size() // 4 + 1, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.zeros_like(th)
+    hist = []
+    perm = torch.from_numpy(rng.permutation(I.shape[0])).cuda()
+    for step in range(1, steps + 1):
+        k = (step - 1) * batch % I.shape[0]
+        idx = perm[k:k + batch]
+        adm.MLP.loss_grad(th, nd, Id[idx].contiguous(), pd[idx].contiguous(), gd[idx].contiguous(), 1.0, loss,
+                          grad, ws)
+        adm.MLP.adam(th, m, v, grad, step, lr * (0.1 ** (step / steps)))
+        if step % 50 == 1:
+            hist.append(loss.item())
+    return th, hist
+
+
+def test_mlp_training_gains_over_stvk():
+    """Trained on oracle Neo-Hookean samples, the network's density, gradient
+    and Hessian in the invariants are far closer to Neo-Hookean than the
+    membrane without it (StVK with the same Lame parameters) on held-out
+    stretches in [0.7, 1.4]."""
+    _, I, psi, g = samples(65536, 5)
+    norm = norm_of(I, psi)
+    th, hist = train(I, psi, g, norm)
+    assert hist[-1] < 0.05 * hist[0]
+    _, It, pt, gt = samples(4000, 77)
+    out = torch.zeros((It.shape[0], 10), dtype=torch.float32, device="cuda")
+    adm.MLP.eval(th, cuda32(norm), cuda32(It), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    # StVK in the invariants: tr C = I1 - 1, det C = I3
+    trC, detC = It[:, 0] - 1, It[:, 2]
+    nE2 = 0.25 * (trC ** 2 - 2 * detC - 2 * trC + 2)
+    psi_stvk = MU * nE2 + 0.5 * LAM * (0.5 * (trC - 2)) ** 2
+    err_mlp = rel(got[:, 0], pt)
+    err_stvk = rel(psi_stvk, pt)
+    assert err_mlp < 0.05 and err_stvk / err_mlp > 5.0, (err_mlp, err_stvk)
+    # gradient in the invariants against Neo-Hookean
+    assert rel(got[:, 1:4], gt) < 0.1
+
+
+def test_mlp_membrane_mesh_matches_oracle():
+    rng = np.random.default_rng(4)
+    v, f = synth.icosphere(1)
+    x = synth.perturb(v, 2e-2, 8)
+    _, I, psi, _ = samples(2000, 14)
+    th = init_theta(rng)
+    norm = norm_of(I, psi)
+    m = adm.Mesh(v, f, 3)
+    m.set_params(adm.MLP_MEMBRANE, [E, NU, 1e-3])
+    m.mlp_attach(cuda32(th), cuda32(norm))
+    _, nV, nnzb, rp, col = m.pattern(adm.MLP_MEMBRANE)
+    xd = cuda32(x)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gd = torch.zeros(nV * 3, dtype=torch.float32, device="cuda")
+    Hd = torch.zeros(nnzb * 9, dtype=torch.float32, device="cuda")
+    m.eval(adm.MLP_MEMBRANE, adm.FP32, xd, e, gd, Hd)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    oracle.mlp_set(bf16(th), norm)
+    P = oracle.Problem(v, f, oracle.MLP, 3, params=[E, NU, 1e-3])
+    ref = P.assemble(x.astype(np.float32).astype(np.float64))
+    assert abs(e.item() - ref["energy"]) <= 3e-2 * abs(ref["energy"])
+    assert rel(gd.cpu().numpy().reshape(-1, 3), ref["grad"]) < 3e-2
+    assert rel(Hd.cpu().numpy().reshape(-1, 3, 3), ref["vals"]) < 3e-2
