@@ -135,8 +135,8 @@ adm_status ensure_shell(adm_ctx *h)
 // device arrays of a tile set (freed before a rebuild)
 void free_tiles(adm_ctx *h, TileSet &ts)
 {
-    void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_row_start, ts.d_code_off, ts.d_tri_loc, ts.d_hinge_loc, ts.d_tri_perm,
-                    ts.d_codes, ts.d_zero_blocks, ts.d_zero_verts, ts.d_mesh_tile_off, ts.d_tri_rest[0],
+    void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_meta, ts.d_meta_off, ts.d_tri_loc, ts.d_hinge_loc, ts.d_tri_perm,
+                    ts.d_zero_blocks, ts.d_zero_verts, ts.d_mesh_tile_off, ts.d_tri_rest[0],
                     ts.d_tri_rest[1], ts.d_hinge_rest[0], ts.d_hinge_rest[1]};
     for (void *p : ptrs) dev_free(h, p);
     ts = TileSet();
@@ -164,9 +164,8 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
     if ((s = up(&ts.d_tri_loc, ts.tri_loc)) != ADM_OK) return s;
     if ((s = up(&ts.d_hinge_loc, ts.hinge_loc)) != ADM_OK) return s;
     if ((s = up(&ts.d_foot, ts.foot)) != ADM_OK) return s;
-    if ((s = up(&ts.d_row_start, ts.row_start)) != ADM_OK) return s;
-    if ((s = up(&ts.d_code_off, ts.code_off)) != ADM_OK) return s;
-    if ((s = up(&ts.d_codes, ts.codes)) != ADM_OK) return s;
+    if ((s = up(&ts.d_meta, ts.meta)) != ADM_OK) return s;
+    if ((s = up(&ts.d_meta_off, ts.meta_off)) != ADM_OK) return s;
     if ((s = up(&ts.d_zero_blocks, ts.zero_blocks)) != ADM_OK) return s;
     if ((s = up(&ts.d_zero_verts, ts.zero_verts)) != ADM_OK) return s;
     if ((s = up(&ts.d_mesh_tile_off, ts.mesh_tile_off)) != ADM_OK) return s;

@@ -42,6 +42,41 @@ __device__ __forceinline__ double block_sum(double v)
     return s;  // valid in thread 0
 }
 
+// ------------------------------------------------- bulk (TMA) copies --
+// One thread: initialise the mbarrier for one arrival, arm it with the byte
+// count and start a bulk copy global -> shared that completes it.  dst, src
+// and bytes must be multiples of 16 (bytes below 2^20).
+__device__ __forceinline__ void bulk_load_start(uint64_t *bar, void *dst, const void *src, uint32_t bytes)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// Wait for phase 0 of the mbarrier; gives up after about a second (2^20
+// waits of at most ~1 us each) and returns false.
+__device__ __forceinline__ bool bulk_load_wait(uint64_t *bar)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(b), "r"(1000u)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // ----------------------------------------------------- term evaluation --
 template <int ENERGY>
 struct TriTraits {

@@ -36,7 +36,7 @@ extern "C" {
 //   block_writer[b] = tile id if exactly one tile writes it with a plain
 //   store, -2 if it is shared (zeroed and atomically added), -1 if no tile
 //   writes it; block_adds[b] = number of tiles that add into it.
-// stats: {n_tiles, n_zero_blocks, n_zero_verts, max_smem_units, nnzb, nH,
+// stats: {n_tiles, n_zero_blocks, n_zero_verts, FP64 shared-memory bytes (VD = 3), nnzb, nH,
 //         build_ms}.  Returns 0 or an adm_status.
 int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t nT, const int64_t *v_off,
                         const int64_t *f_off, int32_t n_mesh, int32_t with_hinges, int32_t tile_tris,
@@ -84,13 +84,35 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
     stats[0] = ts.n_tiles;
     stats[1] = (double)ts.zero_blocks.size();
     stats[2] = (double)ts.zero_verts.size();
-    stats[3] = (double)ts.max_smem_units;
+    stats[3] = (double)ts.smem_bytes[1][0];
     stats[4] = (double)P.nnzb;
     stats[5] = (double)m.nH();
     stats[6] = std::chrono::duration<double, std::milli>(t1 - t0).count();
     // every zeroed block is shared
     for (int32_t b : ts.zero_blocks)
         if (block_writer[b] != -2) return -102;
+    // each tile's metadata blob holds its rows' starts, code offsets and codes
+    if ((int64_t)ts.meta_off.size() != ts.n_tiles + 1 || ts.meta_off.back() != (int64_t)ts.meta.size()) return -105;
+    for (int32_t t = 0; t < ts.n_tiles; ++t) {
+        const int32_t *hd = &ts.hdr[8 * (size_t)t];
+        const int32_t foot_begin = hd[4], nf = hd[5];
+        const int64_t m0 = ts.meta_off[t];
+        if (m0 % 16 != 0 || (ts.meta_off[t + 1] - m0) % 16 != 0) return -105;
+        const unsigned char *blob = ts.meta.data() + m0;
+        const int32_t cbase = ts.code_off[foot_begin + t];
+        for (int32_t r = 0; r <= nf; ++r) {
+            uint16_t c;
+            std::memcpy(&c, blob + 4 * nf + 2 * r, 2);
+            if (c != ts.code_off[foot_begin + t + r] - cbase) return -106;
+            if (r == nf) break;
+            int32_t rs;
+            std::memcpy(&rs, blob + 4 * r, 4);
+            if (rs != ts.row_start[foot_begin + r]) return -106;
+        }
+        const int32_t nc = ts.code_off[foot_begin + t + nf] - cbase;
+        if (6 * nf + 2 + 2 * nc > ts.meta_off[t + 1] - m0) return -106;
+        if (std::memcmp(blob + 6 * nf + 2, &ts.codes[cbase], 2 * (size_t)nc) != 0) return -106;
+    }
     // every triangle and hinge belongs to exactly one tile
     std::vector<char> seen_t(nT, 0), seen_h(m.nH(), 0);
     for (int32_t e : ts.tri_perm)

