@@ -61,6 +61,20 @@ def workload(rank: int, n_mesh: int = 700):
     return levels, mesh
 
 
+def combine_ranks(dist, seconds: float, units: int, device: str = "cuda") -> tuple[float, int]:
+    """Whole-job view of a timed region: the slowest rank's time and the units
+    all ranks processed (one process per GPU; dist is None on one GPU)."""
+    if dist is None:
+        return seconds, units
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.int64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def counts(mesh):
     """Element and pattern counts of a batch of closed meshes (every edge is a
     hinge): E = 3T/2 per mesh, nnzb = V + 4E."""
@@ -427,12 +441,9 @@ def run_ours(args, rank: int, world: int, local: int):
     ms_total = ev0.elapsed_time(ev1)
     prof = m.profile_read()
     m.set_option(adm.OPT_PROFILE, 0)
-    if dist:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, n_el_all = combine_ranks(dist, ms_total, n_el)
     ms_step = ms_total / args.steps
-    value = world * n_el / (ms_step * 1e-3)
+    value = n_el_all / (ms_step * 1e-3)
 
     # dominant kernel and its roofline
     kern = {k: v for k, v in prof.items() if k != "zero" and v[1] > 0}
@@ -471,11 +482,8 @@ def run_ours(args, rank: int, world: int, local: int):
     for _ in range(k_e2e):
         m.eval_batch_host(adm.SHELL, adm.FP32, xh.numpy(), eh.numpy(), gnh.numpy())
     e2e_s = (time.perf_counter() - t0) / k_e2e
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * n_el / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
+    e2e_s, _ = combine_ranks(dist, e2e_s, n_el)
+    e2e = {"value": n_el_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
            "d2h_bytes_per_step": int(2 * mesh.n_mesh * 8),
            "note": "adm_eval_batch_host: x in, per-mesh energy + gradient norm out; gradient and "
                    "Hessian stay in device staging buffers"}

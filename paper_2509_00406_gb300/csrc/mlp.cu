@@ -131,80 +131,126 @@ __device__ __forceinline__ float quad_sum(float v)
     return v;
 }
 
-// Forward mode through the network for the 16 samples of a warp.
-// u[16][3]: standardised inputs (shared memory).  out[16][10] (shared):
-// y, dy/du_k (3), upper Hessian in u (uu00, uu01, uu11, uu02, uu12, uu22).
-// scratch: per-warp shared floats, 5 * 32 * 32.
-__device__ void warp_forward10(const MlpSmem &S, const float (*u)[3], float (*out)[10], float *scr)
+// Forward mode through the network for 8 samples per warp, all in registers.
+// The hidden layer runs transposed, z2^T = W2 a1^T: W2 (64 x 64, row = output
+// unit) is the A operand, read from shared memory, and the 10 channels of the
+// activations a1^T (64 units x 8 samples) are B operands built by the lanes
+// themselves.  Lane (g, t) takes sample g: it evaluates layer 1 for units
+// 16 kt + 2 t + {0, 1, 8, 9}, exactly the rows of its B fragments, and after
+// the contraction holds every channel of z2 for units 16 mt + g + {0, 8} and
+// samples 2 t + {0, 1}, so the second-order chain rule through the second
+// SiLU stays in the lane.  Output sums over units close with shuffles.
+// u: standardised input of sample g = lane / 4.  y[n][c]: channel c of sample
+// 2 t + n (value, dy/du_k, upper Hessian uu00, uu01, uu11, uu02, uu12, uu22),
+// identical in the 8 lanes of a column t.
+__device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)[3], float (&y)[2][10])
 {
-    const int lane = threadIdx.x & 31;
-    // lane-strided slabs [e * 32 + lane]: z1 (1024), s'(z2) and s''(z2)
-    // (2 x 1024), d z2 / d u_k (3 x 1024)
-    float *sZ1 = scr, *sS2 = scr + 1024, *sD = scr + 3072;
-    float v[32];
-    // layer 1: z1 for the lane's (sample, unit) elements
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    constexpr int K2[6] = {0, 0, 1, 0, 1, 2}, L2[6] = {0, 1, 1, 2, 2, 2};
+    // layer 1 -> B fragments: b[kt][c][0] = units 16kt + 2t, +1; [1] = +8, +9
+    uint32_t b[4][10][2];
 #pragma unroll
-    for (int e = 0; e < 32; ++e) {
-        const int r = elem_row(e), j = elem_col(e);
-        const float z = S.b1[j] + S.W1[3 * j] * u[r][0] + S.W1[3 * j + 1] * u[r][1] + S.W1[3 * j + 2] * u[r][2];
-        sZ1[e * 32 + lane] = z;
-    }
-    float acc[8][4];
-    uint32_t a[4][4];
-    // channel order: value, tangents 0..2, second order (00, 01, 11, 02, 12, 22)
-#pragma unroll 1
-    for (int c = 0; c < 10; ++c) {
-        const int k = c == 0 ? -1 : (c < 4 ? c - 1 : (c == 4 || c == 5 || c == 7 ? 0 : (c == 6 || c == 8 ? 1 : 2)));
-        const int l = c < 4 ? -1 : (c == 4 ? 0 : (c == 5 || c == 6 ? 1 : 2));
+    for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            const float z = sZ1[e * 32 + lane];
-            float sg, s, s1, s2;
-            silu_all(z, sg, s, s1, s2);
-            const int j = elem_col(e);
-            v[e] = c == 0 ? s : (l < 0 ? s1 * S.W1[3 * j + k] : s2 * S.W1[3 * j + k] * S.W1[3 * j + l]);
-        }
-        to_frag(v, a);
-        zero(acc);
-        mma_16x64(acc, a, S.W2);
-        // layer 2 and output, per element of the accumulator
-        float p0 = 0.0f, p1 = 0.0f;  // rows g and g+8
+        for (int h = 0; h < 2; ++h) {
+            float v[2][10];
 #pragma unroll
-        for (int nn = 0; nn < 8; ++nn)
+            for (int o = 0; o < 2; ++o) {
+                const int i = 16 * kt + 2 * t + 8 * h + o;
+                const float w0 = S.W1[3 * i], w1 = S.W1[3 * i + 1], w2 = S.W1[3 * i + 2];
+                const float z = S.b1[i] + w0 * u[0] + w1 * u[1] + w2 * u[2];
+                float sg, s0, s1, s2;
+                silu_all(z, sg, s0, s1, s2);
+                const float wk[3] = {w0, w1, w2};
+                v[o][0] = s0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = nn * 4 + q, i = elem_col(e);
-                float w;
-                if (c == 0) {
-                    const float z2 = acc[nn][q] + S.b2[i];
-                    float sg, s, s1, s2;
-                    silu_all(z2, sg, s, s1, s2);
-                    sS2[e * 32 + lane] = s1;                // s'(z2)
-                    sS2[(32 + e) * 32 + lane] = s2;         // s''(z2)
-                    w = S.w3[i] * s;
-                } else if (l < 0) {
-                    sD[(k * 32 + e) * 32 + lane] = acc[nn][q];  // d z2 / d u_k
-                    w = S.w3[i] * sS2[e * 32 + lane] * acc[nn][q];
-                } else {
-                    const float dk = sD[(k * 32 + e) * 32 + lane], dl = sD[(l * 32 + e) * 32 + lane];
-                    w = S.w3[i] * (sS2[(32 + e) * 32 + lane] * dk * dl + sS2[e * 32 + lane] * acc[nn][q]);
-                }
-                if (q < 2) p0 += w;
-                else p1 += w;
+                for (int k = 0; k < 3; ++k) v[o][1 + k] = s1 * wk[k];
+#pragma unroll
+                for (int m = 0; m < 6; ++m) v[o][4 + m] = s2 * wk[K2[m]] * wk[L2[m]];
             }
-        p0 = quad_sum(p0);
-        p1 = quad_sum(p1);
-        if ((lane & 3) == 0) {
-            out[lane >> 2][c] = p0 + (c == 0 ? S.b3 : 0.0f);
-            out[(lane >> 2) + 8][c] = p1 + (c == 0 ? S.b3 : 0.0f);
+#pragma unroll
+            for (int c = 0; c < 10; ++c) b[kt][c][h] = pack_bf16(v[0][c], v[1][c]);
+        }
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int c = 0; c < 10; ++c) y[n][c] = 0.0f;
+#pragma unroll 1
+    for (int mt = 0; mt < 4; ++mt) {
+        float acc[10][4];
+#pragma unroll
+        for (int c = 0; c < 10; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[c][q] = 0.0f;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const __nv_bfloat16 *w = S.W2 + (16 * mt + g) * LDW + 16 * kt + 2 * t;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(w);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(w + 8 * LDW);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(w + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(w + 8 * LDW + 8);
+#pragma unroll
+            for (int c = 0; c < 10; ++c)
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                    "{%0,%1,%2,%3};\n"
+                    : "+f"(acc[c][0]), "+f"(acc[c][1]), "+f"(acc[c][2]), "+f"(acc[c][3])
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b[kt][c][0]), "r"(b[kt][c][1]));
+        }
+        // layer 2 and the output layer for units j = 16 mt + g + 8 (q >> 1),
+        // samples 2 t + (q & 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 16 * mt + g + 8 * (q >> 1), n = q & 1;
+            float sg, s0, s1, s2;
+            silu_all(acc[0][q] + S.b2[j], sg, s0, s1, s2);
+            const float w = S.w3[j];
+            const float d[3] = {acc[1][q], acc[2][q], acc[3][q]};
+            y[n][0] += w * s0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) y[n][1 + k] += w * s1 * d[k];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) y[n][4 + m] += w * (s2 * d[K2[m]] * d[L2[m]] + s1 * acc[4 + m][q]);
         }
     }
-    __syncwarp();
+    // sum over the 8 lanes g of each column t
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int c = 0; c < 10; ++c) {
+            float v = y[n][c];
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 16);
+            y[n][c] = v + (c == 0 ? S.b3 : 0.0f);
+        }
 }
 
-// scratch floats per warp of warp_forward10: z1 (1024), s'(z2) and s''(z2)
-// (2048), d z2 / d u_k (3 * 1024)
-constexpr int FWD_SCRATCH = 1024 + 2048 + 3 * 1024;
+// network outputs of sample p (channel order of warp_forward8) in the units
+// of the invariants: psi, dpsi/dI (3), upper Hessian in I (6).  Lane (g, t)
+// writes channels g and g + 8 of samples 2 t + n.
+__device__ __forceinline__ void store_unstandardised(const MlpSmem &S, const float (&y)[2][10], int64_t base,
+                                                     int64_t n_valid, float *out)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float sp = S.norm[7];
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+        const int64_t p = base + 2 * t + n;
+        if (p >= n_valid) continue;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) {
+            if ((c & 7) != g) continue;
+            float v;
+            if (c == 0) v = sp * y[n][0] + S.norm[6];
+            else if (c < 4) v = sp * y[n][c] / S.norm[3 + c - 1];
+            else  // second-order channel m = c - 4 is (k, l) = nibble m of 0x210100, 0x222110
+                v = sp * y[n][c] / (S.norm[3 + ((0x210100 >> (4 * (c - 4))) & 0xf)] *
+                                    S.norm[3 + ((0x222110 >> (4 * (c - 4))) & 0xf)]);
+            out[10 * p + c] = v;
+        }
+    }
+}
 
 // ---------------------------------------------------------------- kernels --
 // samples: invariants I (n x 3) -> psi, dpsi/dI (3), upper Hessian in I (6)
@@ -212,33 +258,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_mlp_eval(const float *th, const 
                                                           const float *I, float *out)
 {
     __shared__ MlpSmem S;
-    __shared__ float su[WARPS][16][3], so[WARPS][16][10];
-    extern __shared__ float scr_all[];
     load_params(S, th, norm);
     __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *scr = scr_all + w * FWD_SCRATCH;
-    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 16; base < n; base += (int64_t)gridDim.x * WARPS * 16) {
-        if (lane < 16) {
-            const int64_t s = base + lane;
+    const int w = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
+    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 8; base < n; base += (int64_t)gridDim.x * WARPS * 8) {
+        const int64_t s = base + g;
+        float u[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                su[w][lane][k] = s < n ? (I[3 * s + k] - S.norm[k]) / S.norm[3 + k] : 0.0f;
-        }
-        __syncwarp();
-        warp_forward10(S, su[w], so[w], scr);
-        if (lane < 16 && base + lane < n) {
-            const int64_t s = base + lane;
-            const float sp = S.norm[7], si[3] = {S.norm[3], S.norm[4], S.norm[5]};
-            float *o = out + 10 * s;
-            o[0] = sp * so[w][lane][0] + S.norm[6];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) o[1 + k] = sp * so[w][lane][1 + k] / si[k];
-            const int HK[6] = {0, 0, 1, 0, 1, 2}, HL[6] = {0, 1, 1, 2, 2, 2};
-#pragma unroll
-            for (int q = 0; q < 6; ++q) o[4 + q] = sp * so[w][lane][4 + q] / (si[HK[q]] * si[HL[q]]);
-        }
-        __syncwarp();
+        for (int k = 0; k < 3; ++k) u[k] = s < n ? (I[3 * s + k] - S.norm[k]) / S.norm[3 + k] : 0.0f;
+        float y[2][10];
+        warp_forward8(S, u, y);
+        store_unstandardised(S, y, base, n, out);
     }
 }
 
@@ -585,55 +615,41 @@ __global__ void __launch_bounds__(WARPS * 32) k_mlp_tri(const float *th, const f
                                                          const float *rest, const float *x, float *table)
 {
     __shared__ MlpSmem S;
-    __shared__ float su[WARPS][16][3], so[WARPS][16][10];
-    extern __shared__ float scr_all[];
     load_params(S, th, norm);
     __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *scr = scr_all + w * FWD_SCRATCH;
-    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 16; base < nT; base += (int64_t)gridDim.x * WARPS * 16) {
-        if (lane < 16) {
-            const int64_t p = base + lane;
-            float uu[3] = {0.0f, 0.0f, 0.0f};
-            if (p < nT) {
-                const int64_t tri = perm[p];
-                float xv[9];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
+    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 8; base < nT; base += (int64_t)gridDim.x * WARPS * 8) {
+        // lanes 0..7 form the invariants of triangles base + lane
+        float uu[3] = {0.0f, 0.0f, 0.0f};
+        const int64_t p = base + (lane & 7);
+        if (lane < 8 && p < nT) {
+            const int64_t tri = perm[p];
+            float xv[9];
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * (int64_t)Fv[3 * tri + c] + d];
-                const float D0 = rest[p], D1 = rest[nT + p], D2 = rest[2 * nT + p], D3 = rest[3 * nT + p];
-                float c11 = 0.0f, c22 = 0.0f, c12 = 0.0f;
+                for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * (int64_t)Fv[3 * tri + c] + d];
+            const float D0 = rest[p], D1 = rest[nT + p], D2 = rest[2 * nT + p], D3 = rest[3 * nT + p];
+            float c11 = 0.0f, c22 = 0.0f, c12 = 0.0f;
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float u1 = xv[3 + d] - xv[d], w1 = xv[6 + d] - xv[d];
-                    const float f1 = u1 * D0 + w1 * D2, f2 = u1 * D1 + w1 * D3;
-                    c11 += f1 * f1;
-                    c22 += f2 * f2;
-                    c12 += f1 * f2;
-                }
-                const float i3 = c11 * c22 - c12 * c12;
-                const float I3[3] = {c11 + c22 + 1.0f, i3 + c11 + c22, i3};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) uu[k] = (I3[k] - S.norm[k]) / S.norm[3 + k];
+            for (int d = 0; d < 3; ++d) {
+                const float u1 = xv[3 + d] - xv[d], w1 = xv[6 + d] - xv[d];
+                const float f1 = u1 * D0 + w1 * D2, f2 = u1 * D1 + w1 * D3;
+                c11 += f1 * f1;
+                c22 += f2 * f2;
+                c12 += f1 * f2;
             }
+            const float i3 = c11 * c22 - c12 * c12;
+            const float I3[3] = {c11 + c22 + 1.0f, i3 + c11 + c22, i3};
 #pragma unroll
-            for (int k = 0; k < 3; ++k) su[w][lane][k] = uu[k];
+            for (int k = 0; k < 3; ++k) uu[k] = (I3[k] - S.norm[k]) / S.norm[3 + k];
         }
-        __syncwarp();
-        warp_forward10(S, su[w], so[w], scr);
-        if (lane < 16 && base + lane < nT) {
-            const int64_t p = base + lane;
-            const float sp = S.norm[7], si[3] = {S.norm[3], S.norm[4], S.norm[5]};
-            float *o = table + 10 * p;
-            o[0] = sp * so[w][lane][0] + S.norm[6];
+        float u[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) o[1 + k] = sp * so[w][lane][1 + k] / si[k];
-            const int HK[6] = {0, 0, 1, 0, 1, 2}, HL[6] = {0, 1, 1, 2, 2, 2};
-#pragma unroll
-            for (int q = 0; q < 6; ++q) o[4 + q] = sp * so[w][lane][4 + q] / (si[HK[q]] * si[HL[q]]);
-        }
-        __syncwarp();
+        for (int k = 0; k < 3; ++k) u[k] = __shfl_sync(0xffffffffu, uu[k], g);
+        float y[2][10];
+        warp_forward8(S, u, y);
+        store_unstandardised(S, y, base, nT, table);
     }
 }
 
@@ -643,10 +659,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_mlp_tri(const float *th, const f
 adm_status mlp_eval_samples(const float *th, const float *norm, int64_t n, const float *I, float *out,
                             cudaStream_t s)
 {
-    const size_t dyn = (size_t)WARPS * FWD_SCRATCH * sizeof(float);
-    cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    const int64_t blocks = std::min<int64_t>((n + WARPS * 16 - 1) / (WARPS * 16), 152 * 8);
-    if (blocks > 0) k_mlp_eval<<<(unsigned)blocks, WARPS * 32, dyn, s>>>(th, norm, n, I, out);
+    const int64_t blocks = std::min<int64_t>((n + WARPS * 8 - 1) / (WARPS * 8), 152 * 8);
+    if (blocks > 0) k_mlp_eval<<<(unsigned)blocks, WARPS * 32, 0, s>>>(th, norm, n, I, out);
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
@@ -688,10 +702,8 @@ adm_status mlp_nh_targets(int64_t n, const float *F, double mu, double lam, floa
 adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *perm, const int32_t *Fv,
                               const float *rest_tiled, const float *x, float *table, cudaStream_t s)
 {
-    const size_t dyn = (size_t)WARPS * FWD_SCRATCH * sizeof(float);
-    cudaFuncSetAttribute(k_mlp_tri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    const int64_t blocks = std::min<int64_t>((nT + WARPS * 16 - 1) / (WARPS * 16), 152 * 8);
-    if (blocks > 0) k_mlp_tri<<<(unsigned)blocks, WARPS * 32, dyn, s>>>(th, norm, nT, perm, Fv, rest_tiled, x, table);
+    const int64_t blocks = std::min<int64_t>((nT + WARPS * 8 - 1) / (WARPS * 8), 152 * 8);
+    if (blocks > 0) k_mlp_tri<<<(unsigned)blocks, WARPS * 32, 0, s>>>(th, norm, nT, perm, Fv, rest_tiled, x, table);
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 

@@ -61,7 +61,7 @@ def cuda32(a):
 
 def test_mlp_eval_matches_oracle():
     rng = np.random.default_rng(0)
-    _, I, psi, _ = samples(1000, 11)
+    _, I, psi, _ = samples(1003, 11)  # ragged: not a multiple of the 8 samples of a warp
     th = init_theta(rng)
     norm = norm_of(I, psi)
     out = torch.zeros((I.shape[0], 10), dtype=torch.float32, device="cuda")
