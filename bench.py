@@ -457,6 +457,7 @@ def run_ours(args, rank: int, world: int, local: int):
     achieved = ab / (dom_ms * 1e-3) / 1e9
     pass_bytes = algorithmic_bytes(c, "pass")
     traffic = None
+    pipes = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         from paper_2509_00406_gb300 import _build
@@ -467,6 +468,9 @@ def run_ours(args, rank: int, world: int, local: int):
             # bytes of a full launch: the capture's bytes scaled by the
             # algorithmic bytes of this workload over the captured workload's
             traffic = int(ent["dram_bytes_per_launch"] * ab / ent["algorithmic_bytes"])
+            pipes = {"fma_pipe_active_pct": ent.get("fma_pipe_active_pct"),
+                     "issue_active_pct": ent.get("issue_active_pct"),
+                     "source": "ncu capture of the same kernel source: " + ent["workload"]}
     except Exception:
         traffic = None
 
@@ -499,7 +503,7 @@ def run_ours(args, rank: int, world: int, local: int):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": ab,
-                     "avg_ms": dom_ms, "peak_source": peak_src},
+                     "avg_ms": dom_ms, "peak_source": peak_src, "pipes": pipes},
         "pass": {"algorithmic_bytes": pass_bytes, "achieved_gbs": pass_bytes / (ms_step * 1e-3) / 1e9,
                  "frac_of_hbm": pass_bytes / (ms_step * 1e-3) / 1e9 / peak,
                  "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}},
