@@ -115,26 +115,80 @@ ADM_HD void store_local(const R &r, Local<T, K> &out)
     for (int k = 0; k < K * (K + 1) / 2; ++k) out.H[k] = hbit(R::hl, R::hh, k) ? r.h[k] : T(0);
 }
 
+// ------------------------------------------------ edge-vector expansion --
+// Terms are differentiated in the coordinates of NE edge vectors of their
+// element (edge p = sum_a C[a][p] x_a over the NV vertices, C in {-1, 0, 1})
+// and carried to the vertex DOFs by the chain rule through that constant map:
+//   g_(a,d) = sum_p C[a][p] ge_(p,d),
+//   H_(a,r),(b,s) = sum_(p,q) C[a][p] C[b][q] He_(p,r),(q,s).
+// A triangle has 2 edge vectors (6 DOF instead of 9 for VD = 3), a hinge 3
+// (9 instead of 12), so the invariants and the composition carry 21 / 45
+// Hessian entries instead of 45 / 78.
+// C[a][p] is packed two bits per entry at bit 2 (a NE + p): 0 -> 0, 1 -> +1, 2 -> -1
+ADM_HD constexpr int edge_coef(uint64_t packed, int k) { return (int)((packed >> (2 * k)) & 1u) - (int)((packed >> (2 * k + 1)) & 1u); }
+struct TriEdges {  // u = x1 - x0, w = x2 - x0: C = {{-1, -1}, {1, 0}, {0, 1}}
+    static constexpr int NV = 3, NE = 2;
+    ADM_HD static constexpr int C(int a, int p) { return edge_coef(0x41Au, a * NE + p); }
+};
+struct HingeEdges {  // e = x1 - x0, u = xa - x0, v = xb - x1: C = {{-1, -1, 0}, {1, 0, -1}, {0, 1, 0}, {0, 0, 1}}
+    static constexpr int NV = 4, NE = 3;
+    ADM_HD static constexpr int C(int a, int p) { return edge_coef(0x40484Au, a * NE + p); }
+};
+static_assert(TriEdges::C(0, 0) == -1 && TriEdges::C(0, 1) == -1 && TriEdges::C(1, 0) == 1 && TriEdges::C(1, 1) == 0 &&
+              TriEdges::C(2, 0) == 0 && TriEdges::C(2, 1) == 1, "triangle edge map");
+static_assert(HingeEdges::C(0, 0) == -1 && HingeEdges::C(0, 1) == -1 && HingeEdges::C(0, 2) == 0 &&
+              HingeEdges::C(1, 0) == 1 && HingeEdges::C(1, 1) == 0 && HingeEdges::C(1, 2) == -1 &&
+              HingeEdges::C(2, 0) == 0 && HingeEdges::C(2, 1) == 1 && HingeEdges::C(2, 2) == 0 &&
+              HingeEdges::C(3, 0) == 0 && HingeEdges::C(3, 1) == 0 && HingeEdges::C(3, 2) == 1, "hinge edge map");
+
+template <class E, int VD, typename T>
+ADM_HD void expand_edges(const Local<T, E::NE * VD> &le, Local<T, E::NV * VD> &out)
+{
+    constexpr int NE = E::NE, K = E::NV * VD;
+    out.f = le.f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const int a = i / VD, d = i % VD;
+        T acc = -T(0);
+#pragma unroll
+        for (int p = 0; p < NE; ++p) {
+            if (E::C(a, p) == 0) continue;
+            acc = E::C(a, p) > 0 ? acc + le.g[p * VD + d] : acc - le.g[p * VD + d];
+        }
+        out.g[i] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int i = 0; i <= j; ++i) {
+            const int a = i / VD, r = i % VD, b = j / VD, s = j % VD;
+            T acc = -T(0);
+#pragma unroll
+            for (int p = 0; p < NE; ++p)
+#pragma unroll
+                for (int q = 0; q < NE; ++q) {
+                    const int c = E::C(a, p) * E::C(b, q);
+                    if (c == 0) continue;
+                    const int ii = p * VD + r, jj = q * VD + s;
+                    const T h = le.H[ii <= jj ? hix(ii, jj) : hix(jj, ii)];
+                    acc = c > 0 ? acc + h : acc - h;
+                }
+            out.H[hix(i, j)] = acc;
+        }
+}
+
 // ------------------------------------------------------ triangle, VD = 3 --
-// C = F^T F of F = [x1-x0, x2-x0] Dinv;  Dinv row-major (d00, d01, d10, d11)
+// C = F^T F of F = [x1-x0, x2-x0] Dinv;  Dinv row-major (d00, d01, d10, d11).
+// Differentiated in the edge vectors u = x1 - x0, w = x2 - x0.
 template <typename T, class Psi>
 ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Local<T, 9> &out)
 {
-    auto X0 = seed<T, 9, 0>(x[0]);
-    auto X1 = seed<T, 9, 1>(x[1]);
-    auto X2 = seed<T, 9, 2>(x[2]);
-    auto X3 = seed<T, 9, 3>(x[3]);
-    auto X4 = seed<T, 9, 4>(x[4]);
-    auto X5 = seed<T, 9, 5>(x[5]);
-    auto X6 = seed<T, 9, 6>(x[6]);
-    auto X7 = seed<T, 9, 7>(x[7]);
-    auto X8 = seed<T, 9, 8>(x[8]);
-    auto u0 = X3 - X0;  // x1 - x0
-    auto u1 = X4 - X1;
-    auto u2 = X5 - X2;
-    auto w0 = X6 - X0;  // x2 - x0
-    auto w1 = X7 - X1;
-    auto w2 = X8 - X2;
+    auto u0 = seed<T, 6, 0>(x[3] - x[0]);
+    auto u1 = seed<T, 6, 1>(x[4] - x[1]);
+    auto u2 = seed<T, 6, 2>(x[5] - x[2]);
+    auto w0 = seed<T, 6, 3>(x[6] - x[0]);
+    auto w1 = seed<T, 6, 4>(x[7] - x[1]);
+    auto w2 = seed<T, 6, 5>(x[8] - x[2]);
     auto a0 = u0 * D[0] + w0 * D[2];               // first column of F
     auto a1 = u1 * D[0] + w1 * D[2];
     auto a2 = u2 * D[0] + w2 * D[2];
@@ -145,50 +199,40 @@ ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Loc
     auto c22 = sq(b0) + sq(b1) + sq(b2);
     auto c12 = a0 * b0 + a1 * b1 + a2 * b2;
     auto p = psi(seed<T, 3, 0>(c11.v), seed<T, 3, 1>(c22.v), seed<T, 3, 2>(c12.v));
-    store_local(compose(p, c11, c22, c12), out);
+    Local<T, 6> le;
+    store_local(compose(p, c11, c22, c12), le);
+    expand_edges<TriEdges, 3>(le, out);
 }
 
-// area term (test energy of Sec. 7.6)
+// area term (test energy of Sec. 7.6), in the edge vectors u, w
 template <typename T>
 ADM_HD void area_local(const T (&x)[9], Local<T, 9> &out)
 {
-    auto X0 = seed<T, 9, 0>(x[0]);
-    auto X1 = seed<T, 9, 1>(x[1]);
-    auto X2 = seed<T, 9, 2>(x[2]);
-    auto X3 = seed<T, 9, 3>(x[3]);
-    auto X4 = seed<T, 9, 4>(x[4]);
-    auto X5 = seed<T, 9, 5>(x[5]);
-    auto X6 = seed<T, 9, 6>(x[6]);
-    auto X7 = seed<T, 9, 7>(x[7]);
-    auto X8 = seed<T, 9, 8>(x[8]);
-    auto u0 = X3 - X0;
-    auto u1 = X4 - X1;
-    auto u2 = X5 - X2;
-    auto w0 = X6 - X0;
-    auto w1 = X7 - X1;
-    auto w2 = X8 - X2;
+    auto u0 = seed<T, 6, 0>(x[3] - x[0]);
+    auto u1 = seed<T, 6, 1>(x[4] - x[1]);
+    auto u2 = seed<T, 6, 2>(x[5] - x[2]);
+    auto w0 = seed<T, 6, 3>(x[6] - x[0]);
+    auto w1 = seed<T, 6, 4>(x[7] - x[1]);
+    auto w2 = seed<T, 6, 5>(x[8] - x[2]);
     auto uu = sq(u0) + sq(u1) + sq(u2);
     auto ww = sq(w0) + sq(w1) + sq(w2);
     auto uw = u0 * w0 + u1 * w1 + u2 * w2;
     auto p = PsiArea<T>{}(seed<T, 3, 0>(uu.v), seed<T, 3, 1>(ww.v), seed<T, 3, 2>(uw.v));
-    store_local(compose(p, uu, ww, uw), out);
+    Local<T, 6> le;
+    store_local(compose(p, uu, ww, uw), le);
+    expand_edges<TriEdges, 3>(le, out);
 }
 
 // ------------------------------------------------------ triangle, VD = 2 --
-// C = J^T J of the UV Jacobian J = [b-a, c-a] Dinv; returns det J (value)
+// C = J^T J of the UV Jacobian J = [b-a, c-a] Dinv, differentiated in the
+// edge vectors b - a, c - a; returns det J (value)
 template <typename T, class Psi>
 ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> &out)
 {
-    auto X0 = seed<T, 6, 0>(x[0]);
-    auto X1 = seed<T, 6, 1>(x[1]);
-    auto X2 = seed<T, 6, 2>(x[2]);
-    auto X3 = seed<T, 6, 3>(x[3]);
-    auto X4 = seed<T, 6, 4>(x[4]);
-    auto X5 = seed<T, 6, 5>(x[5]);
-    auto u0 = X2 - X0;  // b - a
-    auto u1 = X3 - X1;
-    auto w0 = X4 - X0;  // c - a
-    auto w1 = X5 - X1;
+    auto u0 = seed<T, 4, 0>(x[2] - x[0]);  // b - a
+    auto u1 = seed<T, 4, 1>(x[3] - x[1]);
+    auto w0 = seed<T, 4, 2>(x[4] - x[0]);  // c - a
+    auto w1 = seed<T, 4, 3>(x[5] - x[1]);
     auto j00 = u0 * D[0] + w0 * D[2];
     auto j10 = u1 * D[0] + w1 * D[2];
     auto j01 = u0 * D[1] + w0 * D[3];
@@ -197,37 +241,28 @@ ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> 
     auto c22 = sq(j01) + sq(j11);
     auto c12 = j00 * j01 + j10 * j11;
     auto p = psi(seed<T, 3, 0>(c11.v), seed<T, 3, 1>(c22.v), seed<T, 3, 2>(c12.v));
-    store_local(compose(p, c11, c22, c12), out);
+    Local<T, 4> le;
+    store_local(compose(p, c11, c22, c12), le);
+    expand_edges<TriEdges, 2>(le, out);
     return j00.v * j11.v - j01.v * j10.v;
 }
 
 // ----------------------------------------------------------------- hinge --
 // hinge (x0, x1, xa, xb), face A = (x0, x1, xa), face B = (x1, x0, xb);
-// psi = w (theta - thetabar)^2.  Returns false for a degenerate hinge.
+// psi = w (theta - thetabar)^2, differentiated in the edge vectors e, u, v.
+// Returns false for a degenerate hinge.
 template <typename T>
 ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out)
 {
-    auto X0 = seed<T, 12, 0>(x[0]);
-    auto X1 = seed<T, 12, 1>(x[1]);
-    auto X2 = seed<T, 12, 2>(x[2]);
-    auto X3 = seed<T, 12, 3>(x[3]);
-    auto X4 = seed<T, 12, 4>(x[4]);
-    auto X5 = seed<T, 12, 5>(x[5]);
-    auto X6 = seed<T, 12, 6>(x[6]);
-    auto X7 = seed<T, 12, 7>(x[7]);
-    auto X8 = seed<T, 12, 8>(x[8]);
-    auto X9 = seed<T, 12, 9>(x[9]);
-    auto X10 = seed<T, 12, 10>(x[10]);
-    auto X11 = seed<T, 12, 11>(x[11]);
-    auto e0 = X3 - X0;    // x1 - x0
-    auto e1 = X4 - X1;
-    auto e2 = X5 - X2;
-    auto u0 = X6 - X0;    // xa - x0
-    auto u1 = X7 - X1;
-    auto u2 = X8 - X2;
-    auto v0 = X9 - X3;  // xb - x1
-    auto v1 = X10 - X4;
-    auto v2 = X11 - X5;
+    auto e0 = seed<T, 9, 0>(x[3] - x[0]);  // e = x1 - x0
+    auto e1 = seed<T, 9, 1>(x[4] - x[1]);
+    auto e2 = seed<T, 9, 2>(x[5] - x[2]);
+    auto u0 = seed<T, 9, 3>(x[6] - x[0]);  // u = xa - x0
+    auto u1 = seed<T, 9, 4>(x[7] - x[1]);
+    auto u2 = seed<T, 9, 5>(x[8] - x[2]);
+    auto v0 = seed<T, 9, 6>(x[9] - x[3]);  // v = xb - x1
+    auto v1 = seed<T, 9, 7>(x[10] - x[4]);
+    auto v2 = seed<T, 9, 8>(x[11] - x[5]);
     auto ee = sq(e0) + sq(e1) + sq(e2);
     auto eu = e0 * u0 + e1 * u1 + e2 * u2;
     auto ev = e0 * v0 + e1 * v1 + e2 * v2;
@@ -243,7 +278,9 @@ ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out)
     if (!(xc.v != T(0) || ys.v != T(0))) return false;
     auto th = atan2(ys, xc);
     auto p = sq(th - thetabar) * w;
-    store_local(compose(p, ee, eu, ev, uv, det), out);
+    Local<T, 9> le;
+    store_local(compose(p, ee, eu, ev, uv, det), le);
+    expand_edges<HingeEdges, 3>(le, out);
     return true;
 }
 

@@ -175,26 +175,31 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
         // one warp per footprint row: the row's blocks are contiguous in the
         // BSR and its codes say, per block, where the tile's sum is (none,
         // the vertex's diagonal, a pair block or its transpose) and whether
-        // other tiles add into the same block
+        // other tiles add into the same block.  A warp iteration writes BPI
+        // consecutive blocks; lane = sub * NB + k takes entry k of block sub,
+        // so the lane's offsets into the three source layouts are fixed.
+        constexpr int BPI = 32 / NB;
         constexpr uint64_t DTAB = VD == 3 ? 0x543421310ull : 0x2110ull;  // (r,s) -> packed upper
         constexpr uint64_t TTAB = VD == 3 ? 0x852741630ull : 0x3120ull;  // (r,s) -> (s,r)
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int sub = lane / NB, k = lane - sub * NB;
+        const bool active = sub < BPI;
+        const int off_d = (int)((DTAB >> (4 * k)) & 0xf), off_t = (int)((TTAB >> (4 * k)) & 0xf);
         for (int r = warp; r < nf; r += THREADS / 32) {
             const int64_t rs = ms_row[r] & 0x7fffffff;
-            const int c0 = ms_coff[r], c1 = ms_coff[r + 1];
-            T *out = A.bsr + rs * NB;
-            for (int idx = lane; idx < (c1 - c0) * NB; idx += 32) {
-                const int e = idx / NB, k = idx - e * NB;
+            const int c0 = ms_coff[r], nb = ms_coff[r + 1] - c0;
+            T *out = A.bsr + rs * NB + lane;
+            if (!active) continue;
+            for (int e = sub; e < nb; e += BPI) {
                 const uint32_t code = ms_codes[c0 + e];
                 const uint32_t kind = code >> 14;
                 if (kind == 0) continue;
                 const int slot = (int)(code & 0x1fffu);
-                T val;
-                if (kind == 1) val = dacc[r * ND + (int)((DTAB >> (4 * k)) & 0xf)];
-                else if (kind == 2) val = pacc[slot * NB + k];
-                else val = pacc[slot * NB + (int)((TTAB >> (4 * k)) & 0xf)];
-                if (code & 0x2000u) atomicAdd(out + idx, val);
-                else out[idx] = val;
+                const T *src = kind == 1 ? dacc + r * ND + off_d : pacc + slot * NB + (kind == 2 ? k : off_t);
+                const T val = *src;
+                T *dst = out + (e - sub) * NB;
+                if (code & 0x2000u) atomicAdd(dst, val);
+                else *dst = val;
             }
         }
     }
