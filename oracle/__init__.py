@@ -202,6 +202,21 @@ class Problem:
             out["elem_energy"] = elem[: self.n_elements()]
         return out
 
+    def hvp(self, x: np.ndarray, v: np.ndarray, route: int = 0):
+        """Matrix-free mode (Sec. 5.5 and Sec. 6.2: each element's local
+        Hessian applied to its gathered part of v, the products accumulated;
+        the CG solver of Sec. 7.2 uses it).  That sum, sum_j S_j^T H_j S_j v,
+        is the assembled Hessian of Eq. 2 applied to v, which is what this
+        computes: the oracle's BSR values times v, block by block.  Returns
+        the energy, the gradient and hv, both (nV, vdim)."""
+        out = self.assemble(x, route=route)
+        vd = self.vdim
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(self.nV, vd)
+        rows = np.repeat(np.arange(self.nV), np.diff(self.row_ptr))
+        hv = np.zeros((self.nV, vd))
+        np.add.at(hv, rows, np.einsum("bij,bj->bi", out["vals"], v[self.col]))
+        return {"energy": out["energy"], "grad": out["grad"], "hv": hv, "n_domain_err": out["n_domain_err"]}
+
     def arap_jacobian(self, uv: np.ndarray):
         """Residual r (4 nT), CSR Jacobian (row_ptr, col, val)."""
         uv = np.ascontiguousarray(uv, dtype=np.float64).reshape(self.nV, 2)
