@@ -217,6 +217,39 @@ class Problem:
         np.add.at(hv, rows, np.einsum("bij,bj->bi", out["vals"], v[self.col]))
         return {"energy": out["energy"], "grad": out["grad"], "hv": hv, "n_domain_err": out["n_domain_err"]}
 
+    def assemble_projected(self, x: np.ndarray, eps: float = 0.0):
+        """Hessian filtering (Sec. 7.1, after Teran et al. 2005): the local
+        Hessian of every element term has its negative eigenvalues set to
+        eps (>= 0) before Eq. 2 assembles it; energy and gradient are those
+        of assemble().  For the shell, the membrane triangle and the hinge
+        are separate terms.  A Python loop over elements: small meshes only."""
+        vd = self.vdim
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.nV, vd)
+        base = self.assemble(x, hessian=False)
+        vals = np.zeros((self.nnzb, vd, vd))
+
+        def scatter(vid, Hl):
+            for a, va in enumerate(vid):
+                lo, hi = self.row_ptr[va], self.row_ptr[va + 1]
+                for b, vb in enumerate(vid):
+                    k = lo + int(np.searchsorted(self.col[lo:hi], vb))
+                    vals[k] += Hl[a * vd:(a + 1) * vd, b * vd:(b + 1) * vd]
+
+        p = [] if self.params is None else list(self.params)
+        if self.energy != HINGE:
+            te = STVK if self.energy == SHELL else self.energy
+            for t in range(self.nT):
+                vid = self.F[t]
+                loc = local(te, x[vid], vd, self.Dinv[t], self.area[t], params=p[:3] or None)
+                scatter(vid, spd_project(loc["H"], eps))
+        if self.energy in (HINGE, SHELL):
+            ph = _shell_hinge_params(p) if self.energy == SHELL else (p or None)
+            for h in range(self.nH):
+                vid = self.H[h]
+                loc = local(HINGE, x[vid], 3, thetabar=self.thetabar[h], abar=self.abar[h], params=ph)
+                scatter(vid, spd_project(loc["H"], eps))
+        return {"energy": base["energy"], "grad": base["grad"], "vals": vals, "n_domain_err": base["n_domain_err"]}
+
     def arap_jacobian(self, uv: np.ndarray):
         """Residual r (4 nT), CSR Jacobian (row_ptr, col, val)."""
         uv = np.ascontiguousarray(uv, dtype=np.float64).reshape(self.nV, 2)
@@ -296,6 +329,25 @@ def hd_probe(op: int, *inputs):
     out = np.zeros(1 + n + n * n)
     lib().orc_hd_probe(op, np.asarray(inputs, dtype=np.float64), n, out)
     return out[0], out[1:1 + n], out[1 + n:].reshape(n, n)
+
+
+def spd_project(H: np.ndarray, eps: float = 0.0) -> np.ndarray:
+    """A symmetric matrix with its negative eigenvalues set to eps (the
+    per-term Hessian filtering of Sec. 7.1): Q max'(L) Q^T from eigh."""
+    lam, Q = np.linalg.eigh(0.5 * (H + H.T))
+    lam = np.where(lam < 0.0, eps, lam)
+    return (Q * lam) @ Q.T
+
+
+def _shell_hinge_params(p):
+    """Hinge parameters {k_b, h} of a shell parameter list {E, nu, t, k_b, h}
+    (the same defaults as the membrane: k_b = E t^3 / (12 (1 - nu^2)), h = 1)."""
+    E = p[0] if len(p) > 0 else 1.0e5
+    nu = p[1] if len(p) > 1 else 0.3
+    t = p[2] if len(p) > 2 else 1.0e-3
+    kb = p[3] if len(p) > 3 and p[3] >= 0 else E * t ** 3 / (12.0 * (1.0 - nu * nu))
+    h = p[4] if len(p) > 4 else 1.0
+    return [kb, h]
 
 
 def bsr_to_dense(nV: int, vd: int, row_ptr, col, vals) -> np.ndarray:
