@@ -257,6 +257,19 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
     m.set_option(adm.OPT_GRAPH, 0)
     out["graph"] = {"ms_per_step": ms, "value": n_el / (ms * 1e-3), "unit": UNIT}
 
+    # matrix-free Hessian-vector product on the same batch (energy, gradient
+    # and H v; no BSR written)
+    vv = torch.from_numpy(np.random.default_rng(7).normal(size=x.numel()).astype(np.float32)).cuda()
+    hv = torch.zeros_like(vv)
+    e1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    m.set_option(adm.OPT_PROFILE, steps)
+    ms = _time_steps(torch, lambda: m.eval_hvp(adm.SHELL, adm.FP32, x, vv, hv, e1, g, stream=stream), steps, stream)
+    prof = m.profile_read()
+    m.set_option(adm.OPT_PROFILE, 0)
+    out["hvp"] = {"workload": "matrix-free H v + gradient + energy on the shell batch, FP32",
+                  "value": n_el / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                  "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}}
+
     # learned membrane: train on the library's analytic Neo-Hookean targets
     # (1M deformation samples, stretches in [0.7, 1.4]), then evaluate on the
     # batch next to the analytic Neo-Hookean membrane
@@ -364,11 +377,18 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
     eg = torch.zeros(1, dtype=torch.float64, device="cuda")
     gg2 = torch.zeros(nVg * 2, dtype=torch.float64, device="cuda")
     Hg = torch.zeros(nnzbg * 4, dtype=torch.float64, device="cuda")
+    vg = torch.from_numpy(np.random.default_rng(8).normal(size=nVg * 2)).cuda()
+    hvg = torch.zeros_like(vg)
     msg = _time_steps(torch, lambda: mg.eval(adm.SYMDIR2D, adm.FP64, xg, eg, gg2, Hg, stream=stream), steps, stream)
+    msh = _time_steps(torch, lambda: mg.eval_hvp(adm.SYMDIR2D, adm.FP64, xg, vg, hvg, eg, gg2, stream=stream),
+                      steps, stream)
     mg.set_option(adm.OPT_GRAPH, 1)
     msgg = _time_steps(torch, lambda: mg.eval(adm.SYMDIR2D, adm.FP64, xg, eg, gg2, Hg, stream=stream), steps, stream)
+    mshg = _time_steps(torch, lambda: mg.eval_hvp(adm.SYMDIR2D, adm.FP64, xg, vg, hvg, eg, gg2, stream=stream),
+                       steps, stream)
     out["symdir_grid33_fp64"] = {"workload": "symmetric Dirichlet, 33x33 grid (2,048 triangles), FP64",
-                                 "us_per_pass": msg * 1e3, "us_per_pass_graph": msgg * 1e3}
+                                 "us_per_pass": msg * 1e3, "us_per_pass_graph": msgg * 1e3,
+                                 "hvp_us_per_call": msh * 1e3, "hvp_us_per_call_graph": mshg * 1e3}
     mg.close()
     return out
 

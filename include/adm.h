@@ -183,6 +183,25 @@ adm_status adm_slot_map(adm_handle h, adm_energy energy, const int32_t **slots_d
 adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
                     double *energy_dev, void *grad_dev, void *bsr_vals_dev, void *stream);
 
+/* Matrix-free Hessian-vector product (the paper's matrix-free mode,
+ * Sec. 5.5 and Sec. 6.2, which its Newton-CG parameterisation of Sec. 7.2
+ * calls once per CG iteration): hv = H(x) v = sum_j S_j^T H_j S_j v, each
+ * element's local Hessian applied to its gathered part of v and the products
+ * accumulated, without forming the global Hessian.  The same pass gives the
+ * energy and, optionally, the gradient.
+ *   x_dev, v_dev: device, n_rows * var_dim of the precision's type (v is the
+ *                 direction, vertex-major like x);
+ *   energy_dev:   device double, F(x) over every mesh (nullable);
+ *   grad_dev:     device, n_rows * var_dim (nullable);
+ *   hv_dev:       device, n_rows * var_dim, fully overwritten.
+ * All buffers are owned by the caller.  Runs on the tiled kernel whatever
+ * ADM_OPT_ASSEMBLER says (building its tiles on first use); takes part in
+ * ADM_OPT_GRAPH like adm_eval.  Errors: ADM_ERR_ARG (NULL x, v or hv, bad
+ * precision), ADM_ERR_UNSUPPORTED (residual energies; the learned membrane
+ * without attached weights or in FP64), ADM_ERR_CUDA. */
+adm_status adm_eval_hvp(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
+                        const void *v_dev, double *energy_dev, void *grad_dev, void *hv_dev, void *stream);
+
 /* Batched form: per-mesh energies (device, n_mesh doubles, nullable) and
  * per-mesh gradient 2-norms in FP64 (device, n_mesh doubles, nullable),
  * plus the batch gradient and Hessian as in adm_eval. */

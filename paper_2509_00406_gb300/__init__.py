@@ -70,6 +70,7 @@ def lib():
         "adm_hinges": (i32, [vp, pp, C.POINTER(i64)]),
         "adm_slot_map": (i32, [vp, i32, pp, C.POINTER(i64)]),
         "adm_eval": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
+        "adm_eval_hvp": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "adm_eval_batch": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "adm_eval_batch_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_eval_jacobian": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
@@ -203,6 +204,11 @@ class Mesh:
     def eval(self, energy: int, prec: int, x, energy_out=None, grad=None, bsr=None, stream=None):
         _check(lib().adm_eval(self._h, energy, prec, _ptr(x), _ptr(energy_out), _ptr(grad), _ptr(bsr),
                               _stream(stream)), "adm_eval")
+
+    def eval_hvp(self, energy: int, prec: int, x, v, hv, energy_out=None, grad=None, stream=None):
+        """Matrix-free H(x) v into hv (with the energy and, optionally, the gradient)."""
+        _check(lib().adm_eval_hvp(self._h, energy, prec, _ptr(x), _ptr(v), _ptr(energy_out), _ptr(grad),
+                                  _ptr(hv), _stream(stream)), "adm_eval_hvp")
 
     def eval_batch(self, energy: int, prec: int, x, energy_per_mesh=None, gnorm=None, grad=None,
                    bsr=None, stream=None):

@@ -216,12 +216,14 @@ bool energy_ok(int energy, int vdim)
 
 bool needs_hinges(int energy) { return energy == ADM_HINGE_BENDING || energy == ADM_SHELL; }
 
-adm_status prepare(adm_ctx *h, int energy)
+// tiles are built for the tiled assembler, and for the matrix-free product
+// (which only the tiled kernel implements) whatever the assembler option
+adm_status prepare(adm_ctx *h, int energy, bool need_tiles = false)
 {
     if (!energy_ok(energy, h->m.vdim)) return ADM_ERR_UNSUPPORTED;
     adm_status s = needs_hinges(energy) ? ensure_shell(h) : build_pattern(h, PAT_TRI);
     if (energy == ADM_MLP_MEMBRANE && h->assembler != 0) return ADM_ERR_UNSUPPORTED;
-    if (s != ADM_OK || h->assembler != 0 || energy == ADM_ARAP2D_RESIDUAL) return s;
+    if (s != ADM_OK || (h->assembler != 0 && !need_tiles) || energy == ADM_ARAP2D_RESIDUAL) return s;
     s = ensure_tiles(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
     if (s == ADM_OK && energy == ADM_MLP_MEMBRANE && !h->d_mlp_table)
         s = dev_alloc(h, &h->d_mlp_table, (size_t)h->m.nT * 10 * sizeof(float));
@@ -246,7 +248,8 @@ adm_status run_pass(adm_ctx *h, const EvalArgs &a)
     GraphEntry *hit = nullptr;
     for (auto &g : h->graphs)
         if (g.energy == a.energy && g.prec == a.prec && g.x == a.x && g.grad == a.grad && g.bsr == a.bsr &&
-            g.e_total == a.energy_total && g.e_mesh == a.energy_per_mesh && g.gnorm == a.gnorm_per_mesh)
+            g.e_total == a.energy_total && g.e_mesh == a.energy_per_mesh && g.gnorm == a.gnorm_per_mesh &&
+            g.v == a.v && g.hv == a.hv)
             hit = &g;
     if (!hit) {
         if (!h->capture_stream &&
@@ -261,6 +264,8 @@ adm_status run_pass(adm_ctx *h, const EvalArgs &a)
         g.e_total = a.energy_total;
         g.e_mesh = a.energy_per_mesh;
         g.gnorm = a.gnorm_per_mesh;
+        g.v = a.v;
+        g.hv = a.hv;
         EvalArgs c = a;
         c.stream = h->capture_stream;
         const int ring = h->prof_ring;
@@ -565,6 +570,30 @@ adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const v
     a.energy_per_mesh = nullptr;
     a.gnorm_per_mesh = nullptr;
     a.stream = as_stream(stream);
+    return run_pass(h, a);
+}
+
+adm_status adm_eval_hvp(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev, const void *v_dev,
+                        double *energy_dev, void *grad_dev, void *hv_dev, void *stream)
+{
+    if (!h || !x_dev || !v_dev || !hv_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
+    if (energy == ADM_ARAP2D_RESIDUAL) return ADM_ERR_UNSUPPORTED;
+    if (energy == ADM_MLP_MEMBRANE && (prec != ADM_FP32 || !h->d_mlp_theta)) return ADM_ERR_UNSUPPORTED;
+    adm_status s = prepare(h, energy, true);
+    if (s != ADM_OK) return s;
+    EvalArgs a;
+    a.energy = energy;
+    a.prec = prec;
+    a.vdim = h->m.vdim;
+    a.x = x_dev;
+    a.grad = grad_dev;
+    a.bsr = nullptr;
+    a.energy_total = energy_dev;
+    a.energy_per_mesh = nullptr;
+    a.gnorm_per_mesh = nullptr;
+    a.stream = as_stream(stream);
+    a.v = v_dev;
+    a.hv = hv_dev;
     return run_pass(h, a);
 }
 

@@ -16,7 +16,8 @@ constexpr int kThreads = 128;      // per-element kernels
 constexpr int kRedThreads = 256;   // reductions
 constexpr int kTileThreads = 256;  // tiled kernel
 
-enum Mode { MODE_VALUE = 0, MODE_GRAD = 1, MODE_HESS = 2 };
+// passive, gradient, full Hessian, matrix-free Hessian-vector product
+enum Mode { MODE_VALUE = 0, MODE_GRAD = 1, MODE_HESS = 2, MODE_HVP = 3 };
 
 template <typename T>
 struct TermConsts {

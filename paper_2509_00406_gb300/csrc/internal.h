@@ -126,6 +126,8 @@ struct GraphEntry {
     const void *x = nullptr;
     void *grad = nullptr, *bsr = nullptr;
     double *e_total = nullptr, *e_mesh = nullptr, *gnorm = nullptr;
+    const void *v = nullptr;
+    void *hv = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -211,6 +213,8 @@ struct EvalArgs {
     double *energy_per_mesh;   // nullable, device
     double *gnorm_per_mesh;    // nullable, device
     cudaStream_t stream;
+    const void *v = nullptr;   // matrix-free mode: direction (device, like x)
+    void *hv = nullptr;        // matrix-free mode: H v (device, like the gradient)
 };
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
 // brackets one stage of one evaluation with events when profiling is on

@@ -24,6 +24,8 @@ struct TiledArgs {
     int64_t nT, nH;                   // SoA strides
     const T *x;
     T *grad, *bsr;
+    const T *v;                       // matrix-free mode: direction
+    T *hv;                            // matrix-free mode: H v
     double *epart;
     int *status;
     TermConsts<T> c;
@@ -41,7 +43,7 @@ __device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint
     for (int a = 0; a < NV; ++a)
 #pragma unroll
         for (int d = 0; d < VD; ++d) atomicAdd(gacc + lid[a] * VD + d, L.g[a * VD + d]);
-    if (mode < MODE_HESS) return;
+    if (mode != MODE_HESS) return;
 #pragma unroll
     for (int a = 0; a < NV; ++a)
 #pragma unroll
@@ -58,6 +60,27 @@ __device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint
 #pragma unroll
             for (int s = 0; s < VD; ++s)
                 atomicAdd(dst + r * VD + s, fwd ? H(a * VD + r, b * VD + s) : H(b * VD + r, a * VD + s));
+    }
+}
+
+// matrix-free mode: the element's local Hessian applied to its gathered
+// part of v, added with its gradient into the footprint accumulators
+template <typename T, int VD, int NV, int K>
+__device__ __forceinline__ void tile_hvp(const Local<T, K> &L, const uint16_t (&lid)[NV], const T *vs, T *gacc,
+                                         T *hacc)
+{
+    T vl[K];
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int d = 0; d < VD; ++d) vl[a * VD + d] = vs[lid[a] * VD + d];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        T y = -T(0);
+#pragma unroll
+        for (int j = 0; j < K; ++j) y += L.H[i <= j ? hix(i, j) : hix(j, i)] * vl[j];
+        atomicAdd(hacc + lid[i / VD] * VD + i % VD, y);
+        atomicAdd(gacc + lid[i / VD] * VD + i % VD, L.g[i]);
     }
 }
 
@@ -80,6 +103,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
     T *gacc = xs + VD * nf;
     T *dacc = gacc + VD * nf;
     T *pacc = dacc + ND * nf;
+    T *vs = gacc + VD * nf;    // matrix-free mode: v of the footprint ...
+    T *hacc = vs + VD * nf;    // ... and the H v accumulators (in place of dacc, pacc)
     // the tile's row metadata follows the accumulators; one thread starts
     // its bulk copy now, and it lands while the elements are evaluated
     const size_t acc_bytes = sizeof(T) * (size_t)((2 * VD + ND) * nf + NB * np);
@@ -95,8 +120,17 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
         const int64_t v = A.foot[foot_begin + i];
 #pragma unroll
         for (int d = 0; d < VD; ++d) xs[VD * i + d] = A.x[v * VD + d];
+        if (MODE == MODE_HVP) {
+#pragma unroll
+            for (int d = 0; d < VD; ++d) {
+                vs[VD * i + d] = A.v[v * VD + d];
+                gacc[VD * i + d] = T(0);
+                hacc[VD * i + d] = T(0);
+            }
+        }
     }
-    for (int i = threadIdx.x; i < (VD + ND) * nf + NB * np; i += THREADS) gacc[i] = T(0);
+    if (MODE != MODE_HVP)
+        for (int i = threadIdx.x; i < (VD + ND) * nf + NB * np; i += THREADS) gacc[i] = T(0);
     __syncthreads();
     double fe = 0.0;
     if constexpr (TRIS) {
@@ -124,7 +158,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
                 continue;
             }
             fe += (double)L.f;
-            if (MODE >= MODE_GRAD) tile_accumulate<T, VD, 3, 3, K>(L, lid, slot, TP, gacc, dacc, pacc, MODE);
+            if (MODE == MODE_HVP) tile_hvp<T, VD, 3, K>(L, lid, vs, gacc, hacc);
+            else if (MODE >= MODE_GRAD) tile_accumulate<T, VD, 3, 3, K>(L, lid, slot, TP, gacc, dacc, pacc, MODE);
         }
     }
     if constexpr (HINGES) {
@@ -149,7 +184,8 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
                 continue;
             }
             fe += (double)L.f;
-            if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 4, 6, 12>(L, lid, slot, HP, gacc, dacc, pacc, MODE);
+            if (MODE == MODE_HVP) tile_hvp<T, 3, 4, 12>(L, lid, vs, gacc, hacc);
+            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 4, 6, 12>(L, lid, slot, HP, gacc, dacc, pacc, MODE);
         }
     }
     __syncthreads();
@@ -171,7 +207,19 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
             }
         }
     }
-    if (MODE >= MODE_HESS && meta_ok) {
+    if (MODE == MODE_HVP && meta_ok) {  // H v rows: shared exactly where gradient rows are
+        for (int i = threadIdx.x; i < nf; i += THREADS) {
+            const int32_t rs = ms_row[i];
+            const int64_t v = A.foot[foot_begin + i];
+#pragma unroll
+            for (int d = 0; d < VD; ++d) {
+                const T val = hacc[VD * i + d];
+                if (rs < 0) atomicAdd(A.hv + v * VD + d, val);
+                else A.hv[v * VD + d] = val;
+            }
+        }
+    }
+    if (MODE == MODE_HESS && meta_ok) {
         // one warp per footprint row: the row's blocks are contiguous in the
         // BSR and its codes say, per block, where the tile's sum is (none,
         // the vertex's diagonal, a pair block or its transpose) and whether
@@ -207,10 +255,10 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
     if (threadIdx.x == 0) A.epart[t] = sum;
 }
 
-// zero the blocks and gradient rows that several tiles add into
+// zero the blocks and gradient (and H v) rows that several tiles add into
 template <typename T, int VD>
 __global__ void k_zero_shared(const int32_t *blocks, int64_t nb, const int32_t *verts, int64_t nv, T *bsr,
-                              T *grad)
+                              T *grad, T *hv)
 {
     constexpr int NB = VD * VD;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -219,6 +267,8 @@ __global__ void k_zero_shared(const int32_t *blocks, int64_t nb, const int32_t *
         for (int64_t i = i0; i < nb * NB; i += stride) bsr[(int64_t)blocks[i / NB] * NB + i % NB] = T(0);
     if (grad)
         for (int64_t i = i0; i < nv * VD; i += stride) grad[(int64_t)verts[i / VD] * VD + i % VD] = T(0);
+    if (hv)
+        for (int64_t i = i0; i < nv * VD; i += stride) hv[(int64_t)verts[i / VD] * VD + i % VD] = T(0);
 }
 
 template <typename T, int ENERGY, bool TRIS, bool HINGES>
@@ -230,7 +280,8 @@ static void launch_tiled_modes(int mode, int n_tiles, size_t smem, cudaStream_t 
     };
     if (mode == MODE_VALUE) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_VALUE, kTileThreads>);
     else if (mode == MODE_GRAD) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_GRAD, kTileThreads>);
-    else go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_HESS, kTileThreads>);
+    else if (mode == MODE_HESS) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_HESS, kTileThreads>);
+    else go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_HVP, kTileThreads>);
 }
 
 template <typename T>
@@ -259,7 +310,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     const int vd = m.vdim;
     const bool hin = has_hinges(a.energy);
     const TileSet &ts = h->tiles[hin ? PAT_SHELL : PAT_TRI];
-    const int mode = a.bsr ? MODE_HESS : (a.grad ? MODE_GRAD : MODE_VALUE);
+    const int mode = a.hv ? MODE_HVP : (a.bsr ? MODE_HESS : (a.grad ? MODE_GRAD : MODE_VALUE));
     const size_t smem = (size_t)ts.smem_bytes[vd == 3][sizeof(T) == 4 ? ADM_FP32 : ADM_FP64];
     if (smem > 227 * 1024) return ADM_ERR_UNSUPPORTED;
     cudaStream_t s = a.stream;
@@ -267,16 +318,16 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     tm.begin(ADM_STAGE_ZERO);
     if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
     const int64_t nzb = a.bsr ? (int64_t)ts.zero_blocks.size() : 0;
-    const int64_t nzv = a.grad ? (int64_t)ts.zero_verts.size() : 0;
+    const int64_t nzv = (a.grad || a.hv) ? (int64_t)ts.zero_verts.size() : 0;
     if (nzb + nzv > 0) {
         const int64_t work = std::max(nzb * vd * vd, nzv * vd);
         const int blocks = (int)std::min<int64_t>((work + 255) / 256, 152 * 8);
         if (vd == 3)
             k_zero_shared<T, 3><<<blocks, 256, 0, s>>>(ts.d_zero_blocks, nzb, ts.d_zero_verts, nzv,
-                                                        (T *)a.bsr, (T *)a.grad);
+                                                        (T *)a.bsr, (T *)a.grad, (T *)a.hv);
         else
             k_zero_shared<T, 2><<<blocks, 256, 0, s>>>(ts.d_zero_blocks, nzb, ts.d_zero_verts, nzv,
-                                                        (T *)a.bsr, (T *)a.grad);
+                                                        (T *)a.bsr, (T *)a.grad, (T *)a.hv);
     }
     tm.end(ADM_STAGE_ZERO);
     TiledArgs<T> A;
@@ -293,6 +344,8 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     A.x = (const T *)a.x;
     A.grad = (T *)a.grad;
     A.bsr = (T *)a.bsr;
+    A.v = (const T *)a.v;
+    A.hv = (T *)a.hv;
     A.epart = h->d_epart;
     A.status = h->d_status;
     A.c = consts<T>(h, a.energy);

@@ -26,7 +26,7 @@ def cases():
     xs = synth.perturb(V, sigma=2e-2, seed=12)
     out = [("symdir", oracle.Problem(grid.rest, grid.faces, oracle.SYMDIR, 2), grid.x)]
     for name, e in [("stvk", oracle.STVK), ("nh", oracle.NH), ("hinge", oracle.HINGE), ("shell", oracle.SHELL)]:
-        out.append((name, oracle.Problem(V, F, e, 3, SHELL_P), xs))
+        out.append((name, oracle.Problem(V, F, e, 3, [0.5, 1.0] if e == oracle.HINGE else SHELL_P), xs))
     return out
 
 
