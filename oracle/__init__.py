@@ -222,7 +222,9 @@ class Problem:
         Hessian of every element term has its negative eigenvalues set to
         eps (>= 0) before Eq. 2 assembles it; energy and gradient are those
         of assemble().  For the shell, the membrane triangle and the hinge
-        are separate terms.  A Python loop over elements: small meshes only."""
+        are separate terms.  Reading: the term's rigid translations are exact
+        zeros of its Hessian, not negative eigenvalues, and stay zero.  A
+        Python loop over elements: small meshes only."""
         vd = self.vdim
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(self.nV, vd)
         base = self.assemble(x, hessian=False)
@@ -241,13 +243,13 @@ class Problem:
             for t in range(self.nT):
                 vid = self.F[t]
                 loc = local(te, x[vid], vd, self.Dinv[t], self.area[t], params=p[:3] or None)
-                scatter(vid, spd_project(loc["H"], eps))
+                scatter(vid, spd_project(loc["H"], eps, translations(3, vd)))
         if self.energy in (HINGE, SHELL):
             ph = _shell_hinge_params(p) if self.energy == SHELL else (p or None)
             for h in range(self.nH):
                 vid = self.H[h]
                 loc = local(HINGE, x[vid], 3, thetabar=self.thetabar[h], abar=self.abar[h], params=ph)
-                scatter(vid, spd_project(loc["H"], eps))
+                scatter(vid, spd_project(loc["H"], eps, translations(4, 3)))
         return {"energy": base["energy"], "grad": base["grad"], "vals": vals, "n_domain_err": base["n_domain_err"]}
 
     def arap_jacobian(self, uv: np.ndarray):
@@ -331,12 +333,34 @@ def hd_probe(op: int, *inputs):
     return out[0], out[1:1 + n], out[1 + n:].reshape(n, n)
 
 
-def spd_project(H: np.ndarray, eps: float = 0.0) -> np.ndarray:
+def spd_project(H: np.ndarray, eps: float = 0.0, keep=None) -> np.ndarray:
     """A symmetric matrix with its negative eigenvalues set to eps (the
-    per-term Hessian filtering of Sec. 7.1): Q max'(L) Q^T from eigh."""
-    lam, Q = np.linalg.eigh(0.5 * (H + H.T))
+    per-term Hessian filtering of Sec. 7.1): Q max'(L) Q^T from eigh.
+
+    keep: optional (n, m) orthonormal columns spanning exact null directions
+    of H that must stay null (a term's translations).  The spectrum is then
+    taken on their orthogonal complement only, so round-off in those exact
+    zeros cannot turn them into clamped 'negative' eigenvalues."""
+    Hs = 0.5 * (H + H.T)
+    if keep is None:
+        lam, Q = np.linalg.eigh(Hs)
+        lam = np.where(lam < 0.0, eps, lam)
+        return (Q * lam) @ Q.T
+    n = Hs.shape[0]
+    U, _, _ = np.linalg.svd(keep, full_matrices=True)
+    B = U[:, keep.shape[1]:]                      # orthonormal complement
+    lam, Q = np.linalg.eigh(B.T @ Hs @ B)
     lam = np.where(lam < 0.0, eps, lam)
-    return (Q * lam) @ Q.T
+    W = B @ Q
+    return (W * lam) @ W.T
+
+
+def translations(nv: int, vd: int) -> np.ndarray:
+    """Orthonormal basis (nv vd, vd) of rigid translations of nv vertices."""
+    T = np.zeros((nv * vd, vd))
+    for d in range(vd):
+        T[d::vd, d] = 1.0 / np.sqrt(nv)
+    return T
 
 
 def _shell_hinge_params(p):

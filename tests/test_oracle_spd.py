@@ -9,7 +9,9 @@ to facts outside it:
   the plain Hessian by a positive semidefinite matrix (only eigenvalues
   below zero were raised);
 * at the rest state, where StVK's local Hessians are already semidefinite,
-  projection changes nothing."""
+  projection changes nothing;
+* a term's translations, exact zeros of its Hessian, stay zero when eps > 0
+  (the reading of the filter), while its negative eigenvalues become eps."""
 import numpy as np
 import pytest
 
@@ -84,3 +86,19 @@ def test_eps_sets_clamped_eigenvalues():
     lp = np.sort(np.linalg.eigvalsh(oracle.spd_project(loc["H"], eps)))
     want = np.sort(np.where(lam < 0, eps, lam))
     assert np.abs(lp - want).max() <= 1e-10 * np.abs(lam).max()
+
+
+def test_translations_stay_null_with_positive_eps():
+    V, F = synth.icosphere(1)
+    x = synth.perturb(V, sigma=5e-2, seed=7)
+    P = oracle.Problem(V, F, oracle.HINGE, 3, [0.5, 1.0])
+    loc = oracle.local(oracle.HINGE, x[P.H[0]], 3, thetabar=P.thetabar[0], abar=P.abar[0], params=[0.5, 1.0])
+    T = oracle.translations(4, 3)
+    eps = 1e-2 * np.abs(loc["H"]).max()
+    Hp = oracle.spd_project(loc["H"], eps, T)
+    assert np.abs(Hp @ T).max() <= 1e-12 * np.abs(Hp).max()       # translations stay in the null space
+    B = np.linalg.svd(T, full_matrices=True)[0][:, 3:]
+    lam = np.linalg.eigvalsh(B.T @ loc["H"] @ B)
+    want = np.sort(np.where(lam < 0, eps, lam))
+    got = np.sort(np.linalg.eigvalsh(B.T @ Hp @ B))
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(lam).max()
