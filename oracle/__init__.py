@@ -382,3 +382,96 @@ def bsr_to_dense(nV: int, vd: int, row_ptr, col, vals) -> np.ndarray:
             j = col[p]
             Hd[i * vd:(i + 1) * vd, j * vd:(j + 1) * vd] += vals[p]
     return Hd
+
+
+# --------------------------------------------------------------------------
+# mass-spring cloth (Sec. 7.1): per-edge springs, per-vertex inertia and
+# gravity, written out from their definitions with numpy
+# --------------------------------------------------------------------------
+CLOTH = 8
+
+
+def mesh_edges(F: np.ndarray) -> np.ndarray:
+    """Unique undirected edges (min, max) of a triangle list, sorted."""
+    F = np.asarray(F, dtype=np.int64)
+    e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
+    e.sort(axis=1)
+    return np.unique(e, axis=0)
+
+
+def lumped_mass(rest: np.ndarray, F: np.ndarray, rho: float) -> np.ndarray:
+    """Lumped (diagonal) mass: each vertex gets a third of the rest area of
+    every triangle around it, times the areal density rho."""
+    rest = np.asarray(rest, dtype=np.float64)
+    F = np.asarray(F, dtype=np.int64)
+    a = 0.5 * np.linalg.norm(np.cross(rest[F[:, 1]] - rest[F[:, 0]], rest[F[:, 2]] - rest[F[:, 0]]), axis=1)
+    m = np.zeros(rest.shape[0])
+    for c in range(3):
+        np.add.at(m, F[:, c], rho * a / 3.0)
+    return m
+
+
+def cloth_params(p=None):
+    """{k, h, rho, gx, gy, gz}: spring stiffness, time step, areal density,
+    gravity; defaults 1e4, 1/60, 1, (0, 0, -9.81)."""
+    d = [1.0e4, 1.0 / 60.0, 1.0, 0.0, 0.0, -9.81]
+    p = [] if p is None else list(p)
+    return [p[i] if i < len(p) else d[i] for i in range(6)]
+
+
+def cloth_assemble(rest, F, x, xhat, params=None, row_ptr=None, col=None, project=False, eps=0.0):
+    """Implicit-Euler cloth energy of Sec. 7.1 and its derivatives:
+        E(x) = sum_v m_v/2 |x_v - xhat_v|^2 + h^2 ( sum_e P_e(x) - sum_v m_v g.x_v ),
+        P_e = l^2 k/2 (|x_i - x_j|^2 / l^2 - 1)^2  (edge e = (i, j), rest length l).
+    Returns energy, gradient (nV, 3) and, given the block pattern, the BSR
+    values of the Hessian (3x3 blocks).  With project, every spring's
+    local Hessian is filtered as in Problem.assemble_projected (the vertex
+    terms' m_v I needs none)."""
+    k, h, rho = cloth_params(params)[:3]
+    g = np.asarray(cloth_params(params)[3:6])
+    rest = np.asarray(rest, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    xhat = np.asarray(xhat, dtype=np.float64).reshape(-1, 3)
+    nV = x.shape[0]
+    E = mesh_edges(F)
+    m = lumped_mass(rest, F, rho)
+    i, j = E[:, 0], E[:, 1]
+    l2 = np.sum((rest[i] - rest[j]) ** 2, axis=1)
+    d = x[i] - x[j]
+    s = np.sum(d * d, axis=1) / l2
+    energy = np.sum(0.5 * m * np.sum((x - xhat) ** 2, axis=1)) \
+        + h * h * (np.sum(0.5 * k * l2 * (s - 1.0) ** 2) - np.sum(m * (x @ g)))
+    gs = (h * h * 2.0 * k * (s - 1.0))[:, None] * d
+    grad = m[:, None] * (x - xhat) - h * h * m[:, None] * g[None, :]
+    np.add.at(grad, i, gs)
+    np.add.at(grad, j, -gs)
+    out = {"energy": float(energy), "grad": grad}
+    if row_ptr is None:
+        return out
+    I3 = np.eye(3)
+    A = h * h * (2.0 * k * (s - 1.0))[:, None, None] * I3 + h * h * (4.0 * k / l2)[:, None, None] * \
+        d[:, :, None] * d[:, None, :]
+    if project:
+        T = translations(2, 3)
+        loc = np.zeros((len(E), 6, 6))
+        for q in range(len(E)):
+            L = np.block([[A[q], -A[q]], [-A[q], A[q]]])
+            loc[q] = spd_project(L, eps, T)
+        Aii, Ajj, Aij = loc[:, :3, :3], loc[:, 3:, 3:], loc[:, :3, 3:]
+    else:
+        Aii, Ajj, Aij = A, A, -A
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    keys = np.repeat(np.arange(nV), np.diff(row_ptr)) * nV + col
+
+    def blk(r, c):
+        return np.searchsorted(keys, np.asarray(r) * nV + np.asarray(c))
+
+    vals = np.zeros((col.shape[0], 3, 3))
+    np.add.at(vals, blk(np.arange(nV), np.arange(nV)), m[:, None, None] * I3)
+    np.add.at(vals, blk(i, i), Aii)
+    np.add.at(vals, blk(j, j), Ajj)
+    np.add.at(vals, blk(i, j), Aij)
+    np.add.at(vals, blk(j, i), np.transpose(Aij, (0, 2, 1)))
+    out["vals"] = vals
+    return out

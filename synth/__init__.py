@@ -38,6 +38,7 @@ __all__ = [
     "icosphere",
     "perturb",
     "noisy_disk",
+    "cloth_grid",
     "shell_batch",
     "shell_batch_levels",
     "membrane_samples",
@@ -62,6 +63,7 @@ class Mesh:
     v_off: np.ndarray = field(default=None)
     f_off: np.ndarray = field(default=None)
     name: str = ""
+    xhat: np.ndarray = field(default=None)  # (nV, 3) inertial target of a time step (cloth), or None
 
     def __post_init__(self):
         if self.v_off is None:
@@ -112,6 +114,34 @@ def grid_uv(n: int = 33, sigma: float = 0.01, seed: int = 1, relative: bool = Tr
     s_abs = sigma / (n - 1) if relative else sigma
     x = rest[:, :2] + rng.normal(0.0, s_abs, size=(n * n, 2))
     return Mesh(rest=rest, faces=faces, x=x, name=f"grid{n}")
+
+
+# --------------------------------------------------------------------------
+# Cloth grid (mass-spring workload)
+# --------------------------------------------------------------------------
+def cloth_grid(n: int = 100, sigma: float = 0.05, seed: int = 6) -> Mesh:
+    """n x n vertex cloth on [0,1]^2 at z = 0, triangulated as grid_uv.
+    x = rest + N(0, s^2) on all three coordinates and the inertial target
+    xhat (standing for x^n + h v^n of an implicit Euler step) = rest +
+    N(0, s^2) independently, with s = sigma / (n - 1), a fraction of the
+    grid spacing."""
+    s = np.linspace(0.0, 1.0, n)
+    gx, gy = np.meshgrid(s, s, indexing="xy")
+    rest = np.zeros((n * n, 3))
+    rest[:, 0] = gx.ravel()
+    rest[:, 1] = gy.ravel()
+    j, i = np.meshgrid(np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    v00 = (j * n + i).ravel()
+    v10, v01 = v00 + 1, v00 + n
+    v11 = v01 + 1
+    faces = np.empty((2 * v00.size, 3), dtype=np.int32)
+    faces[0::2] = np.stack([v00, v10, v11], axis=1)
+    faces[1::2] = np.stack([v00, v11, v01], axis=1)
+    rng = np.random.default_rng(seed)
+    sd = sigma / (n - 1)
+    x = rest + rng.normal(0.0, sd, size=rest.shape)
+    xhat = rest + rng.normal(0.0, sd, size=rest.shape)
+    return Mesh(rest=rest, faces=faces, x=x, name=f"cloth{n}", xhat=xhat)
 
 
 # --------------------------------------------------------------------------
