@@ -333,9 +333,16 @@ def hd_probe(op: int, *inputs):
     return out[0], out[1:1 + n], out[1 + n:].reshape(n, n)
 
 
-def spd_project(H: np.ndarray, eps: float = 0.0, keep=None) -> np.ndarray:
+SPD_TAU = 1e-10  # an eigenvalue is negative below -SPD_TAU * max |eigenvalue|
+
+
+def spd_project(H: np.ndarray, eps: float = 0.0, keep=None, tau: float = SPD_TAU) -> np.ndarray:
     """A symmetric matrix with its negative eigenvalues set to eps (the
     per-term Hessian filtering of Sec. 7.1): Q max'(L) Q^T from eigh.
+
+    An eigenvalue counts as negative below -tau max|lambda| (reading: a
+    term's structural zeros, which round-off puts on either side of zero,
+    are not negative; every hinge term has one besides its translations).
 
     keep: optional (n, m) orthonormal columns spanning exact null directions
     of H that must stay null (a term's translations).  The spectrum is then
@@ -344,13 +351,13 @@ def spd_project(H: np.ndarray, eps: float = 0.0, keep=None) -> np.ndarray:
     Hs = 0.5 * (H + H.T)
     if keep is None:
         lam, Q = np.linalg.eigh(Hs)
-        lam = np.where(lam < 0.0, eps, lam)
+        lam = np.where(lam < -tau * np.abs(lam).max(), eps, lam)
         return (Q * lam) @ Q.T
     n = Hs.shape[0]
     U, _, _ = np.linalg.svd(keep, full_matrices=True)
     B = U[:, keep.shape[1]:]                      # orthonormal complement
     lam, Q = np.linalg.eigh(B.T @ Hs @ B)
-    lam = np.where(lam < 0.0, eps, lam)
+    lam = np.where(lam < -tau * np.abs(lam).max(), eps, lam)
     W = B @ Q
     return (W * lam) @ W.T
 

@@ -78,13 +78,16 @@ def test_eps_sets_clamped_eigenvalues():
     V, F = synth.icosphere(1)
     x = synth.perturb(V, sigma=5e-2, seed=6)
     P = oracle.Problem(V, F, oracle.NH, 3, SHELL_P)
-    t = 0
-    vid = P.F[t]
-    loc = oracle.local(oracle.NH, x[vid], 3, P.Dinv[t], P.area[t], params=SHELL_P)
-    lam = np.linalg.eigvalsh(loc["H"])
+    for t in range(P.nT):  # the first triangle whose Hessian is indefinite
+        loc = oracle.local(oracle.NH, x[P.F[t]], 3, P.Dinv[t], P.area[t], params=SHELL_P)
+        lam = np.linalg.eigvalsh(loc["H"])
+        if lam.min() < -1e-3 * np.abs(lam).max():
+            break
     eps = 1e-3 * np.abs(lam).max()
     lp = np.sort(np.linalg.eigvalsh(oracle.spd_project(loc["H"], eps)))
-    want = np.sort(np.where(lam < 0, eps, lam))
+    # negative: below -tau max|lambda|; the translations' round-off zeros stay zero
+    want = np.sort(np.where(lam < -oracle.SPD_TAU * np.abs(lam).max(), eps, lam))
+    assert np.sum(lam < -oracle.SPD_TAU * np.abs(lam).max()) >= 1
     assert np.abs(lp - want).max() <= 1e-10 * np.abs(lam).max()
 
 
@@ -102,3 +105,21 @@ def test_translations_stay_null_with_positive_eps():
     want = np.sort(np.where(lam < 0, eps, lam))
     got = np.sort(np.linalg.eigvalsh(B.T @ Hp @ B))
     assert np.abs(got - want).max() <= 1e-10 * np.abs(lam).max()
+
+
+def test_hinge_structural_zero_not_clamped():
+    """Every hinge Hessian has one structural zero besides its translations
+    (theta depends on 5 of the 6 Gram invariants of its edge vectors); with
+    eps > 0 it must stay zero whatever sign round-off gives it."""
+    V, F = synth.icosphere(2)
+    x = synth.perturb(V, sigma=5e-2, seed=33)
+    P = oracle.Problem(V, F, oracle.HINGE, 3, [0.5, 1.0])
+    T = oracle.translations(4, 3)
+    B = np.linalg.svd(T, full_matrices=True)[0][:, 3:]
+    for h in range(0, P.nH, 37):
+        loc = oracle.local(oracle.HINGE, x[P.H[h]], 3, thetabar=P.thetabar[h], abar=P.abar[h], params=[0.5, 1.0])
+        lam = np.linalg.eigvalsh(B.T @ loc["H"] @ B)
+        assert np.sort(np.abs(lam))[0] <= 1e-14 * np.abs(lam).max()      # the structural zero
+        eps = 1e-2 * np.abs(lam).max()
+        lp = np.linalg.eigvalsh(B.T @ oracle.spd_project(loc["H"], eps, T) @ B)
+        assert np.sort(np.abs(lp))[0] <= 1e-12 * np.abs(lam).max()       # still zero, not eps
