@@ -270,6 +270,18 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
                   "value": n_el / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                   "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}}
 
+    # the same pass with per-term Hessian filtering (negative local
+    # eigenvalues clamped to 0 by an in-register Jacobi eigensolve)
+    m.set_projection(True, 0.0)
+    m.set_option(adm.OPT_PROFILE, steps)
+    ms = _time_steps(torch, lambda: m.eval_batch(adm.SHELL, adm.FP32, x, e, gn, g, H, stream=stream), steps, stream)
+    prof = m.profile_read()
+    m.set_option(adm.OPT_PROFILE, 0)
+    m.set_projection(False, 0.0)
+    out["hessian_filtered"] = {"workload": "grad + BSR Hessian with per-term SPD projection, shell batch, FP32",
+                               "value": n_el / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                               "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}}
+
     # learned membrane: train on the library's analytic Neo-Hookean targets
     # (1M deformation samples, stretches in [0.7, 1.4]), then evaluate on the
     # batch next to the analytic Neo-Hookean membrane
@@ -368,6 +380,27 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
     out["arap_jacobian"] = {"workload": f"ARAP-style residual Jacobian + J^T J, noisy disk ({d.nT} triangles), FP32",
                             "value": d.nT / (msd * 1e-3), "unit": "triangles/s", "ms_per_step": msd}
     md.close()
+
+    # mass-spring cloth (Sec. 7.1, the paper's Table 1 sizes): energy, gradient
+    # and BSR Hessian of springs + inertia + gravity, FP32
+    cloth = []
+    for n in (100, 500, 1000):
+        cg = synth.cloth_grid(n, seed=6)
+        mc = adm.Mesh(cg.rest, cg.faces, 3)
+        mc.set_inertia_target(cg.xhat)
+        _, nVc, nnzbc, _, _ = mc.pattern(adm.MASS_SPRING)
+        xc = torch.from_numpy(cg.x.astype(np.float32)).cuda()
+        ec = torch.zeros(1, dtype=torch.float64, device="cuda")
+        gc = torch.zeros(nVc * 3, dtype=torch.float32, device="cuda")
+        Hc = torch.zeros(nnzbc * 9, dtype=torch.float32, device="cuda")
+        msc = _time_steps(torch, lambda: mc.eval(adm.MASS_SPRING, adm.FP32, xc, ec, gc, Hc, stream=stream),
+                          min(steps, 100), stream)
+        n_edge = (nnzbc - nVc) // 2
+        cloth.append({"vertices": nVc, "edges": n_edge, "ms_per_eval": msc,
+                      "elements_per_s": (n_edge + nVc) / (msc * 1e-3)})
+        mc.close()
+    out["mass_spring_cloth"] = {"workload": "cloth grids n x n, springs + lumped inertia + gravity, grad + BSR "
+                                            "Hessian, FP32", "sizes": cloth}
 
     # symmetric Dirichlet, 33 x 33 grid, FP64 (launch-bound): direct and graph
     gu = synth.grid_uv()

@@ -76,6 +76,11 @@ typedef enum {
     ADM_NH_MEMBRANE = 5,      /* Neo-Hookean on the invariants of C (Sec. 7.7)      */
     ADM_MLP_MEMBRANE = 6,     /* learned Neo-Hookean surrogate (adm_mlp_* calls)    */
     ADM_AREA = 7,             /* 1/2 |(x_j - x_i) x (x_k - x_i)| (Sec. 7.6)         */
+    ADM_MASS_SPRING = 8,      /* implicit-Euler cloth (Sec. 7.1): per-vertex
+                                 m_v/2 |x_v - xhat_v|^2 - h^2 m_v g.x_v and
+                                 per-edge springs h^2 l^2 k/2 (|x_i - x_j|^2 / l^2
+                                 - 1)^2; lumped m_v = rho * a third of the rest
+                                 area around v; var_dim 3; tiled kernel only  */
     ADM_ARAP2D_RESIDUAL = 16  /* 4 residuals sqrt(A) vec(J - R(J)) per triangle,
                                  var_dim 2 (vector-valued term, Eq. 3)              */
 } adm_energy;
@@ -87,7 +92,10 @@ typedef enum {
     ADM_OPT_ASSEMBLER = 1,    /* 0 = tiled (shared-memory patches, default),
                                  1 = per-element atomic scatter (the paper's
                                  Sec. 5.5 scheme, kept as a reference path)    */
-    ADM_OPT_TILE_TRIS = 2,    /* triangles per tile of the tiled assembler      */
+    ADM_OPT_TILE_TRIS = 2,    /* triangles per tile of the tiled assembler,
+                                 32..4096; 0 (default): 512, the paper's patch
+                                 size, lowered for small meshes to about nT /
+                                 304 (two tiles per SM), never below 32 */
     ADM_OPT_BLOCK_THREADS = 3,/* threads per block of the element kernels       */
     ADM_OPT_PROFILE = 4,      /* > 0: record CUDA events around every kernel of
                                  each evaluation, on the evaluation's stream,
@@ -137,9 +145,17 @@ adm_status adm_create_batch(const double *V, const int64_t *v_off, const int32_t
                             const int64_t *f_off, int32_t n_mesh, int32_t var_dim,
                             adm_handle *out);
 
+/* Inertial target xhat of ADM_MASS_SPRING (x^n + h v^n of the time step;
+ * host, n_rows * 3 doubles, copied into library memory in both precisions).
+ * Until it is set the target is the rest shape.  Errors: ADM_ERR_ARG
+ * (NULL, non-finite entries), ADM_ERR_UNSUPPORTED (var_dim != 3). */
+adm_status adm_set_inertia_target(adm_handle h, const double *xhat_host);
+
 /* Material parameters of an energy (host array, copied).  Membranes
  * (ADM_STVK_MEMBRANE, ADM_NH_MEMBRANE, ADM_MLP_MEMBRANE): {E, nu, thickness};
- * ADM_HINGE_BENDING: {k_b, h}; ADM_SHELL: {E, nu, thickness, k_b, h}.
+ * ADM_HINGE_BENDING: {k_b, h}; ADM_SHELL: {E, nu, thickness, k_b, h};
+ * ADM_MASS_SPRING: {k, h, rho, g_x, g_y, g_z} (spring stiffness, time step,
+ * areal density, gravity; defaults 1e4, 1/60, 1, (0, 0, -9.81)).
  * Missing trailing values keep their defaults E = 1e5, nu = 0.3,
  * thickness = 1e-3, h = 1, k_b = E t^3 / (12 (1 - nu^2)).  Lame parameters
  * are the plane-stress ones, mu = E / (2 (1 + nu)), lambda = E nu / (1 - nu^2). */
@@ -182,6 +198,17 @@ adm_status adm_slot_map(adm_handle h, adm_energy energy, const int32_t **slots_d
  * Errors: ADM_ERR_ARG, ADM_ERR_UNSUPPORTED, ADM_ERR_CUDA (launch). */
 adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
                     double *energy_dev, void *grad_dev, void *bsr_vals_dev, void *stream);
+
+/* Hessian filtering (Sec. 7.1, after Teran et al. 2005): with enable = 1,
+ * every element term's local Hessian has its negative eigenvalues set to eps
+ * (>= 0, finite) before assembly, in adm_eval, adm_eval_batch(_host) and
+ * adm_eval_hvp; energies and gradients are unchanged.  For the shell the
+ * membrane triangle and the hinge are separate terms.  The filtered passes
+ * run on the tiled kernel whatever ADM_OPT_ASSEMBLER says.  Clamping acts on
+ * the spectrum of the term as a function of its vertex positions; the three
+ * translations, exact zeros of every term here, are left alone.  Errors:
+ * ADM_ERR_ARG.  Drops captured graphs when the setting changes. */
+adm_status adm_set_projection(adm_handle h, int32_t enable, double eps);
 
 /* Matrix-free Hessian-vector product (the paper's matrix-free mode,
  * Sec. 5.5 and Sec. 6.2, which its Newton-CG parameterisation of Sec. 7.2

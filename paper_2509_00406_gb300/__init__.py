@@ -24,6 +24,7 @@ HEADER = os.path.join(ROOT, "include", "adm.h")
 # adm_energy
 SYMDIR2D, STVK_MEMBRANE, HINGE_BENDING, SHELL, NH_MEMBRANE, MLP_MEMBRANE, AREA = 1, 2, 3, 4, 5, 6, 7
 ARAP2D_RESIDUAL = 16
+MASS_SPRING = 8
 # adm_precision
 FP64, FP32 = 0, 1
 # adm_option
@@ -71,6 +72,8 @@ def lib():
         "adm_slot_map": (i32, [vp, i32, pp, C.POINTER(i64)]),
         "adm_eval": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_eval_hvp": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
+        "adm_set_projection": (i32, [vp, i32, C.c_double]),
+        "adm_set_inertia_target": (i32, [vp, vp]),
         "adm_eval_batch": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "adm_eval_batch_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_eval_jacobian": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
@@ -204,6 +207,15 @@ class Mesh:
     def eval(self, energy: int, prec: int, x, energy_out=None, grad=None, bsr=None, stream=None):
         _check(lib().adm_eval(self._h, energy, prec, _ptr(x), _ptr(energy_out), _ptr(grad), _ptr(bsr),
                               _stream(stream)), "adm_eval")
+
+    def set_inertia_target(self, xhat):
+        """Inertial target of the mass-spring energy (host, (nV, 3), copied)."""
+        xhat = np.ascontiguousarray(xhat, dtype=np.float64)
+        _check(lib().adm_set_inertia_target(self._h, _ptr(xhat)), "adm_set_inertia_target")
+
+    def set_projection(self, enable: bool, eps: float = 0.0):
+        """Hessian filtering: negative local eigenvalues set to eps before assembly."""
+        _check(lib().adm_set_projection(self._h, int(bool(enable)), float(eps)), "adm_set_projection")
 
     def eval_hvp(self, energy: int, prec: int, x, v, hv, energy_out=None, grad=None, stream=None):
         """Matrix-free H(x) v into hv (with the energy and, optionally, the gradient)."""

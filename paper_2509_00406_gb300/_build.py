@@ -20,6 +20,11 @@ INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu", "noalloc.cu", "mlp.cu",
            "mesh.cpp", "tiles.cpp", "api.cpp"]
+# tiled-kernel variant groups, each tiled_inst.cu compiled with its own defines
+# (object name, defines): sets 0-4 = passive+gradient, Hessian, filtered
+# Hessian, matrix-free product, filtered matrix-free product
+VARIANT_UNITS = [(f"tiled_{t}_{k}", [f"-DADM_INST_T={ty}", f"-DADM_INST_SET={k}"])
+                 for t, ty in (("f32", "float"), ("f64", "double")) for k in range(5)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++20", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
           "--expt-relaxed-constexpr"]
@@ -45,7 +50,7 @@ def _digest() -> str:
 
 # sources of the tiled FP32 kernel; a change to any of them (or to the flags)
 # invalidates ncu counters recorded for that kernel
-TILED_KERNEL_SOURCES = ["ad.cuh", "terms.cuh", "device_common.cuh", "tiled_impl.cuh", "tiled_f32.cu"]
+TILED_KERNEL_SOURCES = ["ad.cuh", "spd.cuh", "terms.cuh", "device_common.cuh", "tiled_impl.cuh", "tiled_inst.cu"]
 
 
 def kernel_digest(files=None) -> str:
@@ -67,13 +72,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(OUT, src + ".o")
-        cmd = [nvcc, *ARCH, *COMMON, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit) -> str:
+        src, name, defs = (unit, unit, []) if isinstance(unit, str) else ("tiled_inst.cu", unit[0], unit[1])
+        obj = os.path.join(OUT, name + ".o")
+        cmd = [nvcc, *ARCH, *COMMON, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
-        with open(os.path.join(OUT, src + ".log"), "w") as f:
+        with open(os.path.join(OUT, name + ".log"), "w") as f:
             f.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr[-6000:]}")
@@ -81,8 +87,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    units = SOURCES + VARIANT_UNITS
+    with cf.ThreadPoolExecutor(len(units)) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lpthread"],
                        capture_output=True, text=True)

@@ -132,11 +132,22 @@ adm_status ensure_shell(adm_ctx *h)
     return build_pattern(h, PAT_SHELL);
 }
 
+// triangles per tile: the option, else 512 (the paper's default patch size,
+// Sec. 7.1) shrunk for small meshes so that there are about two tiles per SM
+// of the 152, never below 32
+int tile_tris_for(const adm_ctx *h)
+{
+    if (h->tile_tris > 0) return h->tile_tris;
+    const int64_t per = h->m.nT / (2 * 152);
+    return (int)std::min<int64_t>(512, std::max<int64_t>(32, per));
+}
+
 // device arrays of a tile set (freed before a rebuild)
 void free_tiles(adm_ctx *h, TileSet &ts)
 {
     void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_meta, ts.d_meta_off, ts.d_tri_loc, ts.d_hinge_loc, ts.d_tri_perm,
-                    ts.d_zero_blocks, ts.d_zero_verts, ts.d_mesh_tile_off, ts.d_tri_rest[0],
+                    ts.d_cloth_hdr, ts.d_edge_loc, ts.d_vert_loc, ts.d_edge_l2[0], ts.d_edge_l2[1],
+                    ts.d_vert_area3[0], ts.d_vert_area3[1], ts.d_zero_blocks, ts.d_zero_verts, ts.d_mesh_tile_off, ts.d_tri_rest[0],
                     ts.d_tri_rest[1], ts.d_hinge_rest[0], ts.d_hinge_rest[1]};
     for (void *p : ptrs) dev_free(h, p);
     ts = TileSet();
@@ -153,7 +164,7 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
     }
     adm_status s = build_pattern(h, kind);
     if (s != ADM_OK) return s;
-    s = tiles_build(h->m, h->pat[kind], kind == PAT_SHELL, h->tile_tris, ts);
+    s = tiles_build(h->m, h->pat[kind], kind == PAT_SHELL, tile_tris_for(h), ts);
     if (s != ADM_OK) {
         ts = TileSet();
         return s;
@@ -209,12 +220,33 @@ bool energy_ok(int energy, int vdim)
     case ADM_SHELL:
     case ADM_NH_MEMBRANE:
     case ADM_MLP_MEMBRANE:
-    case ADM_AREA: return vdim == 3;
+    case ADM_AREA:
+    case ADM_MASS_SPRING: return vdim == 3;
     default: return false;
     }
 }
 
 bool needs_hinges(int energy) { return energy == ADM_HINGE_BENDING || energy == ADM_SHELL; }
+
+// upload the tile set's mass-spring lists (once) and the default inertial
+// target (the rest shape) if none was set
+adm_status ensure_cloth(adm_ctx *h)
+{
+    TileSet &ts = h->tiles[PAT_TRI];
+    adm_status s = ADM_OK;
+    if (!ts.cloth_built) {
+        if ((s = tiles_build_cloth(h->m, ts)) != ADM_OK) return s;
+        auto up = [&](auto **dst, const auto &v) { return upload(h, dst, v.data(), v.size() * sizeof(v[0])); };
+        if ((s = up(&ts.d_cloth_hdr, ts.cloth_hdr)) != ADM_OK) return s;
+        if ((s = up(&ts.d_edge_loc, ts.edge_loc)) != ADM_OK) return s;
+        if ((s = up(&ts.d_vert_loc, ts.vert_loc)) != ADM_OK) return s;
+        std::vector<std::vector<double>> fe{ts.edge_l2}, fv{ts.vert_area3};
+        if ((s = upload_rest(h, ts.d_edge_l2, fe, (int64_t)ts.edge_l2.size())) != ADM_OK) return s;
+        if ((s = upload_rest(h, ts.d_vert_area3, fv, (int64_t)ts.vert_area3.size())) != ADM_OK) return s;
+    }
+    if (!h->d_xhat[ADM_FP64]) return adm_set_inertia_target(h, h->m.V.data());
+    return ADM_OK;
+}
 
 // tiles are built for the tiled assembler, and for the matrix-free product
 // (which only the tiled kernel implements) whatever the assembler option
@@ -223,8 +255,11 @@ adm_status prepare(adm_ctx *h, int energy, bool need_tiles = false)
     if (!energy_ok(energy, h->m.vdim)) return ADM_ERR_UNSUPPORTED;
     adm_status s = needs_hinges(energy) ? ensure_shell(h) : build_pattern(h, PAT_TRI);
     if (energy == ADM_MLP_MEMBRANE && h->assembler != 0) return ADM_ERR_UNSUPPORTED;
-    if (s != ADM_OK || (h->assembler != 0 && !need_tiles) || energy == ADM_ARAP2D_RESIDUAL) return s;
+    const bool cloth = energy == ADM_MASS_SPRING;
+    if (s != ADM_OK || (h->assembler != 0 && !need_tiles && !h->proj && !cloth) || energy == ADM_ARAP2D_RESIDUAL)
+        return s;
     s = ensure_tiles(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
+    if (s == ADM_OK && cloth) s = ensure_cloth(h);
     if (s == ADM_OK && energy == ADM_MLP_MEMBRANE && !h->d_mlp_table)
         s = dev_alloc(h, &h->d_mlp_table, (size_t)h->m.nT * 10 * sizeof(float));
     return s;
@@ -400,6 +435,13 @@ adm_status adm_set_params(adm_handle h, adm_energy energy, const double *p, int3
         if (np > 2) q.t = p[2];
         if (np > 3) q.kb = p[3];
         if (np > 4) q.h = p[4];
+    } else if (energy == ADM_MASS_SPRING) {
+        if (np > 6) return ADM_ERR_ARG;
+        double *dst[6] = {&q.k, &q.dt, &q.rho, &q.g[0], &q.g[1], &q.g[2]};
+        for (int i = 0; i < np; ++i) {
+            if (!std::isfinite(p[i])) return ADM_ERR_ARG;
+            *dst[i] = p[i];
+        }
     } else if (np != 0) {
         return ADM_ERR_ARG;
     }
@@ -422,7 +464,7 @@ adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
         h->assembler = (int)value;
         return ADM_OK;
     case ADM_OPT_TILE_TRIS:
-        if (value < 32 || value > 4096) return ADM_ERR_ARG;
+        if (value != 0 && (value < 32 || value > 4096)) return ADM_ERR_ARG;
         if (value != h->tile_tris)
             for (auto &ts : h->tiles) ts.built = false;  // rebuilt on next use
         h->tile_tris = (int)value;
@@ -571,6 +613,30 @@ adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const v
     a.gnorm_per_mesh = nullptr;
     a.stream = as_stream(stream);
     return run_pass(h, a);
+}
+
+adm_status adm_set_inertia_target(adm_handle h, const double *xhat_host)
+{
+    if (!h || !xhat_host) return ADM_ERR_ARG;
+    if (h->m.vdim != 3) return ADM_ERR_UNSUPPORTED;
+    const int64_t n = h->m.nV * 3;
+    std::vector<std::vector<double>> f(1, std::vector<double>(xhat_host, xhat_host + n));  // vertex-major like x
+    for (double v : f[0])
+        if (!std::isfinite(v)) return ADM_ERR_ARG;
+    dev_free(h, h->d_xhat[0]);
+    dev_free(h, h->d_xhat[1]);
+    h->d_xhat[0] = h->d_xhat[1] = nullptr;
+    drop_graphs(h);
+    return upload_rest(h, h->d_xhat, f, n);
+}
+
+adm_status adm_set_projection(adm_handle h, int32_t enable, double eps)
+{
+    if (!h || (enable != 0 && enable != 1) || !(eps >= 0.0) || !std::isfinite(eps)) return ADM_ERR_ARG;
+    if (h->proj != enable || h->proj_eps != eps) drop_graphs(h);
+    h->proj = enable;
+    h->proj_eps = eps;
+    return ADM_OK;
 }
 
 adm_status adm_eval_hvp(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev, const void *v_dev,

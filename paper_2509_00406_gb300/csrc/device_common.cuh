@@ -22,6 +22,8 @@ enum Mode { MODE_VALUE = 0, MODE_GRAD = 1, MODE_HESS = 2, MODE_HVP = 3 };
 template <typename T>
 struct TermConsts {
     T mu, lam, thick, kbh2;
+    T eps;  // Hessian filtering: value negative local eigenvalues are raised to
+    T kh2, h2, rho, g[3];  // mass-spring: k h^2, h^2, areal density, gravity
 };
 
 // deterministic block sum of one double per thread (fixed tree order)
@@ -86,23 +88,24 @@ struct TriTraits {
 };
 
 // local f, g, H of one triangle term; false outside the energy's domain
-template <typename T, int ENERGY>
+// (PROJ: with the local Hessian filtered, spd.cuh)
+template <typename T, int ENERGY, bool PROJ = false>
 __device__ __forceinline__ bool tri_term(const T (&x)[TriTraits<ENERGY>::K], const T (&D)[4], T area,
                                          const TermConsts<T> &c, Local<T, TriTraits<ENERGY>::K> &L,
                                          const float *tab = nullptr)
 {
     bool ok = true;
     if constexpr (ENERGY == ADM_SYMDIR2D) {
-        T det = uv_local(x, D, PsiSymDir<T>{area}, L);
+        T det = uv_local<T, PsiSymDir<T>, PROJ>(x, D, PsiSymDir<T>{area}, L, c.eps);
         ok = det > T(0);
     } else if constexpr (ENERGY == ADM_STVK_MEMBRANE || ENERGY == ADM_SHELL) {
-        membrane_local(x, D, PsiStVK<T>{c.mu, c.lam, c.thick * area}, L);
+        membrane_local<T, PsiStVK<T>, PROJ>(x, D, PsiStVK<T>{c.mu, c.lam, c.thick * area}, L, c.eps);
     } else if constexpr (ENERGY == ADM_NH_MEMBRANE) {
-        membrane_local(x, D, PsiNH<T>{c.mu, c.lam, c.thick * area}, L);
+        membrane_local<T, PsiNH<T>, PROJ>(x, D, PsiNH<T>{c.mu, c.lam, c.thick * area}, L, c.eps);
     } else if constexpr (ENERGY == ADM_AREA) {
-        area_local(x, L);
+        area_local<T, PROJ>(x, L, c.eps);
     } else if constexpr (ENERGY == ADM_MLP_MEMBRANE) {
-        membrane_local(x, D, PsiTable<T>{tab, c.thick * area}, L);
+        membrane_local<T, PsiTable<T>, PROJ>(x, D, PsiTable<T>{tab, c.thick * area}, L, c.eps);
     }
     return ok && isfinite(L.f);
 }
@@ -125,6 +128,11 @@ inline TermConsts<T> consts(const adm_ctx *h, int energy)
     c.lam = (T)p.lambda();
     c.thick = (T)p.t;
     c.kbh2 = (T)(p.kbend() * p.h * p.h);
+    c.eps = (T)h->proj_eps;
+    c.kh2 = (T)(p.k * p.dt * p.dt);
+    c.h2 = (T)(p.dt * p.dt);
+    c.rho = (T)p.rho;
+    for (int d = 0; d < 3; ++d) c.g[d] = (T)p.g[d];
     return c;
 }
 

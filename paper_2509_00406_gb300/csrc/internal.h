@@ -100,6 +100,18 @@ struct TileSet {
     std::vector<int32_t> zero_blocks;    // shared blocks, zeroed before a pass
     std::vector<int32_t> zero_verts;     // shared gradient rows
     std::vector<int32_t> mesh_tile_off;  // n_mesh + 1
+    // mass-spring cloth (tiles_build_cloth, triangle tile sets only): every
+    // edge and vertex owned by the lowest-indexed tile whose footprint has it
+    bool cloth_built = false;
+    std::vector<int32_t> cloth_hdr;      // 4 per tile: edge begin/count, vertex begin/count
+    std::vector<uint16_t> edge_loc;      // 3 per edge (tile order): 2 local ids, pair slot
+    std::vector<uint16_t> vert_loc;      // 1 per vertex (tile order): local id
+    std::vector<double> edge_l2;         // squared rest length per edge (tile order)
+    std::vector<double> vert_area3;      // a third of the rest area around each vertex (tile order)
+    int32_t *d_cloth_hdr = nullptr;
+    uint16_t *d_edge_loc = nullptr, *d_vert_loc = nullptr;
+    void *d_edge_l2[2] = {nullptr, nullptr};
+    void *d_vert_area3[2] = {nullptr, nullptr};
     std::vector<unsigned char> meta;     // per tile: row starts, row code offsets, codes (16-byte padded)
     std::vector<int64_t> meta_off;       // n_tiles + 1 byte offsets into meta
     // device copies
@@ -115,6 +127,8 @@ struct TileSet {
 
 struct EnergyParams {
     double E = 1.0e5, nu = 0.3, t = 1.0e-3, kb = -1.0, h = 1.0;
+    // mass-spring cloth: stiffness, time step, areal density, gravity
+    double k = 1.0e4, dt = 1.0 / 60.0, rho = 1.0, g[3] = {0.0, 0.0, -9.81};
     double mu() const { return E / (2.0 * (1.0 + nu)); }
     double lambda() const { return E * nu / (1.0 - nu * nu); }
     double kbend() const { return kb >= 0.0 ? kb : E * t * t * t / (12.0 * (1.0 - nu * nu)); }
@@ -160,7 +174,10 @@ struct adm_ctx {
     std::map<int, adm::EnergyParams> params;
     // options
     int assembler = 0;
-    int tile_tris = 512;
+    void *d_xhat[2] = {nullptr, nullptr};  // mass-spring inertial target, per precision (null: rest shape)
+    int proj = 0;            // per-term Hessian filtering on (adm_set_projection)
+    double proj_eps = 0.0;   // value negative local eigenvalues are raised to
+    int tile_tris = 0;  // 0: automatic (tile_tris_for)
     int block_threads = 128;
     // host-buffer path
     void *d_stage_x = nullptr, *d_stage_grad = nullptr, *d_stage_bsr = nullptr;
@@ -197,6 +214,8 @@ void mesh_build_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr,
 
 // tiles.cpp
 adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_tris, TileSet &ts);
+// per-tile edge and vertex lists of the mass-spring energy, on a triangle tile set
+adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts);
 // bytes of a tile's metadata blob, and of its dynamic shared memory
 int64_t tile_meta_bytes(int64_t nf, int64_t ncodes);
 int64_t tile_smem_bytes(int elem_bytes, int64_t units, int64_t nf, int64_t ncodes);

@@ -17,6 +17,7 @@
 #pragma once
 
 #include "ad.cuh"
+#include "spd.cuh"
 
 namespace adm {
 
@@ -141,6 +142,12 @@ static_assert(HingeEdges::C(0, 0) == -1 && HingeEdges::C(0, 1) == -1 && HingeEdg
               HingeEdges::C(2, 0) == 0 && HingeEdges::C(2, 1) == 1 && HingeEdges::C(2, 2) == 0 &&
               HingeEdges::C(3, 0) == 0 && HingeEdges::C(3, 1) == 0 && HingeEdges::C(3, 2) == 1, "hinge edge map");
 
+struct SpringEdges {  // d = x0 - x1: C = {{1}, {-1}}
+    static constexpr int NV = 2, NE = 1;
+    ADM_HD static constexpr int C(int a, int p) { return edge_coef(0x9u, a * NE + p); }
+};
+static_assert(SpringEdges::C(0, 0) == 1 && SpringEdges::C(1, 0) == -1, "spring edge map");
+
 template <class E, int VD, typename T>
 ADM_HD void expand_edges(const Local<T, E::NE * VD> &le, Local<T, E::NV * VD> &out)
 {
@@ -180,8 +187,8 @@ ADM_HD void expand_edges(const Local<T, E::NE * VD> &le, Local<T, E::NV * VD> &o
 // ------------------------------------------------------ triangle, VD = 3 --
 // C = F^T F of F = [x1-x0, x2-x0] Dinv;  Dinv row-major (d00, d01, d10, d11).
 // Differentiated in the edge vectors u = x1 - x0, w = x2 - x0.
-template <typename T, class Psi>
-ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Local<T, 9> &out)
+template <typename T, class Psi, bool PROJ = false>
+ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Local<T, 9> &out, T eps = T(0))
 {
     auto u0 = seed<T, 6, 0>(x[3] - x[0]);
     auto u1 = seed<T, 6, 1>(x[4] - x[1]);
@@ -201,12 +208,13 @@ ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Loc
     auto p = psi(seed<T, 3, 0>(c11.v), seed<T, 3, 1>(c22.v), seed<T, 3, 2>(c12.v));
     Local<T, 6> le;
     store_local(compose(p, c11, c22, c12), le);
+    if constexpr (PROJ) project_edges<TriEdges, 3>(le.H, eps);
     expand_edges<TriEdges, 3>(le, out);
 }
 
 // area term (test energy of Sec. 7.6), in the edge vectors u, w
-template <typename T>
-ADM_HD void area_local(const T (&x)[9], Local<T, 9> &out)
+template <typename T, bool PROJ = false>
+ADM_HD void area_local(const T (&x)[9], Local<T, 9> &out, T eps = T(0))
 {
     auto u0 = seed<T, 6, 0>(x[3] - x[0]);
     auto u1 = seed<T, 6, 1>(x[4] - x[1]);
@@ -220,14 +228,15 @@ ADM_HD void area_local(const T (&x)[9], Local<T, 9> &out)
     auto p = PsiArea<T>{}(seed<T, 3, 0>(uu.v), seed<T, 3, 1>(ww.v), seed<T, 3, 2>(uw.v));
     Local<T, 6> le;
     store_local(compose(p, uu, ww, uw), le);
+    if constexpr (PROJ) project_edges<TriEdges, 3>(le.H, eps);
     expand_edges<TriEdges, 3>(le, out);
 }
 
 // ------------------------------------------------------ triangle, VD = 2 --
 // C = J^T J of the UV Jacobian J = [b-a, c-a] Dinv, differentiated in the
 // edge vectors b - a, c - a; returns det J (value)
-template <typename T, class Psi>
-ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> &out)
+template <typename T, class Psi, bool PROJ = false>
+ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> &out, T eps = T(0))
 {
     auto u0 = seed<T, 4, 0>(x[2] - x[0]);  // b - a
     auto u1 = seed<T, 4, 1>(x[3] - x[1]);
@@ -243,6 +252,7 @@ ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> 
     auto p = psi(seed<T, 3, 0>(c11.v), seed<T, 3, 1>(c22.v), seed<T, 3, 2>(c12.v));
     Local<T, 4> le;
     store_local(compose(p, c11, c22, c12), le);
+    if constexpr (PROJ) project_edges<TriEdges, 2>(le.H, eps);
     expand_edges<TriEdges, 2>(le, out);
     return j00.v * j11.v - j01.v * j10.v;
 }
@@ -251,8 +261,8 @@ ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> 
 // hinge (x0, x1, xa, xb), face A = (x0, x1, xa), face B = (x1, x0, xb);
 // psi = w (theta - thetabar)^2, differentiated in the edge vectors e, u, v.
 // Returns false for a degenerate hinge.
-template <typename T>
-ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out)
+template <typename T, bool PROJ = false>
+ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out, T eps = T(0))
 {
     auto e0 = seed<T, 9, 0>(x[3] - x[0]);  // e = x1 - x0
     auto e1 = seed<T, 9, 1>(x[4] - x[1]);
@@ -280,8 +290,41 @@ ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out)
     auto p = sq(th - thetabar) * w;
     Local<T, 9> le;
     store_local(compose(p, ee, eu, ev, uv, det), le);
+    if constexpr (PROJ) project_edges<HingeEdges, 3>(le.H, eps);
     expand_edges<HingeEdges, 3>(le, out);
     return true;
+}
+
+// ------------------------------------------------- mass-spring (Sec. 7.1) --
+// spring of edge (x0, x1), squared rest length l2, times h^2:
+// kh2 l2/2 (|d|^2 / l2 - 1)^2 = kh2 / (2 l2) (|d|^2 - l2)^2, d = x0 - x1,
+// differentiated in d
+template <typename T, bool PROJ = false>
+ADM_HD void spring_local(const T (&x)[6], T l2, T kh2, Local<T, 6> &out, T eps = T(0))
+{
+    auto d0 = seed<T, 3, 0>(x[0] - x[3]);
+    auto d1 = seed<T, 3, 1>(x[1] - x[4]);
+    auto d2 = seed<T, 3, 2>(x[2] - x[5]);
+    auto q = sq(d0) + sq(d1) + sq(d2);
+    auto Q = seed<T, 1, 0>(q.v);
+    auto p = sq(Q - l2) * (kh2 / (T(2) * l2));
+    Local<T, 3> le;
+    store_local(compose(p, q), le);
+    if constexpr (PROJ) project_edges<SpringEdges, 3>(le.H, eps);
+    expand_edges<SpringEdges, 3>(le, out);
+}
+
+// per-vertex inertia and gravity: m/2 |x - xhat|^2 - h2 m g.x (Hessian m I,
+// semidefinite, so filtering never changes it)
+template <typename T>
+ADM_HD void vertex_local(const T (&x)[3], const T (&xh)[3], T m, T h2, const T (&g)[3], Local<T, 3> &out)
+{
+    auto X0 = seed<T, 3, 0>(x[0]);
+    auto X1 = seed<T, 3, 1>(x[1]);
+    auto X2 = seed<T, 3, 2>(x[2]);
+    auto f = (sq(X0 - xh[0]) + sq(X1 - xh[1]) + sq(X2 - xh[2])) * (T(0.5) * m) -
+             (X0 * g[0] + X1 * g[1] + X2 * g[2]) * (h2 * m);
+    store_local(f, out);
 }
 
 // --------------------------------------------- ARAP-style residual (Eq. 3) --

@@ -30,6 +30,12 @@ struct TiledArgs {
     int *status;
     TermConsts<T> c;
     const float *mlp_table;           // learned membrane: 10 per triangle, tile order
+    // mass-spring: per tile {edge begin, count, vertex begin, count}; per edge
+    // 2 local ids + pair slot and squared rest length; per vertex its local id
+    // and a third of the rest area around it; the inertial target (like x)
+    const int32_t *cloth_hdr;
+    const uint16_t *edge_loc, *vert_loc;
+    const T *edge_l2, *vert_area3, *xhat;
 };
 
 template <typename T, int VD, int NV, int NP, int K>
@@ -85,9 +91,10 @@ __device__ __forceinline__ void tile_hvp(const Local<T, K> &L, const uint16_t (&
 }
 
 // FP32 tiles are register-capped at two resident blocks per SM (128 registers
-// for 256 threads); FP64 keeps one block and the full register file
-template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(TiledArgs<T> A)
+// for 256 threads); FP64, and the Hessian-filtering variant (PROJ: an
+// in-register eigensolve per element), keep one block and the full register file
+template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS, bool PROJ = false>
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_tiled(TiledArgs<T> A)
 {
     constexpr int VD = TriTraits<ENERGY>::VD;
     constexpr int K = 3 * VD;
@@ -153,7 +160,7 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
             for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nT + e];
             const T area = A.tri_rest[4 * A.nT + e];
             Local<T, K> L;
-            if (!tri_term<T, ENERGY>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * e : nullptr)) {
+            if (!tri_term<T, ENERGY, PROJ>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * e : nullptr)) {
                 atomicOr(A.status, ST_DOMAIN);
                 continue;
             }
@@ -179,13 +186,60 @@ __global__ void __launch_bounds__(THREADS, sizeof(T) == 4 ? 2 : 1) k_tiled(Tiled
             const T thetabar = A.hinge_rest[e];
             const T w = A.c.kbh2 * A.hinge_rest[A.nH + e];
             Local<T, 12> L;
-            if (!(hinge_local(x, thetabar, w, L) && isfinite(L.f))) {
+            if (!(hinge_local<T, PROJ>(x, thetabar, w, L, A.c.eps) && isfinite(L.f))) {
                 atomicOr(A.status, ST_DOMAIN);
                 continue;
             }
             fe += (double)L.f;
             if (MODE == MODE_HVP) tile_hvp<T, 3, 4, 12>(L, lid, vs, gacc, hacc);
             else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 4, 6, 12>(L, lid, slot, HP, gacc, dacc, pacc, MODE);
+        }
+    }
+    if constexpr (ENERGY == ADM_MASS_SPRING) {
+        static constexpr int EP[1][2] = {{0, 1}};
+        const int32_t *ch = A.cloth_hdr + 4 * t;
+        const int32_t edge_begin = ch[0], n_edge = ch[1], vert_begin = ch[2], n_vert = ch[3];
+        for (int i = threadIdx.x; i < n_edge; i += THREADS) {
+            const int64_t e = (int64_t)edge_begin + i;
+            const uint16_t lid[2] = {A.edge_loc[3 * e], A.edge_loc[3 * e + 1]};
+            const uint16_t slot[1] = {A.edge_loc[3 * e + 2]};
+            T x[6];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) x[a * 3 + d] = xs[lid[a] * 3 + d];
+            Local<T, 6> L;
+            spring_local<T, PROJ>(x, A.edge_l2[e], A.c.kh2, L, A.c.eps);
+            if (!isfinite(L.f)) {
+                atomicOr(A.status, ST_DOMAIN);
+                continue;
+            }
+            fe += (double)L.f;
+            if (MODE == MODE_HVP) tile_hvp<T, 3, 2, 6>(L, lid, vs, gacc, hacc);
+            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 2, 1, 6>(L, lid, slot, EP, gacc, dacc, pacc, MODE);
+        }
+        for (int i = threadIdx.x; i < n_vert; i += THREADS) {
+            const int64_t e = (int64_t)vert_begin + i;
+            const uint16_t lid[1] = {A.vert_loc[e]};
+            const int64_t v = A.foot[foot_begin + lid[0]];
+            T x[3], xh[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                x[d] = xs[lid[0] * 3 + d];
+                xh[d] = A.xhat[v * 3 + d];
+            }
+            Local<T, 3> L;
+            vertex_local(x, xh, A.c.rho * A.vert_area3[e], A.c.h2, A.c.g, L);
+            fe += (double)L.f;
+            if (MODE == MODE_HVP) {
+                tile_hvp<T, 3, 1, 3>(L, lid, vs, gacc, hacc);
+            } else if (MODE >= MODE_GRAD) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) atomicAdd(gacc + lid[0] * 3 + d, L.g[d]);
+                if (MODE == MODE_HESS)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) atomicAdd(dacc + lid[0] * ND + hix(d, d), L.H[hix(d, d)]);
+            }
         }
     }
     __syncthreads();
@@ -271,36 +325,49 @@ __global__ void k_zero_shared(const int32_t *blocks, int64_t nb, const int32_t *
         for (int64_t i = i0; i < nv * VD; i += stride) hv[(int64_t)verts[i / VD] * VD + i % VD] = T(0);
 }
 
-template <typename T, int ENERGY, bool TRIS, bool HINGES>
-static void launch_tiled_modes(int mode, int n_tiles, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
+// Launch of one (precision, mode, filtering) variant for any energy.  Each
+// variant is instantiated in its own translation unit (tiled_inst.cu) so
+// that they compile in parallel.
+template <typename T, int MODE, bool PROJ>
+void launch_tiled_mode(int energy, int n_tiles, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
 {
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<n_tiles, kTileThreads, smem, s>>>(A);
     };
-    if (mode == MODE_VALUE) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_VALUE, kTileThreads>);
-    else if (mode == MODE_GRAD) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_GRAD, kTileThreads>);
-    else if (mode == MODE_HESS) go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_HESS, kTileThreads>);
-    else go(k_tiled<T, ENERGY, TRIS, HINGES, MODE_HVP, kTileThreads>);
-}
-
-template <typename T>
-static void launch_tiled(int energy, int mode, int n_tiles, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
-{
     switch (energy) {
-    case ADM_SYMDIR2D: launch_tiled_modes<T, ADM_SYMDIR2D, true, false>(mode, n_tiles, smem, s, A); break;
-    case ADM_STVK_MEMBRANE: launch_tiled_modes<T, ADM_STVK_MEMBRANE, true, false>(mode, n_tiles, smem, s, A); break;
-    case ADM_NH_MEMBRANE: launch_tiled_modes<T, ADM_NH_MEMBRANE, true, false>(mode, n_tiles, smem, s, A); break;
-    case ADM_AREA: launch_tiled_modes<T, ADM_AREA, true, false>(mode, n_tiles, smem, s, A); break;
+    case ADM_SYMDIR2D: go(k_tiled<T, ADM_SYMDIR2D, true, false, MODE, kTileThreads, PROJ>); break;
+    case ADM_STVK_MEMBRANE: go(k_tiled<T, ADM_STVK_MEMBRANE, true, false, MODE, kTileThreads, PROJ>); break;
+    case ADM_NH_MEMBRANE: go(k_tiled<T, ADM_NH_MEMBRANE, true, false, MODE, kTileThreads, PROJ>); break;
+    case ADM_AREA: go(k_tiled<T, ADM_AREA, true, false, MODE, kTileThreads, PROJ>); break;
     case ADM_MLP_MEMBRANE:
-        if constexpr (sizeof(T) == 4) launch_tiled_modes<T, ADM_MLP_MEMBRANE, true, false>(mode, n_tiles, smem, s, A);
+        if constexpr (sizeof(T) == 4) go(k_tiled<T, ADM_MLP_MEMBRANE, true, false, MODE, kTileThreads, PROJ>);
         break;
-    case ADM_SHELL: launch_tiled_modes<T, ADM_SHELL, true, true>(mode, n_tiles, smem, s, A); break;
-    case ADM_HINGE_BENDING:
-        launch_tiled_modes<T, ADM_STVK_MEMBRANE, false, true>(mode, n_tiles, smem, s, A);
-        break;
+    case ADM_SHELL: go(k_tiled<T, ADM_SHELL, true, true, MODE, kTileThreads, PROJ>); break;
+    case ADM_HINGE_BENDING: go(k_tiled<T, ADM_STVK_MEMBRANE, false, true, MODE, kTileThreads, PROJ>); break;
+    case ADM_MASS_SPRING: go(k_tiled<T, ADM_MASS_SPRING, false, false, MODE, kTileThreads, PROJ>); break;
     default: break;
     }
+}
+
+#define ADM_TILED_VARIANTS(X, T)                                                                          \
+    X(T, MODE_VALUE, false) X(T, MODE_GRAD, false) X(T, MODE_HESS, false) X(T, MODE_HESS, true)           \
+    X(T, MODE_HVP, false) X(T, MODE_HVP, true)
+#define ADM_TILED_EXTERN(T, M, P)                                                                          \
+    extern template void launch_tiled_mode<T, M, P>(int, int, size_t, cudaStream_t, const TiledArgs<T> &);
+#define ADM_TILED_INST(T, M, P) \
+    template void launch_tiled_mode<T, M, P>(int, int, size_t, cudaStream_t, const TiledArgs<T> &);
+
+template <typename T>
+static void launch_tiled(int energy, int mode, bool proj, int n_tiles, size_t smem, cudaStream_t s,
+                         const TiledArgs<T> &A)
+{
+    if (mode == MODE_VALUE) launch_tiled_mode<T, MODE_VALUE, false>(energy, n_tiles, smem, s, A);
+    else if (mode == MODE_GRAD) launch_tiled_mode<T, MODE_GRAD, false>(energy, n_tiles, smem, s, A);
+    else if (mode == MODE_HESS && !proj) launch_tiled_mode<T, MODE_HESS, false>(energy, n_tiles, smem, s, A);
+    else if (mode == MODE_HESS) launch_tiled_mode<T, MODE_HESS, true>(energy, n_tiles, smem, s, A);
+    else if (!proj) launch_tiled_mode<T, MODE_HVP, false>(energy, n_tiles, smem, s, A);
+    else launch_tiled_mode<T, MODE_HVP, true>(energy, n_tiles, smem, s, A);
 }
 
 template <typename T>
@@ -350,6 +417,13 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     A.status = h->d_status;
     A.c = consts<T>(h, a.energy);
     A.mlp_table = nullptr;
+    A.cloth_hdr = ts.d_cloth_hdr;
+    A.edge_loc = ts.d_edge_loc;
+    A.vert_loc = ts.d_vert_loc;
+    A.edge_l2 = (const T *)ts.d_edge_l2[a.prec];
+    A.vert_area3 = (const T *)ts.d_vert_area3[a.prec];
+    A.xhat = (const T *)h->d_xhat[a.prec];
+    if (a.energy == ADM_MASS_SPRING && (!ts.cloth_built || !A.xhat)) return ADM_ERR_UNSUPPORTED;
     if (a.energy == ADM_MLP_MEMBRANE) {
         if (sizeof(T) != 4 || !h->d_mlp_theta || !ts.d_tri_perm) return ADM_ERR_UNSUPPORTED;
         tm.begin(ADM_STAGE_MLP);
@@ -361,7 +435,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
         A.mlp_table = h->d_mlp_table;
     }
     tm.begin(ADM_STAGE_TILED);
-    launch_tiled<T>(a.energy, mode, ts.n_tiles, smem, s, A);
+    launch_tiled<T>(a.energy, mode, h->proj != 0, ts.n_tiles, smem, s, A);
     tm.end(ADM_STAGE_TILED);
     if (cudaGetLastError() != cudaSuccess) return ADM_ERR_CUDA;
     return launch_reduce(h, a, ts.d_mesh_tile_off, nullptr, 0, tm);

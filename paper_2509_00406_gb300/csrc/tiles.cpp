@@ -443,4 +443,95 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     return ADM_OK;
 }
 
+// Mass-spring elements on a built triangle tile set (Sec. 7.1: per-edge
+// springs, per-vertex inertia and gravity).  An edge belongs to the tile of
+// the first triangle (in tile order) that has it, so both its vertices are in
+// that tile's footprint and their pair has a slot there (read from that
+// triangle's record); a vertex belongs to the first tile whose footprint has
+// it.  Both lists are stored interleaved like the triangles.
+adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts)
+{
+    if (!ts.built || ts.n_tiles == 0) return ADM_ERR_ARG;
+    const int32_t n_tiles = ts.n_tiles;
+    struct Cand {
+        uint64_t key;   // lo * nV + hi
+        int64_t pos;    // triangle position in tile order
+        int32_t pair;   // which of its 3 pairs
+    };
+    std::vector<Cand> cand;
+    cand.reserve(3 * (size_t)m.nT);
+    for (int32_t t = 0; t < n_tiles; ++t) {
+        const int32_t *hd = &ts.hdr[8 * (size_t)t];
+        for (int64_t i = hd[0]; i < (int64_t)hd[0] + hd[1]; ++i) {
+            const int32_t *f = &m.F[3 * (int64_t)ts.tri_perm[i]];
+            for (int p = 0; p < 3; ++p) {
+                const int64_t a = f[TP[p][0]], b = f[TP[p][1]];
+                cand.push_back({(uint64_t)std::min(a, b) * (uint64_t)m.nV + (uint64_t)std::max(a, b), i, p});
+            }
+        }
+    }
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.key < y.key; });
+    std::vector<int32_t> tile_of_pos(m.nT);
+    for (int32_t t = 0; t < n_tiles; ++t)
+        for (int64_t i = ts.hdr[8 * (size_t)t]; i < (int64_t)ts.hdr[8 * (size_t)t] + ts.hdr[8 * (size_t)t + 1]; ++i)
+            tile_of_pos[i] = t;
+    std::vector<std::vector<int64_t>> tile_edges(n_tiles);  // index into cand of the owning record
+    for (size_t i = 0; i < cand.size();) {
+        size_t j = i;
+        while (j < cand.size() && cand[j].key == cand[i].key) ++j;
+        tile_edges[tile_of_pos[cand[i].pos]].push_back((int64_t)i);  // first in tile order (stable sort)
+        i = j;
+    }
+    std::vector<char> vseen(m.nV, 0);
+    ts.cloth_hdr.assign(4 * (size_t)n_tiles, 0);
+    ts.edge_loc.clear();
+    ts.vert_loc.clear();
+    ts.edge_l2.clear();
+    ts.vert_area3.clear();
+    std::vector<double> area3(m.nV, 0.0);
+    for (int64_t t = 0; t < m.nT; ++t)
+        for (int c = 0; c < 3; ++c) area3[m.F[3 * t + c]] += m.tri_area[t] / 3.0;
+    for (int32_t t = 0; t < n_tiles; ++t) {
+        const int32_t *hd = &ts.hdr[8 * (size_t)t];
+        const int32_t foot_begin = hd[4], nf = hd[5];
+        // edges, interleaved
+        std::vector<int32_t> ord(tile_edges[t].size()), il(ord.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        interleave32(ord, il.data());
+        ts.cloth_hdr[4 * (size_t)t] = (int32_t)(ts.edge_loc.size() / 3);
+        ts.cloth_hdr[4 * (size_t)t + 1] = (int32_t)ord.size();
+        for (int32_t q : il) {
+            const Cand &c = cand[tile_edges[t][q]];
+            const uint16_t *tl = &ts.tri_loc[6 * c.pos];
+            ts.edge_loc.push_back(tl[TP[c.pair][0]]);
+            ts.edge_loc.push_back(tl[TP[c.pair][1]]);
+            ts.edge_loc.push_back(tl[3 + c.pair]);
+            const int64_t a = ts.foot[foot_begin + tl[TP[c.pair][0]]], b = ts.foot[foot_begin + tl[TP[c.pair][1]]];
+            double l2 = 0.0;
+            for (int d = 0; d < 3; ++d) l2 += (m.V[3 * a + d] - m.V[3 * b + d]) * (m.V[3 * a + d] - m.V[3 * b + d]);
+            if (!(l2 > 0.0)) return ADM_ERR_MESH;
+            ts.edge_l2.push_back(l2);
+        }
+        // vertices first seen in this tile, interleaved
+        std::vector<int32_t> vl;
+        for (int32_t r = 0; r < nf; ++r) {
+            const int32_t v = ts.foot[foot_begin + r];
+            if (!vseen[v]) {
+                vseen[v] = 1;
+                vl.push_back(r);
+            }
+        }
+        std::vector<int32_t> vil(vl.size());
+        interleave32(vl, vil.data());
+        ts.cloth_hdr[4 * (size_t)t + 2] = (int32_t)ts.vert_loc.size();
+        ts.cloth_hdr[4 * (size_t)t + 3] = (int32_t)vil.size();
+        for (int32_t r : vil) {
+            ts.vert_loc.push_back((uint16_t)r);
+            ts.vert_area3.push_back(area3[ts.foot[foot_begin + r]]);
+        }
+    }
+    ts.cloth_built = true;
+    return ADM_OK;
+}
+
 }  // namespace adm
