@@ -85,8 +85,9 @@ struct TileSet {
     int tile_tris = 0;
     int32_t n_tiles = 0;
     // dynamic shared memory of the tiled kernel, [VD == 3][ADM_FP64 = 0 / ADM_FP32 = 1]:
-    // accumulators (VD = 3: 12 per footprint vertex + 9 per pair; VD = 2: 7
-    // and 4) padded to 16 bytes, then the tile's metadata blob
+    // accumulators (VD = 3: 13 per footprint vertex + 9 per pair; VD = 2: 7
+    // and 5; x, gradient, padded diagonal, pair blocks) padded to 16 bytes,
+    // then the tile's metadata blob
     int64_t smem_bytes[2][2] = {{0, 0}, {0, 0}};
     std::vector<int32_t> hdr;            // 8 per tile: tri begin/count, hinge begin/count,
                                          // footprint begin/count, pairs, code begin

@@ -13,6 +13,17 @@ namespace adm {
 // local id) with shared-memory atomics, then write every footprint row of the
 // BSR with row-contiguous stores (plain for blocks only this tile touches,
 // global atomic adds into pre-zeroed shared blocks).
+// shared-memory strides of the accumulators, in elements: a vertex's diagonal
+// block keeps its VD (VD + 1) / 2 upper entries, a pair block its VD^2, each
+// padded to an odd stride (7 for 3x3 diagonals, 5 for 2x2 pairs) so that the
+// same entry of different vertices or pairs maps the slot index mod 32
+// one-to-one onto the 32 banks
+template <int VD>
+struct AccStride {
+    static constexpr int D = VD == 3 ? 7 : 3;
+    static constexpr int P = VD == 3 ? 9 : 5;
+};
+
 template <typename T>
 struct TiledArgs {
     const int32_t *hdr;
@@ -43,7 +54,7 @@ __device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint
                                                 const uint16_t (&slot)[NP], const int (&pr)[NP][2], T *gacc,
                                                 T *dacc, T *pacc, int mode)
 {
-    constexpr int ND = VD * (VD + 1) / 2, NB = VD * VD;
+    constexpr int NDS = AccStride<VD>::D, NPS = AccStride<VD>::P;
     auto H = [&](int i, int j) { return L.H[i <= j ? hix(i, j) : hix(j, i)]; };
 #pragma unroll
     for (int a = 0; a < NV; ++a)
@@ -55,12 +66,12 @@ __device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint
 #pragma unroll
         for (int s = 0; s < VD; ++s)
 #pragma unroll
-            for (int r = 0; r <= s; ++r) atomicAdd(dacc + lid[a] * ND + hix(r, s), H(a * VD + r, a * VD + s));
+            for (int r = 0; r <= s; ++r) atomicAdd(dacc + lid[a] * NDS + hix(r, s), H(a * VD + r, a * VD + s));
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = pr[p][0], b = pr[p][1];
         const bool fwd = lid[a] < lid[b];
-        T *dst = pacc + slot[p] * NB;
+        T *dst = pacc + slot[p] * NPS;
 #pragma unroll
         for (int r = 0; r < VD; ++r)
 #pragma unroll
@@ -98,7 +109,8 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
 {
     constexpr int VD = TriTraits<ENERGY>::VD;
     constexpr int K = 3 * VD;
-    constexpr int ND = VD * (VD + 1) / 2, NB = VD * VD;
+    constexpr int NB = VD * VD;
+    constexpr int NDS = AccStride<VD>::D, NPS = AccStride<VD>::P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t meta_bar;
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -109,12 +121,12 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
     T *xs = sm;
     T *gacc = xs + VD * nf;
     T *dacc = gacc + VD * nf;
-    T *pacc = dacc + ND * nf;
+    T *pacc = dacc + NDS * nf;
     T *vs = gacc + VD * nf;    // matrix-free mode: v of the footprint ...
     T *hacc = vs + VD * nf;    // ... and the H v accumulators (in place of dacc, pacc)
     // the tile's row metadata follows the accumulators; one thread starts
     // its bulk copy now, and it lands while the elements are evaluated
-    const size_t acc_bytes = sizeof(T) * (size_t)((2 * VD + ND) * nf + NB * np);
+    const size_t acc_bytes = sizeof(T) * (size_t)((2 * VD + NDS) * nf + NPS * np);
     unsigned char *meta_s = smem_raw + ((acc_bytes + 15) & ~size_t(15));
     const int32_t *ms_row = reinterpret_cast<const int32_t *>(meta_s);
     const uint16_t *ms_coff = reinterpret_cast<const uint16_t *>(meta_s + 4 * nf);
@@ -137,7 +149,7 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
         }
     }
     if (MODE != MODE_HVP)
-        for (int i = threadIdx.x; i < (VD + ND) * nf + NB * np; i += THREADS) gacc[i] = T(0);
+        for (int i = threadIdx.x; i < (VD + NDS) * nf + NPS * np; i += THREADS) gacc[i] = T(0);
     __syncthreads();
     double fe = 0.0;
     if constexpr (TRIS) {
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
                 for (int d = 0; d < 3; ++d) atomicAdd(gacc + lid[0] * 3 + d, L.g[d]);
                 if (MODE == MODE_HESS)
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) atomicAdd(dacc + lid[0] * ND + hix(d, d), L.H[hix(d, d)]);
+                    for (int d = 0; d < 3; ++d) atomicAdd(dacc + lid[0] * NDS + hix(d, d), L.H[hix(d, d)]);
             }
         }
     }
@@ -297,7 +309,7 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
                 const uint32_t kind = code >> 14;
                 if (kind == 0) continue;
                 const int slot = (int)(code & 0x1fffu);
-                const T *src = kind == 1 ? dacc + r * ND + off_d : pacc + slot * NB + (kind == 2 ? k : off_t);
+                const T *src = kind == 1 ? dacc + r * NDS + off_d : pacc + slot * NPS + (kind == 2 ? k : off_t);
                 const T val = *src;
                 T *dst = out + (e - sub) * NB;
                 if (code & 0x2000u) atomicAdd(dst, val);

@@ -136,6 +136,54 @@ void interleave32(const std::vector<int32_t> &in, int32_t *out)
         for (int64_t m = r; m < n; m += q) out[j++] = in[m];
 }
 
+// Warp groups with few shared-memory bank conflicts.  Element e of a tile has
+// R "roles" (its vertices and its pairs, in their fixed order); in role r one
+// warp instruction of the kernel touches, for each of its 32 lanes, the
+// accumulator of that lane's element, whose bank is key[e][r] = (slot index)
+// mod 32 (the accumulator strides are odd).  Consecutive runs of 32 stored
+// elements are one warp's lanes, so the stored order is built group by group:
+// each element, in the given order, joins the group (with room left) where
+// its keys collide least with those already there.  Distinct banks also mean
+// distinct addresses, so colliding float atomics retry less.
+void bank_groups(int64_t n, int R, const std::vector<uint8_t> &key, std::vector<int32_t> &perm)
+{
+    const int64_t G = (n + 31) / 32;
+    std::vector<uint8_t> occ((size_t)G * R * 32, 0);
+    std::vector<int32_t> fill(G, 0);
+    std::vector<std::vector<int32_t>> members(G);
+    for (int64_t e = 0; e < n; ++e) {
+        int64_t best = -1, best_c = 0;
+        for (int64_t g = 0; g < G; ++g) {
+            const int64_t capg = g + 1 < G ? 32 : n - 32 * (G - 1);
+            if (fill[g] >= capg) continue;
+            int64_t c = 0;
+            for (int r = 0; r < R; ++r) c += occ[((size_t)g * R + r) * 32 + key[(size_t)e * R + r]];
+            if (best < 0 || c < best_c) {
+                best = g;
+                best_c = c;
+                if (c == 0) break;
+            }
+        }
+        for (int r = 0; r < R; ++r) occ[((size_t)best * R + r) * 32 + key[(size_t)e * R + r]]++;
+        fill[best]++;
+        members[best].push_back((int32_t)e);
+    }
+    perm.clear();
+    for (auto &m : members) perm.insert(perm.end(), m.begin(), m.end());
+}
+
+// reorder n records of W uint16 (and their permutation entries) by perm
+void apply_order(const std::vector<int32_t> &perm, int W, uint16_t *loc, int32_t *elem_perm)
+{
+    const size_t n = perm.size();
+    std::vector<uint16_t> l(loc, loc + n * W);
+    std::vector<int32_t> ep(elem_perm, elem_perm + n);
+    for (size_t j = 0; j < n; ++j) {
+        for (int w = 0; w < W; ++w) loc[j * W + w] = l[(size_t)perm[j] * W + w];
+        elem_perm[j] = ep[perm[j]];
+    }
+}
+
 }  // namespace
 
 int64_t tile_meta_bytes(int64_t nf, int64_t ncodes) { return (4 * nf + 2 * (nf + 1) + 2 * ncodes + 15) & ~int64_t(15); }
@@ -189,7 +237,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         int64_t ncodes = 0;
         for (int32_t v : w.foot) ncodes += P.row_ptr[v + 1] - P.row_ptr[v];
         const int64_t nf = (int64_t)w.foot.size();
-        const int64_t bytes = tile_smem_bytes(8, 12 * nf + 9 * np, nf, ncodes);
+        const int64_t bytes = tile_smem_bytes(8, 13 * nf + 9 * np, nf, ncodes);
         for (int32_t v : w.foot) w.lid[v] = -1;
         w.clear_pairs();
         return ncodes < 65536 ? bytes : INT64_MAX;
@@ -299,6 +347,27 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
             for (int p = 0; p < 6; ++p)
                 ts.hinge_loc[10 * i + 4 + p] =
                     w.value(pkey(ts.hinge_loc[10 * i + HP[p][0]], ts.hinge_loc[10 * i + HP[p][1]]));
+        // final stored order: bank-aware warp groups (keys: local ids and
+        // pair slots mod 32, in the kernel's role order)
+        {
+            std::vector<uint8_t> key;
+            std::vector<int32_t> perm;
+            const int64_t t0 = tile_tri_off[t], nt = tile_tri_off[t + 1] - t0;
+            key.resize((size_t)nt * 6);
+            for (int64_t i = 0; i < nt; ++i)
+                for (int r = 0; r < 6; ++r) key[(size_t)i * 6 + r] = (uint8_t)(ts.tri_loc[6 * (t0 + i) + r] & 31);
+            bank_groups(nt, 6, key, perm);
+            apply_order(perm, 6, &ts.tri_loc[6 * t0], &ts.tri_perm[t0]);
+            const int64_t h0 = tile_hinge_off[t], nh = tile_hinge_off[t + 1] - h0;
+            if (nh > 0) {
+                key.resize((size_t)nh * 10);
+                for (int64_t i = 0; i < nh; ++i)
+                    for (int r = 0; r < 10; ++r)
+                        key[(size_t)i * 10 + r] = (uint8_t)(ts.hinge_loc[10 * (h0 + i) + r] & 31);
+                bank_groups(nh, 10, key, perm);
+                apply_order(perm, 10, &ts.hinge_loc[10 * h0], &ts.hinge_perm[h0]);
+            }
+        }
         pairs[t] = w.pairs;
         w.clear_pairs();
         for (int32_t v : foot) w.lid[v] = -1;
@@ -427,9 +496,9 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         for (int p = 0; p < 2; ++p) {
             const int eb = p == 0 ? 8 : 4;  // index: ADM_FP64 = 0, ADM_FP32 = 1
             ts.smem_bytes[1][p] =
-                std::max(ts.smem_bytes[1][p], tile_smem_bytes(eb, 12 * (int64_t)nf + 9 * (int64_t)np, nf, ncodes));
+                std::max(ts.smem_bytes[1][p], tile_smem_bytes(eb, 13 * (int64_t)nf + 9 * (int64_t)np, nf, ncodes));
             ts.smem_bytes[0][p] =
-                std::max(ts.smem_bytes[0][p], tile_smem_bytes(eb, 7 * (int64_t)nf + 4 * (int64_t)np, nf, ncodes));
+                std::max(ts.smem_bytes[0][p], tile_smem_bytes(eb, 7 * (int64_t)nf + 5 * (int64_t)np, nf, ncodes));
         }
     }
     // code_off has one sentinel per tile: footprint row r of tile t is at
@@ -448,7 +517,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
 // the first triangle (in tile order) that has it, so both its vertices are in
 // that tile's footprint and their pair has a slot there (read from that
 // triangle's record); a vertex belongs to the first tile whose footprint has
-// it.  Both lists are stored interleaved like the triangles.
+// it.  Both lists are stored in bank-aware warp groups like the triangles.
 adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts)
 {
     if (!ts.built || ts.n_tiles == 0) return ADM_ERR_ARG;
@@ -494,12 +563,20 @@ adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts)
     for (int32_t t = 0; t < n_tiles; ++t) {
         const int32_t *hd = &ts.hdr[8 * (size_t)t];
         const int32_t foot_begin = hd[4], nf = hd[5];
-        // edges, interleaved
-        std::vector<int32_t> ord(tile_edges[t].size()), il(ord.size());
-        std::iota(ord.begin(), ord.end(), 0);
-        interleave32(ord, il.data());
+        // edges in bank-aware warp groups (keys: both local ids, the pair slot)
+        const int64_t ne = (int64_t)tile_edges[t].size();
+        std::vector<uint8_t> key((size_t)ne * 3);
+        for (int64_t q = 0; q < ne; ++q) {
+            const Cand &c = cand[tile_edges[t][q]];
+            const uint16_t *tl = &ts.tri_loc[6 * c.pos];
+            key[(size_t)q * 3] = (uint8_t)(tl[TP[c.pair][0]] & 31);
+            key[(size_t)q * 3 + 1] = (uint8_t)(tl[TP[c.pair][1]] & 31);
+            key[(size_t)q * 3 + 2] = (uint8_t)(tl[3 + c.pair] & 31);
+        }
+        std::vector<int32_t> il;
+        bank_groups(ne, 3, key, il);
         ts.cloth_hdr[4 * (size_t)t] = (int32_t)(ts.edge_loc.size() / 3);
-        ts.cloth_hdr[4 * (size_t)t + 1] = (int32_t)ord.size();
+        ts.cloth_hdr[4 * (size_t)t + 1] = (int32_t)ne;
         for (int32_t q : il) {
             const Cand &c = cand[tile_edges[t][q]];
             const uint16_t *tl = &ts.tri_loc[6 * c.pos];
@@ -512,7 +589,7 @@ adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts)
             if (!(l2 > 0.0)) return ADM_ERR_MESH;
             ts.edge_l2.push_back(l2);
         }
-        // vertices first seen in this tile, interleaved
+        // vertices first seen in this tile, in bank-aware warp groups
         std::vector<int32_t> vl;
         for (int32_t r = 0; r < nf; ++r) {
             const int32_t v = ts.foot[foot_begin + r];
@@ -521,8 +598,11 @@ adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts)
                 vl.push_back(r);
             }
         }
-        std::vector<int32_t> vil(vl.size());
-        interleave32(vl, vil.data());
+        std::vector<uint8_t> vkey(vl.size());
+        for (size_t q = 0; q < vl.size(); ++q) vkey[q] = (uint8_t)(vl[q] & 31);
+        std::vector<int32_t> vperm, vil(vl.size());
+        bank_groups((int64_t)vl.size(), 1, vkey, vperm);
+        for (size_t q = 0; q < vl.size(); ++q) vil[q] = vl[vperm[q]];
         ts.cloth_hdr[4 * (size_t)t + 2] = (int32_t)ts.vert_loc.size();
         ts.cloth_hdr[4 * (size_t)t + 3] = (int32_t)vil.size();
         for (int32_t r : vil) {
