@@ -609,6 +609,11 @@ def run_ours(args, rank: int, world: int, local: int):
 
     # CPU baseline and FP32-vs-FP64 error on the same sample (rank 0, N = 1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the extras leave other results in the buffers: one plain pass first
+        m.set_projection(False, 0.0)
+        step()
+        torch.cuda.synchronize()
+        assert m.status() == 0
         n = meshes_for_elements(mesh, 550_000)
         P, xs = oracle_sample(levels, mesh, n)
         t0 = time.perf_counter()
