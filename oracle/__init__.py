@@ -482,3 +482,78 @@ def cloth_assemble(rest, F, x, xhat, params=None, row_ptr=None, col=None, projec
     np.add.at(vals, blk(j, i), np.transpose(Aij, (0, 2, 1)))
     out["vals"] = vals
     return out
+
+
+# --------------------------------------------------------------------------
+# interaction terms over vertex pairs (Sec. 4.3; the contact barrier of
+# Sec. 7.7) and the pattern they extend (Sec. 6.3, Alg. 1)
+# --------------------------------------------------------------------------
+def contact_vv(xi, xj, kappa: float, dhat: float, area: float, h: float):
+    """Vertex-vertex barrier of Sec. 7.7:
+        E(d) = kappa/2 dhat A_c (s - 1) ln(s) h^2,  s = d / dhat,  for d < dhat,
+    0 otherwise, d = |x_i - x_j|.  Returns f, gradient (6) and Hessian (6, 6)
+    over (x_i, x_j), from the scalar derivatives of E in d and the chain rule
+    through d = |x_i - x_j|."""
+    xi = np.asarray(xi, dtype=np.float64)
+    xj = np.asarray(xj, dtype=np.float64)
+    r = xi - xj
+    d = float(np.linalg.norm(r))
+    g = np.zeros(6)
+    H = np.zeros((6, 6))
+    if not (d < dhat) or d == 0.0:
+        return 0.0, g, H
+    c = 0.5 * kappa * area * h * h
+    s = d / dhat
+    f = c * dhat * (s - 1.0) * np.log(s)
+    e1 = c * (np.log(s) + (s - 1.0) / s)               # dE/dd
+    e2 = c / dhat * (1.0 / s + 1.0 / (s * s))          # d2E/dd2
+    u = r / d
+    gd = e1 * u
+    Hd = e2 * np.outer(u, u) + (e1 / d) * (np.eye(3) - np.outer(u, u))
+    g[:3], g[3:] = gd, -gd
+    H[:3, :3], H[3:, 3:], H[:3, 3:], H[3:, :3] = Hd, Hd, -Hd, -Hd
+    return f, g, H
+
+
+def extended_pattern(row_ptr, col, pairs):
+    """Block pattern with the blocks of vertex pairs added (Alg. 1 inserts the
+    new (i, j) and (j, i) entries): per row, the original columns in their
+    order, then the new columns ascending.  Pairs already in the pattern add
+    nothing.  Returns (row_ptr, col)."""
+    nV = len(row_ptr) - 1
+    rows = [list(col[row_ptr[r]:row_ptr[r + 1]]) for r in range(nV)]
+    extra = [set() for _ in range(nV)]
+    for i, j in np.asarray(pairs, dtype=np.int64).reshape(-1, 2):
+        if j not in rows[i]:
+            extra[i].add(int(j))
+            extra[j].add(int(i))
+    rp = [0]
+    out = []
+    for r in range(nV):
+        out.extend(rows[r])
+        out.extend(sorted(extra[r]))
+        rp.append(len(out))
+    return np.asarray(rp, dtype=np.int64), np.asarray(out, dtype=np.int64)
+
+
+def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col):
+    """Energy, gradient and Hessian blocks {(row, col): 3x3} of a mesh energy
+    (base: energy, grad, vals over the pattern row_ptr, col) plus a
+    vertex-vertex barrier per pair, assembled by their plain definition."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    energy = base["energy"]
+    grad = np.array(base["grad"], dtype=np.float64)
+    blocks = {}
+    for r in range(len(row_ptr) - 1):
+        for k in range(row_ptr[r], row_ptr[r + 1]):
+            blocks[(r, int(col[k]))] = np.array(base["vals"][k])
+    for i, j in np.asarray(pairs, dtype=np.int64).reshape(-1, 2):
+        f, g, H = contact_vv(x[i], x[j], kappa, dhat, area, h)
+        energy += f
+        grad[i] += g[:3]
+        grad[j] += g[3:]
+        for a, va in ((0, int(i)), (1, int(j))):
+            for b, vb in ((0, int(i)), (1, int(j))):
+                blk = blocks.setdefault((va, vb), np.zeros((3, 3)))
+                blk += H[3 * a:3 * a + 3, 3 * b:3 * b + 3]
+    return {"energy": energy, "grad": grad, "blocks": blocks}
