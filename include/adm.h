@@ -124,7 +124,8 @@ typedef enum {
     ADM_STAGE_TILED = 5,      /* fused tiled element + assembly kernel          */
     ADM_STAGE_GRAPH = 6,      /* a whole captured pass replayed (ADM_OPT_GRAPH) */
     ADM_STAGE_MLP = 7,        /* per-triangle network table (learned membrane)  */
-    ADM_N_STAGES = 8
+    ADM_STAGE_PAIRS = 8,      /* interaction terms over vertex pairs            */
+    ADM_N_STAGES = 9
 } adm_stage;
 
 /* --- creation ---------------------------------------------------------- */
@@ -144,6 +145,30 @@ adm_status adm_create(const double *V, int64_t nV, const int32_t *F, int64_t nF,
 adm_status adm_create_batch(const double *V, const int64_t *v_off, const int32_t *F,
                             const int64_t *f_off, int32_t n_mesh, int32_t var_dim,
                             adm_handle *out);
+
+/* Interaction terms over vertex pairs (Sec. 4.3) with the dynamic block
+ * pattern they induce (Sec. 6.3, Alg. 1).  Replaces the pair set of the
+ * pattern `energy` uses (membranes and ADM_MASS_SPRING: the triangle
+ * pattern; ADM_SHELL and ADM_HINGE_BENDING: the shell pattern; one pattern
+ * per handle) with n_pairs unordered vertex pairs (pairs: 2 * n_pairs int32,
+ * host or device, copied), n_pairs = 0 clearing it.  Every later evaluation
+ * of an energy on that pattern adds, per pair, the contact barrier of
+ * Sec. 7.7, kappa/2 dhat area (s - 1) ln(s) h^2 with s = |x_i - x_j| / dhat,
+ * for s < 1 (var_dim 3).
+ *
+ * The block pattern is extended on the GPU: every row keeps its mesh
+ * columns, in their order, followed by the columns of its new pair blocks in
+ * ascending order; pairs whose blocks the mesh pattern has add no blocks.
+ * adm_pattern then returns the extended pattern (device pointers valid until
+ * the next call of this function), whose nnzb sizes the Hessian buffers.
+ * Synchronous on `stream` (reads back the new block count).  Pair energies
+ * count towards the total and towards the mesh of the first vertex (in
+ * per-mesh energies their order of summation is not fixed).  The Hessian
+ * and matrix-free passes run on the tiled kernel.  Errors: ADM_ERR_ARG
+ * (vertex out of range, i == j, a pair given twice, dhat <= 0; the set is
+ * then cleared), ADM_ERR_UNSUPPORTED (var_dim != 3, a second pattern kind). */
+adm_status adm_set_interactions(adm_handle h, adm_energy energy, const int32_t *pairs, int64_t n_pairs,
+                                double kappa, double dhat, double area, double h_step, void *stream);
 
 /* Inertial target xhat of ADM_MASS_SPRING (x^n + h v^n of the time step;
  * host, n_rows * 3 doubles, copied into library memory in both precisions).

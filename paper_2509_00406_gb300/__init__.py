@@ -30,7 +30,7 @@ FP64, FP32 = 0, 1
 # adm_option
 OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE, OPT_GRAPH = 1, 2, 3, 4, 5
 # adm_stage
-STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled", "graph", "mlp"]
+STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled", "graph", "mlp", "pairs"]
 MLP_NPARAM = 4481
 
 STATUS = {0: "ADM_OK", -1: "ADM_ERR_ARG", -2: "ADM_ERR_MESH", -3: "ADM_ERR_DOMAIN",
@@ -74,6 +74,7 @@ def lib():
         "adm_eval_hvp": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "adm_set_projection": (i32, [vp, i32, C.c_double]),
         "adm_set_inertia_target": (i32, [vp, vp]),
+        "adm_set_interactions": (i32, [vp, i32, vp, i64, C.c_double, C.c_double, C.c_double, C.c_double, vp]),
         "adm_eval_batch": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "adm_eval_batch_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_eval_jacobian": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
@@ -207,6 +208,16 @@ class Mesh:
     def eval(self, energy: int, prec: int, x, energy_out=None, grad=None, bsr=None, stream=None):
         _check(lib().adm_eval(self._h, energy, prec, _ptr(x), _ptr(energy_out), _ptr(grad), _ptr(bsr),
                               _stream(stream)), "adm_eval")
+
+    def set_interactions(self, energy: int, pairs, kappa: float, dhat: float, area: float, h: float = 1.0,
+                         stream=None):
+        """Vertex-pair contact terms (device or host int32 (n, 2), unique
+        unordered pairs) for the pattern of `energy`; n = 0 clears them.
+        The block pattern changes: query pattern() again."""
+        n = 0 if pairs is None else int(pairs.shape[0])
+        _check(lib().adm_set_interactions(self._h, energy, _ptr(pairs) if n else None, n, float(kappa),
+                                          float(dhat), float(area), float(h), _stream(stream)),
+               "adm_set_interactions")
 
     def set_inertia_target(self, xhat):
         """Inertial target of the mass-spring energy (host, (nV, 3), copied)."""

@@ -207,7 +207,7 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
         h->epart_cap = (size_t)ts.n_tiles + 1;
     }
     ts.built = true;
-    return ADM_OK;
+    return interactions_retile(h, kind, 0);  // pair-extended pattern: remap the new tiles
 }
 
 bool energy_ok(int energy, int vdim)
@@ -498,12 +498,15 @@ adm_status adm_pattern(adm_handle h, adm_energy energy, int32_t *block, int64_t 
     if (energy == ADM_ARAP2D_RESIDUAL) energy = ADM_SYMDIR2D;  // J^T J lives on the triangle pattern
     adm_status s = prepare(h, energy);
     if (s != ADM_OK) return s;
-    const Pattern &P = h->pat[needs_hinges(energy) ? PAT_SHELL : PAT_TRI];
+    const int kind = needs_hinges(energy) ? PAT_SHELL : PAT_TRI;
+    const Pattern &P = h->pat[kind];
+    const Interactions &I = h->inter;
+    const bool ext = I.kind == kind && I.d_rp[I.active];  // extended by interaction pairs
     if (block) *block = h->m.vdim;
     if (n_rows) *n_rows = h->m.nV;
-    if (nnzb) *nnzb = P.nnzb;
-    if (row_ptr_dev) *row_ptr_dev = P.d_row_ptr;
-    if (col_dev) *col_dev = P.d_col;
+    if (nnzb) *nnzb = ext ? I.nnzb : P.nnzb;
+    if (row_ptr_dev) *row_ptr_dev = ext ? I.d_rp[I.active] : P.d_row_ptr;
+    if (col_dev) *col_dev = ext ? I.d_col[I.active] : P.d_col;
     return ADM_OK;
 }
 
@@ -613,6 +616,20 @@ adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const v
     a.gnorm_per_mesh = nullptr;
     a.stream = as_stream(stream);
     return run_pass(h, a);
+}
+
+adm_status adm_set_interactions(adm_handle h, adm_energy energy, const int32_t *pairs, int64_t n_pairs,
+                                double kappa, double dhat, double area, double h_step, void *stream)
+{
+    if (!h || n_pairs < 0 || (n_pairs > 0 && !pairs) || !(dhat > 0.0) || !std::isfinite(kappa) ||
+        !std::isfinite(area) || !std::isfinite(h_step))
+        return ADM_ERR_ARG;
+    if (h->m.vdim != 3 || !energy_ok(energy, 3) || energy == ADM_ARAP2D_RESIDUAL) return ADM_ERR_UNSUPPORTED;
+    adm_status s = prepare(h, energy, true);
+    if (s != ADM_OK) return s;
+    drop_graphs(h);
+    return interactions_set(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI, pairs, n_pairs, kappa, dhat, area,
+                            h_step, as_stream(stream));
 }
 
 adm_status adm_set_inertia_target(adm_handle h, const double *xhat_host)

@@ -1,0 +1,512 @@
+// dyn.cu -- interaction terms over vertex pairs and the dynamic block
+// pattern they induce (Sec. 4.3, Sec. 6.3, Alg. 1).
+//
+// A pair set replaces the previous one and extends the mesh pattern on the
+// GPU, following Alg. 1: per-row counts (the mesh row plus the pair blocks
+// not already present), an exclusive scan into the new row pointer, a copy of
+// the mesh columns, and an atomic append of the new columns.  Each row's
+// appended run is then sorted, which fixes the layout (mesh columns first in
+// their order, new columns ascending) and exposes duplicate pairs.  Two
+// pattern buffers alternate.  The tiles of the mesh kernel keep their
+// per-row codes; only their row starts and shared-block indices are
+// remapped.  Evaluation adds, per pair, the contact barrier of Sec. 7.7 on
+// (x_i, x_j): the diagonal blocks and the gradient with atomic additions, the
+// new off-diagonal blocks with plain stores (one pair writes each), blocks
+// already in the mesh pattern with atomic additions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+
+namespace adm {
+
+namespace {
+
+constexpr int kDynThreads = 256;
+constexpr int kScanItems = 4;  // per thread of the scan
+
+int blocks_for(int64_t n, int per = kDynThreads) { return (int)std::max<int64_t>(1, (n + per - 1) / per); }
+
+template <typename P>
+adm_status alloc(adm_ctx *h, P **out, size_t bytes)
+{
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return ADM_ERR_OOM;
+    }
+    h->owned.push_back(p);
+    *out = (P *)p;
+    return ADM_OK;
+}
+
+void release(adm_ctx *h, void *p)
+{
+    if (!p) return;
+    auto it = std::find(h->owned.begin(), h->owned.end(), p);
+    if (it != h->owned.end()) h->owned.erase(it);
+    cudaFree(p);
+}
+
+// ------------------------------------------------------------- Alg. 1 --
+__global__ void k_row_len(int64_t nV, const int32_t *rp, int32_t *cnt)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nV) cnt[r] = rp[r + 1] - rp[r];
+    if (r == nV) cnt[r] = 0;
+}
+
+// position of column c in the sorted run col[a, b), or -1
+__device__ __forceinline__ int32_t find_col(const int32_t *col, int32_t a, int32_t b, int32_t c)
+{
+    const int32_t end = b;
+    while (a < b) {
+        const int32_t m = (a + b) >> 1;
+        if (col[m] < c) a = m + 1;
+        else b = m;
+    }
+    return (a < end && col[a] == c) ? a : -1;
+}
+
+// step (1): count the new entries of every row; mark pairs whose blocks the
+// mesh pattern already has
+__global__ void k_count(int64_t n, const int32_t *pairs, int64_t nV, const int32_t *rp, const int32_t *col,
+                        int32_t *cnt, int32_t *slot, int *status)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+    if (i < 0 || j < 0 || i >= nV || j >= nV || i == j) {
+        atomicOr(status, ST_DOMAIN);
+        slot[2 * p] = slot[2 * p + 1] = -1;
+        return;
+    }
+    const int32_t k = find_col(col, rp[i], rp[i + 1], j);
+    if (k >= 0) {  // in the mesh pattern: (i, j) at offset k - rp[i], (j, i) found below
+        slot[2 * p] = (int32_t)(0x80000000u | (uint32_t)(k - rp[i]));
+        const int32_t k2 = find_col(col, rp[j], rp[j + 1], i);
+        slot[2 * p + 1] = (int32_t)(0x80000000u | (uint32_t)(k2 - rp[j]));
+        return;
+    }
+    slot[2 * p] = slot[2 * p + 1] = 0;
+    atomicAdd(&cnt[i], 1);
+    atomicAdd(&cnt[j], 1);
+}
+
+// step (2): exclusive scan of n int32 in three launches
+template <int THREADS>
+__global__ void k_scan_local(int64_t n, const int32_t *in, int32_t *out, int32_t *bsum)
+{
+    __shared__ int32_t part[THREADS];
+    const int64_t base = (int64_t)blockIdx.x * THREADS * kScanItems + (int64_t)threadIdx.x * kScanItems;
+    int32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < THREADS; off <<= 1) {  // inclusive Hillis-Steele over thread sums
+        const int32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - s;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == THREADS - 1) bsum[blockIdx.x] = part[THREADS - 1];
+}
+
+template <int THREADS>
+__global__ void k_scan_sums(int nb, int32_t *bsum)
+{
+    __shared__ int32_t part[THREADS];
+    const int per = (nb + THREADS - 1) / THREADS;
+    const int b0 = threadIdx.x * per;
+    int32_t s = 0;
+    for (int b = b0; b < b0 + per && b < nb; ++b) s += bsum[b];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < THREADS; off <<= 1) {
+        const int32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - s;
+    for (int b = b0; b < b0 + per && b < nb; ++b) {
+        const int32_t t = bsum[b];
+        bsum[b] = run;
+        run += t;
+    }
+}
+
+__global__ void k_scan_add(int64_t n, int32_t *out, const int32_t *bsum)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += bsum[i / (kDynThreads * kScanItems)];
+}
+
+// step (3): copy the mesh columns; acc = next free offset of every row
+__global__ void k_copy_rows(int64_t nV, const int32_t *rp, const int32_t *col, const int32_t *rpx, int32_t *colx,
+                            int32_t *acc)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nV) return;
+    const int32_t a = rp[r], len = rp[r + 1] - a, o = rpx[r];
+    for (int32_t k = 0; k < len; ++k) colx[o + k] = col[a + k];
+    acc[r] = len;
+}
+
+// step (4): append the new columns
+__global__ void k_append(int64_t n, const int32_t *pairs, const int32_t *slot, const int32_t *rpx, int32_t *acc,
+                         int32_t *colx)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n || slot[2 * p] != 0) return;
+    const int32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+    colx[rpx[i] + atomicAdd(&acc[i], 1)] = j;
+    colx[rpx[j] + atomicAdd(&acc[j], 1)] = i;
+}
+
+// sort every row's appended run (insertion sort: runs are short); a repeated
+// column means a duplicate pair
+__global__ void k_sort_tails(int64_t nV, const int32_t *rp, const int32_t *rpx, int32_t *colx, int *status)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nV) return;
+    const int32_t a = rpx[r] + (rp[r + 1] - rp[r]), b = rpx[r + 1];
+    for (int32_t k = a + 1; k < b; ++k) {
+        const int32_t c = colx[k];
+        int32_t q = k - 1;
+        while (q >= a && colx[q] > c) {
+            colx[q + 1] = colx[q];
+            --q;
+        }
+        colx[q + 1] = c;
+    }
+    for (int32_t k = a + 1; k < b; ++k)
+        if (colx[k] == colx[k - 1]) atomicOr(status, ST_DUPLICATE);
+}
+
+// final block index of both blocks of every pair (bit 31: a mesh block)
+__global__ void k_slots(int64_t n, const int32_t *pairs, const int32_t *rp, const int32_t *rpx, const int32_t *colx,
+                        int32_t *slot)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t i = pairs[2 * p], j = pairs[2 * p + 1];
+    if (slot[2 * p] == -1) return;
+    if (slot[2 * p] & 0x80000000) {
+        slot[2 * p] = (int32_t)(0x80000000u | (uint32_t)(rpx[i] + (slot[2 * p] & 0x7fffffff)));
+        slot[2 * p + 1] = (int32_t)(0x80000000u | (uint32_t)(rpx[j] + (slot[2 * p + 1] & 0x7fffffff)));
+        return;
+    }
+    slot[2 * p] = find_col(colx, rpx[i] + (rp[i + 1] - rp[i]), rpx[i + 1], j);
+    slot[2 * p + 1] = find_col(colx, rpx[j] + (rp[j + 1] - rp[j]), rpx[j + 1], i);
+}
+
+// tiles: row starts in the metadata blobs and shared-block indices follow the
+// extended pattern (the per-row codes are unchanged: mesh columns come first)
+__global__ void k_remap_tiles(int32_t n_tiles, const int32_t *hdr, const int32_t *foot, const int64_t *meta_off,
+                              unsigned char *meta, const int32_t *rpx)
+{
+    const int32_t t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const int32_t foot_begin = hdr[8 * t + 4], nf = hdr[8 * t + 5];
+    int32_t *rows = reinterpret_cast<int32_t *>(meta + meta_off[t]);
+    for (int r = threadIdx.x; r < nf; r += blockDim.x)
+        rows[r] = (int32_t)(((uint32_t)rows[r] & 0x80000000u) | (uint32_t)rpx[foot[foot_begin + r]]);
+}
+
+__global__ void k_remap_zero(int64_t n, const int32_t *row, const int32_t *off, const int32_t *rpx, int32_t *blocks)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) blocks[k] = rpx[row[k]] + off[k];
+}
+
+// --------------------------------------------------------- evaluation --
+template <typename T>
+struct PairArgs {
+    int64_t n;
+    const int32_t *pairs, *slot, *rpx, *diag_off;
+    const T *x, *v;
+    T *grad, *bsr, *hv;
+    double *pair_e;
+    T c, dhat, eps;
+};
+
+template <typename T, int MODE, bool PROJ>
+__global__ void __launch_bounds__(kDynThreads) k_pairs(PairArgs<T> A)
+{
+    const int64_t p = (int64_t)blockIdx.x * kDynThreads + threadIdx.x;
+    if (p >= A.n) return;
+    const int32_t vid[2] = {A.pairs[2 * p], A.pairs[2 * p + 1]};
+    T x[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) x[3 * a + d] = A.x[3 * (int64_t)vid[a] + d];
+    Local<T, 6> L;
+    const bool active = contact_local<T, PROJ>(x, A.c, A.dhat, L, A.eps);
+    A.pair_e[p] = (double)L.f;
+    auto H = [&](int i, int j) { return L.H[i <= j ? hix(i, j) : hix(j, i)]; };
+    if (active && MODE >= MODE_GRAD && A.grad)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) atomicAdd(A.grad + 3 * (int64_t)vid[a] + d, L.g[3 * a + d]);
+    if (MODE == MODE_HVP) {
+        if (!active) return;
+        T vl[6];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) vl[3 * a + d] = A.v[3 * (int64_t)vid[a] + d];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            T y = -T(0);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) y += H(i, j) * vl[j];
+            atomicAdd(A.hv + 3 * (int64_t)vid[i / 3] + i % 3, y);
+        }
+        return;
+    }
+    if (MODE != MODE_HESS) return;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {  // own blocks: the mesh pattern's diagonal, several writers
+        if (!active) break;
+        T *blk = A.bsr + 9 * ((int64_t)A.rpx[vid[a]] + A.diag_off[vid[a]]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) atomicAdd(blk + 3 * r + s, H(3 * a + r, 3 * a + s));
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {  // (i, j) and (j, i)
+        const int32_t sl = A.slot[2 * p + a];
+        const bool mesh = (sl & 0x80000000) != 0;
+        T *blk = A.bsr + 9 * (int64_t)(sl & 0x7fffffff);
+        const int b = 1 - a;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                const T val = H(3 * a + r, 3 * b + s);
+                if (mesh) {
+                    if (active) atomicAdd(blk + 3 * r + s, val);
+                } else {
+                    blk[3 * r + s] = val;  // the only writer of a new block (zero when inactive)
+                }
+            }
+    }
+}
+
+// pair energies: fixed-order sum into the total, and each pair's energy
+// credited to the mesh of its first vertex
+template <int THREADS>
+__global__ void k_pair_energy(int64_t n, const int32_t *pairs, const double *pair_e, int n_mesh,
+                              const int64_t *v_off, double *e_mesh, double *e_total)
+{
+    double s = 0.0;
+    for (int64_t p = threadIdx.x; p < n; p += THREADS) {
+        s += pair_e[p];
+        if (e_mesh && pair_e[p] != 0.0) {
+            int64_t lo = 0, hi = n_mesh;  // mesh k with v_off[k] <= i < v_off[k + 1]
+            const int64_t i = pairs[2 * p];
+            while (hi - lo > 1) {
+                const int64_t m = (lo + hi) >> 1;
+                if (v_off[m] <= i) lo = m;
+                else hi = m;
+            }
+            atomicAdd(&e_mesh[lo], pair_e[p]);
+        }
+    }
+    s = block_sum<THREADS>(s);
+    if (threadIdx.x == 0 && e_total) *e_total += s;
+}
+
+template <typename T>
+adm_status eval_pairs(adm_ctx *h, const EvalArgs &a, int mode)
+{
+    Interactions &I = h->inter;
+    PairArgs<T> A;
+    A.n = I.n_pairs;
+    A.pairs = I.d_pairs;
+    A.slot = I.d_slot;
+    A.rpx = I.d_rp[I.active];
+    A.diag_off = I.d_diag_off;
+    A.x = (const T *)a.x;
+    A.v = (const T *)a.v;
+    A.grad = (T *)a.grad;
+    A.bsr = (T *)a.bsr;
+    A.hv = (T *)a.hv;
+    A.pair_e = I.d_pair_e;
+    A.c = (T)(0.5 * I.kappa * I.area * I.h * I.h);
+    A.dhat = (T)I.dhat;
+    A.eps = (T)h->proj_eps;
+    const int nb = blocks_for(A.n);
+    cudaStream_t s = a.stream;
+    const bool proj = h->proj != 0;
+    if (mode == MODE_VALUE) k_pairs<T, MODE_VALUE, false><<<nb, kDynThreads, 0, s>>>(A);
+    else if (mode == MODE_GRAD) k_pairs<T, MODE_GRAD, false><<<nb, kDynThreads, 0, s>>>(A);
+    else if (mode == MODE_HESS && proj) k_pairs<T, MODE_HESS, true><<<nb, kDynThreads, 0, s>>>(A);
+    else if (mode == MODE_HESS) k_pairs<T, MODE_HESS, false><<<nb, kDynThreads, 0, s>>>(A);
+    else if (proj) k_pairs<T, MODE_HVP, true><<<nb, kDynThreads, 0, s>>>(A);
+    else k_pairs<T, MODE_HVP, false><<<nb, kDynThreads, 0, s>>>(A);
+    return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+}  // namespace
+
+adm_status interactions_eval(adm_ctx *h, const EvalArgs &a, int mode)
+{
+    const Interactions &I = h->inter;
+    if (I.kind < 0 || I.n_pairs == 0) return ADM_OK;
+    if (h->m.vdim != 3) return ADM_ERR_UNSUPPORTED;
+    return a.prec == ADM_FP32 ? eval_pairs<float>(h, a, mode) : eval_pairs<double>(h, a, mode);
+}
+
+adm_status interactions_energy(adm_ctx *h, const EvalArgs &a)
+{
+    const Interactions &I = h->inter;
+    if (I.kind < 0 || I.n_pairs == 0 || (!a.energy_total && !a.energy_per_mesh)) return ADM_OK;
+    k_pair_energy<1024><<<1, 1024, 0, a.stream>>>(I.n_pairs, I.d_pairs, I.d_pair_e, h->m.n_mesh, I.d_v_off,
+                                                  a.energy_per_mesh, a.energy_total);
+    return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+adm_status interactions_retile(adm_ctx *h, int kind, cudaStream_t s)
+{
+    Interactions &I = h->inter;
+    if (I.kind != kind || !I.d_rp[I.active]) return ADM_OK;
+    const Pattern &P = h->pat[kind];
+    TileSet &ts = h->tiles[kind];
+    if (!ts.built) return ADM_OK;
+    // the tiles' shared blocks as (row, offset in the mesh row), then indices
+    // in the active pattern
+    const size_t nz = ts.zero_blocks.size();
+    std::vector<int32_t> zr(nz), zo(nz);
+    for (size_t k = 0; k < nz; ++k) {
+        const int32_t b = ts.zero_blocks[k];
+        const int32_t r = (int32_t)(std::upper_bound(P.row_ptr.begin(), P.row_ptr.end(), b) - P.row_ptr.begin()) - 1;
+        zr[k] = r;
+        zo[k] = b - P.row_ptr[r];
+    }
+    release(h, I.d_zero_row);
+    release(h, I.d_zero_off);
+    I.d_zero_row = I.d_zero_off = nullptr;
+    adm_status st;
+    if ((st = alloc(h, &I.d_zero_row, nz * 4)) != ADM_OK) return st;
+    if ((st = alloc(h, &I.d_zero_off, nz * 4)) != ADM_OK) return st;
+    if (nz && (cudaMemcpy(I.d_zero_row, zr.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+               cudaMemcpy(I.d_zero_off, zo.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess))
+        return ADM_ERR_CUDA;
+    const int32_t *rpx = I.d_rp[I.active];
+    k_remap_tiles<<<ts.n_tiles, 256, 0, s>>>(ts.n_tiles, ts.d_hdr, ts.d_foot, ts.d_meta_off, ts.d_meta, rpx);
+    if (nz)
+        k_remap_zero<<<blocks_for((int64_t)nz), kDynThreads, 0, s>>>((int64_t)nz, I.d_zero_row, I.d_zero_off, rpx,
+                                                                      ts.d_zero_blocks);
+    return cudaStreamSynchronize(s) == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+}
+
+adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t n, double kappa, double dhat,
+                            double area, double hstep, cudaStream_t s)
+{
+    Interactions &I = h->inter;
+    const Pattern &P = h->pat[kind];
+    TileSet &ts = h->tiles[kind];
+    const int64_t nV = h->m.nV;
+    if (!P.built || !ts.built) return ADM_ERR_ARG;
+    adm_status st;
+    // one-time data of this pattern kind
+    if (I.kind != kind) {
+        if (I.kind >= 0) return ADM_ERR_UNSUPPORTED;  // one pattern kind per handle
+        std::vector<int32_t> doff(nV);
+        for (int64_t v = 0; v < nV; ++v) {
+            const auto b = P.col.begin() + P.row_ptr[v], e = P.col.begin() + P.row_ptr[v + 1];
+            doff[v] = (int32_t)(std::lower_bound(b, e, (int32_t)v) - b);
+        }
+        if ((st = alloc(h, &I.d_diag_off, nV * 4)) != ADM_OK) return st;
+        if ((st = alloc(h, &I.d_v_off, (h->m.n_mesh + 1) * 8)) != ADM_OK) return st;
+        if ((st = alloc(h, &I.d_cnt, (nV + 1) * 4)) != ADM_OK) return st;
+        if ((st = alloc(h, &I.d_acc, nV * 4)) != ADM_OK) return st;
+        const int nsb = blocks_for(nV + 1, kDynThreads * kScanItems);
+        if ((st = alloc(h, &I.d_bsum, nsb * 4)) != ADM_OK) return st;
+        for (int b = 0; b < 2; ++b)
+            if ((st = alloc(h, &I.d_rp[b], (nV + 1) * 4)) != ADM_OK) return st;
+        if (cudaMemcpy(I.d_diag_off, doff.data(), nV * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(I.d_v_off, h->m.v_off.data(), (h->m.n_mesh + 1) * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return ADM_ERR_CUDA;
+        I.kind = kind;
+    }
+    // room for the pairs and the extended pattern (the inactive buffer)
+    if (n > I.cap_pairs) {
+        release(h, I.d_pairs);
+        release(h, I.d_slot);
+        release(h, I.d_pair_e);
+        I.d_pairs = I.d_slot = nullptr;
+        I.d_pair_e = nullptr;
+        I.cap_pairs = 0;
+        if ((st = alloc(h, &I.d_pairs, n * 8)) != ADM_OK) return st;
+        if ((st = alloc(h, &I.d_slot, n * 8)) != ADM_OK) return st;
+        if ((st = alloc(h, &I.d_pair_e, n * 8)) != ADM_OK) return st;
+        I.cap_pairs = n;
+    }
+    const int nxt = 1 - I.active;
+    const int64_t need = P.nnzb + 2 * n;
+    if (need > I.col_cap[nxt]) {
+        release(h, I.d_col[nxt]);
+        I.d_col[nxt] = nullptr;
+        if ((st = alloc(h, &I.d_col[nxt], need * 4)) != ADM_OK) return st;
+        I.col_cap[nxt] = need;
+    }
+    if (n > 0 && cudaMemcpyAsync(I.d_pairs, pairs, n * 8, cudaMemcpyDefault, s) != cudaSuccess) return ADM_ERR_CUDA;
+    if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
+    int32_t *rpx = I.d_rp[nxt], *colx = I.d_col[nxt];
+    // (1) counts, (2) scan, (3) copy, (4) append, then sorted tails and slots
+    k_row_len<<<blocks_for(nV + 1), kDynThreads, 0, s>>>(nV, P.d_row_ptr, I.d_cnt);
+    if (n > 0)
+        k_count<<<blocks_for(n), kDynThreads, 0, s>>>(n, I.d_pairs, nV, P.d_row_ptr, P.d_col, I.d_cnt, I.d_slot,
+                                                       h->d_status);
+    const int nsb = blocks_for(nV + 1, kDynThreads * kScanItems);
+    k_scan_local<kDynThreads><<<nsb, kDynThreads, 0, s>>>(nV + 1, I.d_cnt, rpx, I.d_bsum);
+    k_scan_sums<1024><<<1, 1024, 0, s>>>(nsb, I.d_bsum);
+    k_scan_add<<<blocks_for(nV + 1), kDynThreads, 0, s>>>(nV + 1, rpx, I.d_bsum);
+    k_copy_rows<<<blocks_for(nV), kDynThreads, 0, s>>>(nV, P.d_row_ptr, P.d_col, rpx, colx, I.d_acc);
+    if (n > 0) {
+        k_append<<<blocks_for(n), kDynThreads, 0, s>>>(n, I.d_pairs, I.d_slot, rpx, I.d_acc, colx);
+        k_sort_tails<<<blocks_for(nV), kDynThreads, 0, s>>>(nV, P.d_row_ptr, rpx, colx, h->d_status);
+        k_slots<<<blocks_for(n), kDynThreads, 0, s>>>(n, I.d_pairs, P.d_row_ptr, rpx, colx, I.d_slot);
+    }
+    int32_t total = 0;
+    int status = 0;
+    if (cudaMemcpyAsync(&total, rpx + nV, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    if (status != 0) {  // an invalid or repeated pair: back to the mesh pattern, no pairs
+        if (n > 0) interactions_set(h, kind, nullptr, 0, kappa, dhat, area, hstep, s);
+        return ADM_ERR_ARG;
+    }
+    // switch: tiles follow the new pattern
+    I.active = nxt;
+    if ((st = interactions_retile(h, kind, s)) != ADM_OK) return st;
+    I.nnzb = total;
+    I.n_pairs = n;
+    I.kappa = kappa;
+    I.dhat = dhat;
+    I.area = area;
+    I.h = hstep;
+    return ADM_OK;
+}
+
+}  // namespace adm

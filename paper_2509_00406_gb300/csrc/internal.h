@@ -18,7 +18,7 @@ namespace adm {
 enum PatternKind { PAT_TRI = 0, PAT_SHELL = 1, PAT_COUNT = 2 };
 
 // device status bits (latched by kernels with atomicOr)
-enum StatusBits { ST_DOMAIN = 1, ST_TIMEOUT = 2 };
+enum StatusBits { ST_DOMAIN = 1, ST_TIMEOUT = 2, ST_DUPLICATE = 4 };
 
 struct DevMem {
     void *p = nullptr;
@@ -126,6 +126,25 @@ struct TileSet {
     void *d_hinge_rest[2] = {nullptr, nullptr};
 };
 
+// vertex-pair interaction terms and the block pattern they extend (dyn.cu;
+// Sec. 4.3, Sec. 6.3, Alg. 1)
+struct Interactions {
+    int kind = -1;                  // pattern kind extended, -1: none
+    int64_t n_pairs = 0, cap_pairs = 0;
+    int32_t *d_pairs = nullptr;     // 2 per pair
+    int32_t *d_slot = nullptr;      // 2 per pair: blocks (i,j), (j,i); bit 31: block of the mesh pattern
+    double *d_pair_e = nullptr;     // energy per pair of the last pass
+    int32_t *d_rp[2] = {nullptr, nullptr}, *d_col[2] = {nullptr, nullptr};  // double-buffered pattern
+    int64_t col_cap[2] = {0, 0};
+    int active = 0;
+    int64_t nnzb = 0;
+    int32_t *d_cnt = nullptr, *d_acc = nullptr, *d_bsum = nullptr;  // scratch of the insertion
+    int32_t *d_diag_off = nullptr;  // position of v's own block in its mesh-pattern row
+    int32_t *d_zero_row = nullptr, *d_zero_off = nullptr;  // shared blocks of the tiles as (row, offset)
+    int64_t *d_v_off = nullptr;     // mesh vertex offsets
+    double kappa = 0.0, dhat = 0.0, area = 0.0, h = 1.0;
+};
+
 struct EnergyParams {
     double E = 1.0e5, nu = 0.3, t = 1.0e-3, kb = -1.0, h = 1.0;
     // mass-spring cloth: stiffness, time step, areal density, gravity
@@ -176,6 +195,7 @@ struct adm_ctx {
     // options
     int assembler = 0;
     void *d_xhat[2] = {nullptr, nullptr};  // mass-spring inertial target, per precision (null: rest shape)
+    adm::Interactions inter;
     int proj = 0;            // per-term Hessian filtering on (adm_set_projection)
     double proj_eps = 0.0;   // value negative local eigenvalues are raised to
     int tile_tris = 0;  // 0: automatic (tile_tris_for)
@@ -237,6 +257,14 @@ struct EvalArgs {
     void *hv = nullptr;        // matrix-free mode: H v (device, like the gradient)
 };
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
+// vertex-pair interactions (dyn.cu): replace the pair set of pattern `kind`
+// and extend its block pattern on the GPU; evaluate the pairs of a pass
+// (after the tiled kernel) and add their energies (after the reduction)
+adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t n, double kappa, double dhat,
+                            double area, double hstep, cudaStream_t s);
+adm_status interactions_eval(adm_ctx *h, const EvalArgs &a, int mode);
+adm_status interactions_retile(adm_ctx *h, int kind, cudaStream_t s);  // after a tile rebuild
+adm_status interactions_energy(adm_ctx *h, const EvalArgs &a);
 // brackets one stage of one evaluation with events when profiling is on
 struct StageTimer {
     adm_ctx *h;

@@ -101,9 +101,13 @@ __device__ __forceinline__ void zero(float (&acc)[8][4])
 __device__ __forceinline__ int elem_row(int e) { return ((threadIdx.x & 31) >> 2) + 8 * ((e & 3) >> 1); }
 __device__ __forceinline__ int elem_col(int e) { return 8 * (e >> 2) + 2 * (threadIdx.x & 3) + (e & 1); }
 
+// SiLU and its first two derivatives: sg = sigma(z), s = z sg,
+// s1 = sg (1 + z (1 - sg)), s2 = sg (1 - sg) (2 + z (1 - 2 sg)).  The fast
+// exponential and reciprocal intrinsics suffice: the network's activations
+// are rounded to BF16 before every contraction.
 __device__ __forceinline__ void silu_all(float z, float &sg, float &s, float &s1, float &s2)
 {
-    sg = 1.0f / (1.0f + expf(-z));
+    sg = __frcp_rn(1.0f + __expf(-z));
     s = z * sg;
     s1 = sg * (1.0f + z * (1.0f - sg));
     s2 = sg * (1.0f - sg) * (2.0f + z * (1.0f - 2.0f * sg));

@@ -314,6 +314,36 @@ ADM_HD void spring_local(const T (&x)[6], T l2, T kh2, Local<T, 6> &out, T eps =
     expand_edges<SpringEdges, 3>(le, out);
 }
 
+// vertex-vertex contact barrier (Sec. 7.7): c dhat (s - 1) ln s for
+// s = |d| / dhat < 1 (else 0), d = x0 - x1, c = kappa/2 A_c h^2; differentiated
+// in d.  Returns false outside the activation distance (out zeroed).
+template <typename T, bool PROJ = false>
+ADM_HD bool contact_local(const T (&x)[6], T c, T dhat, Local<T, 6> &out, T eps = T(0))
+{
+    const T r0 = x[0] - x[3], r1 = x[1] - x[4], r2 = x[2] - x[5];
+    const T q0 = r0 * r0 + r1 * r1 + r2 * r2;
+    if (!(q0 < dhat * dhat) || !(q0 > T(0))) {
+        out.f = T(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) out.g[i] = T(0);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) out.H[k] = T(0);
+        return false;
+    }
+    auto d0 = seed<T, 3, 0>(r0);
+    auto d1 = seed<T, 3, 1>(r1);
+    auto d2 = seed<T, 3, 2>(r2);
+    auto q = sq(d0) + sq(d1) + sq(d2);
+    auto Q = seed<T, 1, 0>(q.v);
+    auto sv = sqrt(Q) * (T(1) / dhat);
+    auto p = (sv - T(1)) * log(sv) * (c * dhat);
+    Local<T, 3> le;
+    store_local(compose(p, q), le);
+    if constexpr (PROJ) project_edges<SpringEdges, 3>(le.H, eps);
+    expand_edges<SpringEdges, 3>(le, out);
+    return true;
+}
+
 // per-vertex inertia and gravity: m/2 |x - xhat|^2 - h2 m g.x (Hessian m I,
 // semidefinite, so filtering never changes it)
 template <typename T>
