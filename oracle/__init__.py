@@ -557,3 +557,69 @@ def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col):
                 blk = blocks.setdefault((va, vb), np.zeros((3, 3)))
                 blk += H[3 * a:3 * a + 3, 3 * b:3 * b + 3]
     return {"energy": energy, "grad": grad, "blocks": blocks}
+
+
+# --------------------------------------------------------------------------
+# per-vertex one-ring term: uniform-Laplacian (umbrella) smoothing
+# --------------------------------------------------------------------------
+UMBRELLA = 9
+
+
+def vertex_rings(nV: int, F) -> list:
+    """Edge-adjacent neighbours of every vertex, ascending."""
+    nb = [set() for _ in range(nV)]
+    for f in np.asarray(F, dtype=np.int64):
+        for c in range(3):
+            a, b = int(f[c]), int(f[(c + 1) % 3])
+            nb[a].add(b)
+            nb[b].add(a)
+    return [sorted(s) for s in nb]
+
+
+def ring_pattern(nV: int, F):
+    """Block pattern of one-ring terms: every pair of vertices of a closed
+    one-ring {v} + N(v), as (row_ptr, col) with columns ascending."""
+    rings = vertex_rings(nV, F)
+    rows = [set([r]) for r in range(nV)]
+    for v in range(nV):
+        R = [v] + rings[v]
+        for a in R:
+            rows[a].update(R)
+    rp, col = [0], []
+    for r in range(nV):
+        col.extend(sorted(rows[r]))
+        rp.append(len(col))
+    return np.asarray(rp, dtype=np.int64), np.asarray(col, dtype=np.int64)
+
+
+def umbrella_assemble(F, x, w: float = 1.0, row_ptr=None, col=None):
+    """sum_v w/2 |x_v - (1/k_v) sum_{u in N(v)} x_u|^2 (k_v the valence;
+    vertices without neighbours contribute nothing), its gradient and, given
+    the pattern, its BSR Hessian: with c = (1, -1/k, .., -1/k) over the
+    closed ring, the term's Hessian is w c c^T per coordinate."""
+    x = np.asarray(x, dtype=np.float64)
+    nV, vd = x.shape
+    rings = vertex_rings(nV, F)
+    energy = 0.0
+    grad = np.zeros_like(x)
+    vals = None if row_ptr is None else np.zeros((len(col), vd, vd))
+    for v in range(nV):
+        k = len(rings[v])
+        if k == 0:
+            continue
+        R = [v] + rings[v]
+        c = np.array([1.0] + [-1.0 / k] * k)
+        L = c @ x[R]
+        energy += 0.5 * w * float(L @ L)
+        for a, va in enumerate(R):
+            grad[va] += w * c[a] * L
+        if vals is not None:
+            for a, va in enumerate(R):
+                lo, hi = row_ptr[va], row_ptr[va + 1]
+                for b, vb in enumerate(R):
+                    kk = lo + int(np.searchsorted(col[lo:hi], vb))
+                    vals[kk] += w * c[a] * c[b] * np.eye(vd)
+    out = {"energy": energy, "grad": grad}
+    if vals is not None:
+        out["vals"] = vals
+    return out
