@@ -311,6 +311,35 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
                   "value": n_el / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
                   "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}}
 
+    # dynamic sparsity: 100k vertex pairs (same mesh, not necessarily close)
+    # inserted into the batch's pattern on the GPU (Alg. 1), then the pass
+    # with their barrier terms; the pattern is restored afterwards
+    rng = np.random.default_rng(9)
+    nv_mesh = np.diff(mesh.v_off)
+    mi = rng.integers(mesh.n_mesh, size=150_000)
+    pi = mesh.v_off[mi] + rng.integers(nv_mesh[mi])
+    pj = mesh.v_off[mi] + rng.integers(nv_mesh[mi])
+    keep = pi != pj
+    pr = np.unique(np.sort(np.stack([pi[keep], pj[keep]], axis=1), axis=1), axis=0)[:100_000].astype(np.int32)
+    pr_d = torch.from_numpy(pr).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.set_interactions(adm.SHELL, pr_d, 1.0e3, 0.2, 1e-3, 1.0, stream=stream)
+    t_ins = (time.perf_counter() - t0) * 1e3
+    _, _, nnzb_x, _, _ = m.pattern(adm.SHELL)
+    Hx = torch.zeros(nnzb_x * 9, dtype=torch.float32, device="cuda")
+    m.set_option(adm.OPT_PROFILE, steps)
+    ms = _time_steps(torch, lambda: m.eval_batch(adm.SHELL, adm.FP32, x, e, gn, g, Hx, stream=stream), steps, stream)
+    prof = m.profile_read()
+    m.set_option(adm.OPT_PROFILE, 0)
+    m.set_interactions(adm.SHELL, None, 1.0e3, 0.2, 1e-3, 1.0, stream=stream)
+    del Hx
+    out["dynamic_pattern"] = {"workload": f"{len(pr)} vertex pairs inserted into the shell batch's BSR pattern "
+                                          f"(Alg. 1 on the GPU), then grad + Hessian with their barrier terms, FP32",
+                              "insert_ms": t_ins, "nnzb_before": int(H.numel() // 9), "nnzb_after": int(nnzb_x),
+                              "ms_per_step": ms, "value": n_el / (ms * 1e-3), "unit": UNIT,
+                              "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}}
+
     # the same pass with per-term Hessian filtering (negative local
     # eigenvalues clamped to 0 by an in-register Jacobi eigensolve)
     m.set_projection(True, 0.0)
@@ -442,6 +471,19 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
         mc.close()
     out["mass_spring_cloth"] = {"workload": "cloth grids n x n, springs + lumped inertia + gravity, grad + BSR "
                                             "Hessian, FP32", "sizes": cloth}
+
+    # per-vertex one-ring term (two-ring pattern) on the level-7 shell, FP32
+    mu7 = adm.Mesh(sh.rest, sh.faces, 3)
+    _, nVu, nnzbu, _, _ = mu7.pattern(adm.UMBRELLA)
+    xu = torch.from_numpy(sh.x.astype(np.float32)).cuda()
+    eu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gu_ = torch.zeros(nVu * 3, dtype=torch.float32, device="cuda")
+    Hu = torch.zeros(nnzbu * 9, dtype=torch.float32, device="cuda")
+    msu = _time_steps(torch, lambda: mu7.eval(adm.UMBRELLA, adm.FP32, xu, eu, gu_, Hu, stream=stream), steps, stream)
+    out["one_ring_umbrella"] = {"workload": "per-vertex one-ring Laplacian term, icosphere level 7 (163,842 V; "
+                                            f"two-ring pattern, {nnzbu} blocks), FP32",
+                                "value": nVu / (msu * 1e-3), "unit": "vertices/s", "ms_per_step": msu}
+    mu7.close()
 
     # symmetric Dirichlet, 33 x 33 grid, FP64 (launch-bound): direct and graph
     gu = synth.grid_uv()

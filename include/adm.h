@@ -76,6 +76,10 @@ typedef enum {
     ADM_NH_MEMBRANE = 5,      /* Neo-Hookean on the invariants of C (Sec. 7.7)      */
     ADM_MLP_MEMBRANE = 6,     /* learned Neo-Hookean surrogate (adm_mlp_* calls)    */
     ADM_AREA = 7,             /* 1/2 |(x_j - x_i) x (x_k - x_i)| (Sec. 7.6)         */
+    ADM_UMBRELLA = 9,         /* per-vertex one-ring term: w/2 |x_v - mean of the
+                                 one-ring neighbours of v|^2 (uniform Laplacian
+                                 smoothing); block pattern = two-ring of every
+                                 vertex; valence <= 12; var_dim 2 or 3       */
     ADM_MASS_SPRING = 8,      /* implicit-Euler cloth (Sec. 7.1): per-vertex
                                  m_v/2 |x_v - xhat_v|^2 - h^2 m_v g.x_v and
                                  per-edge springs h^2 l^2 k/2 (|x_i - x_j|^2 / l^2
@@ -179,6 +183,7 @@ adm_status adm_set_inertia_target(adm_handle h, const double *xhat_host);
 /* Material parameters of an energy (host array, copied).  Membranes
  * (ADM_STVK_MEMBRANE, ADM_NH_MEMBRANE, ADM_MLP_MEMBRANE): {E, nu, thickness};
  * ADM_HINGE_BENDING: {k_b, h}; ADM_SHELL: {E, nu, thickness, k_b, h};
+ * ADM_UMBRELLA: {w};
  * ADM_MASS_SPRING: {k, h, rho, g_x, g_y, g_z} (spring stiffness, time step,
  * areal density, gravity; defaults 1e4, 1/60, 1, (0, 0, -9.81)).
  * Missing trailing values keep their defaults E = 1e5, nu = 0.3,
@@ -209,6 +214,8 @@ adm_status adm_jac_pattern(adm_handle h, adm_energy energy, int64_t *n_rows, int
  * order, then hinges) and every ordered local vertex pair (a, b), the index
  * of block (v_a, v_b) in the BSR pattern (device int32, n_elem x nv x nv). */
 adm_status adm_hinges(adm_handle h, const int32_t **hinges_dev, int64_t *n_hinges);
+/* (ADM_ERR_UNSUPPORTED for ADM_UMBRELLA and ADM_MASS_SPRING, which have no
+ * per-triangle or per-hinge elements.) */
 adm_status adm_slot_map(adm_handle h, adm_energy energy, const int32_t **slots_dev,
                         int64_t *n_entries);
 

@@ -25,6 +25,7 @@ HEADER = os.path.join(ROOT, "include", "adm.h")
 SYMDIR2D, STVK_MEMBRANE, HINGE_BENDING, SHELL, NH_MEMBRANE, MLP_MEMBRANE, AREA = 1, 2, 3, 4, 5, 6, 7
 ARAP2D_RESIDUAL = 16
 MASS_SPRING = 8
+UMBRELLA = 9
 # adm_precision
 FP64, FP32 = 0, 1
 # adm_option

@@ -18,7 +18,7 @@ HOST_LIB = os.path.join(OUT, "libadm_host.so")
 HOST_SOURCES = ["host_check.cpp", "mesh.cpp", "tiles.cpp"]
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu", "noalloc.cu", "mlp.cu", "dyn.cu",
+SOURCES = ["atomic_f32.cu", "atomic_f64.cu", "tiled_f32.cu", "tiled_f64.cu", "reduce.cu", "noalloc.cu", "mlp.cu", "dyn.cu", "ring.cu",
            "mesh.cpp", "tiles.cpp", "api.cpp"]
 # tiled-kernel variant groups, each tiled_inst.cu compiled with its own defines
 # (object name, defines): sets 0-4 = passive+gradient, Hessian, filtered

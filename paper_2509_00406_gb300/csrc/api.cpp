@@ -88,7 +88,8 @@ adm_status build_blocks(adm_ctx *h, BlockTable &bt, const std::vector<int64_t> &
 
 adm_status ensure_epart(adm_ctx *h)
 {
-    size_t need = (size_t)h->tri_blocks.n_blocks + (size_t)h->hinge_blocks.n_blocks + 1;
+    size_t need = std::max((size_t)h->tri_blocks.n_blocks + (size_t)h->hinge_blocks.n_blocks,
+                           (size_t)h->vert_blocks.n_blocks) + 1;
     if (need <= h->epart_cap) return ADM_OK;
     dev_free(h, h->d_epart);
     h->d_epart = nullptr;
@@ -101,6 +102,25 @@ adm_status build_pattern(adm_ctx *h, int kind)
 {
     Pattern &P = h->pat[kind];
     if (P.built) return ADM_OK;
+    if (kind == PAT_RING) {  // one-ring terms: two-ring pattern, rings and their slot map
+        adm_status s = mesh_build_rings(h->m);
+        if (s != ADM_OK) return s;
+        std::vector<int32_t> sl, so;
+        mesh_build_ring_pattern(h->m, P.row_ptr, P.col);
+        P.nnzb = (int64_t)P.col.size();
+        mesh_build_ring_slots(h->m, P.row_ptr, P.col, sl, so);
+        if ((s = upload(h, &P.d_row_ptr, P.row_ptr.data(), P.row_ptr.size() * 4)) != ADM_OK) return s;
+        if ((s = upload(h, &P.d_col, P.col.data(), P.col.size() * 4)) != ADM_OK) return s;
+        if ((s = upload(h, &P.d_ring_off, h->m.ring_off.data(), h->m.ring_off.size() * 4)) != ADM_OK) return s;
+        if ((s = upload(h, &P.d_ring, h->m.ring.data(), std::max<size_t>(1, h->m.ring.size()) * 4)) != ADM_OK)
+            return s;
+        if ((s = upload(h, &P.d_ring_slots, sl.data(), sl.size() * 4)) != ADM_OK) return s;
+        if ((s = upload(h, &P.d_ring_slot_off, so.data(), so.size() * 4)) != ADM_OK) return s;
+        if ((s = build_blocks(h, h->vert_blocks, h->m.v_off, kElemThreads)) != ADM_OK) return s;
+        if ((s = ensure_epart(h)) != ADM_OK) return s;
+        P.built = true;
+        return ADM_OK;
+    }
     std::vector<int32_t> ts, hs;
     mesh_build_pattern(h->m, kind == PAT_SHELL, P.row_ptr, P.col);
     P.nnzb = (int64_t)P.col.size();
@@ -222,6 +242,7 @@ bool energy_ok(int energy, int vdim)
     case ADM_MLP_MEMBRANE:
     case ADM_AREA:
     case ADM_MASS_SPRING: return vdim == 3;
+    case ADM_UMBRELLA: return true;
     default: return false;
     }
 }
@@ -253,6 +274,7 @@ adm_status ensure_cloth(adm_ctx *h)
 adm_status prepare(adm_ctx *h, int energy, bool need_tiles = false)
 {
     if (!energy_ok(energy, h->m.vdim)) return ADM_ERR_UNSUPPORTED;
+    if (energy == ADM_UMBRELLA) return build_pattern(h, PAT_RING);  // its own per-vertex kernel, no tiles
     adm_status s = needs_hinges(energy) ? ensure_shell(h) : build_pattern(h, PAT_TRI);
     if (energy == ADM_MLP_MEMBRANE && h->assembler != 0) return ADM_ERR_UNSUPPORTED;
     const bool cloth = energy == ADM_MASS_SPRING;
@@ -435,6 +457,9 @@ adm_status adm_set_params(adm_handle h, adm_energy energy, const double *p, int3
         if (np > 2) q.t = p[2];
         if (np > 3) q.kb = p[3];
         if (np > 4) q.h = p[4];
+    } else if (energy == ADM_UMBRELLA) {
+        if (np > 1 || (np == 1 && !std::isfinite(p[0]))) return ADM_ERR_ARG;
+        if (np == 1) q.w = p[0];
     } else if (energy == ADM_MASS_SPRING) {
         if (np > 6) return ADM_ERR_ARG;
         double *dst[6] = {&q.k, &q.dt, &q.rho, &q.g[0], &q.g[1], &q.g[2]};
@@ -498,7 +523,7 @@ adm_status adm_pattern(adm_handle h, adm_energy energy, int32_t *block, int64_t 
     if (energy == ADM_ARAP2D_RESIDUAL) energy = ADM_SYMDIR2D;  // J^T J lives on the triangle pattern
     adm_status s = prepare(h, energy);
     if (s != ADM_OK) return s;
-    const int kind = needs_hinges(energy) ? PAT_SHELL : PAT_TRI;
+    const int kind = energy == ADM_UMBRELLA ? PAT_RING : (needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
     const Pattern &P = h->pat[kind];
     const Interactions &I = h->inter;
     const bool ext = I.kind == kind && I.d_rp[I.active];  // extended by interaction pairs
@@ -551,6 +576,9 @@ adm_status adm_hinges(adm_handle h, const int32_t **hinges_dev, int64_t *n_hinge
 adm_status adm_slot_map(adm_handle h, adm_energy energy, const int32_t **slots_dev, int64_t *n_entries)
 {
     if (!h) return ADM_ERR_ARG;
+    // triangle and hinge elements only (the one-ring and mass-spring terms
+    // have no per-triangle slot map)
+    if (energy == ADM_UMBRELLA || energy == ADM_MASS_SPRING) return ADM_ERR_UNSUPPORTED;
     adm_status s = prepare(h, energy);
     if (s != ADM_OK) return s;
     const bool hin = needs_hinges(energy);
@@ -624,7 +652,8 @@ adm_status adm_set_interactions(adm_handle h, adm_energy energy, const int32_t *
     if (!h || n_pairs < 0 || (n_pairs > 0 && !pairs) || !(dhat > 0.0) || !std::isfinite(kappa) ||
         !std::isfinite(area) || !std::isfinite(h_step))
         return ADM_ERR_ARG;
-    if (h->m.vdim != 3 || !energy_ok(energy, 3) || energy == ADM_ARAP2D_RESIDUAL) return ADM_ERR_UNSUPPORTED;
+    if (h->m.vdim != 3 || !energy_ok(energy, 3) || energy == ADM_ARAP2D_RESIDUAL || energy == ADM_UMBRELLA)
+        return ADM_ERR_UNSUPPORTED;
     adm_status s = prepare(h, energy, true);
     if (s != ADM_OK) return s;
     drop_graphs(h);
@@ -690,7 +719,7 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
     const HostMesh &m = h->m;
     const size_t es = prec == ADM_FP32 ? 4 : 8;
     const size_t xb = es * m.nV * m.vdim;
-    const int64_t nnzb = h->pat[needs_hinges(energy) ? PAT_SHELL : PAT_TRI].nnzb;
+    const int64_t nnzb = h->pat[energy == ADM_UMBRELLA ? PAT_RING : (needs_hinges(energy) ? PAT_SHELL : PAT_TRI)].nnzb;
     const size_t bb = es * nnzb * m.vdim * m.vdim;
     if (!h->own_stream && cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return ADM_ERR_CUDA;
@@ -734,7 +763,8 @@ adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, con
                         int32_t *best_tile_tris, float *best_ms)
 {
     if (!h || !x_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
-    if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE || !energy_ok(energy, h->m.vdim))
+    if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE || energy == ADM_UMBRELLA ||
+        !energy_ok(energy, h->m.vdim))
         return ADM_ERR_UNSUPPORTED;
     const int saved_asm = h->assembler, saved_graph = h->use_graph, saved_ring = h->prof_ring;
     h->assembler = 0;

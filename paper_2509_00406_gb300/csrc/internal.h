@@ -15,7 +15,8 @@
 namespace adm {
 
 // stencil sets that own a block pattern
-enum PatternKind { PAT_TRI = 0, PAT_SHELL = 1, PAT_COUNT = 2 };
+enum PatternKind { PAT_TRI = 0, PAT_SHELL = 1, PAT_RING = 2, PAT_COUNT = 3 };
+constexpr int kMaxValence = 12;  // one-ring terms: vertices of higher valence are rejected
 
 // device status bits (latched by kernels with atomicOr)
 enum StatusBits { ST_DOMAIN = 1, ST_TIMEOUT = 2, ST_DUPLICATE = 4 };
@@ -46,6 +47,10 @@ struct HostMesh {
     std::vector<double> h_thetabar; // nH
     std::vector<double> h_abar;     // nH, mean rest area of the two faces
     int64_t nH() const { return (int64_t)H.size() / 4; }
+    // one-rings (built on demand): ascending edge-adjacent neighbours
+    bool rings_built = false;
+    std::vector<int32_t> ring_off;  // nV + 1
+    std::vector<int32_t> ring;
 };
 
 struct Pattern {
@@ -58,6 +63,8 @@ struct Pattern {
     int32_t *d_hinge_slots = nullptr;  // nH * 16 (shell pattern only)
     int32_t *d_all_slots = nullptr;    // concatenation exported by adm_slot_map
     int64_t n_all_slots = 0;
+    // one-ring pattern only: rings and the ring slot map (mesh_build_ring_slots)
+    int32_t *d_ring_off = nullptr, *d_ring = nullptr, *d_ring_slots = nullptr, *d_ring_slot_off = nullptr;
 };
 
 // element work split into blocks that never straddle two meshes
@@ -149,6 +156,7 @@ struct EnergyParams {
     double E = 1.0e5, nu = 0.3, t = 1.0e-3, kb = -1.0, h = 1.0;
     // mass-spring cloth: stiffness, time step, areal density, gravity
     double k = 1.0e4, dt = 1.0 / 60.0, rho = 1.0, g[3] = {0.0, 0.0, -9.81};
+    double w = 1.0;  // one-ring (umbrella) term weight
     double mu() const { return E / (2.0 * (1.0 + nu)); }
     double lambda() const { return E * nu / (1.0 - nu * nu); }
     double kbend() const { return kb >= 0.0 ? kb : E * t * t * t / (12.0 * (1.0 - nu * nu)); }
@@ -183,7 +191,7 @@ struct adm_ctx {
     // ARAP Jacobian column pattern
     int32_t *d_jac_row_ptr = nullptr, *d_jac_col = nullptr;
     // element block tables (keyed by threads per block)
-    adm::BlockTable tri_blocks, hinge_blocks;
+    adm::BlockTable tri_blocks, hinge_blocks, vert_blocks;
     adm::ChunkTable chunks;
     // scratch for reductions
     double *d_epart = nullptr;      // energy partial per element block
@@ -229,6 +237,10 @@ void mesh_rest_triangles(HostMesh &m);
 adm_status mesh_build_hinges(HostMesh &m);
 void mesh_build_pattern(const HostMesh &m, bool with_hinges, std::vector<int32_t> &row_ptr,
                         std::vector<int32_t> &col);
+adm_status mesh_build_rings(HostMesh &m);
+void mesh_build_ring_pattern(const HostMesh &m, std::vector<int32_t> &row_ptr, std::vector<int32_t> &col);
+void mesh_build_ring_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
+                           std::vector<int32_t> &slots, std::vector<int32_t> &slot_off);
 void mesh_build_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr,
                       const std::vector<int32_t> &col, bool hinges, std::vector<int32_t> &tri_slots,
                       std::vector<int32_t> &hinge_slots);
@@ -264,6 +276,8 @@ adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t 
                             double area, double hstep, cudaStream_t s);
 adm_status interactions_eval(adm_ctx *h, const EvalArgs &a, int mode);
 adm_status interactions_retile(adm_ctx *h, int kind, cudaStream_t s);  // after a tile rebuild
+// per-vertex one-ring terms (ring.cu): the whole pass of ADM_UMBRELLA
+adm_status eval_ring(adm_ctx *h, const EvalArgs &a);
 adm_status interactions_energy(adm_ctx *h, const EvalArgs &a);
 // brackets one stage of one evaluation with events when profiling is on
 struct StageTimer {

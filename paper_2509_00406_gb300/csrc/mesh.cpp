@@ -230,4 +230,67 @@ void mesh_build_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr,
                 hinge_slots[16 * i + 4 * a + b] = block_of(row_ptr, col, m.H[4 * i + a], m.H[4 * i + b]);
 }
 
+// one-rings: the edge-adjacent neighbours of every vertex, ascending (CSR)
+adm_status mesh_build_rings(HostMesh &m)
+{
+    if (m.rings_built) return ADM_OK;
+    std::vector<std::vector<int32_t>> nb(m.nV);
+    for (int64_t t = 0; t < m.nT; ++t)
+        for (int c = 0; c < 3; ++c) {
+            const int32_t a = m.F[3 * t + c], b = m.F[3 * t + (c + 1) % 3];
+            nb[a].push_back(b);
+            nb[b].push_back(a);
+        }
+    m.ring_off.assign(m.nV + 1, 0);
+    m.ring.clear();
+    for (int64_t v = 0; v < m.nV; ++v) {
+        std::sort(nb[v].begin(), nb[v].end());
+        nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
+        if ((int)nb[v].size() > kMaxValence) return ADM_ERR_UNSUPPORTED;
+        m.ring.insert(m.ring.end(), nb[v].begin(), nb[v].end());
+        m.ring_off[v + 1] = (int32_t)m.ring.size();
+    }
+    m.rings_built = true;
+    return ADM_OK;
+}
+
+// block pattern of one-ring terms: a term couples every pair of vertices of a
+// closed one-ring, so row a holds every vertex within two edges of a
+void mesh_build_ring_pattern(const HostMesh &m, std::vector<int32_t> &row_ptr, std::vector<int32_t> &col)
+{
+    row_ptr.assign(m.nV + 1, 0);
+    col.clear();
+    std::vector<int32_t> nb;
+    for (int64_t a = 0; a < m.nV; ++a) {
+        nb.clear();
+        nb.push_back((int32_t)a);
+        for (int32_t k = m.ring_off[a]; k < m.ring_off[a + 1]; ++k) {
+            const int32_t w = m.ring[k];  // a is in the closed ring of w and of every neighbour of w
+            nb.push_back(w);
+            for (int32_t q = m.ring_off[w]; q < m.ring_off[w + 1]; ++q) nb.push_back(m.ring[q]);
+        }
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        col.insert(col.end(), nb.begin(), nb.end());
+        row_ptr[a + 1] = (int32_t)col.size();
+    }
+}
+
+// ring slot map: for vertex v with closed ring (v, n_0, .., n_{k-1}), the
+// block of every ordered pair (a, b) of it, row-major over (k + 1)^2
+void mesh_build_ring_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr, const std::vector<int32_t> &col,
+                           std::vector<int32_t> &slots, std::vector<int32_t> &slot_off)
+{
+    slot_off.assign(m.nV + 1, 0);
+    slots.clear();
+    std::vector<int32_t> r;
+    for (int64_t v = 0; v < m.nV; ++v) {
+        r.assign(1, (int32_t)v);
+        r.insert(r.end(), m.ring.begin() + m.ring_off[v], m.ring.begin() + m.ring_off[v + 1]);
+        for (int32_t a : r)
+            for (int32_t b : r) slots.push_back(block_of(row_ptr, col, a, b));
+        slot_off[v + 1] = (int32_t)slots.size();
+    }
+}
+
 }  // namespace adm
