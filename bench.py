@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip graph/MLP/secondary measurements")
+    ap.add_argument("--profile-case", choices=["mlp", "filtered", "hvp"], default=None,
+                    help="run a few passes of one secondary case on the first --meshes meshes and exit "
+                         "(a small workload for ncu)")
     return ap.parse_args()
 
 
@@ -510,6 +513,48 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
 
 
 # ------------------------------------------------------------------ our arm --
+def run_profile_case(args):
+    """A few passes of one secondary case on the first args.meshes meshes,
+    for a small ncu capture; prints one line with the case and its time."""
+    import torch
+
+    import __graft_entry__
+    import paper_2509_00406_gb300 as adm
+
+    __graft_entry__.build()
+    _, mesh = workload(0, args.meshes)
+    m = adm.Mesh(mesh.rest, mesh.faces, 3, v_off=mesh.v_off, f_off=mesh.f_off)
+    x = torch.from_numpy(mesh.x.astype(np.float32)).cuda()
+    e = torch.zeros(mesh.n_mesh, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    if args.profile_case == "mlp":
+        energy = adm.MLP_MEMBRANE
+        rng = np.random.default_rng(0)
+        th = np.zeros(adm.MLP_NPARAM, dtype=np.float32)
+        th[:192] = rng.normal(scale=0.6, size=192)
+        th[256:4352] = rng.normal(scale=1 / 8, size=4096)
+        th[4416:4480] = rng.normal(scale=1 / 8, size=64)
+        norm = np.array([3.0, 3.0, 1.0, 0.3, 0.5, 0.3, 1e3, 1e3], dtype=np.float32)
+        m.mlp_attach(torch.from_numpy(th).cuda(), torch.from_numpy(norm).cuda())
+    else:
+        energy = adm.SHELL
+        if args.profile_case == "filtered":
+            m.set_projection(True, 0.0)
+    m.set_params(energy, SHELL_PARAMS)
+    _, nV, nnzb, _, _ = m.pattern(energy)
+    g = torch.zeros(nV * 3, dtype=torch.float32, device="cuda")
+    if args.profile_case == "hvp":
+        hv = torch.zeros_like(g)
+        run = lambda: m.eval_hvp(energy, adm.FP32, x, x, hv, None, g, stream=stream)  # noqa: E731
+    else:
+        H = torch.zeros(nnzb * 9, dtype=torch.float32, device="cuda")
+        run = lambda: m.eval_batch(energy, adm.FP32, x, e, None, g, H, stream=stream)  # noqa: E731
+    ms = _time_steps(torch, run, max(1, args.steps), stream)
+    assert m.status() == 0
+    print(json.dumps({"profile_case": args.profile_case, "meshes": args.meshes, "ms_per_pass": ms}), flush=True)
+    m.close()
+
+
 def run_ours(args, rank: int, world: int, local: int):
     import torch
 
@@ -693,7 +738,9 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local)

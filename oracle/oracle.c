@@ -32,8 +32,8 @@
  *   5  Neo-Hookean membrane on the three invariants of C       (Sec. 7.7)
  *   7  surface area 1/2 |(x_j - x_i) x (x_k - x_i)|            (Sec. 7.6)
  *  16  ARAP-style residual sqrt(A) vec(J - R(J)), 4 per face  (Sec. 4.1 Eq. 3)
- * Readings of ambiguous passages are listed in the design doc and repeated at each
- * function below.
+ * The reading taken for each ambiguous passage is stated at the function
+ * that implements it.
  */
 #include <math.h>
 #include <stdint.h>

@@ -11,8 +11,8 @@ Every generator takes an explicit integer seed and draws from
 ``numpy.random.default_rng(seed)`` (PCG64); the same seed gives bit-identical
 arrays on x86_64 and aarch64.
 
-Workloads (sizes follow the paper's application scales, Sec. 7, and the
-synthetic stand-ins described in the design doc):
+Workloads (sizes follow the paper's application scales, Sec. 7; they stand
+in for the paper's meshes, which are not available):
 
 * ``grid_uv``        -- 33x33 regular grid of the unit square, 2,048 triangles,
                         UV = rest + N(0, 0.01^2)  (symmetric Dirichlet, Sec. 7.2)
