@@ -712,9 +712,12 @@ static int cmp_i64(const void *a, const void *b)
 int64_t orc_pattern(int64_t nV, int64_t nT, const int32_t *F, int64_t nH, const int32_t *H,
                     int32_t *row_ptr, int32_t *col)
 {
-    int64_t cap = 9 * nT + 16 * nH;
+    /* reading: the pattern is {(i, i)} plus the stencil pairs, so a vertex
+       no element touches still has its (zero) diagonal block */
+    int64_t cap = nV + 9 * nT + 16 * nH;
     int64_t *keys = malloc(sizeof(int64_t) * (size_t)(cap > 0 ? cap : 1));
     int64_t n = 0;
+    for (int64_t v = 0; v < nV; ++v) keys[n++] = v * nV + v;
     for (int64_t t = 0; t < nT; ++t)
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) keys[n++] = (int64_t)F[3 * t + a] * nV + F[3 * t + b];

@@ -88,9 +88,18 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
     stats[4] = (double)P.nnzb;
     stats[5] = (double)m.nH();
     stats[6] = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    // every zeroed block is shared
-    for (int32_t b : ts.zero_blocks)
+    // every zeroed block is shared, or the diagonal block of a vertex no
+    // element touches (written by nothing but the zero fill; reported as -2)
+    for (int32_t b : ts.zero_blocks) {
+        if (block_writer[b] == -1) {
+            const int32_t r = (int32_t)(std::upper_bound(P.row_ptr.begin(), P.row_ptr.end(), b) - P.row_ptr.begin()) - 1;
+            if (P.col[b] != r) return -102;
+            block_writer[b] = -2;
+            block_adds[b] = 2;
+            continue;
+        }
         if (block_writer[b] != -2) return -102;
+    }
     // each tile's metadata blob holds its rows' starts, code offsets and codes
     if ((int64_t)ts.meta_off.size() != ts.n_tiles + 1 || ts.meta_off.back() != (int64_t)ts.meta.size()) return -105;
     for (int32_t t = 0; t < ts.n_tiles; ++t) {

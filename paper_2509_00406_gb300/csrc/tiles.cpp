@@ -508,6 +508,16 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     ts.zero_blocks.erase(std::unique(ts.zero_blocks.begin(), ts.zero_blocks.end()), ts.zero_blocks.end());
     for (int64_t v = 0; v < m.nV; ++v)
         if (v_owner[v] == -2) ts.zero_verts.push_back((int32_t)v);
+    // vertices no element touches: no tile writes their gradient row or
+    // diagonal block, so both are zeroed with the shared ones every pass
+    for (int64_t v = 0; v < m.nV; ++v)
+        if (v_owner[v] == -1) {
+            ts.zero_verts.push_back((int32_t)v);
+            const auto b = P.col.begin() + P.row_ptr[v], e = P.col.begin() + P.row_ptr[v + 1];
+            ts.zero_blocks.push_back((int32_t)(std::lower_bound(b, e, (int32_t)v) - P.col.begin()));
+        }
+    std::sort(ts.zero_verts.begin(), ts.zero_verts.end());
+    std::sort(ts.zero_blocks.begin(), ts.zero_blocks.end());
     ts.built = true;
     return ADM_OK;
 }

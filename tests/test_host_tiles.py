@@ -67,3 +67,15 @@ def test_one_tile_per_mesh_has_nothing_shared(H):
     rc, bw, ba, st = run(H, mesh, 1, 100000)
     assert rc == 0
     assert int(st[0]) == 3 and int(st[1]) == 0 and int(st[2]) == 0
+
+
+def test_unused_vertex_is_zeroed(H):
+    """A vertex no triangle references: nothing writes its gradient row or
+    diagonal block, so the builder lists both for the per-pass zero fill."""
+    V, F = synth.icosphere(2)
+    rest = np.concatenate([V, [[3.0, 0.0, 0.0]]])
+    mesh = synth.Mesh(rest=rest, faces=F, x=rest)
+    rc, bw, ba, st = run(H, mesh, 1, 64)
+    assert rc == 0, rc
+    assert (bw != -1).all()
+    assert int(st[2]) >= 1                          # the unused vertex is in the zero list
