@@ -391,25 +391,29 @@ adm_status interactions_retile(adm_ctx *h, int kind, cudaStream_t s)
     const Pattern &P = h->pat[kind];
     TileSet &ts = h->tiles[kind];
     if (!ts.built) return ADM_OK;
-    // the tiles' shared blocks as (row, offset in the mesh row), then indices
-    // in the active pattern
+    // the tiles' shared blocks as (row, offset in the mesh row), once per tile
+    // build; then their indices in the active pattern
     const size_t nz = ts.zero_blocks.size();
-    std::vector<int32_t> zr(nz), zo(nz);
-    for (size_t k = 0; k < nz; ++k) {
-        const int32_t b = ts.zero_blocks[k];
-        const int32_t r = (int32_t)(std::upper_bound(P.row_ptr.begin(), P.row_ptr.end(), b) - P.row_ptr.begin()) - 1;
-        zr[k] = r;
-        zo[k] = b - P.row_ptr[r];
+    if (I.zero_for_build != ts.build_id) {
+        std::vector<int32_t> zr(nz), zo(nz);
+        for (size_t k = 0; k < nz; ++k) {
+            const int32_t b = ts.zero_blocks[k];
+            const int32_t r =
+                (int32_t)(std::upper_bound(P.row_ptr.begin(), P.row_ptr.end(), b) - P.row_ptr.begin()) - 1;
+            zr[k] = r;
+            zo[k] = b - P.row_ptr[r];
+        }
+        release(h, I.d_zero_row);
+        release(h, I.d_zero_off);
+        I.d_zero_row = I.d_zero_off = nullptr;
+        adm_status st;
+        if ((st = alloc(h, &I.d_zero_row, nz * 4)) != ADM_OK) return st;
+        if ((st = alloc(h, &I.d_zero_off, nz * 4)) != ADM_OK) return st;
+        if (nz && (cudaMemcpy(I.d_zero_row, zr.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(I.d_zero_off, zo.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess))
+            return ADM_ERR_CUDA;
+        I.zero_for_build = ts.build_id;
     }
-    release(h, I.d_zero_row);
-    release(h, I.d_zero_off);
-    I.d_zero_row = I.d_zero_off = nullptr;
-    adm_status st;
-    if ((st = alloc(h, &I.d_zero_row, nz * 4)) != ADM_OK) return st;
-    if ((st = alloc(h, &I.d_zero_off, nz * 4)) != ADM_OK) return st;
-    if (nz && (cudaMemcpy(I.d_zero_row, zr.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-               cudaMemcpy(I.d_zero_off, zo.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess))
-        return ADM_ERR_CUDA;
     const int32_t *rpx = I.d_rp[I.active];
     k_remap_tiles<<<ts.n_tiles, 256, 0, s>>>(ts.n_tiles, ts.d_hdr, ts.d_foot, ts.d_meta_off, ts.d_meta, rpx);
     if (nz)

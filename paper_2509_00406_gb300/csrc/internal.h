@@ -89,6 +89,7 @@ struct ChunkTable {
 // shared-memory tiles of the tiled assembler (tiles.cpp)
 struct TileSet {
     bool built = false;
+    int64_t build_id = 0;                // distinct for every build (tiles_build)
     int tile_tris = 0;
     int32_t n_tiles = 0;
     // dynamic shared memory of the tiled kernel, [VD == 3][ADM_FP64 = 0 / ADM_FP32 = 1]:
@@ -148,6 +149,7 @@ struct Interactions {
     int32_t *d_cnt = nullptr, *d_acc = nullptr, *d_bsum = nullptr;  // scratch of the insertion
     int32_t *d_diag_off = nullptr;  // position of v's own block in its mesh-pattern row
     int32_t *d_zero_row = nullptr, *d_zero_off = nullptr;  // shared blocks of the tiles as (row, offset)
+    int64_t zero_for_build = -1;    // tile build the (row, offset) list belongs to
     int64_t *d_v_off = nullptr;     // mesh vertex offsets
     double kappa = 0.0, dhat = 0.0, area = 0.0, h = 1.0;
 };

@@ -518,6 +518,8 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         }
     std::sort(ts.zero_verts.begin(), ts.zero_verts.end());
     std::sort(ts.zero_blocks.begin(), ts.zero_blocks.end());
+    static std::atomic<int64_t> builds(0);
+    ts.build_id = ++builds;
     ts.built = true;
     return ADM_OK;
 }
