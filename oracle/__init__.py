@@ -515,15 +515,25 @@ def contact_vv(xi, xj, kappa: float, dhat: float, area: float, h: float):
     return f, g, H
 
 
-def extended_pattern(row_ptr, col, pairs):
-    """Block pattern with the blocks of vertex pairs added (Alg. 1 inserts the
-    new (i, j) and (j, i) entries): per row, the original columns in their
-    order, then the new columns ascending.  Pairs already in the pattern add
-    nothing.  Returns (row_ptr, col)."""
+def quad_pairs(quads) -> np.ndarray:
+    """The six unordered vertex pairs of every vertex-face element (p, a, b, c):
+    the off-diagonal blocks its Hessian touches."""
+    q = np.asarray(quads, dtype=np.int64).reshape(-1, 4)
+    return np.asarray([(t[i], t[j]) for t in q for i in range(4) for j in range(i + 1, 4)],
+                      dtype=np.int64).reshape(-1, 2)
+
+
+def extended_pattern(row_ptr, col, pairs, quads=()):
+    """Block pattern with the blocks of interaction terms added (Alg. 1 inserts
+    the new (i, j) and (j, i) entries): per row, the original columns in their
+    order, then the new columns ascending, each once.  The blocks are those of
+    the vertex pairs and of the six vertex pairs of every vertex-face element;
+    blocks already in the pattern add nothing.  Returns (row_ptr, col)."""
     nV = len(row_ptr) - 1
     rows = [list(col[row_ptr[r]:row_ptr[r + 1]]) for r in range(nV)]
     extra = [set() for _ in range(nV)]
-    for i, j in np.asarray(pairs, dtype=np.int64).reshape(-1, 2):
+    allp = np.concatenate([np.asarray(pairs, dtype=np.int64).reshape(-1, 2), quad_pairs(quads)])
+    for i, j in allp:
         if j not in rows[i]:
             extra[i].add(int(j))
             extra[j].add(int(i))
@@ -536,10 +546,11 @@ def extended_pattern(row_ptr, col, pairs):
     return np.asarray(rp, dtype=np.int64), np.asarray(out, dtype=np.int64)
 
 
-def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col):
+def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col, quads=()):
     """Energy, gradient and Hessian blocks {(row, col): 3x3} of a mesh energy
     (base: energy, grad, vals over the pattern row_ptr, col) plus a
-    vertex-vertex barrier per pair, assembled by their plain definition."""
+    vertex-vertex barrier per pair and a vertex-face barrier per element
+    (p, a, b, c), assembled by their plain definition."""
     x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
     energy = base["energy"]
     grad = np.array(base["grad"], dtype=np.float64)
@@ -547,13 +558,15 @@ def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col):
     for r in range(len(row_ptr) - 1):
         for k in range(row_ptr[r], row_ptr[r + 1]):
             blocks[(r, int(col[k]))] = np.array(base["vals"][k])
-    for i, j in np.asarray(pairs, dtype=np.int64).reshape(-1, 2):
-        f, g, H = contact_vv(x[i], x[j], kappa, dhat, area, h)
+    terms = [(contact_vv(x[i], x[j], kappa, dhat, area, h), (int(i), int(j)))
+             for i, j in np.asarray(pairs, dtype=np.int64).reshape(-1, 2)]
+    terms += [(contact_vf(x[t[0]], x[t[1]], x[t[2]], x[t[3]], kappa, dhat, area, h), tuple(int(v) for v in t))
+              for t in np.asarray(quads, dtype=np.int64).reshape(-1, 4)]
+    for (f, g, H), verts in terms:
         energy += f
-        grad[i] += g[:3]
-        grad[j] += g[3:]
-        for a, va in ((0, int(i)), (1, int(j))):
-            for b, vb in ((0, int(i)), (1, int(j))):
+        for a, va in enumerate(verts):
+            grad[va] += g[3 * a:3 * a + 3]
+            for b, vb in enumerate(verts):
                 blk = blocks.setdefault((va, vb), np.zeros((3, 3)))
                 blk += H[3 * a:3 * a + 3, 3 * b:3 * b + 3]
     return {"energy": energy, "grad": grad, "blocks": blocks}
@@ -623,3 +636,146 @@ def umbrella_assemble(F, x, w: float = 1.0, row_ptr=None, col=None):
     if vals is not None:
         out["vals"] = vals
     return out
+
+
+# --------------------------------------------------------------------------
+# vertex-face contact (the second interaction term of Sec. 7.7), on a small
+# dense hyper-dual number in numpy: value, gradient and Hessian over n seeds
+# --------------------------------------------------------------------------
+class HD:
+    """Dense second-order forward-mode number (slow; tiny cases only)."""
+
+    def __init__(self, v, g, H):
+        self.v, self.g, self.H = float(v), np.asarray(g, dtype=np.float64), np.asarray(H, dtype=np.float64)
+
+    @staticmethod
+    def var(v, i, n):
+        g = np.zeros(n)
+        g[i] = 1.0
+        return HD(v, g, np.zeros((n, n)))
+
+    def _wrap(self, o):
+        return o if isinstance(o, HD) else HD(o, np.zeros_like(self.g), np.zeros_like(self.H))
+
+    def __add__(self, o):
+        o = self._wrap(o)
+        return HD(self.v + o.v, self.g + o.g, self.H + o.H)
+
+    __radd__ = __add__
+
+    def __neg__(self):
+        return HD(-self.v, -self.g, -self.H)
+
+    def __sub__(self, o):
+        return self + (-self._wrap(o))
+
+    def __rsub__(self, o):
+        return self._wrap(o) - self
+
+    def __mul__(self, o):
+        o = self._wrap(o)
+        return HD(self.v * o.v, self.v * o.g + o.v * self.g,
+                  self.v * o.H + o.v * self.H + np.outer(self.g, o.g) + np.outer(o.g, self.g))
+
+    __rmul__ = __mul__
+
+    def chain(self, f, f1, f2):
+        return HD(f, f1 * self.g, f1 * self.H + f2 * np.outer(self.g, self.g))
+
+    def recip(self):
+        return self.chain(1.0 / self.v, -1.0 / self.v ** 2, 2.0 / self.v ** 3)
+
+    def __truediv__(self, o):
+        return self * self._wrap(o).recip()
+
+    def sqrt(self):
+        r = np.sqrt(self.v)
+        return self.chain(r, 0.5 / r, -0.25 / (r * self.v))
+
+    def log(self):
+        return self.chain(np.log(self.v), 1.0 / self.v, -1.0 / self.v ** 2)
+
+
+def _dot(u, w):
+    return u[0] * w[0] + u[1] * w[1] + u[2] * w[2]
+
+
+def _cross(u, w):
+    return [u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]]
+
+
+def closest_region(p, a, b, c):
+    """Where on triangle (a, b, c) the point closest to p lies: ('v', k) for
+    vertex k, ('e', k, l) for the edge from vertex k to vertex l, ('f',) for
+    the interior; by the signs of the barycentric-style dot products of the
+    standard closest-point construction (Voronoi regions of the triangle)."""
+    p, a, b, c = (np.asarray(z, dtype=np.float64) for z in (p, a, b, c))
+    ab, ac, ap = b - a, c - a, p - a
+    d1, d2 = ab @ ap, ac @ ap
+    if d1 <= 0 and d2 <= 0:
+        return ("v", 0)
+    bp = p - b
+    d3, d4 = ab @ bp, ac @ bp
+    if d3 >= 0 and d4 <= d3:
+        return ("v", 1)
+    vc = d1 * d4 - d3 * d2
+    if vc <= 0 and d1 >= 0 and d3 <= 0:
+        return ("e", 0, 1)
+    cp = p - c
+    d5, d6 = ab @ cp, ac @ cp
+    if d6 >= 0 and d5 <= d6:
+        return ("v", 2)
+    vb = d5 * d2 - d1 * d6
+    if vb <= 0 and d2 >= 0 and d6 <= 0:
+        return ("e", 0, 2)
+    va = d3 * d6 - d5 * d4
+    if va <= 0 and (d4 - d3) >= 0 and (d5 - d6) >= 0:
+        return ("e", 1, 2)
+    return ("f",)
+
+
+def contact_vf(p, a, b, c, kappa: float, dhat: float, area: float, h: float):
+    """Vertex-face barrier of Sec. 7.7 on (p, a, b, c): the printed energy
+    kappa/2 dhat A_c (s - 1) ln(s) h^2, s = d / dhat < 1, d the distance from
+    p to the triangle, A_c the given (rest) face area.  The squared distance
+    is written per closest-point region (vertex, edge, interior) and
+    differentiated by the dense hyper-dual number.  Returns f, g (12), H (12, 12)."""
+    X = np.concatenate([np.asarray(z, dtype=np.float64) for z in (p, a, b, c)])
+    P = [HD.var(X[k], k, 12) for k in range(12)]
+    pts = [P[0:3], P[3:6], P[6:9], P[9:12]]            # p, a, b, c
+    reg = closest_region(p, a, b, c)
+    if reg[0] == "v":
+        r = [pts[0][i] - pts[1 + reg[1]][i] for i in range(3)]
+        q = _dot(r, r)
+    elif reg[0] == "e":
+        u, w = pts[1 + reg[1]], pts[1 + reg[2]]
+        r = [pts[0][i] - u[i] for i in range(3)]
+        e = [w[i] - u[i] for i in range(3)]
+        q = _dot(r, r) - _dot(r, e) * _dot(r, e) / _dot(e, e)
+    else:
+        e1 = [pts[2][i] - pts[1][i] for i in range(3)]
+        e2 = [pts[3][i] - pts[1][i] for i in range(3)]
+        r = [pts[0][i] - pts[1][i] for i in range(3)]
+        n = _cross(e1, e2)
+        q = _dot(n, r) * _dot(n, r) / _dot(n, n)
+    if not (q.v < dhat * dhat) or q.v <= 0.0:
+        return 0.0, np.zeros(12), np.zeros((12, 12))
+    s = q.sqrt() * (1.0 / dhat)
+    E = (s - 1.0) * s.log() * (0.5 * kappa * area * h * h * dhat)
+    return E.v, E.g, E.H
+
+
+def vf_distance(p, a, b, c) -> float:
+    """Distance from p to triangle (a, b, c) by the same region formulas as
+    contact_vf (plain floats)."""
+    reg = closest_region(p, a, b, c)
+    p, a, b, c = (np.asarray(z, dtype=np.float64) for z in (p, a, b, c))
+    pts = [a, b, c]
+    if reg[0] == "v":
+        return float(np.linalg.norm(p - pts[reg[1]]))
+    if reg[0] == "e":
+        u, w = pts[reg[1]], pts[reg[2]]
+        r, e = p - u, w - u
+        return float(np.sqrt(max(r @ r - (r @ e) ** 2 / (e @ e), 0.0)))
+    n = np.cross(b - a, c - a)
+    return float(abs(n @ (p - a)) / np.linalg.norm(n))
