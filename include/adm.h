@@ -150,27 +150,38 @@ adm_status adm_create_batch(const double *V, const int64_t *v_off, const int32_t
                             const int64_t *f_off, int32_t n_mesh, int32_t var_dim,
                             adm_handle *out);
 
-/* Interaction terms over vertex pairs (Sec. 4.3) with the dynamic block
- * pattern they induce (Sec. 6.3, Alg. 1).  Replaces the pair set of the
- * pattern `energy` uses (membranes and ADM_MASS_SPRING: the triangle
- * pattern; ADM_SHELL and ADM_HINGE_BENDING: the shell pattern; one pattern
- * per handle) with n_pairs unordered vertex pairs (pairs: 2 * n_pairs int32,
- * host or device, copied), n_pairs = 0 clearing it.  Every later evaluation
- * of an energy on that pattern adds, per pair, the contact barrier of
- * Sec. 7.7, kappa/2 dhat area (s - 1) ln(s) h^2 with s = |x_i - x_j| / dhat,
- * for s < 1 (var_dim 3).
+/* Interaction terms (Sec. 4.3) with the dynamic block pattern they induce
+ * (Sec. 6.3, Alg. 1).  Replaces the interaction set of the pattern `energy`
+ * uses (membranes and ADM_MASS_SPRING: the triangle pattern; ADM_SHELL and
+ * ADM_HINGE_BENDING: the shell pattern; one pattern per handle) with
+ *   - n_pairs vertex-vertex terms: pairs, 2 * n_pairs int32 (i, j);
+ *   - n_vf vertex-face terms: vf, 4 * n_vf int32 (p, a, b, c), vertex p
+ *     against the triangle (a, b, c);
+ * (host or device, copied; both counts 0 clear the set).  Every later
+ * evaluation of an energy on that pattern adds, per term, the contact
+ * barrier of Sec. 7.7, kappa/2 dhat area (s - 1) ln(s) h^2 with s = d / dhat
+ * for s < 1 (var_dim 3): d = |x_i - x_j| for a pair, the distance from x_p to
+ * the triangle for a vertex-face term (its square written for the corner,
+ * edge or interior of the triangle nearest to x_p, decided in the precision
+ * of the pass).  A term listed twice counts twice.
  *
  * The block pattern is extended on the GPU: every row keeps its mesh
- * columns, in their order, followed by the columns of its new pair blocks in
- * ascending order; pairs whose blocks the mesh pattern has add no blocks.
- * adm_pattern then returns the extended pattern (device pointers valid until
- * the next call of this function), whose nnzb sizes the Hessian buffers.
- * Synchronous on `stream` (reads back the new block count).  Pair energies
- * count towards the total and towards the mesh of the first vertex (in
- * per-mesh energies their order of summation is not fixed).  The Hessian
- * and matrix-free passes run on the tiled kernel.  Errors: ADM_ERR_ARG
- * (vertex out of range, i == j, a pair given twice, dhat <= 0; the set is
- * then cleared), ADM_ERR_UNSUPPORTED (var_dim != 3, a second pattern kind). */
+ * columns, in their order, followed by the columns of the new blocks of the
+ * terms (each pair of a term's vertices), ascending and each once; blocks
+ * the mesh pattern has add nothing.  adm_pattern then returns the extended
+ * pattern (device pointers valid until the next call of this function),
+ * whose nnzb sizes the Hessian buffers.  Synchronous on `stream` (reads back
+ * the new block count).  Term energies count towards the total and towards
+ * the mesh of the term's first vertex (in per-mesh energies their order of
+ * summation is not fixed).  The Hessian and matrix-free passes run on the
+ * tiled kernel.  Errors: ADM_ERR_ARG (a vertex out of range or repeated
+ * within a term, dhat <= 0, a pattern past 2^31 blocks; the set is then
+ * cleared), ADM_ERR_UNSUPPORTED (var_dim != 3, a second pattern kind). */
+adm_status adm_set_contacts(adm_handle h, adm_energy energy, const int32_t *pairs, int64_t n_pairs,
+                            const int32_t *vf, int64_t n_vf, double kappa, double dhat, double area,
+                            double h_step, void *stream);
+
+/* adm_set_contacts with vertex-vertex pairs only. */
 adm_status adm_set_interactions(adm_handle h, adm_energy energy, const int32_t *pairs, int64_t n_pairs,
                                 double kappa, double dhat, double area, double h_step, void *stream);
 

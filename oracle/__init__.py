@@ -546,11 +546,12 @@ def extended_pattern(row_ptr, col, pairs, quads=()):
     return np.asarray(rp, dtype=np.int64), np.asarray(out, dtype=np.int64)
 
 
-def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col, quads=()):
+def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col, quads=(), project=False, eps=0.0):
     """Energy, gradient and Hessian blocks {(row, col): 3x3} of a mesh energy
     (base: energy, grad, vals over the pattern row_ptr, col) plus a
     vertex-vertex barrier per pair and a vertex-face barrier per element
-    (p, a, b, c), assembled by their plain definition."""
+    (p, a, b, c), assembled by their plain definition.  project: each
+    term's Hessian filtered first (spd_project, translations kept null)."""
     x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
     energy = base["energy"]
     grad = np.array(base["grad"], dtype=np.float64)
@@ -563,6 +564,8 @@ def add_interactions(base, x, pairs, kappa, dhat, area, h, row_ptr, col, quads=(
     terms += [(contact_vf(x[t[0]], x[t[1]], x[t[2]], x[t[3]], kappa, dhat, area, h), tuple(int(v) for v in t))
               for t in np.asarray(quads, dtype=np.int64).reshape(-1, 4)]
     for (f, g, H), verts in terms:
+        if project and f != 0.0:
+            H = spd_project(H, eps, keep=translations(len(verts), 3))
         energy += f
         for a, va in enumerate(verts):
             grad[va] += g[3 * a:3 * a + 3]

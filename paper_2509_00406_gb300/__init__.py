@@ -76,6 +76,7 @@ def lib():
         "adm_set_projection": (i32, [vp, i32, C.c_double]),
         "adm_set_inertia_target": (i32, [vp, vp]),
         "adm_set_interactions": (i32, [vp, i32, vp, i64, C.c_double, C.c_double, C.c_double, C.c_double, vp]),
+        "adm_set_contacts": (i32, [vp, i32, vp, i64, vp, i64, C.c_double, C.c_double, C.c_double, C.c_double, vp]),
         "adm_eval_batch": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp]),
         "adm_eval_batch_host": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
         "adm_eval_jacobian": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
@@ -212,13 +213,25 @@ class Mesh:
 
     def set_interactions(self, energy: int, pairs, kappa: float, dhat: float, area: float, h: float = 1.0,
                          stream=None):
-        """Vertex-pair contact terms (device or host int32 (n, 2), unique
-        unordered pairs) for the pattern of `energy`; n = 0 clears them.
-        The block pattern changes: query pattern() again."""
+        """Vertex-pair contact terms (device or host int32 (n, 2)) for the
+        pattern of `energy`; n = 0 clears them.  The block pattern changes:
+        query pattern() again."""
         n = 0 if pairs is None else int(pairs.shape[0])
         _check(lib().adm_set_interactions(self._h, energy, _ptr(pairs) if n else None, n, float(kappa),
                                           float(dhat), float(area), float(h), _stream(stream)),
                "adm_set_interactions")
+
+    def set_contacts(self, energy: int, pairs, vf, kappa: float, dhat: float, area: float, h: float = 1.0,
+                     stream=None):
+        """Vertex-vertex (int32 (n, 2)) and vertex-face (int32 (m, 4): p, a, b,
+        c) contact terms, device or host, for the pattern of `energy`; None
+        or empty arrays for none.  The block pattern changes: query
+        pattern() again."""
+        n = 0 if pairs is None else int(pairs.shape[0])
+        m = 0 if vf is None else int(vf.shape[0])
+        _check(lib().adm_set_contacts(self._h, energy, _ptr(pairs) if n else None, n, _ptr(vf) if m else None, m,
+                                      float(kappa), float(dhat), float(area), float(h), _stream(stream)),
+               "adm_set_contacts")
 
     def set_inertia_target(self, xhat):
         """Inertial target of the mass-spring energy (host, (nV, 3), copied)."""

@@ -646,19 +646,26 @@ adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const v
     return run_pass(h, a);
 }
 
-adm_status adm_set_interactions(adm_handle h, adm_energy energy, const int32_t *pairs, int64_t n_pairs,
-                                double kappa, double dhat, double area, double h_step, void *stream)
+adm_status adm_set_contacts(adm_handle h, adm_energy energy, const int32_t *pairs, int64_t n_pairs,
+                            const int32_t *vf, int64_t n_vf, double kappa, double dhat, double area, double h_step,
+                            void *stream)
 {
-    if (!h || n_pairs < 0 || (n_pairs > 0 && !pairs) || !(dhat > 0.0) || !std::isfinite(kappa) ||
-        !std::isfinite(area) || !std::isfinite(h_step))
+    if (!h || n_pairs < 0 || n_vf < 0 || (n_pairs > 0 && !pairs) || (n_vf > 0 && !vf) || !(dhat > 0.0) ||
+        !std::isfinite(kappa) || !std::isfinite(area) || !std::isfinite(h_step))
         return ADM_ERR_ARG;
     if (h->m.vdim != 3 || !energy_ok(energy, 3) || energy == ADM_ARAP2D_RESIDUAL || energy == ADM_UMBRELLA)
         return ADM_ERR_UNSUPPORTED;
     adm_status s = prepare(h, energy, true);
     if (s != ADM_OK) return s;
     drop_graphs(h);
-    return interactions_set(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI, pairs, n_pairs, kappa, dhat, area,
-                            h_step, as_stream(stream));
+    return interactions_set(h, needs_hinges(energy) ? PAT_SHELL : PAT_TRI, pairs, n_pairs, vf, n_vf, kappa, dhat,
+                            area, h_step, as_stream(stream));
+}
+
+adm_status adm_set_interactions(adm_handle h, adm_energy energy, const int32_t *pairs, int64_t n_pairs,
+                                double kappa, double dhat, double area, double h_step, void *stream)
+{
+    return adm_set_contacts(h, energy, pairs, n_pairs, nullptr, 0, kappa, dhat, area, h_step, stream);
 }
 
 adm_status adm_set_inertia_target(adm_handle h, const double *xhat_host)

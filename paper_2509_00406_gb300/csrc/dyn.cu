@@ -1,22 +1,25 @@
-// dyn.cu -- interaction terms over vertex pairs and the dynamic block
-// pattern they induce (Sec. 4.3, Sec. 6.3, Alg. 1).
+// dyn.cu -- interaction terms (vertex-vertex pairs, vertex-face elements)
+// and the dynamic block pattern they induce (Sec. 4.3, Sec. 6.3, Alg. 1).
 //
-// A pair set replaces the previous one and extends the mesh pattern on the
-// GPU, following Alg. 1: per-row counts (the mesh row plus the pair blocks
-// not already present), an exclusive scan into the new row pointer, a copy of
-// the mesh columns, and an atomic append of the new columns.  Each row's
-// appended run is then sorted, which fixes the layout (mesh columns first in
-// their order, new columns ascending) and exposes duplicate pairs.  Two
-// pattern buffers alternate.  The tiles of the mesh kernel keep their
-// per-row codes; only their row starts and shared-block indices are
-// remapped.  Evaluation adds, per pair, the contact barrier of Sec. 7.7 on
-// (x_i, x_j): the diagonal blocks and the gradient with atomic additions, the
-// new off-diagonal blocks with plain stores (one pair writes each), blocks
-// already in the mesh pattern with atomic additions.
+// An interaction set replaces the previous one and extends the mesh pattern
+// on the GPU, following Alg. 1.  Every term touches the blocks of its vertex
+// pairs (one pair for a vertex-vertex term, six for a vertex-face element),
+// the candidates.  Per-row counts (the mesh row plus the candidate blocks not
+// already present), an exclusive scan into a row pointer, a copy of the mesh
+// columns and an atomic append of the new ones give a pattern in which a
+// block touched by several terms appears several times; each row's appended
+// run is sorted, its distinct columns counted, and a second scan and copy
+// give the final pattern (mesh columns first in their order, new columns
+// ascending, each once).  Two pattern buffers alternate.  The tiles of the
+// mesh kernel keep their per-row codes; only their row starts and
+// shared-block indices are remapped.  Evaluation adds the barriers of
+// Sec. 7.7 with atomic additions after the tiled mesh pass: the new blocks
+// are zeroed first (several terms may share one).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "device_common.cuh"
@@ -177,29 +180,69 @@ __global__ void k_append(int64_t n, const int32_t *pairs, const int32_t *slot, c
     colx[rpx[j] + atomicAdd(&acc[j], 1)] = i;
 }
 
-// sort every row's appended run (insertion sort: runs are short); a repeated
-// column means a duplicate pair
-__global__ void k_sort_tails(int64_t nV, const int32_t *rp, const int32_t *rpx, int32_t *colx, int *status)
+// the six vertex pairs of every vertex-face element (p, a, b, c), in the
+// order (p,a) (p,b) (p,c) (a,b) (a,c) (b,c)
+__global__ void k_quad_pairs(int64_t nq, const int32_t *quads, int32_t *cand)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    int32_t v[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) v[a] = quads[4 * q + a];
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a + 1; b < 4; ++b, ++k) {
+            cand[12 * q + 2 * k] = v[a];
+            cand[12 * q + 2 * k + 1] = v[b];
+        }
+}
+
+// sort every row's appended run (insertion sort: runs are short) and count
+// its distinct columns: cnt = mesh row length + distinct new columns
+__global__ void k_sort_tails(int64_t nV, const int32_t *rp, const int32_t *rpt, int32_t *colt, int32_t *cnt)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == nV) cnt[r] = 0;
+    if (r >= nV) return;
+    const int32_t len = rp[r + 1] - rp[r];
+    const int32_t a = rpt[r] + len, b = rpt[r + 1];
+    for (int32_t k = a + 1; k < b; ++k) {
+        const int32_t c = colt[k];
+        int32_t q = k - 1;
+        while (q >= a && colt[q] > c) {
+            colt[q + 1] = colt[q];
+            --q;
+        }
+        colt[q + 1] = c;
+    }
+    int32_t u = b > a ? 1 : 0;
+    for (int32_t k = a + 1; k < b; ++k) u += colt[k] != colt[k - 1];
+    cnt[r] = len + u;
+}
+
+// final rows: the mesh columns, then the distinct new columns; every new
+// block's index into the list of new blocks (rows before r hold
+// rpx[r] - rp[r] of them)
+__global__ void k_copy_unique(int64_t nV, const int32_t *rp, const int32_t *rpt, const int32_t *colt,
+                              const int32_t *rpx, int32_t *colx, int32_t *newb)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nV) return;
-    const int32_t a = rpx[r] + (rp[r + 1] - rp[r]), b = rpx[r + 1];
-    for (int32_t k = a + 1; k < b; ++k) {
-        const int32_t c = colx[k];
-        int32_t q = k - 1;
-        while (q >= a && colx[q] > c) {
-            colx[q + 1] = colx[q];
-            --q;
-        }
-        colx[q + 1] = c;
+    const int32_t len = rp[r + 1] - rp[r], o = rpx[r], t = rpt[r];
+    for (int32_t k = 0; k < len; ++k) colx[o + k] = colt[t + k];
+    int32_t w = o + len, nb = rpx[r] - rp[r];
+    for (int32_t k = t + len; k < rpt[r + 1]; ++k) {
+        if (k > t + len && colt[k] == colt[k - 1]) continue;
+        colx[w] = colt[k];
+        newb[nb++] = w++;
     }
-    for (int32_t k = a + 1; k < b; ++k)
-        if (colx[k] == colx[k - 1]) atomicOr(status, ST_DUPLICATE);
 }
 
 // final block index of both blocks of every pair (bit 31: a mesh block)
 __global__ void k_slots(int64_t n, const int32_t *pairs, const int32_t *rp, const int32_t *rpx, const int32_t *colx,
-                        int32_t *slot)
+                        int32_t *slot, int *status)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -212,6 +255,7 @@ __global__ void k_slots(int64_t n, const int32_t *pairs, const int32_t *rp, cons
     }
     slot[2 * p] = find_col(colx, rpx[i] + (rp[i + 1] - rp[i]), rpx[i + 1], j);
     slot[2 * p + 1] = find_col(colx, rpx[j] + (rp[j + 1] - rp[j]), rpx[j + 1], i);
+    if (slot[2 * p] < 0 || slot[2 * p + 1] < 0) atomicOr(status, ST_DOMAIN);  // never a block index past the pattern
 }
 
 // tiles: row starts in the metadata blobs and shared-block indices follow the
@@ -235,113 +279,125 @@ __global__ void k_remap_zero(int64_t n, const int32_t *row, const int32_t *off, 
 
 // --------------------------------------------------------- evaluation --
 template <typename T>
-struct PairArgs {
+struct ContactArgs {
     int64_t n;
-    const int32_t *pairs, *slot, *rpx, *diag_off;
+    const int32_t *verts, *slot, *rpx, *diag_off;  // NV vertices and NV(NV-1) slots per term
     const T *x, *v;
     T *grad, *bsr, *hv;
-    double *pair_e;
+    double *term_e;
     T c, dhat, eps;
 };
 
-template <typename T, int MODE, bool PROJ>
-__global__ void __launch_bounds__(kDynThreads) k_pairs(PairArgs<T> A)
+// one thread per term: NV = 2 a vertex-vertex pair, NV = 4 a vertex-face
+// element; gradient, Hessian blocks and H v with atomic additions
+template <typename T, int NV, int MODE, bool PROJ>
+__global__ void __launch_bounds__(kDynThreads) k_contact(ContactArgs<T> A)
 {
+    constexpr int K = 3 * NV;
     const int64_t p = (int64_t)blockIdx.x * kDynThreads + threadIdx.x;
     if (p >= A.n) return;
-    const int32_t vid[2] = {A.pairs[2 * p], A.pairs[2 * p + 1]};
-    T x[6];
+    int32_t vid[NV];
+    T x[K];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < NV; ++a) {
+        vid[a] = A.verts[NV * p + a];
 #pragma unroll
         for (int d = 0; d < 3; ++d) x[3 * a + d] = A.x[3 * (int64_t)vid[a] + d];
-    Local<T, 6> L;
-    const bool active = contact_local<T, PROJ>(x, A.c, A.dhat, L, A.eps);
-    A.pair_e[p] = (double)L.f;
+    }
+    Local<T, K> L;
+    bool active;
+    if constexpr (NV == 2) active = contact_local<T, PROJ>(x, A.c, A.dhat, L, A.eps);
+    else active = vf_local<T, PROJ>(x, A.c, A.dhat, L, A.eps);
+    A.term_e[p] = (double)L.f;
+    if (!active) return;
     auto H = [&](int i, int j) { return L.H[i <= j ? hix(i, j) : hix(j, i)]; };
-    if (active && MODE >= MODE_GRAD && A.grad)
+    if (MODE >= MODE_GRAD && A.grad)
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) atomicAdd(A.grad + 3 * (int64_t)vid[a] + d, L.g[3 * a + d]);
+        for (int i = 0; i < K; ++i) atomicAdd(A.grad + 3 * (int64_t)vid[i / 3] + i % 3, L.g[i]);
     if (MODE == MODE_HVP) {
-        if (!active) return;
-        T vl[6];
+        T vl[K];
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+        for (int i = 0; i < K; ++i) vl[i] = A.v[3 * (int64_t)vid[i / 3] + i % 3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) vl[3 * a + d] = A.v[3 * (int64_t)vid[a] + d];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
+        for (int i = 0; i < K; ++i) {
             T y = -T(0);
 #pragma unroll
-            for (int j = 0; j < 6; ++j) y += H(i, j) * vl[j];
+            for (int j = 0; j < K; ++j) y += H(i, j) * vl[j];
             atomicAdd(A.hv + 3 * (int64_t)vid[i / 3] + i % 3, y);
         }
         return;
     }
-    if (MODE != MODE_HESS) return;
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {  // own blocks: the mesh pattern's diagonal, several writers
-        if (!active) break;
-        T *blk = A.bsr + 9 * ((int64_t)A.rpx[vid[a]] + A.diag_off[vid[a]]);
+    if (MODE != MODE_HESS || !A.bsr) return;
+    auto add_block = [&](T *blk, int a, int b) {
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int s = 0; s < 3; ++s) atomicAdd(blk + 3 * r + s, H(3 * a + r, 3 * a + s));
-    }
+            for (int s = 0; s < 3; ++s) atomicAdd(blk + 3 * r + s, H(3 * a + r, 3 * b + s));
+    };
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {  // (i, j) and (j, i)
-        const int32_t sl = A.slot[2 * p + a];
-        const bool mesh = (sl & 0x80000000) != 0;
-        T *blk = A.bsr + 9 * (int64_t)(sl & 0x7fffffff);
-        const int b = 1 - a;
+    for (int a = 0; a < NV; ++a) add_block(A.bsr + 9 * ((int64_t)A.rpx[vid[a]] + A.diag_off[vid[a]]), a, a);
+    int k = 0;
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+    for (int a = 0; a < NV; ++a)
 #pragma unroll
-            for (int s = 0; s < 3; ++s) {
-                const T val = H(3 * a + r, 3 * b + s);
-                if (mesh) {
-                    if (active) atomicAdd(blk + 3 * r + s, val);
-                } else {
-                    blk[3 * r + s] = val;  // the only writer of a new block (zero when inactive)
-                }
-            }
-    }
+        for (int b = a + 1; b < NV; ++b, ++k) {  // (a, b) and (b, a), pair order of the candidates
+            const int32_t *sl = A.slot + (int64_t)NV * (NV - 1) * p + 2 * k;
+            add_block(A.bsr + 9 * (int64_t)(sl[0] & 0x7fffffff), a, b);
+            add_block(A.bsr + 9 * (int64_t)(sl[1] & 0x7fffffff), b, a);
+        }
 }
 
-// pair energies: fixed-order sum into the total, and each pair's energy
+template <typename T>
+__global__ void k_zero_new(int64_t n, const int32_t *blocks, T *bsr)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < 9 * n) bsr[9 * (int64_t)blocks[k / 9] + k % 9] = T(0);
+}
+
+// term energies: fixed-order sum into the total, and each term's energy
 // credited to the mesh of its first vertex
 template <int THREADS>
-__global__ void k_pair_energy(int64_t n, const int32_t *pairs, const double *pair_e, int n_mesh,
+__global__ void k_term_energy(int64_t n, int stride, const int32_t *verts, const double *term_e, int n_mesh,
                               const int64_t *v_off, double *e_mesh, double *e_total)
 {
     double s = 0.0;
     for (int64_t p = threadIdx.x; p < n; p += THREADS) {
-        s += pair_e[p];
-        if (e_mesh && pair_e[p] != 0.0) {
+        s += term_e[p];
+        if (e_mesh && term_e[p] != 0.0) {
             int64_t lo = 0, hi = n_mesh;  // mesh k with v_off[k] <= i < v_off[k + 1]
-            const int64_t i = pairs[2 * p];
+            const int64_t i = verts[(int64_t)stride * p];
             while (hi - lo > 1) {
                 const int64_t m = (lo + hi) >> 1;
                 if (v_off[m] <= i) lo = m;
                 else hi = m;
             }
-            atomicAdd(&e_mesh[lo], pair_e[p]);
+            atomicAdd(&e_mesh[lo], term_e[p]);
         }
     }
     s = block_sum<THREADS>(s);
     if (threadIdx.x == 0 && e_total) *e_total += s;
 }
 
+template <typename T, int NV>
+void launch_contact(const ContactArgs<T> &A, int mode, bool proj, cudaStream_t s)
+{
+    const int nb = blocks_for(A.n);
+    if (mode == MODE_VALUE) k_contact<T, NV, MODE_VALUE, false><<<nb, kDynThreads, 0, s>>>(A);
+    else if (mode == MODE_GRAD) k_contact<T, NV, MODE_GRAD, false><<<nb, kDynThreads, 0, s>>>(A);
+    else if (mode == MODE_HESS && proj) k_contact<T, NV, MODE_HESS, true><<<nb, kDynThreads, 0, s>>>(A);
+    else if (mode == MODE_HESS) k_contact<T, NV, MODE_HESS, false><<<nb, kDynThreads, 0, s>>>(A);
+    else if (proj) k_contact<T, NV, MODE_HVP, true><<<nb, kDynThreads, 0, s>>>(A);
+    else k_contact<T, NV, MODE_HVP, false><<<nb, kDynThreads, 0, s>>>(A);
+}
+
 template <typename T>
-adm_status eval_pairs(adm_ctx *h, const EvalArgs &a, int mode)
+adm_status eval_contacts(adm_ctx *h, const EvalArgs &a, int mode)
 {
     Interactions &I = h->inter;
-    PairArgs<T> A;
-    A.n = I.n_pairs;
-    A.pairs = I.d_pairs;
-    A.slot = I.d_slot;
+    cudaStream_t s = a.stream;
+    if (mode == MODE_HESS && a.bsr && I.n_new > 0)
+        k_zero_new<T><<<blocks_for(9 * I.n_new), kDynThreads, 0, s>>>(I.n_new, I.d_new, (T *)a.bsr);
+    ContactArgs<T> A;
     A.rpx = I.d_rp[I.active];
     A.diag_off = I.d_diag_off;
     A.x = (const T *)a.x;
@@ -349,19 +405,24 @@ adm_status eval_pairs(adm_ctx *h, const EvalArgs &a, int mode)
     A.grad = (T *)a.grad;
     A.bsr = (T *)a.bsr;
     A.hv = (T *)a.hv;
-    A.pair_e = I.d_pair_e;
     A.c = (T)(0.5 * I.kappa * I.area * I.h * I.h);
     A.dhat = (T)I.dhat;
     A.eps = (T)h->proj_eps;
-    const int nb = blocks_for(A.n);
-    cudaStream_t s = a.stream;
     const bool proj = h->proj != 0;
-    if (mode == MODE_VALUE) k_pairs<T, MODE_VALUE, false><<<nb, kDynThreads, 0, s>>>(A);
-    else if (mode == MODE_GRAD) k_pairs<T, MODE_GRAD, false><<<nb, kDynThreads, 0, s>>>(A);
-    else if (mode == MODE_HESS && proj) k_pairs<T, MODE_HESS, true><<<nb, kDynThreads, 0, s>>>(A);
-    else if (mode == MODE_HESS) k_pairs<T, MODE_HESS, false><<<nb, kDynThreads, 0, s>>>(A);
-    else if (proj) k_pairs<T, MODE_HVP, true><<<nb, kDynThreads, 0, s>>>(A);
-    else k_pairs<T, MODE_HVP, false><<<nb, kDynThreads, 0, s>>>(A);
+    if (I.n_pairs > 0) {
+        A.n = I.n_pairs;
+        A.verts = I.d_cand;
+        A.slot = I.d_slot;
+        A.term_e = I.d_pair_e;
+        launch_contact<T, 2>(A, mode, proj, s);
+    }
+    if (I.n_vf > 0) {
+        A.n = I.n_vf;
+        A.verts = I.d_quads;
+        A.slot = I.d_slot + 2 * I.n_pairs;
+        A.term_e = I.d_vf_e;
+        launch_contact<T, 4>(A, mode, proj, s);
+    }
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
@@ -370,17 +431,21 @@ adm_status eval_pairs(adm_ctx *h, const EvalArgs &a, int mode)
 adm_status interactions_eval(adm_ctx *h, const EvalArgs &a, int mode)
 {
     const Interactions &I = h->inter;
-    if (I.kind < 0 || I.n_pairs == 0) return ADM_OK;
+    if (I.kind < 0 || I.n_terms() == 0) return ADM_OK;
     if (h->m.vdim != 3) return ADM_ERR_UNSUPPORTED;
-    return a.prec == ADM_FP32 ? eval_pairs<float>(h, a, mode) : eval_pairs<double>(h, a, mode);
+    return a.prec == ADM_FP32 ? eval_contacts<float>(h, a, mode) : eval_contacts<double>(h, a, mode);
 }
 
 adm_status interactions_energy(adm_ctx *h, const EvalArgs &a)
 {
     const Interactions &I = h->inter;
-    if (I.kind < 0 || I.n_pairs == 0 || (!a.energy_total && !a.energy_per_mesh)) return ADM_OK;
-    k_pair_energy<1024><<<1, 1024, 0, a.stream>>>(I.n_pairs, I.d_pairs, I.d_pair_e, h->m.n_mesh, I.d_v_off,
-                                                  a.energy_per_mesh, a.energy_total);
+    if (I.kind < 0 || I.n_terms() == 0 || (!a.energy_total && !a.energy_per_mesh)) return ADM_OK;
+    if (I.n_pairs > 0)
+        k_term_energy<1024><<<1, 1024, 0, a.stream>>>(I.n_pairs, 2, I.d_cand, I.d_pair_e, h->m.n_mesh, I.d_v_off,
+                                                       a.energy_per_mesh, a.energy_total);
+    if (I.n_vf > 0)
+        k_term_energy<1024><<<1, 1024, 0, a.stream>>>(I.n_vf, 4, I.d_quads, I.d_vf_e, h->m.n_mesh, I.d_v_off,
+                                                       a.energy_per_mesh, a.energy_total);
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
@@ -422,8 +487,21 @@ adm_status interactions_retile(adm_ctx *h, int kind, cudaStream_t s)
     return cudaStreamSynchronize(s) == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
-adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t n, double kappa, double dhat,
-                            double area, double hstep, cudaStream_t s)
+// device buffer of at least n elements (contents not kept when it grows)
+template <typename P>
+adm_status ensure(adm_ctx *h, P **buf, int64_t &cap, int64_t n)
+{
+    if (n <= cap && *buf) return ADM_OK;
+    release(h, *buf);
+    *buf = nullptr;
+    cap = 0;
+    adm_status st = alloc(h, buf, (size_t)std::max<int64_t>(n, 1) * sizeof(P));
+    if (st == ADM_OK) cap = std::max<int64_t>(n, 1);
+    return st;
+}
+
+adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t n, const int32_t *quads, int64_t nq,
+                            double kappa, double dhat, double area, double hstep, cudaStream_t s)
 {
     Interactions &I = h->inter;
     const Pattern &P = h->pat[kind];
@@ -443,6 +521,7 @@ adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t 
         if ((st = alloc(h, &I.d_v_off, (h->m.n_mesh + 1) * 8)) != ADM_OK) return st;
         if ((st = alloc(h, &I.d_cnt, (nV + 1) * 4)) != ADM_OK) return st;
         if ((st = alloc(h, &I.d_acc, nV * 4)) != ADM_OK) return st;
+        if ((st = alloc(h, &I.d_rp_tmp, (nV + 1) * 4)) != ADM_OK) return st;
         const int nsb = blocks_for(nV + 1, kDynThreads * kScanItems);
         if ((st = alloc(h, &I.d_bsum, nsb * 4)) != ADM_OK) return st;
         for (int b = 0; b < 2; ++b)
@@ -452,60 +531,64 @@ adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t 
             return ADM_ERR_CUDA;
         I.kind = kind;
     }
-    // room for the pairs and the extended pattern (the inactive buffer)
-    if (n > I.cap_pairs) {
-        release(h, I.d_pairs);
-        release(h, I.d_slot);
-        release(h, I.d_pair_e);
-        I.d_pairs = I.d_slot = nullptr;
-        I.d_pair_e = nullptr;
-        I.cap_pairs = 0;
-        if ((st = alloc(h, &I.d_pairs, n * 8)) != ADM_OK) return st;
-        if ((st = alloc(h, &I.d_slot, n * 8)) != ADM_OK) return st;
-        if ((st = alloc(h, &I.d_pair_e, n * 8)) != ADM_OK) return st;
-        I.cap_pairs = n;
-    }
+    // room for the terms, their candidate pairs and the extended pattern
+    // (the inactive buffer); the pattern before deduplication bounds the final one
+    const int64_t nc = n + 6 * nq;
+    if (P.nnzb + 2 * nc > (int64_t)INT32_MAX) return ADM_ERR_ARG;  // block indices are int32
     const int nxt = 1 - I.active;
-    const int64_t need = P.nnzb + 2 * n;
-    if (need > I.col_cap[nxt]) {
-        release(h, I.d_col[nxt]);
-        I.d_col[nxt] = nullptr;
-        if ((st = alloc(h, &I.d_col[nxt], need * 4)) != ADM_OK) return st;
-        I.col_cap[nxt] = need;
-    }
-    if (n > 0 && cudaMemcpyAsync(I.d_pairs, pairs, n * 8, cudaMemcpyDefault, s) != cudaSuccess) return ADM_ERR_CUDA;
+    if ((st = ensure(h, &I.d_cand, I.cap_cand, 2 * nc)) != ADM_OK) return st;
+    if ((st = ensure(h, &I.d_slot, I.cap_slot, 2 * nc)) != ADM_OK) return st;
+    if ((st = ensure(h, &I.d_pair_e, I.cap_pairs, n)) != ADM_OK) return st;
+    if ((st = ensure(h, &I.d_quads, I.cap_vf, 4 * nq)) != ADM_OK) return st;
+    if ((st = ensure(h, &I.d_vf_e, I.cap_vf_e, nq)) != ADM_OK) return st;
+    if ((st = ensure(h, &I.d_new, I.cap_new, 2 * nc)) != ADM_OK) return st;
+    if ((st = ensure(h, &I.d_col_tmp, I.cap_col_tmp, P.nnzb + 2 * nc)) != ADM_OK) return st;
+    if ((st = ensure(h, &I.d_col[nxt], I.col_cap[nxt], P.nnzb + 2 * nc)) != ADM_OK) return st;
+    if (n > 0 && cudaMemcpyAsync(I.d_cand, pairs, n * 8, cudaMemcpyDefault, s) != cudaSuccess) return ADM_ERR_CUDA;
+    if (nq > 0 && cudaMemcpyAsync(I.d_quads, quads, nq * 16, cudaMemcpyDefault, s) != cudaSuccess)
+        return ADM_ERR_CUDA;
     if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
     int32_t *rpx = I.d_rp[nxt], *colx = I.d_col[nxt];
-    // (1) counts, (2) scan, (3) copy, (4) append, then sorted tails and slots
-    k_row_len<<<blocks_for(nV + 1), kDynThreads, 0, s>>>(nV, P.d_row_ptr, I.d_cnt);
-    if (n > 0)
-        k_count<<<blocks_for(n), kDynThreads, 0, s>>>(n, I.d_pairs, nV, P.d_row_ptr, P.d_col, I.d_cnt, I.d_slot,
-                                                       h->d_status);
     const int nsb = blocks_for(nV + 1, kDynThreads * kScanItems);
-    k_scan_local<kDynThreads><<<nsb, kDynThreads, 0, s>>>(nV + 1, I.d_cnt, rpx, I.d_bsum);
-    k_scan_sums<1024><<<1, 1024, 0, s>>>(nsb, I.d_bsum);
-    k_scan_add<<<blocks_for(nV + 1), kDynThreads, 0, s>>>(nV + 1, rpx, I.d_bsum);
-    k_copy_rows<<<blocks_for(nV), kDynThreads, 0, s>>>(nV, P.d_row_ptr, P.d_col, rpx, colx, I.d_acc);
-    if (n > 0) {
-        k_append<<<blocks_for(n), kDynThreads, 0, s>>>(n, I.d_pairs, I.d_slot, rpx, I.d_acc, colx);
-        k_sort_tails<<<blocks_for(nV), kDynThreads, 0, s>>>(nV, P.d_row_ptr, rpx, colx, h->d_status);
-        k_slots<<<blocks_for(n), kDynThreads, 0, s>>>(n, I.d_pairs, P.d_row_ptr, rpx, colx, I.d_slot);
-    }
+    auto scan = [&](int32_t *out) {
+        k_scan_local<kDynThreads><<<nsb, kDynThreads, 0, s>>>(nV + 1, I.d_cnt, out, I.d_bsum);
+        k_scan_sums<1024><<<1, 1024, 0, s>>>(nsb, I.d_bsum);
+        k_scan_add<<<blocks_for(nV + 1), kDynThreads, 0, s>>>(nV + 1, out, I.d_bsum);
+    };
+    // (1) counts, (2) scan, (3) copy, (4) append; then sorted, deduplicated
+    // tails, a second scan and copy, and the slots of every candidate
+    if (nq > 0) k_quad_pairs<<<blocks_for(nq), kDynThreads, 0, s>>>(nq, I.d_quads, I.d_cand + 2 * n);
+    k_row_len<<<blocks_for(nV + 1), kDynThreads, 0, s>>>(nV, P.d_row_ptr, I.d_cnt);
+    if (nc > 0)
+        k_count<<<blocks_for(nc), kDynThreads, 0, s>>>(nc, I.d_cand, nV, P.d_row_ptr, P.d_col, I.d_cnt, I.d_slot,
+                                                        h->d_status);
+    scan(I.d_rp_tmp);
+    k_copy_rows<<<blocks_for(nV), kDynThreads, 0, s>>>(nV, P.d_row_ptr, P.d_col, I.d_rp_tmp, I.d_col_tmp, I.d_acc);
+    if (nc > 0) k_append<<<blocks_for(nc), kDynThreads, 0, s>>>(nc, I.d_cand, I.d_slot, I.d_rp_tmp, I.d_acc,
+                                                                 I.d_col_tmp);
+    k_sort_tails<<<blocks_for(nV + 1), kDynThreads, 0, s>>>(nV, P.d_row_ptr, I.d_rp_tmp, I.d_col_tmp, I.d_cnt);
+    scan(rpx);
+    k_copy_unique<<<blocks_for(nV), kDynThreads, 0, s>>>(nV, P.d_row_ptr, I.d_rp_tmp, I.d_col_tmp, rpx, colx,
+                                                          I.d_new);
+    if (nc > 0) k_slots<<<blocks_for(nc), kDynThreads, 0, s>>>(nc, I.d_cand, P.d_row_ptr, rpx, colx, I.d_slot,
+                                                        h->d_status);
     int32_t total = 0;
     int status = 0;
     if (cudaMemcpyAsync(&total, rpx + nV, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return ADM_ERR_CUDA;
-    if (status != 0) {  // an invalid or repeated pair: back to the mesh pattern, no pairs
-        if (n > 0) interactions_set(h, kind, nullptr, 0, kappa, dhat, area, hstep, s);
+    if (status != 0) {  // an invalid vertex or a repeated one within a term: back to the mesh pattern
+        if (nc > 0) interactions_set(h, kind, nullptr, 0, nullptr, 0, kappa, dhat, area, hstep, s);
         return ADM_ERR_ARG;
     }
     // switch: tiles follow the new pattern
     I.active = nxt;
     if ((st = interactions_retile(h, kind, s)) != ADM_OK) return st;
     I.nnzb = total;
+    I.n_new = total - P.nnzb;
     I.n_pairs = n;
+    I.n_vf = nq;
     I.kappa = kappa;
     I.dhat = dhat;
     I.area = area;

@@ -19,7 +19,7 @@ enum PatternKind { PAT_TRI = 0, PAT_SHELL = 1, PAT_RING = 2, PAT_COUNT = 3 };
 constexpr int kMaxValence = 12;  // one-ring terms: vertices of higher valence are rejected
 
 // device status bits (latched by kernels with atomicOr)
-enum StatusBits { ST_DOMAIN = 1, ST_TIMEOUT = 2, ST_DUPLICATE = 4 };
+enum StatusBits { ST_DOMAIN = 1, ST_TIMEOUT = 2 };
 
 struct DevMem {
     void *p = nullptr;
@@ -138,20 +138,27 @@ struct TileSet {
 // Sec. 4.3, Sec. 6.3, Alg. 1)
 struct Interactions {
     int kind = -1;                  // pattern kind extended, -1: none
-    int64_t n_pairs = 0, cap_pairs = 0;
-    int32_t *d_pairs = nullptr;     // 2 per pair
-    int32_t *d_slot = nullptr;      // 2 per pair: blocks (i,j), (j,i); bit 31: block of the mesh pattern
-    double *d_pair_e = nullptr;     // energy per pair of the last pass
+    int64_t n_pairs = 0, n_vf = 0;  // vertex-vertex pairs, vertex-face elements
+    int64_t cap_pairs = 0, cap_vf = 0, cap_vf_e = 0, cap_cand = 0, cap_slot = 0;  // buffer capacities (elements)
+    int32_t *d_cand = nullptr;      // candidate vertex pairs: the pairs, then 6 per vertex-face element
+    int32_t *d_slot = nullptr;      // 2 per candidate: blocks (i,j), (j,i); bit 31: block of the mesh pattern
+    int32_t *d_quads = nullptr;     // 4 per vertex-face element: p, a, b, c
+    double *d_pair_e = nullptr, *d_vf_e = nullptr;  // energy per term of the last pass
     int32_t *d_rp[2] = {nullptr, nullptr}, *d_col[2] = {nullptr, nullptr};  // double-buffered pattern
     int64_t col_cap[2] = {0, 0};
     int active = 0;
     int64_t nnzb = 0;
+    int32_t *d_new = nullptr;       // blocks the mesh pattern lacks (zeroed before every Hessian pass)
+    int64_t n_new = 0, cap_new = 0;
     int32_t *d_cnt = nullptr, *d_acc = nullptr, *d_bsum = nullptr;  // scratch of the insertion
+    int32_t *d_rp_tmp = nullptr, *d_col_tmp = nullptr;              // pattern with repeated new columns
+    int64_t cap_col_tmp = 0;
     int32_t *d_diag_off = nullptr;  // position of v's own block in its mesh-pattern row
     int32_t *d_zero_row = nullptr, *d_zero_off = nullptr;  // shared blocks of the tiles as (row, offset)
     int64_t zero_for_build = -1;    // tile build the (row, offset) list belongs to
     int64_t *d_v_off = nullptr;     // mesh vertex offsets
     double kappa = 0.0, dhat = 0.0, area = 0.0, h = 1.0;
+    int64_t n_terms() const { return n_pairs + n_vf; }
 };
 
 struct EnergyParams {
@@ -274,8 +281,8 @@ adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
 // vertex-pair interactions (dyn.cu): replace the pair set of pattern `kind`
 // and extend its block pattern on the GPU; evaluate the pairs of a pass
 // (after the tiled kernel) and add their energies (after the reduction)
-adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t n, double kappa, double dhat,
-                            double area, double hstep, cudaStream_t s);
+adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t n, const int32_t *quads, int64_t nq,
+                            double kappa, double dhat, double area, double hstep, cudaStream_t s);
 adm_status interactions_eval(adm_ctx *h, const EvalArgs &a, int mode);
 adm_status interactions_retile(adm_ctx *h, int kind, cudaStream_t s);  // after a tile rebuild
 // per-vertex one-ring terms (ring.cu): the whole pass of ADM_UMBRELLA

@@ -160,7 +160,7 @@ adm_status launch_eval(adm_ctx *h, const EvalArgs &a)
 {
     if (a.energy == ADM_UMBRELLA) return eval_ring(h, a);
     // the matrix-free product and Hessian filtering are implemented by the tiled kernel only
-    if (h->assembler == 0 || a.hv || (h->proj && a.bsr) || a.energy == ADM_MASS_SPRING || h->inter.n_pairs > 0)
+    if (h->assembler == 0 || a.hv || (h->proj && a.bsr) || a.energy == ADM_MASS_SPRING || h->inter.n_terms() > 0)
         return a.prec == ADM_FP32 ? eval_tiled<float>(h, a) : eval_tiled<double>(h, a);
     return a.prec == ADM_FP32 ? eval_atomic<float>(h, a) : eval_atomic<double>(h, a);
 }

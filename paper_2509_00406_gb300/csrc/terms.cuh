@@ -344,6 +344,115 @@ ADM_HD bool contact_local(const T (&x)[6], T c, T dhat, Local<T, 6> &out, T eps 
     return true;
 }
 
+// vertex-face contact (Sec. 7.7) on (p, a, b, c), differentiated in
+// r = p - a, e1 = b - a, e2 = c - a: C = {{1, 0, 0}, {-1, -1, -1}, {0, 1, 0}, {0, 0, 1}}
+struct VFEdges {
+    static constexpr int NV = 4, NE = 3;
+    ADM_HD static constexpr int C(int a, int p) { return edge_coef(0x404A81u, a * NE + p); }
+};
+static_assert(VFEdges::C(0, 0) == 1 && VFEdges::C(0, 1) == 0 && VFEdges::C(0, 2) == 0 && VFEdges::C(1, 0) == -1 &&
+                  VFEdges::C(1, 1) == -1 && VFEdges::C(1, 2) == -1 && VFEdges::C(2, 0) == 0 &&
+                  VFEdges::C(2, 1) == 1 && VFEdges::C(2, 2) == 0 && VFEdges::C(3, 0) == 0 &&
+                  VFEdges::C(3, 1) == 0 && VFEdges::C(3, 2) == 1,
+              "vertex-face edge map");
+
+// part of the triangle nearest to p: 0, 1, 2 the corners a, b, c; 3, 4, 5
+// the edges ab, ac, bc; 6 the interior.  Signs of the projections of p onto
+// the edge directions from each corner (the corners' and edges' Voronoi
+// regions in the triangle's plane), in the precision of the term.
+template <typename T>
+ADM_HD int vf_region(const T (&r)[3], const T (&e1)[3], const T (&e2)[3])
+{
+    auto dot = [](const T *u, const T *w) { return u[0] * w[0] + u[1] * w[1] + u[2] * w[2]; };
+    const T d1 = dot(e1, r), d2 = dot(e2, r);
+    if (d1 <= T(0) && d2 <= T(0)) return 0;
+    const T rb[3] = {r[0] - e1[0], r[1] - e1[1], r[2] - e1[2]};
+    const T d3 = dot(e1, rb), d4 = dot(e2, rb);
+    if (d3 >= T(0) && d4 <= d3) return 1;
+    if (d1 * d4 - d3 * d2 <= T(0) && d1 >= T(0) && d3 <= T(0)) return 3;
+    const T rc[3] = {r[0] - e2[0], r[1] - e2[1], r[2] - e2[2]};
+    const T d5 = dot(e1, rc), d6 = dot(e2, rc);
+    if (d6 >= T(0) && d5 <= d6) return 2;
+    if (d5 * d2 - d1 * d6 <= T(0) && d2 >= T(0) && d6 <= T(0)) return 4;
+    if (d3 * d6 - d5 * d4 <= T(0) && d4 >= d3 && d5 >= d6) return 5;
+    return 6;
+}
+
+// squared distance from a point at w (relative to the edge start) to the
+// line of direction t: |w|^2 - (w.t)^2 / |t|^2
+template <class W0, class W1, class W2, class D0, class D1, class D2>
+ADM_HD auto line_sq(const W0 &w0, const W1 &w1, const W2 &w2, const D0 &t0, const D1 &t1, const D2 &t2)
+{
+    return sq(w0) + sq(w1) + sq(w2) - sq(w0 * t0 + w1 * t1 + w2 * t2) / (sq(t0) + sq(t1) + sq(t2));
+}
+
+// barrier c dhat (s - 1) ln s of s = sqrt(q) / dhat, composed with q(x);
+// false (nothing stored) when q is outside (0, dhat^2)
+template <typename T, class Q>
+ADM_HD bool barrier_of_sq(const Q &q, T c, T dhat, Local<T, 9> &le)
+{
+    if (!(q.v < dhat * dhat) || !(q.v > T(0))) return false;
+    auto Q1 = seed<T, 1, 0>(q.v);
+    auto sv = sqrt(Q1) * (T(1) / dhat);
+    auto p = (sv - T(1)) * log(sv) * (c * dhat);
+    store_local(compose(p, q), le);
+    return true;
+}
+
+// vertex-face contact barrier: c dhat (s - 1) ln s, s = d / dhat < 1, d the
+// distance from p to triangle (a, b, c), c = kappa/2 A_c h^2; the squared
+// distance written for the region nearest to p (corner: |p - v|^2; edge:
+// distance to its line; interior: ((p - a).n)^2 / |n|^2, n = e1 x e2).
+// x = (p, a, b, c), 3 coordinates each.  Returns false outside dhat (out zeroed).
+template <typename T, bool PROJ = false>
+ADM_HD bool vf_local(const T (&x)[12], T c, T dhat, Local<T, 12> &out, T eps = T(0))
+{
+    T r[3], e1[3], e2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        r[d] = x[d] - x[3 + d];
+        e1[d] = x[6 + d] - x[3 + d];
+        e2[d] = x[9 + d] - x[3 + d];
+    }
+    const int reg = vf_region(r, e1, e2);
+    auto R0 = seed<T, 9, 0>(r[0]);
+    auto R1 = seed<T, 9, 1>(r[1]);
+    auto R2 = seed<T, 9, 2>(r[2]);
+    auto U0 = seed<T, 9, 3>(e1[0]);
+    auto U1 = seed<T, 9, 4>(e1[1]);
+    auto U2 = seed<T, 9, 5>(e1[2]);
+    auto W0 = seed<T, 9, 6>(e2[0]);
+    auto W1 = seed<T, 9, 7>(e2[1]);
+    auto W2 = seed<T, 9, 8>(e2[2]);
+    Local<T, 9> le;
+    bool active;
+    switch (reg) {
+    case 0: active = barrier_of_sq(sq(R0) + sq(R1) + sq(R2), c, dhat, le); break;
+    case 1: active = barrier_of_sq(sq(R0 - U0) + sq(R1 - U1) + sq(R2 - U2), c, dhat, le); break;
+    case 2: active = barrier_of_sq(sq(R0 - W0) + sq(R1 - W1) + sq(R2 - W2), c, dhat, le); break;
+    case 3: active = barrier_of_sq(line_sq(R0, R1, R2, U0, U1, U2), c, dhat, le); break;
+    case 4: active = barrier_of_sq(line_sq(R0, R1, R2, W0, W1, W2), c, dhat, le); break;
+    case 5: active = barrier_of_sq(line_sq(R0 - U0, R1 - U1, R2 - U2, W0 - U0, W1 - U1, W2 - U2), c, dhat, le); break;
+    default: {
+        auto n0 = U1 * W2 - U2 * W1;
+        auto n1 = U2 * W0 - U0 * W2;
+        auto n2 = U0 * W1 - U1 * W0;
+        active = barrier_of_sq(sq(n0 * R0 + n1 * R1 + n2 * R2) / (sq(n0) + sq(n1) + sq(n2)), c, dhat, le);
+    }
+    }
+    if (!active) {
+        out.f = T(0);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) out.g[i] = T(0);
+#pragma unroll
+        for (int k = 0; k < 78; ++k) out.H[k] = T(0);
+        return false;
+    }
+    if constexpr (PROJ) project_edges<VFEdges, 3>(le.H, eps);
+    expand_edges<VFEdges, 3>(le, out);
+    return true;
+}
+
 // per-vertex inertia and gravity: m/2 |x - xhat|^2 - h2 m g.x (Hessian m I,
 // semidefinite, so filtering never changes it)
 template <typename T>

@@ -450,7 +450,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     launch_tiled<T>(a.energy, mode, h->proj != 0, ts.n_tiles, smem, s, A);
     tm.end(ADM_STAGE_TILED);
     if (cudaGetLastError() != cudaSuccess) return ADM_ERR_CUDA;
-    const bool pairs = h->inter.kind == (hin ? PAT_SHELL : PAT_TRI) && h->inter.n_pairs > 0;
+    const bool pairs = h->inter.kind == (hin ? PAT_SHELL : PAT_TRI) && h->inter.n_terms() > 0;
     if (pairs) {
         tm.begin(ADM_STAGE_PAIRS);
         adm_status st = interactions_eval(h, a, mode);

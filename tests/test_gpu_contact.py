@@ -179,7 +179,7 @@ def test_contact_argument_errors():
     rp0 = m.pattern(adm.STVK_MEMBRANE)[2]
     brp, bcol = oracle.pattern(len(V), F)
     far = next(j for j in range(len(V)) if j not in bcol[brp[0]:brp[1]])   # not adjacent to vertex 0
-    for bad in (np.array([[0, 0]]), np.array([[0, 99999]]), np.array([[0, far], [far, 0]])):
+    for bad in (np.array([[0, 0]]), np.array([[0, 99999]]), np.array([[far, -1]])):
         with pytest.raises(adm.AdmError):
             m.set_interactions(adm.STVK_MEMBRANE, bad.astype(np.int32), KAPPA, DHAT, AREA, HSTEP)
         assert m.pattern(adm.STVK_MEMBRANE)[2] == rp0            # cleared back to the mesh pattern
