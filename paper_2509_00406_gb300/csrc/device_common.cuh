@@ -14,7 +14,11 @@ namespace adm {
 
 constexpr int kThreads = 128;      // per-element kernels
 constexpr int kRedThreads = 256;   // reductions
-constexpr int kTileThreads = 256;  // tiled kernel
+// tiled kernel: FP32 tiles run 512 threads at two blocks per SM (64
+// registers, 32 warps per SM); FP64 and the Hessian-filtering variants keep
+// 256 threads and the full register file
+template <typename T, bool PROJ>
+constexpr int tile_threads() { return (sizeof(T) == 4 && !PROJ) ? 512 : 256; }
 
 // passive, gradient, full Hessian, matrix-free Hessian-vector product
 enum Mode { MODE_VALUE = 0, MODE_GRAD = 1, MODE_HESS = 2, MODE_HVP = 3 };
@@ -89,10 +93,9 @@ struct TriTraits {
 
 // local f, g, H of one triangle term; false outside the energy's domain
 // (PROJ: with the local Hessian filtered, spd.cuh)
-template <typename T, int ENERGY, bool PROJ = false>
+template <typename T, int ENERGY, bool PROJ = false, class Out>
 __device__ __forceinline__ bool tri_term(const T (&x)[TriTraits<ENERGY>::K], const T (&D)[4], T area,
-                                         const TermConsts<T> &c, Local<T, TriTraits<ENERGY>::K> &L,
-                                         const float *tab = nullptr)
+                                         const TermConsts<T> &c, Out &L, const float *tab = nullptr)
 {
     bool ok = true;
     if constexpr (ENERGY == ADM_SYMDIR2D) {
@@ -107,7 +110,7 @@ __device__ __forceinline__ bool tri_term(const T (&x)[TriTraits<ENERGY>::K], con
     } else if constexpr (ENERGY == ADM_MLP_MEMBRANE) {
         membrane_local<T, PsiTable<T>, PROJ>(x, D, PsiTable<T>{tab, c.thick * area}, L, c.eps);
     }
-    return ok && isfinite(L.f);
+    return ok && isfinite(local_f(L));
 }
 
 inline bool has_tris(int energy)

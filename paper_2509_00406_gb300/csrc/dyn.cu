@@ -258,6 +258,30 @@ __global__ void k_slots(int64_t n, const int32_t *pairs, const int32_t *rp, cons
     if (slot[2 * p] < 0 || slot[2 * p + 1] < 0) atomicOr(status, ST_DOMAIN);  // never a block index past the pattern
 }
 
+// position of every vertex's own block in its mesh-pattern row
+__global__ void k_diag_off(int64_t nV, const int32_t *rp, const int32_t *col, int32_t *doff)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < nV) doff[v] = find_col(col, rp[v], rp[v + 1], (int32_t)v) - rp[v];
+}
+
+// (row, offset in the row) of mesh-pattern block indices
+__global__ void k_block_rows(int64_t n, const int32_t *blocks, int64_t nV, const int32_t *rp, int32_t *row,
+                             int32_t *off)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t b = blocks[k];
+    int64_t lo = 0, hi = nV;  // row r with rp[r] <= b < rp[r + 1]
+    while (hi - lo > 1) {
+        const int64_t m = (lo + hi) >> 1;
+        if (rp[m] <= b) lo = m;
+        else hi = m;
+    }
+    row[k] = (int32_t)lo;
+    off[k] = b - rp[lo];
+}
+
 // tiles: row starts in the metadata blobs and shared-block indices follow the
 // extended pattern (the per-row codes are unchanged: mesh columns come first)
 __global__ void k_remap_tiles(int32_t n_tiles, const int32_t *hdr, const int32_t *foot, const int64_t *meta_off,
@@ -457,26 +481,19 @@ adm_status interactions_retile(adm_ctx *h, int kind, cudaStream_t s)
     TileSet &ts = h->tiles[kind];
     if (!ts.built) return ADM_OK;
     // the tiles' shared blocks as (row, offset in the mesh row), once per tile
-    // build; then their indices in the active pattern
-    const size_t nz = ts.zero_blocks.size();
+    // build (the tile build has just uploaded them as mesh-pattern indices);
+    // then their indices in the active pattern
+    const int64_t nz = (int64_t)ts.zero_blocks.size();
     if (I.zero_for_build != ts.build_id) {
-        std::vector<int32_t> zr(nz), zo(nz);
-        for (size_t k = 0; k < nz; ++k) {
-            const int32_t b = ts.zero_blocks[k];
-            const int32_t r =
-                (int32_t)(std::upper_bound(P.row_ptr.begin(), P.row_ptr.end(), b) - P.row_ptr.begin()) - 1;
-            zr[k] = r;
-            zo[k] = b - P.row_ptr[r];
-        }
         release(h, I.d_zero_row);
         release(h, I.d_zero_off);
         I.d_zero_row = I.d_zero_off = nullptr;
         adm_status st;
         if ((st = alloc(h, &I.d_zero_row, nz * 4)) != ADM_OK) return st;
         if ((st = alloc(h, &I.d_zero_off, nz * 4)) != ADM_OK) return st;
-        if (nz && (cudaMemcpy(I.d_zero_row, zr.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-                   cudaMemcpy(I.d_zero_off, zo.data(), nz * 4, cudaMemcpyHostToDevice) != cudaSuccess))
-            return ADM_ERR_CUDA;
+        if (nz)
+            k_block_rows<<<blocks_for(nz), kDynThreads, 0, s>>>(nz, ts.d_zero_blocks, h->m.nV, P.d_row_ptr,
+                                                                 I.d_zero_row, I.d_zero_off);
         I.zero_for_build = ts.build_id;
     }
     const int32_t *rpx = I.d_rp[I.active];
@@ -512,11 +529,6 @@ adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t 
     // one-time data of this pattern kind
     if (I.kind != kind) {
         if (I.kind >= 0) return ADM_ERR_UNSUPPORTED;  // one pattern kind per handle
-        std::vector<int32_t> doff(nV);
-        for (int64_t v = 0; v < nV; ++v) {
-            const auto b = P.col.begin() + P.row_ptr[v], e = P.col.begin() + P.row_ptr[v + 1];
-            doff[v] = (int32_t)(std::lower_bound(b, e, (int32_t)v) - b);
-        }
         if ((st = alloc(h, &I.d_diag_off, nV * 4)) != ADM_OK) return st;
         if ((st = alloc(h, &I.d_v_off, (h->m.n_mesh + 1) * 8)) != ADM_OK) return st;
         if ((st = alloc(h, &I.d_cnt, (nV + 1) * 4)) != ADM_OK) return st;
@@ -526,9 +538,10 @@ adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t 
         if ((st = alloc(h, &I.d_bsum, nsb * 4)) != ADM_OK) return st;
         for (int b = 0; b < 2; ++b)
             if ((st = alloc(h, &I.d_rp[b], (nV + 1) * 4)) != ADM_OK) return st;
-        if (cudaMemcpy(I.d_diag_off, doff.data(), nV * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(I.d_v_off, h->m.v_off.data(), (h->m.n_mesh + 1) * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemcpyAsync(I.d_v_off, h->m.v_off.data(), (h->m.n_mesh + 1) * 8, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
             return ADM_ERR_CUDA;
+        k_diag_off<<<blocks_for(nV), kDynThreads, 0, s>>>(nV, P.d_row_ptr, P.d_col, I.d_diag_off);
         I.kind = kind;
     }
     // room for the terms, their candidate pairs and the extended pattern

@@ -184,11 +184,81 @@ ADM_HD void expand_edges(const Local<T, E::NE * VD> &le, Local<T, E::NV * VD> &o
         }
 }
 
+// A term's derivatives kept in its edge-vector coordinates.  The vertex-DOF
+// gradient and Hessian entries are formed on demand (local_g, local_H) by the
+// sums expand_edges does, in the same order, so a consumer that adds them
+// into accumulators one at a time never holds the expanded Hessian.
+template <class E, int VD, typename T>
+struct EdgeLocal {
+    using Edges = E;
+    static constexpr int vd = VD;
+    Local<T, E::NE * VD> e;
+};
+template <class Out>
+struct IsEdgeLocal : std::false_type {};
+template <class E, int VD, typename T>
+struct IsEdgeLocal<EdgeLocal<E, VD, T>> : std::true_type {};
+
+// hand a term's edge-coordinate result to its output: kept as it is, or
+// expanded to the vertex DOFs
+template <class E, int VD, typename T, class Out>
+ADM_HD void emit_local(const Local<T, E::NE * VD> &le, Out &out)
+{
+    if constexpr (IsEdgeLocal<Out>::value) {
+        static_assert(std::is_same_v<typename Out::Edges, E> && Out::vd == VD, "edge map of the term");
+        out.e = le;
+    } else {
+        expand_edges<E, VD>(le, out);
+    }
+}
+
+template <typename T, int K>
+ADM_HD T local_f(const Local<T, K> &L) { return L.f; }
+template <typename T, int K>
+ADM_HD T local_g(const Local<T, K> &L, int i) { return L.g[i]; }
+template <typename T, int K>
+ADM_HD T local_H(const Local<T, K> &L, int i, int j) { return L.H[i <= j ? hix(i, j) : hix(j, i)]; }
+
+template <class E, int VD, typename T>
+ADM_HD T local_f(const EdgeLocal<E, VD, T> &L) { return L.e.f; }
+
+template <class E, int VD, typename T>
+ADM_HD T local_g(const EdgeLocal<E, VD, T> &L, int i)
+{
+    const int a = i / VD, d = i % VD;
+    T acc = -T(0);
+#pragma unroll
+    for (int p = 0; p < E::NE; ++p) {
+        if (E::C(a, p) == 0) continue;
+        acc = E::C(a, p) > 0 ? acc + L.e.g[p * VD + d] : acc - L.e.g[p * VD + d];
+    }
+    return acc;
+}
+
+template <class E, int VD, typename T>
+ADM_HD T local_H(const EdgeLocal<E, VD, T> &L, int i0, int j0)
+{
+    const int i = i0 <= j0 ? i0 : j0, j = i0 <= j0 ? j0 : i0;  // the upper entry, as expand_edges forms it
+    const int a = i / VD, r = i % VD, b = j / VD, s = j % VD;
+    T acc = -T(0);
+#pragma unroll
+    for (int p = 0; p < E::NE; ++p)
+#pragma unroll
+        for (int q = 0; q < E::NE; ++q) {
+            const int c = E::C(a, p) * E::C(b, q);
+            if (c == 0) continue;
+            const int ii = p * VD + r, jj = q * VD + s;
+            const T h = L.e.H[ii <= jj ? hix(ii, jj) : hix(jj, ii)];
+            acc = c > 0 ? acc + h : acc - h;
+        }
+    return acc;
+}
+
 // ------------------------------------------------------ triangle, VD = 3 --
 // C = F^T F of F = [x1-x0, x2-x0] Dinv;  Dinv row-major (d00, d01, d10, d11).
 // Differentiated in the edge vectors u = x1 - x0, w = x2 - x0.
-template <typename T, class Psi, bool PROJ = false>
-ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Local<T, 9> &out, T eps = T(0))
+template <typename T, class Psi, bool PROJ = false, class Out>
+ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Out &out, T eps = T(0))
 {
     auto u0 = seed<T, 6, 0>(x[3] - x[0]);
     auto u1 = seed<T, 6, 1>(x[4] - x[1]);
@@ -209,12 +279,12 @@ ADM_HD void membrane_local(const T (&x)[9], const T (&D)[4], const Psi &psi, Loc
     Local<T, 6> le;
     store_local(compose(p, c11, c22, c12), le);
     if constexpr (PROJ) project_edges<TriEdges, 3>(le.H, eps);
-    expand_edges<TriEdges, 3>(le, out);
+    emit_local<TriEdges, 3>(le, out);
 }
 
 // area term (test energy of Sec. 7.6), in the edge vectors u, w
-template <typename T, bool PROJ = false>
-ADM_HD void area_local(const T (&x)[9], Local<T, 9> &out, T eps = T(0))
+template <typename T, bool PROJ = false, class Out>
+ADM_HD void area_local(const T (&x)[9], Out &out, T eps = T(0))
 {
     auto u0 = seed<T, 6, 0>(x[3] - x[0]);
     auto u1 = seed<T, 6, 1>(x[4] - x[1]);
@@ -229,14 +299,14 @@ ADM_HD void area_local(const T (&x)[9], Local<T, 9> &out, T eps = T(0))
     Local<T, 6> le;
     store_local(compose(p, uu, ww, uw), le);
     if constexpr (PROJ) project_edges<TriEdges, 3>(le.H, eps);
-    expand_edges<TriEdges, 3>(le, out);
+    emit_local<TriEdges, 3>(le, out);
 }
 
 // ------------------------------------------------------ triangle, VD = 2 --
 // C = J^T J of the UV Jacobian J = [b-a, c-a] Dinv, differentiated in the
 // edge vectors b - a, c - a; returns det J (value)
-template <typename T, class Psi, bool PROJ = false>
-ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> &out, T eps = T(0))
+template <typename T, class Psi, bool PROJ = false, class Out>
+ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Out &out, T eps = T(0))
 {
     auto u0 = seed<T, 4, 0>(x[2] - x[0]);  // b - a
     auto u1 = seed<T, 4, 1>(x[3] - x[1]);
@@ -253,7 +323,7 @@ ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> 
     Local<T, 4> le;
     store_local(compose(p, c11, c22, c12), le);
     if constexpr (PROJ) project_edges<TriEdges, 2>(le.H, eps);
-    expand_edges<TriEdges, 2>(le, out);
+    emit_local<TriEdges, 2>(le, out);
     return j00.v * j11.v - j01.v * j10.v;
 }
 
@@ -261,8 +331,8 @@ ADM_HD T uv_local(const T (&x)[6], const T (&D)[4], const Psi &psi, Local<T, 6> 
 // hinge (x0, x1, xa, xb), face A = (x0, x1, xa), face B = (x1, x0, xb);
 // psi = w (theta - thetabar)^2, differentiated in the edge vectors e, u, v.
 // Returns false for a degenerate hinge.
-template <typename T, bool PROJ = false>
-ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out, T eps = T(0))
+template <typename T, bool PROJ = false, class Out>
+ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Out &out, T eps = T(0))
 {
     auto e0 = seed<T, 9, 0>(x[3] - x[0]);  // e = x1 - x0
     auto e1 = seed<T, 9, 1>(x[4] - x[1]);
@@ -291,7 +361,7 @@ ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out, T 
     Local<T, 9> le;
     store_local(compose(p, ee, eu, ev, uv, det), le);
     if constexpr (PROJ) project_edges<HingeEdges, 3>(le.H, eps);
-    expand_edges<HingeEdges, 3>(le, out);
+    emit_local<HingeEdges, 3>(le, out);
     return true;
 }
 
@@ -299,8 +369,8 @@ ADM_HD bool hinge_local(const T (&x)[12], T thetabar, T w, Local<T, 12> &out, T 
 // spring of edge (x0, x1), squared rest length l2, times h^2:
 // kh2 l2/2 (|d|^2 / l2 - 1)^2 = kh2 / (2 l2) (|d|^2 - l2)^2, d = x0 - x1,
 // differentiated in d
-template <typename T, bool PROJ = false>
-ADM_HD void spring_local(const T (&x)[6], T l2, T kh2, Local<T, 6> &out, T eps = T(0))
+template <typename T, bool PROJ = false, class Out>
+ADM_HD void spring_local(const T (&x)[6], T l2, T kh2, Out &out, T eps = T(0))
 {
     auto d0 = seed<T, 3, 0>(x[0] - x[3]);
     auto d1 = seed<T, 3, 1>(x[1] - x[4]);
@@ -311,7 +381,7 @@ ADM_HD void spring_local(const T (&x)[6], T l2, T kh2, Local<T, 6> &out, T eps =
     Local<T, 3> le;
     store_local(compose(p, q), le);
     if constexpr (PROJ) project_edges<SpringEdges, 3>(le.H, eps);
-    expand_edges<SpringEdges, 3>(le, out);
+    emit_local<SpringEdges, 3>(le, out);
 }
 
 // vertex-vertex contact barrier (Sec. 7.7): c dhat (s - 1) ln s for

@@ -49,24 +49,26 @@ struct TiledArgs {
     const T *edge_l2, *vert_area3, *xhat;
 };
 
-template <typename T, int VD, int NV, int NP, int K>
-__device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint16_t (&lid)[NV],
-                                                const uint16_t (&slot)[NP], const int (&pr)[NP][2], T *gacc,
-                                                T *dacc, T *pacc, int mode)
+// the element's gradient and Hessian blocks added into the footprint
+// accumulators (LT: a Local in vertex DOFs or an EdgeLocal, whose entries are
+// formed as they are added)
+template <typename T, int VD, int NV, int NP, class LT>
+__device__ __forceinline__ void tile_accumulate(const LT &L, const uint16_t (&lid)[NV], const uint16_t (&slot)[NP],
+                                                const int (&pr)[NP][2], T *gacc, T *dacc, T *pacc, int mode)
 {
     constexpr int NDS = AccStride<VD>::D, NPS = AccStride<VD>::P;
-    auto H = [&](int i, int j) { return L.H[i <= j ? hix(i, j) : hix(j, i)]; };
 #pragma unroll
     for (int a = 0; a < NV; ++a)
 #pragma unroll
-        for (int d = 0; d < VD; ++d) atomicAdd(gacc + lid[a] * VD + d, L.g[a * VD + d]);
+        for (int d = 0; d < VD; ++d) atomicAdd(gacc + lid[a] * VD + d, local_g(L, a * VD + d));
     if (mode != MODE_HESS) return;
 #pragma unroll
     for (int a = 0; a < NV; ++a)
 #pragma unroll
         for (int s = 0; s < VD; ++s)
 #pragma unroll
-            for (int r = 0; r <= s; ++r) atomicAdd(dacc + lid[a] * NDS + hix(r, s), H(a * VD + r, a * VD + s));
+            for (int r = 0; r <= s; ++r)
+                atomicAdd(dacc + lid[a] * NDS + hix(r, s), local_H(L, a * VD + r, a * VD + s));
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int a = pr[p][0], b = pr[p][1];
@@ -76,7 +78,7 @@ __device__ __forceinline__ void tile_accumulate(const Local<T, K> &L, const uint
         for (int r = 0; r < VD; ++r)
 #pragma unroll
             for (int s = 0; s < VD; ++s)
-                atomicAdd(dst + r * VD + s, fwd ? H(a * VD + r, b * VD + s) : H(b * VD + r, a * VD + s));
+                atomicAdd(dst + r * VD + s, fwd ? local_H(L, a * VD + r, b * VD + s) : local_H(L, b * VD + r, a * VD + s));
     }
 }
 
@@ -95,15 +97,60 @@ __device__ __forceinline__ void tile_hvp(const Local<T, K> &L, const uint16_t (&
     for (int i = 0; i < K; ++i) {
         T y = -T(0);
 #pragma unroll
-        for (int j = 0; j < K; ++j) y += L.H[i <= j ? hix(i, j) : hix(j, i)] * vl[j];
+        for (int j = 0; j < K; ++j) y += local_H(L, i, j) * vl[j];
         atomicAdd(hacc + lid[i / VD] * VD + i % VD, y);
         atomicAdd(gacc + lid[i / VD] * VD + i % VD, L.g[i]);
     }
 }
 
-// FP32 tiles are register-capped at two resident blocks per SM (128 registers
-// for 256 threads); FP64, and the Hessian-filtering variant (PROJ: an
-// in-register eigensolve per element), keep one block and the full register file
+// the same in edge-vector coordinates: v_e = C^T v (per edge the signed sum
+// of its vertices' v), y_e = H_e v_e, y = C y_e
+template <typename T, int VD, int NV, class E>
+__device__ __forceinline__ void tile_hvp(const EdgeLocal<E, VD, T> &L, const uint16_t (&lid)[NV], const T *vs,
+                                         T *gacc, T *hacc)
+{
+    static_assert(E::NV == NV, "vertices of the edge map");
+    constexpr int NE = E::NE, KE = NE * VD;
+    T ve[KE], ye[KE];
+#pragma unroll
+    for (int p = 0; p < NE; ++p)
+#pragma unroll
+        for (int d = 0; d < VD; ++d) {
+            T acc = -T(0);
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+                if (E::C(a, p) == 0) continue;
+                const T va = vs[lid[a] * VD + d];
+                acc = E::C(a, p) > 0 ? acc + va : acc - va;
+            }
+            ve[p * VD + d] = acc;
+        }
+#pragma unroll
+    for (int i = 0; i < KE; ++i) {
+        T y = -T(0);
+#pragma unroll
+        for (int j = 0; j < KE; ++j) y += L.e.H[i <= j ? hix(i, j) : hix(j, i)] * ve[j];
+        ye[i] = y;
+    }
+#pragma unroll
+    for (int a = 0; a < NV; ++a)
+#pragma unroll
+        for (int d = 0; d < VD; ++d) {
+            T acc = -T(0);
+#pragma unroll
+            for (int p = 0; p < NE; ++p) {
+                if (E::C(a, p) == 0) continue;
+                acc = E::C(a, p) > 0 ? acc + ye[p * VD + d] : acc - ye[p * VD + d];
+            }
+            atomicAdd(hacc + lid[a] * VD + d, acc);
+            atomicAdd(gacc + lid[a] * VD + d, local_g(L, a * VD + d));
+        }
+}
+
+// FP32 tiles are register-capped at two resident blocks per SM (64 registers
+// for 512 threads); FP64, and the Hessian-filtering variant (PROJ: an
+// in-register eigensolve per element), keep one block of 256 threads and the
+// full register file
 template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS, bool PROJ = false>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_tiled(TiledArgs<T> A)
 {
@@ -171,14 +218,14 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
 #pragma unroll
             for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nT + e];
             const T area = A.tri_rest[4 * A.nT + e];
-            Local<T, K> L;
+            EdgeLocal<TriEdges, VD, T> L;
             if (!tri_term<T, ENERGY, PROJ>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * e : nullptr)) {
                 atomicOr(A.status, ST_DOMAIN);
                 continue;
             }
-            fe += (double)L.f;
-            if (MODE == MODE_HVP) tile_hvp<T, VD, 3, K>(L, lid, vs, gacc, hacc);
-            else if (MODE >= MODE_GRAD) tile_accumulate<T, VD, 3, 3, K>(L, lid, slot, TP, gacc, dacc, pacc, MODE);
+            fe += (double)local_f(L);
+            if (MODE == MODE_HVP) tile_hvp<T, VD, 3>(L, lid, vs, gacc, hacc);
+            else if (MODE >= MODE_GRAD) tile_accumulate<T, VD, 3, 3>(L, lid, slot, TP, gacc, dacc, pacc, MODE);
         }
     }
     if constexpr (HINGES) {
@@ -197,14 +244,14 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
                 for (int d = 0; d < 3; ++d) x[a * 3 + d] = xs[lid[a] * 3 + d];
             const T thetabar = A.hinge_rest[e];
             const T w = A.c.kbh2 * A.hinge_rest[A.nH + e];
-            Local<T, 12> L;
-            if (!(hinge_local<T, PROJ>(x, thetabar, w, L, A.c.eps) && isfinite(L.f))) {
+            EdgeLocal<HingeEdges, 3, T> L;
+            if (!(hinge_local<T, PROJ>(x, thetabar, w, L, A.c.eps) && isfinite(local_f(L)))) {
                 atomicOr(A.status, ST_DOMAIN);
                 continue;
             }
-            fe += (double)L.f;
-            if (MODE == MODE_HVP) tile_hvp<T, 3, 4, 12>(L, lid, vs, gacc, hacc);
-            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 4, 6, 12>(L, lid, slot, HP, gacc, dacc, pacc, MODE);
+            fe += (double)local_f(L);
+            if (MODE == MODE_HVP) tile_hvp<T, 3, 4>(L, lid, vs, gacc, hacc);
+            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 4, 6>(L, lid, slot, HP, gacc, dacc, pacc, MODE);
         }
     }
     if constexpr (ENERGY == ADM_MASS_SPRING) {
@@ -220,15 +267,15 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_
             for (int a = 0; a < 2; ++a)
 #pragma unroll
                 for (int d = 0; d < 3; ++d) x[a * 3 + d] = xs[lid[a] * 3 + d];
-            Local<T, 6> L;
+            EdgeLocal<SpringEdges, 3, T> L;
             spring_local<T, PROJ>(x, A.edge_l2[e], A.c.kh2, L, A.c.eps);
-            if (!isfinite(L.f)) {
+            if (!isfinite(local_f(L))) {
                 atomicOr(A.status, ST_DOMAIN);
                 continue;
             }
-            fe += (double)L.f;
-            if (MODE == MODE_HVP) tile_hvp<T, 3, 2, 6>(L, lid, vs, gacc, hacc);
-            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 2, 1, 6>(L, lid, slot, EP, gacc, dacc, pacc, MODE);
+            fe += (double)local_f(L);
+            if (MODE == MODE_HVP) tile_hvp<T, 3, 2>(L, lid, vs, gacc, hacc);
+            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 2, 1>(L, lid, slot, EP, gacc, dacc, pacc, MODE);
         }
         for (int i = threadIdx.x; i < n_vert; i += THREADS) {
             const int64_t e = (int64_t)vert_begin + i;
@@ -343,21 +390,22 @@ __global__ void k_zero_shared(const int32_t *blocks, int64_t nb, const int32_t *
 template <typename T, int MODE, bool PROJ>
 void launch_tiled_mode(int energy, int n_tiles, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
 {
+    constexpr int TT = tile_threads<T, PROJ>();
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<n_tiles, kTileThreads, smem, s>>>(A);
+        kern<<<n_tiles, TT, smem, s>>>(A);
     };
     switch (energy) {
-    case ADM_SYMDIR2D: go(k_tiled<T, ADM_SYMDIR2D, true, false, MODE, kTileThreads, PROJ>); break;
-    case ADM_STVK_MEMBRANE: go(k_tiled<T, ADM_STVK_MEMBRANE, true, false, MODE, kTileThreads, PROJ>); break;
-    case ADM_NH_MEMBRANE: go(k_tiled<T, ADM_NH_MEMBRANE, true, false, MODE, kTileThreads, PROJ>); break;
-    case ADM_AREA: go(k_tiled<T, ADM_AREA, true, false, MODE, kTileThreads, PROJ>); break;
+    case ADM_SYMDIR2D: go(k_tiled<T, ADM_SYMDIR2D, true, false, MODE, TT, PROJ>); break;
+    case ADM_STVK_MEMBRANE: go(k_tiled<T, ADM_STVK_MEMBRANE, true, false, MODE, TT, PROJ>); break;
+    case ADM_NH_MEMBRANE: go(k_tiled<T, ADM_NH_MEMBRANE, true, false, MODE, TT, PROJ>); break;
+    case ADM_AREA: go(k_tiled<T, ADM_AREA, true, false, MODE, TT, PROJ>); break;
     case ADM_MLP_MEMBRANE:
-        if constexpr (sizeof(T) == 4) go(k_tiled<T, ADM_MLP_MEMBRANE, true, false, MODE, kTileThreads, PROJ>);
+        if constexpr (sizeof(T) == 4) go(k_tiled<T, ADM_MLP_MEMBRANE, true, false, MODE, TT, PROJ>);
         break;
-    case ADM_SHELL: go(k_tiled<T, ADM_SHELL, true, true, MODE, kTileThreads, PROJ>); break;
-    case ADM_HINGE_BENDING: go(k_tiled<T, ADM_STVK_MEMBRANE, false, true, MODE, kTileThreads, PROJ>); break;
-    case ADM_MASS_SPRING: go(k_tiled<T, ADM_MASS_SPRING, false, false, MODE, kTileThreads, PROJ>); break;
+    case ADM_SHELL: go(k_tiled<T, ADM_SHELL, true, true, MODE, TT, PROJ>); break;
+    case ADM_HINGE_BENDING: go(k_tiled<T, ADM_STVK_MEMBRANE, false, true, MODE, TT, PROJ>); break;
+    case ADM_MASS_SPRING: go(k_tiled<T, ADM_MASS_SPRING, false, false, MODE, TT, PROJ>); break;
     default: break;
     }
 }
