@@ -453,29 +453,26 @@ ADM_HD auto compose(const SHD<T, M, PG, PL, PH> &psi, const Q0 &q0, const Q &...
         });
         r.g[i] = acc;
     }
-    // K[b][i] = sum_a psi_ab dq_a[i]
-    T K[M][N];
-    sfor<0, M>([&](auto B) {
-        constexpr int b = decltype(B)::value;
+    // Hessian: sum_a psi_a d2q_a + sum_b K[b][i] dq_b^T, row by row with
+    // K[b][i] = sum_a psi_ab dq_a[i] formed for row i only (M values live
+    // instead of M N)
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            if (!gbit(G, i)) continue;
+    for (int i = 0; i < N; ++i) {
+        T K[M];
+        sfor<0, M>([&](auto B) {
+            constexpr int b = decltype(B)::value;
             T acc = -T(0);
             sfor<0, M>([&](auto A) {
                 constexpr int a = decltype(A)::value;
                 const auto &qa = pick<a>(q0, qs...);
                 using QA = std::decay_t<decltype(qa)>;
                 constexpr int k = a <= b ? hix(a, b) : hix(b, a);
-                if (hbit(PL, PH, k) && gbit(QA::gm, i)) acc += psi.h[k] * qa.g[i];
+                if (gbit(G, i) && hbit(PL, PH, k) && gbit(QA::gm, i)) acc += psi.h[k] * qa.g[i];
             });
-            K[b][i] = acc;
-        }
-    });
-    // Hessian: sum_a psi_a d2q_a + sum_b K[b] dq_b^T
+            K[b] = acc;
+        });
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-#pragma unroll
-        for (int i = 0; i <= j; ++i) {
+        for (int j = i; j < N; ++j) {
             const int k = hix(i, j);
             if (!hbit(L, H, k)) continue;
             T acc = -T(0);
@@ -484,7 +481,7 @@ ADM_HD auto compose(const SHD<T, M, PG, PL, PH> &psi, const Q0 &q0, const Q &...
                 const auto &qa = pick<a>(q0, qs...);
                 using QA = std::decay_t<decltype(qa)>;
                 if (gbit(PG, a) && hbit(QA::hl, QA::hh, k)) acc += psi.g[a] * qa.h[k];
-                if (gbit(G, i) && gbit(QA::gm, j)) acc += K[a][i] * qa.g[j];
+                if (gbit(G, i) && gbit(QA::gm, j)) acc += K[a] * qa.g[j];
             });
             r.h[k] = acc;
         }
