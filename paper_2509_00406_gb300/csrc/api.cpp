@@ -430,6 +430,7 @@ adm_status adm_create_batch(const double *V, const int64_t *v_off, const int32_t
         if (s == ADM_OK) s = upload(h, &h->chunks.d_end, ce.data(), ce.size() * 4);
         if (s == ADM_OK) s = upload(h, &h->chunks.d_mesh_chunk_off, co.data(), co.size() * 4);
         if (s == ADM_OK) s = dev_alloc(h, &h->d_gpart, cb.size() * sizeof(double));
+        if (s == ADM_OK) s = dev_alloc(h, &h->d_emesh, (size_t)n_mesh * sizeof(double));
         h->chunks.built = true;
     }
     if (s == ADM_OK) s = build_pattern(h, PAT_TRI);
@@ -747,10 +748,69 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
         if ((s = dev_alloc(h, &h->d_stage_gn, m.n_mesh * sizeof(double))) != ADM_OK) return s;
     }
     cudaStream_t st = h->own_stream;
-    if (cudaMemcpyAsync(h->d_stage_x, x_host, xb, cudaMemcpyHostToDevice, st) != cudaSuccess) return ADM_ERR_CUDA;
-    s = adm_eval_batch(h, energy, prec, h->d_stage_x, h->d_stage_e, h->d_stage_gn, h->d_stage_grad,
-                       h->d_stage_bsr, st);
-    if (s != ADM_OK) return s;
+    // A batch on the tiled path is fed in mesh ranges: range k's copy runs on
+    // the copy stream while the kernels of the ranges before it run, and its
+    // own kernels wait for it.
+    const int kSplit = 4;
+    const bool tiled = h->assembler == 0 || energy == ADM_MASS_SPRING || h->proj;
+    const bool split = m.n_mesh >= 2 && tiled && h->inter.n_terms() == 0 && energy != ADM_MLP_MEMBRANE &&
+                       energy != ADM_UMBRELLA && energy != ADM_ARAP2D_RESIDUAL && energy_ok(energy, m.vdim);
+    if (split) {
+        if (!h->copy_stream && cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return ADM_ERR_CUDA;
+        const int n_split = std::min<int>(kSplit, (int)m.n_mesh);
+        for (cudaStream_t &cs : h->split_stream)
+            if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ADM_ERR_CUDA;
+        if (!h->split_start && cudaEventCreateWithFlags(&h->split_start, cudaEventDisableTiming) != cudaSuccess)
+            return ADM_ERR_CUDA;
+        for (auto *evs : {&h->split_ev, &h->split_done})
+            while ((int)evs->size() < n_split) {
+                cudaEvent_t e;
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return ADM_ERR_CUDA;
+                evs->push_back(e);
+            }
+        // the first range is half the size of the others, so that the
+        // kernels start after a short copy: boundaries at (2k - 1) / (2n - 1)
+        // of the vertices, each range at least one mesh
+        h->split_mesh.assign(1, 0);
+        for (int k = 1; k < n_split; ++k) {
+            const int64_t target = m.nV * (2 * k - 1) / (2 * n_split - 1);
+            int32_t mk = (int32_t)(std::lower_bound(m.v_off.begin(), m.v_off.end(), target) - m.v_off.begin());
+            mk = std::max(mk, h->split_mesh.back() + 1);
+            mk = std::min(mk, (int32_t)m.n_mesh - (n_split - k));
+            h->split_mesh.push_back(mk);
+        }
+        h->split_mesh.push_back((int32_t)m.n_mesh);
+        const size_t vb = es * m.vdim;  // bytes of one vertex of x
+        for (int k = 0; k < n_split; ++k) {
+            const int64_t v0 = m.v_off[h->split_mesh[k]], v1 = m.v_off[h->split_mesh[k + 1]];
+            if (cudaMemcpyAsync((char *)h->d_stage_x + v0 * vb, (const char *)x_host + v0 * vb, (v1 - v0) * vb,
+                                cudaMemcpyHostToDevice, h->copy_stream) != cudaSuccess ||
+                cudaEventRecord(h->split_ev[k], h->copy_stream) != cudaSuccess)
+                return ADM_ERR_CUDA;
+        }
+        EvalArgs a;
+        a.energy = energy;
+        a.prec = prec;
+        a.vdim = m.vdim;
+        a.x = h->d_stage_x;
+        a.grad = h->d_stage_grad;
+        a.bsr = h->d_stage_bsr;
+        a.energy_total = nullptr;
+        a.energy_per_mesh = h->d_stage_e;
+        a.gnorm_per_mesh = h->d_stage_gn;
+        a.stream = st;
+        a.n_split = n_split;
+        a.split_mesh = h->split_mesh.data();
+        a.split_ready = h->split_ev.data();
+        if ((s = launch_eval(h, a)) != ADM_OK) return s;
+    } else {
+        if (cudaMemcpyAsync(h->d_stage_x, x_host, xb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return ADM_ERR_CUDA;
+        s = adm_eval_batch(h, energy, prec, h->d_stage_x, h->d_stage_e, h->d_stage_gn, h->d_stage_grad,
+                           h->d_stage_bsr, st);
+        if (s != ADM_OK) return s;
+    }
     if (energy_per_mesh_host &&
         cudaMemcpyAsync(energy_per_mesh_host, h->d_stage_e, m.n_mesh * sizeof(double), cudaMemcpyDeviceToHost,
                         st) != cudaSuccess)
@@ -962,6 +1022,18 @@ void adm_destroy(adm_handle h)
     }
     drop_graphs(h);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+    }
+    for (cudaStream_t cs : h->split_stream)
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+    for (cudaEvent_t e : h->split_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->split_done) cudaEventDestroy(e);
+    if (h->split_start) cudaEventDestroy(h->split_start);
     for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
     for (void *p : h->owned) cudaFree(p);
     delete h;

@@ -206,6 +206,7 @@ struct adm_ctx {
     double *d_epart = nullptr;      // energy partial per element block
     size_t epart_cap = 0;
     double *d_gpart = nullptr;      // sum of squares partial per gradient chunk
+    double *d_emesh = nullptr;      // per-mesh energies when only the total is asked for
     double *d_mesh_energy = nullptr;  // n_mesh
     int *d_status = nullptr;
     std::map<int, adm::EnergyParams> params;
@@ -222,6 +223,12 @@ struct adm_ctx {
     double *d_stage_e = nullptr, *d_stage_gn = nullptr;
     size_t stage_x_bytes = 0, stage_grad_bytes = 0, stage_bsr_bytes = 0;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;         // host-to-device copies of the mesh ranges
+    std::vector<cudaEvent_t> split_ev;          // one per mesh range: its x has arrived
+    std::vector<int32_t> split_mesh;            // first mesh of every range, n_split + 1
+    cudaStream_t split_stream[2] = {nullptr, nullptr};  // the ranges' kernels, alternating
+    std::vector<cudaEvent_t> split_done;        // one per mesh range: its kernels have run
+    cudaEvent_t split_start = nullptr;          // the pass's stream has reached the ranges
     // CUDA graphs of whole passes (ADM_OPT_GRAPH)
     int use_graph = 0;
     std::vector<adm::GraphEntry> graphs;
@@ -276,6 +283,12 @@ struct EvalArgs {
     cudaStream_t stream;
     const void *v = nullptr;   // matrix-free mode: direction (device, like x)
     void *hv = nullptr;        // matrix-free mode: H v (device, like the gradient)
+    // host-fed pass: x arrives in n_split mesh ranges (range k = meshes
+    // [split_mesh[k], split_mesh[k + 1]), host array), and the kernels of
+    // range k wait for split_ready[k]; 0 = x is resident
+    int n_split = 0;
+    const int32_t *split_mesh = nullptr;
+    const cudaEvent_t *split_ready = nullptr;
 };
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
 // vertex-pair interactions (dyn.cu): replace the pair set of pattern `kind`

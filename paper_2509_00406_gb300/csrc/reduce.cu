@@ -10,41 +10,69 @@ __global__ void __launch_bounds__(THREADS) k_sumsq(const T *g, const int32_t *cb
                                                    double *gpart)
 {
     double s = 0.0;
-    for (int64_t i = cb[blockIdx.x] + threadIdx.x; i < ce[blockIdx.x]; i += THREADS) {
-        double v = (double)g[i];
+    const int64_t e = ce[blockIdx.x];
+    int64_t i = cb[blockIdx.x] + threadIdx.x;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 entries: squares, and sums of four of them, in FP32 (relative
+        // error below 2^-22 per group of four), groups accumulated in FP64.
+        // The FP64 pipe of this GPU runs at a small fraction of the FP32
+        // rate; it now does one add per four entries instead of a convert
+        // and a fused multiply-add per entry.
+        for (; i + 3 * THREADS < e; i += 4 * THREADS) {
+            const float v0 = g[i], v1 = g[i + THREADS], v2 = g[i + 2 * THREADS], v3 = g[i + 3 * THREADS];
+            s += (double)((v0 * v0 + v1 * v1) + (v2 * v2 + v3 * v3));
+        }
+    }
+    for (; i < e; i += THREADS) {
+        const double v = (double)g[i];
         s += v * v;
     }
     s = block_sum<THREADS>(s);
     if (threadIdx.x == 0) gpart[blockIdx.x] = s;
 }
 
-// per mesh: energy = sum of its element-block partials (triangle blocks, then
-// hinge blocks), gnorm = sqrt(sum of its chunk partials); total = sum over
-// meshes.  One block, fixed order.
+// per mesh, one warp: energy = sum of its element-block partials (triangle
+// blocks, then hinge blocks), gnorm = sqrt(sum of its chunk partials).  The
+// lanes stride over the partials and a fixed shuffle tree adds them, so the
+// result does not depend on scheduling.
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;  // valid in lane 0
+}
+
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_finalize(int n_mesh, const double *epart,
-                                                      const int32_t *tri_off, const int32_t *hinge_off,
-                                                      int32_t hinge_base, const double *gpart,
-                                                      const int32_t *chunk_off, double *e_mesh,
-                                                      double *gn_mesh, double *e_total)
+__global__ void __launch_bounds__(THREADS) k_mesh_sums(int n_mesh, const double *epart, const int32_t *tri_off,
+                                                       const int32_t *hinge_off, int32_t hinge_base,
+                                                       const double *gpart, const int32_t *chunk_off,
+                                                       double *e_mesh, double *gn_mesh)
+{
+    const int m = blockIdx.x * (THREADS / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (m >= n_mesh) return;
+    double e = 0.0;
+    if (tri_off)
+        for (int b = tri_off[m] + lane; b < tri_off[m + 1]; b += 32) e += epart[b];
+    if (hinge_off)
+        for (int b = hinge_off[m] + lane; b < hinge_off[m + 1]; b += 32) e += epart[hinge_base + b];
+    e = warp_sum(e);
+    if (lane == 0 && e_mesh) e_mesh[m] = e;
+    if (gn_mesh) {
+        double q = 0.0;
+        for (int c = chunk_off[m] + lane; c < chunk_off[m + 1]; c += 32) q += gpart[c];
+        q = warp_sum(q);
+        if (lane == 0) gn_mesh[m] = ::sqrt(q);
+    }
+}
+
+// total = sum of the per-mesh energies, fixed order (one block)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_total(int n_mesh, const double *e_mesh, double *e_total)
 {
     double tot = 0.0;
-    for (int m = threadIdx.x; m < n_mesh; m += THREADS) {
-        double e = 0.0;
-        if (tri_off)
-            for (int b = tri_off[m]; b < tri_off[m + 1]; ++b) e += epart[b];
-        if (hinge_off)
-            for (int b = hinge_off[m]; b < hinge_off[m + 1]; ++b) e += epart[hinge_base + b];
-        if (e_mesh) e_mesh[m] = e;
-        tot += e;
-        if (gn_mesh) {
-            double s = 0.0;
-            for (int c = chunk_off[m]; c < chunk_off[m + 1]; ++c) s += gpart[c];
-            gn_mesh[m] = ::sqrt(s);
-        }
-    }
+    for (int m = threadIdx.x; m < n_mesh; m += THREADS) tot += e_mesh[m];
     tot = block_sum<THREADS>(tot);
-    if (threadIdx.x == 0 && e_total) *e_total = tot;
+    if (threadIdx.x == 0) *e_total = tot;
 }
 
 // ------------------------------------------------------ ARAP Jacobian ---
@@ -149,19 +177,29 @@ adm_status launch_reduce(adm_ctx *h, const EvalArgs &a, const int32_t *tri_off, 
         tm.end(ADM_STAGE_GNORM);
     }
     tm.begin(ADM_STAGE_FINALIZE);
-    k_finalize<1024><<<1, 1024, 0, s>>>(m.n_mesh, h->d_epart, tri_off, hinge_off, hinge_base, h->d_gpart,
-                                        h->chunks.d_mesh_chunk_off, a.energy_per_mesh, a.gnorm_per_mesh,
-                                        a.energy_total);
+    double *e_mesh = a.energy_per_mesh ? a.energy_per_mesh : (a.energy_total ? h->d_emesh : nullptr);
+    if (e_mesh || a.gnorm_per_mesh) {
+        constexpr int kSumThreads = 256;
+        const int nb = (m.n_mesh + kSumThreads / 32 - 1) / (kSumThreads / 32);
+        k_mesh_sums<kSumThreads><<<nb, kSumThreads, 0, s>>>(m.n_mesh, h->d_epart, tri_off, hinge_off, hinge_base,
+                                                            h->d_gpart, h->chunks.d_mesh_chunk_off, e_mesh,
+                                                            a.gnorm_per_mesh);
+    }
+    if (a.energy_total) k_total<1024><<<1, 1024, 0, s>>>(m.n_mesh, e_mesh, a.energy_total);
     tm.end(ADM_STAGE_FINALIZE);
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a)
 {
-    if (a.energy == ADM_UMBRELLA) return eval_ring(h, a);
     // the matrix-free product and Hessian filtering are implemented by the tiled kernel only
-    if (h->assembler == 0 || a.hv || (h->proj && a.bsr) || a.energy == ADM_MASS_SPRING || h->inter.n_terms() > 0)
-        return a.prec == ADM_FP32 ? eval_tiled<float>(h, a) : eval_tiled<double>(h, a);
+    const bool tiled = a.energy != ADM_UMBRELLA && (h->assembler == 0 || a.hv || (h->proj && a.bsr) ||
+                                                    a.energy == ADM_MASS_SPRING || h->inter.n_terms() > 0);
+    if (a.n_split > 0 && !tiled)  // x arriving in ranges: only the tiled pass consumes them one by one
+        for (int k = 0; k < a.n_split; ++k)
+            if (cudaStreamWaitEvent(a.stream, a.split_ready[k], 0) != cudaSuccess) return ADM_ERR_CUDA;
+    if (a.energy == ADM_UMBRELLA) return eval_ring(h, a);
+    if (tiled) return a.prec == ADM_FP32 ? eval_tiled<float>(h, a) : eval_tiled<double>(h, a);
     return a.prec == ADM_FP32 ? eval_atomic<float>(h, a) : eval_atomic<double>(h, a);
 }
 

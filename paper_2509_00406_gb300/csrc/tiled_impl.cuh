@@ -442,21 +442,33 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     if (smem > 227 * 1024) return ADM_ERR_UNSUPPORTED;
     cudaStream_t s = a.stream;
     StageTimer tm(h, s);
-    tm.begin(ADM_STAGE_ZERO);
+    const bool pairs = h->inter.kind == (hin ? PAT_SHELL : PAT_TRI) && h->inter.n_terms() > 0;
     if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
-    const int64_t nzb = a.bsr ? (int64_t)ts.zero_blocks.size() : 0;
-    const int64_t nzv = (a.grad || a.hv) ? (int64_t)ts.zero_verts.size() : 0;
-    if (nzb + nzv > 0) {
+    const bool with_bsr = a.bsr != nullptr, with_rows = a.grad || a.hv;
+    // zero the shared outputs listed in [zb0, zb1) and [zv0, zv1)
+    auto zero_range = [&](int64_t zb0, int64_t zb1, int64_t zv0, int64_t zv1, cudaStream_t zs) {
+        const int64_t nzb = with_bsr ? zb1 - zb0 : 0, nzv = with_rows ? zv1 - zv0 : 0;
+        if (nzb + nzv == 0) return;
         const int64_t work = std::max(nzb * vd * vd, nzv * vd);
         const int blocks = (int)std::min<int64_t>((work + 255) / 256, 152 * 8);
         if (vd == 3)
-            k_zero_shared<T, 3><<<blocks, 256, 0, s>>>(ts.d_zero_blocks, nzb, ts.d_zero_verts, nzv,
-                                                        (T *)a.bsr, (T *)a.grad, (T *)a.hv);
+            k_zero_shared<T, 3><<<blocks, 256, 0, zs>>>(ts.d_zero_blocks + zb0, nzb, ts.d_zero_verts + zv0, nzv,
+                                                         (T *)a.bsr, (T *)a.grad, (T *)a.hv);
         else
-            k_zero_shared<T, 2><<<blocks, 256, 0, s>>>(ts.d_zero_blocks, nzb, ts.d_zero_verts, nzv,
-                                                        (T *)a.bsr, (T *)a.grad, (T *)a.hv);
+            k_zero_shared<T, 2><<<blocks, 256, 0, zs>>>(ts.d_zero_blocks + zb0, nzb, ts.d_zero_verts + zv0, nzv,
+                                                         (T *)a.bsr, (T *)a.grad, (T *)a.hv);
+    };
+    const bool split = a.n_split > 0 && a.split_mesh && a.split_ready && !pairs && a.energy != ADM_MLP_MEMBRANE &&
+                       h->split_stream[0] && h->split_stream[1] && h->split_start &&
+                       (int)h->split_done.size() >= a.n_split;
+    if (a.n_split > 0 && !split)  // x arriving in ranges, consumed whole here: wait for all of them
+        for (int k = 0; k < a.n_split; ++k)
+            if (cudaStreamWaitEvent(s, a.split_ready[k], 0) != cudaSuccess) return ADM_ERR_CUDA;
+    if (!split) {
+        tm.begin(ADM_STAGE_ZERO);
+        zero_range(0, (int64_t)ts.zero_blocks.size(), 0, (int64_t)ts.zero_verts.size(), s);
+        tm.end(ADM_STAGE_ZERO);
     }
-    tm.end(ADM_STAGE_ZERO);
     TiledArgs<T> A;
     A.hdr = ts.d_hdr;
     A.tri_loc = ts.d_tri_loc;
@@ -494,11 +506,48 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
         if (st != ADM_OK) return st;
         A.mlp_table = h->d_mlp_table;
     }
+    // tiles [t0, t1): the kernel indexes its per-tile arrays by block, so a
+    // range is a launch over offset pointers
+    auto tiled_range = [&](int32_t t0, int32_t t1, cudaStream_t ks) {
+        if (t1 <= t0) return;
+        TiledArgs<T> B = A;
+        B.hdr += 8 * (int64_t)t0;
+        B.meta_off += t0;
+        B.epart += t0;
+        if (B.cloth_hdr) B.cloth_hdr += 4 * (int64_t)t0;
+        launch_tiled<T>(a.energy, mode, h->proj != 0, t1 - t0, smem, ks, B);
+    };
     tm.begin(ADM_STAGE_TILED);
-    launch_tiled<T>(a.energy, mode, h->proj != 0, ts.n_tiles, smem, s, A);
+    if (!split) {
+        tiled_range(0, ts.n_tiles, s);
+    } else {
+        // per mesh range, on two streams in turn: wait for its x, zero its
+        // shared outputs (they lie in its own rows) and run its tiles.  The
+        // copies of later ranges overlap the kernels of earlier ones, and a
+        // range's launch overlaps the tail of the one before; the pass's
+        // stream resumes when every range is done.
+        const Pattern &P = h->pat[hin ? PAT_SHELL : PAT_TRI];
+        auto lb = [](const std::vector<int32_t> &v, int64_t key) {
+            return (int64_t)(std::lower_bound(v.begin(), v.end(), (int32_t)key) - v.begin());
+        };
+        if (cudaEventRecord(h->split_start, s) != cudaSuccess) return ADM_ERR_CUDA;
+        for (int k = 0; k < a.n_split; ++k) {
+            cudaStream_t ks = h->split_stream[k & 1];
+            const int32_t m0 = a.split_mesh[k], m1 = a.split_mesh[k + 1];
+            const int64_t v0 = m.v_off[m0], v1 = m.v_off[m1];
+            if (cudaStreamWaitEvent(ks, h->split_start, 0) != cudaSuccess ||
+                cudaStreamWaitEvent(ks, a.split_ready[k], 0) != cudaSuccess)
+                return ADM_ERR_CUDA;
+            zero_range(lb(ts.zero_blocks, P.row_ptr[v0]), lb(ts.zero_blocks, P.row_ptr[v1]), lb(ts.zero_verts, v0),
+                       lb(ts.zero_verts, v1), ks);
+            tiled_range(ts.mesh_tile_off[m0], ts.mesh_tile_off[m1], ks);
+            if (cudaEventRecord(h->split_done[k], ks) != cudaSuccess) return ADM_ERR_CUDA;
+        }
+        for (int k = 0; k < a.n_split; ++k)
+            if (cudaStreamWaitEvent(s, h->split_done[k], 0) != cudaSuccess) return ADM_ERR_CUDA;
+    }
     tm.end(ADM_STAGE_TILED);
     if (cudaGetLastError() != cudaSuccess) return ADM_ERR_CUDA;
-    const bool pairs = h->inter.kind == (hin ? PAT_SHELL : PAT_TRI) && h->inter.n_terms() > 0;
     if (pairs) {
         tm.begin(ADM_STAGE_PAIRS);
         adm_status st = interactions_eval(h, a, mode);

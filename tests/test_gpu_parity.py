@@ -224,9 +224,15 @@ def test_batch_per_mesh_energy_and_gnorm(prec, assembler):
         assert abs(out["gnorm"][k] - np.linalg.norm(gk)) <= tol * np.linalg.norm(gk)
 
 
-def test_host_buffer_path_matches_device_path():
-    b = synth.shell_batch([2, 3], sigma=1e-2, seed=12)
+@pytest.mark.parametrize("levels,assembler", [([2, 3], 0), ([1, 2, 3, 1, 2, 2, 3], 0), ([2, 1, 3], 1)])
+def test_host_buffer_path_matches_device_path(levels, assembler):
+    """adm_eval_batch_host feeds a tiled batch in up to four mesh ranges whose
+    copies overlap the kernels of earlier ranges; the atomic assembler takes
+    x whole.  Both must give the device path's results (energies bitwise:
+    the same tiles and partial sums)."""
+    b = synth.shell_batch(levels, sigma=1e-2, seed=12)
     m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_option(adm.OPT_ASSEMBLER, assembler)
     dev = gpu_eval(m, adm.SHELL, adm.FP32, b.x.astype(np.float32), batch=True)
     nnzb = dev["vals"].shape[0]
     x = np.ascontiguousarray(b.x.astype(np.float32))
