@@ -702,6 +702,7 @@ def run_ours(args, rank: int, world: int, local: int):
                      "avg_ms": dom_ms, "peak_source": peak_src, "pipes": pipes},
         "pass": {"algorithmic_bytes": pass_bytes, "achieved_gbs": pass_bytes / (ms_step * 1e-3) / 1e9,
                  "frac_of_hbm": pass_bytes / (ms_step * 1e-3) / 1e9 / peak,
+                 "assembled_scalars_per_s": c["nnzb"] * 9 * world / (ms_step * 1e-3),
                  "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}},
         "e2e": e2e,
         "clocks": clk,

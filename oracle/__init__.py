@@ -63,6 +63,8 @@ def lib():
             L.orc_local.restype = i32
             L.orc_local.argtypes = [i32, i32, vp, i32, _dp, i32, _dp, C.c_double, C.c_double,
                                     C.c_double, _dp, _dp, _dp]
+            L.orc_hd_flops.restype = i64
+            L.orc_hd_flops.argtypes = [i32]
             L.orc_hd_probe.restype = None
             L.orc_hd_probe.argtypes = [i32, _dp, i32, _dp]
             L.orc_invariants_from_F.restype = None
@@ -279,6 +281,17 @@ def local(energy: int, xl, vdim: int = 3, Dinv=None, area: float = 0.0, thetabar
     if err < 0:
         raise ValueError(f"no route {route} for energy {energy}")
     return {"f": float(f[0]), "g": g, "H": H.reshape(k, k), "err": int(err)}
+
+
+def dense_flops(energy: int, xl, vdim: int = 3, Dinv=None, area: float = 0.0, thetabar: float = 0.0,
+                abar: float = 0.0, params=None) -> int:
+    """Scalar floating-point operations of one element's energy, gradient and
+    Hessian by dense forward mode (route 0: the paper's ActiveT form, a
+    k-gradient and a k x k Hessian carried through every operation), counted
+    by the oracle's hyper-dual rules."""
+    lib().orc_hd_flops(1)
+    local(energy, xl, vdim, Dinv, area, thetabar, abar, params, route=0)
+    return int(lib().orc_hd_flops(1))
 
 
 MLP_NPARAM = 4481

@@ -60,6 +60,13 @@ typedef struct {
     double h[KMAX][KMAX];
 } hd;
 
+/* Scalar floating-point operations of the dense rules below, counted as
+ * written (value, k gradient entries, k x k Hessian entries; the scalar
+ * derivatives f, f', f'' callers pass in are not counted).  A measurement
+ * of what dense forward mode costs per element; it changes no result. */
+static int64_t g_hd_flops;
+#define HD_COUNT(n) (g_hd_flops += (int64_t)(n))
+
 static hd hd_const(int k, double c)
 {
     hd r;
@@ -78,6 +85,7 @@ static hd hd_var(int k, double value, int i)
 
 static hd hd_add(hd a, hd b)
 {
+    HD_COUNT(1 + a.k + a.k * a.k);
     hd r = a;
     r.v = a.v + b.v;
     for (int i = 0; i < a.k; ++i) {
@@ -89,6 +97,7 @@ static hd hd_add(hd a, hd b)
 
 static hd hd_scale(hd a, double s)
 {
+    HD_COUNT(1 + a.k + a.k * a.k);
     hd r = a;
     r.v = a.v * s;
     for (int i = 0; i < a.k; ++i) {
@@ -102,6 +111,7 @@ static hd hd_sub(hd a, hd b) { return hd_add(a, hd_scale(b, -1.0)); }
 
 static hd hd_addc(hd a, double c)
 {
+    HD_COUNT(1);
     a.v += c;
     return a;
 }
@@ -109,6 +119,7 @@ static hd hd_addc(hd a, double c)
 /* product rule: (ab)'' = a'' b + a b'' + a' b'^T + b' a'^T */
 static hd hd_mul(hd a, hd b)
 {
+    HD_COUNT(1 + 3 * a.k + 7 * a.k * a.k);  /* per Hessian entry: 4 products, 3 sums */
     hd r = hd_const(a.k, a.v * b.v);
     for (int i = 0; i < a.k; ++i) r.g[i] = a.g[i] * b.v + a.v * b.g[i];
     for (int i = 0; i < a.k; ++i)
@@ -120,6 +131,7 @@ static hd hd_mul(hd a, hd b)
 /* univariate chain rule: r = f(a), r' = f1 a', r'' = f1 a'' + f2 a' a'^T */
 static hd hd_chain1(hd a, double f, double f1, double f2)
 {
+    HD_COUNT(a.k + 4 * a.k * a.k);
     hd r = hd_const(a.k, f);
     for (int i = 0; i < a.k; ++i) r.g[i] = f1 * a.g[i];
     for (int i = 0; i < a.k; ++i)
@@ -131,6 +143,7 @@ static hd hd_chain1(hd a, double f, double f1, double f2)
 static hd hd_chain2(hd a, hd b, double f, double fa, double fb, double faa, double fab,
                     double fbb)
 {
+    HD_COUNT(3 * a.k + 14 * a.k * a.k);
     hd r = hd_const(a.k, f);
     for (int i = 0; i < a.k; ++i) r.g[i] = fa * a.g[i] + fb * b.g[i];
     for (int i = 0; i < a.k; ++i)
@@ -952,6 +965,14 @@ void orc_hinge_rest(int64_t nH, const int32_t *H, const double *Vrest, double *t
 }
 
 /* single-element entry points (for pins and finite differences) */
+/* the dense-rule operation count since the last reset (reset != 0 clears it) */
+int64_t orc_hd_flops(int reset)
+{
+    const int64_t v = g_hd_flops;
+    if (reset) g_hd_flops = 0;
+    return v;
+}
+
 int orc_local(int energy, int route, const double *p, int np, const double *xl, int vdim,
               const double *Dinv, double area, double thetabar, double abar, double *f,
               double *g, double *H)
