@@ -1,0 +1,94 @@
+"""Parity at the full sizes of the timed workloads, in the launch
+configuration the bench times, on outputs the oracle can recompute piece by
+piece:
+
+* the 700-icosphere shell batch (2.16M vertices, FP32, default tiles):
+  sampled meshes, each recomputed alone by the oracle (per-mesh energy and
+  gradient norm, its gradient rows and Hessian block rows; its rows of the
+  batch pattern bit-exact against the oracle's pattern shifted by the
+  mesh's first vertex);
+* the 1M-triangle ARAP residual disk (FP32): sampled triangles, their four
+  residual rows and 24 Jacobian entries (values and columns) recomputed by
+  the oracle on those triangles alone."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from util import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import __graft_entry__  # noqa: E402
+import paper_2509_00406_gb300 as adm  # noqa: E402
+
+SHELL_P = [1.0e5, 0.3, 1.0e-3]
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def test_shell_batch_700_sampled_meshes_fp32():
+    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
+    x32 = b.x.astype(np.float32)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    _, nV, nnzb, rp, col = m.pattern(adm.SHELL)
+    xd = torch.from_numpy(x32).cuda()
+    e = torch.zeros(b.n_mesh, dtype=torch.float64, device="cuda")
+    gn = torch.zeros_like(e)
+    g = torch.full((nV * 3,), float("nan"), device="cuda")
+    H = torch.full((nnzb * 9,), float("nan"), device="cuda")
+    m.eval_batch(adm.SHELL, adm.FP32, xd, e, gn, g, H)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    assert not torch.isnan(H).any() and not torch.isnan(g).any()     # every output written
+    rp, col = rp.cpu().numpy(), col.cpu().numpy()
+    e, gn = e.cpu().numpy(), gn.cpu().numpy()
+    g = g.cpu().numpy().reshape(-1, 3)
+    H = H.cpu().numpy().reshape(-1, 3, 3)
+    nv_mesh = np.diff(b.v_off)
+    rng = np.random.default_rng(7)
+    big = np.flatnonzero(nv_mesh == nv_mesh.max())
+    small = np.flatnonzero(nv_mesh == nv_mesh.min())
+    picks = [int(rng.choice(big)), int(rng.choice(small)), int(rng.choice(small)), b.n_mesh - 1]
+    for k in picks:
+        v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.SHELL, 3, params=SHELL_P)
+        ref = P.assemble(x32[v0:v1].astype(np.float64), route=1)
+        blk = slice(rp[v0], rp[v1])
+        assert np.array_equal(rp[v0:v1 + 1] - rp[v0], P.row_ptr) and np.array_equal(col[blk] - v0, P.col)
+        assert abs(e[k] - ref["energy"]) <= TOL * abs(ref["energy"])
+        assert rel(g[v0:v1], ref["grad"]) <= TOL
+        assert abs(gn[k] - np.linalg.norm(ref["grad"])) <= TOL * np.linalg.norm(ref["grad"])
+        assert rel(H[blk], ref["vals"]) <= TOL
+    m.close()
+
+
+def test_arap_disk_1m_sampled_triangles_fp32():
+    d = synth.noisy_disk()
+    m = adm.Mesh(d.rest, d.faces, 2)
+    nr, nc, nnz, jrp, jcol = m.jac_pattern()
+    _, nV, nnzb, _, _ = m.pattern(adm.ARAP2D_RESIDUAL)
+    x32 = d.x.astype(np.float32)
+    r = torch.zeros(nr, device="cuda")
+    jv = torch.zeros(nnz, device="cuda")
+    jtj = torch.zeros(nnzb * 4, device="cuda")
+    m.eval_jacobian(adm.ARAP2D_RESIDUAL, adm.FP32, torch.from_numpy(x32).cuda(), r, jv, jtj)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    r, jv, jcol = r.cpu().numpy(), jv.cpu().numpy(), jcol.cpu().numpy()
+    ts = np.sort(np.random.default_rng(8).choice(d.faces.shape[0], 500, replace=False))
+    P = oracle.Problem(d.rest, d.faces[ts], oracle.ARAP, 2)
+    ref = P.arap_jacobian(x32.astype(np.float64))
+    rows = (4 * ts[:, None] + np.arange(4)).ravel()
+    ents = (24 * ts[:, None] + np.arange(24)).ravel()
+    assert rel(r[rows], ref["r"]) <= TOL
+    assert rel(jv[ents], ref["val"]) <= TOL
+    assert np.array_equal(jcol[ents], ref["col"])
+    m.close()
