@@ -291,9 +291,10 @@ struct EvalArgs {
     const cudaEvent_t *split_ready = nullptr;
 };
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
-// vertex-pair interactions (dyn.cu): replace the pair set of pattern `kind`
-// and extend its block pattern on the GPU; evaluate the pairs of a pass
-// (after the tiled kernel) and add their energies (after the reduction)
+// contact terms (dyn.cu): replace the vertex-vertex pairs and vertex-face
+// elements (p, a, b, c) of pattern `kind` and extend its block pattern on the
+// GPU; evaluate the terms of a pass (after the tiled kernel) and add their
+// energies (after the reduction)
 adm_status interactions_set(adm_ctx *h, int kind, const int32_t *pairs, int64_t n, const int32_t *quads, int64_t nq,
                             double kappa, double dhat, double area, double hstep, cudaStream_t s);
 adm_status interactions_eval(adm_ctx *h, const EvalArgs &a, int mode);
