@@ -55,13 +55,16 @@ TILED_KERNEL_SOURCES = ["ad.cuh", "spd.cuh", "terms.cuh", "device_common.cuh", "
 
 
 def kernel_digest(files=None) -> str:
-    """Digest of the sources one kernel is compiled from, plus the flags."""
+    """Digest of the sources one kernel is compiled from, plus the flags
+    (include paths relative to the repository, so that the digest is the
+    same on every machine the repository is copied to)."""
     h = hashlib.sha256()
     for name in (files or TILED_KERNEL_SOURCES):
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
-    h.update(" ".join(ARCH + COMMON).encode())
+    flags = [os.path.relpath(f, ROOT) if os.path.isabs(f) else f for f in ARCH + COMMON]
+    h.update(" ".join(flags).encode())
     return h.hexdigest()[:16]
 
 
