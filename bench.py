@@ -524,6 +524,44 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
                                  "us_per_pass": msg * 1e3, "us_per_pass_graph": msgg * 1e3,
                                  "hvp_us_per_call": msh * 1e3, "hvp_us_per_call_graph": mshg * 1e3}
     mg.close()
+
+    # the literal reading of the batched-shell workload: 700 meshes with
+    # levels drawn uniformly from {4, 5, 6} (about 13.3M vertices, 6.2 GB of
+    # FP32 Hessian blocks); creation (hinges, pattern, tiles) is timed apart
+    bu = synth.shell_batch(synth.shell_batch_levels("uniform"), sigma=1e-3, seed=4)
+    cu = counts(bu)
+    t0 = time.perf_counter()
+    mu = adm.Mesh(bu.rest, bu.faces, 3, v_off=bu.v_off, f_off=bu.f_off)
+    mu.set_params(adm.SHELL, SHELL_PARAMS)
+    _, nVu, nnzbu, _, _ = mu.pattern(adm.SHELL)
+    xu = torch.from_numpy(bu.x.astype(np.float32)).cuda()
+    eu = torch.zeros(bu.n_mesh, dtype=torch.float64, device="cuda")
+    gnu = torch.zeros_like(eu)
+    gu = torch.zeros(nVu * 3, dtype=torch.float32, device="cuda")
+    Hu = torch.zeros(nnzbu * 9, dtype=torch.float32, device="cuda")
+    mu.eval_batch(adm.SHELL, adm.FP32, xu, eu, gnu, gu, Hu, stream=stream)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    assert nnzbu == cu["nnzb"] and mu.status() == 0
+    su = max(5, min(args.steps, 20))
+    mu.set_option(adm.OPT_PROFILE, su)
+    msu = _time_steps(torch, lambda: mu.eval_batch(adm.SHELL, adm.FP32, xu, eu, gnu, gu, Hu, stream=stream), su,
+                      stream)
+    profu = mu.profile_read()
+    mu.set_option(adm.OPT_PROFILE, 0)
+    nelu = cu["n_triangles"] + cu["n_hinges"]
+    abu = algorithmic_bytes(cu, "pass")
+    peak, _ = measured_peaks()
+    out["shell_batch_uniform_levels"] = {
+        "workload": f"700 icospheres, levels uniform in {{4, 5, 6}} ({cu['n_vertices']} V, {cu['n_triangles']} T, "
+                    f"{cu['n_hinges']} hinges, {cu['nnzb']} blocks), FP32 grad + BSR Hessian",
+        "value": nelu / (msu * 1e-3), "unit": UNIT, "ms_per_step": msu,
+        "tiled_ms": profu["tiled"][0],
+        "tiled_algorithmic_gbs": abu / (profu["tiled"][0] * 1e-3) / 1e9,
+        "tiled_frac_of_hbm": abu / (profu["tiled"][0] * 1e-3) / 1e9 / peak,
+        "create_and_first_pass_s": round(create_s, 2)}
+    mu.close()
+    del xu, eu, gnu, gu, Hu
     return out
 
 
