@@ -2,11 +2,11 @@
 configuration the bench times, on outputs the oracle can recompute piece by
 piece:
 
-* the 700-icosphere shell batch (2.16M vertices, FP32, default tiles):
-  sampled meshes, each recomputed alone by the oracle (per-mesh energy and
-  gradient norm, its gradient rows and Hessian block rows; its rows of the
-  batch pattern bit-exact against the oracle's pattern shifted by the
-  mesh's first vertex);
+* the 700-icosphere shell batch (2.16M vertices, FP32, default tiles), the
+  shell and its bending term alone: sampled meshes, each recomputed alone by
+  the oracle (per-mesh energy and gradient norm, its gradient rows and
+  Hessian block rows; its rows of the batch pattern bit-exact against the
+  oracle's pattern shifted by the mesh's first vertex);
 * the 1M-triangle ARAP residual disk (FP32): sampled triangles, their four
   residual rows and 24 Jacobian entries (values and columns) recomputed by
   the oracle on those triangles alone."""
@@ -33,34 +33,40 @@ def built():
     assert torch.cuda.is_available()
 
 
-def test_shell_batch_700_sampled_meshes_fp32():
-    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
-    x32 = b.x.astype(np.float32)
-    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
-    m.set_params(adm.SHELL, SHELL_P)
-    _, nV, nnzb, rp, col = m.pattern(adm.SHELL)
+def batch_eval(m, energy, x32):
+    _, nV, nnzb, rp, col = m.pattern(energy)
     xd = torch.from_numpy(x32).cuda()
-    e = torch.zeros(b.n_mesh, dtype=torch.float64, device="cuda")
+    e = torch.zeros(m.n_mesh, dtype=torch.float64, device="cuda")
     gn = torch.zeros_like(e)
     g = torch.full((nV * 3,), float("nan"), device="cuda")
     H = torch.full((nnzb * 9,), float("nan"), device="cuda")
-    m.eval_batch(adm.SHELL, adm.FP32, xd, e, gn, g, H)
+    m.eval_batch(energy, adm.FP32, xd, e, gn, g, H)
     torch.cuda.synchronize()
     assert m.status() == 0
     assert not torch.isnan(H).any() and not torch.isnan(g).any()     # every output written
-    rp, col = rp.cpu().numpy(), col.cpu().numpy()
-    e, gn = e.cpu().numpy(), gn.cpu().numpy()
-    g = g.cpu().numpy().reshape(-1, 3)
-    H = H.cpu().numpy().reshape(-1, 3, 3)
+    return (rp.cpu().numpy(), col.cpu().numpy(), e.cpu().numpy(), gn.cpu().numpy(),
+            g.cpu().numpy().reshape(-1, 3), H.cpu().numpy().reshape(-1, 3, 3))
+
+
+# the shell, and its bending term alone: the hinge Hessian is about 1e-8 of
+# the membrane's, so only a separate check sees its errors
+@pytest.mark.parametrize("energy,params", [(adm.SHELL, SHELL_P), (adm.HINGE_BENDING, [0.5, 1.0])])
+def test_shell_batch_700_sampled_meshes_fp32(energy, params):
+    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
+    x32 = b.x.astype(np.float32)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(energy, params)
+    rp, col, e, gn, g, H = batch_eval(m, energy, x32)
     nv_mesh = np.diff(b.v_off)
     rng = np.random.default_rng(7)
     big = np.flatnonzero(nv_mesh == nv_mesh.max())
     small = np.flatnonzero(nv_mesh == nv_mesh.min())
     picks = [int(rng.choice(big)), int(rng.choice(small)), int(rng.choice(small)), b.n_mesh - 1]
+    orc = oracle.SHELL if energy == adm.SHELL else oracle.HINGE
     for k in picks:
         v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
-        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.SHELL, 3, params=SHELL_P)
-        ref = P.assemble(x32[v0:v1].astype(np.float64), route=1)
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, orc, 3, params=params)
+        ref = P.assemble(x32[v0:v1].astype(np.float64))          # hyper-dual route: every Hessian
         blk = slice(rp[v0], rp[v1])
         assert np.array_equal(rp[v0:v1 + 1] - rp[v0], P.row_ptr) and np.array_equal(col[blk] - v0, P.col)
         assert abs(e[k] - ref["energy"]) <= TOL * abs(ref["energy"])
