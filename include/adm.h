@@ -171,7 +171,8 @@ adm_status adm_create_batch(const double *V, const int64_t *v_off, const int32_t
  * the mesh pattern has add nothing.  adm_pattern then returns the extended
  * pattern (device pointers valid until the next call of this function),
  * whose nnzb sizes the Hessian buffers.  Synchronous on `stream` (reads back
- * the new block count).  Term energies count towards the total and towards
+ * the new block count); no pass of this handle may be in flight on another
+ * stream meanwhile (the term buffers are rewritten).  Term energies count towards the total and towards
  * the mesh of the term's first vertex (in per-mesh energies their order of
  * summation is not fixed).  The Hessian and matrix-free passes run on the
  * tiled kernel.  Errors: ADM_ERR_ARG (a vertex out of range or repeated
