@@ -212,3 +212,38 @@ def test_vertex_face_argument_errors():
             m.set_contacts(adm.STVK_MEMBRANE, None, np.array([bad], dtype=np.int32), KAPPA, DHAT, AREA, HSTEP)
         assert m.pattern(adm.STVK_MEMBRANE)[2] == rp0                      # cleared back to the mesh pattern
     m.close()
+
+
+def test_cloth_vertex_face_hvp_fp64():
+    """Vertex-face terms on the mass-spring cloth (the triangle pattern) in a
+    folded state, through the Hessian pass and the matrix-free product."""
+    c = synth.cloth_grid(14, sigma=0.3, seed=73)
+    c.x[:, 2] += 0.3 * np.sin(6 * c.rest[:, 0])  # folds bring distant parts near each other
+    m = adm.Mesh(c.rest, c.faces, 3)
+    m.set_inertia_target(c.xhat)
+    cp = [2.0e3, 0.02, 1.5, 0.0, 0.0, -9.81]
+    m.set_params(adm.MASS_SPRING, cp)
+    vf, _ = pick_vf(c.faces, c.x, 40, seed=74)
+    m.set_contacts(adm.MASS_SPRING, None, vf, KAPPA, DHAT, AREA, HSTEP)
+    rp0, col0 = oracle.pattern(c.nV, c.faces)
+    base = oracle.cloth_assemble(c.rest, c.faces, c.x, c.xhat, cp, rp0, col0)
+    none = np.zeros((0, 2), np.int32)
+    erp, ecol = oracle.extended_pattern(rp0, col0, none, vf)
+    ref = oracle.add_interactions(base, c.x, none, KAPPA, DHAT, AREA, HSTEP, rp0, col0, vf)
+    e, g, H, rp, col = gpu_eval(m, adm.MASS_SPRING, adm.FP64, c.x)
+    assert np.array_equal(rp, erp) and np.array_equal(col, ecol)
+    assert abs(e - ref["energy"]) <= 1e-12 * abs(ref["energy"])
+    assert rel(g, ref["grad"]) <= 1e-12
+    want = np.stack([ref["blocks"].get((r, int(cc)), np.zeros((3, 3))) for r in range(c.nV)
+                     for cc in col[rp[r]:rp[r + 1]]])
+    assert rel(H, want) <= 1e-12
+    v = np.random.default_rng(9).normal(size=c.x.shape)
+    xd = torch.from_numpy(np.ascontiguousarray(c.x).reshape(-1)).cuda()
+    hv = torch.zeros_like(xd)
+    m.eval_hvp(adm.MASS_SPRING, adm.FP64, xd, torch.from_numpy(v.reshape(-1)).cuda(), hv)
+    torch.cuda.synchronize()
+    hv_ref = np.zeros_like(c.x)
+    for (r, cc), blk in ref["blocks"].items():
+        hv_ref[r] += blk @ v[cc]
+    assert rel(hv.cpu().numpy().reshape(-1, 3), hv_ref) <= 1e-12
+    m.close()
