@@ -285,8 +285,10 @@ adm_status adm_eval_batch(adm_handle h, adm_energy energy, adm_precision prec,
  * device staging buffers, copies back those outputs whose host pointer is
  * not NULL, and returns after the copies completed (synchronous).  Outputs
  * not copied back stay in the staging buffers (for a solver on the device).
- * Staging buffers are allocated on first use; the call uses the library's
- * own stream.  Pinned host buffers make the copies faster. */
+ * Staging buffers are allocated on first use (and grown when contact terms
+ * extend the pattern); the call uses the library's own stream.  bsr_vals_host
+ * holds the nnzb of adm_pattern at the time of the call.  Pinned host
+ * buffers make the copies faster. */
 adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision prec,
                                const void *x_host, double *energy_per_mesh_host,
                                double *gnorm_host, void *grad_host, void *bsr_vals_host);

@@ -727,7 +727,11 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
     const HostMesh &m = h->m;
     const size_t es = prec == ADM_FP32 ? 4 : 8;
     const size_t xb = es * m.nV * m.vdim;
-    const int64_t nnzb = h->pat[energy == ADM_UMBRELLA ? PAT_RING : (needs_hinges(energy) ? PAT_SHELL : PAT_TRI)].nnzb;
+    // the block count of the pattern the pass writes: extended by contact
+    // terms when they are set on it
+    const int kind = energy == ADM_UMBRELLA ? PAT_RING : (needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
+    const bool ext = h->inter.kind == kind && h->inter.d_rp[h->inter.active];
+    const int64_t nnzb = ext ? h->inter.nnzb : h->pat[kind].nnzb;
     const size_t bb = es * nnzb * m.vdim * m.vdim;
     if (!h->own_stream && cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return ADM_ERR_CUDA;

@@ -224,15 +224,20 @@ def test_batch_per_mesh_energy_and_gnorm(prec, assembler):
         assert abs(out["gnorm"][k] - np.linalg.norm(gk)) <= tol * np.linalg.norm(gk)
 
 
-@pytest.mark.parametrize("levels,assembler", [([2, 3], 0), ([1, 2, 3, 1, 2, 2, 3], 0), ([2, 1, 3], 1)])
-def test_host_buffer_path_matches_device_path(levels, assembler):
+@pytest.mark.parametrize("levels,assembler,contacts",
+                         [([2, 3], 0, False), ([1, 2, 3, 1, 2, 2, 3], 0, False), ([2, 1, 3], 1, False),
+                          ([2, 2, 1], 0, True)])
+def test_host_buffer_path_matches_device_path(levels, assembler, contacts):
     """adm_eval_batch_host feeds a tiled batch in up to four mesh ranges whose
-    copies overlap the kernels of earlier ranges; the atomic assembler takes
-    x whole.  Both must give the device path's results (energies bitwise:
-    the same tiles and partial sums)."""
+    copies overlap the kernels of earlier ranges; the atomic assembler, and a
+    pass with contact terms, take x whole.  All must give the device path's
+    results (energies bitwise: the same tiles and partial sums)."""
     b = synth.shell_batch(levels, sigma=1e-2, seed=12)
     m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
     m.set_option(adm.OPT_ASSEMBLER, assembler)
+    if contacts:  # pairs across the first two meshes, whatever their distance
+        pairs = np.array([[i, b.v_off[1] + i] for i in range(0, 40, 3)], dtype=np.int32)
+        m.set_contacts(adm.SHELL, pairs, None, 1.0e3, 10.0, 0.05, 0.1)
     dev = gpu_eval(m, adm.SHELL, adm.FP32, b.x.astype(np.float32), batch=True)
     nnzb = dev["vals"].shape[0]
     x = np.ascontiguousarray(b.x.astype(np.float32))
