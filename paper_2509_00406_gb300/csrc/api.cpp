@@ -517,6 +517,17 @@ adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
     }
 }
 
+// whether contact terms extend pattern `kind`, and the block count a pass on
+// it writes
+static bool pattern_extended(const adm_ctx *h, int kind)
+{
+    return h->inter.kind == kind && h->inter.d_rp[h->inter.active] != nullptr;
+}
+static int64_t pass_nnzb(const adm_ctx *h, int kind)
+{
+    return pattern_extended(h, kind) ? h->inter.nnzb : h->pat[kind].nnzb;
+}
+
 adm_status adm_pattern(adm_handle h, adm_energy energy, int32_t *block, int64_t *n_rows, int64_t *nnzb,
                        const int32_t **row_ptr_dev, const int32_t **col_dev)
 {
@@ -527,10 +538,10 @@ adm_status adm_pattern(adm_handle h, adm_energy energy, int32_t *block, int64_t 
     const int kind = energy == ADM_UMBRELLA ? PAT_RING : (needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
     const Pattern &P = h->pat[kind];
     const Interactions &I = h->inter;
-    const bool ext = I.kind == kind && I.d_rp[I.active];  // extended by interaction pairs
+    const bool ext = pattern_extended(h, kind);  // extended by contact terms
     if (block) *block = h->m.vdim;
     if (n_rows) *n_rows = h->m.nV;
-    if (nnzb) *nnzb = ext ? I.nnzb : P.nnzb;
+    if (nnzb) *nnzb = pass_nnzb(h, kind);
     if (row_ptr_dev) *row_ptr_dev = ext ? I.d_rp[I.active] : P.d_row_ptr;
     if (col_dev) *col_dev = ext ? I.d_col[I.active] : P.d_col;
     return ADM_OK;
@@ -730,8 +741,7 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
     // the block count of the pattern the pass writes: extended by contact
     // terms when they are set on it
     const int kind = energy == ADM_UMBRELLA ? PAT_RING : (needs_hinges(energy) ? PAT_SHELL : PAT_TRI);
-    const bool ext = h->inter.kind == kind && h->inter.d_rp[h->inter.active];
-    const int64_t nnzb = ext ? h->inter.nnzb : h->pat[kind].nnzb;
+    const int64_t nnzb = pass_nnzb(h, kind);
     const size_t bb = es * nnzb * m.vdim * m.vdim;
     if (!h->own_stream && cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
         return ADM_ERR_CUDA;
@@ -850,7 +860,7 @@ adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, con
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (s == ADM_OK && (cudaMalloc(&g, es * h->m.nV * vd) != cudaSuccess ||
-                        cudaMalloc(&H, es * h->pat[kind].nnzb * vd * vd) != cudaSuccess ||
+                        cudaMalloc(&H, es * pass_nnzb(h, kind) * vd * vd) != cudaSuccess ||
                         cudaMalloc(&e, sizeof(double) * h->m.n_mesh) != cudaSuccess ||
                         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))

@@ -247,3 +247,20 @@ def test_cloth_vertex_face_hvp_fp64():
         hv_ref[r] += blk @ v[cc]
     assert rel(hv.cpu().numpy().reshape(-1, 3), hv_ref) <= 1e-12
     m.close()
+
+
+def test_autotune_with_contacts_then_parity():
+    """The tile-size autotuner runs the pass on the pattern the contact terms
+    extend (its scratch Hessian sized for it) and rebuilds the tiles, which
+    are then remapped to that pattern: the pass after it still matches."""
+    V, F = synth.icosphere(3)
+    x = synth.perturb(V, sigma=1e-2, seed=75)
+    m = adm.Mesh(V, F, 3)
+    m.set_params(adm.STVK_MEMBRANE, SHELL_P)
+    vf, _ = pick_vf(F, x, 40, seed=76)
+    m.set_contacts(adm.STVK_MEMBRANE, None, vf, KAPPA, DHAT, AREA, HSTEP)
+    best, ms = m.autotune(adm.STVK_MEMBRANE, adm.FP64, torch.from_numpy(x.reshape(-1)).cuda())
+    assert best > 0 and ms > 0
+    got = gpu_eval(m, adm.STVK_MEMBRANE, adm.FP64, x)
+    check(V, F, x, np.zeros((0, 2), np.int32), vf, got, False, 1e-12)
+    m.close()
