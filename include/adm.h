@@ -341,6 +341,16 @@ adm_status adm_profile_read(adm_handle h, float *avg_ms, int32_t *n_launches, in
 adm_status adm_grad_norm_noalloc(const void *v_dev, int64_t n, adm_precision prec, double *norm_dev,
                                  void *stream);
 
+/* Failure-detection check of the device waits.  Every wait in this
+ * library's kernels is bounded: the tiled kernel waits for the bulk copy of
+ * a tile's metadata for about a second at most, then latches ADM_ERR_TIMEOUT
+ * in the status word and skips its write-out, leaving the context usable.
+ * This call runs that same bounded wait, in one thread, on a shared-memory
+ * barrier that nothing completes, and returns ADM_ERR_TIMEOUT when the wait
+ * gave up as it must (about a second; synchronous on `stream`).  Any other
+ * result is ADM_ERR_CUDA.  The handle-free call touches no caller memory. */
+adm_status adm_check_bounded_wait(void *stream);
+
 /* --- learned membrane energy ------------------------------------------- */
 /* A per-triangle MLP surrogate of the Neo-Hookean membrane density on the
  * invariants (I1, I2, I3) of C3 = diag(F^T F, 1): u = (I - m_I)/s_I,

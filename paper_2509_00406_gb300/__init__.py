@@ -83,6 +83,7 @@ def lib():
         "adm_get_status": (i32, [vp]),
         "adm_profile_read": (i32, [vp, C.POINTER(C.c_float), C.POINTER(i32), i32]),
         "adm_grad_norm_noalloc": (i32, [vp, i64, i32, vp, vp]),
+        "adm_check_bounded_wait": (i32, [vp]),
         "adm_autotune": (i32, [vp, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_float)]),
         "adm_mlp_eval": (i32, [vp, vp, i64, vp, vp, vp]),
         "adm_mlp_workspace_size": (C.c_size_t, []),
@@ -280,6 +281,12 @@ class Mesh:
 
     def status(self) -> int:
         return int(lib().adm_get_status(self._h))
+
+
+def check_bounded_wait(stream=None) -> int:
+    """Run the library's bounded device wait on a barrier nothing completes;
+    returns the status (ADM_ERR_TIMEOUT, -5, when the wait gave up as it must)."""
+    return int(lib().adm_check_bounded_wait(_stream(stream)))
 
 
 def grad_norm_noalloc(v, prec: int, norm_out, stream=None):

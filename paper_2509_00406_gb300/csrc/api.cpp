@@ -840,6 +840,8 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
     return cudaStreamSynchronize(st) == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
+adm_status adm_check_bounded_wait(void *stream) { return bounded_wait_check(as_stream(stream)); }
+
 adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
                         int32_t *best_tile_tris, float *best_ms)
 {

@@ -291,6 +291,9 @@ struct EvalArgs {
     const cudaEvent_t *split_ready = nullptr;
 };
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a);
+// a device wait that nothing completes, bounded like the tiled kernel's
+// (reduce.cu): ADM_ERR_TIMEOUT once it gives up
+adm_status bounded_wait_check(cudaStream_t s);
 // contact terms (dyn.cu): replace the vertex-vertex pairs and vertex-face
 // elements (p, a, b, c) of pattern `kind` and extend its block pattern on the
 // GPU; evaluate the terms of a pass (after the tiled kernel) and add their

@@ -6,8 +6,9 @@
 // invalidates the capture), callers inside a real-time loop whose memory
 // budget is fixed up front, and hosts that route every device allocation
 // through their own pool and forbid the library from allocating behind it.
-// adm_grad_norm_noalloc gives them the chunked FP64 sum-of-squares reduction
-// that adm_eval_batch uses for its per-mesh gradient norms, with its scratch
+// adm_grad_norm_noalloc gives them a chunked sum-of-squares reduction like the
+// one adm_eval_batch uses for its per-mesh gradient norms, all in FP64, with
+// its scratch
 // (one FP64 partial per chunk) in a fixed-size static device array of this
 // file instead of a buffer owned by a handle.
 #include <cuda_runtime.h>

@@ -190,6 +190,33 @@ adm_status launch_reduce(adm_ctx *h, const EvalArgs &a, const int32_t *tri_off, 
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
+// ------------------------------------------------- bounded-wait check --
+// One thread waits, through the bounded wait the tiled kernel uses for its
+// metadata copy, on a shared-memory barrier that expects two arrivals and
+// gets one: the phase never completes, so the wait must give up.
+static __device__ int g_wait_result;
+
+__global__ void k_wait_check()
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+    g_wait_result = bulk_load_wait(&bar) ? 0 : ST_TIMEOUT;
+}
+
+adm_status bounded_wait_check(cudaStream_t s)
+{
+    k_wait_check<<<1, 1, 0, s>>>();
+    int r = -1;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyFromSymbolAsync(&r, g_wait_result, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return ADM_ERR_CUDA;
+    return r == ST_TIMEOUT ? ADM_ERR_TIMEOUT : ADM_ERR_CUDA;  // a completed wait would be a defect
+}
+
 adm_status launch_eval(adm_ctx *h, const EvalArgs &a)
 {
     // the matrix-free product and Hessian filtering are implemented by the tiled kernel only
