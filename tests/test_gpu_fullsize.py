@@ -9,7 +9,9 @@ piece:
   oracle's pattern shifted by the mesh's first vertex);
 * the 1M-triangle ARAP residual disk (FP32): sampled triangles, their four
   residual rows and 24 Jacobian entries (values and columns) recomputed by
-  the oracle on those triangles alone."""
+  the oracle on those triangles alone;
+* the matrix-free product on the whole shell batch: sampled meshes' H v
+  rows against the oracle's mesh Hessian times v."""
 import numpy as np
 import pytest
 
@@ -97,4 +99,37 @@ def test_arap_disk_1m_sampled_triangles_fp32():
     assert rel(r[rows], ref["r"]) <= TOL
     assert rel(jv[ents], ref["val"]) <= TOL
     assert np.array_equal(jcol[ents], ref["col"])
+    m.close()
+
+
+def test_shell_batch_700_hvp_sampled_meshes_fp32():
+    """The matrix-free product on the whole batch (the bench's H v line):
+    sampled meshes' H v rows against the oracle's assembled Hessian of that
+    mesh times v."""
+    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
+    x32 = b.x.astype(np.float32)
+    v32 = np.random.default_rng(7).normal(size=x32.shape).astype(np.float32)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    xd = torch.from_numpy(x32.reshape(-1)).cuda()
+    vd = torch.from_numpy(v32.reshape(-1)).cuda()
+    hv = torch.full_like(xd, float("nan"))
+    m.eval_hvp(adm.SHELL, adm.FP32, xd, vd, hv)
+    torch.cuda.synchronize()
+    assert m.status() == 0 and not torch.isnan(hv).any()
+    hv = hv.cpu().numpy().reshape(-1, 3)
+    nv_mesh = np.diff(b.v_off)
+    rng = np.random.default_rng(9)
+    picks = [int(rng.choice(np.flatnonzero(nv_mesh == nv_mesh.max()))),
+             int(rng.choice(np.flatnonzero(nv_mesh == nv_mesh.min())))]
+    for k in picks:
+        v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.SHELL, 3, params=SHELL_P)
+        ref = P.assemble(x32[v0:v1].astype(np.float64))
+        vm = v32[v0:v1].astype(np.float64)
+        want = np.zeros_like(vm)
+        for r in range(P.nV):
+            for q in range(P.row_ptr[r], P.row_ptr[r + 1]):
+                want[r] += ref["vals"][q] @ vm[P.col[q]]
+        assert rel(hv[v0:v1], want) <= TOL
     m.close()
