@@ -11,7 +11,9 @@ piece:
   residual rows and 24 Jacobian entries (values and columns) recomputed by
   the oracle on those triangles alone;
 * the matrix-free product on the whole shell batch: sampled meshes' H v
-  rows against the oracle's mesh Hessian times v."""
+  rows against the oracle's mesh Hessian times v;
+* the batch with 100k vertex-vertex and 100k vertex-face contact terms:
+  sampled meshes' rows of the extended pattern and their values."""
 import numpy as np
 import pytest
 
@@ -132,4 +134,59 @@ def test_shell_batch_700_hvp_sampled_meshes_fp32():
             for q in range(P.row_ptr[r], P.row_ptr[r + 1]):
                 want[r] += ref["vals"][q] @ vm[P.col[q]]
         assert rel(hv[v0:v1], want) <= TOL
+    m.close()
+
+
+def contact_terms(b, seed):
+    """Vertex-vertex pairs and vertex-face elements drawn within meshes of the
+    batch (as the bench's contact workload draws them)."""
+    rng = np.random.default_rng(seed)
+    nv_mesh, nf_mesh = np.diff(b.v_off), np.diff(b.f_off)
+    mi = rng.integers(b.n_mesh, size=150_000)
+    pi = b.v_off[mi] + rng.integers(nv_mesh[mi])
+    pj = b.v_off[mi] + rng.integers(nv_mesh[mi])
+    keep = pi != pj
+    pr = np.unique(np.sort(np.stack([pi[keep], pj[keep]], axis=1), axis=1), axis=0)
+    pr = rng.permutation(pr)[:100_000].astype(np.int32)
+    mi = rng.integers(b.n_mesh, size=110_000)
+    vp = b.v_off[mi] + rng.integers(nv_mesh[mi])
+    fq = b.faces[b.f_off[mi] + rng.integers(nf_mesh[mi])]
+    keep = (fq != vp[:, None]).all(axis=1)
+    vf = np.concatenate([vp[keep, None], fq[keep]], axis=1)[:100_000].astype(np.int32)
+    return pr, vf
+
+
+def test_shell_batch_700_with_contacts_sampled_meshes_fp32():
+    """100k vertex-vertex and 100k vertex-face terms on the whole batch (the
+    bench's contact line): sampled meshes' rows of the extended pattern
+    bit-exact, and their energies, gradient rows and Hessian rows against the
+    oracle's mesh terms plus the contact terms inside that mesh."""
+    kappa, dhat, area, hstep = 1.0e3, 0.2, 1e-3, 1.0
+    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
+    x32 = b.x.astype(np.float32)
+    pr, vf = contact_terms(b, 9)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    m.set_contacts(adm.SHELL, pr, vf, kappa, dhat, area, hstep)
+    rp, col, e, gn, g, H = batch_eval(m, adm.SHELL, x32)
+    nv_mesh = np.diff(b.v_off)
+    rng = np.random.default_rng(10)
+    picks = [int(rng.choice(np.flatnonzero(nv_mesh == nv_mesh.max()))),
+             int(rng.choice(np.flatnonzero(nv_mesh == nv_mesh.min())))]
+    for k in picks:
+        v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+        pk = pr[(pr[:, 0] >= v0) & (pr[:, 0] < v1)] - v0
+        qk = vf[(vf[:, 0] >= v0) & (vf[:, 0] < v1)] - v0
+        xk = x32[v0:v1].astype(np.float64)
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.SHELL, 3, params=SHELL_P)
+        base = P.assemble(xk)
+        erp, ecol = oracle.extended_pattern(P.row_ptr, P.col, pk, qk)
+        ref = oracle.add_interactions(base, xk, pk, kappa, dhat, area, hstep, P.row_ptr, P.col, qk)
+        blk = slice(rp[v0], rp[v1])
+        assert np.array_equal(rp[v0:v1 + 1] - rp[v0], erp) and np.array_equal(col[blk] - v0, ecol)
+        assert abs(e[k] - ref["energy"]) <= TOL * abs(ref["energy"])
+        assert rel(g[v0:v1], ref["grad"]) <= TOL
+        want = np.stack([ref["blocks"].get((r, int(c)), np.zeros((3, 3)))
+                         for r in range(P.nV) for c in ecol[erp[r]:erp[r + 1]]])
+        assert rel(H[blk], want) <= TOL
     m.close()
