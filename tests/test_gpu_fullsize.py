@@ -13,7 +13,9 @@ piece:
 * the matrix-free product on the whole shell batch: sampled meshes' H v
   rows against the oracle's mesh Hessian times v;
 * the batch with 100k vertex-vertex and 100k vertex-face contact terms:
-  sampled meshes' rows of the extended pattern and their values."""
+  sampled meshes' rows of the extended pattern and their values;
+* the filtered pass on the whole batch: sampled meshes against the oracle's
+  per-element projection."""
 import numpy as np
 import pytest
 
@@ -189,4 +191,26 @@ def test_shell_batch_700_with_contacts_sampled_meshes_fp32():
         want = np.stack([ref["blocks"].get((r, int(c)), np.zeros((3, 3)))
                          for r in range(P.nV) for c in ecol[erp[r]:erp[r + 1]]])
         assert rel(H[blk], want) <= TOL
+    m.close()
+
+
+def test_shell_batch_700_filtered_sampled_meshes_fp32():
+    """Per-term Hessian filtering on the whole batch (the bench's filtered
+    line): two sampled meshes against the oracle's per-element eigh
+    projection."""
+    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
+    x32 = b.x.astype(np.float32)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    m.set_projection(True, 0.0)
+    rp, col, e, gn, g, H = batch_eval(m, adm.SHELL, x32)
+    nv_mesh = np.diff(b.v_off)
+    small = np.flatnonzero(nv_mesh == nv_mesh.min())
+    for k in np.random.default_rng(11).choice(small, 2, replace=False):
+        v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.SHELL, 3, params=SHELL_P)
+        ref = P.assemble_projected(x32[v0:v1].astype(np.float64), 0.0)
+        blk = slice(rp[v0], rp[v1])
+        assert rel(H[blk], ref["vals"]) <= TOL
+        assert rel(g[v0:v1], ref["grad"]) <= TOL
     m.close()
