@@ -15,7 +15,8 @@ piece:
 * the batch with 100k vertex-vertex and 100k vertex-face contact terms:
   sampled meshes' rows of the extended pattern and their values;
 * the filtered pass on the whole batch: sampled meshes against the oracle's
-  per-element projection."""
+  per-element projection;
+* the 1000 x 1000 mass-spring cloth, whole."""
 import numpy as np
 import pytest
 
@@ -213,4 +214,30 @@ def test_shell_batch_700_filtered_sampled_meshes_fp32():
         blk = slice(rp[v0], rp[v1])
         assert rel(H[blk], ref["vals"]) <= TOL
         assert rel(g[v0:v1], ref["grad"]) <= TOL
+    m.close()
+
+
+def test_cloth_1000_full_fp32():
+    """The largest cloth of the bench (1000 x 1000 vertices, 3M springs,
+    FP32), whole: energy, gradient and every Hessian block against the
+    oracle."""
+    c = synth.cloth_grid(1000, sigma=0.05, seed=6)
+    cp = [1.0e4, 1.0 / 60.0, 1.0, 0.0, 0.0, -9.81]
+    m = adm.Mesh(c.rest, c.faces, 3)
+    m.set_inertia_target(c.xhat)
+    m.set_params(adm.MASS_SPRING, cp)
+    x32 = c.x.astype(np.float32)
+    _, nV, nnzb, rp, col = m.pattern(adm.MASS_SPRING)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.full((nV * 3,), float("nan"), device="cuda")
+    H = torch.full((nnzb * 9,), float("nan"), device="cuda")
+    m.eval(adm.MASS_SPRING, adm.FP32, torch.from_numpy(x32.reshape(-1)).cuda(), e, g, H)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    orp, ocol = oracle.pattern(c.nV, c.faces)
+    assert np.array_equal(rp.cpu().numpy(), orp) and np.array_equal(col.cpu().numpy(), ocol)
+    ref = oracle.cloth_assemble(c.rest, c.faces, x32.astype(np.float64), c.xhat, cp, orp, ocol)
+    assert abs(e.item() - ref["energy"]) <= TOL * abs(ref["energy"])
+    assert rel(g.cpu().numpy().reshape(-1, 3), ref["grad"]) <= TOL
+    assert rel(H.cpu().numpy().reshape(-1, 3, 3), ref["vals"]) <= TOL
     m.close()
