@@ -58,10 +58,59 @@ def parse():
 
 
 # ----------------------------------------------------------------- workload --
-def workload(rank: int, n_mesh: int = 700):
+def workload(rank: int = 0, n_mesh: int = 700):
+    """The seeded 700-icosphere shell batch (or its first n_mesh meshes).
+    Every rank draws the same batch; partition_meshes splits it."""
     levels = synth.shell_batch_levels("paper")[:n_mesh]
-    mesh = synth.shell_batch(levels, sigma=1e-3, seed=4 + rank)
+    mesh = synth.shell_batch(levels, sigma=1e-3, seed=4)
     return levels, mesh
+
+
+def partition_meshes(v_off, world: int) -> list[tuple[int, int]]:
+    """Contiguous mesh ranges [a, b), one per rank, with about equal vertex
+    counts: the cut between ranks r - 1 and r is the mesh boundary nearest to
+    r V / N (every rank keeps at least one mesh while there are N of them).
+    Meshes are independent units, so the ranks share no data on the path."""
+    v_off = np.asarray(v_off, dtype=np.int64)
+    n = len(v_off) - 1
+    total = int(v_off[-1])
+    cuts = [0]
+    for r in range(1, world):
+        # the mesh boundary nearest to r V / N, after the previous cut and
+        # leaving at least one mesh for each later rank (while meshes last)
+        lo = min(cuts[-1] + 1, n)
+        hi = max(lo, n - (world - r))
+        k = int(np.argmin(np.abs(v_off[lo:hi + 1] - (r * total) / world))) + lo
+        cuts.append(k)
+    cuts.append(n)
+    return [(cuts[r], cuts[r + 1]) for r in range(world)]
+
+
+def mesh_slice(mesh, a: int, b: int):
+    """Meshes [a, b) of a batch as a batch of their own (vertex and face
+    indices rebased)."""
+    vo, fo = mesh.v_off, mesh.f_off
+    return synth.Mesh(rest=mesh.rest[vo[a]:vo[b]], faces=mesh.faces[fo[a]:fo[b]] - vo[a],
+                      x=mesh.x[vo[a]:vo[b]], v_off=vo[a:b + 1] - vo[a], f_off=fo[a:b + 1] - fo[a],
+                      name=f"{mesh.name}[{a}:{b}]")
+
+
+def gather_per_mesh(dist, local: np.ndarray, ranges) -> np.ndarray:
+    """Per-mesh values of every rank's meshes, in batch order, on every rank
+    (one all_gather of padded rows); local is (n_local, k)."""
+    if dist is None:
+        return local
+    import torch
+
+    width = max(b - a for a, b in ranges)
+    k = local.shape[1]
+    buf = torch.zeros((width, k), dtype=torch.float64)
+    buf[: local.shape[0]] = torch.from_numpy(local)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    buf = buf.to(dev)
+    out = [torch.zeros_like(buf) for _ in ranges]
+    dist.all_gather(out, buf)
+    return np.concatenate([o.cpu().numpy()[: b - a] for o, (a, b) in zip(out, ranges)])
 
 
 def combine_ranks(dist, seconds: float, units: int, device: str = "cuda") -> tuple[float, int]:
@@ -100,6 +149,14 @@ def algorithmic_bytes(c, stage: str) -> int:
     if stage == "hinges":
         return 12 * V + 24 * H + 12 * V + 36 * nnzb
     return 12 * V + 32 * T + 24 * H + 12 * V + 36 * nnzb
+
+
+def algorithmic_bytes_fp64(c) -> int:
+    """The fused pass in FP64: x 24 B/V, faces 12 B/T, hinges 16 B/H,
+    triangle rest data 40 B/T, hinge rest data 16 B/H, gradient 24 B/V,
+    BSR 72 B per block."""
+    V, T, H, nnzb = c["n_vertices"], c["n_triangles"], c["n_hinges"], c["nnzb"]
+    return 48 * V + 52 * T + 32 * H + 72 * nnzb
 
 
 def measured_peaks():
@@ -248,7 +305,7 @@ def run_reference(args, rank: int, world: int):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(c, None),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -256,7 +313,7 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(c, assembler, n_mesh=700):
+def config_dict(c, assembler, n_mesh=700, world=1):
     return {
         "workload": "shell_batch: 700 icospheres, levels 4/5/6 = 668/28/4, StVK membrane + dihedral hinges"
                     + ("" if n_mesh == 700 else f" (first {n_mesh} meshes)"),
@@ -265,7 +322,9 @@ def config_dict(c, assembler, n_mesh=700):
         "precision": "fp32 local forward-mode AD, fp64 per-mesh energy and gradient norm",
         "assembler": assembler,
         "l2": "no flush: working set (inputs, slot maps, BSR output) > 1 GB >> 129 MB L2",
-        "parallelism": "replicas (one independent batch per GPU)",
+        "parallelism": (f"meshes partitioned over {world} ranks by vertex count (contiguous ranges), no data-path "
+                        "collective; per-mesh energies and norms all_gathered after the timed region")
+                       if world > 1 else "one GPU (the batch's meshes are partitioned across ranks when N > 1)",
     }
 
 
@@ -300,6 +359,39 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
     ms = _time_steps(torch, lambda: m.eval_batch(adm.SHELL, adm.FP32, x, e, gn, g, H, stream=stream), steps, stream)
     m.set_option(adm.OPT_GRAPH, 0)
     out["graph"] = {"ms_per_step": ms, "value": n_el / (ms * 1e-3), "unit": UNIT}
+
+    # the plain FP64 form of the same pass beside the FP32 one, and the
+    # FP32-vs-FP64 difference on the whole batch
+    c = counts(mesh)
+    x64 = torch.from_numpy(mesh.x.astype(np.float32).astype(np.float64)).cuda()
+    e64 = torch.zeros_like(e)
+    gn64 = torch.zeros_like(gn)
+    g64 = torch.zeros(g.numel(), dtype=torch.float64, device="cuda")
+    H64 = torch.zeros(H.numel(), dtype=torch.float64, device="cuda")
+    m.set_option(adm.OPT_PROFILE, steps)
+    ms64 = _time_steps(torch, lambda: m.eval_batch(adm.SHELL, adm.FP64, x64, e64, gn64, g64, H64, stream=stream),
+                       steps, stream)
+    prof = m.profile_read()
+    m.set_option(adm.OPT_PROFILE, 0)
+    assert m.status() == 0
+    m.eval_batch(adm.SHELL, adm.FP32, x, e, gn, g, H, stream=stream)
+    torch.cuda.synchronize()
+    ab64 = algorithmic_bytes_fp64(c)
+    peak, peak_src = measured_peaks()
+    k64 = prof["tiled"][0]
+    out["fp64_shell_batch"] = {
+        "workload": "the same 700-mesh shell batch, FP64 local AD and FP64 outputs (inputs: the FP32-rounded x)",
+        "value": n_el / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+        "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0},
+        "roofline": {"bound": "hbm", "kernel": "tiled", "algorithmic_bytes": ab64, "avg_ms": k64,
+                     "achieved": ab64 / (k64 * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": ab64 / (k64 * 1e-3) / 1e9 / peak, "peak_source": peak_src},
+        "fp32_vs_fp64_gpu": {
+            "hessian_rel_fro": (torch.linalg.norm(H.double() - H64) / torch.linalg.norm(H64)).item(),
+            "gradient_rel": (torch.linalg.norm(g.double() - g64) / torch.linalg.norm(g64)).item(),
+            "energy_rel": ((e - e64).abs().sum() / e64.abs().sum()).item(),
+            "sample": "whole batch"}}
+    del H64, g64
 
     # matrix-free Hessian-vector product on the same batch (energy, gradient
     # and H v; no BSR written)
@@ -424,13 +516,35 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
     relH = (torch.linalg.norm((H1 - H2).double()) / torch.linalg.norm(H2.double())).item()
     relg = (torch.linalg.norm((g1 - g2).double()) / torch.linalg.norm(g2.double())).item()
     relE = ((e1 - e2).abs().sum() / e2.abs().sum()).item()
+    # near rest the Neo-Hookean energy is almost zero: the energy error also
+    # in units that do not vanish there, the training spread of psi (s_psi)
+    # times thickness times the rest area of the batch
+    area_t = SHELL_PARAMS[2] * float(np.sum(np.linalg.norm(np.cross(
+        mesh.rest[mesh.faces[:, 1]] - mesh.rest[mesh.faces[:, 0]],
+        mesh.rest[mesh.faces[:, 2]] - mesh.rest[mesh.faces[:, 0]]), axis=1)) / 2)
+    s_psi = float(norm[7].item())
+    absE = ((e1 - e2).abs().sum()).item() / (s_psi * area_t)
+    # the same comparison on the batch deformed inside the training range
+    # (each mesh stretched by s_k in [0.7, 1.4] along seeded axes)
+    xs = torch.from_numpy(synth.stretched_batch(mesh).astype(np.float32)).cuda()
+    m.eval_batch(adm.MLP_MEMBRANE, adm.FP32, xs, e1, None, g1, H1, stream=stream)
+    m.eval_batch(adm.NH_MEMBRANE, adm.FP32, xs, e2, None, g2, H2, stream=stream)
+    torch.cuda.synchronize()
+    assert m.status() == 0
+    in_range = {"hessian_fro": (torch.linalg.norm((H1 - H2).double()) / torch.linalg.norm(H2.double())).item(),
+                "gradient": (torch.linalg.norm((g1 - g2).double()) / torch.linalg.norm(g2.double())).item(),
+                "energy": ((e1 - e2).abs().sum() / e2.abs().sum()).item(),
+                "batch": "synth.stretched_batch: per mesh x = c + R diag(s) R^T (X - c), s_k ~ U[0.7, 1.4]"}
     nT = mesh.nT
     out["mlp_membrane"] = {
         "workload": "learned Neo-Hookean membrane (MLP 3-64-64-1, BF16 tensor cores) on the shell batch triangles",
         "value": nT / (ms_mlp * 1e-3), "unit": "triangles/s", "ms_per_step": ms_mlp,
         "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0},
         "analytic_nh_ms_per_step": ms_nh, "analytic_nh_triangles_per_s": nT / (ms_nh * 1e-3),
-        "rel_err_vs_analytic_nh": {"hessian_fro": relH, "gradient": relg, "energy": relE},
+        "rel_err_vs_analytic_nh": {"hessian_fro": relH, "gradient": relg, "energy": relE,
+                                   "energy_abs_over_s_psi_area": absE,
+                                   "batch": "the shell batch (within 1e-3 of rest)"},
+        "rel_err_vs_analytic_nh_in_range": in_range,
         "training": {"samples": ns, "steps": n_train, "batch": batch, "first_loss": first,
                      "final_loss": loss.item(), "ms_total": train_ms,
                      "targets": "adm_mlp_nh_targets (library's analytic Neo-Hookean)"},
@@ -622,7 +736,9 @@ def run_ours(args, rank: int, world: int, local: int):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    levels, mesh = workload(rank, args.meshes)
+    levels, full = workload(0, args.meshes)
+    ranges = partition_meshes(full.v_off, world)
+    mesh = mesh_slice(full, *ranges[rank]) if world > 1 else full
     c = counts(mesh)
     m = adm.Mesh(mesh.rest, mesh.faces, 3, v_off=mesh.v_off, f_off=mesh.f_off)
     m.set_params(adm.SHELL, SHELL_PARAMS)
@@ -724,16 +840,42 @@ def run_ours(args, rank: int, world: int, local: int):
     e2e = {"value": n_el_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
            "d2h_bytes_per_step": int(2 * mesh.n_mesh * 8),
            "note": "adm_eval_batch_host: x in, per-mesh energy + gradient norm out; gradient and "
-                   "Hessian stay in device staging buffers"}
+                   "Hessian stay on the device (for an on-device solver)"}
+    # the same call with every output returned: the gradient and the BSR
+    # Hessian are copied to pinned host buffers each step as well
+    gh = torch.zeros(nV * 3, dtype=torch.float32).pin_memory()
+    Hh = torch.zeros(nnzb * 9, dtype=torch.float32).pin_memory()
+    m.eval_batch_host(adm.SHELL, adm.FP32, xh.numpy(), eh.numpy(), gnh.numpy(), gh.numpy(), Hh.numpy())
+    k_full = max(3, min(args.steps, 20))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_full):
+        m.eval_batch_host(adm.SHELL, adm.FP32, xh.numpy(), eh.numpy(), gnh.numpy(), gh.numpy(), Hh.numpy())
+    full_s = (time.perf_counter() - t0) / k_full
+    full_s, _ = combine_ranks(dist, full_s, n_el)
+    e2e_full = {"value": n_el_all / full_s, "unit": UNIT, "ms_per_step": full_s * 1e3,
+                "h2d_bytes_per_step": int(xh.numel() * 4),
+                "d2h_bytes_per_step": int(2 * mesh.n_mesh * 8 + gh.numel() * 4 + Hh.numel() * 4),
+                "note": "adm_eval_batch_host: x in; per-mesh energy and gradient norm, the gradient and the "
+                        "BSR Hessian out to pinned host memory every step"}
+    del Hh, gh
+
+    # per-mesh energies and gradient norms of every rank's meshes, in batch
+    # order (one all_gather after the timed region)
+    per_mesh = gather_per_mesh(dist, np.stack([e.cpu().numpy(), gn.cpu().numpy()], axis=1), ranges)
+    partition = {"ranges": [list(r) for r in ranges],
+                 "vertices_per_rank": [int(full.v_off[b] - full.v_off[a]) for a, b in ranges],
+                 "meshes_gathered": int(per_mesh.shape[0]), "energy_total": float(per_mesh[:, 0].sum())}
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and world == 1:
         extras = measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_dict(c, assembler, args.meshes),
+        "config": config_dict(counts(full), assembler, args.meshes, world),
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": ab,
@@ -743,6 +885,8 @@ def run_ours(args, rank: int, world: int, local: int):
                  "assembled_scalars_per_s": c["nnzb"] * 9 * world / (ms_step * 1e-3),
                  "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0}},
         "e2e": e2e,
+        "e2e_all_outputs": e2e_full,
+        "partition": partition,
         "clocks": clk,
         "autotune": tuned,
         **extras,
@@ -775,6 +919,22 @@ def run_ours(args, rank: int, world: int, local: int):
         Hs = H[: P.nnzb * 9].cpu().numpy().reshape(-1, 3, 3).astype(np.float64)
         gs = g[: P.nV * 3].cpu().numpy().reshape(-1, 3).astype(np.float64)
         es = e[:n].sum().item()
+        # the FP64 form on the same sample (its own pass into FP64 buffers)
+        x64 = torch.from_numpy(mesh.x.astype(np.float32).astype(np.float64)).cuda()
+        e64 = torch.zeros_like(e)
+        g64 = torch.zeros(g.numel(), dtype=torch.float64, device="cuda")
+        H64 = torch.zeros(H.numel(), dtype=torch.float64, device="cuda")
+        m.eval_batch(adm.SHELL, adm.FP64, x64, e64, None, g64, H64, stream=stream)
+        torch.cuda.synchronize()
+        assert m.status() == 0
+        H64s = H64[: P.nnzb * 9].cpu().numpy().reshape(-1, 3, 3)
+        g64s = g64[: P.nV * 3].cpu().numpy().reshape(-1, 3)
+        line["error_fp64_gpu_vs_fp64_oracle"] = {
+            "hessian_rel_fro": float(np.linalg.norm(H64s - ref["vals"]) / np.linalg.norm(ref["vals"])),
+            "gradient_rel": float(np.linalg.norm(g64s - ref["grad"]) / np.linalg.norm(ref["grad"])),
+            "energy_rel": float(abs(e64[:n].sum().item() - ref["energy"]) / abs(ref["energy"])),
+            "sample": f"first {n} meshes", "tolerance": 1e-12}
+        del H64, g64
         line["error_vs_fp64_oracle"] = {
             "hessian_rel_fro": float(np.linalg.norm(Hs - ref["vals"]) / np.linalg.norm(ref["vals"])),
             "gradient_rel": float(np.linalg.norm(gs - ref["grad"]) / np.linalg.norm(ref["grad"])),

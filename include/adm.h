@@ -323,16 +323,19 @@ adm_status adm_profile_read(adm_handle h, float *avg_ms, int32_t *n_launches, in
  * `stream`.  This is the gradient-norm reduction of adm_eval_batch as a call
  * that allocates nothing and needs no handle; the paper has no counterpart.
  * It is meant for callers that cannot call cudaMalloc where they need the
- * norm: code running while its stream is captured into a CUDA graph,
- * real-time loops whose device memory is fixed in advance, and hosts that
- * own every device allocation through their own pool.
+ * norm: real-time loops whose device memory is fixed in advance (an
+ * allocation there can stall or fail mid-loop), plug-ins inside a host
+ * framework that owns the device's memory budget, and hosts that route
+ * every device allocation through their own pool.
  *  - Scratch: a static device array of 4096 FP64 partial sums (32 KiB) that
  *    every GPU loading the library holds until the process exits; n may be at
  *    most 4096 * 8192 = 33,554,432 entries, larger n returns ADM_ERR_ARG and
  *    launches nothing.
  *  - The first call on a device, with that device current, resolves the
- *    array's device address (cudaGetSymbolAddress); make that first call
- *    before any stream capture.
+ *    array's device address (cudaGetSymbolAddress) and keeps it for that
+ *    device; make that first call before any stream capture.  The kept
+ *    address belongs to the device's primary context: do not use this call
+ *    after a cudaDeviceReset of that device, nor from another context on it.
  *  - All calls share the one array and it keeps the last call's partials:
  *    calls whose work overlaps on the GPU (different streams, no ordering)
  *    race on it.  Calls ordered on one stream are safe; nothing needs

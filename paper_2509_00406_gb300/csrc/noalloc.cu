@@ -1,11 +1,11 @@
 // noalloc.cu -- FP64 gradient 2-norm that allocates nothing.
 //
 // Some callers cannot call cudaMalloc at the point where they need this
-// reduction: code that runs while a stream is being captured into a CUDA
-// graph (an allocation there is not a stream operation and breaks or
-// invalidates the capture), callers inside a real-time loop whose memory
-// budget is fixed up front, and hosts that route every device allocation
-// through their own pool and forbid the library from allocating behind it.
+// reduction: callers inside a real-time loop whose memory budget is fixed up
+// front (an allocation there can stall or fail mid-loop), plug-ins running
+// inside a host framework that owns the device's memory budget, and hosts
+// that route every device allocation through their own pool and forbid the
+// library from allocating behind it.
 // adm_grad_norm_noalloc gives them a chunked sum-of-squares reduction like the
 // one adm_eval_batch uses for its per-mesh gradient norms, all in FP64, with
 // its scratch
@@ -30,6 +30,8 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
 
 // Device address of g_noalloc_partials per device, resolved on the first call
 // made with that device current (the name itself is only a host-side handle).
+// The address is that of the module loaded in the device's primary context;
+// a cudaDeviceReset unloads it, so the call is not for use after a reset.
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double *g_partials_addr[kMaxDevices] = {};

@@ -42,6 +42,7 @@ __all__ = [
     "shell_batch",
     "shell_batch_levels",
     "membrane_samples",
+    "stretched_batch",
     "tiny_meshes",
 ]
 
@@ -334,6 +335,23 @@ def shell_batch(levels, sigma: float = 1e-3, spacing: float = 3.0, seed: int = 4
         f_off=np.asarray(f_off, dtype=np.int64),
         name=f"shell_batch{len(levels)}",
     )
+
+
+def stretched_batch(mesh: Mesh, lo: float = 0.7, hi: float = 1.4, seed: int = 9) -> np.ndarray:
+    """Deformed positions of a shell batch inside the learned membrane's
+    training range: mesh m is mapped about its rest centroid c_m by
+    x = c_m + R_m diag(s_1, s_2, s_3) R_m^T (X - c_m), s_k ~ U[lo, hi] and
+    R_m a uniform random rotation, so every triangle's in-plane principal
+    stretches lie in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    x = np.empty_like(mesh.rest)
+    for m in range(len(mesh.v_off) - 1):
+        a, b = mesh.v_off[m], mesh.v_off[m + 1]
+        R = _random_rotation(rng)
+        A = R @ np.diag(rng.uniform(lo, hi, size=3)) @ R.T
+        c = mesh.rest[a:b].mean(0)
+        x[a:b] = c + (mesh.rest[a:b] - c) @ A.T
+    return x
 
 
 # --------------------------------------------------------------------------

@@ -16,7 +16,12 @@ piece:
   sampled meshes' rows of the extended pattern and their values;
 * the filtered pass on the whole batch: sampled meshes against the oracle's
   per-element projection;
-* the 1000 x 1000 mass-spring cloth, whole."""
+* the 1000 x 1000 mass-spring cloth, whole;
+* the shell batch in FP64: sampled meshes at 1e-12;
+* the learned membrane with weights trained by the bench's recipe, on the
+  bench's batch and on the batch stretched inside the training range:
+  sampled meshes (and sampled rows of a 160-tile mesh) against the oracle's
+  network on the same BF16 weights."""
 import numpy as np
 import pytest
 
@@ -240,4 +245,122 @@ def test_cloth_1000_full_fp32():
     assert abs(e.item() - ref["energy"]) <= TOL * abs(ref["energy"])
     assert rel(g.cpu().numpy().reshape(-1, 3), ref["grad"]) <= TOL
     assert rel(H.cpu().numpy().reshape(-1, 3, 3), ref["vals"]) <= TOL
+    m.close()
+
+
+def test_shell_batch_700_sampled_meshes_fp64():
+    """The FP64 form of the shell batch (the bench's FP64 line): sampled
+    meshes against the oracle at the FP64 bar."""
+    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
+    x64 = b.x.astype(np.float32).astype(np.float64)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    _, nV, nnzb, rp, col = m.pattern(adm.SHELL)
+    e = torch.zeros(m.n_mesh, dtype=torch.float64, device="cuda")
+    gn = torch.zeros_like(e)
+    g = torch.full((nV * 3,), float("nan"), dtype=torch.float64, device="cuda")
+    H = torch.full((nnzb * 9,), float("nan"), dtype=torch.float64, device="cuda")
+    m.eval_batch(adm.SHELL, adm.FP64, torch.from_numpy(x64).cuda(), e, gn, g, H)
+    torch.cuda.synchronize()
+    assert m.status() == 0 and not torch.isnan(H).any() and not torch.isnan(g).any()
+    rp, e, gn = rp.cpu().numpy(), e.cpu().numpy(), gn.cpu().numpy()
+    g, H = g.cpu().numpy().reshape(-1, 3), H.cpu().numpy().reshape(-1, 3, 3)
+    nv_mesh = np.diff(b.v_off)
+    rng = np.random.default_rng(12)
+    picks = [int(rng.choice(np.flatnonzero(nv_mesh == nv_mesh.max()))),
+             int(rng.choice(np.flatnonzero(nv_mesh == nv_mesh.min()))), b.n_mesh - 1]
+    for k in picks:
+        v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.SHELL, 3, params=SHELL_P)
+        ref = P.assemble(x64[v0:v1])
+        blk = slice(rp[v0], rp[v1])
+        assert abs(e[k] - ref["energy"]) <= 1e-12 * abs(ref["energy"])
+        assert rel(g[v0:v1], ref["grad"]) <= 1e-12
+        assert abs(gn[k] - np.linalg.norm(ref["grad"])) <= 1e-12 * np.linalg.norm(ref["grad"])
+        assert rel(H[blk], ref["vals"]) <= 1e-12
+    m.close()
+
+
+def _bf16(a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _train_bench_recipe():
+    """The bench's learned-membrane training: 2^20 samples (stretches in
+    [0.7, 1.4], seed 5) with the library's analytic Neo-Hookean targets,
+    1,500 Adam steps of 8,192, lr 3e-3 decaying to 3e-4, seeded start."""
+    ns = 1 << 20
+    Fs = torch.from_numpy(synth.membrane_samples(ns, seed=5).reshape(ns, 6).astype(np.float32)).cuda()
+    Ig = torch.zeros((ns, 3), device="cuda")
+    pg = torch.zeros(ns, device="cuda")
+    gg = torch.zeros((ns, 3), device="cuda")
+    adm.MLP.nh_targets(Fs, SHELL_P[0], SHELL_P[1], Ig, pg, gg)
+    norm = torch.cat([Ig.mean(0), Ig.std(0), pg.mean()[None], pg.std()[None]]).contiguous()
+    rng = np.random.default_rng(0)
+    th0 = np.zeros(adm.MLP_NPARAM, dtype=np.float32)
+    th0[:192] = rng.normal(scale=0.6, size=192)
+    th0[256:4352] = rng.normal(scale=1 / 8, size=4096)
+    th0[4416:4480] = rng.normal(scale=1 / 8, size=64)
+    th = torch.from_numpy(th0).cuda()
+    mo, vo, gr = torch.zeros_like(th), torch.zeros_like(th), torch.zeros_like(th)
+    ws = torch.zeros(adm.MLP.workspace_size() // 4 + 1, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    n_train, batch = 1500, 8192
+    perm = torch.randperm(ns, device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    for step in range(1, n_train + 1):
+        idx = perm[(step - 1) * batch % ns:(step - 1) * batch % ns + batch]
+        adm.MLP.loss_grad(th, norm, Ig[idx].contiguous(), pg[idx].contiguous(), gg[idx].contiguous(), 1.0,
+                          loss, gr, ws)
+        adm.MLP.adam(th, mo, vo, gr, step, 3e-3 * (0.1 ** (step / n_train)))
+    torch.cuda.synchronize()
+    return th, norm
+
+
+@pytest.mark.parametrize("deform", ["bench", "in_range"])
+def test_learned_membrane_batch_700_trained_sampled_meshes(deform):
+    """The timed learned-membrane path -- per-triangle network table, then the
+    tiled composition -- with trained weights on the whole 700-mesh batch,
+    against the oracle's network on the same BF16 weights (FP64, no
+    activation rounding; reading: BF16-level agreement, 3e-2).  Sampled
+    meshes: two of the smallest and the last one whole (energy, gradient rows,
+    Hessian rows), and 200 sampled vertices of a level-6 mesh (160 tiles):
+    their gradient and Hessian rows.
+
+    On the bench's batch (within 1e-3 of rest) the gradient is left out: the
+    terms psi_a dI_a/dx of a stress-free state cancel to about 1e-3 of their
+    size, so the BF16 rounding of the network's activations (about 1e-3 of
+    psi_a) is of the order of the gradient itself.  The batch stretched inside
+    the training range has gradients of full size and checks them."""
+    b = synth.shell_batch(synth.shell_batch_levels("paper"), sigma=1e-3, seed=4)
+    x = b.x if deform == "bench" else synth.stretched_batch(b)
+    x32 = x.astype(np.float32)
+    th, norm = _train_bench_recipe()
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.MLP_MEMBRANE, SHELL_P)
+    m.mlp_attach(th, norm)
+    rp, col, e, gn, g, H = batch_eval(m, adm.MLP_MEMBRANE, x32)
+    oracle.mlp_set(_bf16(th.cpu().numpy()), norm.cpu().numpy().astype(np.float64))
+    nv_mesh = np.diff(b.v_off)
+    rng = np.random.default_rng(13)
+    small = np.flatnonzero(nv_mesh == nv_mesh.min())
+    whole = [int(k) for k in rng.choice(small[small != b.n_mesh - 1], 2, replace=False)] + [b.n_mesh - 1]
+    for k in whole:
+        v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.MLP, 3, params=SHELL_P)
+        ref = P.assemble(x32[v0:v1].astype(np.float64))
+        blk = slice(rp[v0], rp[v1])
+        assert abs(e[k] - ref["energy"]) <= 3e-2 * abs(ref["energy"]), (k, e[k], ref["energy"])
+        if deform == "in_range":
+            assert rel(g[v0:v1], ref["grad"]) <= 3e-2
+        assert rel(H[blk], ref["vals"]) <= 3e-2
+    k = int(rng.choice(np.flatnonzero(nv_mesh == nv_mesh.max())))
+    v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+    P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.MLP, 3, params=SHELL_P)
+    rows = np.sort(rng.choice(P.nV, 200, replace=False))
+    ref = P.assemble(x32[v0:v1].astype(np.float64), rows=rows)
+    bl = np.concatenate([np.arange(P.row_ptr[r], P.row_ptr[r + 1]) for r in rows])
+    Hm = H[rp[v0]:rp[v1]]
+    if deform == "in_range":
+        assert rel(g[v0:v1][rows], ref["grad"][rows]) <= 3e-2
+    assert rel(Hm[bl], ref["vals"][bl]) <= 3e-2
     m.close()

@@ -1,6 +1,7 @@
 """adm_grad_norm_noalloc: the FP64 gradient-norm reduction for callers that
-cannot allocate device memory where they need it (inside a stream capture,
-in a loop with a fixed memory budget, under a host-owned allocator).  Its
+cannot allocate device memory where they need it (in a loop with a fixed
+memory budget, inside a host framework that owns the device's memory, under
+a host-owned allocator).  Its
 scratch is a static device array of the library, so it needs no handle and
 calls no cudaMalloc.  It must give the same norm as the handle-based batched
 evaluation (adm_eval_batch) within the tolerances of the other GPU tests, on
