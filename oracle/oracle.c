@@ -588,9 +588,35 @@ static int nh_cf(const double *x, const double *Dinv, double area, params_t q, d
  * dtheta/dx0 = -(1 - sa) dtheta/dxa - (1 - sb) dtheta/dxb,
  * dtheta/dx1 = -sa dtheta/dxa - sb dtheta/dxb,
  * with s_w = (x_w - x0).e/|e|^2 the position of the wing's foot on the edge
- * (discrete-shells bending gradient, Grinspun et al. 2003; Tamstorf 2013) */
+ * (discrete-shells bending gradient, Grinspun et al. 2003; Tamstorf 2013).
+ * The Hessian of theta is the derivative of these four vectors, taken by the
+ * product rule with
+ *   d nA = de x u + e x du,  d nB = dm x v + m x dv   (m = x0 - x1, v = xb - x1),
+ *   d |e| = e.de / |e|,      d s_w = (dw.e + w.de)/|e|^2 - 2 s_w e.de/|e|^2,
+ * and E = w (theta - thetabar)^2 gives
+ *   H = 2 w (grad theta grad theta^T + (theta - thetabar) Hess theta). */
+
+/* [a]x, the matrix of b -> a x b */
+static void skew3(const double *a, double S[3][3])
+{
+    S[0][0] = 0.0;   S[0][1] = -a[2]; S[0][2] = a[1];
+    S[1][0] = a[2];  S[1][1] = 0.0;   S[1][2] = -a[0];
+    S[2][0] = -a[1]; S[2][1] = a[0];  S[2][2] = 0.0;
+}
+
+/* derivative of the wing gradient g = -el n / |n|^2 with respect to one
+ * vertex, given that vertex's dn (3x3) and d el (3) */
+static void dwing(const double *n, double n2, double el, double N[3][3], const double L[3], double out[3][3])
+{
+    double nN[3];
+    for (int j = 0; j < 3; ++j) nN[j] = n[0] * N[0][j] + n[1] * N[1][j] + n[2] * N[2][j];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            out[i][j] = -n[i] * L[j] / n2 - el * N[i][j] / n2 + 2.0 * el * n[i] * nN[j] / (n2 * n2);
+}
+
 static int hinge_cf(const double *x, double thetabar, double abar, params_t q, double *f,
-                    double *g)
+                    double *g, double *H /* 12x12 row-major or NULL */)
 {
     const double *x0 = x, *x1 = x + 3, *xa = x + 6, *xb = x + 9;
     double e[3], u[3], m[3], v[3], nA[3], nB[3], c[3];
@@ -619,12 +645,61 @@ static int hinge_cf(const double *x, double thetabar, double abar, params_t q, d
     for (int d = 0; d < 3; ++d) wb[d] = xb[d] - x0[d];
     double sa = dot3(u, e) / ee, sb = dot3(wb, e) / ee;
     double fp = 2.0 * w * (th - thetabar);
+    double gt[12];  /* grad theta, vertex order (x0, x1, xa, xb) */
     for (int d = 0; d < 3; ++d) {
-        g[0 + d] = fp * (-(1.0 - sa) * ga[d] - (1.0 - sb) * gb[d]);
-        g[3 + d] = fp * (-sa * ga[d] - sb * gb[d]);
-        g[6 + d] = fp * ga[d];
-        g[9 + d] = fp * gb[d];
+        gt[0 + d] = -(1.0 - sa) * ga[d] - (1.0 - sb) * gb[d];
+        gt[3 + d] = -sa * ga[d] - sb * gb[d];
+        gt[6 + d] = ga[d];
+        gt[9 + d] = gb[d];
     }
+    for (int i = 0; i < 12; ++i) g[i] = fp * gt[i];
+    if (!H) return 0;
+    double Su[3][3], Se[3][3], Sv[3][3], Sm[3][3];
+    skew3(u, Su);
+    skew3(e, Se);
+    skew3(v, Sv);
+    skew3(m, Sm);
+    double eh[3] = {e[0] / el, e[1] / el, e[2] / el};
+    double ue = dot3(u, e), we = dot3(wb, e);
+    double Ht[12][12];
+    for (int k = 0; k < 4; ++k) {
+        double NA[3][3], NB[3][3], L[3] = {0.0, 0.0, 0.0}, dsa[3] = {0.0, 0.0, 0.0}, dsb[3] = {0.0, 0.0, 0.0};
+        double de_sign = k == 0 ? -1.0 : (k == 1 ? 1.0 : 0.0);  /* de = de_sign dx_k */
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                switch (k) {
+                case 0: NA[i][j] = Su[i][j] - Se[i][j]; NB[i][j] = -Sv[i][j]; break;
+                case 1: NA[i][j] = -Su[i][j]; NB[i][j] = Sv[i][j] - Sm[i][j]; break;
+                case 2: NA[i][j] = Se[i][j]; NB[i][j] = 0.0; break;
+                default: NA[i][j] = 0.0; NB[i][j] = Sm[i][j]; break;
+                }
+            }
+        for (int j = 0; j < 3; ++j) {
+            L[j] = de_sign * eh[j];
+            /* d(u.e) and d(wb.e) for this vertex */
+            double due = 0.0, dwe = 0.0;
+            if (k == 0) { due = -(e[j] + u[j]); dwe = -(e[j] + wb[j]); }
+            if (k == 1) { due = u[j]; dwe = wb[j]; }
+            if (k == 2) due = e[j];
+            if (k == 3) dwe = e[j];
+            double dee = 2.0 * de_sign * e[j];
+            dsa[j] = due / ee - ue * dee / (ee * ee);
+            dsb[j] = dwe / ee - we * dee / (ee * ee);
+        }
+        double Da[3][3], Db[3][3];
+        dwing(nA, dA, el, NA, L, Da);
+        dwing(nB, dB, el, NB, L, Db);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                int col = 3 * k + j;
+                Ht[0 + i][col] = -(1.0 - sa) * Da[i][j] + ga[i] * dsa[j] - (1.0 - sb) * Db[i][j] + gb[i] * dsb[j];
+                Ht[3 + i][col] = -sa * Da[i][j] - ga[i] * dsa[j] - sb * Db[i][j] - gb[i] * dsb[j];
+                Ht[6 + i][col] = Da[i][j];
+                Ht[9 + i][col] = Db[i][j];
+            }
+    }
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j) H[i * 12 + j] = 2.0 * w * (gt[i] * gt[j] + (th - thetabar) * Ht[i][j]);
     return 0;
 }
 
@@ -855,10 +930,7 @@ static int tri_local(int energy, int route, const double *xl, int vd, const doub
 static int hinge_local(int route, const double *xl, double thetabar, double abar, params_t q,
                        double *f, double *g, double *H)
 {
-    if (route == 1) {
-        memset(H, 0, sizeof(double) * 144);
-        return hinge_cf(xl, thetabar, abar, q, f, g);
-    }
+    if (route == 1) return hinge_cf(xl, thetabar, abar, q, f, g, H);
     hd xs[12], r;
     for (int i = 0; i < 12; ++i) xs[i] = hd_var(12, xl[i], i);
     if (hinge_hd(xs, thetabar, abar, q, &r)) return 1;

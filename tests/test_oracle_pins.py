@@ -280,6 +280,49 @@ def test_hinge_routes_fd_invariances():
     assert np.abs(np.cross(x, g).sum(0)).max() < 1e-12 * np.abs(g).max()
 
 
+@pytest.mark.parametrize("pa,pb", [(0.2, -0.4), (0.9, 0.7), (-1.3, 0.4), (2.6, -2.5)])
+def test_hinge_closed_form_hessian(pa, pb):
+    """The closed-form hinge Hessian (product rule on the discrete-shells
+    gradient) against the hyper-dual route and against Richardson
+    differences of the closed-form gradient; symmetric, translations in its
+    null space; at rest it is 2 w dtheta dtheta^T."""
+    x = _hinge_x(pa, pb) + RNG.normal(scale=0.05, size=(4, 3))
+    kw = dict(thetabar=0.35, abar=0.6, params=[1.5, 0.5])
+    cf = oracle.local(oracle.HINGE, x.ravel(), route=1, **kw)
+    hd = oracle.local(oracle.HINGE, x.ravel(), route=0, **kw)
+    assert rel(cf["H"], hd["H"]) < 1e-11
+    assert rel(cf["H"], cf["H"].T) < 1e-13
+    fdH = np.stack([fd_grad(lambda y: oracle.local(oracle.HINGE, y, route=1, **kw)["g"][i], x.ravel(), h=1e-4)
+                    for i in range(12)])
+    assert rel(cf["H"], fdH) < 1e-8
+    for d in range(3):
+        t = np.zeros((4, 3))
+        t[:, d] = 1.0
+        assert np.abs(cf["H"] @ t.ravel()).max() < 1e-11 * np.abs(cf["H"]).max()
+    rest = oracle.hinge_rest(np.array([[0, 1, 2, 3]], dtype=np.int32), x)
+    at = oracle.local(oracle.HINGE, x.ravel(), thetabar=rest[0][0], abar=0.6, params=[1.5, 0.5], route=1)
+    w = 1.5 * 0.6 / 3.0 * 0.5 ** 2
+    near = oracle.local(oracle.HINGE, x.ravel(), thetabar=rest[0][0] - 1e-3, abar=0.6, params=[1.5, 0.5], route=1)
+    dth = near["g"] / (2 * w * 1e-3)
+    assert rel(at["H"], 2 * w * np.outer(dth, dth)) < 1e-10
+
+
+def test_shell_closed_form_route_assembles_hyperdual_result():
+    """Route 1 of the whole shell (closed-form StVK and hinge Hessians)
+    assembles the same gradient and BSR Hessian as route 0."""
+    sh = synth.icosphere_shell(2, sigma=2e-2, seed=3)
+    P = oracle.Problem(sh.rest, sh.faces, oracle.SHELL, 3, params=[E, NU, T])
+    a = P.assemble(sh.x, route=0)
+    b = P.assemble(sh.x, route=1)
+    assert np.isclose(a["energy"], b["energy"], rtol=1e-12)
+    assert rel(b["grad"], a["grad"]) < 1e-12
+    assert rel(b["vals"], a["vals"]) < 1e-12
+    Pb = oracle.Problem(sh.rest, sh.faces, oracle.HINGE, 3, params=[0.7, 1.0])
+    a = Pb.assemble(sh.x, route=0)
+    b = Pb.assemble(sh.x, route=1)
+    assert rel(b["vals"], a["vals"]) < 1e-11
+
+
 # --------------------------------------------------------------------------
 # 7. area (Sec. 7.6, gradient printed in the paper)
 # --------------------------------------------------------------------------
