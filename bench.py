@@ -241,14 +241,14 @@ def _oracle_worker(args):
     x = mesh.x[vo[a]:vo[b]].astype(np.float32).astype(np.float64)
     P = oracle.Problem(rest, faces, oracle.SHELL, 3, params=SHELL_PARAMS)
     t0 = time.perf_counter()
-    P.assemble(x)
+    P.assemble(x, route=1)
     return P.nT + P.nH, time.perf_counter() - t0
 
 
 def oracle_all_cores(mesh, per_worker: int):
-    """The oracle on every host core at once (one spawned process per core,
-    each on its own run of meshes, about per_worker elements each): elements
-    over the slowest worker's assembly time."""
+    """The oracle's closed-form route on every host core at once (one spawned
+    process per core, each on its own run of meshes, about per_worker
+    elements each): elements over the slowest worker's assembly time."""
     import multiprocessing as mp
 
     n = max(1, os.cpu_count() or 1)
@@ -286,22 +286,23 @@ def run_reference(args, rank: int, world: int):
     c = counts(mesh)
     # calibrate on one mesh, then size each step so that K + W steps take
     # about two minutes
-    P1, x1 = oracle_sample(levels, mesh, 1)
+    P1, x1 = oracle_sample(levels, mesh, 4)
     t0 = time.perf_counter()
-    P1.assemble(x1)
+    P1.assemble(x1, route=1)
     rate = (P1.nT + P1.nH) / (time.perf_counter() - t0)
     per_step_s = max(0.2, 120.0 / max(1, args.steps + args.warmup))
     n = meshes_for_elements(mesh, int(rate * per_step_s))
     P, x = oracle_sample(levels, mesh, n)
     n_el = P.nT + P.nH
     for _ in range(args.warmup):
-        P.assemble(x)
+        P.assemble(x, route=1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        P.assemble(x)
+        P.assemble(x, route=1)
     dt = (time.perf_counter() - t0) / args.steps
     value = n_el / dt
-    sample = f"first {n} of 700 meshes ({n_el} elements) per step, hyper-dual route, 1 thread"
+    sample = (f"first {n} of 700 meshes ({n_el} elements) per step, closed-form route (hand-derived StVK and "
+              f"discrete-shells hinge Hessians), 1 thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
@@ -560,12 +561,13 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
     gn7 = torch.zeros(1, dtype=torch.float64, device="cuda")
     g7 = torch.zeros(nV7 * 3, dtype=torch.float32, device="cuda")
     H7 = torch.zeros(nnzb7 * 9, dtype=torch.float32, device="cuda")
-    best7, _ = m7.autotune(adm.SHELL, adm.FP32, x7)
+    best7, thr7, _ = m7.autotune(adm.SHELL, adm.FP32, x7)
     ms7 = _time_steps(torch, lambda: m7.eval_batch(adm.SHELL, adm.FP32, x7, e7, gn7, g7, H7, stream=stream), steps,
                       stream)
     nel7 = sh.nT + 3 * sh.nT // 2
     out["shell_level7"] = {"workload": "elastic shell, icosphere level 7 (163,842 V), FP32, no L2 flush",
-                           "value": nel7 / (ms7 * 1e-3), "unit": UNIT, "ms_per_step": ms7, "tile_tris": best7}
+                           "value": nel7 / (ms7 * 1e-3), "unit": UNIT, "ms_per_step": ms7,
+                           "tile_units": best7, "tile_threads": thr7}
     m7.close()
 
     # least-squares Jacobian, ~1M-triangle noisy disk, FP32
@@ -747,17 +749,17 @@ def run_ours(args, rank: int, world: int, local: int):
     if args.tile_tris > 0:
         m.set_option(adm.OPT_TILE_TRIS, args.tile_tris)
     assembler = "per-element atomic scatter" if args.assembler == 1 else \
-        f"tiled shared-memory (tile_tris={args.tile_tris if args.tile_tris > 0 else 512})"
+        f"staged-gather tiles (units per tile <= {args.tile_tris if args.tile_tris > 0 else 224})"
     _, nV, nnzb, _, _ = m.pattern(adm.SHELL)
     assert nnzb == c["nnzb"] and nV == c["n_vertices"]
     n_el = c["n_triangles"] + c["n_hinges"]
     x = torch.from_numpy(mesh.x.astype(np.float32)).cuda()
     tuned = None
     if args.assembler != 1 and args.tile_tris <= 0 and not args.no_autotune:
-        best, best_ms = m.autotune(adm.SHELL, adm.FP32, x)
-        tuned = {"tile_tris": best, "ms_per_pass": round(best_ms, 4),
-                 "candidates": [128, 192, 256, 384, 512, 768]}
-        assembler = f"tiled shared-memory (autotuned tile_tris={best})"
+        best, thr, best_ms = m.autotune(adm.SHELL, adm.FP32, x)
+        tuned = {"tile_units": best, "tile_threads": thr, "ms_per_pass": round(best_ms, 4),
+                 "candidates": {"256 threads": [96, 128, 160, 192, 224], "128 threads": [48, 64, 96, 112]}}
+        assembler = f"staged-gather tiles (autotuned: {thr} threads per block, units per tile <= {best})"
     e = torch.zeros(mesh.n_mesh, dtype=torch.float64, device="cuda")
     gn = torch.zeros(mesh.n_mesh, dtype=torch.float64, device="cuda")
     g = torch.zeros(nV * 3, dtype=torch.float32, device="cuda")
@@ -800,8 +802,8 @@ def run_ours(args, rank: int, world: int, local: int):
     dom = max(kern, key=lambda k: kern[k][0] * kern[k][1])
     dom_ms = kern[dom][0]
     launches_per_step = sum(v[1] for v in kern.values()) / args.steps
-    if args.assembler != 1:
-        launches_per_step += prof["zero"][1] / args.steps   # k_zero_shared
+    if args.assembler == 1:
+        launches_per_step += prof["zero"][1] / args.steps   # the atomic scatter's zero fill
     peak, peak_src = measured_peaks()
     ab = algorithmic_bytes(c, dom)
     achieved = ab / (dom_ms * 1e-3) / 1e9
@@ -899,21 +901,22 @@ def run_ours(args, rank: int, world: int, local: int):
         step()
         torch.cuda.synchronize()
         assert m.status() == 0
-        n = meshes_for_elements(mesh, 550_000)
+        n = meshes_for_elements(mesh, 5_000_000)
         P, xs = oracle_sample(levels, mesh, n)
         t0 = time.perf_counter()
-        ref = P.assemble(xs)
+        ref = P.assemble(xs, route=1)
         dt = time.perf_counter() - t0
         n_s = P.nT + P.nH
         line["cpu_baseline"] = {"value": n_s / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {n} of 700 meshes ({n_s} elements), hyper-dual route, "
-                                          f"1 thread, {dt:.1f} s"}
+                                "sample": f"first {n} of 700 meshes ({n_s} elements), closed-form route "
+                                          f"(hand-derived StVK and discrete-shells hinge Hessians), 1 thread, "
+                                          f"{dt:.1f} s"}
         try:
-            v_all, cores, el_all = oracle_all_cores(mesh, 300_000)
+            v_all, cores, el_all = oracle_all_cores(mesh, 700_000)
             line["cpu_baseline_all_cores"] = {
                 "value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": f"{el_all} elements of the batch split over {cores} spawned processes (one per core), "
-                          f"hyper-dual route; elements / slowest worker's assembly time"}
+                          f"closed-form route; elements / slowest worker's assembly time"}
         except Exception as exc:  # the baseline is reported, never required
             line["cpu_baseline_all_cores"] = {"unavailable": str(exc)[:200]}
         Hs = H[: P.nnzb * 9].cpu().numpy().reshape(-1, 3, 3).astype(np.float64)

@@ -96,16 +96,21 @@ typedef enum {
     ADM_OPT_ASSEMBLER = 1,    /* 0 = tiled (shared-memory patches, default),
                                  1 = per-element atomic scatter (the paper's
                                  Sec. 5.5 scheme, kept as a reference path)    */
-    ADM_OPT_TILE_TRIS = 2,    /* triangles per tile of the tiled assembler,
-                                 32..4096; 0 (default): 512, the paper's patch
-                                 size, lowered for small meshes to about nT /
-                                 304 (two tiles per SM), never below 32 */
+    ADM_OPT_TILE_TRIS = 2,    /* units (triangles with their attached hinges or
+                                 springs) per tile of the tiled assembler,
+                                 1..4096; 0 (default): 224, lowered for small
+                                 meshes to about nT / 304 (two tiles per SM),
+                                 never below 32; tiles are split further until
+                                 their shared memory fits */
     ADM_OPT_BLOCK_THREADS = 3,/* threads per block of the element kernels       */
     ADM_OPT_PROFILE = 4,      /* > 0: record CUDA events around every kernel of
                                  each evaluation, on the evaluation's stream,
                                  keeping the last `value` evaluations (a ring);
                                  0: off (default).  Creates events, allocates no
                                  device memory. */
+    ADM_OPT_TILE_THREADS = 6, /* threads per block of the tiled kernel in FP32
+                                 without filtering: 128 or 256 (0, default:
+                                 256); FP64 and filtered passes use 256 */
     ADM_OPT_GRAPH = 5         /* 1: adm_eval / adm_eval_batch capture their
                                  whole pass (zero-fill, element kernel,
                                  reductions) into a CUDA graph on the first call
@@ -295,14 +300,16 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
 
 /* Autotuner of the tiled assembler (the batched evaluation's work split):
  * times the full pass of `energy` at `prec` on x (device) for each candidate
- * tile size {128, 192, 256, 384, 512, 768} triangles, keeps the fastest for
- * this handle and returns it (and its time per pass in ms; either output may
- * be NULL).  Synchronous; allocates temporary output buffers and rebuilds the
- * tiles for every candidate (host work of a few seconds on a 2M-vertex
- * batch).  Not part of the paper (Sec. 7 uses a fixed patch size of 512
- * faces). */
+ * pair (threads per block, units per tile) -- 256 threads with {96, 128, 160,
+ * 192, 224} units, and in FP32 128 threads (four blocks per SM at 128
+ * registers) with {48, 64, 96, 112} units -- keeps the fastest pair for this
+ * handle (as ADM_OPT_TILE_THREADS and ADM_OPT_TILE_TRIS) and returns it and
+ * its time per pass in ms (any output may be NULL).  Synchronous; allocates
+ * temporary output buffers and rebuilds the tiles for every tile size (host
+ * work of seconds on a 2M-vertex batch).  Not part of the paper (Sec. 7 uses
+ * a fixed patch size of 512 faces). */
 adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
-                        int32_t *best_tile_tris, float *best_ms);
+                        int32_t *best_tile_tris, int32_t *best_threads, float *best_ms);
 
 /* Residual r (device, 4 nT), CSR Jacobian values (device, 24 nT, in the
  * order of adm_jac_pattern) and the Gauss-Newton matrix J^T J assembled into

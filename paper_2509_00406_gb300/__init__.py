@@ -29,7 +29,7 @@ UMBRELLA = 9
 # adm_precision
 FP64, FP32 = 0, 1
 # adm_option
-OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE, OPT_GRAPH = 1, 2, 3, 4, 5
+OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE, OPT_GRAPH, OPT_TILE_THREADS = 1, 2, 3, 4, 5, 6
 # adm_stage
 STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled", "graph", "mlp", "pairs"]
 MLP_NPARAM = 4481
@@ -84,7 +84,7 @@ def lib():
         "adm_profile_read": (i32, [vp, C.POINTER(C.c_float), C.POINTER(i32), i32]),
         "adm_grad_norm_noalloc": (i32, [vp, i64, i32, vp, vp]),
         "adm_check_bounded_wait": (i32, [vp]),
-        "adm_autotune": (i32, [vp, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_float)]),
+        "adm_autotune": (i32, [vp, i32, i32, vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_float)]),
         "adm_mlp_eval": (i32, [vp, vp, i64, vp, vp, vp]),
         "adm_mlp_workspace_size": (C.c_size_t, []),
         "adm_mlp_loss_grad": (i32, [vp, vp, i64, vp, vp, vp, C.c_float, vp, vp, vp, C.c_size_t, vp]),
@@ -263,10 +263,12 @@ class Mesh:
                                        _stream(stream)), "adm_eval_jacobian")
 
     def autotune(self, energy: int, prec: int, x):
-        """(best tile size, ms per pass) of the tiled assembler on x."""
-        best, ms = C.c_int32(), C.c_float()
-        _check(lib().adm_autotune(self._h, energy, prec, _ptr(x), C.byref(best), C.byref(ms)), "adm_autotune")
-        return best.value, ms.value
+        """(best units per tile, best threads per block, ms per pass) of the
+        tiled assembler on x."""
+        best, thr, ms = C.c_int32(), C.c_int32(), C.c_float()
+        _check(lib().adm_autotune(self._h, energy, prec, _ptr(x), C.byref(best), C.byref(thr), C.byref(ms)),
+               "adm_autotune")
+        return best.value, thr.value, ms.value
 
     def mlp_attach(self, theta, norm):
         _check(lib().adm_mlp_attach(self._h, _ptr(theta), _ptr(norm)), "adm_mlp_attach")

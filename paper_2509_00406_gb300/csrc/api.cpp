@@ -152,28 +152,29 @@ adm_status ensure_shell(adm_ctx *h)
     return build_pattern(h, PAT_SHELL);
 }
 
-// triangles per tile: the option, else 512 (the paper's default patch size,
-// Sec. 7.1) shrunk for small meshes so that there are about two tiles per SM
-// of the 152, never below 32
+// units (triangles) per tile: the option, else 224 (two blocks per SM in
+// FP32, one in FP64) shrunk for small meshes so that there are about two
+// tiles per SM of the 152, never below 32; the builder splits tiles further
+// until they fit shared memory
 int tile_tris_for(const adm_ctx *h)
 {
     if (h->tile_tris > 0) return h->tile_tris;
     const int64_t per = h->m.nT / (2 * 152);
-    return (int)std::min<int64_t>(512, std::max<int64_t>(32, per));
+    return (int)std::min<int64_t>(224, std::max<int64_t>(32, per));
 }
 
 // device arrays of a tile set (freed before a rebuild)
 void free_tiles(adm_ctx *h, TileSet &ts)
 {
-    void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_meta, ts.d_meta_off, ts.d_tri_loc, ts.d_hinge_loc, ts.d_tri_perm,
-                    ts.d_cloth_hdr, ts.d_edge_loc, ts.d_vert_loc, ts.d_edge_l2[0], ts.d_edge_l2[1],
-                    ts.d_vert_area3[0], ts.d_vert_area3[1], ts.d_zero_blocks, ts.d_zero_verts, ts.d_mesh_tile_off, ts.d_tri_rest[0],
-                    ts.d_tri_rest[1], ts.d_hinge_rest[0], ts.d_hinge_rest[1]};
+    void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_tri_perm, ts.d_tri_verts, ts.d_unit, ts.d_unit_dst, ts.d_slot_dst,
+                    ts.d_meta, ts.d_meta_off, ts.d_grp, ts.d_grp_items, ts.d_zero_verts, ts.d_zero_blocks,
+                    ts.d_mesh_tile_off, ts.d_sync, ts.d_partials[0], ts.d_partials[1], ts.d_tri_rest[0],
+                    ts.d_tri_rest[1], ts.d_slot_rest[0], ts.d_slot_rest[1], ts.d_vterm_rest[0], ts.d_vterm_rest[1]};
     for (void *p : ptrs) dev_free(h, p);
     ts = TileSet();
 }
 
-// tiles of the tiled assembler for one pattern kind, with rest data in tile order
+// tiles of the tiled assembler for one pattern kind, with rest data in unit order
 adm_status ensure_tiles(adm_ctx *h, int kind)
 {
     TileSet &ts = h->tiles[kind];
@@ -189,36 +190,41 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
         ts = TileSet();
         return s;
     }
-    const HostMesh &m = h->m;
-    auto up = [&](auto **dst, const auto &v) { return upload(h, dst, v.data(), v.size() * sizeof(v[0])); };
+    auto up = [&](auto **dst, const auto &v) {
+        return v.empty() ? dev_alloc(h, dst, 16) : upload(h, dst, v.data(), v.size() * sizeof(v[0]));
+    };
     if ((s = up(&ts.d_hdr, ts.hdr)) != ADM_OK) return s;
-    if ((s = up(&ts.d_tri_loc, ts.tri_loc)) != ADM_OK) return s;
-    if ((s = up(&ts.d_hinge_loc, ts.hinge_loc)) != ADM_OK) return s;
     if ((s = up(&ts.d_foot, ts.foot)) != ADM_OK) return s;
+    if ((s = up(&ts.d_tri_perm, ts.tri_perm)) != ADM_OK) return s;
+    if ((s = up(&ts.d_tri_verts, ts.tri_verts)) != ADM_OK) return s;
+    if ((s = up(&ts.d_unit, ts.unit)) != ADM_OK) return s;
+    if ((s = up(&ts.d_unit_dst, ts.unit_dst)) != ADM_OK) return s;
+    if ((s = up(&ts.d_slot_dst, ts.slot_dst)) != ADM_OK) return s;
     if ((s = up(&ts.d_meta, ts.meta)) != ADM_OK) return s;
     if ((s = up(&ts.d_meta_off, ts.meta_off)) != ADM_OK) return s;
-    if ((s = up(&ts.d_zero_blocks, ts.zero_blocks)) != ADM_OK) return s;
+    if ((s = up(&ts.d_grp, ts.grp)) != ADM_OK) return s;
+    if ((s = up(&ts.d_grp_items, ts.grp_items)) != ADM_OK) return s;
     if ((s = up(&ts.d_zero_verts, ts.zero_verts)) != ADM_OK) return s;
+    if ((s = up(&ts.d_zero_blocks, ts.zero_blocks)) != ADM_OK) return s;
     if ((s = up(&ts.d_mesh_tile_off, ts.mesh_tile_off)) != ADM_OK) return s;
-    if ((s = up(&ts.d_tri_perm, ts.tri_perm)) != ADM_OK) return s;
-    {
-        std::vector<std::vector<double>> f(5, std::vector<double>(m.nT));
-        for (int64_t i = 0; i < m.nT; ++i) {
-            const int64_t t = ts.tri_perm[i];
-            for (int k = 0; k < 4; ++k) f[k][i] = m.tri_Dinv[4 * t + k];
-            f[4][i] = m.tri_area[t];
-        }
-        if ((s = upload_rest(h, ts.d_tri_rest, f, m.nT)) != ADM_OK) return s;
+    if ((s = dev_alloc(h, &ts.d_sync, (8 + (size_t)ts.n_groups) * sizeof(int32_t))) != ADM_OK) return s;
+    for (int p = 0; p < 2; ++p) {
+        const size_t eb = p == ADM_FP32 ? 4 : 8;
+        char *buf = nullptr;
+        if ((s = dev_alloc(h, &buf, std::max<size_t>(256, (size_t)ts.partial_floats * eb))) != ADM_OK) return s;
+        ts.d_partials[p] = buf;
     }
-    if (kind == PAT_SHELL) {
-        const int64_t nH = m.nH();
-        std::vector<std::vector<double>> f(2, std::vector<double>(nH));
-        for (int64_t i = 0; i < nH; ++i) {
-            const int64_t e = ts.hinge_perm[i];
-            f[0][i] = m.h_thetabar[e];
-            f[1][i] = m.h_abar[e] / 3.0;
-        }
-        if ((s = upload_rest(h, ts.d_hinge_rest, f, nH)) != ADM_OK) return s;
+    {
+        const int64_t nU = (int64_t)ts.tri_perm.size();
+        std::vector<std::vector<double>> f(5, std::vector<double>(nU));
+        for (int64_t i = 0; i < nU; ++i)
+            for (int k = 0; k < 5; ++k) f[k][i] = ts.tri_rest[5 * i + k];
+        if ((s = upload_rest(h, ts.d_tri_rest, f, nU)) != ADM_OK) return s;
+        const int64_t nS = std::max<int64_t>(ts.n_slots, 1);
+        std::vector<std::vector<double>> g(2, std::vector<double>(nS, 0.0));
+        for (int64_t i = 0; i < ts.n_slots; ++i)
+            for (int k = 0; k < 2; ++k) g[k][i] = ts.slot_rest[2 * i + k];
+        if ((s = upload_rest(h, ts.d_slot_rest, g, nS)) != ADM_OK) return s;
     }
     if ((size_t)ts.n_tiles + 1 > h->epart_cap) {
         dev_free(h, h->d_epart);
@@ -249,21 +255,22 @@ bool energy_ok(int energy, int vdim)
 
 bool needs_hinges(int energy) { return energy == ADM_HINGE_BENDING || energy == ADM_SHELL; }
 
-// upload the tile set's mass-spring lists (once) and the default inertial
-// target (the rest shape) if none was set
+// the tile set's cloth data (once): vertex terms in the unit records, their
+// rest data; and the default inertial target (the rest shape) if none was set
 adm_status ensure_cloth(adm_ctx *h)
 {
     TileSet &ts = h->tiles[PAT_TRI];
     adm_status s = ADM_OK;
     if (!ts.cloth_built) {
         if ((s = tiles_build_cloth(h->m, ts)) != ADM_OK) return s;
-        auto up = [&](auto **dst, const auto &v) { return upload(h, dst, v.data(), v.size() * sizeof(v[0])); };
-        if ((s = up(&ts.d_cloth_hdr, ts.cloth_hdr)) != ADM_OK) return s;
-        if ((s = up(&ts.d_edge_loc, ts.edge_loc)) != ADM_OK) return s;
-        if ((s = up(&ts.d_vert_loc, ts.vert_loc)) != ADM_OK) return s;
-        std::vector<std::vector<double>> fe{ts.edge_l2}, fv{ts.vert_area3};
-        if ((s = upload_rest(h, ts.d_edge_l2, fe, (int64_t)ts.edge_l2.size())) != ADM_OK) return s;
-        if ((s = upload_rest(h, ts.d_vert_area3, fv, (int64_t)ts.vert_area3.size())) != ADM_OK) return s;
+        if (cudaMemcpy(ts.d_unit, ts.unit.data(), ts.unit.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(ts.d_hdr, ts.hdr.data(), ts.hdr.size() * sizeof(int32_t), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+            return ADM_ERR_CUDA;
+        std::vector<std::vector<double>> fv{ts.vterm_rest};
+        if (fv[0].empty()) fv[0].push_back(0.0);
+        if ((s = upload_rest(h, ts.d_vterm_rest, fv, (int64_t)fv[0].size())) != ADM_OK) return s;
     }
     if (!h->d_xhat[ADM_FP64]) return adm_set_inertia_target(h, h->m.V.data());
     return ADM_OK;
@@ -489,8 +496,13 @@ adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
         if (value != 0 && value != 1) return ADM_ERR_ARG;
         h->assembler = (int)value;
         return ADM_OK;
+    case ADM_OPT_TILE_THREADS:
+        if (value != 0 && value != 128 && value != 256) return ADM_ERR_ARG;
+        if ((value == 0 ? 256 : (int)value) != h->tile_threads) drop_graphs(h);
+        h->tile_threads = value == 0 ? 256 : (int)value;
+        return ADM_OK;
     case ADM_OPT_TILE_TRIS:
-        if (value != 0 && (value < 32 || value > 4096)) return ADM_ERR_ARG;
+        if (value != 0 && (value < 1 || value > 4096)) return ADM_ERR_ARG;
         if (value != h->tile_tris)
             for (auto &ts : h->tiles) ts.built = false;  // rebuilt on next use
         h->tile_tris = (int)value;
@@ -843,7 +855,7 @@ adm_status adm_eval_batch_host(adm_handle h, adm_energy energy, adm_precision pr
 adm_status adm_check_bounded_wait(void *stream) { return bounded_wait_check(as_stream(stream)); }
 
 adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, const void *x_dev,
-                        int32_t *best_tile_tris, float *best_ms)
+                        int32_t *best_tile_tris, int32_t *best_threads, float *best_ms)
 {
     if (!h || !x_dev || (prec != ADM_FP32 && prec != ADM_FP64)) return ADM_ERR_ARG;
     if (energy == ADM_ARAP2D_RESIDUAL || energy == ADM_MLP_MEMBRANE || energy == ADM_UMBRELLA ||
@@ -867,14 +879,27 @@ adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, con
                         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         s = ADM_ERR_OOM;
-    static const int cand[] = {128, 192, 256, 384, 512, 768};
-    int best = -1;
+    // (threads per block, units per tile); 128-thread blocks only in FP32,
+    // where four of them share an SM at 128 registers
+    struct Cand {
+        int threads, units;
+    };
+    std::vector<Cand> cand;
+    for (int u : {96, 128, 160, 192, 224}) cand.push_back({256, u});
+    if (prec == ADM_FP32 && !h->proj)
+        for (int u : {48, 64, 96, 112}) cand.push_back({128, u});
+    Cand best{-1, -1};
     float best_t = 1e30f;
-    for (int c : cand) {
+    int built_units = -1;
+    for (const Cand &c : cand) {
         if (s != ADM_OK) break;
-        h->tile_tris = c;
-        h->tiles[kind].built = false;
-        if ((s = ensure_tiles(h, kind)) != ADM_OK) break;
+        h->tile_threads = c.threads;
+        if (c.units != built_units) {
+            h->tile_tris = c.units;
+            h->tiles[kind].built = false;
+            if ((s = ensure_tiles(h, kind)) != ADM_OK) break;
+            built_units = c.units;
+        }
         EvalArgs a;
         a.energy = energy;
         a.prec = prec;
@@ -908,11 +933,14 @@ adm_status adm_autotune(adm_handle h, adm_energy energy, adm_precision prec, con
     h->use_graph = saved_graph;
     h->prof_ring = saved_ring;
     if (s != ADM_OK) return s;
-    h->tile_tris = best;
+    h->tile_tris = best.units;
+    h->tile_threads = best.threads;
     h->tiles[kind].built = false;
     if ((s = ensure_tiles(h, kind)) != ADM_OK) return s;
-    h->tuned[{(int)energy, (int)prec}] = best;
-    if (best_tile_tris) *best_tile_tris = best;
+    h->tuned[{(int)energy, (int)prec}] = best.units;
+    drop_graphs(h);
+    if (best_tile_tris) *best_tile_tris = best.units;
+    if (best_threads) *best_threads = best.threads;
     if (best_ms) *best_ms = best_t;
     return ADM_OK;
 }

@@ -20,9 +20,6 @@ constexpr int kRedThreads = 256;   // reductions
 template <typename T, bool PROJ>
 constexpr int tile_threads() { return (sizeof(T) == 4 && !PROJ) ? 512 : 256; }
 
-// passive, gradient, full Hessian, matrix-free Hessian-vector product
-enum Mode { MODE_VALUE = 0, MODE_GRAD = 1, MODE_HESS = 2, MODE_HVP = 3 };
-
 template <typename T>
 struct TermConsts {
     T mu, lam, thick, kbh2;

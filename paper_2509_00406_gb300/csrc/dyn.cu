@@ -282,17 +282,18 @@ __global__ void k_block_rows(int64_t n, const int32_t *blocks, int64_t nV, const
     off[k] = b - rp[lo];
 }
 
-// tiles: row starts in the metadata blobs and shared-block indices follow the
-// extended pattern (the per-row codes are unchanged: mesh columns come first)
+// tiles: the row starts in the metadata blobs follow the extended pattern
+// (the tiles' codes are unchanged: a row's mesh columns come first)
 __global__ void k_remap_tiles(int32_t n_tiles, const int32_t *hdr, const int32_t *foot, const int64_t *meta_off,
                               unsigned char *meta, const int32_t *rpx)
 {
     const int32_t t = blockIdx.x;
     if (t >= n_tiles) return;
-    const int32_t foot_begin = hdr[8 * t + 4], nf = hdr[8 * t + 5];
+    const int32_t foot_begin = hdr[kHdr * t + kHdrFoot], nf = hdr[kHdr * t + kHdrNF];
     int32_t *rows = reinterpret_cast<int32_t *>(meta + meta_off[t]);
     for (int r = threadIdx.x; r < nf; r += blockDim.x)
-        rows[r] = (int32_t)(((uint32_t)rows[r] & 0x80000000u) | (uint32_t)rpx[foot[foot_begin + r]]);
+        rows[kRowWords * r] = (int32_t)(((uint32_t)rows[kRowWords * r] & 0x80000000u) |
+                                        (uint32_t)rpx[foot[foot_begin + r]]);
 }
 
 __global__ void k_remap_zero(int64_t n, const int32_t *row, const int32_t *off, const int32_t *rpx, int32_t *blocks)

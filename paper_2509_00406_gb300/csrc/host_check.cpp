@@ -32,12 +32,14 @@ HostMesh make_mesh(const double *V, int64_t nV, const int32_t *F, int64_t nT, co
 extern "C" {
 
 // Builds hinges (if with_hinges), the block pattern and the tiles, and
-// reports, per block of the pattern, which tile writes it:
-//   block_writer[b] = tile id if exactly one tile writes it with a plain
-//   store, -2 if it is shared (zeroed and atomically added), -1 if no tile
-//   writes it; block_adds[b] = number of tiles that add into it.
-// stats: {n_tiles, n_zero_blocks, n_zero_verts, FP64 shared-memory bytes (VD = 3), nnzb, nH,
-//         build_ms}.  Returns 0 or an adm_status.
+// reports, per block of the pattern, which tile produces it:
+//   block_writer[b] = tile id if exactly one tile produces it (written with a
+//   plain store), -2 if several do (each writes a partial, the group's last
+//   tile writes the sum), -1 if no tile does; block_adds[b] = number of tiles
+//   producing a shared block (0 otherwise).
+// stats: {n_tiles, n_groups, n_zero_verts, FP64 Hessian-mode shared-memory
+// bytes (VD = 3), nnzb, nH, build_ms, partial floats}.  Returns 0 or an
+// adm_status, or a negative code < -99 naming the check that failed.
 int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t nT, const int64_t *v_off,
                         const int64_t *f_off, int32_t n_mesh, int32_t with_hinges, int32_t tile_tris,
                         int32_t *block_writer, int32_t *block_adds, int64_t nnzb_cap, double *stats)
@@ -60,75 +62,123 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
         block_writer[b] = -1;
         block_adds[b] = 0;
     }
-    for (int32_t t = 0; t < ts.n_tiles; ++t) {
-        const int32_t *hd = &ts.hdr[8 * (size_t)t];
-        const int32_t foot_begin = hd[4], nf = hd[5];
-        for (int32_t r = 0; r < nf; ++r) {
-            const int32_t rs = ts.row_start[foot_begin + r] & 0x7fffffff;
-            const int32_t c0 = ts.code_off[foot_begin + t + r], c1 = ts.code_off[foot_begin + t + r + 1];
-            for (int32_t e = 0; e < c1 - c0; ++e) {
-                const uint16_t code = ts.codes[c0 + e];
-                if ((code >> 14) == 0) continue;
-                const int64_t b = rs + e;
-                if (code & 0x2000) {
-                    if (block_writer[b] >= 0) return -100;  // plain store and atomic add on one block
-                    block_writer[b] = -2;
-                    block_adds[b]++;
-                } else {
-                    if (block_writer[b] != -1) return -101;  // two plain writers
-                    block_writer[b] = t;
-                }
-            }
-        }
-    }
-    stats[0] = ts.n_tiles;
-    stats[1] = (double)ts.zero_blocks.size();
-    stats[2] = (double)ts.zero_verts.size();
-    stats[3] = (double)ts.smem_bytes[1][0];
-    stats[4] = (double)P.nnzb;
-    stats[5] = (double)m.nH();
-    stats[6] = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    // every zeroed block is shared, or the diagonal block of a vertex no
-    // element touches (written by nothing but the zero fill; reported as -2)
-    for (int32_t b : ts.zero_blocks) {
-        if (block_writer[b] == -1) {
-            const int32_t r = (int32_t)(std::upper_bound(P.row_ptr.begin(), P.row_ptr.end(), b) - P.row_ptr.begin()) - 1;
-            if (P.col[b] != r) return -102;
-            block_writer[b] = -2;
-            block_adds[b] = 2;
-            continue;
-        }
-        if (block_writer[b] != -2) return -102;
-    }
-    // each tile's metadata blob holds its rows' starts, code offsets and codes
+    std::vector<int32_t> producers(P.nnzb, 0), shared_flag(P.nnzb, -1);
     if ((int64_t)ts.meta_off.size() != ts.n_tiles + 1 || ts.meta_off.back() != (int64_t)ts.meta.size()) return -105;
+    std::vector<char> seen_dst;
     for (int32_t t = 0; t < ts.n_tiles; ++t) {
-        const int32_t *hd = &ts.hdr[8 * (size_t)t];
-        const int32_t foot_begin = hd[4], nf = hd[5];
+        const int32_t *hd = &ts.hdr[(size_t)kHdr * t];
+        const int32_t fb = hd[kHdrFoot], nf = hd[kHdrNF], nvc = hd[kHdrNVC], npc = hd[kHdrNPC];
         const int64_t m0 = ts.meta_off[t];
         if (m0 % 16 != 0 || (ts.meta_off[t + 1] - m0) % 16 != 0) return -105;
         const unsigned char *blob = ts.meta.data() + m0;
-        const int32_t cbase = ts.code_off[foot_begin + t];
-        for (int32_t r = 0; r <= nf; ++r) {
-            uint16_t c;
-            std::memcpy(&c, blob + 4 * nf + 2 * r, 2);
-            if (c != ts.code_off[foot_begin + t + r] - cbase) return -106;
-            if (r == nf) break;
-            int32_t rs;
-            std::memcpy(&rs, blob + 4 * r, 4);
-            if (rs != ts.row_start[foot_begin + r]) return -106;
+        // every chunk of the tile is written by exactly one unit role
+        std::vector<int> vw(nvc, 0), pw(npc, 0);
+        for (int32_t i = 0; i < hd[kHdrNUnit]; ++i) {
+            const int64_t u = (int64_t)hd[kHdrUnit] + i;
+            const uint16_t *r = &ts.unit[8 * u];
+            const uint16_t *d = &ts.unit_dst[6 * u];
+            for (int q = 0; q < 3; ++q) {
+                if (d[q] >= nvc || d[3 + q] >= npc) return -110;
+                vw[d[q]]++;
+                pw[d[3 + q]]++;
+                if (r[q] >= nf) return -111;
+            }
+            for (int sl = 0; sl < (r[6] & 3); ++sl) {
+                if (!with_hinges || r[3 + sl] == 0xffff) continue;
+                const uint16_t *sd = &ts.slot_dst[4 * ((int64_t)hd[kHdrSlot] + r[7] + sl)];
+                if (sd[0] >= nvc) return -110;
+                vw[sd[0]]++;
+                for (int q = 0; q < 3; ++q) {
+                    if (sd[1 + q] >= npc) return -110;
+                    pw[sd[1 + q]]++;
+                }
+            }
         }
-        const int32_t nc = ts.code_off[foot_begin + t + nf] - cbase;
-        if (6 * nf + 2 + 2 * nc > ts.meta_off[t + 1] - m0) return -106;
-        if (std::memcmp(blob + 6 * nf + 2, &ts.codes[cbase], 2 * (size_t)nc) != 0) return -106;
+        for (int c : vw)
+            if (c != 1) return -112;
+        for (int c : pw)
+            if (c != 1) return -112;
+        // rows and codes: segments tile the chunk arrays; blocks produced
+        int64_t vcov = 0;
+        std::vector<int> pcov(npc, 0);
+        for (int32_t r = 0; r < nf; ++r) {
+            int32_t w[kRowWords];
+            std::memcpy(w, blob + 4 * kRowWords * r, sizeof w);
+            const int32_t v = ts.foot[fb + r];
+            const int32_t rs = w[0] & 0x7fffffff;
+            if (rs != P.row_ptr[v]) return -106;
+            const int c0 = w[1] & 0xffff, nc = (w[1] >> 16) & 0xff, nv = (int)((uint32_t)w[1] >> 24);
+            const int vs0 = w[2] & 0xffff;
+            if (vs0 != vcov) return -113;  // vertex segments in footprint order, back to back
+            vcov += nv;
+            const int32_t bd = rs + w[3];
+            if (P.col[bd] != v) return -114;
+            producers[bd]++;
+            const int sh = w[0] < 0 ? 1 : 0;
+            if (shared_flag[bd] >= 0 && shared_flag[bd] != sh) return -115;
+            shared_flag[bd] = sh;
+            for (int c = c0; c < c0 + nc; ++c) {
+                uint32_t code;
+                std::memcpy(&code, blob + hd[kHdrCodeOff] + 4 * c, 4);
+                const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 31u);
+                const int tr = (int)((code >> 20) & 1u), csh = (int)((code >> 21) & 1u);
+                const int32_t b = rs + (int32_t)(code >> 22);
+                if (b >= P.row_ptr[v + 1] || P.col[b] == v) return -116;
+                const int32_t lc = (int32_t)(std::lower_bound(ts.foot.begin() + fb, ts.foot.begin() + fb + nf, P.col[b]) -
+                                             (ts.foot.begin() + fb));
+                if (lc >= nf || ts.foot[fb + lc] != P.col[b] || tr != (r > lc ? 1 : 0)) return -117;
+                if (cnt == 0 || start + cnt > npc) return -118;
+                for (int q = start; q < start + cnt; ++q) pcov[q]++;
+                producers[b]++;
+                if (shared_flag[b] >= 0 && shared_flag[b] != csh) return -115;
+                shared_flag[b] = csh;
+            }
+        }
+        if (vcov != nvc) return -113;
+        for (int c : pcov)  // every pair chunk is summed by its two blocks, (a, b) and (b, a)
+            if (c != 2) return -119;
     }
-    // every triangle and hinge belongs to exactly one tile
-    std::vector<char> seen_t(nT, 0), seen_h(m.nH(), 0);
+    for (int64_t b = 0; b < P.nnzb; ++b) {
+        if (producers[b] == 0) continue;
+        if ((producers[b] >= 2) != (shared_flag[b] == 1)) return -100;
+        block_writer[b] = producers[b] >= 2 ? -2 : 0;
+        block_adds[b] = producers[b] >= 2 ? producers[b] : 0;
+    }
+    // blocks of vertices no unit touches: the per-pass zero fill
+    for (int32_t b : ts.zero_blocks) {
+        if (block_writer[b] != -1) return -102;
+        block_writer[b] = -2;
+        block_adds[b] = 2;
+    }
+    // every group's tiles are sorted and distinct; partial regions disjoint
+    int64_t prev_end = 0;
+    for (int64_t g = 0; g < ts.n_groups; ++g) {
+        const int32_t *h = &ts.grp[(size_t)kGrpWords * g];
+        if (h[0] < prev_end || h[0] % 32 != 0 || h[1] % 32 != 0 || h[2] < 2) return -120;
+        if (12 * (int64_t)h[3] + 9 * (int64_t)h[4] > h[1]) return -120;
+        prev_end = h[0] + (int64_t)h[1] * h[2];
+    }
+    if (prev_end != ts.partial_floats) return -120;
+    stats[0] = ts.n_tiles;
+    stats[1] = (double)ts.n_groups;
+    stats[2] = (double)ts.zero_verts.size();
+    stats[3] = (double)tile_smem_bytes(ts, MODE_HESS, 3, 8);
+    stats[4] = (double)P.nnzb;
+    stats[5] = (double)m.nH();
+    stats[6] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    stats[7] = (double)ts.partial_floats;
+    // every triangle is exactly one unit
+    std::vector<char> seen_t(nT, 0);
     for (int32_t e : ts.tri_perm)
         if (e < 0 || e >= nT || seen_t[e]++) return -103;
-    if (with_hinges)
-        for (int32_t e : ts.hinge_perm)
-            if (e < 0 || e >= m.nH() || seen_h[e]++) return -104;
+    // every hinge is in exactly one slot
+    if (with_hinges) {
+        std::vector<char> seen_h(m.nH(), 0);
+        for (int32_t e : ts.slot_edge)
+            if (e >= 0 && seen_h[e]++) return -104;
+        for (char c : seen_h)
+            if (!c) return -104;
+    }
     return 0;
 }
 

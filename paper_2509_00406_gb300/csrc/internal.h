@@ -14,6 +14,9 @@
 
 namespace adm {
 
+// passive, gradient, full Hessian, matrix-free Hessian-vector product
+enum Mode { MODE_VALUE = 0, MODE_GRAD = 1, MODE_HESS = 2, MODE_HVP = 3 };
+
 // stencil sets that own a block pattern
 enum PatternKind { PAT_TRI = 0, PAT_SHELL = 1, PAT_RING = 2, PAT_COUNT = 3 };
 constexpr int kMaxValence = 12;  // one-ring terms: vertices of higher valence are rejected
@@ -86,53 +89,95 @@ struct ChunkTable {
     int32_t *d_mesh_chunk_off = nullptr;            // n_mesh + 1
 };
 
-// shared-memory tiles of the tiled assembler (tiles.cpp)
+// Tiles of the staged-gather assembler (tiles.cpp).
+//
+// A unit is one triangle plus the mesh edges attached to it (every edge is
+// attached to exactly one of its faces): on a shell each attached interior
+// edge carries its hinge, on the cloth each attached edge its spring.  The
+// attached edges sit in slots s = 0, 1, 2, the edge (t_k, t_k+1) of
+// k = (rot + s) mod 3 for a per-unit rotation rot that makes the slots
+// consecutive; the hinge of slot s is evaluated in the order (t_k, t_k+1,
+// t_k+2, extra), the same hinge (Sec. 7.7) relabelled.  The triangle keeps
+// its own vertex order.
+//
+// A tile is a run of units in Morton order (per mesh).  Every unit writes its
+// contributions as "chunks": per unit vertex t_i a vertex chunk (gradient,
+// diagonal block upper entries or H v) and per vertex pair a pair chunk (the
+// off-diagonal block, oriented from the lower to the higher footprint index);
+// an attached hinge adds a vertex chunk and three pair chunks for its extra
+// vertex, and adds its other contributions into the unit's own chunks.  The
+// chunks of a tile are laid out sorted by target (vertex, then unit order;
+// pair, then unit order), so every output entry is the fixed-order sum of one
+// contiguous segment: the gather that writes the BSR rows is deterministic
+// and needs no atomics.  Outputs that several tiles produce ("shared" rows and
+// blocks) are written by each of them into partial slots; a group of outputs
+// shared by the same set of tiles is summed, in tile order, by the last of
+// those tiles to finish (an integer counter per group), which also writes the
+// final values.
 struct TileSet {
     bool built = false;
     int64_t build_id = 0;                // distinct for every build (tiles_build)
-    int tile_tris = 0;
+    int tile_units = 0;                  // units per tile at most
     int32_t n_tiles = 0;
-    // dynamic shared memory of the tiled kernel, [VD == 3][ADM_FP64 = 0 / ADM_FP32 = 1]:
-    // accumulators (VD = 3: 13 per footprint vertex + 9 per pair; VD = 2: 7
-    // and 5; x, gradient, padded diagonal, pair blocks) padded to 16 bytes,
-    // then the tile's metadata blob
-    int64_t smem_bytes[2][2] = {{0, 0}, {0, 0}};
-    std::vector<int32_t> hdr;            // 8 per tile: tri begin/count, hinge begin/count,
-                                         // footprint begin/count, pairs, code begin
-    std::vector<uint16_t> tri_loc;       // 6 per triangle (tile order): 3 local ids, 3 pair slots
-    std::vector<uint16_t> hinge_loc;     // 10 per hinge (tile order): 4 local ids, 6 pair slots
-    std::vector<int32_t> tri_perm, hinge_perm;  // tile order -> canonical element index
-    std::vector<int32_t> foot;           // footprint vertex (global id)
-    std::vector<int32_t> row_start;      // BSR block of its row start; bit 31: gradient row shared
-    std::vector<int32_t> code_off;       // per footprint row + one sentinel per tile
-    std::vector<uint16_t> codes;         // per block of every footprint row
-    std::vector<int32_t> zero_blocks;    // shared blocks, zeroed before a pass
-    std::vector<int32_t> zero_verts;     // shared gradient rows
+    int64_t n_slots = 0, n_vterms = 0;   // attached edges, cloth vertex terms
+    // per tile, kHdr int32 (see kHdr* below)
+    std::vector<int32_t> hdr;
+    // per unit (tile order), 8 uint16: footprint ids of t0 t1 t2; the extra
+    // vertex of the hinge in slots 0..2 (0xffff: none; on a cloth tile set the
+    // first field is the unit's first vertex term within the tile); flags
+    // (number of slots | cloth vertex-term mask << 2 | rot << 5); first slot
+    // (within the tile)
+    std::vector<uint16_t> unit;
+    std::vector<uint16_t> unit_dst;      // per unit 6: chunks of V0 V1 V2 (vertex), P01 P02 P12 (pair)
+    std::vector<uint16_t> slot_dst;      // per slot 4: chunks of X (vertex), PX(h0) PX(h1) PX(h2) (pair)
+    std::vector<int32_t> tri_perm;       // unit -> canonical triangle
+    std::vector<int32_t> tri_verts;      // unit -> its vertices (global ids), 3 per unit
+    std::vector<double> tri_rest;        // 5 per unit (Dm^-1 row-major, area)
+    std::vector<int32_t> slot_edge;      // slot -> (hinge index) or -1; per slot
+    std::vector<double> slot_rest;       // 2 per slot: hinge (thetabar, abar/3) or spring (l^2, 0)
+    std::vector<double> vterm_rest;      // per cloth vertex term: a third of the rest area around it
+    std::vector<int32_t> foot;           // footprint vertices (global ids), sorted, per tile
     std::vector<int32_t> mesh_tile_off;  // n_mesh + 1
-    // mass-spring cloth (tiles_build_cloth, triangle tile sets only): every
-    // edge and vertex owned by the lowest-indexed tile whose footprint has it
-    bool cloth_built = false;
-    std::vector<int32_t> cloth_hdr;      // 4 per tile: edge begin/count, vertex begin/count
-    std::vector<uint16_t> edge_loc;      // 3 per edge (tile order): 2 local ids, pair slot
-    std::vector<uint16_t> vert_loc;      // 1 per vertex (tile order): local id
-    std::vector<double> edge_l2;         // squared rest length per edge (tile order)
-    std::vector<double> vert_area3;      // a third of the rest area around each vertex (tile order)
-    int32_t *d_cloth_hdr = nullptr;
-    uint16_t *d_edge_loc = nullptr, *d_vert_loc = nullptr;
-    void *d_edge_l2[2] = {nullptr, nullptr};
-    void *d_vert_area3[2] = {nullptr, nullptr};
-    std::vector<unsigned char> meta;     // per tile: row starts, row code offsets, codes (16-byte padded)
-    std::vector<int64_t> meta_off;       // n_tiles + 1 byte offsets into meta
-    // device copies
-    int32_t *d_hdr = nullptr, *d_foot = nullptr;
-    uint16_t *d_tri_loc = nullptr, *d_hinge_loc = nullptr;
+    // per tile metadata blob (copied into shared memory): rows, codes, shared
+    // destinations, groups; kRowWords int32 per footprint row
+    std::vector<unsigned char> meta;
+    std::vector<int64_t> meta_off;       // n_tiles + 1
+    // groups of shared outputs: kGrpWords int32 each, then their items
+    std::vector<int32_t> grp;
+    std::vector<int32_t> grp_items;      // rows: (vertex, diagonal position); blocks: (row vertex, position)
+    int64_t n_groups = 0, partial_floats = 0;
+    std::vector<int32_t> zero_verts;     // vertices no unit touches (zero row and diagonal block)
+    std::vector<int32_t> zero_blocks;    // their diagonal blocks
+    int64_t max_nvc = 0, max_npc = 0, max_nf = 0, max_meta = 0;  // largest counts over the tiles
+    int64_t smem_cache[4][2][2] = {};    // tile_smem_bytes by (mode, VD == 3, FP64), 0: not yet computed
+    int32_t *d_hdr = nullptr, *d_foot = nullptr, *d_tri_perm = nullptr, *d_tri_verts = nullptr;
+    uint16_t *d_unit = nullptr, *d_unit_dst = nullptr, *d_slot_dst = nullptr;
     unsigned char *d_meta = nullptr;
     int64_t *d_meta_off = nullptr;
-    int32_t *d_zero_blocks = nullptr, *d_zero_verts = nullptr, *d_mesh_tile_off = nullptr;
-    int32_t *d_tri_perm = nullptr;               // tile order -> canonical triangle (learned membrane)
-    void *d_tri_rest[2] = {nullptr, nullptr};    // rest data permuted to tile order
-    void *d_hinge_rest[2] = {nullptr, nullptr};
+    int32_t *d_grp = nullptr, *d_grp_items = nullptr;
+    int32_t *d_zero_verts = nullptr, *d_zero_blocks = nullptr, *d_mesh_tile_off = nullptr;
+    int32_t *d_sync = nullptr;           // [0]: next tile of the persistent loop, [1..]: group counters
+    void *d_partials[2] = {nullptr, nullptr};  // per precision
+    void *d_tri_rest[2] = {nullptr, nullptr};  // per precision, SoA 5 x units
+    void *d_slot_rest[2] = {nullptr, nullptr}; // per precision, SoA 2 x slots
+    void *d_vterm_rest[2] = {nullptr, nullptr};
+    bool cloth_built = false;
 };
+// tile header words
+enum TileHdr {
+    kHdrUnit = 0, kHdrNUnit, kHdrSlot, kHdrNSlot, kHdrFoot, kHdrNF, kHdrNVC, kHdrNPC, kHdrNCode, kHdrNShared,
+    kHdrNGroup, kHdrCodeOff, kHdrDstOff, kHdrGrpOff, kHdrVTerm, kHdrNVTerm, kHdr = 16
+};
+// footprint row words: [0] BSR start of the row | shared << 31 (its gradient
+// and diagonal block are shared), [1] first code (within the tile) | number
+// of codes << 16 | number of vertex chunks << 24, [2] first vertex chunk |
+// shared-output ordinal of the row's first shared output << 16, [3] position
+// of the diagonal block in the BSR row.
+// code (one per pair block the tile produces): pair-chunk segment start
+// (15 bits) | its chunk count << 15 (5 bits) | transposed << 20 | shared << 21 |
+// position in the BSR row << 22 (10 bits)
+constexpr int kRowWords = 4;
+constexpr int kGrpWords = 8;   // group: partial base, stride, tiles, rows, blocks, items offset, -, -
 
 // vertex-pair interaction terms and the block pattern they extend (dyn.cu;
 // Sec. 4.3, Sec. 6.3, Alg. 1)
@@ -217,6 +262,7 @@ struct adm_ctx {
     int proj = 0;            // per-term Hessian filtering on (adm_set_projection)
     double proj_eps = 0.0;   // value negative local eigenvalues are raised to
     int tile_tris = 0;  // 0: automatic (tile_tris_for)
+    int tile_threads = 256;  // threads per block of the FP32 tiled kernel (128 or 256)
     int block_threads = 128;
     // host-buffer path
     void *d_stage_x = nullptr, *d_stage_grad = nullptr, *d_stage_bsr = nullptr;
@@ -262,12 +308,42 @@ void mesh_build_slots(const HostMesh &m, const std::vector<int32_t> &row_ptr,
                       std::vector<int32_t> &hinge_slots);
 
 // tiles.cpp
-adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_tris, TileSet &ts);
-// per-tile edge and vertex lists of the mass-spring energy, on a triangle tile set
+adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_units, TileSet &ts);
+// cloth data (spring rest lengths, vertex terms) on a triangle tile set
 adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts);
-// bytes of a tile's metadata blob, and of its dynamic shared memory
-int64_t tile_meta_bytes(int64_t nf, int64_t ncodes);
-int64_t tile_smem_bytes(int elem_bytes, int64_t units, int64_t nf, int64_t ncodes);
+// floats of one chunk: vertex and pair chunks per mode and vertex dimension
+#if defined(__CUDACC__)
+#define ADM_TILE_HD __host__ __device__ __forceinline__
+#else
+#define ADM_TILE_HD inline
+#endif
+ADM_TILE_HD constexpr int chunk_floats(int mode, int vd, bool pair)
+{
+    return mode == MODE_GRAD ? (pair ? 0 : vd)
+           : mode == MODE_HESS ? (pair ? vd * vd : vd + vd * (vd + 1) / 2)
+           : mode == MODE_HVP  ? (pair ? 0 : 2 * vd)
+                               : 0;
+}
+// one tile's dynamic shared memory (byte offsets): x of the footprint, v
+// (matrix-free mode), vertex chunks, pair chunks, the metadata blob
+struct TileLayout {
+    int32_t off_vs, off_sv, off_sp, off_blob, total;
+};
+ADM_TILE_HD TileLayout tile_layout(int nf, int nvc, int npc, int meta_bytes, int mode, int vd, int eb)
+{
+    auto a16 = [](int b) { return (b + 15) & ~15; };
+    TileLayout L;
+    const int xs = nf * vd * eb;
+    L.off_vs = a16(xs);
+    L.off_sv = a16(L.off_vs + (mode == MODE_HVP ? xs : 0));
+    L.off_sp = a16(L.off_sv + nvc * chunk_floats(mode, vd, false) * eb);
+    L.off_blob = a16(L.off_sp + npc * chunk_floats(mode, vd, true) * eb);
+    L.total = L.off_blob + (mode >= MODE_GRAD ? meta_bytes : 0);
+    return L;
+}
+// dynamic shared memory of the tiled kernel for a tile set, mode and
+// precision: the largest tile's layout
+int64_t tile_smem_bytes(const TileSet &ts, int mode, int vd, int elem_bytes);
 
 // kernels.cu
 struct EvalArgs {
@@ -325,9 +401,10 @@ adm_status mlp_adam(float *th, float *m, float *v, const float *grad, int64_t st
                     float eps, cudaStream_t s);
 adm_status mlp_nh_targets(int64_t n, const float *F, double mu, double lam, float *I, float *psi, float *dpsi,
                           cudaStream_t s);
-adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *perm,
-                              const int32_t *Fv, const float *rest_tiled, const float *x, float *table,
-                              cudaStream_t s);
+// per-triangle table of the learned membrane in unit order: verts = the
+// units' rotated vertices (3 per unit), rest_tiled = their rest data (SoA)
+adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *verts,
+                              const float *rest_tiled, const float *x, float *table, cudaStream_t s);
 
 adm_status launch_jacobian(adm_ctx *h, int prec, const void *x, void *r, void *jv, void *jtj,
                            cudaStream_t stream);

@@ -616,10 +616,11 @@ __global__ void k_nh_targets(int64_t n, const float *F, double mu, double lam, f
     dpsi[3 * s + 2] = (float)((-mu + lam * lnJ) / (2.0 * i3));
 }
 
-// per-triangle network table in tile order: psi, dpsi/dI, upper Hessian in I
+// per-triangle network table in unit order (the tiles' order and vertex
+// rotation): psi, dpsi/dI, upper Hessian in I
 __global__ void __launch_bounds__(WARPS * 32, 4) k_mlp_tri(const float *th, const float *norm, int64_t nT,
-                                                         const int32_t *perm, const int32_t *Fv,
-                                                         const float *rest, const float *x, float *table)
+                                                         const int32_t *verts, const float *rest, const float *x,
+                                                         float *table)
 {
     __shared__ MlpSmem S;
     load_params(S, th, norm);
@@ -630,12 +631,11 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_mlp_tri(const float *th, cons
         float uu[3] = {0.0f, 0.0f, 0.0f};
         const int64_t p = base + (lane & 7);
         if (lane < 8 && p < nT) {
-            const int64_t tri = perm[p];
             float xv[9];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * (int64_t)Fv[3 * tri + c] + d];
+                for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * (int64_t)verts[3 * p + c] + d];
             const float D0 = rest[p], D1 = rest[nT + p], D2 = rest[2 * nT + p], D3 = rest[3 * nT + p];
             float c11 = 0.0f, c22 = 0.0f, c12 = 0.0f;
 #pragma unroll
@@ -706,11 +706,11 @@ adm_status mlp_nh_targets(int64_t n, const float *F, double mu, double lam, floa
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 
-adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *perm, const int32_t *Fv,
+adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *verts,
                               const float *rest_tiled, const float *x, float *table, cudaStream_t s)
 {
     const int64_t blocks = std::min<int64_t>((nT + WARPS * 8 - 1) / (WARPS * 8), 152 * 8);
-    if (blocks > 0) k_mlp_tri<<<(unsigned)blocks, WARPS * 32, 0, s>>>(th, norm, nT, perm, Fv, rest_tiled, x, table);
+    if (blocks > 0) k_mlp_tri<<<(unsigned)blocks, WARPS * 32, 0, s>>>(th, norm, nT, verts, rest_tiled, x, table);
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
 }
 

@@ -1,116 +1,108 @@
-// tiled_impl.cuh -- the tiled assembler: one block per tile of triangles and
-// hinges, shared-memory staging and accumulation, row-contiguous BSR stores.
+// tiled_impl.cuh -- the staged-gather assembler: a persistent grid whose
+// blocks take tiles of units (a triangle and its attached hinges or springs)
+// from a queue, evaluate them with per-element forward mode, stage every
+// contribution in shared memory sorted by the output it adds to, and write
+// each BSR entry, gradient and H v entry as the fixed-order sum of one
+// contiguous segment.  No float atomics anywhere: outputs that several tiles
+// produce go through partial slots that the last tile of their group sums in
+// tile order, so two passes on the same input give bit-identical results.
 #pragma once
 
 #include "device_common.cuh"
 
 namespace adm {
 
-// ----------------------------------------------------------- tiled pass --
-// One block per tile: stage the footprint positions in shared memory, run
-// every triangle and hinge term of the tile, accumulate gradient rows,
-// diagonal blocks (upper 6) and pair blocks (9, oriented lower -> higher
-// local id) with shared-memory atomics, then write every footprint row of the
-// BSR with row-contiguous stores (plain for blocks only this tile touches,
-// global atomic adds into pre-zeroed shared blocks).
-// shared-memory strides of the accumulators, in elements: a vertex's diagonal
-// block keeps its VD (VD + 1) / 2 upper entries, a pair block its VD^2, each
-// padded to an odd stride (7 for 3x3 diagonals, 5 for 2x2 pairs) so that the
-// same entry of different vertices or pairs maps the slot index mod 32
-// one-to-one onto the 32 banks
-template <int VD>
-struct AccStride {
-    static constexpr int D = VD == 3 ? 7 : 3;
-    static constexpr int P = VD == 3 ? 9 : 5;
-};
-
 template <typename T>
 struct TiledArgs {
-    const int32_t *hdr;
-    const uint16_t *tri_loc, *hinge_loc;
+    const int32_t *hdr;               // kHdr per tile
+    const uint16_t *unit;             // 8 per unit
+    const uint16_t *unit_dst;         // 6 per unit
+    const uint16_t *slot_dst;         // 4 per slot
     const int32_t *foot;
-    const unsigned char *meta;        // per tile: row starts, row code offsets, codes (16-byte aligned)
+    const unsigned char *meta;        // per tile blob (16-byte aligned)
     const int64_t *meta_off;          // n_tiles + 1
-    const T *tri_rest, *hinge_rest;   // SoA in tile order
-    int64_t nT, nH;                   // SoA strides
+    const T *tri_rest;                // SoA 5 x nU, unit order (rotated triangles)
+    const T *slot_rest;               // SoA 2 x nS
+    const T *vterm_rest;              // cloth vertex terms
+    int64_t nU, nS;
     const T *x;
     T *grad, *bsr;
     const T *v;                       // matrix-free mode: direction
     T *hv;                            // matrix-free mode: H v
-    double *epart;
+    T *partials;                      // shared outputs, per group and tile
+    int32_t *next;                    // work queue position of this launch
+    int32_t *counters;                // per group: tiles finished
+    const int32_t *grp, *grp_items;
+    const int32_t *row_ptr;           // the pattern written (mesh or contact-extended)
+    int32_t tile_begin, tile_end;     // this launch's tiles
+    double *epart;                    // per tile
     int *status;
     TermConsts<T> c;
-    const float *mlp_table;           // learned membrane: 10 per triangle, tile order
-    // mass-spring: per tile {edge begin, count, vertex begin, count}; per edge
-    // 2 local ids + pair slot and squared rest length; per vertex its local id
-    // and a third of the rest area around it; the inertial target (like x)
-    const int32_t *cloth_hdr;
-    const uint16_t *edge_loc, *vert_loc;
-    const T *edge_l2, *vert_area3, *xhat;
+    const float *mlp_table;           // learned membrane: 10 per unit
+    const T *xhat;                    // cloth inertial target
 };
 
-// the element's gradient and Hessian blocks added into the footprint
-// accumulators (LT: a Local in vertex DOFs or an EdgeLocal, whose entries are
-// formed as they are added)
-template <typename T, int VD, int NV, int NP, class LT>
-__device__ __forceinline__ void tile_accumulate(const LT &L, const uint16_t (&lid)[NV], const uint16_t (&slot)[NP],
-                                                const int (&pr)[NP][2], T *gacc, T *dacc, T *pacc, int mode)
+// floats of a vertex and of a pair chunk
+template <int MODE, int VD>
+struct Chunk {
+    static constexpr int V = MODE == MODE_HESS ? VD + VD * (VD + 1) / 2 : (MODE == MODE_HVP ? 2 * VD : (MODE == MODE_GRAD ? VD : 0));
+    static constexpr int P = MODE == MODE_HESS ? VD * VD : 0;
+};
+
+template <typename U>
+__device__ __forceinline__ U sel3(int k, U a, U b, U c) { return k == 0 ? a : (k == 1 ? b : c); }
+
+// ------------------------------------------------------- chunk writers --
+// vertex a of an element's local result into a vertex chunk: gradient, then
+// (Hessian mode) the upper entries of its diagonal block; ADD adds into what
+// the chunk holds (the unit's own chunk), otherwise stores
+template <int MODE, int VD, int A, bool ADD, typename T, class LT>
+__device__ __forceinline__ void put_vertex(const LT &L, T *ch)
 {
-    constexpr int NDS = AccStride<VD>::D, NPS = AccStride<VD>::P;
 #pragma unroll
-    for (int a = 0; a < NV; ++a)
-#pragma unroll
-        for (int d = 0; d < VD; ++d) atomicAdd(gacc + lid[a] * VD + d, local_g(L, a * VD + d));
-    if (mode != MODE_HESS) return;
-#pragma unroll
-    for (int a = 0; a < NV; ++a)
+    for (int d = 0; d < VD; ++d) {
+        const T g = local_g(L, A * VD + d);
+        if (ADD) ch[d] += g;
+        else ch[d] = g;
+    }
+    if constexpr (MODE == MODE_HESS) {
 #pragma unroll
         for (int s = 0; s < VD; ++s)
 #pragma unroll
-            for (int r = 0; r <= s; ++r)
-                atomicAdd(dacc + lid[a] * NDS + hix(r, s), local_H(L, a * VD + r, a * VD + s));
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        const int a = pr[p][0], b = pr[p][1];
-        const bool fwd = lid[a] < lid[b];
-        T *dst = pacc + slot[p] * NPS;
-#pragma unroll
-        for (int r = 0; r < VD; ++r)
-#pragma unroll
-            for (int s = 0; s < VD; ++s)
-                atomicAdd(dst + r * VD + s, fwd ? local_H(L, a * VD + r, b * VD + s) : local_H(L, b * VD + r, a * VD + s));
+            for (int r = 0; r <= s; ++r) {
+                const T h = local_H(L, A * VD + r, A * VD + s);
+                if (ADD) ch[VD + hix(r, s)] += h;
+                else ch[VD + hix(r, s)] = h;
+            }
     }
 }
 
-// matrix-free mode: the element's local Hessian applied to its gathered
-// part of v, added with its gradient into the footprint accumulators
-template <typename T, int VD, int NV, int K>
-__device__ __forceinline__ void tile_hvp(const Local<T, K> &L, const uint16_t (&lid)[NV], const T *vs, T *gacc,
-                                         T *hacc)
+// the block of element vertices (A, B) into a pair chunk, oriented from the
+// lower to the higher footprint index (tr: B's is the lower)
+template <int VD, int A, int B, bool ADD, typename T, class LT>
+__device__ __forceinline__ void put_pair(const LT &L, T *ch, bool tr)
 {
-    T vl[K];
+    T v[VD][VD];
 #pragma unroll
-    for (int a = 0; a < NV; ++a)
+    for (int r = 0; r < VD; ++r)
 #pragma unroll
-        for (int d = 0; d < VD; ++d) vl[a * VD + d] = vs[lid[a] * VD + d];
+        for (int s = 0; s < VD; ++s) v[r][s] = local_H(L, A * VD + r, B * VD + s);
 #pragma unroll
-    for (int i = 0; i < K; ++i) {
-        T y = -T(0);
+    for (int r = 0; r < VD; ++r)
 #pragma unroll
-        for (int j = 0; j < K; ++j) y += local_H(L, i, j) * vl[j];
-        atomicAdd(hacc + lid[i / VD] * VD + i % VD, y);
-        atomicAdd(gacc + lid[i / VD] * VD + i % VD, L.g[i]);
-    }
+        for (int s = 0; s < VD; ++s) {
+            const T val = tr ? v[s][r] : v[r][s];
+            if (ADD) ch[r * VD + s] += val;
+            else ch[r * VD + s] = val;
+        }
 }
 
-// the same in edge-vector coordinates: v_e = C^T v (per edge the signed sum
-// of its vertices' v), y_e = H_e v_e, y = C y_e
-template <typename T, int VD, int NV, class E>
-__device__ __forceinline__ void tile_hvp(const EdgeLocal<E, VD, T> &L, const uint16_t (&lid)[NV], const T *vs,
-                                         T *gacc, T *hacc)
+// matrix-free mode: y = H_e v_e of an element in edge coordinates
+// (v_e = C^T v, y = C y_e), gradient and y per vertex into vertex chunks
+template <int VD, class E, typename T>
+__device__ __forceinline__ void hvp_edge(const EdgeLocal<E, VD, T> &L, const T (&vl)[E::NV * VD], T (&y)[E::NV * VD])
 {
-    static_assert(E::NV == NV, "vertices of the edge map");
-    constexpr int NE = E::NE, KE = NE * VD;
+    constexpr int NE = E::NE, NV = E::NV, KE = NE * VD;
     T ve[KE], ye[KE];
 #pragma unroll
     for (int p = 0; p < NE; ++p)
@@ -120,17 +112,16 @@ __device__ __forceinline__ void tile_hvp(const EdgeLocal<E, VD, T> &L, const uin
 #pragma unroll
             for (int a = 0; a < NV; ++a) {
                 if (E::C(a, p) == 0) continue;
-                const T va = vs[lid[a] * VD + d];
-                acc = E::C(a, p) > 0 ? acc + va : acc - va;
+                acc = E::C(a, p) > 0 ? acc + vl[a * VD + d] : acc - vl[a * VD + d];
             }
             ve[p * VD + d] = acc;
         }
 #pragma unroll
     for (int i = 0; i < KE; ++i) {
-        T y = -T(0);
+        T acc = -T(0);
 #pragma unroll
-        for (int j = 0; j < KE; ++j) y += L.e.H[i <= j ? hix(i, j) : hix(j, i)] * ve[j];
-        ye[i] = y;
+        for (int j = 0; j < KE; ++j) acc += L.e.H[i <= j ? hix(i, j) : hix(j, i)] * ve[j];
+        ye[i] = acc;
     }
 #pragma unroll
     for (int a = 0; a < NV; ++a)
@@ -142,258 +133,511 @@ __device__ __forceinline__ void tile_hvp(const EdgeLocal<E, VD, T> &L, const uin
                 if (E::C(a, p) == 0) continue;
                 acc = E::C(a, p) > 0 ? acc + ye[p * VD + d] : acc - ye[p * VD + d];
             }
-            atomicAdd(hacc + lid[a] * VD + d, acc);
-            atomicAdd(gacc + lid[a] * VD + d, local_g(L, a * VD + d));
+            y[a * VD + d] = acc;
         }
 }
 
-// FP32 tiles are register-capped at two resident blocks per SM (64 registers
-// for 512 threads); FP64, and the Hessian-filtering variant (PROJ: an
-// in-register eigensolve per element), keep one block of 256 threads and the
-// full register file
-template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS, bool PROJ = false>
-__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 && !PROJ) ? 2 : 1) k_tiled(TiledArgs<T> A)
+template <int VD, int A, bool ADD, typename T, class LT>
+__device__ __forceinline__ void put_vertex_hvp(const LT &L, const T *y, T *ch)
+{
+#pragma unroll
+    for (int d = 0; d < VD; ++d) {
+        const T g = local_g(L, A * VD + d), hy = y[A * VD + d];
+        if (ADD) {
+            ch[d] += g;
+            ch[VD + d] += hy;
+        } else {
+            ch[d] = g;
+            ch[VD + d] = hy;
+        }
+    }
+}
+
+// the element's contributions for vertices (A) / pairs (A, B) into chunks
+// given by pointer arrays; a whole element at once
+template <int MODE, int VD, int NV, bool ADD, typename T, class LT>
+__device__ __forceinline__ void put_vertices(const LT &L, T *const (&vch)[NV], const T *y)
+{
+    sfor<0, NV>([&](auto Ai) {
+        constexpr int A = decltype(Ai)::value;
+        if constexpr (MODE == MODE_HVP) put_vertex_hvp<VD, A, ADD>(L, y, vch[A]);
+        else put_vertex<MODE, VD, A, ADD>(L, vch[A]);
+    });
+}
+
+// ------------------------------------------------------------ waits --
+__device__ __forceinline__ void bar_init(uint64_t *bar)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one thread: arm the barrier with the byte count and start the bulk copy
+// (dst, src, bytes multiples of 16); generic-proxy reads of dst by the
+// previous tile are ordered before the async-proxy writes
+__device__ __forceinline__ void bulk_copy_start(uint64_t *bar, void *dst, const void *src, uint32_t bytes)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+
+// wait for the barrier phase of the given parity; gives up after about a
+// second (2^20 waits of at most ~1 us) and returns false
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(b), "r"(parity), "r"(1000u)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void discard_l2_line(const void *p)
+{
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
+// ------------------------------------------------------------- kernel --
+// resident blocks per SM the register budget is sized for: FP32 tiles run
+// 512 threads per SM at 128 registers (two blocks of 256 or four of 128);
+// FP64 and filtered tiles one block of 256 with the full register file
+template <typename T, bool PROJ, int THREADS>
+constexpr int tile_min_blocks() { return (sizeof(T) == 4 && !PROJ) ? 512 / THREADS : 1; }
+constexpr int kMaxGroups = 64;   // groups of a tile whose counters are taken per round
+
+template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS, bool PROJ>
+__global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())) k_tiled(TiledArgs<T> A)
 {
     constexpr int VD = TriTraits<ENERGY>::VD;
-    constexpr int K = 3 * VD;
-    constexpr int NB = VD * VD;
-    constexpr int NDS = AccStride<VD>::D, NPS = AccStride<VD>::P;
+    constexpr int CV = Chunk<MODE, VD>::V, CP = Chunk<MODE, VD>::P;
+    constexpr bool CLOTH = ENERGY == ADM_MASS_SPRING;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t meta_bar;
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    const int t = blockIdx.x;
-    const int32_t *hd = A.hdr + 8 * t;
-    const int32_t tri_begin = hd[0], n_tri = hd[1], hinge_begin = hd[2], n_hinge = hd[3];
-    const int32_t foot_begin = hd[4], nf = hd[5], np = hd[6];
-    T *xs = sm;
-    T *gacc = xs + VD * nf;
-    T *dacc = gacc + VD * nf;
-    T *pacc = dacc + NDS * nf;
-    T *vs = gacc + VD * nf;    // matrix-free mode: v of the footprint ...
-    T *hacc = vs + VD * nf;    // ... and the H v accumulators (in place of dacc, pacc)
-    // the tile's row metadata follows the accumulators; one thread starts
-    // its bulk copy now, and it lands while the elements are evaluated
-    const size_t acc_bytes = sizeof(T) * (size_t)((2 * VD + NDS) * nf + NPS * np);
-    unsigned char *meta_s = smem_raw + ((acc_bytes + 15) & ~size_t(15));
-    const int32_t *ms_row = reinterpret_cast<const int32_t *>(meta_s);
-    const uint16_t *ms_coff = reinterpret_cast<const uint16_t *>(meta_s + 4 * nf);
-    const uint16_t *ms_codes = ms_coff + nf + 1;
-    if (MODE >= MODE_GRAD && threadIdx.x == 0) {
+    __shared__ int s_tile, s_nlast;
+    __shared__ int s_last[kMaxGroups];
+    const int tid = threadIdx.x;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    if (MODE >= MODE_GRAD && tid == 0) bar_init(&meta_bar);
+    __syncthreads();
+    uint32_t phase = 0;
+    const int32_t cap = A.tile_end - A.tile_begin + 1;  // every iteration takes one queue position
+    int32_t iter = 0;
+    for (; iter < cap; ++iter) {
+        if (tid == 0) s_tile = A.tile_begin + atomicAdd(A.next, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= A.tile_end) break;
+        const int32_t *hd = A.hdr + kHdr * (int64_t)t;
+        const int32_t u0 = hd[kHdrUnit], nu = hd[kHdrNUnit], slot0 = hd[kHdrSlot];
+        const int32_t fb = hd[kHdrFoot], nf = hd[kHdrNF];
         const int64_t m0 = A.meta_off[t];
-        bulk_load_start(&meta_bar, meta_s, A.meta + m0, (uint32_t)(A.meta_off[t + 1] - m0));
-    }
-    for (int i = threadIdx.x; i < nf; i += THREADS) {
-        const int64_t v = A.foot[foot_begin + i];
+        const int32_t meta_bytes = (int32_t)(A.meta_off[t + 1] - m0);
+        const TileLayout lay = tile_layout(nf, hd[kHdrNVC], hd[kHdrNPC], meta_bytes, MODE, VD, (int)sizeof(T));
+        T *vsm = reinterpret_cast<T *>(smem_raw + lay.off_vs);
+        T *sv = reinterpret_cast<T *>(smem_raw + lay.off_sv);
+        T *sp = reinterpret_cast<T *>(smem_raw + lay.off_sp);
+        unsigned char *blob = smem_raw + lay.off_blob;
+        if (MODE >= MODE_GRAD && tid == 0) {
+            bulk_copy_start(&meta_bar, blob, A.meta + m0, (uint32_t)meta_bytes);
+        }
+        for (int i = tid; i < nf; i += THREADS) {
+            const int64_t v = A.foot[fb + i];
 #pragma unroll
-        for (int d = 0; d < VD; ++d) xs[VD * i + d] = A.x[v * VD + d];
-        if (MODE == MODE_HVP) {
+            for (int d = 0; d < VD; ++d) xs[VD * i + d] = A.x[v * VD + d];
+            if (MODE == MODE_HVP)
 #pragma unroll
-            for (int d = 0; d < VD; ++d) {
-                vs[VD * i + d] = A.v[v * VD + d];
-                gacc[VD * i + d] = T(0);
-                hacc[VD * i + d] = T(0);
+                for (int d = 0; d < VD; ++d) vsm[VD * i + d] = A.v[v * VD + d];
+        }
+        __syncthreads();
+
+        // ---- units: evaluate, stage contributions in their chunks
+        double fe = 0.0;
+        for (int ul = tid; ul < nu; ul += THREADS) {
+            const int64_t u = (int64_t)u0 + ul;
+            const uint4 rec = *reinterpret_cast<const uint4 *>(A.unit + 8 * u);
+            const int l[3] = {(int)(rec.x & 0xffffu), (int)(rec.x >> 16), (int)(rec.y & 0xffffu)};
+            const int ex[3] = {(int)(rec.y >> 16), (int)(rec.z & 0xffffu), (int)(rec.z >> 16)};
+            const int flags = (int)(rec.w & 0xffffu), ufirst = (int)(rec.w >> 16);
+            const int nslot = flags & 3, rot = (flags >> 5) & 3;
+            const uint16_t *ud = A.unit_dst + 6 * u;
+            T *vch[3] = {nullptr, nullptr, nullptr}, *pch[3] = {nullptr, nullptr, nullptr};
+            if constexpr (MODE >= MODE_GRAD) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) vch[q] = sv + CV * (int)ud[q];
+                if constexpr (CP > 0)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) pch[q] = sp + CP * (int)ud[3 + q];
+            }
+            const bool tr01 = l[0] > l[1], tr02 = l[0] > l[2], tr12 = l[1] > l[2];
+            T yv[3 * VD];  // matrix-free: the element's H v per vertex
+            // -- the triangle term (stores every unit chunk first), or zeros
+            bool wrote = false;
+            if constexpr (TRIS) {
+                T x[3 * VD];
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int d = 0; d < VD; ++d) x[q * VD + d] = xs[l[q] * VD + d];
+                T D[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nU + u];
+                const T area = A.tri_rest[4 * A.nU + u];
+                EdgeLocal<TriEdges, VD, T> L;
+                if (tri_term<T, ENERGY, PROJ>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * u : nullptr)) {
+                    fe += (double)local_f(L);
+                    if constexpr (MODE >= MODE_GRAD) {
+                        if constexpr (MODE == MODE_HVP) {
+                            T vl[3 * VD];
+#pragma unroll
+                            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                                for (int d = 0; d < VD; ++d) vl[q * VD + d] = vsm[l[q] * VD + d];
+                            hvp_edge<VD>(L, vl, yv);
+                        }
+                        put_vertices<MODE, VD, 3, false>(L, vch, yv);
+                        if constexpr (CP > 0) {
+                            put_pair<VD, 0, 1, false>(L, pch[0], tr01);
+                            put_pair<VD, 0, 2, false>(L, pch[1], tr02);
+                            put_pair<VD, 1, 2, false>(L, pch[2], tr12);
+                        }
+                    }
+                    wrote = true;
+                } else {
+                    atomicOr(A.status, ST_DOMAIN);
+                }
+            }
+            if (MODE >= MODE_GRAD && !wrote) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int k = 0; k < CV; ++k) vch[q][k] = T(0);
+                if constexpr (CP > 0)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int k = 0; k < CP; ++k) pch[q][k] = T(0);
+            }
+            // -- hinges of the attached edges: slot s (edge k) is evaluated as
+            // the hinge (t_k, t_k+1, t_k+2, extra)
+            if constexpr (HINGES) {
+                for (int s = 0; s < nslot; ++s) {
+                    const int xe = sel3(s, ex[0], ex[1], ex[2]);
+                    if (xe == 0xffff) continue;
+                    // the slot's edge (t_k, t_k+1), k = rot + s mod 3
+                    const int k0 = rot + s >= 3 ? rot + s - 3 : rot + s;
+                    const int s1 = k0 == 2 ? 0 : k0 + 1, s2 = k0 == 0 ? 2 : k0 - 1;
+                    const int hl[4] = {sel3(k0, l[0], l[1], l[2]), sel3(s1, l[0], l[1], l[2]),
+                                       sel3(s2, l[0], l[1], l[2]), xe};
+                    T x[12];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) x[q * 3 + d] = xs[hl[q] * 3 + d];
+                    const int64_t sg = (int64_t)slot0 + ufirst + s;
+                    const T thetabar = A.slot_rest[sg];
+                    const T w = A.c.kbh2 * A.slot_rest[A.nS + sg];
+                    EdgeLocal<HingeEdges, 3, T> L;
+                    if (!(hinge_local<T, PROJ>(x, thetabar, w, L, A.c.eps) && isfinite(local_f(L)))) {
+                        atomicOr(A.status, ST_DOMAIN);
+                        if constexpr (MODE >= MODE_GRAD) {  // its own chunks still need values
+                            const uint16_t *sd = A.slot_dst + 4 * sg;
+#pragma unroll
+                            for (int k = 0; k < CV; ++k) sv[CV * (int)sd[0] + k] = T(0);
+                            if constexpr (CP > 0)
+#pragma unroll
+                                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                                    for (int k = 0; k < CP; ++k) sp[CP * (int)sd[1 + q] + k] = T(0);
+                        }
+                        continue;
+                    }
+                    fe += (double)local_f(L);
+                    if constexpr (MODE >= MODE_GRAD) {
+                        const uint16_t *sd = A.slot_dst + 4 * sg;
+                        T *hv4[4] = {sel3(k0, vch[0], vch[1], vch[2]), sel3(s1, vch[0], vch[1], vch[2]),
+                                     sel3(s2, vch[0], vch[1], vch[2]), sv + CV * (int)sd[0]};
+                        T hy[12];
+                        if constexpr (MODE == MODE_HVP) {
+                            T vl[12];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                                for (int d = 0; d < 3; ++d) vl[q * 3 + d] = vsm[hl[q] * 3 + d];
+                            hvp_edge<3>(L, vl, hy);
+                        }
+                        // unit vertices add, the extra vertex stores
+                        T *const vadd[3] = {hv4[0], hv4[1], hv4[2]};
+                        put_vertices<MODE, 3, 3, true>(L, vadd, hy);
+                        if constexpr (MODE == MODE_HVP) put_vertex_hvp<3, 3, false>(L, hy, hv4[3]);
+                        else put_vertex<MODE, 3, 3, false>(L, hv4[3]);
+                        if constexpr (CP > 0) {
+                            // unit pairs (tri vertices p, q: role p + q - 1)
+                            const int p01 = k0 + s1 - 1, p02 = k0 + s2 - 1, p12 = s1 + s2 - 1;
+                            put_pair<3, 0, 1, true>(L, sel3(p01, pch[0], pch[1], pch[2]), hl[0] > hl[1]);
+                            put_pair<3, 0, 2, true>(L, sel3(p02, pch[0], pch[1], pch[2]), hl[0] > hl[2]);
+                            put_pair<3, 1, 2, true>(L, sel3(p12, pch[0], pch[1], pch[2]), hl[1] > hl[2]);
+                            // pairs with the extra vertex: chunk holds (lower, higher)
+                            put_pair<3, 0, 3, false>(L, sp + CP * (int)sd[1], hl[0] > xe);
+                            put_pair<3, 1, 3, false>(L, sp + CP * (int)sd[2], hl[1] > xe);
+                            put_pair<3, 2, 3, false>(L, sp + CP * (int)sd[3], hl[2] > xe);
+                        }
+                    }
+                }
+            }
+            // -- cloth: springs on the attached edges, vertex terms
+            if constexpr (CLOTH) {
+                for (int s = 0; s < nslot; ++s) {
+                    const int k0 = rot + s >= 3 ? rot + s - 3 : rot + s;
+                    const int s1 = k0 == 2 ? 0 : k0 + 1;
+                    const int sl[2] = {sel3(k0, l[0], l[1], l[2]), sel3(s1, l[0], l[1], l[2])};
+                    T x[6];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) x[q * 3 + d] = xs[sl[q] * 3 + d];
+                    const int64_t sg = (int64_t)slot0 + ufirst + s;
+                    EdgeLocal<SpringEdges, 3, T> L;
+                    spring_local<T, PROJ>(x, A.slot_rest[sg], A.c.kh2, L, A.c.eps);
+                    if (!isfinite(local_f(L))) {
+                        atomicOr(A.status, ST_DOMAIN);
+                        continue;
+                    }
+                    fe += (double)local_f(L);
+                    if constexpr (MODE >= MODE_GRAD) {
+                        T hy[6];
+                        if constexpr (MODE == MODE_HVP) {
+                            T vl[6];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q)
+#pragma unroll
+                                for (int d = 0; d < 3; ++d) vl[q * 3 + d] = vsm[sl[q] * 3 + d];
+                            hvp_edge<3>(L, vl, hy);
+                        }
+                        T *const va[2] = {sel3(k0, vch[0], vch[1], vch[2]), sel3(s1, vch[0], vch[1], vch[2])};
+                        put_vertices<MODE, 3, 2, true>(L, va, hy);
+                        if constexpr (CP > 0) put_pair<3, 0, 1, true>(L, sel3(k0 + s1 - 1, pch[0], pch[1], pch[2]), sl[0] > sl[1]);
+                    }
+                }
+                const int vmask = flags >> 2;
+                int vt = hd[kHdrVTerm] + ex[0];  // the unit's first vertex term (cloth units carry no hinge extras)
+                for (int q = 0; q < 3; ++q) {
+                    if (!((vmask >> q) & 1)) continue;
+                    const int lq = l[q];
+                    const int64_t vg = A.foot[fb + lq];
+                    T x[3], xh[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        x[d] = xs[lq * 3 + d];
+                        xh[d] = A.xhat[vg * 3 + d];
+                    }
+                    Local<T, 3> L;
+                    vertex_local(x, xh, A.c.rho * A.vterm_rest[vt], A.c.h2, A.c.g, L);
+                    ++vt;
+                    fe += (double)L.f;
+                    if constexpr (MODE >= MODE_GRAD) {
+                        T *ch = sel3(q, vch[0], vch[1], vch[2]);
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) ch[d] += L.g[d];
+                        if constexpr (MODE == MODE_HVP) {
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) ch[3 + d] += L.H[hix(d, d)] * vsm[lq * 3 + d];
+                        }
+                        if constexpr (MODE == MODE_HESS) {
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) ch[3 + hix(d, d)] += L.H[hix(d, d)];
+                        }
+                    }
+                }
             }
         }
-    }
-    if (MODE != MODE_HVP)
-        for (int i = threadIdx.x; i < (VD + NDS) * nf + NPS * np; i += THREADS) gacc[i] = T(0);
-    __syncthreads();
-    double fe = 0.0;
-    if constexpr (TRIS) {
-        static constexpr int TP[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-        for (int i = threadIdx.x; i < n_tri; i += THREADS) {
-            const int64_t e = (int64_t)tri_begin + i;
-            uint16_t lid[3], slot[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                lid[a] = A.tri_loc[6 * e + a];
-                slot[a] = A.tri_loc[6 * e + 3 + a];
+        __syncthreads();
+
+        // ---- gather: every output entry is the sum of its segment
+        bool meta_ok = true;
+        if (MODE >= MODE_GRAD) {
+            if (!bar_wait(&meta_bar, phase & 1u)) {
+                atomicOr(A.status, ST_TIMEOUT);
+                meta_ok = false;
+                bar_wait(&meta_bar, phase & 1u);  // give the copy into this block's shared memory time to land
             }
-            T x[K];
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int d = 0; d < VD; ++d) x[a * VD + d] = xs[lid[a] * VD + d];
-            T D[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nT + e];
-            const T area = A.tri_rest[4 * A.nT + e];
-            EdgeLocal<TriEdges, VD, T> L;
-            if (!tri_term<T, ENERGY, PROJ>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * e : nullptr)) {
-                atomicOr(A.status, ST_DOMAIN);
-                continue;
-            }
-            fe += (double)local_f(L);
-            if (MODE == MODE_HVP) tile_hvp<T, VD, 3>(L, lid, vs, gacc, hacc);
-            else if (MODE >= MODE_GRAD) tile_accumulate<T, VD, 3, 3>(L, lid, slot, TP, gacc, dacc, pacc, MODE);
+            ++phase;
         }
-    }
-    if constexpr (HINGES) {
-        static constexpr int HP[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
-        for (int i = threadIdx.x; i < n_hinge; i += THREADS) {
-            const int64_t e = (int64_t)hinge_begin + i;
-            uint16_t lid[4], slot[6];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) lid[a] = A.hinge_loc[10 * e + a];
-#pragma unroll
-            for (int p = 0; p < 6; ++p) slot[p] = A.hinge_loc[10 * e + 4 + p];
-            T x[12];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) x[a * 3 + d] = xs[lid[a] * 3 + d];
-            const T thetabar = A.hinge_rest[e];
-            const T w = A.c.kbh2 * A.hinge_rest[A.nH + e];
-            EdgeLocal<HingeEdges, 3, T> L;
-            if (!(hinge_local<T, PROJ>(x, thetabar, w, L, A.c.eps) && isfinite(local_f(L)))) {
-                atomicOr(A.status, ST_DOMAIN);
-                continue;
-            }
-            fe += (double)local_f(L);
-            if (MODE == MODE_HVP) tile_hvp<T, 3, 4>(L, lid, vs, gacc, hacc);
-            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 4, 6>(L, lid, slot, HP, gacc, dacc, pacc, MODE);
-        }
-    }
-    if constexpr (ENERGY == ADM_MASS_SPRING) {
-        static constexpr int EP[1][2] = {{0, 1}};
-        const int32_t *ch = A.cloth_hdr + 4 * t;
-        const int32_t edge_begin = ch[0], n_edge = ch[1], vert_begin = ch[2], n_vert = ch[3];
-        for (int i = threadIdx.x; i < n_edge; i += THREADS) {
-            const int64_t e = (int64_t)edge_begin + i;
-            const uint16_t lid[2] = {A.edge_loc[3 * e], A.edge_loc[3 * e + 1]};
-            const uint16_t slot[1] = {A.edge_loc[3 * e + 2]};
-            T x[6];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) x[a * 3 + d] = xs[lid[a] * 3 + d];
-            EdgeLocal<SpringEdges, 3, T> L;
-            spring_local<T, PROJ>(x, A.edge_l2[e], A.c.kh2, L, A.c.eps);
-            if (!isfinite(local_f(L))) {
-                atomicOr(A.status, ST_DOMAIN);
-                continue;
-            }
-            fe += (double)local_f(L);
-            if (MODE == MODE_HVP) tile_hvp<T, 3, 2>(L, lid, vs, gacc, hacc);
-            else if (MODE >= MODE_GRAD) tile_accumulate<T, 3, 2, 1>(L, lid, slot, EP, gacc, dacc, pacc, MODE);
-        }
-        for (int i = threadIdx.x; i < n_vert; i += THREADS) {
-            const int64_t e = (int64_t)vert_begin + i;
-            const uint16_t lid[1] = {A.vert_loc[e]};
-            const int64_t v = A.foot[foot_begin + lid[0]];
-            T x[3], xh[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                x[d] = xs[lid[0] * 3 + d];
-                xh[d] = A.xhat[v * 3 + d];
-            }
-            Local<T, 3> L;
-            vertex_local(x, xh, A.c.rho * A.vert_area3[e], A.c.h2, A.c.g, L);
-            fe += (double)L.f;
-            if (MODE == MODE_HVP) {
-                tile_hvp<T, 3, 1, 3>(L, lid, vs, gacc, hacc);
-            } else if (MODE >= MODE_GRAD) {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) atomicAdd(gacc + lid[0] * 3 + d, L.g[d]);
-                if (MODE == MODE_HESS)
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) atomicAdd(dacc + lid[0] * NDS + hix(d, d), L.H[hix(d, d)]);
+        const int32_t *rows = reinterpret_cast<const int32_t *>(blob);
+        const uint32_t *codes = reinterpret_cast<const uint32_t *>(blob + hd[kHdrCodeOff]);
+        const int32_t *pdst = reinterpret_cast<const int32_t *>(blob + hd[kHdrDstOff]);
+        if (MODE >= MODE_GRAD && meta_ok) {
+            // gradient (and H v) rows: lanes over (row, entry)
+            constexpr int RW = MODE == MODE_HVP ? 2 * VD : VD;
+            for (int i = tid; i < nf * RW; i += THREADS) {
+                const int r = i / RW, e = i - r * RW;
+                const int4 rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
+                const int nv = (int)((uint32_t)rw.y >> 24), vs0 = rw.z & 0xffff;
+                T acc = -T(0);
+                for (int q = 0; q < nv; ++q) acc += sv[CV * (vs0 + q) + e];
+                const int64_t vg = A.foot[fb + r];
+                if (rw.x < 0) {
+                    A.partials[pdst[(uint32_t)rw.z >> 16] + (MODE == MODE_HVP ? e : e)] = acc;
+                } else if (e < VD) {
+                    if (A.grad) A.grad[vg * VD + e] = acc;
+                } else {
+                    A.hv[vg * VD + e - VD] = acc;
+                }
             }
         }
-    }
-    __syncthreads();
-    bool meta_ok = true;
-    if (MODE >= MODE_GRAD && !bulk_load_wait(&meta_bar)) {
-        atomicOr(A.status, ST_TIMEOUT);
-        meta_ok = false;
-        bulk_load_wait(&meta_bar);  // give the copy into this block's shared memory time to land
-    }
-    if (MODE >= MODE_GRAD && A.grad && meta_ok) {
-        for (int i = threadIdx.x; i < nf; i += THREADS) {
-            const int32_t rs = ms_row[i];
-            const int64_t v = A.foot[foot_begin + i];
-#pragma unroll
-            for (int d = 0; d < VD; ++d) {
-                const T val = gacc[VD * i + d];
-                if (rs < 0) atomicAdd(A.grad + v * VD + d, val);
-                else A.grad[v * VD + d] = val;
+        if (MODE == MODE_HESS && meta_ok) {
+            // blocks: one warp per footprint row, BPI blocks per warp pass,
+            // lane = sub * NB + k takes entry k of block sub; block 0 of a
+            // row is its diagonal, the others its codes
+            constexpr int NB = VD * VD, BPI = 32 / NB;
+            constexpr uint64_t DTAB = VD == 3 ? 0x543421310ull : 0x2110ull;  // (r,s) -> packed upper
+            constexpr uint64_t TTAB = VD == 3 ? 0x852741630ull : 0x3120ull;  // (r,s) -> (s,r)
+            const int warp = tid >> 5, lane = tid & 31;
+            const int sub = lane / NB, k = lane - sub * NB;
+            const int off_d = VD + (int)((DTAB >> (4 * k)) & 0xf), off_t = (int)((TTAB >> (4 * k)) & 0xf);
+            for (int r = warp; r < nf; r += THREADS / 32) {
+                const int4 rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
+                const int64_t rs = rw.x & 0x7fffffff;
+                const bool rshared = rw.x < 0;
+                const int c0 = rw.y & 0xffff, nc = (rw.y >> 16) & 0xff, nv = (int)((uint32_t)rw.y >> 24);
+                const int vs0 = rw.z & 0xffff, ord0 = (int)((uint32_t)rw.z >> 16), dpos = rw.w;
+                int ord = ord0 + (rshared ? 1 : 0);  // ordinal of the row's next shared block
+                for (int b0 = 0; b0 <= nc; b0 += BPI) {
+                    const int jb = b0 + sub;
+                    const bool act = sub < BPI && jb <= nc;
+                    uint32_t code = 0;
+                    if (act && jb > 0) code = codes[c0 + jb - 1];
+                    const bool sh = jb == 0 ? rshared : ((code >> 21) & 1u) != 0;
+                    const uint32_t m = __ballot_sync(0xffffffffu, act && k == 0 && jb > 0 && sh);
+                    if (act) {
+                        T acc = -T(0);
+                        int64_t dst;
+                        T *out;
+                        if (jb == 0) {
+                            const T *src = sv + CV * vs0 + off_d;
+                            for (int q = 0; q < nv; ++q) acc += src[CV * q];
+                            out = rshared ? A.partials : A.bsr;
+                            dst = rshared ? (int64_t)pdst[ord0] + VD + k : (rs + dpos) * NB + k;
+                        } else {
+                            const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 31u);
+                            const T *src = sp + CP * start + (((code >> 20) & 1u) ? off_t : k);
+                            for (int q = 0; q < cnt; ++q) acc += src[CP * q];
+                            const int my = ord + __popc(m & ((1u << (sub * NB)) - 1u));
+                            out = sh ? A.partials : A.bsr;
+                            dst = sh ? (int64_t)pdst[my] + k : (rs + (int64_t)(code >> 22)) * NB + k;
+                        }
+                        out[dst] = acc;
+                    }
+                    ord += __popc(m);
+                }
             }
         }
-    }
-    if (MODE == MODE_HVP && meta_ok) {  // H v rows: shared exactly where gradient rows are
-        for (int i = threadIdx.x; i < nf; i += THREADS) {
-            const int32_t rs = ms_row[i];
-            const int64_t v = A.foot[foot_begin + i];
-#pragma unroll
-            for (int d = 0; d < VD; ++d) {
-                const T val = hacc[VD * i + d];
-                if (rs < 0) atomicAdd(A.hv + v * VD + d, val);
-                else A.hv[v * VD + d] = val;
+        const double sum = block_sum<THREADS>(fe);
+        if (tid == 0) A.epart[t] = sum;
+
+        // ---- shared outputs: the last tile of each group sums the partials
+        // (the tile's groups in rounds of kMaxGroups)
+        const int ng = hd[kHdrNGroup];
+        if (MODE >= MODE_GRAD && meta_ok && ng > 0) {
+            const int32_t *groups = reinterpret_cast<const int32_t *>(blob + hd[kHdrGrpOff]);
+            __threadfence();
+            __syncthreads();
+            for (int g0 = 0; g0 < ng; g0 += kMaxGroups) {
+                if (tid == 0) s_nlast = 0;
+                __syncthreads();
+                for (int i = g0 + tid; i < min(ng, g0 + kMaxGroups); i += THREADS) {
+                    const int g = groups[i];
+                    const int kt = A.grp[kGrpWords * (int64_t)g + 2];
+                    if (atomicAdd(A.counters + g, 1) == kt - 1) s_last[atomicAdd(&s_nlast, 1)] = g;
+                }
+                __threadfence();
+                __syncthreads();
+                const int nl = s_nlast;
+                for (int j = 0; j < nl; ++j) {
+                    const int32_t *gh = A.grp + kGrpWords * (int64_t)s_last[j];
+                    const int64_t base = gh[0], stride = gh[1];
+                    const int kt = gh[2], nr = gh[3], nb = gh[4];
+                    const int32_t *items = A.grp_items + gh[5];
+                    constexpr int RE = MODE == MODE_HESS ? VD + VD * VD : (MODE == MODE_HVP ? 2 * VD : VD);
+                    for (int i = tid; i < nr * RE; i += THREADS) {
+                        const int it = i / RE, e = i - it * RE;
+                        T acc = -T(0);
+                        for (int q = 0; q < kt; ++q) acc += __ldcg(A.partials + base + q * stride + 12 * it + e);
+                        const int64_t v = items[2 * it];
+                        if (e < VD) {
+                            if (A.grad) A.grad[v * VD + e] = acc;
+                        } else if (MODE == MODE_HVP) {
+                            A.hv[v * VD + e - VD] = acc;
+                        } else {
+                            A.bsr[((int64_t)A.row_ptr[v] + items[2 * it + 1]) * (VD * VD) + e - VD] = acc;
+                        }
+                    }
+                    if (MODE == MODE_HESS)
+                        for (int i = tid; i < nb * VD * VD; i += THREADS) {
+                            const int it = i / (VD * VD), e = i - it * (VD * VD);
+                            T acc = -T(0);
+                            for (int q = 0; q < kt; ++q)
+                                acc += __ldcg(A.partials + base + q * stride + 12 * nr + 9 * it + e);
+                            const int64_t v = items[2 * nr + 2 * it];
+                            A.bsr[((int64_t)A.row_ptr[v] + items[2 * nr + 2 * it + 1]) * (VD * VD) + e] = acc;
+                        }
+                    __syncthreads();
+                    // the partial lines are dead: drop them from L2 without a write-back
+                    const int64_t lines = (int64_t)kt * stride * (int64_t)sizeof(T) / 128;
+                    const char *p0 = reinterpret_cast<const char *>(A.partials + base);
+                    for (int64_t i = tid; i < lines; i += THREADS) discard_l2_line(p0 + 128 * i);
+                }
+                __syncthreads();
             }
         }
+        __syncthreads();
     }
-    if (MODE == MODE_HESS && meta_ok) {
-        // one warp per footprint row: the row's blocks are contiguous in the
-        // BSR and its codes say, per block, where the tile's sum is (none,
-        // the vertex's diagonal, a pair block or its transpose) and whether
-        // other tiles add into the same block.  A warp iteration writes BPI
-        // consecutive blocks; lane = sub * NB + k takes entry k of block sub,
-        // so the lane's offsets into the three source layouts are fixed.
-        constexpr int BPI = 32 / NB;
-        constexpr uint64_t DTAB = VD == 3 ? 0x543421310ull : 0x2110ull;  // (r,s) -> packed upper
-        constexpr uint64_t TTAB = VD == 3 ? 0x852741630ull : 0x3120ull;  // (r,s) -> (s,r)
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int sub = lane / NB, k = lane - sub * NB;
-        const bool active = sub < BPI;
-        const int off_d = (int)((DTAB >> (4 * k)) & 0xf), off_t = (int)((TTAB >> (4 * k)) & 0xf);
-        for (int r = warp; r < nf; r += THREADS / 32) {
-            const int64_t rs = ms_row[r] & 0x7fffffff;
-            const int c0 = ms_coff[r], nb = ms_coff[r + 1] - c0;
-            T *out = A.bsr + rs * NB + lane;
-            if (!active) continue;
-            for (int e = sub; e < nb; e += BPI) {
-                const uint32_t code = ms_codes[c0 + e];
-                const uint32_t kind = code >> 14;
-                if (kind == 0) continue;
-                const int slot = (int)(code & 0x1fffu);
-                const T *src = kind == 1 ? dacc + r * NDS + off_d : pacc + slot * NPS + (kind == 2 ? k : off_t);
-                const T val = *src;
-                T *dst = out + (e - sub) * NB;
-                if (code & 0x2000u) atomicAdd(dst, val);
-                else *dst = val;
-            }
-        }
-    }
-    const double sum = block_sum<THREADS>(fe);
-    if (threadIdx.x == 0) A.epart[t] = sum;
+    if (iter == cap) atomicOr(A.status, ST_TIMEOUT);  // the queue never ran dry within its bound
 }
 
-// zero the blocks and gradient (and H v) rows that several tiles add into
+// zero the gradient rows and diagonal blocks of vertices no unit touches
 template <typename T, int VD>
-__global__ void k_zero_shared(const int32_t *blocks, int64_t nb, const int32_t *verts, int64_t nv, T *bsr,
-                              T *grad, T *hv)
+__global__ void k_zero_untouched(const int32_t *verts, const int32_t *blocks, int64_t n, T *grad, T *bsr, T *hv)
 {
-    constexpr int NB = VD * VD;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int d = 0; d < VD; ++d) {
+        if (grad) grad[(int64_t)verts[i] * VD + d] = T(0);
+        if (hv) hv[(int64_t)verts[i] * VD + d] = T(0);
+    }
     if (bsr)
-        for (int64_t i = i0; i < nb * NB; i += stride) bsr[(int64_t)blocks[i / NB] * NB + i % NB] = T(0);
-    if (grad)
-        for (int64_t i = i0; i < nv * VD; i += stride) grad[(int64_t)verts[i / VD] * VD + i % VD] = T(0);
-    if (hv)
-        for (int64_t i = i0; i < nv * VD; i += stride) hv[(int64_t)verts[i / VD] * VD + i % VD] = T(0);
+#pragma unroll
+        for (int k = 0; k < VD * VD; ++k) bsr[(int64_t)blocks[i] * VD * VD + k] = T(0);
 }
 
 // Launch of one (precision, mode, filtering) variant for any energy.  Each
 // variant is instantiated in its own translation unit (tiled_inst.cu) so
-// that they compile in parallel.
-template <typename T, int MODE, bool PROJ>
-void launch_tiled_mode(int energy, int n_tiles, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
+// that they compile in parallel.  Grid: the resident blocks of the whole GPU
+// (persistent), at most one per tile.
+template <typename T, int MODE, bool PROJ, int TT>
+void launch_tiled_threads(int energy, int n_sm, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
 {
-    constexpr int TT = tile_threads<T, PROJ>();
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<n_tiles, TT, smem, s>>>(A);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TT, smem) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        const int grid = (int)std::min<int64_t>((int64_t)per_sm * n_sm, A.tile_end - A.tile_begin);
+        if (grid > 0) kern<<<grid, TT, smem, s>>>(A);
     };
     switch (energy) {
     case ADM_SYMDIR2D: go(k_tiled<T, ADM_SYMDIR2D, true, false, MODE, TT, PROJ>); break;
@@ -410,24 +654,41 @@ void launch_tiled_mode(int energy, int n_tiles, size_t smem, cudaStream_t s, con
     }
 }
 
+// Launch of one (precision, mode, filtering) variant for any energy.  Each
+// variant is instantiated in its own translation unit (tiled_inst.cu) so
+// that they compile in parallel.  Grid: the resident blocks of the whole GPU
+// (persistent), at most one per tile.  FP32 without filtering also has a
+// 128-thread variant (ADM_OPT_TILE_THREADS, the autotuner's second axis).
+template <typename T, int MODE, bool PROJ>
+void launch_tiled_mode(int energy, int threads, int n_sm, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
+{
+    if constexpr (sizeof(T) == 4 && !PROJ) {
+        if (threads == 128) {
+            launch_tiled_threads<T, MODE, PROJ, 128>(energy, n_sm, smem, s, A);
+            return;
+        }
+    }
+    launch_tiled_threads<T, MODE, PROJ, 256>(energy, n_sm, smem, s, A);
+}
+
 #define ADM_TILED_VARIANTS(X, T)                                                                          \
     X(T, MODE_VALUE, false) X(T, MODE_GRAD, false) X(T, MODE_HESS, false) X(T, MODE_HESS, true)           \
     X(T, MODE_HVP, false) X(T, MODE_HVP, true)
 #define ADM_TILED_EXTERN(T, M, P)                                                                          \
-    extern template void launch_tiled_mode<T, M, P>(int, int, size_t, cudaStream_t, const TiledArgs<T> &);
+    extern template void launch_tiled_mode<T, M, P>(int, int, int, size_t, cudaStream_t, const TiledArgs<T> &);
 #define ADM_TILED_INST(T, M, P) \
-    template void launch_tiled_mode<T, M, P>(int, int, size_t, cudaStream_t, const TiledArgs<T> &);
+    template void launch_tiled_mode<T, M, P>(int, int, int, size_t, cudaStream_t, const TiledArgs<T> &);
 
 template <typename T>
-static void launch_tiled(int energy, int mode, bool proj, int n_tiles, size_t smem, cudaStream_t s,
+static void launch_tiled(int energy, int mode, bool proj, int threads, int n_sm, size_t smem, cudaStream_t s,
                          const TiledArgs<T> &A)
 {
-    if (mode == MODE_VALUE) launch_tiled_mode<T, MODE_VALUE, false>(energy, n_tiles, smem, s, A);
-    else if (mode == MODE_GRAD) launch_tiled_mode<T, MODE_GRAD, false>(energy, n_tiles, smem, s, A);
-    else if (mode == MODE_HESS && !proj) launch_tiled_mode<T, MODE_HESS, false>(energy, n_tiles, smem, s, A);
-    else if (mode == MODE_HESS) launch_tiled_mode<T, MODE_HESS, true>(energy, n_tiles, smem, s, A);
-    else if (!proj) launch_tiled_mode<T, MODE_HVP, false>(energy, n_tiles, smem, s, A);
-    else launch_tiled_mode<T, MODE_HVP, true>(energy, n_tiles, smem, s, A);
+    if (mode == MODE_VALUE) launch_tiled_mode<T, MODE_VALUE, false>(energy, threads, n_sm, smem, s, A);
+    else if (mode == MODE_GRAD) launch_tiled_mode<T, MODE_GRAD, false>(energy, threads, n_sm, smem, s, A);
+    else if (mode == MODE_HESS && !proj) launch_tiled_mode<T, MODE_HESS, false>(energy, threads, n_sm, smem, s, A);
+    else if (mode == MODE_HESS) launch_tiled_mode<T, MODE_HESS, true>(energy, threads, n_sm, smem, s, A);
+    else if (!proj) launch_tiled_mode<T, MODE_HVP, false>(energy, threads, n_sm, smem, s, A);
+    else launch_tiled_mode<T, MODE_HVP, true>(energy, threads, n_sm, smem, s, A);
 }
 
 template <typename T>
@@ -436,111 +697,107 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     const HostMesh &m = h->m;
     const int vd = m.vdim;
     const bool hin = has_hinges(a.energy);
-    const TileSet &ts = h->tiles[hin ? PAT_SHELL : PAT_TRI];
+    const int kind = hin ? PAT_SHELL : PAT_TRI;
+    TileSet &ts = h->tiles[kind];
     const int mode = a.hv ? MODE_HVP : (a.bsr ? MODE_HESS : (a.grad ? MODE_GRAD : MODE_VALUE));
-    const size_t smem = (size_t)ts.smem_bytes[vd == 3][sizeof(T) == 4 ? ADM_FP32 : ADM_FP64];
+    const int eb = (int)sizeof(T);
+    int64_t &cached = ts.smem_cache[mode][vd == 3][eb == 8];
+    if (cached == 0) cached = std::max<int64_t>(16, tile_smem_bytes(ts, mode, vd, eb));
+    const size_t smem = (size_t)cached;
     if (smem > 227 * 1024) return ADM_ERR_UNSUPPORTED;
     cudaStream_t s = a.stream;
     StageTimer tm(h, s);
-    const bool pairs = h->inter.kind == (hin ? PAT_SHELL : PAT_TRI) && h->inter.n_terms() > 0;
+    const bool pairs = h->inter.kind == kind && h->inter.n_terms() > 0;
     if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
-    const bool with_bsr = a.bsr != nullptr, with_rows = a.grad || a.hv;
-    // zero the shared outputs listed in [zb0, zb1) and [zv0, zv1)
-    auto zero_range = [&](int64_t zb0, int64_t zb1, int64_t zv0, int64_t zv1, cudaStream_t zs) {
-        const int64_t nzb = with_bsr ? zb1 - zb0 : 0, nzv = with_rows ? zv1 - zv0 : 0;
-        if (nzb + nzv == 0) return;
-        const int64_t work = std::max(nzb * vd * vd, nzv * vd);
-        const int blocks = (int)std::min<int64_t>((work + 255) / 256, 152 * 8);
-        if (vd == 3)
-            k_zero_shared<T, 3><<<blocks, 256, 0, zs>>>(ts.d_zero_blocks + zb0, nzb, ts.d_zero_verts + zv0, nzv,
-                                                         (T *)a.bsr, (T *)a.grad, (T *)a.hv);
-        else
-            k_zero_shared<T, 2><<<blocks, 256, 0, zs>>>(ts.d_zero_blocks + zb0, nzb, ts.d_zero_verts + zv0, nzv,
-                                                         (T *)a.bsr, (T *)a.grad, (T *)a.hv);
-    };
-    const bool split = a.n_split > 0 && a.split_mesh && a.split_ready && !pairs && a.energy != ADM_MLP_MEMBRANE &&
-                       h->split_stream[0] && h->split_stream[1] && h->split_start &&
-                       (int)h->split_done.size() >= a.n_split;
-    if (a.n_split > 0 && !split)  // x arriving in ranges, consumed whole here: wait for all of them
-        for (int k = 0; k < a.n_split; ++k)
-            if (cudaStreamWaitEvent(s, a.split_ready[k], 0) != cudaSuccess) return ADM_ERR_CUDA;
-    if (!split) {
-        tm.begin(ADM_STAGE_ZERO);
-        zero_range(0, (int64_t)ts.zero_blocks.size(), 0, (int64_t)ts.zero_verts.size(), s);
-        tm.end(ADM_STAGE_ZERO);
-    }
+    if (a.energy == ADM_MASS_SPRING && (!ts.cloth_built || !h->d_xhat[a.prec])) return ADM_ERR_UNSUPPORTED;
+    // queue positions and group counters start at zero every pass
+    const int64_t n_sync = 8 + ts.n_groups;
+    if (cudaMemsetAsync(ts.d_sync, 0, n_sync * sizeof(int32_t), s) != cudaSuccess) return ADM_ERR_CUDA;
     TiledArgs<T> A;
     A.hdr = ts.d_hdr;
-    A.tri_loc = ts.d_tri_loc;
-    A.hinge_loc = ts.d_hinge_loc;
+    A.unit = ts.d_unit;
+    A.unit_dst = ts.d_unit_dst;
+    A.slot_dst = ts.d_slot_dst;
     A.foot = ts.d_foot;
     A.meta = ts.d_meta;
     A.meta_off = ts.d_meta_off;
     A.tri_rest = (const T *)ts.d_tri_rest[a.prec];
-    A.hinge_rest = (const T *)ts.d_hinge_rest[a.prec];
-    A.nT = m.nT;
-    A.nH = hin ? m.nH() : 0;
+    A.slot_rest = (const T *)ts.d_slot_rest[a.prec];
+    A.vterm_rest = (const T *)ts.d_vterm_rest[a.prec];
+    A.nU = m.nT;
+    A.nS = ts.n_slots;
     A.x = (const T *)a.x;
     A.grad = (T *)a.grad;
     A.bsr = (T *)a.bsr;
     A.v = (const T *)a.v;
     A.hv = (T *)a.hv;
+    A.partials = (T *)ts.d_partials[a.prec];
+    A.counters = ts.d_sync + 8;
+    A.grp = ts.d_grp;
+    A.grp_items = ts.d_grp_items;
+    A.row_ptr = (pairs && h->inter.d_rp[h->inter.active]) ? h->inter.d_rp[h->inter.active] : h->pat[kind].d_row_ptr;
     A.epart = h->d_epart;
     A.status = h->d_status;
     A.c = consts<T>(h, a.energy);
     A.mlp_table = nullptr;
-    A.cloth_hdr = ts.d_cloth_hdr;
-    A.edge_loc = ts.d_edge_loc;
-    A.vert_loc = ts.d_vert_loc;
-    A.edge_l2 = (const T *)ts.d_edge_l2[a.prec];
-    A.vert_area3 = (const T *)ts.d_vert_area3[a.prec];
     A.xhat = (const T *)h->d_xhat[a.prec];
-    if (a.energy == ADM_MASS_SPRING && (!ts.cloth_built || !A.xhat)) return ADM_ERR_UNSUPPORTED;
     if (a.energy == ADM_MLP_MEMBRANE) {
-        if (sizeof(T) != 4 || !h->d_mlp_theta || !ts.d_tri_perm) return ADM_ERR_UNSUPPORTED;
+        if (sizeof(T) != 4 || !h->d_mlp_theta || !ts.d_tri_verts) return ADM_ERR_UNSUPPORTED;
         tm.begin(ADM_STAGE_MLP);
-        adm_status st = mlp_triangle_table(h->d_mlp_theta, h->d_mlp_norm, m.nT, ts.d_tri_perm, h->d_F,
+        adm_status st = mlp_triangle_table(h->d_mlp_theta, h->d_mlp_norm, m.nT, ts.d_tri_verts,
                                            (const float *)ts.d_tri_rest[ADM_FP32], (const float *)a.x,
                                            h->d_mlp_table, s);
         tm.end(ADM_STAGE_MLP);
         if (st != ADM_OK) return st;
         A.mlp_table = h->d_mlp_table;
     }
-    // tiles [t0, t1): the kernel indexes its per-tile arrays by block, so a
-    // range is a launch over offset pointers
-    auto tiled_range = [&](int32_t t0, int32_t t1, cudaStream_t ks) {
-        if (t1 <= t0) return;
-        TiledArgs<T> B = A;
-        B.hdr += 8 * (int64_t)t0;
-        B.meta_off += t0;
-        B.epart += t0;
-        if (B.cloth_hdr) B.cloth_hdr += 4 * (int64_t)t0;
-        launch_tiled<T>(a.energy, mode, h->proj != 0, t1 - t0, smem, ks, B);
-    };
+    int n_sm = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const bool split = a.n_split > 0 && a.split_mesh && a.split_ready && !pairs && a.energy != ADM_MLP_MEMBRANE &&
+                       h->split_stream[0] && h->split_stream[1] && h->split_start &&
+                       (int)h->split_done.size() >= a.n_split && a.n_split <= 8;
+    if (a.n_split > 0 && !split)  // x arriving in ranges, consumed whole here: wait for all of them
+        for (int k = 0; k < a.n_split; ++k)
+            if (cudaStreamWaitEvent(s, a.split_ready[k], 0) != cudaSuccess) return ADM_ERR_CUDA;
+    const int64_t nz = (int64_t)ts.zero_verts.size();
+    if (nz > 0 && (a.grad || a.bsr || a.hv)) {
+        tm.begin(ADM_STAGE_ZERO);
+        const int blocks = (int)((nz + 255) / 256);
+        if (vd == 3)
+            k_zero_untouched<T, 3><<<blocks, 256, 0, s>>>(ts.d_zero_verts, ts.d_zero_blocks, nz, (T *)a.grad,
+                                                           (T *)a.bsr, (T *)a.hv);
+        else
+            k_zero_untouched<T, 2><<<blocks, 256, 0, s>>>(ts.d_zero_verts, ts.d_zero_blocks, nz, (T *)a.grad,
+                                                           (T *)a.bsr, (T *)a.hv);
+        tm.end(ADM_STAGE_ZERO);
+    }
     tm.begin(ADM_STAGE_TILED);
     if (!split) {
-        tiled_range(0, ts.n_tiles, s);
+        A.next = ts.d_sync;
+        A.tile_begin = 0;
+        A.tile_end = ts.n_tiles;
+        launch_tiled<T>(a.energy, mode, h->proj != 0, h->tile_threads, n_sm, smem, s, A);
     } else {
-        // per mesh range, on two streams in turn: wait for its x, zero its
-        // shared outputs (they lie in its own rows) and run its tiles.  The
-        // copies of later ranges overlap the kernels of earlier ones, and a
-        // range's launch overlaps the tail of the one before; the pass's
-        // stream resumes when every range is done.
-        const Pattern &P = h->pat[hin ? PAT_SHELL : PAT_TRI];
-        auto lb = [](const std::vector<int32_t> &v, int64_t key) {
-            return (int64_t)(std::lower_bound(v.begin(), v.end(), (int32_t)key) - v.begin());
-        };
+        // per mesh range, on two streams in turn: wait for its x and run its
+        // tiles (tiles and groups never span meshes).  The copies of later
+        // ranges overlap the kernels of earlier ones, and a range's launch
+        // overlaps the tail of the one before; the pass's stream resumes when
+        // every range is done.
         if (cudaEventRecord(h->split_start, s) != cudaSuccess) return ADM_ERR_CUDA;
         for (int k = 0; k < a.n_split; ++k) {
             cudaStream_t ks = h->split_stream[k & 1];
-            const int32_t m0 = a.split_mesh[k], m1 = a.split_mesh[k + 1];
-            const int64_t v0 = m.v_off[m0], v1 = m.v_off[m1];
             if (cudaStreamWaitEvent(ks, h->split_start, 0) != cudaSuccess ||
                 cudaStreamWaitEvent(ks, a.split_ready[k], 0) != cudaSuccess)
                 return ADM_ERR_CUDA;
-            zero_range(lb(ts.zero_blocks, P.row_ptr[v0]), lb(ts.zero_blocks, P.row_ptr[v1]), lb(ts.zero_verts, v0),
-                       lb(ts.zero_verts, v1), ks);
-            tiled_range(ts.mesh_tile_off[m0], ts.mesh_tile_off[m1], ks);
+            TiledArgs<T> B = A;
+            B.next = ts.d_sync + k;
+            B.tile_begin = ts.mesh_tile_off[a.split_mesh[k]];
+            B.tile_end = ts.mesh_tile_off[a.split_mesh[k + 1]];
+            if (B.tile_end > B.tile_begin)
+                launch_tiled<T>(a.energy, mode, h->proj != 0, h->tile_threads, n_sm, smem, ks, B);
             if (cudaEventRecord(h->split_done[k], ks) != cudaSuccess) return ADM_ERR_CUDA;
         }
         for (int k = 0; k < a.n_split; ++k)

@@ -1,23 +1,20 @@
-// tiles.cpp -- host construction of the shared-memory tiles of the tiled
-// assembler.
+// tiles.cpp -- host construction of the tiles of the staged-gather assembler.
 //
 // The paper evaluates each term over RXMesh patches staged in shared memory
 // (Sec. 2.4, Sec. 5.2) and scatters with global atomics (Sec. 5.5).  Here a
-// tile is a run of about `tile_tris` triangles in Morton order of their rest
-// centroids (per mesh, never across meshes) plus the hinges whose face A is
-// one of them.  A tile stages the positions of its footprint vertices,
-// accumulates gradient and Hessian contributions of all its elements in
-// shared memory (diagonal blocks as their upper-triangle entries, one block
-// per unordered vertex pair), and writes every BSR row of its footprint with
-// row-contiguous stores.  Blocks and gradient rows that also receive
-// contributions from another tile are "shared": they are zeroed before the
-// pass and written with global atomic additions; all others are written once
-// with plain stores.  Tiles are built in parallel on the host.
+// tile is a run of units (a triangle and its attached edges, see TileSet in
+// internal.h) in Morton order of their rest centroids, per mesh.  The builder
+// lays out, per tile, where every unit writes its contributions ("chunks",
+// sorted by the output they add to), the segments the gather sums, the codes
+// that map segments to BSR positions, and the groups of outputs that several
+// tiles produce.  Everything is built once per mesh, in parallel over meshes
+// and tiles; nothing here runs per pass.
 #include <algorithm>
 #include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <thread>
 
@@ -70,195 +67,233 @@ unsigned worker_count() { return std::max(1u, std::min(16u, std::thread::hardwar
 template <class F>
 void parallel_for(int64_t n, unsigned nt, F &&f)
 {
-    if (n < 64 || nt == 1) {
+    if (n < 2 || nt == 1) {
         for (int64_t i = 0; i < n; ++i) f(i, 0u);
         return;
     }
     std::atomic<int64_t> next(0);
     std::vector<std::thread> th;
-    for (unsigned k = 0; k < nt; ++k)
+    for (unsigned k = 0; k < std::min<int64_t>(nt, n); ++k)
         th.emplace_back([&, k] {
             for (int64_t i; (i = next.fetch_add(1)) < n;) f(i, k);
         });
     for (auto &t : th) t.join();
 }
 
-constexpr int TP[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-constexpr int HP[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+uint64_t pkey(int64_t a, int64_t b, int64_t nV)
+{
+    return a < b ? (uint64_t)a * (uint64_t)nV + (uint64_t)b : (uint64_t)b * (uint64_t)nV + (uint64_t)a;
+}
 
-// per-thread scratch: vertex -> local id map and an open-addressing set of
-// local vertex pairs (keys lo << 16 | hi)
-struct Work {
-    std::vector<int32_t> lid;   // nV, -1 when unused
-    std::vector<uint32_t> hkey; // 0xffffffff = empty
-    std::vector<uint16_t> hval; // slot per key
-    std::vector<uint32_t> hused;
-    std::vector<int32_t> foot;
-    std::vector<uint32_t> pairs;
-    explicit Work(int64_t nV) : lid(nV, -1), hkey(1u << 16, 0xffffffffu), hval(1u << 16, 0) {}
-    static uint32_t hash(uint32_t k) { return (k * 2654435761u) >> 16; }
-    bool insert(uint32_t k)  // true if new
-    {
-        uint32_t h = hash(k);
-        while (hkey[h] != 0xffffffffu) {
-            if (hkey[h] == k) return false;
-            h = (h + 1) & 0xffffu;
-        }
-        hkey[h] = k;
-        hused.push_back(h);
-        return true;
-    }
-    uint16_t &value(uint32_t k)
-    {
-        uint32_t h = hash(k);
-        while (hkey[h] != k) h = (h + 1) & 0xffffu;
-        return hval[h];
-    }
-    void clear_pairs()
-    {
-        for (uint32_t h : hused) hkey[h] = 0xffffffffu;
-        hused.clear();
-        pairs.clear();
-    }
+// A face with its rotation and attached edges, as a unit.
+struct UnitRec {
+    int32_t face;
+    int32_t t[3];       // vertices (global), in the triangle's own order
+    int32_t extra[3];   // per slot: the vertex across the slot's edge, -1 if none (boundary)
+    int32_t hinge[3];   // per slot: canonical hinge index, -1 if none or no hinges
+    int nslot;
+    int rot;            // slot s is the edge (t_k, t_k+1) of k = (rot + s) mod 3
 };
 
-uint32_t pkey(uint32_t a, uint32_t b) { return a < b ? (a << 16 | b) : (b << 16 | a); }
+}  // namespace
 
-// out[j] = in[m_j], where m_j runs over m mod q, then m div q, q = ceil(n / 32):
-// stored neighbours are about n/32 apart in the input order.  Concurrent lanes
-// then rarely accumulate into the same shared-memory entry, and each warp's
-// loads stay contiguous.
-void interleave32(const std::vector<int32_t> &in, int32_t *out)
+static int64_t align16(int64_t b) { return (b + 15) & ~int64_t(15); }
+
+int64_t tile_smem_bytes(const TileSet &ts, int mode, int vd, int elem_bytes)
 {
-    const int64_t n = (int64_t)in.size(), q = (n + 31) / 32;
-    int64_t j = 0;
-    for (int64_t r = 0; r < q; ++r)
-        for (int64_t m = r; m < n; m += q) out[j++] = in[m];
+    int64_t best = 0;
+    for (int32_t t = 0; t < ts.n_tiles; ++t) {
+        const int32_t *hd = &ts.hdr[(size_t)kHdr * t];
+        const TileLayout L = tile_layout(hd[kHdrNF], hd[kHdrNVC], hd[kHdrNPC],
+                                         (int)(ts.meta_off[t + 1] - ts.meta_off[t]), mode, vd, elem_bytes);
+        best = std::max<int64_t>(best, L.total);
+    }
+    return best;
 }
 
-// Warp groups with few shared-memory bank conflicts.  Element e of a tile has
-// R "roles" (its vertices and its pairs, in their fixed order); in role r one
-// warp instruction of the kernel touches, for each of its 32 lanes, the
-// accumulator of that lane's element, whose bank is key[e][r] = (slot index)
-// mod 32 (the accumulator strides are odd).  Consecutive runs of 32 stored
-// elements are one warp's lanes, so the stored order is built group by group:
-// each element, in the given order, joins the group (with room left) where
-// its keys collide least with those already there.  Distinct banks also mean
-// distinct addresses, so colliding float atomics retry less.
-void bank_groups(int64_t n, int R, const std::vector<uint8_t> &key, std::vector<int32_t> &perm)
-{
-    const int64_t G = (n + 31) / 32;
-    std::vector<uint8_t> occ((size_t)G * R * 32, 0);
-    std::vector<int32_t> fill(G, 0);
-    std::vector<std::vector<int32_t>> members(G);
-    for (int64_t e = 0; e < n; ++e) {
-        int64_t best = -1, best_c = 0;
-        for (int64_t g = 0; g < G; ++g) {
-            const int64_t capg = g + 1 < G ? 32 : n - 32 * (G - 1);
-            if (fill[g] >= capg) continue;
-            int64_t c = 0;
-            for (int r = 0; r < R; ++r) c += occ[((size_t)g * R + r) * 32 + key[(size_t)e * R + r]];
-            if (best < 0 || c < best_c) {
-                best = g;
-                best_c = c;
-                if (c == 0) break;
-            }
-        }
-        for (int r = 0; r < R; ++r) occ[((size_t)best * R + r) * 32 + key[(size_t)e * R + r]]++;
-        fill[best]++;
-        members[best].push_back((int32_t)e);
-    }
-    perm.clear();
-    for (auto &m : members) perm.insert(perm.end(), m.begin(), m.end());
-}
+namespace {
 
-// reorder n records of W uint16 (and their permutation entries) by perm
-void apply_order(const std::vector<int32_t> &perm, int W, uint16_t *loc, int32_t *elem_perm)
+// per tile: the sizes that decide its shared memory (HESS, VD = 3)
+struct TileCount {
+    int64_t nf = 0, nvc = 0, npc = 0, ncodes = 0;
+};
+
+int64_t hess_bytes(const TileCount &c, int elem_bytes)
 {
-    const size_t n = perm.size();
-    std::vector<uint16_t> l(loc, loc + n * W);
-    std::vector<int32_t> ep(elem_perm, elem_perm + n);
-    for (size_t j = 0; j < n; ++j) {
-        for (int w = 0; w < W; ++w) loc[j * W + w] = l[(size_t)perm[j] * W + w];
-        elem_perm[j] = ep[perm[j]];
-    }
+    // x, staging (vertex and pair chunks of 9), metadata bound (rows, codes,
+    // and at most one shared output and one group per row and code)
+    return align16(c.nf * 3 * elem_bytes) + align16((c.nvc + c.npc) * 9 * elem_bytes) +
+           align16(16 * c.nf + 4 * c.ncodes + 4 * (c.nf + c.ncodes) + 4 * (c.nf + c.ncodes));
 }
 
 }  // namespace
 
-int64_t tile_meta_bytes(int64_t nf, int64_t ncodes) { return (4 * nf + 2 * (nf + 1) + 2 * ncodes + 15) & ~int64_t(15); }
+// FP32 tiles run two blocks per SM (about 112 KB each), FP64 tiles one
+constexpr int64_t kBudget32 = 110 * 1024, kBudget64 = 220 * 1024;
 
-int64_t tile_smem_bytes(int elem_bytes, int64_t units, int64_t nf, int64_t ncodes)
+adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_units, TileSet &ts)
 {
-    return ((elem_bytes * units + 15) & ~int64_t(15)) + tile_meta_bytes(nf, ncodes);
-}
-
-adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_tris, TileSet &ts)
-{
-    const int64_t nT = m.nT, nH = with_hinges ? m.nH() : 0;
+    const int64_t nT = m.nT, nV = m.nV;
     ts = TileSet();
-    ts.tile_tris = tile_tris;
-    // hinges by face A
-    std::vector<int64_t> hof_off(nT + 1, 0);
-    std::vector<int32_t> hinges_of_face(nH);
-    for (int64_t h = 0; h < nH; ++h) hof_off[m.H_face[h] + 1]++;
-    for (int64_t t = 0; t < nT; ++t) hof_off[t + 1] += hof_off[t];
-    {
-        std::vector<int64_t> pos(hof_off.begin(), hof_off.end() - 1);
-        for (int64_t h = 0; h < nH; ++h) hinges_of_face[pos[m.H_face[h]]++] = (int32_t)h;
-    }
+    ts.tile_units = tile_units = std::max(1, std::min(tile_units, 4096));
     const unsigned nthr = worker_count();
-    std::vector<Work> work;
-    work.reserve(nthr);
-    for (unsigned k = 0; k < nthr; ++k) work.emplace_back(m.nV);
 
-    // shared-memory bytes of the FP64 kernel (VD = 3) for the triangles
-    // order[a, b) and their hinges: accumulators plus the row metadata; a
-    // tile whose rows hold 65,536 or more BSR blocks counts as too large
-    std::vector<int32_t> order(nT);
-    auto units = [&](Work &w, int64_t a, int64_t b) -> int64_t {
-        w.foot.clear();
-        w.clear_pairs();
-        int64_t np = 0;
-        auto add = [&](const int32_t *q, int n) {
-            for (int i = 0; i < n; ++i)
-                if (w.lid[q[i]] < 0) {
-                    w.lid[q[i]] = (int32_t)w.foot.size();
-                    w.foot.push_back(q[i]);
+    // ---- edges: partner face and across vertex of every directed face edge
+    std::vector<int32_t> partner(3 * nT, -1), across(3 * nT, -1);
+    {
+        std::vector<std::pair<uint64_t, int64_t>> de(3 * nT);  // (undirected key, 3 t + k)
+        parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned) {
+            for (int64_t t = m.f_off[k]; t < m.f_off[k + 1]; ++t)
+                for (int c = 0; c < 3; ++c)
+                    de[3 * t + c] = {pkey(m.F[3 * t + c], m.F[3 * t + (c + 1) % 3], nV), 3 * t + c};
+            std::sort(de.begin() + 3 * m.f_off[k], de.begin() + 3 * m.f_off[k + 1]);
+        });
+        for (int64_t i = 0; i < 3 * nT;) {
+            int64_t j = i;
+            while (j < 3 * nT && de[j].first == de[i].first) ++j;
+            if (j - i == 2) {  // two faces: a manifold interior edge if they traverse it oppositely
+                const int64_t a = de[i].second, b = de[i + 1].second;
+                const int64_t ta = a / 3, tb = b / 3;
+                const int ka = (int)(a % 3), kb = (int)(b % 3);
+                if (m.F[3 * ta + ka] == m.F[3 * tb + (kb + 1) % 3]) {
+                    partner[a] = (int32_t)b;
+                    partner[b] = (int32_t)a;
+                    across[a] = m.F[3 * tb + (kb + 2) % 3];
+                    across[b] = m.F[3 * ta + (ka + 2) % 3];
                 }
-            for (int i = 0; i < n; ++i)
-                for (int j = i + 1; j < n; ++j) np += w.insert(pkey(w.lid[q[i]], w.lid[q[j]]));
-        };
-        for (int64_t i = a; i < b; ++i) {
-            add(&m.F[3 * (int64_t)order[i]], 3);
-            for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k)
-                add(&m.H[4 * (int64_t)hinges_of_face[k]], 4);
+            }
+            i = j;
         }
-        int64_t ncodes = 0;
-        for (int32_t v : w.foot) ncodes += P.row_ptr[v + 1] - P.row_ptr[v];
-        const int64_t nf = (int64_t)w.foot.size();
-        const int64_t bytes = tile_smem_bytes(8, 13 * nf + 9 * np, nf, ncodes);
-        for (int32_t v : w.foot) w.lid[v] = -1;
-        w.clear_pairs();
-        return ncodes < 65536 ? bytes : INT64_MAX;
+    }
+    // ---- attach every edge to one of its faces, at most two per face where
+    // the counts allow (greedy over faces, then edges)
+    std::vector<uint8_t> att(nT, 0), natt(nT, 0);
+    parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned) {
+        for (int64_t t = m.f_off[k]; t < m.f_off[k + 1]; ++t)
+            for (int c = 0; c < 3; ++c) {
+                const int64_t e = 3 * t + c, p = partner[e];
+                if (p < 0) {  // boundary (or non-manifold) edge: its own face
+                    att[t] |= (uint8_t)(1u << c);
+                    natt[t]++;
+                    continue;
+                }
+                if (p < e) continue;  // decided from the other side
+                const int64_t tp = p / 3;
+                const int cp = (int)(p % 3);
+                if (natt[t] <= natt[tp]) {
+                    att[t] |= (uint8_t)(1u << c);
+                    natt[t]++;
+                } else {
+                    att[tp] |= (uint8_t)(1u << cp);
+                    natt[tp]++;
+                }
+            }
+    });
+    // canonical hinge of an edge (hinges sorted by (e0, e1), e0 < e1)
+    auto hinge_of = [&](int32_t a, int32_t b) -> int32_t {
+        const int32_t e0 = std::min(a, b), e1 = std::max(a, b);
+        int64_t lo = 0, hi = m.nH();
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            const int32_t x0 = m.H[4 * mid], x1 = m.H[4 * mid + 1];
+            if (x0 < e0 || (x0 == e0 && x1 < e1)) lo = mid + 1;
+            else hi = mid;
+        }
+        return (lo < m.nH() && m.H[4 * lo] == e0 && m.H[4 * lo + 1] == e1) ? (int32_t)lo : -1;
     };
+    // ---- units: rotation so that the attached edges are slots 0, 1, 2
+    std::vector<UnitRec> U(nT);
+    parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned) {
+        for (int64_t t = m.f_off[k]; t < m.f_off[k + 1]; ++t) {
+            const int a = att[t];
+            const int n = __builtin_popcount(a);
+            int r = 0;
+            if (n == 1) r = a == 1 ? 0 : (a == 2 ? 1 : 2);
+            else if (n == 2) {
+                const int k1 = (a & 1) ? 0 : 1, k2 = (a & 4) ? 2 : 1;  // the two set bits, k1 < k2
+                r = ((k1 + 1) % 3 == k2) ? k1 : k2;
+            }
+            UnitRec &u = U[t];
+            u.face = (int32_t)t;
+            u.nslot = n;
+            u.rot = r;
+            for (int i = 0; i < 3; ++i) u.t[i] = m.F[3 * t + i];
+            for (int s = 0; s < 3; ++s) {
+                u.extra[s] = -1;
+                u.hinge[s] = -1;
+                if (s >= n) continue;
+                const int k = (r + s) % 3;  // the slot's edge (t_k, t_k+1)
+                const int64_t e = 3 * t + k;
+                if (with_hinges && partner[e] >= 0) {
+                    u.extra[s] = across[e];
+                    u.hinge[s] = hinge_of(u.t[k], u.t[(k + 1) % 3]);
+                    if (u.hinge[s] < 0) u.extra[s] = -1;
+                }
+            }
+        }
+    });
 
-    // ---- triangle order and tiles per mesh (never across meshes); tiles
-    // must fit the shared memory of the FP64 kernel, larger ones split
-    const int64_t budget = 227 * 1024;
+    // ---- tiles per mesh (never across meshes): runs of units in Morton
+    // order of balanced size, split further until they fit shared memory
+    std::vector<int32_t> order(nT);
     std::vector<std::vector<std::pair<int64_t, int64_t>>> mesh_tiles(m.n_mesh);
+    struct Scratch {
+        std::vector<int32_t> mark;
+        explicit Scratch(int64_t n) : mark(n, -1) {}
+    };
+    std::vector<Scratch> scr;
+    scr.reserve(nthr);
+    for (unsigned k = 0; k < nthr; ++k) scr.emplace_back(nV);
+    auto count_range = [&](Scratch &w, int64_t a, int64_t b) {
+        TileCount c;
+        std::vector<uint64_t> pairs;
+        std::vector<int32_t> touched;
+        for (int64_t i = a; i < b; ++i) {
+            const UnitRec &u = U[order[i]];
+            int32_t vs[6];
+            int nv = 0;
+            for (int q = 0; q < 3; ++q) vs[nv++] = u.t[q];
+            for (int s = 0; s < u.nslot; ++s)
+                if (u.extra[s] >= 0) vs[nv++] = u.extra[s];
+            for (int q = 0; q < nv; ++q)
+                if (w.mark[vs[q]] < 0) {
+                    w.mark[vs[q]] = 1;
+                    touched.push_back(vs[q]);
+                }
+            c.nvc += nv;
+            for (int p = 0; p < 3; ++p) pairs.push_back(pkey(u.t[p], u.t[(p + 1) % 3], nV));
+            for (int s = 0; s < u.nslot; ++s)
+                if (u.extra[s] >= 0) {
+                    c.npc += 3;
+                    for (int q = 0; q < 3; ++q) pairs.push_back(pkey(u.extra[s], u.t[q], nV));
+                }
+            c.npc += 3;
+        }
+        for (int32_t v : touched) w.mark[v] = -1;
+        std::sort(pairs.begin(), pairs.end());
+        c.nf = (int64_t)touched.size();
+        c.ncodes = 2 * (int64_t)(std::unique(pairs.begin(), pairs.end()) - pairs.begin());
+        return c;
+    };
+    std::atomic<int> fail(0);
     parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned th) {
         const int64_t a = m.f_off[k], b = m.f_off[k + 1];
         morton_order(m, a, b, order.data() + a);
         const int64_t n = b - a;
-        const int64_t ntile = (n + tile_tris - 1) / tile_tris;
+        const int64_t ntile = (n + tile_units - 1) / tile_units;
         std::vector<std::pair<int64_t, int64_t>> stack;
-        for (int64_t i = ntile - 1; i >= 0; --i)  // balanced split, processed in order
-            stack.emplace_back(a + (n * i) / ntile, a + (n * (i + 1)) / ntile);
+        for (int64_t i = ntile - 1; i >= 0; --i) stack.emplace_back(a + (n * i) / ntile, a + (n * (i + 1)) / ntile);
         while (!stack.empty()) {
             auto [s0, s1] = stack.back();
             stack.pop_back();
-            if (s1 - s0 > 1 && units(work[th], s0, s1) > budget) {
+            const TileCount c = count_range(scr[th], s0, s1);
+            const bool fits = hess_bytes(c, 4) <= kBudget32 && hess_bytes(c, 8) <= kBudget64 && c.nf < 65536 &&
+                              c.npc < 32768 && c.nvc < 65536 && c.ncodes < 65536;
+            if (!fits) {
+                if (s1 - s0 <= 1) {
+                    fail = ADM_ERR_UNSUPPORTED;
+                    return;
+                }
                 const int64_t mid = (s0 + s1) / 2;
                 stack.emplace_back(mid, s1);
                 stack.emplace_back(s0, mid);
@@ -267,361 +302,441 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
             mesh_tiles[k].emplace_back(s0, s1);
         }
     });
-    std::vector<int64_t> tile_tri_off(1, 0);
+    if (fail) return (adm_status)fail.load();
+    std::vector<int64_t> tile_off(1, 0);
     ts.mesh_tile_off.assign(m.n_mesh + 1, 0);
+    std::vector<int32_t> tile_mesh;
     for (int k = 0; k < m.n_mesh; ++k) {
-        for (auto &r : mesh_tiles[k]) tile_tri_off.push_back(r.second);
-        ts.mesh_tile_off[k + 1] = (int32_t)(tile_tri_off.size() - 1);
+        for (auto &r : mesh_tiles[k]) {
+            tile_off.push_back(r.second);
+            tile_mesh.push_back(k);
+        }
+        ts.mesh_tile_off[k + 1] = (int32_t)(tile_off.size() - 1);
     }
-    const int32_t n_tiles = (int32_t)tile_tri_off.size() - 1;
+    const int32_t n_tiles = (int32_t)tile_off.size() - 1;
     ts.n_tiles = n_tiles;
-    // hinges grouped by tile, in the order of their faces A inside the tile
-    std::vector<int64_t> tile_hinge_off(n_tiles + 1, 0);
-    for (int32_t t = 0; t < n_tiles; ++t) {
-        int64_t c = 0;
-        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) c += hof_off[order[i] + 1] - hof_off[order[i]];
-        tile_hinge_off[t + 1] = tile_hinge_off[t] + c;
-    }
 
-    // ---- per tile: footprint (sorted global ids = local ids), pair slots
-    // (rank in (lo, hi) order), element local ids and slots
-    ts.hdr.assign((size_t)n_tiles * 8, 0);
-    ts.tri_loc.resize(nT * 6);
-    ts.hinge_loc.resize(nH * 10);
-    ts.tri_perm.resize(nT);
-    ts.hinge_perm.resize(nH);
-    std::vector<std::vector<int32_t>> foots(n_tiles);
-    std::vector<std::vector<uint32_t>> pairs(n_tiles);
-    std::atomic<int> fail(0);
-    parallel_for(n_tiles, nthr, [&](int64_t t, unsigned th) {
-        Work &w = work[th];
-        std::vector<int32_t> &foot = foots[t];
-        auto visit = [&](const int32_t *q, int n) {
-            for (int i = 0; i < n; ++i)
-                if (w.lid[q[i]] < 0) {
-                    w.lid[q[i]] = 0;
-                    foot.push_back(q[i]);
-                }
-        };
-        // elements in Morton order, then stored interleaved so that the 32
-        // lanes of a warp (consecutive stored elements) are far apart in it
-        std::vector<int32_t> tri_m, hinge_m;
-        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) {
-            visit(&m.F[3 * (int64_t)order[i]], 3);
-            tri_m.push_back(order[i]);
-            for (int64_t k = hof_off[order[i]]; k < hof_off[order[i] + 1]; ++k) {
-                const int32_t h = hinges_of_face[k];
-                visit(&m.H[4 * (int64_t)h], 4);
-                hinge_m.push_back(h);
-            }
-        }
-        interleave32(tri_m, &ts.tri_perm[tile_tri_off[t]]);
-        interleave32(hinge_m, &ts.hinge_perm[tile_hinge_off[t]]);
-        std::sort(foot.begin(), foot.end());
-        if (foot.size() > 65535) fail = ADM_ERR_UNSUPPORTED;
-        for (size_t r = 0; r < foot.size(); ++r) w.lid[foot[r]] = (int32_t)r;
-        w.clear_pairs();
-        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i) {
-            const int32_t *f = &m.F[3 * (int64_t)ts.tri_perm[i]];
-            for (int a = 0; a < 3; ++a) ts.tri_loc[6 * i + a] = (uint16_t)w.lid[f[a]];
-            for (int p = 0; p < 3; ++p) {
-                const uint32_t k = pkey(w.lid[f[TP[p][0]]], w.lid[f[TP[p][1]]]);
-                if (w.insert(k)) w.pairs.push_back(k);
-            }
-        }
-        for (int64_t i = tile_hinge_off[t]; i < tile_hinge_off[t + 1]; ++i) {
-            const int32_t *q = &m.H[4 * (int64_t)ts.hinge_perm[i]];
-            for (int a = 0; a < 4; ++a) ts.hinge_loc[10 * i + a] = (uint16_t)w.lid[q[a]];
-            for (int p = 0; p < 6; ++p) {
-                const uint32_t k = pkey(w.lid[q[HP[p][0]]], w.lid[q[HP[p][1]]]);
-                if (w.insert(k)) w.pairs.push_back(k);
-            }
-        }
-        std::sort(w.pairs.begin(), w.pairs.end());
-        if (w.pairs.size() > 8191) fail = ADM_ERR_UNSUPPORTED;
-        for (size_t s = 0; s < w.pairs.size(); ++s) w.value(w.pairs[s]) = (uint16_t)s;
-        for (int64_t i = tile_tri_off[t]; i < tile_tri_off[t + 1]; ++i)
-            for (int p = 0; p < 3; ++p)
-                ts.tri_loc[6 * i + 3 + p] = w.value(pkey(ts.tri_loc[6 * i + TP[p][0]], ts.tri_loc[6 * i + TP[p][1]]));
-        for (int64_t i = tile_hinge_off[t]; i < tile_hinge_off[t + 1]; ++i)
-            for (int p = 0; p < 6; ++p)
-                ts.hinge_loc[10 * i + 4 + p] =
-                    w.value(pkey(ts.hinge_loc[10 * i + HP[p][0]], ts.hinge_loc[10 * i + HP[p][1]]));
-        // final stored order: bank-aware warp groups (keys: local ids and
-        // pair slots mod 32, in the kernel's role order)
-        {
-            std::vector<uint8_t> key;
-            std::vector<int32_t> perm;
-            const int64_t t0 = tile_tri_off[t], nt = tile_tri_off[t + 1] - t0;
-            key.resize((size_t)nt * 6);
-            for (int64_t i = 0; i < nt; ++i)
-                for (int r = 0; r < 6; ++r) key[(size_t)i * 6 + r] = (uint8_t)(ts.tri_loc[6 * (t0 + i) + r] & 31);
-            bank_groups(nt, 6, key, perm);
-            apply_order(perm, 6, &ts.tri_loc[6 * t0], &ts.tri_perm[t0]);
-            const int64_t h0 = tile_hinge_off[t], nh = tile_hinge_off[t + 1] - h0;
-            if (nh > 0) {
-                key.resize((size_t)nh * 10);
-                for (int64_t i = 0; i < nh; ++i)
-                    for (int r = 0; r < 10; ++r)
-                        key[(size_t)i * 10 + r] = (uint8_t)(ts.hinge_loc[10 * (h0 + i) + r] & 31);
-                bank_groups(nh, 10, key, perm);
-                apply_order(perm, 10, &ts.hinge_loc[10 * h0], &ts.hinge_perm[h0]);
-            }
-        }
-        pairs[t] = w.pairs;
-        w.clear_pairs();
-        for (int32_t v : foot) w.lid[v] = -1;
-    });
-    if (fail) return (adm_status)fail.load();
-
-    // ---- ownership: vertices touched by several tiles, and the vertex pairs
-    // added into by several tiles (only pairs of two such vertices can be)
-    std::vector<int32_t> v_owner(m.nV, -1);  // tile, or -2 if shared
-    for (int32_t t = 0; t < n_tiles; ++t)
-        for (int32_t v : foots[t]) v_owner[v] = (v_owner[v] == -1) ? t : -2;
-    std::vector<std::pair<uint64_t, int32_t>> bnd;
-    for (int32_t t = 0; t < n_tiles; ++t) {
-        const std::vector<int32_t> &foot = foots[t];
-        for (uint32_t k : pairs[t]) {
-            const int32_t a = foot[k >> 16], b = foot[k & 0xffff];
-            if (v_owner[a] == -2 && v_owner[b] == -2) bnd.emplace_back((uint64_t)a * (uint64_t)m.nV + b, t);
-        }
-    }
-    std::sort(bnd.begin(), bnd.end());
-    std::vector<uint64_t> shared_pairs;
-    for (size_t i = 0; i < bnd.size();) {
-        size_t j = i;
-        while (j < bnd.size() && bnd[j].first == bnd[i].first) ++j;
-        if (j - i > 1) shared_pairs.push_back(bnd[i].first);
-        i = j;
-    }
-    auto pair_shared = [&](int32_t a, int32_t b) {  // global ids, a < b
-        return std::binary_search(shared_pairs.begin(), shared_pairs.end(), (uint64_t)a * (uint64_t)m.nV + b);
+    // ---- per tile: unit order (more slots first, then Morton), footprint,
+    // chunks sorted by target, destinations, segments, codes
+    struct TileOut {
+        std::vector<int32_t> units;                 // canonical faces, in tile order
+        std::vector<int32_t> foot;
+        std::vector<uint16_t> unit, unit_dst, slot_dst;
+        std::vector<int32_t> slot_hinge;            // per slot
+        std::vector<std::array<int32_t, 2>> slot_v; // per slot: its edge (for spring data)
+        std::vector<int32_t> rows;                  // kRowWords per footprint row (shared fields later)
+        std::vector<uint32_t> codes;
+        std::vector<uint64_t> pair_keys;            // produced unordered pairs (global key)
+        int64_t nvc = 0, npc = 0;
     };
-
-    // ---- row codes: the columns a tile touches in footprint row r are, in
-    // ascending order, the lower partners of r (pairs (c, r)), r itself and
-    // the upper partners (pairs (r, c)); walk them against the BSR row
-    std::vector<std::vector<uint16_t>> t_codes(n_tiles);
-    std::vector<std::vector<int32_t>> t_code_off(n_tiles), t_row_start(n_tiles), t_zero(n_tiles);
-    parallel_for(n_tiles, nthr, [&](int64_t t, unsigned) {
-        const std::vector<int32_t> &foot = foots[t];
-        const std::vector<uint32_t> &pp = pairs[t];
-        const int32_t nf = (int32_t)foot.size();
-        std::vector<int32_t> lo_off(nf + 1, 0), up_off(nf + 1, 0);
-        for (uint32_t k : pp) {
-            up_off[(k >> 16) + 1]++;
-            lo_off[(k & 0xffff) + 1]++;
+    std::vector<TileOut> T(n_tiles);
+    const int64_t maxrow = 1024;
+    parallel_for(n_tiles, nthr, [&](int64_t t, unsigned th) {
+        TileOut &o = T[t];
+        Scratch &w = scr[th];
+        std::vector<int32_t> &un = o.units;
+        for (int64_t i = tile_off[t]; i < tile_off[t + 1]; ++i) un.push_back(order[i]);
+        std::stable_sort(un.begin(), un.end(), [&](int32_t x, int32_t y) { return U[x].nslot > U[y].nslot; });
+        // footprint (sorted global ids) and local ids
+        for (int32_t f : un) {
+            const UnitRec &u = U[f];
+            for (int q = 0; q < 3; ++q) o.foot.push_back(u.t[q]);
+            for (int s = 0; s < u.nslot; ++s)
+                if (u.extra[s] >= 0) o.foot.push_back(u.extra[s]);
         }
-        for (int32_t r = 0; r < nf; ++r) {
-            up_off[r + 1] += up_off[r];
-            lo_off[r + 1] += lo_off[r];
-        }
-        // lower partners of every row, ascending (pp is sorted by lo)
-        std::vector<uint32_t> lower(pp.size());  // partner << 16 | slot
-        {
-            std::vector<int32_t> pos(lo_off.begin(), lo_off.end() - 1);
-            for (size_t s = 0; s < pp.size(); ++s) lower[pos[pp[s] & 0xffff]++] = (pp[s] >> 16) << 16 | (uint32_t)s;
-        }
-        std::vector<uint16_t> &codes = t_codes[t];
-        for (int32_t r = 0; r < nf; ++r) {
-            const int32_t v = foot[r];
-            const bool v_sh = v_owner[v] == -2;
-            t_row_start[t].push_back((int32_t)((uint32_t)P.row_ptr[v] | (v_sh ? 0x80000000u : 0u)));
-            t_code_off[t].push_back((int32_t)codes.size());
-            int32_t li = lo_off[r], ui = up_off[r];
-            bool diag_done = false;
-            for (int32_t b = P.row_ptr[v]; b < P.row_ptr[v + 1]; ++b) {
-                const int32_t c = P.col[b];
-                uint16_t code = 0;  // kind 0: block not produced by this tile
-                if (li < lo_off[r + 1] && foot[lower[li] >> 16] == c) {
-                    code = (uint16_t)(3u << 14 | (lower[li] & 0xffffu));  // transposed pair (c, v)
-                    if (v_sh && v_owner[c] == -2 && pair_shared(c, v)) code |= (uint16_t)(1u << 13);
-                    ++li;
-                } else if (!diag_done && c == v) {
-                    code = (uint16_t)(1u << 14);  // diagonal
-                    if (v_sh) code |= (uint16_t)(1u << 13);
-                    diag_done = true;
-                } else if (ui < up_off[r + 1] && foot[pp[ui] & 0xffff] == c) {
-                    code = (uint16_t)(2u << 14 | (uint32_t)ui);  // pair (v, c)
-                    if (v_sh && v_owner[c] == -2 && pair_shared(v, c)) code |= (uint16_t)(1u << 13);
-                    ++ui;
+        std::sort(o.foot.begin(), o.foot.end());
+        o.foot.erase(std::unique(o.foot.begin(), o.foot.end()), o.foot.end());
+        for (size_t r = 0; r < o.foot.size(); ++r) w.mark[o.foot[r]] = (int32_t)r;
+        // chunk records: (target, unit, role) -> position after sorting
+        struct VRec {
+            int32_t lid, unit, role;
+        };
+        struct PRec {
+            int32_t lo, hi, unit, role;
+        };
+        std::vector<VRec> vr;
+        std::vector<PRec> pr;
+        int32_t slot = 0;
+        std::vector<int32_t> slot_first(un.size());
+        for (size_t i = 0; i < un.size(); ++i) {
+            const UnitRec &u = U[un[i]];
+            slot_first[i] = slot;
+            const int32_t l[3] = {w.mark[u.t[0]], w.mark[u.t[1]], w.mark[u.t[2]]};
+            for (int q = 0; q < 3; ++q) vr.push_back({l[q], (int32_t)i, q});
+            const int pp[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+            for (int p = 0; p < 3; ++p)
+                pr.push_back({std::min(l[pp[p][0]], l[pp[p][1]]), std::max(l[pp[p][0]], l[pp[p][1]]), (int32_t)i, p});
+            for (int s = 0; s < u.nslot; ++s, ++slot) {
+                if (u.extra[s] < 0) continue;
+                const int32_t lx = w.mark[u.extra[s]];
+                vr.push_back({lx, (int32_t)i, 3 + s});
+                for (int q = 0; q < 3; ++q) {  // hinge vertex q = tri vertex (rot + s + q) % 3
+                    const int32_t lq = l[(u.rot + s + q) % 3];
+                    pr.push_back({std::min(lx, lq), std::max(lx, lq), (int32_t)i, 3 + 3 * s + q});
                 }
-                codes.push_back(code);
-                if (code & 0x2000) t_zero[t].push_back(b);
             }
-            if (li != lo_off[r + 1] || ui != up_off[r + 1] || !diag_done) fail = ADM_ERR_MESH;
         }
+        std::sort(vr.begin(), vr.end(), [](const VRec &x, const VRec &y) {
+            return x.lid != y.lid ? x.lid < y.lid : (x.unit != y.unit ? x.unit < y.unit : x.role < y.role);
+        });
+        std::sort(pr.begin(), pr.end(), [](const PRec &x, const PRec &y) {
+            if (x.lo != y.lo) return x.lo < y.lo;
+            if (x.hi != y.hi) return x.hi < y.hi;
+            return x.unit != y.unit ? x.unit < y.unit : x.role < y.role;
+        });
+        o.nvc = (int64_t)vr.size();
+        o.npc = (int64_t)pr.size();
+        o.unit.assign(8 * un.size(), 0xffff);
+        o.unit_dst.assign(6 * un.size(), 0xffff);
+        o.slot_dst.assign(4 * (size_t)slot, 0xffff);
+        o.slot_hinge.assign(slot, -1);
+        o.slot_v.assign(slot, {-1, -1});
+        std::vector<int32_t> vseg_start(o.foot.size(), 0), vseg_n(o.foot.size(), 0);
+        for (size_t c = 0; c < vr.size(); ++c) {
+            const VRec &r = vr[c];
+            if (vseg_n[r.lid]++ == 0) vseg_start[r.lid] = (int32_t)c;
+            if (r.role < 3) o.unit_dst[6 * r.unit + r.role] = (uint16_t)c;
+            else o.slot_dst[4 * (slot_first[r.unit] + r.role - 3)] = (uint16_t)c;
+        }
+        // pair segments, keyed by (lo, hi) local ids
+        std::vector<std::array<int32_t, 4>> pseg;  // lo, hi, start, count
+        for (size_t c = 0; c < pr.size(); ++c) {
+            const PRec &r = pr[c];
+            if (pseg.empty() || pseg.back()[0] != r.lo || pseg.back()[1] != r.hi)
+                pseg.push_back({r.lo, r.hi, (int32_t)c, 0});
+            pseg.back()[3]++;
+            if (r.role < 3) o.unit_dst[6 * r.unit + 3 + r.role] = (uint16_t)c;
+            else {
+                const int s = (r.role - 3) / 3, q = (r.role - 3) % 3;
+                o.slot_dst[4 * (slot_first[r.unit] + s) + 1 + q] = (uint16_t)c;
+            }
+        }
+        for (auto &p : pseg) o.pair_keys.push_back(pkey(o.foot[p[0]], o.foot[p[1]], nV));
+        // unit records
+        for (size_t i = 0; i < un.size(); ++i) {
+            const UnitRec &u = U[un[i]];
+            uint16_t *r = &o.unit[8 * i];
+            for (int q = 0; q < 3; ++q) r[q] = (uint16_t)w.mark[u.t[q]];
+            for (int s = 0; s < 3; ++s) r[3 + s] = (s < u.nslot && u.extra[s] >= 0) ? (uint16_t)w.mark[u.extra[s]] : 0xffff;
+            r[6] = (uint16_t)(u.nslot | u.rot << 5);
+            r[7] = (uint16_t)slot_first[i];
+            for (int s = 0; s < u.nslot; ++s) {
+                const int k = (u.rot + s) % 3;
+                o.slot_hinge[slot_first[i] + s] = u.hinge[s];
+                o.slot_v[slot_first[i] + s] = {u.t[k], u.t[(k + 1) % 3]};
+            }
+        }
+        // rows and codes: walk every footprint row's BSR row
+        auto find_pseg = [&](int32_t a, int32_t b) -> const std::array<int32_t, 4> * {
+            const int32_t lo = std::min(a, b), hi = std::max(a, b);
+            auto it = std::lower_bound(pseg.begin(), pseg.end(), std::array<int32_t, 4>{lo, hi, 0, 0},
+                                       [](const std::array<int32_t, 4> &x, const std::array<int32_t, 4> &y) {
+                                           return x[0] != y[0] ? x[0] < y[0] : x[1] < y[1];
+                                       });
+            return (it != pseg.end() && (*it)[0] == lo && (*it)[1] == hi) ? &*it : nullptr;
+        };
+        const int32_t nf = (int32_t)o.foot.size();
+        o.rows.assign((size_t)kRowWords * nf, 0);
+        for (int32_t r = 0; r < nf; ++r) {
+            const int32_t v = o.foot[r];
+            const int32_t b0 = P.row_ptr[v], b1 = P.row_ptr[v + 1];
+            if (b1 - b0 > maxrow) fail = ADM_ERR_UNSUPPORTED;
+            const uint32_t code0 = (uint32_t)o.codes.size();
+            int32_t diag = -1;
+            for (int32_t b = b0; b < b1; ++b) {
+                const int32_t c = P.col[b];
+                if (c == v) {
+                    diag = b - b0;
+                    continue;
+                }
+                const int32_t lc = (c >= 0 && c < nV) ? w.mark[c] : -1;
+                if (lc < 0) continue;
+                const auto *ps = find_pseg(r, lc);
+                if (!ps) continue;
+                if ((*ps)[2] >= 32768 || (*ps)[3] >= 32) fail = ADM_ERR_UNSUPPORTED;
+                o.codes.push_back((uint32_t)(*ps)[2] | (uint32_t)(*ps)[3] << 15 | (uint32_t)(r > lc) << 20 |
+                                  (uint32_t)(b - b0) << 22);
+            }
+            const uint32_t ncode = (uint32_t)o.codes.size() - code0;
+            if (diag < 0 || ncode > 255 || vseg_n[r] > 255 || vseg_n[r] == 0) fail = ADM_ERR_MESH;
+            int32_t *row = &o.rows[(size_t)kRowWords * r];
+            row[0] = b0;
+            row[1] = (int32_t)(code0 | ncode << 16 | (uint32_t)vseg_n[r] << 24);
+            row[2] = vseg_start[r];
+            row[3] = diag;
+        }
+        for (int32_t v : o.foot) w.mark[v] = -1;
     });
     if (fail) return (adm_status)fail.load();
 
-    // ---- concatenate; per tile, the metadata blob the kernel copies into
-    // shared memory: row starts (int32), row code offsets relative to the
-    // tile (uint16, nf + 1) and the codes (uint16), padded to 16 bytes
-    for (auto &x : ts.smem_bytes) x[0] = x[1] = 0;
+    // ---- outputs shared between tiles: rows (vertex in several footprints)
+    // and pair blocks (pair produced by several tiles); groups by tile set
+    // (tile sets never span meshes, so meshes are handled in parallel)
+    struct MeshGroups {
+        std::map<std::vector<int32_t>, int32_t> gid;
+        std::vector<std::vector<int32_t>> sets;
+        std::vector<std::vector<std::array<int32_t, 2>>> rows, blocks;  // items
+        // lookups: shared vertex -> (group, item), shared pair key -> (group, item of (a,b), item of (b,a))
+        std::vector<std::pair<int32_t, std::array<int32_t, 2>>> vmap;
+        std::vector<std::pair<uint64_t, std::array<int32_t, 3>>> pmap;
+    };
+    std::vector<MeshGroups> MG(m.n_mesh);
+    auto diag_pos = [&](int32_t v) {
+        return (int32_t)(std::lower_bound(P.col.begin() + P.row_ptr[v], P.col.begin() + P.row_ptr[v + 1], v) -
+                         (P.col.begin() + P.row_ptr[v]));
+    };
+    auto col_pos = [&](int32_t v, int32_t c) {
+        const auto b = P.col.begin() + P.row_ptr[v], e = P.col.begin() + P.row_ptr[v + 1];
+        // mesh columns ascend within a row
+        return (int32_t)(std::lower_bound(b, e, c) - b);
+    };
+    parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned) {
+        MeshGroups &G = MG[k];
+        const int32_t t0 = ts.mesh_tile_off[k], t1 = ts.mesh_tile_off[k + 1];
+        std::vector<std::pair<int32_t, int32_t>> vt;
+        std::vector<std::pair<uint64_t, int32_t>> pt;
+        for (int32_t t = t0; t < t1; ++t) {
+            for (int32_t v : T[t].foot) vt.emplace_back(v, t);
+            for (uint64_t p : T[t].pair_keys) pt.emplace_back(p, t);
+        }
+        std::sort(vt.begin(), vt.end());
+        std::sort(pt.begin(), pt.end());
+        auto group_of = [&](std::vector<int32_t> &&set) {
+            auto it = G.gid.find(set);
+            if (it != G.gid.end()) return it->second;
+            const int32_t g = (int32_t)G.sets.size();
+            G.gid.emplace(set, g);
+            G.sets.push_back(std::move(set));
+            G.rows.emplace_back();
+            G.blocks.emplace_back();
+            return g;
+        };
+        for (size_t i = 0; i < vt.size();) {
+            size_t j = i;
+            while (j < vt.size() && vt[j].first == vt[i].first) ++j;
+            if (j - i > 1) {
+                std::vector<int32_t> set;
+                for (size_t q = i; q < j; ++q) set.push_back(vt[q].second);
+                const int32_t g = group_of(std::move(set));
+                const int32_t v = vt[i].first;
+                G.vmap.push_back({v, {g, (int32_t)G.rows[g].size()}});
+                G.rows[g].push_back({v, diag_pos(v)});
+            }
+            i = j;
+        }
+        for (size_t i = 0; i < pt.size();) {
+            size_t j = i;
+            while (j < pt.size() && pt[j].first == pt[i].first) ++j;
+            if (j - i > 1) {
+                std::vector<int32_t> set;
+                for (size_t q = i; q < j; ++q) set.push_back(pt[q].second);
+                const int32_t g = group_of(std::move(set));
+                const int32_t a = (int32_t)(pt[i].first / (uint64_t)nV), b = (int32_t)(pt[i].first % (uint64_t)nV);
+                const int32_t ia = (int32_t)G.blocks[g].size();
+                G.blocks[g].push_back({a, col_pos(a, b)});
+                G.blocks[g].push_back({b, col_pos(b, a)});
+                G.pmap.push_back({pt[i].first, {g, ia, ia + 1}});
+            }
+            i = j;
+        }
+    });
+    // global group numbering and partial layout (each tile's region of a
+    // group aligned to 32 floats; rows 12 floats, blocks 9)
+    std::vector<int64_t> mesh_g0(m.n_mesh + 1, 0);
+    for (int k = 0; k < m.n_mesh; ++k) mesh_g0[k + 1] = mesh_g0[k] + (int64_t)MG[k].sets.size();
+    ts.n_groups = mesh_g0[m.n_mesh];
+    ts.grp.assign((size_t)kGrpWords * ts.n_groups, 0);
+    {
+        int64_t base = 0, items = 0;
+        for (int k = 0; k < m.n_mesh; ++k) {
+            const MeshGroups &G = MG[k];
+            for (size_t g = 0; g < G.sets.size(); ++g) {
+                int32_t *h = &ts.grp[(size_t)kGrpWords * (mesh_g0[k] + g)];
+                const int64_t nr = (int64_t)G.rows[g].size(), nb = (int64_t)G.blocks[g].size();
+                const int64_t stride = (12 * nr + 9 * nb + 31) & ~int64_t(31);
+                if (base + stride * (int64_t)G.sets[g].size() > (int64_t)INT32_MAX) return ADM_ERR_UNSUPPORTED;
+                h[0] = (int32_t)base;
+                h[1] = (int32_t)stride;
+                h[2] = (int32_t)G.sets[g].size();
+                h[3] = (int32_t)nr;
+                h[4] = (int32_t)nb;
+                h[5] = (int32_t)items;
+                base += stride * (int64_t)G.sets[g].size();
+                for (auto &r : G.rows[g]) ts.grp_items.insert(ts.grp_items.end(), r.begin(), r.end());
+                for (auto &b : G.blocks[g]) ts.grp_items.insert(ts.grp_items.end(), b.begin(), b.end());
+                items += 2 * (nr + nb);
+            }
+        }
+        ts.partial_floats = base;
+    }
+    for (auto &G : MG) {
+        std::sort(G.vmap.begin(), G.vmap.end());
+        std::sort(G.pmap.begin(), G.pmap.end());
+    }
+
+    // ---- per tile: shared flags, shared-output destinations, groups; blobs
+    ts.hdr.assign((size_t)kHdr * n_tiles, 0);
+    std::vector<std::vector<int32_t>> dst(n_tiles), grps(n_tiles);
+    parallel_for(n_tiles, nthr, [&](int64_t t, unsigned) {
+        TileOut &o = T[t];
+        const int k = tile_mesh[t];
+        const MeshGroups &G = MG[k];
+        auto rank_in = [&](int32_t g) {
+            const auto &set = G.sets[g];
+            return (int32_t)(std::lower_bound(set.begin(), set.end(), (int32_t)t) - set.begin());
+        };
+        auto pdst = [&](int32_t g, int32_t item, bool row) {
+            const int32_t *h = &ts.grp[(size_t)kGrpWords * (mesh_g0[k] + g)];
+            const int64_t off = row ? 12 * (int64_t)item : 12 * (int64_t)h[3] + 9 * (int64_t)item;
+            return (int32_t)(h[0] + (int64_t)rank_in(g) * h[1] + off);
+        };
+        const int32_t nf = (int32_t)o.foot.size();
+        std::vector<int32_t> gl;
+        for (int32_t r = 0; r < nf; ++r) {
+            int32_t *row = &o.rows[(size_t)kRowWords * r];
+            const int32_t v = o.foot[r];
+            row[2] |= (int32_t)((uint32_t)dst[t].size() << 16);
+            auto it = std::lower_bound(G.vmap.begin(), G.vmap.end(), std::make_pair(v, std::array<int32_t, 2>{INT32_MIN, 0}));
+            if (it != G.vmap.end() && it->first == v) {
+                row[0] = (int32_t)((uint32_t)row[0] | 0x80000000u);
+                dst[t].push_back(pdst(it->second[0], it->second[1], true));
+                gl.push_back(it->second[0]);
+            }
+            const uint32_t c0 = (uint32_t)row[1] & 0xffffu, nc = ((uint32_t)row[1] >> 16) & 0xffu;
+            for (uint32_t c = c0; c < c0 + nc; ++c) {
+                const uint32_t pos = o.codes[c] >> 22;
+                const int32_t col = P.col[P.row_ptr[v] + pos];
+                const uint64_t key = pkey(v, col, nV);
+                auto pit = std::lower_bound(G.pmap.begin(), G.pmap.end(),
+                                            std::make_pair(key, std::array<int32_t, 3>{INT32_MIN, 0, 0}));
+                if (pit == G.pmap.end() || pit->first != key) continue;
+                o.codes[c] |= 1u << 21;
+                dst[t].push_back(pdst(pit->second[0], v < col ? pit->second[1] : pit->second[2], false));
+                gl.push_back(pit->second[0]);
+            }
+        }
+        std::sort(gl.begin(), gl.end());
+        gl.erase(std::unique(gl.begin(), gl.end()), gl.end());
+        for (int32_t g : gl) grps[t].push_back((int32_t)(mesh_g0[k] + g));
+        if (dst[t].size() >= 65536) fail = ADM_ERR_UNSUPPORTED;
+    });
+    if (fail) return (adm_status)fail.load();
+
+    // ---- concatenate
     ts.meta_off.assign(n_tiles + 1, 0);
     ts.meta.clear();
     for (int32_t t = 0; t < n_tiles; ++t) {
-        const int32_t nf = (int32_t)foots[t].size(), np = (int32_t)pairs[t].size();
-        const int32_t foot_begin = (int32_t)ts.foot.size();
-        const int32_t code_begin = (int32_t)ts.codes.size();
-        ts.foot.insert(ts.foot.end(), foots[t].begin(), foots[t].end());
-        ts.row_start.insert(ts.row_start.end(), t_row_start[t].begin(), t_row_start[t].end());
-        for (int32_t c : t_code_off[t]) ts.code_off.push_back(c + code_begin);
-        ts.code_off.push_back(code_begin + (int32_t)t_codes[t].size());  // sentinel of the last row
-        ts.codes.insert(ts.codes.end(), t_codes[t].begin(), t_codes[t].end());
-        ts.zero_blocks.insert(ts.zero_blocks.end(), t_zero[t].begin(), t_zero[t].end());
-        int32_t *hd = &ts.hdr[8 * (size_t)t];
-        hd[0] = (int32_t)tile_tri_off[t];
-        hd[1] = (int32_t)(tile_tri_off[t + 1] - tile_tri_off[t]);
-        hd[2] = (int32_t)tile_hinge_off[t];
-        hd[3] = (int32_t)(tile_hinge_off[t + 1] - tile_hinge_off[t]);
-        hd[4] = foot_begin;
-        hd[5] = nf;
-        hd[6] = np;
-        hd[7] = code_begin;
-        const int64_t ncodes = (int64_t)t_codes[t].size();
-        if (ncodes >= 65536) return ADM_ERR_UNSUPPORTED;
-        const int64_t mb = tile_meta_bytes(nf, ncodes);
+        TileOut &o = T[t];
+        int32_t *hd = &ts.hdr[(size_t)kHdr * t];
+        const int32_t nf = (int32_t)o.foot.size();
+        hd[kHdrUnit] = (int32_t)tile_off[t];
+        hd[kHdrNUnit] = (int32_t)(tile_off[t + 1] - tile_off[t]);
+        hd[kHdrSlot] = (int32_t)ts.slot_edge.size();
+        hd[kHdrNSlot] = (int32_t)o.slot_hinge.size();
+        hd[kHdrFoot] = (int32_t)ts.foot.size();
+        hd[kHdrNF] = nf;
+        hd[kHdrNVC] = (int32_t)o.nvc;
+        hd[kHdrNPC] = (int32_t)o.npc;
+        hd[kHdrNCode] = (int32_t)o.codes.size();
+        hd[kHdrNShared] = (int32_t)dst[t].size();
+        hd[kHdrNGroup] = (int32_t)grps[t].size();
+        const int64_t rows_b = 4 * (int64_t)kRowWords * nf;
+        const int64_t codes_b = 4 * (int64_t)o.codes.size();
+        const int64_t dst_b = 4 * (int64_t)dst[t].size();
+        const int64_t grp_b = 4 * (int64_t)grps[t].size();
+        hd[kHdrCodeOff] = (int32_t)rows_b;
+        hd[kHdrDstOff] = (int32_t)(rows_b + codes_b);
+        hd[kHdrGrpOff] = (int32_t)(rows_b + codes_b + dst_b);
+        const int64_t mb = align16(rows_b + codes_b + dst_b + grp_b);
         const size_t m0 = ts.meta.size();
         ts.meta.resize(m0 + mb, 0);
         unsigned char *blob = ts.meta.data() + m0;
-        std::memcpy(blob, t_row_start[t].data(), 4 * (size_t)nf);
-        for (int32_t r = 0; r <= nf; ++r) {
-            const uint16_t c = (uint16_t)(r < nf ? t_code_off[t][r] : ncodes);
-            std::memcpy(blob + 4 * nf + 2 * r, &c, 2);
-        }
-        std::memcpy(blob + 6 * nf + 2, t_codes[t].data(), 2 * (size_t)ncodes);
+        std::memcpy(blob, o.rows.data(), rows_b);
+        std::memcpy(blob + rows_b, o.codes.data(), codes_b);
+        std::memcpy(blob + rows_b + codes_b, dst[t].data(), dst_b);
+        std::memcpy(blob + rows_b + codes_b + dst_b, grps[t].data(), grp_b);
         ts.meta_off[t + 1] = (int64_t)ts.meta.size();
-        for (int p = 0; p < 2; ++p) {
-            const int eb = p == 0 ? 8 : 4;  // index: ADM_FP64 = 0, ADM_FP32 = 1
-            ts.smem_bytes[1][p] =
-                std::max(ts.smem_bytes[1][p], tile_smem_bytes(eb, 13 * (int64_t)nf + 9 * (int64_t)np, nf, ncodes));
-            ts.smem_bytes[0][p] =
-                std::max(ts.smem_bytes[0][p], tile_smem_bytes(eb, 7 * (int64_t)nf + 5 * (int64_t)np, nf, ncodes));
+        ts.max_meta = std::max(ts.max_meta, mb);
+        ts.max_nf = std::max<int64_t>(ts.max_nf, nf);
+        ts.max_nvc = std::max(ts.max_nvc, o.nvc);
+        ts.max_npc = std::max(ts.max_npc, o.npc);
+        // unit data
+        ts.foot.insert(ts.foot.end(), o.foot.begin(), o.foot.end());
+        ts.unit.insert(ts.unit.end(), o.unit.begin(), o.unit.end());
+        ts.unit_dst.insert(ts.unit_dst.end(), o.unit_dst.begin(), o.unit_dst.end());
+        ts.slot_dst.insert(ts.slot_dst.end(), o.slot_dst.begin(), o.slot_dst.end());
+        for (size_t s = 0; s < o.slot_hinge.size(); ++s) {
+            ts.slot_edge.push_back(o.slot_hinge[s]);
+            const int32_t h = o.slot_hinge[s];
+            if (h >= 0) {
+                ts.slot_rest.push_back(m.h_thetabar[h]);
+                ts.slot_rest.push_back(m.h_abar[h] / 3.0);
+            } else {  // a spring: squared rest length of the edge
+                const double *a = &m.V[3 * (int64_t)o.slot_v[s][0]], *b = &m.V[3 * (int64_t)o.slot_v[s][1]];
+                double l2 = 0.0;
+                for (int d = 0; d < 3; ++d) l2 += (a[d] - b[d]) * (a[d] - b[d]);
+                ts.slot_rest.push_back(l2);
+                ts.slot_rest.push_back(0.0);
+            }
+        }
+        for (int32_t f : o.units) {
+            ts.tri_perm.push_back(f);
+            for (int q = 0; q < 3; ++q) ts.tri_verts.push_back(m.F[3 * (int64_t)f + q]);
+            for (int q = 0; q < 4; ++q) ts.tri_rest.push_back(m.tri_Dinv[4 * (int64_t)f + q]);
+            ts.tri_rest.push_back(m.tri_area[f]);
         }
     }
-    // code_off has one sentinel per tile: footprint row r of tile t is at
-    // index foot_begin + t + r
-    // shared outputs zeroed before every pass, each listed once
-    std::sort(ts.zero_blocks.begin(), ts.zero_blocks.end());
-    ts.zero_blocks.erase(std::unique(ts.zero_blocks.begin(), ts.zero_blocks.end()), ts.zero_blocks.end());
-    for (int64_t v = 0; v < m.nV; ++v)
-        if (v_owner[v] == -2) ts.zero_verts.push_back((int32_t)v);
-    // vertices no element touches: no tile writes their gradient row or
-    // diagonal block, so both are zeroed with the shared ones every pass
-    for (int64_t v = 0; v < m.nV; ++v)
-        if (v_owner[v] == -1) {
-            ts.zero_verts.push_back((int32_t)v);
-            const auto b = P.col.begin() + P.row_ptr[v], e = P.col.begin() + P.row_ptr[v + 1];
-            ts.zero_blocks.push_back((int32_t)(std::lower_bound(b, e, (int32_t)v) - P.col.begin()));
-        }
-    std::sort(ts.zero_verts.begin(), ts.zero_verts.end());
-    std::sort(ts.zero_blocks.begin(), ts.zero_blocks.end());
+    ts.n_slots = (int64_t)ts.slot_edge.size();
+    // vertices no unit touches: their gradient row and diagonal block are
+    // zeroed every pass
+    {
+        std::vector<char> seen(nV, 0);
+        for (int32_t v : ts.foot) seen[v] = 1;
+        for (int64_t v = 0; v < nV; ++v)
+            if (!seen[v]) {
+                ts.zero_verts.push_back((int32_t)v);
+                ts.zero_blocks.push_back(P.row_ptr[v] + diag_pos((int32_t)v));
+            }
+    }
     static std::atomic<int64_t> builds(0);
     ts.build_id = ++builds;
     ts.built = true;
     return ADM_OK;
 }
 
-// Mass-spring elements on a built triangle tile set (Sec. 7.1: per-edge
-// springs, per-vertex inertia and gravity).  An edge belongs to the tile of
-// the first triangle (in tile order) that has it, so both its vertices are in
-// that tile's footprint and their pair has a slot there (read from that
-// triangle's record); a vertex belongs to the first tile whose footprint has
-// it.  Both lists are stored in bank-aware warp groups like the triangles.
+// Cloth data on a triangle tile set (Sec. 7.1): every slot already carries
+// its edge's squared rest length (a spring); here every vertex becomes the
+// inertia-and-gravity term of the first unit (in tile order) that has it.
 adm_status tiles_build_cloth(const HostMesh &m, TileSet &ts)
 {
     if (!ts.built || ts.n_tiles == 0) return ADM_ERR_ARG;
-    const int32_t n_tiles = ts.n_tiles;
-    struct Cand {
-        uint64_t key;   // lo * nV + hi
-        int64_t pos;    // triangle position in tile order
-        int32_t pair;   // which of its 3 pairs
-    };
-    std::vector<Cand> cand;
-    cand.reserve(3 * (size_t)m.nT);
-    for (int32_t t = 0; t < n_tiles; ++t) {
-        const int32_t *hd = &ts.hdr[8 * (size_t)t];
-        for (int64_t i = hd[0]; i < (int64_t)hd[0] + hd[1]; ++i) {
-            const int32_t *f = &m.F[3 * (int64_t)ts.tri_perm[i]];
-            for (int p = 0; p < 3; ++p) {
-                const int64_t a = f[TP[p][0]], b = f[TP[p][1]];
-                cand.push_back({(uint64_t)std::min(a, b) * (uint64_t)m.nV + (uint64_t)std::max(a, b), i, p});
-            }
-        }
-    }
-    std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.key < y.key; });
-    std::vector<int32_t> tile_of_pos(m.nT);
-    for (int32_t t = 0; t < n_tiles; ++t)
-        for (int64_t i = ts.hdr[8 * (size_t)t]; i < (int64_t)ts.hdr[8 * (size_t)t] + ts.hdr[8 * (size_t)t + 1]; ++i)
-            tile_of_pos[i] = t;
-    std::vector<std::vector<int64_t>> tile_edges(n_tiles);  // index into cand of the owning record
-    for (size_t i = 0; i < cand.size();) {
-        size_t j = i;
-        while (j < cand.size() && cand[j].key == cand[i].key) ++j;
-        tile_edges[tile_of_pos[cand[i].pos]].push_back((int64_t)i);  // first in tile order (stable sort)
-        i = j;
-    }
-    std::vector<char> vseen(m.nV, 0);
-    ts.cloth_hdr.assign(4 * (size_t)n_tiles, 0);
-    ts.edge_loc.clear();
-    ts.vert_loc.clear();
-    ts.edge_l2.clear();
-    ts.vert_area3.clear();
     std::vector<double> area3(m.nV, 0.0);
     for (int64_t t = 0; t < m.nT; ++t)
         for (int c = 0; c < 3; ++c) area3[m.F[3 * t + c]] += m.tri_area[t] / 3.0;
-    for (int32_t t = 0; t < n_tiles; ++t) {
-        const int32_t *hd = &ts.hdr[8 * (size_t)t];
-        const int32_t foot_begin = hd[4], nf = hd[5];
-        // edges in bank-aware warp groups (keys: both local ids, the pair slot)
-        const int64_t ne = (int64_t)tile_edges[t].size();
-        std::vector<uint8_t> key((size_t)ne * 3);
-        for (int64_t q = 0; q < ne; ++q) {
-            const Cand &c = cand[tile_edges[t][q]];
-            const uint16_t *tl = &ts.tri_loc[6 * c.pos];
-            key[(size_t)q * 3] = (uint8_t)(tl[TP[c.pair][0]] & 31);
-            key[(size_t)q * 3 + 1] = (uint8_t)(tl[TP[c.pair][1]] & 31);
-            key[(size_t)q * 3 + 2] = (uint8_t)(tl[3 + c.pair] & 31);
-        }
-        std::vector<int32_t> il;
-        bank_groups(ne, 3, key, il);
-        ts.cloth_hdr[4 * (size_t)t] = (int32_t)(ts.edge_loc.size() / 3);
-        ts.cloth_hdr[4 * (size_t)t + 1] = (int32_t)ne;
-        for (int32_t q : il) {
-            const Cand &c = cand[tile_edges[t][q]];
-            const uint16_t *tl = &ts.tri_loc[6 * c.pos];
-            ts.edge_loc.push_back(tl[TP[c.pair][0]]);
-            ts.edge_loc.push_back(tl[TP[c.pair][1]]);
-            ts.edge_loc.push_back(tl[3 + c.pair]);
-            const int64_t a = ts.foot[foot_begin + tl[TP[c.pair][0]]], b = ts.foot[foot_begin + tl[TP[c.pair][1]]];
-            double l2 = 0.0;
-            for (int d = 0; d < 3; ++d) l2 += (m.V[3 * a + d] - m.V[3 * b + d]) * (m.V[3 * a + d] - m.V[3 * b + d]);
-            if (!(l2 > 0.0)) return ADM_ERR_MESH;
-            ts.edge_l2.push_back(l2);
-        }
-        // vertices first seen in this tile, in bank-aware warp groups
-        std::vector<int32_t> vl;
-        for (int32_t r = 0; r < nf; ++r) {
-            const int32_t v = ts.foot[foot_begin + r];
-            if (!vseen[v]) {
-                vseen[v] = 1;
-                vl.push_back(r);
+    std::vector<char> seen(m.nV, 0);
+    ts.vterm_rest.clear();
+    for (int32_t t = 0; t < ts.n_tiles; ++t) {
+        int32_t *hd = &ts.hdr[(size_t)kHdr * t];
+        hd[kHdrVTerm] = (int32_t)ts.vterm_rest.size();
+        int32_t n = 0;
+        for (int32_t i = 0; i < hd[kHdrNUnit]; ++i) {
+            const int64_t u = (int64_t)hd[kHdrUnit] + i;
+            uint16_t *r = &ts.unit[8 * u];
+            r[6] &= (uint16_t)~(7u << 2);  // the vertex-term mask (slots and rotation kept)
+            r[3] = (uint16_t)n;  // first vertex term of the unit, within the tile
+            for (int q = 0; q < 3; ++q) {
+                const int32_t v = ts.tri_verts[3 * u + q];
+                if (seen[v]) continue;
+                seen[v] = 1;
+                r[6] |= (uint16_t)(1u << (2 + q));
+                ts.vterm_rest.push_back(area3[v]);
+                ++n;
             }
         }
-        std::vector<uint8_t> vkey(vl.size());
-        for (size_t q = 0; q < vl.size(); ++q) vkey[q] = (uint8_t)(vl[q] & 31);
-        std::vector<int32_t> vperm, vil(vl.size());
-        bank_groups((int64_t)vl.size(), 1, vkey, vperm);
-        for (size_t q = 0; q < vl.size(); ++q) vil[q] = vl[vperm[q]];
-        ts.cloth_hdr[4 * (size_t)t + 2] = (int32_t)ts.vert_loc.size();
-        ts.cloth_hdr[4 * (size_t)t + 3] = (int32_t)vil.size();
-        for (int32_t r : vil) {
-            ts.vert_loc.push_back((uint16_t)r);
-            ts.vert_area3.push_back(area3[ts.foot[foot_begin + r]]);
-        }
+        if (n >= 65536) return ADM_ERR_UNSUPPORTED;
+        hd[kHdrNVTerm] = n;
     }
+    ts.n_vterms = (int64_t)ts.vterm_rest.size();
     ts.cloth_built = true;
     return ADM_OK;
 }

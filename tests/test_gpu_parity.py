@@ -60,12 +60,14 @@ def gpu_eval(m: adm.Mesh, energy, prec, x, hess=True, grad=True, batch=False):
     return out
 
 
-def check(energy, prec, rest, faces, x, vd, params=None, tol=None, assembler=0, tile_tris=None):
+def check(energy, prec, rest, faces, x, vd, params=None, tol=None, assembler=0, tile_tris=None, threads=None):
     tol = TOL[prec] if tol is None else tol
     m = adm.Mesh(rest, faces, vd)
     m.set_option(adm.OPT_ASSEMBLER, assembler)
     if tile_tris is not None:
         m.set_option(adm.OPT_TILE_TRIS, tile_tris)
+    if threads is not None:
+        m.set_option(adm.OPT_TILE_THREADS, threads)
     if params is not None:
         m.set_params(energy, params)
     xr = np.asarray(x, dtype=NP[prec])
@@ -313,13 +315,22 @@ def test_graph_replay_matches_direct_launch():
     assert rel(H.cpu().numpy().reshape(-1, 3, 3), ref["vals"]) <= 1e-13
 
 
+@pytest.mark.parametrize("tile", [48, 112, 224])
+def test_shell_128_thread_tiles_fp32(tile):
+    """The autotuner's second axis: 128-thread blocks (several units per
+    thread when the tile is larger than the block), still at the FP32 bar."""
+    sh = synth.icosphere_shell(4, sigma=1e-2, seed=31)
+    check(adm.SHELL, adm.FP32, sh.rest, sh.faces, sh.x, 3, params=SHELL_P, tile_tris=tile, threads=128)
+
+
 def test_autotune_picks_a_candidate_and_stays_correct():
     b = synth.shell_batch([3, 4, 3, 2], sigma=1e-2, seed=22)
     m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
     m.set_params(adm.SHELL, SHELL_P)
     xd = torch.from_numpy(b.x.astype(np.float32)).cuda()
-    best, ms = m.autotune(adm.SHELL, adm.FP32, xd)
-    assert best in (128, 192, 256, 384, 512, 768) and ms > 0
+    best, thr, ms = m.autotune(adm.SHELL, adm.FP32, xd)
+    assert (thr, best) in [(256, u) for u in (96, 128, 160, 192, 224)] + [(128, u) for u in (48, 64, 96, 112)]
+    assert ms > 0
     out = gpu_eval(m, adm.SHELL, adm.FP32, b.x.astype(np.float32), batch=True)
     P = oracle.Problem(b.rest, b.faces, oracle.SHELL, 3, params=SHELL_P)
     ref = P.assemble(b.x.astype(np.float32).astype(np.float64))

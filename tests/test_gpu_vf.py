@@ -259,8 +259,8 @@ def test_autotune_with_contacts_then_parity():
     m.set_params(adm.STVK_MEMBRANE, SHELL_P)
     vf, _ = pick_vf(F, x, 40, seed=76)
     m.set_contacts(adm.STVK_MEMBRANE, None, vf, KAPPA, DHAT, AREA, HSTEP)
-    best, ms = m.autotune(adm.STVK_MEMBRANE, adm.FP64, torch.from_numpy(x.reshape(-1)).cuda())
-    assert best > 0 and ms > 0
+    best, thr, ms = m.autotune(adm.STVK_MEMBRANE, adm.FP64, torch.from_numpy(x.reshape(-1)).cuda())
+    assert best > 0 and thr == 256 and ms > 0
     got = gpu_eval(m, adm.STVK_MEMBRANE, adm.FP64, x)
     check(V, F, x, np.zeros((0, 2), np.int32), vf, got, False, 1e-12)
     m.close()
