@@ -111,7 +111,7 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             const int vs0 = w[2] & 0xffff;
             if (vs0 != vcov) return -113;  // vertex segments in footprint order, back to back
             vcov += nv;
-            const int32_t bd = rs + w[3];
+            const int32_t bd = rs + (w[3] & 0xffff);
             if (P.col[bd] != v) return -114;
             producers[bd]++;
             const int sh = w[0] < 0 ? 1 : 0;

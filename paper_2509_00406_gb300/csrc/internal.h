@@ -166,13 +166,15 @@ struct TileSet {
 // tile header words
 enum TileHdr {
     kHdrUnit = 0, kHdrNUnit, kHdrSlot, kHdrNSlot, kHdrFoot, kHdrNF, kHdrNVC, kHdrNPC, kHdrNCode, kHdrNShared,
-    kHdrNGroup, kHdrCodeOff, kHdrDstOff, kHdrGrpOff, kHdrVTerm, kHdrNVTerm, kHdr = 16
+    kHdrNGroup, kHdrCodeOff, kHdrDstOff, kHdrGrpOff, kHdrVTerm, kHdrNVTerm, kHdrNSharedRows, kHdr = 20
 };
 // footprint row words: [0] BSR start of the row | shared << 31 (its gradient
 // and diagonal block are shared), [1] first code (within the tile) | number
 // of codes << 16 | number of vertex chunks << 24, [2] first vertex chunk |
-// shared-output ordinal of the row's first shared output << 16, [3] position
-// of the diagonal block in the BSR row.
+// the row's shared-output ordinal << 16 (shared rows come first, in row
+// order), [3] position of the diagonal block in the BSR row | number of
+// shared codes in earlier rows << 16 (shared codes follow the shared rows,
+// in code order).
 // code (one per pair block the tile produces): pair-chunk segment start
 // (15 bits) | its chunk count << 15 (5 bits) | transposed << 20 | shared << 21 |
 // position in the BSR row << 22 (10 bits)

@@ -206,6 +206,23 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
+// fixed-order sum of a shared output's kt partials (stride apart), loads
+// issued four at a time
+template <typename T>
+__device__ __forceinline__ T sum_partials(const T *p, int64_t stride, int kt)
+{
+    T acc = -T(0);
+    for (int q0 = 0; q0 < kt; q0 += 4) {
+        T v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = q0 + i < kt ? __ldcg(p + (q0 + i) * stride) : T(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (q0 + i < kt) acc += v[i];
+    }
+    return acc;
+}
+
 __device__ __forceinline__ void discard_l2_line(const void *p)
 {
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
@@ -228,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t meta_bar;
     __shared__ int s_tile, s_nlast;
-    __shared__ int s_last[kMaxGroups];
+    __shared__ int s_last[kMaxGroups], s_eoff[kMaxGroups + 1];
     const int tid = threadIdx.x;
     T *xs = reinterpret_cast<T *>(smem_raw);
     if (MODE >= MODE_GRAD && tid == 0) bar_init(&meta_bar);
@@ -480,68 +497,99 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
         const uint32_t *codes = reinterpret_cast<const uint32_t *>(blob + hd[kHdrCodeOff]);
         const int32_t *pdst = reinterpret_cast<const int32_t *>(blob + hd[kHdrDstOff]);
         if (MODE >= MODE_GRAD && meta_ok) {
-            // gradient (and H v) rows: lanes over (row, entry)
-            constexpr int RW = MODE == MODE_HVP ? 2 * VD : VD;
-            for (int i = tid; i < nf * RW; i += THREADS) {
-                const int r = i / RW, e = i - r * RW;
+            // vertex pass: one lane per footprint row sums the row's vertex
+            // chunks (gradient and diagonal upper entries, or gradient and
+            // H v) in registers and writes its gradient (H v) row and
+            // diagonal block, or the row's partial slot when it is shared
+            for (int r = tid; r < nf; r += THREADS) {
                 const int4 rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
                 const int nv = (int)((uint32_t)rw.y >> 24), vs0 = rw.z & 0xffff;
-                T acc = -T(0);
-                for (int q = 0; q < nv; ++q) acc += sv[CV * (vs0 + q) + e];
+                T acc[CV > 0 ? CV : 1];
+#pragma unroll
+                for (int e = 0; e < CV; ++e) acc[e] = -T(0);
+                const T *src = sv + CV * vs0;
+                for (int q = 0; q < nv; ++q)
+#pragma unroll
+                    for (int e = 0; e < CV; ++e) acc[e] += src[CV * q + e];
                 const int64_t vg = A.foot[fb + r];
-                if (rw.x < 0) {
-                    A.partials[pdst[(uint32_t)rw.z >> 16] + (MODE == MODE_HVP ? e : e)] = acc;
-                } else if (e < VD) {
-                    if (A.grad) A.grad[vg * VD + e] = acc;
+                if (rw.x < 0) {  // shared row: gradient (H v) and diagonal into its partial slot
+                    T *pd = A.partials + pdst[(uint32_t)rw.z >> 16];
+                    if constexpr (MODE == MODE_HESS) {
+#pragma unroll
+                        for (int d = 0; d < VD; ++d) pd[d] = acc[d];
+#pragma unroll
+                        for (int i = 0; i < VD; ++i)
+#pragma unroll
+                            for (int j = 0; j < VD; ++j) pd[VD + i * VD + j] = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < CV; ++e) pd[e] = acc[e];
+                    }
                 } else {
-                    A.hv[vg * VD + e - VD] = acc;
+                    if (A.grad)
+#pragma unroll
+                        for (int d = 0; d < VD; ++d) A.grad[vg * VD + d] = acc[d];
+                    if constexpr (MODE == MODE_HVP) {
+#pragma unroll
+                        for (int d = 0; d < VD; ++d) A.hv[vg * VD + d] = acc[VD + d];
+                    }
+                    if constexpr (MODE == MODE_HESS) {
+                        T *out = A.bsr + ((int64_t)(rw.x & 0x7fffffff) + (rw.w & 0xffff)) * (VD * VD);
+#pragma unroll
+                        for (int i = 0; i < VD; ++i)
+#pragma unroll
+                            for (int j = 0; j < VD; ++j) out[i * VD + j] = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
+                    }
                 }
             }
         }
         if (MODE == MODE_HESS && meta_ok) {
-            // blocks: one warp per footprint row, BPI blocks per warp pass,
-            // lane = sub * NB + k takes entry k of block sub; block 0 of a
-            // row is its diagonal, the others its codes
-            constexpr int NB = VD * VD, BPI = 32 / NB;
-            constexpr uint64_t DTAB = VD == 3 ? 0x543421310ull : 0x2110ull;  // (r,s) -> packed upper
-            constexpr uint64_t TTAB = VD == 3 ? 0x852741630ull : 0x3120ull;  // (r,s) -> (s,r)
-            const int warp = tid >> 5, lane = tid & 31;
-            const int sub = lane / NB, k = lane - sub * NB;
-            const int off_d = VD + (int)((DTAB >> (4 * k)) & 0xf), off_t = (int)((TTAB >> (4 * k)) & 0xf);
-            for (int r = warp; r < nf; r += THREADS / 32) {
-                const int4 rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
+            // pair pass: a half-warp per footprint row, one lane per pair
+            // block of the row; the lane sums the block's segment in chunk
+            // order and transposes once if the row is the higher index
+            constexpr int NB = VD * VD;
+            const int lane = tid & 31, half = lane >> 4, hl16 = lane & 15;
+            const int n_rows_pass = (nf + 1) / 2;
+            const int nsr = hd[kHdrNSharedRows];
+            for (int rr = tid >> 5; rr < n_rows_pass; rr += THREADS / 32) {
+                const int r = 2 * rr + half;
+                int4 rw = make_int4(0, 0, 0, 0);
+                if (r < nf) rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
+                const int c0 = rw.y & 0xffff, nc = r < nf ? (rw.y >> 16) & 0xff : 0;
                 const int64_t rs = rw.x & 0x7fffffff;
-                const bool rshared = rw.x < 0;
-                const int c0 = rw.y & 0xffff, nc = (rw.y >> 16) & 0xff, nv = (int)((uint32_t)rw.y >> 24);
-                const int vs0 = rw.z & 0xffff, ord0 = (int)((uint32_t)rw.z >> 16), dpos = rw.w;
-                int ord = ord0 + (rshared ? 1 : 0);  // ordinal of the row's next shared block
-                for (int b0 = 0; b0 <= nc; b0 += BPI) {
-                    const int jb = b0 + sub;
-                    const bool act = sub < BPI && jb <= nc;
-                    uint32_t code = 0;
-                    if (act && jb > 0) code = codes[c0 + jb - 1];
-                    const bool sh = jb == 0 ? rshared : ((code >> 21) & 1u) != 0;
-                    const uint32_t m = __ballot_sync(0xffffffffu, act && k == 0 && jb > 0 && sh);
+                int ord = nsr + (int)((uint32_t)rw.w >> 16);  // ordinal of the row's first shared code
+                const int nmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
+                for (int j0 = 0; j0 < nmax; j0 += 16) {
+                    const int j = j0 + hl16;
+                    const bool act = j < nc;
+                    const uint32_t code = act ? codes[c0 + j] : 0u;
+                    const bool sh = ((code >> 21) & 1u) != 0;
+                    const uint32_t m = __ballot_sync(0xffffffffu, act && sh);
+                    const uint32_t mine = (m >> (16 * half)) & 0xffffu;
                     if (act) {
-                        T acc = -T(0);
-                        int64_t dst;
-                        T *out;
-                        if (jb == 0) {
-                            const T *src = sv + CV * vs0 + off_d;
-                            for (int q = 0; q < nv; ++q) acc += src[CV * q];
-                            out = rshared ? A.partials : A.bsr;
-                            dst = rshared ? (int64_t)pdst[ord0] + VD + k : (rs + dpos) * NB + k;
-                        } else {
-                            const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 31u);
-                            const T *src = sp + CP * start + (((code >> 20) & 1u) ? off_t : k);
-                            for (int q = 0; q < cnt; ++q) acc += src[CP * q];
-                            const int my = ord + __popc(m & ((1u << (sub * NB)) - 1u));
-                            out = sh ? A.partials : A.bsr;
-                            dst = sh ? (int64_t)pdst[my] + k : (rs + (int64_t)(code >> 22)) * NB + k;
-                        }
-                        out[dst] = acc;
+                        const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 31u);
+                        T acc[NB];
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) acc[k] = -T(0);
+                        const T *src = sp + CP * start;
+                        for (int q = 0; q < cnt; ++q)
+#pragma unroll
+                            for (int k = 0; k < NB; ++k) acc[k] += src[CP * q + k];
+                        if ((code >> 20) & 1u)
+#pragma unroll
+                            for (int i = 0; i < VD; ++i)
+#pragma unroll
+                                for (int k = i + 1; k < VD; ++k) {
+                                    const T tmp = acc[i * VD + k];
+                                    acc[i * VD + k] = acc[k * VD + i];
+                                    acc[k * VD + i] = tmp;
+                                }
+                        T *out = sh ? A.partials + pdst[ord + __popc(mine & ((1u << hl16) - 1u))]
+                                    : A.bsr + (rs + (int64_t)(code >> 22)) * NB;
+#pragma unroll
+                        for (int k = 0; k < NB; ++k) out[k] = acc[k];
                     }
-                    ord += __popc(m);
+                    ord += __popc(mine);
                 }
             }
         }
@@ -549,11 +597,14 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
         if (tid == 0) A.epart[t] = sum;
 
         // ---- shared outputs: the last tile of each group sums the partials
+        // of all the groups it finishes in one flat pass over their entries
         // (the tile's groups in rounds of kMaxGroups)
         const int ng = hd[kHdrNGroup];
         if (MODE >= MODE_GRAD && meta_ok && ng > 0) {
             const int32_t *groups = reinterpret_cast<const int32_t *>(blob + hd[kHdrGrpOff]);
-            __threadfence();
+            constexpr int RE = MODE == MODE_HESS ? VD + VD * VD : (MODE == MODE_HVP ? 2 * VD : VD);
+            constexpr int BE = MODE == MODE_HESS ? VD * VD : 0;
+            __threadfence();  // release: this thread's partials before any counter moves
             __syncthreads();
             for (int g0 = 0; g0 < ng; g0 += kMaxGroups) {
                 if (tid == 0) s_nlast = 0;
@@ -561,21 +612,37 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                 for (int i = g0 + tid; i < min(ng, g0 + kMaxGroups); i += THREADS) {
                     const int g = groups[i];
                     const int kt = A.grp[kGrpWords * (int64_t)g + 2];
-                    if (atomicAdd(A.counters + g, 1) == kt - 1) s_last[atomicAdd(&s_nlast, 1)] = g;
+                    if (atomicAdd(A.counters + g, 1) == kt - 1) {
+                        __threadfence();  // acquire: the other tiles' partials are visible
+                        s_last[atomicAdd(&s_nlast, 1)] = g;
+                    }
                 }
-                __threadfence();
                 __syncthreads();
                 const int nl = s_nlast;
-                for (int j = 0; j < nl; ++j) {
+                if (nl == 0) continue;
+                // entry offsets of the finished groups (rows RE entries, blocks BE)
+                if (tid == 0) {
+                    int acc = 0;
+                    for (int j = 0; j < nl; ++j) {
+                        s_eoff[j] = acc;
+                        const int32_t *gh = A.grp + kGrpWords * (int64_t)s_last[j];
+                        acc += gh[3] * RE + gh[4] * BE;
+                    }
+                    s_eoff[nl] = acc;
+                }
+                __syncthreads();
+                const int ne = s_eoff[nl];
+                for (int i = tid; i < ne; i += THREADS) {
+                    int j = 0;
+                    while (j + 1 < nl && s_eoff[j + 1] <= i) ++j;
                     const int32_t *gh = A.grp + kGrpWords * (int64_t)s_last[j];
                     const int64_t base = gh[0], stride = gh[1];
-                    const int kt = gh[2], nr = gh[3], nb = gh[4];
+                    const int kt = gh[2], nr = gh[3];
                     const int32_t *items = A.grp_items + gh[5];
-                    constexpr int RE = MODE == MODE_HESS ? VD + VD * VD : (MODE == MODE_HVP ? 2 * VD : VD);
-                    for (int i = tid; i < nr * RE; i += THREADS) {
-                        const int it = i / RE, e = i - it * RE;
-                        T acc = -T(0);
-                        for (int q = 0; q < kt; ++q) acc += __ldcg(A.partials + base + q * stride + 12 * it + e);
+                    const int li = i - s_eoff[j];
+                    if (li < nr * RE) {
+                        const int it = li / RE, e = li - it * RE;
+                        const T acc = sum_partials(A.partials + base + 12 * it + e, stride, kt);
                         const int64_t v = items[2 * it];
                         if (e < VD) {
                             if (A.grad) A.grad[v * VD + e] = acc;
@@ -584,23 +651,21 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                         } else {
                             A.bsr[((int64_t)A.row_ptr[v] + items[2 * it + 1]) * (VD * VD) + e - VD] = acc;
                         }
+                    } else if constexpr (BE > 0) {
+                        const int bi = li - nr * RE, it = bi / BE, e = bi - it * BE;
+                        const T acc = sum_partials(A.partials + base + 12 * nr + 9 * it + e, stride, kt);
+                        const int64_t v = items[2 * nr + 2 * it];
+                        A.bsr[((int64_t)A.row_ptr[v] + items[2 * nr + 2 * it + 1]) * (VD * VD) + e] = acc;
                     }
-                    if (MODE == MODE_HESS)
-                        for (int i = tid; i < nb * VD * VD; i += THREADS) {
-                            const int it = i / (VD * VD), e = i - it * (VD * VD);
-                            T acc = -T(0);
-                            for (int q = 0; q < kt; ++q)
-                                acc += __ldcg(A.partials + base + q * stride + 12 * nr + 9 * it + e);
-                            const int64_t v = items[2 * nr + 2 * it];
-                            A.bsr[((int64_t)A.row_ptr[v] + items[2 * nr + 2 * it + 1]) * (VD * VD) + e] = acc;
-                        }
-                    __syncthreads();
-                    // the partial lines are dead: drop them from L2 without a write-back
-                    const int64_t lines = (int64_t)kt * stride * (int64_t)sizeof(T) / 128;
-                    const char *p0 = reinterpret_cast<const char *>(A.partials + base);
-                    for (int64_t i = tid; i < lines; i += THREADS) discard_l2_line(p0 + 128 * i);
                 }
                 __syncthreads();
+                // the partial lines are dead: drop them from L2 without a write-back
+                for (int j = 0; j < nl; ++j) {
+                    const int32_t *gh = A.grp + kGrpWords * (int64_t)s_last[j];
+                    const int64_t lines = (int64_t)gh[2] * gh[1] * (int64_t)sizeof(T) / 128;
+                    const char *p0 = reinterpret_cast<const char *>(A.partials + gh[0]);
+                    for (int64_t i = tid; i < lines; i += THREADS) discard_l2_line(p0 + 128 * i);
+                }
             }
         }
         __syncthreads();

@@ -591,14 +591,16 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
             return (int32_t)(h[0] + (int64_t)rank_in(g) * h[1] + off);
         };
         const int32_t nf = (int32_t)o.foot.size();
-        std::vector<int32_t> gl;
+        std::vector<int32_t> gl, code_dst;
+        int32_t n_shared_codes = 0;
         for (int32_t r = 0; r < nf; ++r) {
             int32_t *row = &o.rows[(size_t)kRowWords * r];
             const int32_t v = o.foot[r];
-            row[2] |= (int32_t)((uint32_t)dst[t].size() << 16);
+            row[3] |= (int32_t)((uint32_t)n_shared_codes << 16);
             auto it = std::lower_bound(G.vmap.begin(), G.vmap.end(), std::make_pair(v, std::array<int32_t, 2>{INT32_MIN, 0}));
             if (it != G.vmap.end() && it->first == v) {
                 row[0] = (int32_t)((uint32_t)row[0] | 0x80000000u);
+                row[2] |= (int32_t)((uint32_t)dst[t].size() << 16);
                 dst[t].push_back(pdst(it->second[0], it->second[1], true));
                 gl.push_back(it->second[0]);
             }
@@ -611,10 +613,13 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
                                             std::make_pair(key, std::array<int32_t, 3>{INT32_MIN, 0, 0}));
                 if (pit == G.pmap.end() || pit->first != key) continue;
                 o.codes[c] |= 1u << 21;
-                dst[t].push_back(pdst(pit->second[0], v < col ? pit->second[1] : pit->second[2], false));
+                code_dst.push_back(pdst(pit->second[0], v < col ? pit->second[1] : pit->second[2], false));
                 gl.push_back(pit->second[0]);
+                ++n_shared_codes;
             }
         }
+        ts.hdr[(size_t)kHdr * t + kHdrNSharedRows] = (int32_t)dst[t].size();
+        dst[t].insert(dst[t].end(), code_dst.begin(), code_dst.end());
         std::sort(gl.begin(), gl.end());
         gl.erase(std::unique(gl.begin(), gl.end()), gl.end());
         for (int32_t g : gl) grps[t].push_back((int32_t)(mesh_g0[k] + g));
