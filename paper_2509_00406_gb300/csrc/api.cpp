@@ -167,8 +167,8 @@ int tile_tris_for(const adm_ctx *h)
 void free_tiles(adm_ctx *h, TileSet &ts)
 {
     void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_tri_perm, ts.d_tri_verts, ts.d_unit, ts.d_unit_dst, ts.d_slot_dst,
-                    ts.d_meta, ts.d_meta_off, ts.d_grp, ts.d_grp_items, ts.d_zero_verts, ts.d_zero_blocks,
-                    ts.d_mesh_tile_off, ts.d_sync, ts.d_partials[0], ts.d_partials[1], ts.d_tri_rest[0],
+                    ts.d_meta, ts.d_meta_off, ts.d_zero_verts, ts.d_zero_blocks,
+                    ts.d_mesh_tile_off, ts.d_sync, ts.d_tri_rest[0],
                     ts.d_tri_rest[1], ts.d_slot_rest[0], ts.d_slot_rest[1], ts.d_vterm_rest[0], ts.d_vterm_rest[1]};
     for (void *p : ptrs) dev_free(h, p);
     ts = TileSet();
@@ -202,18 +202,10 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
     if ((s = up(&ts.d_slot_dst, ts.slot_dst)) != ADM_OK) return s;
     if ((s = up(&ts.d_meta, ts.meta)) != ADM_OK) return s;
     if ((s = up(&ts.d_meta_off, ts.meta_off)) != ADM_OK) return s;
-    if ((s = up(&ts.d_grp, ts.grp)) != ADM_OK) return s;
-    if ((s = up(&ts.d_grp_items, ts.grp_items)) != ADM_OK) return s;
     if ((s = up(&ts.d_zero_verts, ts.zero_verts)) != ADM_OK) return s;
     if ((s = up(&ts.d_zero_blocks, ts.zero_blocks)) != ADM_OK) return s;
     if ((s = up(&ts.d_mesh_tile_off, ts.mesh_tile_off)) != ADM_OK) return s;
-    if ((s = dev_alloc(h, &ts.d_sync, (8 + (size_t)ts.n_groups) * sizeof(int32_t))) != ADM_OK) return s;
-    for (int p = 0; p < 2; ++p) {
-        const size_t eb = p == ADM_FP32 ? 4 : 8;
-        char *buf = nullptr;
-        if ((s = dev_alloc(h, &buf, std::max<size_t>(256, (size_t)ts.partial_floats * eb))) != ADM_OK) return s;
-        ts.d_partials[p] = buf;
-    }
+    if ((s = dev_alloc(h, &ts.d_sync, (8 + (size_t)ts.n_tiles) * sizeof(int32_t))) != ADM_OK) return s;
     {
         const int64_t nU = (int64_t)ts.tri_perm.size();
         std::vector<std::vector<double>> f(5, std::vector<double>(nU));

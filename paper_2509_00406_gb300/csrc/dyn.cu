@@ -292,8 +292,7 @@ __global__ void k_remap_tiles(int32_t n_tiles, const int32_t *hdr, const int32_t
     const int32_t foot_begin = hdr[kHdr * t + kHdrFoot], nf = hdr[kHdr * t + kHdrNF];
     int32_t *rows = reinterpret_cast<int32_t *>(meta + meta_off[t]);
     for (int r = threadIdx.x; r < nf; r += blockDim.x)
-        rows[kRowWords * r] = (int32_t)(((uint32_t)rows[kRowWords * r] & 0x80000000u) |
-                                        (uint32_t)rpx[foot[foot_begin + r]]);
+        rows[kRowWords * r] = rpx[foot[foot_begin + r]];
 }
 
 __global__ void k_remap_zero(int64_t n, const int32_t *row, const int32_t *off, const int32_t *rpx, int32_t *blocks)

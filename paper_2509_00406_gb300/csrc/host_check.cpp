@@ -34,11 +34,12 @@ extern "C" {
 // Builds hinges (if with_hinges), the block pattern and the tiles, and
 // reports, per block of the pattern, which tile produces it:
 //   block_writer[b] = tile id if exactly one tile produces it (written with a
-//   plain store), -2 if several do (each writes a partial, the group's last
-//   tile writes the sum), -1 if no tile does; block_adds[b] = number of tiles
-//   producing a shared block (0 otherwise).
-// stats: {n_tiles, n_groups, n_zero_verts, FP64 Hessian-mode shared-memory
-// bytes (VD = 3), nnzb, nH, build_ms, partial floats}.  Returns 0 or an
+//   plain store), -2 if several do (the lowest stores, the others add in tile
+//   order), -1 if no tile does; block_adds[b] = number of tiles producing a
+//   shared block (0 otherwise).
+// stats: {n_tiles, wait edges (tile, lower tile), n_zero_verts, FP64
+// Hessian-mode shared-memory bytes (VD = 3), nnzb, nH, build_ms, most lower
+// tiles one tile waits for}.  Returns 0 or an
 // adm_status, or a negative code < -99 naming the check that failed.
 int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t nT, const int64_t *v_off,
                         const int64_t *f_off, int32_t n_mesh, int32_t with_hinges, int32_t tile_tris,
@@ -62,9 +63,10 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
         block_writer[b] = -1;
         block_adds[b] = 0;
     }
-    std::vector<int32_t> producers(P.nnzb, 0), shared_flag(P.nnzb, -1);
+    std::vector<int32_t> producers(P.nnzb, 0);
     if ((int64_t)ts.meta_off.size() != ts.n_tiles + 1 || ts.meta_off.back() != (int64_t)ts.meta.size()) return -105;
-    std::vector<char> seen_dst;
+    int64_t n_wait_edges = 0;
+    std::vector<std::vector<int32_t>> who(P.nnzb);  // producing tiles of each block, in order
     for (int32_t t = 0; t < ts.n_tiles; ++t) {
         const int32_t *hd = &ts.hdr[(size_t)kHdr * t];
         const int32_t fb = hd[kHdrFoot], nf = hd[kHdrNF], nvc = hd[kHdrNVC], npc = hd[kHdrNPC];
@@ -85,6 +87,7 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             }
             for (int sl = 0; sl < (r[6] & 3); ++sl) {
                 if (!with_hinges || r[3 + sl] == 0xffff) continue;
+                if (r[3 + sl] >= nf) return -111;
                 const uint16_t *sd = &ts.slot_dst[4 * ((int64_t)hd[kHdrSlot] + r[7] + sl)];
                 if (sd[0] >= nvc) return -110;
                 vw[sd[0]]++;
@@ -98,9 +101,17 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             if (c != 1) return -112;
         for (int c : pw)
             if (c != 1) return -112;
+        // the tiles this one waits for are lower tiles
+        std::vector<int32_t> wl(hd[kHdrNWait]);
+        std::memcpy(wl.data(), blob + hd[kHdrWaitOff], 4 * wl.size());
+        for (int32_t w : wl)
+            if (w < 0 || w >= t) return -121;
+        n_wait_edges += (int64_t)wl.size();
+        auto waits_for = [&](int32_t u) { return std::find(wl.begin(), wl.end(), u) != wl.end(); };
         // rows and codes: segments tile the chunk arrays; blocks produced
         int64_t vcov = 0;
         std::vector<int> pcov(npc, 0);
+        std::vector<std::pair<int32_t, int>> mine;  // blocks this tile produces, with their rank
         for (int32_t r = 0; r < nf; ++r) {
             int32_t w[kRowWords];
             std::memcpy(w, blob + 4 * kRowWords * r, sizeof w);
@@ -113,35 +124,42 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             vcov += nv;
             const int32_t bd = rs + (w[3] & 0xffff);
             if (P.col[bd] != v) return -114;
-            producers[bd]++;
-            const int sh = w[0] < 0 ? 1 : 0;
-            if (shared_flag[bd] >= 0 && shared_flag[bd] != sh) return -115;
-            shared_flag[bd] = sh;
+            mine.emplace_back(bd, w[3] >> 16);
             for (int c = c0; c < c0 + nc; ++c) {
                 uint32_t code;
                 std::memcpy(&code, blob + hd[kHdrCodeOff] + 4 * c, 4);
-                const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 31u);
-                const int tr = (int)((code >> 20) & 1u), csh = (int)((code >> 21) & 1u);
-                const int32_t b = rs + (int32_t)(code >> 22);
+                const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 15u);
+                const int tr = (int)((code >> 19) & 1u), rank = (int)((code >> 20) & 7u);
+                const int32_t b = rs + (int32_t)(code >> 23);
                 if (b >= P.row_ptr[v + 1] || P.col[b] == v) return -116;
                 const int32_t lc = (int32_t)(std::lower_bound(ts.foot.begin() + fb, ts.foot.begin() + fb + nf, P.col[b]) -
                                              (ts.foot.begin() + fb));
                 if (lc >= nf || ts.foot[fb + lc] != P.col[b] || tr != (r > lc ? 1 : 0)) return -117;
                 if (cnt == 0 || start + cnt > npc) return -118;
                 for (int q = start; q < start + cnt; ++q) pcov[q]++;
-                producers[b]++;
-                if (shared_flag[b] >= 0 && shared_flag[b] != csh) return -115;
-                shared_flag[b] = csh;
+                mine.emplace_back(b, rank);
             }
         }
         if (vcov != nvc) return -113;
         for (int c : pcov)  // every pair chunk is summed by its two blocks, (a, b) and (b, a)
             if (c != 2) return -119;
+        // tiles are visited in order: a block of rank r in this tile has been
+        // produced by exactly r lower tiles, all in this tile's wait list
+        if (hd[kHdrRounds] < 1) return -123;
+        for (auto &bm : mine) {
+            const int32_t b = bm.first;
+            if (bm.second != producers[b]) return -115;
+            if (bm.second >= hd[kHdrRounds]) return -123;
+            if (bm.second > 0)
+                for (int32_t u : who[b])
+                    if (!waits_for(u)) return -122;
+            producers[b]++;
+            who[b].push_back(t);
+        }
     }
     for (int64_t b = 0; b < P.nnzb; ++b) {
         if (producers[b] == 0) continue;
-        if ((producers[b] >= 2) != (shared_flag[b] == 1)) return -100;
-        block_writer[b] = producers[b] >= 2 ? -2 : 0;
+        block_writer[b] = producers[b] >= 2 ? -2 : who[b][0];
         block_adds[b] = producers[b] >= 2 ? producers[b] : 0;
     }
     // blocks of vertices no unit touches: the per-pass zero fill
@@ -150,23 +168,14 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
         block_writer[b] = -2;
         block_adds[b] = 2;
     }
-    // every group's tiles are sorted and distinct; partial regions disjoint
-    int64_t prev_end = 0;
-    for (int64_t g = 0; g < ts.n_groups; ++g) {
-        const int32_t *h = &ts.grp[(size_t)kGrpWords * g];
-        if (h[0] < prev_end || h[0] % 32 != 0 || h[1] % 32 != 0 || h[2] < 2) return -120;
-        if (12 * (int64_t)h[3] + 9 * (int64_t)h[4] > h[1]) return -120;
-        prev_end = h[0] + (int64_t)h[1] * h[2];
-    }
-    if (prev_end != ts.partial_floats) return -120;
     stats[0] = ts.n_tiles;
-    stats[1] = (double)ts.n_groups;
+    stats[1] = (double)n_wait_edges;
     stats[2] = (double)ts.zero_verts.size();
     stats[3] = (double)tile_smem_bytes(ts, MODE_HESS, 3, 8);
     stats[4] = (double)P.nnzb;
     stats[5] = (double)m.nH();
     stats[6] = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    stats[7] = (double)ts.partial_floats;
+    stats[7] = (double)ts.max_wait;
     // every triangle is exactly one unit
     std::vector<char> seen_t(nT, 0);
     for (int32_t e : ts.tri_perm)

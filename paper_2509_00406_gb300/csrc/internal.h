@@ -109,11 +109,10 @@ struct ChunkTable {
 // chunks of a tile are laid out sorted by target (vertex, then unit order;
 // pair, then unit order), so every output entry is the fixed-order sum of one
 // contiguous segment: the gather that writes the BSR rows is deterministic
-// and needs no atomics.  Outputs that several tiles produce ("shared" rows and
-// blocks) are written by each of them into partial slots; a group of outputs
-// shared by the same set of tiles is summed, in tile order, by the last of
-// those tiles to finish (an integer counter per group), which also writes the
-// final values.
+// and needs no atomics.  An output that several tiles produce (a "shared" row
+// or block) is stored by the lowest-index of them; each other one waits, with
+// a bounded wait, for the done flags of the lower tiles it shares outputs
+// with and adds its part to what is stored, so the sum runs in tile order.
 struct TileSet {
     bool built = false;
     int64_t build_id = 0;                // distinct for every build (tiles_build)
@@ -138,26 +137,21 @@ struct TileSet {
     std::vector<double> vterm_rest;      // per cloth vertex term: a third of the rest area around it
     std::vector<int32_t> foot;           // footprint vertices (global ids), sorted, per tile
     std::vector<int32_t> mesh_tile_off;  // n_mesh + 1
-    // per tile metadata blob (copied into shared memory): rows, codes, shared
-    // destinations, groups; kRowWords int32 per footprint row
+    // per tile metadata blob (copied into shared memory): kRowWords int32
+    // per footprint row, one code per pair block produced, and the lower
+    // tiles the tile waits for
     std::vector<unsigned char> meta;
     std::vector<int64_t> meta_off;       // n_tiles + 1
-    // groups of shared outputs: kGrpWords int32 each, then their items
-    std::vector<int32_t> grp;
-    std::vector<int32_t> grp_items;      // rows: (vertex, diagonal position); blocks: (row vertex, position)
-    int64_t n_groups = 0, partial_floats = 0;
     std::vector<int32_t> zero_verts;     // vertices no unit touches (zero row and diagonal block)
     std::vector<int32_t> zero_blocks;    // their diagonal blocks
-    int64_t max_nvc = 0, max_npc = 0, max_nf = 0, max_meta = 0;  // largest counts over the tiles
+    int64_t max_nvc = 0, max_npc = 0, max_nf = 0, max_meta = 0, max_wait = 0;  // largest counts over the tiles
     int64_t smem_cache[4][2][2] = {};    // tile_smem_bytes by (mode, VD == 3, FP64), 0: not yet computed
     int32_t *d_hdr = nullptr, *d_foot = nullptr, *d_tri_perm = nullptr, *d_tri_verts = nullptr;
     uint16_t *d_unit = nullptr, *d_unit_dst = nullptr, *d_slot_dst = nullptr;
     unsigned char *d_meta = nullptr;
     int64_t *d_meta_off = nullptr;
-    int32_t *d_grp = nullptr, *d_grp_items = nullptr;
     int32_t *d_zero_verts = nullptr, *d_zero_blocks = nullptr, *d_mesh_tile_off = nullptr;
-    int32_t *d_sync = nullptr;           // [0]: next tile of the persistent loop, [1..]: group counters
-    void *d_partials[2] = {nullptr, nullptr};  // per precision
+    int32_t *d_sync = nullptr;           // [0, 8): work-queue positions; [8, 8 + n_tiles): round progress
     void *d_tri_rest[2] = {nullptr, nullptr};  // per precision, SoA 5 x units
     void *d_slot_rest[2] = {nullptr, nullptr}; // per precision, SoA 2 x slots
     void *d_vterm_rest[2] = {nullptr, nullptr};
@@ -165,21 +159,20 @@ struct TileSet {
 };
 // tile header words
 enum TileHdr {
-    kHdrUnit = 0, kHdrNUnit, kHdrSlot, kHdrNSlot, kHdrFoot, kHdrNF, kHdrNVC, kHdrNPC, kHdrNCode, kHdrNShared,
-    kHdrNGroup, kHdrCodeOff, kHdrDstOff, kHdrGrpOff, kHdrVTerm, kHdrNVTerm, kHdrNSharedRows, kHdr = 20
+    kHdrUnit = 0, kHdrNUnit, kHdrSlot, kHdrNSlot, kHdrFoot, kHdrNF, kHdrNVC, kHdrNPC, kHdrNCode, kHdrNWait,
+    kHdrCodeOff, kHdrWaitOff, kHdrVTerm, kHdrNVTerm, kHdrRounds, kHdr = 16
 };
-// footprint row words: [0] BSR start of the row | shared << 31 (its gradient
-// and diagonal block are shared), [1] first code (within the tile) | number
-// of codes << 16 | number of vertex chunks << 24, [2] first vertex chunk |
-// the row's shared-output ordinal << 16 (shared rows come first, in row
-// order), [3] position of the diagonal block in the BSR row | number of
-// shared codes in earlier rows << 16 (shared codes follow the shared rows,
-// in code order).
+// An output several tiles produce has a rank in each of them: its position
+// in the ascending set of those tiles.  Rank 0 stores it; rank r > 0 adds to
+// it in round r, after the lower tiles have finished round r - 1.
+// footprint row words: [0] BSR start of the row, [1] first code (within the
+// tile) | number of codes << 16 | number of vertex chunks << 24, [2] first
+// vertex chunk, [3] position of the diagonal block in the BSR row | rank of
+// the row (gradient and diagonal block) << 16.
 // code (one per pair block the tile produces): pair-chunk segment start
-// (15 bits) | its chunk count << 15 (5 bits) | transposed << 20 | shared << 21 |
-// position in the BSR row << 22 (10 bits)
+// (15 bits) | its chunk count << 15 (4 bits) | transposed << 19 | rank << 20
+// (3 bits) | position in the BSR row << 23 (9 bits)
 constexpr int kRowWords = 4;
-constexpr int kGrpWords = 8;   // group: partial base, stride, tiles, rows, blocks, items offset, -, -
 
 // vertex-pair interaction terms and the block pattern they extend (dyn.cu;
 // Sec. 4.3, Sec. 6.3, Alg. 1)

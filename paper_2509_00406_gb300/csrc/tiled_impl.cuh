@@ -3,9 +3,10 @@
 // from a queue, evaluate them with per-element forward mode, stage every
 // contribution in shared memory sorted by the output it adds to, and write
 // each BSR entry, gradient and H v entry as the fixed-order sum of one
-// contiguous segment.  No float atomics anywhere: outputs that several tiles
-// produce go through partial slots that the last tile of their group sums in
-// tile order, so two passes on the same input give bit-identical results.
+// contiguous segment.  No float atomics anywhere: an output that several
+// tiles produce is stored by the lowest-index one and added to by the others
+// in tile order (each waits, bounded, for the lower tiles' done flags), so
+// two passes on the same input give bit-identical results.
 #pragma once
 
 #include "device_common.cuh"
@@ -29,11 +30,8 @@ struct TiledArgs {
     T *grad, *bsr;
     const T *v;                       // matrix-free mode: direction
     T *hv;                            // matrix-free mode: H v
-    T *partials;                      // shared outputs, per group and tile
     int32_t *next;                    // work queue position of this launch
-    int32_t *counters;                // per group: tiles finished
-    const int32_t *grp, *grp_items;
-    const int32_t *row_ptr;           // the pattern written (mesh or contact-extended)
+    int32_t *done;                    // per tile: rounds finished (cleared every pass; 255 = all)
     int32_t tile_begin, tile_end;     // this launch's tiles
     double *epart;                    // per tile
     int *status;
@@ -206,26 +204,28 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
-// fixed-order sum of a shared output's kt partials (stride apart), loads
-// issued four at a time
-template <typename T>
-__device__ __forceinline__ T sum_partials(const T *p, int64_t stride, int kt)
+// a tile's round progress (rounds finished), acquire load at GPU scope
+__device__ __forceinline__ int progress_acquire(const int32_t *p)
 {
-    T acc = -T(0);
-    for (int q0 = 0; q0 < kt; q0 += 4) {
-        T v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = q0 + i < kt ? __ldcg(p + (q0 + i) * stride) : T(0);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (q0 + i < kt) acc += v[i];
-    }
-    return acc;
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__device__ __forceinline__ void discard_l2_line(const void *p)
+// wait until a lower tile has finished `rounds` rounds; gives up after about
+// a second (2^22 polls about 250 ns apart) and returns false
+__device__ __forceinline__ bool wait_progress(const int32_t *p, int rounds)
 {
-    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (progress_acquire(p) >= rounds) return true;
+        __nanosleep(256);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void progress_release(int32_t *p, int rounds)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(rounds) : "memory");
 }
 
 // ------------------------------------------------------------- kernel --
@@ -234,7 +234,6 @@ __device__ __forceinline__ void discard_l2_line(const void *p)
 // FP64 and filtered tiles one block of 256 with the full register file
 template <typename T, bool PROJ, int THREADS>
 constexpr int tile_min_blocks() { return (sizeof(T) == 4 && !PROJ) ? 512 / THREADS : 1; }
-constexpr int kMaxGroups = 64;   // groups of a tile whose counters are taken per round
 
 template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS, bool PROJ>
 __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())) k_tiled(TiledArgs<T> A)
@@ -244,8 +243,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
     constexpr bool CLOTH = ENERGY == ADM_MASS_SPRING;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t meta_bar;
-    __shared__ int s_tile, s_nlast;
-    __shared__ int s_last[kMaxGroups], s_eoff[kMaxGroups + 1];
+    __shared__ int s_tile;
     const int tid = threadIdx.x;
     T *xs = reinterpret_cast<T *>(smem_raw);
     if (MODE >= MODE_GRAD && tid == 0) bar_init(&meta_bar);
@@ -495,14 +493,26 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
         }
         const int32_t *rows = reinterpret_cast<const int32_t *>(blob);
         const uint32_t *codes = reinterpret_cast<const uint32_t *>(blob + hd[kHdrCodeOff]);
-        const int32_t *pdst = reinterpret_cast<const int32_t *>(blob + hd[kHdrDstOff]);
-        if (MODE >= MODE_GRAD && meta_ok) {
+        // Round r writes the outputs of rank r: rank 0 stores, rank r > 0 adds
+        // to what the r lower tiles of that output wrote, after every lower
+        // tile this one shares outputs with has finished round r - 1
+        const int rounds = MODE >= MODE_GRAD && meta_ok ? hd[kHdrRounds] : 0;
+        const int nw = hd[kHdrNWait];
+        const int32_t *wl = reinterpret_cast<const int32_t *>(blob + hd[kHdrWaitOff]);
+        for (int rnd = 0; rnd < rounds; ++rnd) {
+            const bool add = rnd > 0;
+            if (add) {
+                for (int i = tid; i < nw; i += THREADS)
+                    if (!wait_progress(A.done + wl[i], rnd)) atomicOr(A.status, ST_TIMEOUT);
+                __syncthreads();
+            }
             // vertex pass: one lane per footprint row sums the row's vertex
             // chunks (gradient and diagonal upper entries, or gradient and
             // H v) in registers and writes its gradient (H v) row and
-            // diagonal block, or the row's partial slot when it is shared
+            // diagonal block
             for (int r = tid; r < nf; r += THREADS) {
                 const int4 rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
+                if ((rw.w >> 16) != rnd) continue;
                 const int nv = (int)((uint32_t)rw.y >> 24), vs0 = rw.z & 0xffff;
                 T acc[CV > 0 ? CV : 1];
 #pragma unroll
@@ -512,62 +522,44 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
 #pragma unroll
                     for (int e = 0; e < CV; ++e) acc[e] += src[CV * q + e];
                 const int64_t vg = A.foot[fb + r];
-                if (rw.x < 0) {  // shared row: gradient (H v) and diagonal into its partial slot
-                    T *pd = A.partials + pdst[(uint32_t)rw.z >> 16];
-                    if constexpr (MODE == MODE_HESS) {
+                if (A.grad) {
+                    T *g = A.grad + vg * VD;
 #pragma unroll
-                        for (int d = 0; d < VD; ++d) pd[d] = acc[d];
+                    for (int d = 0; d < VD; ++d) g[d] = add ? __ldcg(g + d) + acc[d] : acc[d];
+                }
+                if constexpr (MODE == MODE_HVP) {
+                    T *y = A.hv + vg * VD;
 #pragma unroll
-                        for (int i = 0; i < VD; ++i)
+                    for (int d = 0; d < VD; ++d) y[d] = add ? __ldcg(y + d) + acc[VD + d] : acc[VD + d];
+                }
+                if constexpr (MODE == MODE_HESS) {
+                    T *out = A.bsr + ((int64_t)rw.x + (rw.w & 0xffff)) * (VD * VD);
 #pragma unroll
-                            for (int j = 0; j < VD; ++j) pd[VD + i * VD + j] = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
-                    } else {
+                    for (int i = 0; i < VD; ++i)
 #pragma unroll
-                        for (int e = 0; e < CV; ++e) pd[e] = acc[e];
-                    }
-                } else {
-                    if (A.grad)
-#pragma unroll
-                        for (int d = 0; d < VD; ++d) A.grad[vg * VD + d] = acc[d];
-                    if constexpr (MODE == MODE_HVP) {
-#pragma unroll
-                        for (int d = 0; d < VD; ++d) A.hv[vg * VD + d] = acc[VD + d];
-                    }
-                    if constexpr (MODE == MODE_HESS) {
-                        T *out = A.bsr + ((int64_t)(rw.x & 0x7fffffff) + (rw.w & 0xffff)) * (VD * VD);
-#pragma unroll
-                        for (int i = 0; i < VD; ++i)
-#pragma unroll
-                            for (int j = 0; j < VD; ++j) out[i * VD + j] = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
-                    }
+                        for (int j = 0; j < VD; ++j) {
+                            const T val = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
+                            out[i * VD + j] = add ? __ldcg(out + i * VD + j) + val : val;
+                        }
                 }
             }
-        }
-        if (MODE == MODE_HESS && meta_ok) {
-            // pair pass: a half-warp per footprint row, one lane per pair
-            // block of the row; the lane sums the block's segment in chunk
-            // order and transposes once if the row is the higher index
-            constexpr int NB = VD * VD;
-            const int lane = tid & 31, half = lane >> 4, hl16 = lane & 15;
-            const int n_rows_pass = (nf + 1) / 2;
-            const int nsr = hd[kHdrNSharedRows];
-            for (int rr = tid >> 5; rr < n_rows_pass; rr += THREADS / 32) {
-                const int r = 2 * rr + half;
-                int4 rw = make_int4(0, 0, 0, 0);
-                if (r < nf) rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
-                const int c0 = rw.y & 0xffff, nc = r < nf ? (rw.y >> 16) & 0xff : 0;
-                const int64_t rs = rw.x & 0x7fffffff;
-                int ord = nsr + (int)((uint32_t)rw.w >> 16);  // ordinal of the row's first shared code
-                const int nmax = max(nc, __shfl_xor_sync(0xffffffffu, nc, 16));
-                for (int j0 = 0; j0 < nmax; j0 += 16) {
-                    const int j = j0 + hl16;
-                    const bool act = j < nc;
-                    const uint32_t code = act ? codes[c0 + j] : 0u;
-                    const bool sh = ((code >> 21) & 1u) != 0;
-                    const uint32_t m = __ballot_sync(0xffffffffu, act && sh);
-                    const uint32_t mine = (m >> (16 * half)) & 0xffffu;
-                    if (act) {
-                        const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 31u);
+            if constexpr (MODE == MODE_HESS) {
+                // pair pass: a half-warp per footprint row, one lane per pair
+                // block of the row; the lane sums the block's segment in chunk
+                // order and transposes once if the row is the higher index
+                constexpr int NB = VD * VD;
+                const int lane = tid & 31, half = lane >> 4, hl16 = lane & 15;
+                const int n_rows_pass = (nf + 1) / 2;
+                for (int rr = tid >> 5; rr < n_rows_pass; rr += THREADS / 32) {
+                    const int r = 2 * rr + half;
+                    int4 rw = make_int4(0, 0, 0, 0);
+                    if (r < nf) rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
+                    const int c0 = rw.y & 0xffff, nc = r < nf ? (rw.y >> 16) & 0xff : 0;
+                    const int64_t rs = rw.x;
+                    for (int j = hl16; j < nc; j += 16) {
+                        const uint32_t code = codes[c0 + j];
+                        if ((int)((code >> 20) & 7u) != rnd) continue;
+                        const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 15u);
                         T acc[NB];
 #pragma unroll
                         for (int k = 0; k < NB; ++k) acc[k] = -T(0);
@@ -575,7 +567,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                         for (int q = 0; q < cnt; ++q)
 #pragma unroll
                             for (int k = 0; k < NB; ++k) acc[k] += src[CP * q + k];
-                        if ((code >> 20) & 1u)
+                        if ((code >> 19) & 1u)
 #pragma unroll
                             for (int i = 0; i < VD; ++i)
 #pragma unroll
@@ -584,89 +576,32 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                                     acc[i * VD + k] = acc[k * VD + i];
                                     acc[k * VD + i] = tmp;
                                 }
-                        T *out = sh ? A.partials + pdst[ord + __popc(mine & ((1u << hl16) - 1u))]
-                                    : A.bsr + (rs + (int64_t)(code >> 22)) * NB;
+                        T *out = A.bsr + (rs + (int64_t)(code >> 23)) * NB;
+                        if (add) {
 #pragma unroll
-                        for (int k = 0; k < NB; ++k) out[k] = acc[k];
+                            for (int k = 0; k < NB; ++k) out[k] = __ldcg(out + k) + acc[k];
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < NB; ++k) out[k] = acc[k];
+                        }
                     }
-                    ord += __popc(mine);
                 }
+            }
+            // release round rnd to the higher tiles (the last round's release
+            // comes with the tile's end)
+            if (rnd + 1 < rounds) {
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) progress_release(A.done + t, rnd + 1);
             }
         }
         const double sum = block_sum<THREADS>(fe);
         if (tid == 0) A.epart[t] = sum;
-
-        // ---- shared outputs: the last tile of each group sums the partials
-        // of all the groups it finishes in one flat pass over their entries
-        // (the tile's groups in rounds of kMaxGroups)
-        const int ng = hd[kHdrNGroup];
-        if (MODE >= MODE_GRAD && meta_ok && ng > 0) {
-            const int32_t *groups = reinterpret_cast<const int32_t *>(blob + hd[kHdrGrpOff]);
-            constexpr int RE = MODE == MODE_HESS ? VD + VD * VD : (MODE == MODE_HVP ? 2 * VD : VD);
-            constexpr int BE = MODE == MODE_HESS ? VD * VD : 0;
-            __threadfence();  // release: this thread's partials before any counter moves
+        // ---- this tile's outputs are all written: release every round
+        if (MODE >= MODE_GRAD) {
+            __threadfence();
             __syncthreads();
-            for (int g0 = 0; g0 < ng; g0 += kMaxGroups) {
-                if (tid == 0) s_nlast = 0;
-                __syncthreads();
-                for (int i = g0 + tid; i < min(ng, g0 + kMaxGroups); i += THREADS) {
-                    const int g = groups[i];
-                    const int kt = A.grp[kGrpWords * (int64_t)g + 2];
-                    if (atomicAdd(A.counters + g, 1) == kt - 1) {
-                        __threadfence();  // acquire: the other tiles' partials are visible
-                        s_last[atomicAdd(&s_nlast, 1)] = g;
-                    }
-                }
-                __syncthreads();
-                const int nl = s_nlast;
-                if (nl == 0) continue;
-                // entry offsets of the finished groups (rows RE entries, blocks BE)
-                if (tid == 0) {
-                    int acc = 0;
-                    for (int j = 0; j < nl; ++j) {
-                        s_eoff[j] = acc;
-                        const int32_t *gh = A.grp + kGrpWords * (int64_t)s_last[j];
-                        acc += gh[3] * RE + gh[4] * BE;
-                    }
-                    s_eoff[nl] = acc;
-                }
-                __syncthreads();
-                const int ne = s_eoff[nl];
-                for (int i = tid; i < ne; i += THREADS) {
-                    int j = 0;
-                    while (j + 1 < nl && s_eoff[j + 1] <= i) ++j;
-                    const int32_t *gh = A.grp + kGrpWords * (int64_t)s_last[j];
-                    const int64_t base = gh[0], stride = gh[1];
-                    const int kt = gh[2], nr = gh[3];
-                    const int32_t *items = A.grp_items + gh[5];
-                    const int li = i - s_eoff[j];
-                    if (li < nr * RE) {
-                        const int it = li / RE, e = li - it * RE;
-                        const T acc = sum_partials(A.partials + base + 12 * it + e, stride, kt);
-                        const int64_t v = items[2 * it];
-                        if (e < VD) {
-                            if (A.grad) A.grad[v * VD + e] = acc;
-                        } else if (MODE == MODE_HVP) {
-                            A.hv[v * VD + e - VD] = acc;
-                        } else {
-                            A.bsr[((int64_t)A.row_ptr[v] + items[2 * it + 1]) * (VD * VD) + e - VD] = acc;
-                        }
-                    } else if constexpr (BE > 0) {
-                        const int bi = li - nr * RE, it = bi / BE, e = bi - it * BE;
-                        const T acc = sum_partials(A.partials + base + 12 * nr + 9 * it + e, stride, kt);
-                        const int64_t v = items[2 * nr + 2 * it];
-                        A.bsr[((int64_t)A.row_ptr[v] + items[2 * nr + 2 * it + 1]) * (VD * VD) + e] = acc;
-                    }
-                }
-                __syncthreads();
-                // the partial lines are dead: drop them from L2 without a write-back
-                for (int j = 0; j < nl; ++j) {
-                    const int32_t *gh = A.grp + kGrpWords * (int64_t)s_last[j];
-                    const int64_t lines = (int64_t)gh[2] * gh[1] * (int64_t)sizeof(T) / 128;
-                    const char *p0 = reinterpret_cast<const char *>(A.partials + gh[0]);
-                    for (int64_t i = tid; i < lines; i += THREADS) discard_l2_line(p0 + 128 * i);
-                }
-            }
+            if (tid == 0) progress_release(A.done + t, 255);
         }
         __syncthreads();
     }
@@ -775,8 +710,8 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     const bool pairs = h->inter.kind == kind && h->inter.n_terms() > 0;
     if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
     if (a.energy == ADM_MASS_SPRING && (!ts.cloth_built || !h->d_xhat[a.prec])) return ADM_ERR_UNSUPPORTED;
-    // queue positions and group counters start at zero every pass
-    const int64_t n_sync = 8 + ts.n_groups;
+    // queue positions and done flags start at zero every pass
+    const int64_t n_sync = 8 + ts.n_tiles;
     if (cudaMemsetAsync(ts.d_sync, 0, n_sync * sizeof(int32_t), s) != cudaSuccess) return ADM_ERR_CUDA;
     TiledArgs<T> A;
     A.hdr = ts.d_hdr;
@@ -796,11 +731,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     A.bsr = (T *)a.bsr;
     A.v = (const T *)a.v;
     A.hv = (T *)a.hv;
-    A.partials = (T *)ts.d_partials[a.prec];
-    A.counters = ts.d_sync + 8;
-    A.grp = ts.d_grp;
-    A.grp_items = ts.d_grp_items;
-    A.row_ptr = (pairs && h->inter.d_rp[h->inter.active]) ? h->inter.d_rp[h->inter.active] : h->pat[kind].d_row_ptr;
+    A.done = ts.d_sync + 8;
     A.epart = h->d_epart;
     A.status = h->d_status;
     A.c = consts<T>(h, a.energy);

@@ -328,9 +328,10 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         std::vector<uint32_t> codes;
         std::vector<uint64_t> pair_keys;            // produced unordered pairs (global key)
         int64_t nvc = 0, npc = 0;
+        int32_t rounds = 1;                         // 1 + the highest rank of its shared outputs
     };
     std::vector<TileOut> T(n_tiles);
-    const int64_t maxrow = 1024;
+    const int64_t maxrow = 512;
     parallel_for(n_tiles, nthr, [&](int64_t t, unsigned th) {
         TileOut &o = T[t];
         Scratch &w = scr[th];
@@ -453,9 +454,9 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
                 if (lc < 0) continue;
                 const auto *ps = find_pseg(r, lc);
                 if (!ps) continue;
-                if ((*ps)[2] >= 32768 || (*ps)[3] >= 32) fail = ADM_ERR_UNSUPPORTED;
-                o.codes.push_back((uint32_t)(*ps)[2] | (uint32_t)(*ps)[3] << 15 | (uint32_t)(r > lc) << 20 |
-                                  (uint32_t)(b - b0) << 22);
+                if ((*ps)[2] >= 32768 || (*ps)[3] >= 16) fail = ADM_ERR_UNSUPPORTED;
+                o.codes.push_back((uint32_t)(*ps)[2] | (uint32_t)(*ps)[3] << 15 | (uint32_t)(r > lc) << 19 |
+                                  (uint32_t)(b - b0) << 23);
             }
             const uint32_t ncode = (uint32_t)o.codes.size() - code0;
             if (diag < 0 || ncode > 255 || vseg_n[r] > 255 || vseg_n[r] == 0) fail = ADM_ERR_MESH;
@@ -469,29 +470,15 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     });
     if (fail) return (adm_status)fail.load();
 
-    // ---- outputs shared between tiles: rows (vertex in several footprints)
-    // and pair blocks (pair produced by several tiles); groups by tile set
-    // (tile sets never span meshes, so meshes are handled in parallel)
-    struct MeshGroups {
-        std::map<std::vector<int32_t>, int32_t> gid;
-        std::vector<std::vector<int32_t>> sets;
-        std::vector<std::vector<std::array<int32_t, 2>>> rows, blocks;  // items
-        // lookups: shared vertex -> (group, item), shared pair key -> (group, item of (a,b), item of (b,a))
-        std::vector<std::pair<int32_t, std::array<int32_t, 2>>> vmap;
-        std::vector<std::pair<uint64_t, std::array<int32_t, 3>>> pmap;
-    };
-    std::vector<MeshGroups> MG(m.n_mesh);
-    auto diag_pos = [&](int32_t v) {
-        return (int32_t)(std::lower_bound(P.col.begin() + P.row_ptr[v], P.col.begin() + P.row_ptr[v + 1], v) -
-                         (P.col.begin() + P.row_ptr[v]));
-    };
-    auto col_pos = [&](int32_t v, int32_t c) {
-        const auto b = P.col.begin() + P.row_ptr[v], e = P.col.begin() + P.row_ptr[v + 1];
-        // mesh columns ascend within a row
-        return (int32_t)(std::lower_bound(b, e, c) - b);
-    };
+    // ---- outputs several tiles produce: rows (a vertex in several
+    // footprints) and pair blocks (a pair produced by several tiles).  The
+    // lowest-index tile of such an output stores its part; every other one
+    // waits for the lower tiles it shares outputs with and adds its part to
+    // what is there, so the sum runs in tile order.  Tile sets never span
+    // meshes, so meshes are handled in parallel.
+    std::vector<std::vector<int32_t>> waits(n_tiles);
+    std::atomic<int> fail_rank(0);
     parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned) {
-        MeshGroups &G = MG[k];
         const int32_t t0 = ts.mesh_tile_off[k], t1 = ts.mesh_tile_off[k + 1];
         std::vector<std::pair<int32_t, int32_t>> vt;
         std::vector<std::pair<uint64_t, int32_t>> pt;
@@ -501,131 +488,67 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         }
         std::sort(vt.begin(), vt.end());
         std::sort(pt.begin(), pt.end());
-        auto group_of = [&](std::vector<int32_t> &&set) {
-            auto it = G.gid.find(set);
-            if (it != G.gid.end()) return it->second;
-            const int32_t g = (int32_t)G.sets.size();
-            G.gid.emplace(set, g);
-            G.sets.push_back(std::move(set));
-            G.rows.emplace_back();
-            G.blocks.emplace_back();
-            return g;
+        // rank of every tile in the (ascending) tile set of each shared vertex
+        // and pair, and the wait edges (tile, lower tile)
+        std::vector<std::array<int64_t, 3>> vrank, prank;  // (key, tile, rank)
+        std::vector<std::pair<int32_t, int32_t>> edges;
+        auto add_set = [&](auto begin, auto end, std::vector<std::array<int64_t, 3>> &out) {
+            int64_t rk = 0;
+            for (auto a = begin; a != end; ++a, ++rk) {
+                out.push_back({(int64_t)a->first, (int64_t)a->second, rk});
+                for (auto b = begin; b != a; ++b) edges.emplace_back(a->second, b->second);
+            }
         };
         for (size_t i = 0; i < vt.size();) {
             size_t j = i;
             while (j < vt.size() && vt[j].first == vt[i].first) ++j;
-            if (j - i > 1) {
-                std::vector<int32_t> set;
-                for (size_t q = i; q < j; ++q) set.push_back(vt[q].second);
-                const int32_t g = group_of(std::move(set));
-                const int32_t v = vt[i].first;
-                G.vmap.push_back({v, {g, (int32_t)G.rows[g].size()}});
-                G.rows[g].push_back({v, diag_pos(v)});
-            }
+            if (j - i > 1) add_set(vt.begin() + i, vt.begin() + j, vrank);
             i = j;
         }
         for (size_t i = 0; i < pt.size();) {
             size_t j = i;
             while (j < pt.size() && pt[j].first == pt[i].first) ++j;
-            if (j - i > 1) {
-                std::vector<int32_t> set;
-                for (size_t q = i; q < j; ++q) set.push_back(pt[q].second);
-                const int32_t g = group_of(std::move(set));
-                const int32_t a = (int32_t)(pt[i].first / (uint64_t)nV), b = (int32_t)(pt[i].first % (uint64_t)nV);
-                const int32_t ia = (int32_t)G.blocks[g].size();
-                G.blocks[g].push_back({a, col_pos(a, b)});
-                G.blocks[g].push_back({b, col_pos(b, a)});
-                G.pmap.push_back({pt[i].first, {g, ia, ia + 1}});
-            }
+            if (j - i > 1) add_set(pt.begin() + i, pt.begin() + j, prank);
             i = j;
         }
-    });
-    // global group numbering and partial layout (each tile's region of a
-    // group aligned to 32 floats; rows 12 floats, blocks 9)
-    std::vector<int64_t> mesh_g0(m.n_mesh + 1, 0);
-    for (int k = 0; k < m.n_mesh; ++k) mesh_g0[k + 1] = mesh_g0[k] + (int64_t)MG[k].sets.size();
-    ts.n_groups = mesh_g0[m.n_mesh];
-    ts.grp.assign((size_t)kGrpWords * ts.n_groups, 0);
-    {
-        int64_t base = 0, items = 0;
-        for (int k = 0; k < m.n_mesh; ++k) {
-            const MeshGroups &G = MG[k];
-            for (size_t g = 0; g < G.sets.size(); ++g) {
-                int32_t *h = &ts.grp[(size_t)kGrpWords * (mesh_g0[k] + g)];
-                const int64_t nr = (int64_t)G.rows[g].size(), nb = (int64_t)G.blocks[g].size();
-                const int64_t stride = (12 * nr + 9 * nb + 31) & ~int64_t(31);
-                if (base + stride * (int64_t)G.sets[g].size() > (int64_t)INT32_MAX) return ADM_ERR_UNSUPPORTED;
-                h[0] = (int32_t)base;
-                h[1] = (int32_t)stride;
-                h[2] = (int32_t)G.sets[g].size();
-                h[3] = (int32_t)nr;
-                h[4] = (int32_t)nb;
-                h[5] = (int32_t)items;
-                base += stride * (int64_t)G.sets[g].size();
-                for (auto &r : G.rows[g]) ts.grp_items.insert(ts.grp_items.end(), r.begin(), r.end());
-                for (auto &b : G.blocks[g]) ts.grp_items.insert(ts.grp_items.end(), b.begin(), b.end());
-                items += 2 * (nr + nb);
+        std::sort(edges.begin(), edges.end());
+        edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+        for (auto &e : edges) waits[e.first].push_back(e.second);
+        auto rank_of = [](const std::vector<std::array<int64_t, 3>> &rk, int64_t key, int64_t t) -> int64_t {
+            auto it = std::lower_bound(rk.begin(), rk.end(), std::array<int64_t, 3>{key, t, INT64_MIN});
+            return (it != rk.end() && (*it)[0] == key && (*it)[1] == t) ? (*it)[2] : 0;
+        };
+        // per tile, the rank of each output it produces: 0 stores, r > 0
+        // adds in round r
+        for (int32_t t = t0; t < t1; ++t) {
+            TileOut &o = T[t];
+            const int32_t nf = (int32_t)o.foot.size();
+            int64_t rmax = 0;
+            for (int32_t r = 0; r < nf; ++r) {
+                int32_t *row = &o.rows[(size_t)kRowWords * r];
+                const int32_t v = o.foot[r];
+                const int64_t rv = rank_of(vrank, v, t);
+                if (rv > 7) fail_rank = 1;
+                rmax = std::max(rmax, rv);
+                row[3] |= (int32_t)(rv << 16);
+                const uint32_t c0 = (uint32_t)row[1] & 0xffffu, nc = ((uint32_t)row[1] >> 16) & 0xffu;
+                for (uint32_t c = c0; c < c0 + nc; ++c) {
+                    const int32_t col = P.col[P.row_ptr[v] + (o.codes[c] >> 23)];
+                    const int64_t rp = rank_of(prank, (int64_t)pkey(v, col, nV), t);
+                    if (rp > 7) fail_rank = 1;
+                    rmax = std::max(rmax, rp);
+                    o.codes[c] |= (uint32_t)(rp & 7) << 20;
+                }
             }
+            o.rounds = (int32_t)rmax + 1;
         }
-        ts.partial_floats = base;
+    });
+    if (fail_rank) {
+        // an output shared by more than 8 tiles (ranks have 3 bits): larger tiles
+        if (tile_units >= 4096) return ADM_ERR_UNSUPPORTED;
+        return tiles_build(m, P, with_hinges, 2 * tile_units, ts);
     }
-    for (auto &G : MG) {
-        std::sort(G.vmap.begin(), G.vmap.end());
-        std::sort(G.pmap.begin(), G.pmap.end());
-    }
-
-    // ---- per tile: shared flags, shared-output destinations, groups; blobs
     ts.hdr.assign((size_t)kHdr * n_tiles, 0);
-    std::vector<std::vector<int32_t>> dst(n_tiles), grps(n_tiles);
-    parallel_for(n_tiles, nthr, [&](int64_t t, unsigned) {
-        TileOut &o = T[t];
-        const int k = tile_mesh[t];
-        const MeshGroups &G = MG[k];
-        auto rank_in = [&](int32_t g) {
-            const auto &set = G.sets[g];
-            return (int32_t)(std::lower_bound(set.begin(), set.end(), (int32_t)t) - set.begin());
-        };
-        auto pdst = [&](int32_t g, int32_t item, bool row) {
-            const int32_t *h = &ts.grp[(size_t)kGrpWords * (mesh_g0[k] + g)];
-            const int64_t off = row ? 12 * (int64_t)item : 12 * (int64_t)h[3] + 9 * (int64_t)item;
-            return (int32_t)(h[0] + (int64_t)rank_in(g) * h[1] + off);
-        };
-        const int32_t nf = (int32_t)o.foot.size();
-        std::vector<int32_t> gl, code_dst;
-        int32_t n_shared_codes = 0;
-        for (int32_t r = 0; r < nf; ++r) {
-            int32_t *row = &o.rows[(size_t)kRowWords * r];
-            const int32_t v = o.foot[r];
-            row[3] |= (int32_t)((uint32_t)n_shared_codes << 16);
-            auto it = std::lower_bound(G.vmap.begin(), G.vmap.end(), std::make_pair(v, std::array<int32_t, 2>{INT32_MIN, 0}));
-            if (it != G.vmap.end() && it->first == v) {
-                row[0] = (int32_t)((uint32_t)row[0] | 0x80000000u);
-                row[2] |= (int32_t)((uint32_t)dst[t].size() << 16);
-                dst[t].push_back(pdst(it->second[0], it->second[1], true));
-                gl.push_back(it->second[0]);
-            }
-            const uint32_t c0 = (uint32_t)row[1] & 0xffffu, nc = ((uint32_t)row[1] >> 16) & 0xffu;
-            for (uint32_t c = c0; c < c0 + nc; ++c) {
-                const uint32_t pos = o.codes[c] >> 22;
-                const int32_t col = P.col[P.row_ptr[v] + pos];
-                const uint64_t key = pkey(v, col, nV);
-                auto pit = std::lower_bound(G.pmap.begin(), G.pmap.end(),
-                                            std::make_pair(key, std::array<int32_t, 3>{INT32_MIN, 0, 0}));
-                if (pit == G.pmap.end() || pit->first != key) continue;
-                o.codes[c] |= 1u << 21;
-                code_dst.push_back(pdst(pit->second[0], v < col ? pit->second[1] : pit->second[2], false));
-                gl.push_back(pit->second[0]);
-                ++n_shared_codes;
-            }
-        }
-        ts.hdr[(size_t)kHdr * t + kHdrNSharedRows] = (int32_t)dst[t].size();
-        dst[t].insert(dst[t].end(), code_dst.begin(), code_dst.end());
-        std::sort(gl.begin(), gl.end());
-        gl.erase(std::unique(gl.begin(), gl.end()), gl.end());
-        for (int32_t g : gl) grps[t].push_back((int32_t)(mesh_g0[k] + g));
-        if (dst[t].size() >= 65536) fail = ADM_ERR_UNSUPPORTED;
-    });
-    if (fail) return (adm_status)fail.load();
 
     // ---- concatenate
     ts.meta_off.assign(n_tiles + 1, 0);
@@ -643,28 +566,26 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         hd[kHdrNVC] = (int32_t)o.nvc;
         hd[kHdrNPC] = (int32_t)o.npc;
         hd[kHdrNCode] = (int32_t)o.codes.size();
-        hd[kHdrNShared] = (int32_t)dst[t].size();
-        hd[kHdrNGroup] = (int32_t)grps[t].size();
+        hd[kHdrNWait] = (int32_t)waits[t].size();
+        hd[kHdrRounds] = o.rounds;
         const int64_t rows_b = 4 * (int64_t)kRowWords * nf;
         const int64_t codes_b = 4 * (int64_t)o.codes.size();
-        const int64_t dst_b = 4 * (int64_t)dst[t].size();
-        const int64_t grp_b = 4 * (int64_t)grps[t].size();
+        const int64_t wait_b = 4 * (int64_t)waits[t].size();
         hd[kHdrCodeOff] = (int32_t)rows_b;
-        hd[kHdrDstOff] = (int32_t)(rows_b + codes_b);
-        hd[kHdrGrpOff] = (int32_t)(rows_b + codes_b + dst_b);
-        const int64_t mb = align16(rows_b + codes_b + dst_b + grp_b);
+        hd[kHdrWaitOff] = (int32_t)(rows_b + codes_b);
+        const int64_t mb = align16(rows_b + codes_b + wait_b);
         const size_t m0 = ts.meta.size();
         ts.meta.resize(m0 + mb, 0);
         unsigned char *blob = ts.meta.data() + m0;
         std::memcpy(blob, o.rows.data(), rows_b);
         std::memcpy(blob + rows_b, o.codes.data(), codes_b);
-        std::memcpy(blob + rows_b + codes_b, dst[t].data(), dst_b);
-        std::memcpy(blob + rows_b + codes_b + dst_b, grps[t].data(), grp_b);
+        std::memcpy(blob + rows_b + codes_b, waits[t].data(), wait_b);
         ts.meta_off[t + 1] = (int64_t)ts.meta.size();
         ts.max_meta = std::max(ts.max_meta, mb);
         ts.max_nf = std::max<int64_t>(ts.max_nf, nf);
         ts.max_nvc = std::max(ts.max_nvc, o.nvc);
         ts.max_npc = std::max(ts.max_npc, o.npc);
+        ts.max_wait = std::max<int64_t>(ts.max_wait, (int64_t)waits[t].size());
         // unit data
         ts.foot.insert(ts.foot.end(), o.foot.begin(), o.foot.end());
         ts.unit.insert(ts.unit.end(), o.unit.begin(), o.unit.end());
@@ -700,7 +621,8 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         for (int64_t v = 0; v < nV; ++v)
             if (!seen[v]) {
                 ts.zero_verts.push_back((int32_t)v);
-                ts.zero_blocks.push_back(P.row_ptr[v] + diag_pos((int32_t)v));
+                const auto b = P.col.begin() + P.row_ptr[v], e = P.col.begin() + P.row_ptr[v + 1];
+                ts.zero_blocks.push_back((int32_t)(std::lower_bound(b, e, (int32_t)v) - P.col.begin()));
             }
     }
     static std::atomic<int64_t> builds(0);
