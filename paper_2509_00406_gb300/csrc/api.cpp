@@ -168,7 +168,7 @@ void free_tiles(adm_ctx *h, TileSet &ts)
 {
     void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_tri_perm, ts.d_tri_verts, ts.d_unit, ts.d_unit_dst, ts.d_slot_dst,
                     ts.d_meta, ts.d_meta_off, ts.d_zero_verts, ts.d_zero_blocks,
-                    ts.d_mesh_tile_off, ts.d_sync, ts.d_tri_rest[0],
+                    ts.d_mesh_tile_off, ts.d_sync, ts.d_fix_v, ts.d_fix_p, ts.d_vpart, ts.d_ppart, ts.d_tri_rest[0],
                     ts.d_tri_rest[1], ts.d_slot_rest[0], ts.d_slot_rest[1], ts.d_vterm_rest[0], ts.d_vterm_rest[1]};
     for (void *p : ptrs) dev_free(h, p);
     ts = TileSet();
@@ -205,7 +205,15 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
     if ((s = up(&ts.d_zero_verts, ts.zero_verts)) != ADM_OK) return s;
     if ((s = up(&ts.d_zero_blocks, ts.zero_blocks)) != ADM_OK) return s;
     if ((s = up(&ts.d_mesh_tile_off, ts.mesh_tile_off)) != ADM_OK) return s;
-    if ((s = dev_alloc(h, &ts.d_sync, (8 + (size_t)ts.n_tiles) * sizeof(int32_t))) != ADM_OK) return s;
+    if ((s = dev_alloc(h, &ts.d_sync, 8 * sizeof(int32_t))) != ADM_OK) return s;
+    if ((s = up(&ts.d_fix_v, ts.fix_v)) != ADM_OK) return s;
+    if ((s = up(&ts.d_fix_p, ts.fix_p)) != ADM_OK) return s;
+    {
+        // partial slots, sized for FP64 and the largest vertex chunk
+        const size_t cvh = h->m.vdim == 3 ? 9 : 5, nb = (size_t)h->m.vdim * h->m.vdim;
+        if ((s = dev_alloc(h, &ts.d_vpart, std::max<size_t>(16, ts.n_vpart * cvh * 8))) != ADM_OK) return s;
+        if ((s = dev_alloc(h, &ts.d_ppart, std::max<size_t>(16, ts.n_ppart * nb * 8))) != ADM_OK) return s;
+    }
     {
         const int64_t nU = (int64_t)ts.tri_perm.size();
         std::vector<std::vector<double>> f(5, std::vector<double>(nU));
@@ -521,12 +529,7 @@ adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
     }
 }
 
-// whether contact terms extend pattern `kind`, and the block count a pass on
-// it writes
-static bool pattern_extended(const adm_ctx *h, int kind)
-{
-    return h->inter.kind == kind && h->inter.d_rp[h->inter.active] != nullptr;
-}
+// the block count a pass on pattern `kind` writes
 static int64_t pass_nnzb(const adm_ctx *h, int kind)
 {
     return pattern_extended(h, kind) ? h->inter.nnzb : h->pat[kind].nnzb;

@@ -5,6 +5,7 @@
 // is made.
 #include <chrono>
 #include <cstring>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -34,13 +35,13 @@ extern "C" {
 // Builds hinges (if with_hinges), the block pattern and the tiles, and
 // reports, per block of the pattern, which tile produces it:
 //   block_writer[b] = tile id if exactly one tile produces it (written with a
-//   plain store), -2 if several do (the lowest stores, the others add in tile
-//   order), -1 if no tile does; block_adds[b] = number of tiles producing a
-//   shared block (0 otherwise).
-// stats: {n_tiles, wait edges (tile, lower tile), n_zero_verts, FP64
-// Hessian-mode shared-memory bytes (VD = 3), nnzb, nH, build_ms, most lower
-// tiles one tile waits for}.  Returns 0 or an
-// adm_status, or a negative code < -99 naming the check that failed.
+//   plain store), -2 if several do (the lowest stores, the others write
+//   partial slots that the fix-up adds in tile order), -1 if no tile does;
+//   block_adds[b] = number of tiles producing a shared block (0 otherwise).
+// stats: {n_tiles, partial slots (vertex + pair), n_zero_verts, FP64
+// Hessian-mode shared-memory bytes (VD = 3), nnzb, nH, build_ms, largest
+// slot table of a tile}.  Returns 0 or an adm_status, or a negative code
+// < -99 naming the check that failed.
 int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t nT, const int64_t *v_off,
                         const int64_t *f_off, int32_t n_mesh, int32_t with_hinges, int32_t tile_tris,
                         int32_t *block_writer, int32_t *block_adds, int64_t nnzb_cap, double *stats)
@@ -65,7 +66,33 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
     }
     std::vector<int32_t> producers(P.nnzb, 0);
     if ((int64_t)ts.meta_off.size() != ts.n_tiles + 1 || ts.meta_off.back() != (int64_t)ts.meta.size()) return -105;
-    int64_t n_wait_edges = 0;
+    // fix-up entries by output: vertex -> entry, block -> entry
+    if (ts.fix_v.size() % 4 || ts.fix_p.size() % 4) return -120;
+    std::unordered_map<int32_t, int64_t> fixv;
+    std::unordered_map<int64_t, int64_t> fixp;
+    for (size_t i = 0; i < ts.fix_v.size(); i += 4) {
+        const int32_t v = ts.fix_v[i];
+        if (v < 0 || v >= nV || P.col[P.row_ptr[v] + ts.fix_v[i + 1]] != v || !fixv.emplace(v, (int64_t)i).second)
+            return -120;
+    }
+    for (size_t i = 0; i < ts.fix_p.size(); i += 4) {
+        const int32_t v = ts.fix_p[i], pos = ts.fix_p[i + 1];
+        if (v < 0 || v >= nV || pos < 0 || P.row_ptr[v] + pos >= P.row_ptr[v + 1]) return -120;
+        if (!fixp.emplace((int64_t)P.row_ptr[v] + pos, (int64_t)i).second) return -120;
+    }
+    std::vector<int32_t> vslot_use(ts.n_vpart, 0), pslot_use(ts.n_ppart, 0);
+    std::vector<int32_t> pslot_block(ts.n_ppart, -1);  // pair slot -> its block
+    for (auto &f : fixp) {
+        const int32_t n = ts.fix_p[f.second + 2], first = ts.fix_p[f.second + 3];
+        if (n < 1 || first < 0 || first + n > ts.n_ppart) return -120;
+        for (int32_t q = first; q < first + n; ++q) {
+            if (pslot_block[q] >= 0) return -124;
+            pslot_block[q] = (int32_t)f.first;
+        }
+    }
+    for (size_t i = 0; i < ts.fix_v.size(); i += 4)
+        if (ts.fix_v[i + 2] < 1 || ts.fix_v[i + 3] < 0 || ts.fix_v[i + 3] + ts.fix_v[i + 2] > ts.n_vpart) return -120;
+    std::vector<int32_t> vprod(nV, 0);  // producers of each vertex row so far
     std::vector<std::vector<int32_t>> who(P.nnzb);  // producing tiles of each block, in order
     for (int32_t t = 0; t < ts.n_tiles; ++t) {
         const int32_t *hd = &ts.hdr[(size_t)kHdr * t];
@@ -101,17 +128,26 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             if (c != 1) return -112;
         for (int c : pw)
             if (c != 1) return -112;
-        // the tiles this one waits for are lower tiles
-        std::vector<int32_t> wl(hd[kHdrNWait]);
-        std::memcpy(wl.data(), blob + hd[kHdrWaitOff], 4 * wl.size());
-        for (int32_t w : wl)
-            if (w < 0 || w >= t) return -121;
-        n_wait_edges += (int64_t)wl.size();
-        auto waits_for = [&](int32_t u) { return std::find(wl.begin(), wl.end(), u) != wl.end(); };
+        // the tile's slot table: every entry is used by exactly one output
+        const int32_t npart = hd[kHdrNPart];
+        std::vector<int32_t> tab(npart);
+        std::memcpy(tab.data(), blob + hd[kHdrPartOff], 4 * tab.size());
+        std::vector<int> tab_use(npart, 0);
+        // a later producer's slot is slot (producers so far - 1) of its
+        // output's contiguous run; the lowest producer stores
+        auto check_slot = [&](bool part, int idx, int64_t fix_i, const std::vector<int32_t> &fix, int32_t prior,
+                              std::vector<int32_t> &use) -> int {
+            if (!part) return prior == 0 ? 0 : -115;
+            if (prior == 0 || fix_i < 0 || idx < 0 || idx >= npart) return -115;
+            tab_use[idx]++;
+            const int32_t n = fix[fix_i + 2], first = fix[fix_i + 3];
+            if (prior > n || tab[idx] != first + prior - 1) return -121;
+            use[tab[idx]]++;
+            return 0;
+        };
         // rows and codes: segments tile the chunk arrays; blocks produced
         int64_t vcov = 0;
         std::vector<int> pcov(npc, 0);
-        std::vector<std::pair<int32_t, int>> mine;  // blocks this tile produces, with their rank
         for (int32_t r = 0; r < nf; ++r) {
             int32_t w[kRowWords];
             std::memcpy(w, blob + 4 * kRowWords * r, sizeof w);
@@ -122,41 +158,70 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             const int vs0 = w[2] & 0xffff;
             if (vs0 != vcov) return -113;  // vertex segments in footprint order, back to back
             vcov += nv;
-            const int32_t bd = rs + (w[3] & 0xffff);
+            const int32_t bd = rs + (w[3] & 0x7fff);
             if (P.col[bd] != v) return -114;
-            mine.emplace_back(bd, w[3] >> 16);
+            {
+                auto it = fixv.find(v);
+                const int rc = check_slot((w[3] >> 15) & 1, w[3] >> 16, it == fixv.end() ? -1 : it->second, ts.fix_v,
+                                          vprod[v], vslot_use);
+                if (rc) return rc;
+                vprod[v]++;
+                who[bd].push_back(t);
+            }
             for (int c = c0; c < c0 + nc; ++c) {
                 uint32_t code;
                 std::memcpy(&code, blob + hd[kHdrCodeOff] + 4 * c, 4);
                 const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 15u);
-                const int tr = (int)((code >> 19) & 1u), rank = (int)((code >> 20) & 7u);
-                const int32_t b = rs + (int32_t)(code >> 23);
-                if (b >= P.row_ptr[v + 1] || P.col[b] == v) return -116;
+                const int tr = (int)((code >> 19) & 1u), part = (int)((code >> 20) & 1u);
+                // a partial block's position comes from its fix-up entry
+                int32_t b = -1;
+                if (!part) {
+                    b = rs + (int32_t)(code >> 21);
+                } else {
+                    const int idx = (int)(code >> 21);
+                    if (idx >= npart) return -115;
+                    if (tab[idx] < 0 || tab[idx] >= ts.n_ppart) return -121;
+                    b = pslot_block[tab[idx]];  // the entry whose slot run holds this slot
+                    if (b < 0) return -121;
+                }
+                if (b >= P.row_ptr[v + 1] || b < rs || P.col[b] == v) return -116;
                 const int32_t lc = (int32_t)(std::lower_bound(ts.foot.begin() + fb, ts.foot.begin() + fb + nf, P.col[b]) -
                                              (ts.foot.begin() + fb));
                 if (lc >= nf || ts.foot[fb + lc] != P.col[b] || tr != (r > lc ? 1 : 0)) return -117;
                 if (cnt == 0 || start + cnt > npc) return -118;
                 for (int q = start; q < start + cnt; ++q) pcov[q]++;
-                mine.emplace_back(b, rank);
+                auto it = fixp.find(b);
+                const int rc = check_slot(part, (int)(code >> 21), it == fixp.end() ? -1 : it->second, ts.fix_p,
+                                          producers[b], pslot_use);
+                if (rc) return rc;
+                producers[b]++;
+                who[b].push_back(t);
             }
         }
         if (vcov != nvc) return -113;
         for (int c : pcov)  // every pair chunk is summed by its two blocks, (a, b) and (b, a)
             if (c != 2) return -119;
-        // tiles are visited in order: a block of rank r in this tile has been
-        // produced by exactly r lower tiles, all in this tile's wait list
-        if (hd[kHdrRounds] < 1) return -123;
-        for (auto &bm : mine) {
-            const int32_t b = bm.first;
-            if (bm.second != producers[b]) return -115;
-            if (bm.second >= hd[kHdrRounds]) return -123;
-            if (bm.second > 0)
-                for (int32_t u : who[b])
-                    if (!waits_for(u)) return -122;
-            producers[b]++;
-            who[b].push_back(t);
-        }
+        for (int c : tab_use)
+            if (c != 1) return -122;
     }
+    // every fix-up entry lists exactly the later producers of its output,
+    // and every slot belongs to one output
+    for (size_t i = 0; i < ts.fix_v.size(); i += 4)
+        if (vprod[ts.fix_v[i]] != ts.fix_v[i + 2] + 1) return -123;
+    for (auto &f : fixp)
+        if (producers[f.first] != ts.fix_p[f.second + 2] + 1) return -123;
+    for (int32_t c : vslot_use)
+        if (c != 1) return -124;
+    for (int32_t c : pslot_use)
+        if (c != 1) return -124;
+    // outputs with several producers all have fix-up entries
+    for (int64_t v = 0; v < nV; ++v)
+        if (vprod[v] > 1 && !fixv.count((int32_t)v)) return -123;
+    for (int64_t b = 0; b < P.nnzb; ++b)
+        if (producers[b] > 1 && !fixp.count(b)) return -123;
+    for (int64_t v = 0; v < nV; ++v)  // the diagonal blocks: producers of the vertex row
+        for (int32_t b = P.row_ptr[v]; b < P.row_ptr[v + 1]; ++b)
+            if (P.col[b] == v) producers[b] = vprod[v];
     for (int64_t b = 0; b < P.nnzb; ++b) {
         if (producers[b] == 0) continue;
         block_writer[b] = producers[b] >= 2 ? -2 : who[b][0];
@@ -169,13 +234,13 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
         block_adds[b] = 2;
     }
     stats[0] = ts.n_tiles;
-    stats[1] = (double)n_wait_edges;
+    stats[1] = (double)(ts.n_vpart + ts.n_ppart);
     stats[2] = (double)ts.zero_verts.size();
     stats[3] = (double)tile_smem_bytes(ts, MODE_HESS, 3, 8);
     stats[4] = (double)P.nnzb;
     stats[5] = (double)m.nH();
     stats[6] = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    stats[7] = (double)ts.max_wait;
+    stats[7] = (double)ts.max_part;
     // every triangle is exactly one unit
     std::vector<char> seen_t(nT, 0);
     for (int32_t e : ts.tri_perm)

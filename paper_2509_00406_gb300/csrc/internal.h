@@ -110,9 +110,9 @@ struct ChunkTable {
 // pair, then unit order), so every output entry is the fixed-order sum of one
 // contiguous segment: the gather that writes the BSR rows is deterministic
 // and needs no atomics.  An output that several tiles produce (a "shared" row
-// or block) is stored by the lowest-index of them; each other one waits, with
-// a bounded wait, for the done flags of the lower tiles it shares outputs
-// with and adds its part to what is stored, so the sum runs in tile order.
+// or block) is stored by the lowest-index of them; each other one stores its
+// part in a partial slot of its own, and a fix-up pass adds the slots to the
+// output in tile order: no tile ever waits for another.
 struct TileSet {
     bool built = false;
     int64_t build_id = 0;                // distinct for every build (tiles_build)
@@ -138,20 +138,29 @@ struct TileSet {
     std::vector<int32_t> foot;           // footprint vertices (global ids), sorted, per tile
     std::vector<int32_t> mesh_tile_off;  // n_mesh + 1
     // per tile metadata blob (copied into shared memory): kRowWords int32
-    // per footprint row, one code per pair block produced, and the lower
-    // tiles the tile waits for
+    // per footprint row, one code per pair block produced, and the tile's
+    // partial slots (global slot indices)
     std::vector<unsigned char> meta;
     std::vector<int64_t> meta_off;       // n_tiles + 1
     std::vector<int32_t> zero_verts;     // vertices no unit touches (zero row and diagonal block)
     std::vector<int32_t> zero_blocks;    // their diagonal blocks
-    int64_t max_nvc = 0, max_npc = 0, max_nf = 0, max_meta = 0, max_wait = 0;  // largest counts over the tiles
+    int64_t max_nvc = 0, max_npc = 0, max_nf = 0, max_meta = 0, max_part = 0;  // largest counts over the tiles
+    // fix-up lists of the outputs several tiles produce, 4 int32 per output:
+    // row vertex, position of the block in its BSR row (the diagonal block
+    // for a vertex output), number of partial slots, first slot.  Vertex
+    // outputs (gradient row, diagonal block, H v row) sorted by vertex, pair
+    // blocks by block index; slots are allocated in the same order
+    std::vector<int32_t> fix_v, fix_p;
+    int64_t n_vpart = 0, n_ppart = 0;    // partial slots: vertex (Chunk<MODE_HESS> floats each), pair (VD^2)
+    int32_t *d_fix_v = nullptr, *d_fix_p = nullptr;
+    void *d_vpart = nullptr, *d_ppart = nullptr;  // partial slots, sized for FP64
     int64_t smem_cache[4][2][2] = {};    // tile_smem_bytes by (mode, VD == 3, FP64), 0: not yet computed
     int32_t *d_hdr = nullptr, *d_foot = nullptr, *d_tri_perm = nullptr, *d_tri_verts = nullptr;
     uint16_t *d_unit = nullptr, *d_unit_dst = nullptr, *d_slot_dst = nullptr;
     unsigned char *d_meta = nullptr;
     int64_t *d_meta_off = nullptr;
     int32_t *d_zero_verts = nullptr, *d_zero_blocks = nullptr, *d_mesh_tile_off = nullptr;
-    int32_t *d_sync = nullptr;           // [0, 8): work-queue positions; [8, 8 + n_tiles): round progress
+    int32_t *d_sync = nullptr;           // 8 work-queue positions
     void *d_tri_rest[2] = {nullptr, nullptr};  // per precision, SoA 5 x units
     void *d_slot_rest[2] = {nullptr, nullptr}; // per precision, SoA 2 x slots
     void *d_vterm_rest[2] = {nullptr, nullptr};
@@ -159,19 +168,19 @@ struct TileSet {
 };
 // tile header words
 enum TileHdr {
-    kHdrUnit = 0, kHdrNUnit, kHdrSlot, kHdrNSlot, kHdrFoot, kHdrNF, kHdrNVC, kHdrNPC, kHdrNCode, kHdrNWait,
-    kHdrCodeOff, kHdrWaitOff, kHdrVTerm, kHdrNVTerm, kHdrRounds, kHdr = 16
+    kHdrUnit = 0, kHdrNUnit, kHdrSlot, kHdrNSlot, kHdrFoot, kHdrNF, kHdrNVC, kHdrNPC, kHdrNCode, kHdrNPart,
+    kHdrCodeOff, kHdrPartOff, kHdrVTerm, kHdrNVTerm, kHdr = 16
 };
-// An output several tiles produce has a rank in each of them: its position
-// in the ascending set of those tiles.  Rank 0 stores it; rank r > 0 adds to
-// it in round r, after the lower tiles have finished round r - 1.
+// An output several tiles produce is stored by the lowest-index one; each
+// other one writes its part to a partial slot (through the tile's table of
+// slots) that the fix-up pass adds in tile order.
 // footprint row words: [0] BSR start of the row, [1] first code (within the
 // tile) | number of codes << 16 | number of vertex chunks << 24, [2] first
-// vertex chunk, [3] position of the diagonal block in the BSR row | rank of
-// the row (gradient and diagonal block) << 16.
+// vertex chunk, [3] position of the diagonal block in the BSR row (15 bits)
+// | partial << 15 | table index << 16 (partial rows).
 // code (one per pair block the tile produces): pair-chunk segment start
-// (15 bits) | its chunk count << 15 (4 bits) | transposed << 19 | rank << 20
-// (3 bits) | position in the BSR row << 23 (9 bits)
+// (15 bits) | its chunk count << 15 (4 bits) | transposed << 19 | partial
+// << 20 | position in the BSR row, or table index if partial, << 21 (11 bits)
 constexpr int kRowWords = 4;
 
 // vertex-pair interaction terms and the block pattern they extend (dyn.cu;
@@ -287,6 +296,17 @@ struct adm_ctx {
 };
 
 namespace adm {
+
+// whether contact terms extend pattern `kind`, and the BSR row pointer
+// (device) a pass on it writes through
+inline bool pattern_extended(const adm_ctx *h, int kind)
+{
+    return h->inter.kind == kind && h->inter.d_rp[h->inter.active] != nullptr;
+}
+inline const int32_t *active_row_ptr(const adm_ctx *h, int kind)
+{
+    return pattern_extended(h, kind) ? h->inter.d_rp[h->inter.active] : h->pat[kind].d_row_ptr;
+}
 
 // mesh.cpp
 adm_status mesh_validate(const HostMesh &m);

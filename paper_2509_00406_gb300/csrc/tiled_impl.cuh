@@ -3,10 +3,11 @@
 // from a queue, evaluate them with per-element forward mode, stage every
 // contribution in shared memory sorted by the output it adds to, and write
 // each BSR entry, gradient and H v entry as the fixed-order sum of one
-// contiguous segment.  No float atomics anywhere: an output that several
-// tiles produce is stored by the lowest-index one and added to by the others
-// in tile order (each waits, bounded, for the lower tiles' done flags), so
-// two passes on the same input give bit-identical results.
+// contiguous segment.  No float atomics anywhere, and no tile waits for
+// another: an output that several tiles produce is stored by the
+// lowest-index one, the others store their parts in partial slots, and a
+// fix-up kernel adds the slots in tile order, so two passes on the same
+// input give bit-identical results.
 #pragma once
 
 #include "device_common.cuh"
@@ -31,7 +32,7 @@ struct TiledArgs {
     const T *v;                       // matrix-free mode: direction
     T *hv;                            // matrix-free mode: H v
     int32_t *next;                    // work queue position of this launch
-    int32_t *done;                    // per tile: rounds finished (cleared every pass; 255 = all)
+    T *vpart, *ppart;                 // partial slots of shared outputs: Chunk<MODE_HESS, VD>::V, VD^2 each
     int32_t tile_begin, tile_end;     // this launch's tiles
     double *epart;                    // per tile
     int *status;
@@ -202,30 +203,6 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
         if (done) return true;
     }
     return false;
-}
-
-// a tile's round progress (rounds finished), acquire load at GPU scope
-__device__ __forceinline__ int progress_acquire(const int32_t *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// wait until a lower tile has finished `rounds` rounds; gives up after about
-// a second (2^22 polls about 250 ns apart) and returns false
-__device__ __forceinline__ bool wait_progress(const int32_t *p, int rounds)
-{
-    for (int it = 0; it < (1 << 22); ++it) {
-        if (progress_acquire(p) >= rounds) return true;
-        __nanosleep(256);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void progress_release(int32_t *p, int rounds)
-{
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(rounds) : "memory");
 }
 
 // ------------------------------------------------------------- kernel --
@@ -493,26 +470,15 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
         }
         const int32_t *rows = reinterpret_cast<const int32_t *>(blob);
         const uint32_t *codes = reinterpret_cast<const uint32_t *>(blob + hd[kHdrCodeOff]);
-        // Round r writes the outputs of rank r: rank 0 stores, rank r > 0 adds
-        // to what the r lower tiles of that output wrote, after every lower
-        // tile this one shares outputs with has finished round r - 1
-        const int rounds = MODE >= MODE_GRAD && meta_ok ? hd[kHdrRounds] : 0;
-        const int nw = hd[kHdrNWait];
-        const int32_t *wl = reinterpret_cast<const int32_t *>(blob + hd[kHdrWaitOff]);
-        for (int rnd = 0; rnd < rounds; ++rnd) {
-            const bool add = rnd > 0;
-            if (add) {
-                for (int i = tid; i < nw; i += THREADS)
-                    if (!wait_progress(A.done + wl[i], rnd)) atomicOr(A.status, ST_TIMEOUT);
-                __syncthreads();
-            }
+        const int32_t *ptab = reinterpret_cast<const int32_t *>(blob + hd[kHdrPartOff]);
+        if (MODE >= MODE_GRAD && meta_ok) {
             // vertex pass: one lane per footprint row sums the row's vertex
             // chunks (gradient and diagonal upper entries, or gradient and
             // H v) in registers and writes its gradient (H v) row and
-            // diagonal block
+            // diagonal block, or its partial slot
+            constexpr int CVH = Chunk<MODE_HESS, VD>::V;
             for (int r = tid; r < nf; r += THREADS) {
                 const int4 rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
-                if ((rw.w >> 16) != rnd) continue;
                 const int nv = (int)((uint32_t)rw.y >> 24), vs0 = rw.z & 0xffff;
                 T acc[CV > 0 ? CV : 1];
 #pragma unroll
@@ -521,26 +487,29 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                 for (int q = 0; q < nv; ++q)
 #pragma unroll
                     for (int e = 0; e < CV; ++e) acc[e] += src[CV * q + e];
+                if ((rw.w >> 15) & 1) {  // a later producer of a shared row
+                    T *p = A.vpart + (int64_t)ptab[rw.w >> 16] * CVH;
+#pragma unroll
+                    for (int e = 0; e < CV; ++e) p[e] = acc[e];
+                    continue;
+                }
                 const int64_t vg = A.foot[fb + r];
                 if (A.grad) {
                     T *g = A.grad + vg * VD;
 #pragma unroll
-                    for (int d = 0; d < VD; ++d) g[d] = add ? __ldcg(g + d) + acc[d] : acc[d];
+                    for (int d = 0; d < VD; ++d) g[d] = acc[d];
                 }
                 if constexpr (MODE == MODE_HVP) {
                     T *y = A.hv + vg * VD;
 #pragma unroll
-                    for (int d = 0; d < VD; ++d) y[d] = add ? __ldcg(y + d) + acc[VD + d] : acc[VD + d];
+                    for (int d = 0; d < VD; ++d) y[d] = acc[VD + d];
                 }
                 if constexpr (MODE == MODE_HESS) {
-                    T *out = A.bsr + ((int64_t)rw.x + (rw.w & 0xffff)) * (VD * VD);
+                    T *out = A.bsr + ((int64_t)rw.x + (rw.w & 0x7fff)) * (VD * VD);
 #pragma unroll
                     for (int i = 0; i < VD; ++i)
 #pragma unroll
-                        for (int j = 0; j < VD; ++j) {
-                            const T val = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
-                            out[i * VD + j] = add ? __ldcg(out + i * VD + j) + val : val;
-                        }
+                        for (int j = 0; j < VD; ++j) out[i * VD + j] = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
                 }
             }
             if constexpr (MODE == MODE_HESS) {
@@ -558,7 +527,6 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                     const int64_t rs = rw.x;
                     for (int j = hl16; j < nc; j += 16) {
                         const uint32_t code = codes[c0 + j];
-                        if ((int)((code >> 20) & 7u) != rnd) continue;
                         const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 15u);
                         T acc[NB];
 #pragma unroll
@@ -576,36 +544,69 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                                     acc[i * VD + k] = acc[k * VD + i];
                                     acc[k * VD + i] = tmp;
                                 }
-                        T *out = A.bsr + (rs + (int64_t)(code >> 23)) * NB;
-                        if (add) {
+                        T *out = (code >> 20) & 1u ? A.ppart + (int64_t)ptab[code >> 21] * NB
+                                                   : A.bsr + (rs + (int64_t)(code >> 21)) * NB;
 #pragma unroll
-                            for (int k = 0; k < NB; ++k) out[k] = __ldcg(out + k) + acc[k];
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < NB; ++k) out[k] = acc[k];
-                        }
+                        for (int k = 0; k < NB; ++k) out[k] = acc[k];
                     }
                 }
-            }
-            // release round rnd to the higher tiles (the last round's release
-            // comes with the tile's end)
-            if (rnd + 1 < rounds) {
-                __threadfence();
-                __syncthreads();
-                if (tid == 0) progress_release(A.done + t, rnd + 1);
             }
         }
         const double sum = block_sum<THREADS>(fe);
         if (tid == 0) A.epart[t] = sum;
-        // ---- this tile's outputs are all written: release every round
-        if (MODE >= MODE_GRAD) {
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) progress_release(A.done + t, 255);
-        }
         __syncthreads();
     }
     if (iter == cap) atomicOr(A.status, ST_TIMEOUT);  // the queue never ran dry within its bound
+}
+
+// Fix-up of the outputs several tiles produce: one thread per output float
+// adds the output's partial slots, in tile order, to what the lowest tile
+// stored.  Entries: row vertex, position of the block in its BSR row (row
+// start from the active pattern's row pointer), number of slots, first
+// slot; vertex outputs (gradient row, H v row or diagonal block: W floats
+// each) take threads [0, n_v W), pair blocks the next n_p VD^2.  Entries and
+// slots are in output order, so consecutive threads touch consecutive floats.
+template <typename T, int VD, int MODE>
+__global__ void k_tile_fixup(const int4 *__restrict__ fix_v, int64_t n_v, const int4 *__restrict__ fix_p, int64_t n_p,
+                             const T *__restrict__ vpart, const T *__restrict__ ppart,
+                             const int32_t *__restrict__ row_ptr, T *grad, T *bsr, T *hv)
+{
+    constexpr int CVH = Chunk<MODE_HESS, VD>::V, NB = VD * VD;
+    constexpr int W = MODE == MODE_HESS ? VD + NB : (MODE == MODE_HVP ? 2 * VD : VD);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_v * W) {
+        const int64_t ei = i / W;
+        const int k = (int)(i - ei * W);
+        const int4 e = __ldg(fix_v + ei);
+        T *out;
+        int src;  // float of the vertex chunk this output float sums
+        if (k < VD) {
+            if (!grad) return;
+            out = grad + (int64_t)e.x * VD + k;
+            src = k;
+        } else if (MODE == MODE_HVP) {
+            out = hv + (int64_t)e.x * VD + (k - VD);
+            src = k;
+        } else {
+            const int r = (k - VD) / VD, c = (k - VD) % VD;
+            out = bsr + ((int64_t)__ldg(row_ptr + e.x) + e.y) * NB + (k - VD);
+            src = VD + (r <= c ? hix(r, c) : hix(c, r));
+        }
+        const T *p = vpart + (int64_t)e.w * CVH + src;
+        T a = *out;
+        for (int q = 0; q < e.z; ++q) a += p[(int64_t)q * CVH];
+        *out = a;
+    } else if (MODE == MODE_HESS && i < n_v * W + n_p * NB) {
+        const int64_t j = i - n_v * W;
+        const int64_t ei = j / NB;
+        const int k = (int)(j - ei * NB);
+        const int4 e = __ldg(fix_p + ei);
+        T *out = bsr + ((int64_t)__ldg(row_ptr + e.x) + e.y) * NB + k;
+        const T *p = ppart + (int64_t)e.w * NB + k;
+        T a = *out;
+        for (int q = 0; q < e.z; ++q) a += p[(int64_t)q * NB];
+        *out = a;
+    }
 }
 
 // zero the gradient rows and diagonal blocks of vertices no unit touches
@@ -710,9 +711,8 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     const bool pairs = h->inter.kind == kind && h->inter.n_terms() > 0;
     if (cudaMemsetAsync(h->d_status, 0, sizeof(int), s) != cudaSuccess) return ADM_ERR_CUDA;
     if (a.energy == ADM_MASS_SPRING && (!ts.cloth_built || !h->d_xhat[a.prec])) return ADM_ERR_UNSUPPORTED;
-    // queue positions and done flags start at zero every pass
-    const int64_t n_sync = 8 + ts.n_tiles;
-    if (cudaMemsetAsync(ts.d_sync, 0, n_sync * sizeof(int32_t), s) != cudaSuccess) return ADM_ERR_CUDA;
+    // queue positions start at zero every pass
+    if (cudaMemsetAsync(ts.d_sync, 0, 8 * sizeof(int32_t), s) != cudaSuccess) return ADM_ERR_CUDA;
     TiledArgs<T> A;
     A.hdr = ts.d_hdr;
     A.unit = ts.d_unit;
@@ -731,7 +731,8 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     A.bsr = (T *)a.bsr;
     A.v = (const T *)a.v;
     A.hv = (T *)a.hv;
-    A.done = ts.d_sync + 8;
+    A.vpart = (T *)ts.d_vpart;
+    A.ppart = (T *)ts.d_ppart;
     A.epart = h->d_epart;
     A.status = h->d_status;
     A.c = consts<T>(h, a.energy);
@@ -798,6 +799,26 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
         }
         for (int k = 0; k < a.n_split; ++k)
             if (cudaStreamWaitEvent(s, h->split_done[k], 0) != cudaSuccess) return ADM_ERR_CUDA;
+    }
+    // the later producers' parts of shared outputs, added in tile order
+    const int64_t n_fv = mode >= MODE_GRAD ? (int64_t)ts.fix_v.size() / 4 : 0;
+    const int64_t n_fp = mode == MODE_HESS ? (int64_t)ts.fix_p.size() / 4 : 0;
+    if (n_fv + n_fp > 0) {
+        const int32_t *rp = active_row_ptr(h, kind);
+        const int wv = mode == MODE_HESS ? vd + vd * vd : (mode == MODE_HVP ? 2 * vd : vd);
+        const int blocks = (int)((n_fv * wv + n_fp * vd * vd + 255) / 256);
+        const int4 *fv = reinterpret_cast<const int4 *>(ts.d_fix_v), *fp = reinterpret_cast<const int4 *>(ts.d_fix_p);
+        const T *vp = (const T *)ts.d_vpart, *pp = (const T *)ts.d_ppart;
+        auto go = [&](auto kern) { kern<<<blocks, 256, 0, s>>>(fv, n_fv, fp, n_fp, vp, pp, rp, (T *)a.grad, (T *)a.bsr, (T *)a.hv); };
+        if (vd == 3) {
+            if (mode == MODE_HESS) go(k_tile_fixup<T, 3, MODE_HESS>);
+            else if (mode == MODE_HVP) go(k_tile_fixup<T, 3, MODE_HVP>);
+            else go(k_tile_fixup<T, 3, MODE_GRAD>);
+        } else {
+            if (mode == MODE_HESS) go(k_tile_fixup<T, 2, MODE_HESS>);
+            else if (mode == MODE_HVP) go(k_tile_fixup<T, 2, MODE_HVP>);
+            else go(k_tile_fixup<T, 2, MODE_GRAD>);
+        }
     }
     tm.end(ADM_STAGE_TILED);
     if (cudaGetLastError() != cudaSuccess) return ADM_ERR_CUDA;

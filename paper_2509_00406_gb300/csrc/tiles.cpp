@@ -328,7 +328,6 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         std::vector<uint32_t> codes;
         std::vector<uint64_t> pair_keys;            // produced unordered pairs (global key)
         int64_t nvc = 0, npc = 0;
-        int32_t rounds = 1;                         // 1 + the highest rank of its shared outputs
     };
     std::vector<TileOut> T(n_tiles);
     const int64_t maxrow = 512;
@@ -456,7 +455,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
                 if (!ps) continue;
                 if ((*ps)[2] >= 32768 || (*ps)[3] >= 16) fail = ADM_ERR_UNSUPPORTED;
                 o.codes.push_back((uint32_t)(*ps)[2] | (uint32_t)(*ps)[3] << 15 | (uint32_t)(r > lc) << 19 |
-                                  (uint32_t)(b - b0) << 23);
+                                  (uint32_t)(b - b0) << 21);
             }
             const uint32_t ncode = (uint32_t)o.codes.size() - code0;
             if (diag < 0 || ncode > 255 || vseg_n[r] > 255 || vseg_n[r] == 0) fail = ADM_ERR_MESH;
@@ -472,14 +471,27 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
 
     // ---- outputs several tiles produce: rows (a vertex in several
     // footprints) and pair blocks (a pair produced by several tiles).  The
-    // lowest-index tile of such an output stores its part; every other one
-    // waits for the lower tiles it shares outputs with and adds its part to
-    // what is there, so the sum runs in tile order.  Tile sets never span
-    // meshes, so meshes are handled in parallel.
-    std::vector<std::vector<int32_t>> waits(n_tiles);
-    std::atomic<int> fail_rank(0);
+    // lowest-index tile of such an output stores its part in the output;
+    // every other one stores its part in a partial slot of its own.  The
+    // slots of one output are contiguous, in tile order, and a fix-up pass
+    // adds them to the output in that order after the tiles have run, so the
+    // sum is the same on every pass.  Tile sets never span meshes, so meshes
+    // are handled in parallel (mesh-local slots, offset afterwards).
+    struct MeshFix {
+        std::vector<std::array<int32_t, 4>> fv, fp;  // (row vertex, position in the row, slots, first slot)
+        int64_t nv = 0, np = 0;                      // vertex and pair slots of the mesh
+    };
+    std::vector<MeshFix> mfix(m.n_mesh);
+    std::vector<std::vector<int64_t>> ptab(n_tiles);  // per tile: its slots (bit 62: a pair slot), mesh-local
+    std::atomic<int> fail_part(0);
+    auto row_pos = [&](int32_t v, int32_t c) -> int32_t {
+        for (int32_t b = P.row_ptr[v]; b < P.row_ptr[v + 1]; ++b)
+            if (P.col[b] == c) return b - P.row_ptr[v];
+        return -1;
+    };
     parallel_for(m.n_mesh, nthr, [&](int64_t k, unsigned) {
         const int32_t t0 = ts.mesh_tile_off[k], t1 = ts.mesh_tile_off[k + 1];
+        MeshFix &mf = mfix[k];
         std::vector<std::pair<int32_t, int32_t>> vt;
         std::vector<std::pair<uint64_t, int32_t>> pt;
         for (int32_t t = t0; t < t1; ++t) {
@@ -488,65 +500,109 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         }
         std::sort(vt.begin(), vt.end());
         std::sort(pt.begin(), pt.end());
-        // rank of every tile in the (ascending) tile set of each shared vertex
-        // and pair, and the wait edges (tile, lower tile)
-        std::vector<std::array<int64_t, 3>> vrank, prank;  // (key, tile, rank)
-        std::vector<std::pair<int32_t, int32_t>> edges;
-        auto add_set = [&](auto begin, auto end, std::vector<std::array<int64_t, 3>> &out) {
-            int64_t rk = 0;
-            for (auto a = begin; a != end; ++a, ++rk) {
-                out.push_back({(int64_t)a->first, (int64_t)a->second, rk});
-                for (auto b = begin; b != a; ++b) edges.emplace_back(a->second, b->second);
-            }
-        };
+        // later producers of every shared output: (key, tile, rank >= 1),
+        // sorted by (key, tile).  Slots are allocated in output order
+        // (vertex order; block order for pair blocks) so that the fix-up
+        // streams through them.
+        std::vector<std::array<int64_t, 3>> vrank, prank;
         for (size_t i = 0; i < vt.size();) {
             size_t j = i;
             while (j < vt.size() && vt[j].first == vt[i].first) ++j;
-            if (j - i > 1) add_set(vt.begin() + i, vt.begin() + j, vrank);
+            const int32_t n = (int32_t)(j - i) - 1;
+            if (n > 0) {
+                const int32_t v = vt[i].first;
+                mf.fv.push_back({v, row_pos(v, v), n, (int32_t)mf.nv});
+                for (int32_t q = 1; q <= n; ++q) vrank.push_back({v, vt[i + q].second, q});
+                mf.nv += n;
+            }
             i = j;
         }
         for (size_t i = 0; i < pt.size();) {
             size_t j = i;
             while (j < pt.size() && pt[j].first == pt[i].first) ++j;
-            if (j - i > 1) add_set(pt.begin() + i, pt.begin() + j, prank);
+            const int32_t n = (int32_t)(j - i) - 1;
+            if (n > 0) {
+                // blocks (a, b) in row a and (b, a) in row b
+                const int32_t a = (int32_t)(pt[i].first / (uint64_t)nV), b = (int32_t)(pt[i].first % (uint64_t)nV);
+                mf.fp.push_back({a, b, n, 0});
+                mf.fp.push_back({b, a, n, 0});
+                for (int32_t q = 1; q <= n; ++q) prank.push_back({(int64_t)pt[i].first, pt[i + q].second, q});
+            }
             i = j;
         }
-        std::sort(edges.begin(), edges.end());
-        edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
-        for (auto &e : edges) waits[e.first].push_back(e.second);
+        // pair outputs in block order (row, then column): slot runs, then
+        // the column becomes the block's position in its row
+        std::sort(mf.fp.begin(), mf.fp.end());
+        std::vector<std::array<int32_t, 2>> pcols(mf.fp.size());  // (row, column) of each pair output
+        for (size_t i = 0; i < mf.fp.size(); ++i) {
+            auto &e = mf.fp[i];
+            pcols[i] = {e[0], e[1]};
+            e[3] = (int32_t)mf.np;
+            mf.np += e[2];
+            e[1] = row_pos(e[0], e[1]);
+        }
+        for (auto &e : mf.fv)
+            if (e[1] < 0) fail_part = ADM_ERR_MESH;
+        for (auto &e : mf.fp)
+            if (e[1] < 0) fail_part = ADM_ERR_MESH;
         auto rank_of = [](const std::vector<std::array<int64_t, 3>> &rk, int64_t key, int64_t t) -> int64_t {
             auto it = std::lower_bound(rk.begin(), rk.end(), std::array<int64_t, 3>{key, t, INT64_MIN});
             return (it != rk.end() && (*it)[0] == key && (*it)[1] == t) ? (*it)[2] : 0;
         };
-        // per tile, the rank of each output it produces: 0 stores, r > 0
-        // adds in round r
+        // per tile: rows and codes of a later producer point into its table
         for (int32_t t = t0; t < t1; ++t) {
             TileOut &o = T[t];
+            std::vector<int64_t> &tab = ptab[t];
             const int32_t nf = (int32_t)o.foot.size();
-            int64_t rmax = 0;
             for (int32_t r = 0; r < nf; ++r) {
                 int32_t *row = &o.rows[(size_t)kRowWords * r];
                 const int32_t v = o.foot[r];
-                const int64_t rv = rank_of(vrank, v, t);
-                if (rv > 7) fail_rank = 1;
-                rmax = std::max(rmax, rv);
-                row[3] |= (int32_t)(rv << 16);
+                const int64_t qv = rank_of(vrank, v, t);
+                if (qv > 0) {
+                    auto it = std::lower_bound(mf.fv.begin(), mf.fv.end(), std::array<int32_t, 4>{v, INT32_MIN, 0, 0});
+                    if (tab.size() >= 32768) fail_part = 1;
+                    row[3] = (row[3] & 0x7fff) | 1 << 15 | (int32_t)(tab.size() << 16);
+                    tab.push_back((*it)[3] + qv - 1);
+                }
                 const uint32_t c0 = (uint32_t)row[1] & 0xffffu, nc = ((uint32_t)row[1] >> 16) & 0xffu;
                 for (uint32_t c = c0; c < c0 + nc; ++c) {
-                    const int32_t col = P.col[P.row_ptr[v] + (o.codes[c] >> 23)];
-                    const int64_t rp = rank_of(prank, (int64_t)pkey(v, col, nV), t);
-                    if (rp > 7) fail_rank = 1;
-                    rmax = std::max(rmax, rp);
-                    o.codes[c] |= (uint32_t)(rp & 7) << 20;
+                    const int32_t col = P.col[P.row_ptr[v] + (o.codes[c] >> 21)];
+                    const int64_t qp = rank_of(prank, (int64_t)pkey(v, col, nV), t);
+                    if (qp == 0) continue;
+                    const size_t oi = (size_t)(std::lower_bound(pcols.begin(), pcols.end(), std::array<int32_t, 2>{v, col}) -
+                                               pcols.begin());
+                    if (tab.size() >= 2048) fail_part = 1;
+                    o.codes[c] = (o.codes[c] & 0xfffffu) | 1u << 20 | (uint32_t)tab.size() << 21;
+                    tab.push_back((mf.fp[oi][3] + qp - 1) | (int64_t)1 << 62);
                 }
             }
-            o.rounds = (int32_t)rmax + 1;
         }
     });
-    if (fail_rank) {
-        // an output shared by more than 8 tiles (ranks have 3 bits): larger tiles
-        if (tile_units >= 4096) return ADM_ERR_UNSUPPORTED;
-        return tiles_build(m, P, with_hinges, 2 * tile_units, ts);
+    if (fail_part == 1) {
+        // a tile with more shared outputs than its table indexes: smaller tiles
+        if (tile_units <= 16) return ADM_ERR_UNSUPPORTED;
+        return tiles_build(m, P, with_hinges, tile_units / 2, ts);
+    }
+    if (fail_part) return (adm_status)fail_part.load();
+    std::vector<int64_t> voff(m.n_mesh + 1, 0), poff(m.n_mesh + 1, 0);
+    for (int k = 0; k < m.n_mesh; ++k) {
+        voff[k + 1] = voff[k] + mfix[k].nv;
+        poff[k + 1] = poff[k] + mfix[k].np;
+    }
+    if (voff.back() >= INT32_MAX || poff.back() >= INT32_MAX) return ADM_ERR_UNSUPPORTED;
+    ts.n_vpart = voff.back();
+    ts.n_ppart = poff.back();
+    ts.fix_v.clear();
+    ts.fix_p.clear();
+    for (int k = 0; k < m.n_mesh; ++k) {
+        for (auto e : mfix[k].fv) {
+            e[3] += (int32_t)voff[k];
+            ts.fix_v.insert(ts.fix_v.end(), e.begin(), e.end());
+        }
+        for (auto e : mfix[k].fp) {
+            e[3] += (int32_t)poff[k];
+            ts.fix_p.insert(ts.fix_p.end(), e.begin(), e.end());
+        }
     }
     ts.hdr.assign((size_t)kHdr * n_tiles, 0);
 
@@ -566,26 +622,33 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         hd[kHdrNVC] = (int32_t)o.nvc;
         hd[kHdrNPC] = (int32_t)o.npc;
         hd[kHdrNCode] = (int32_t)o.codes.size();
-        hd[kHdrNWait] = (int32_t)waits[t].size();
-        hd[kHdrRounds] = o.rounds;
+        // the tile's partial slots, global: vertex slots offset by the
+        // mesh's first vertex slot, pair slots by its first pair slot
+        const int32_t km = tile_mesh[t];
+        std::vector<int32_t> tab(ptab[t].size());
+        for (size_t j = 0; j < tab.size(); ++j) {
+            const int64_t e = ptab[t][j];
+            tab[j] = (e >> 62) & 1 ? (int32_t)((e & ~((int64_t)1 << 62)) + poff[km]) : (int32_t)(e + voff[km]);
+        }
+        hd[kHdrNPart] = (int32_t)tab.size();
         const int64_t rows_b = 4 * (int64_t)kRowWords * nf;
         const int64_t codes_b = 4 * (int64_t)o.codes.size();
-        const int64_t wait_b = 4 * (int64_t)waits[t].size();
+        const int64_t tab_b = 4 * (int64_t)tab.size();
         hd[kHdrCodeOff] = (int32_t)rows_b;
-        hd[kHdrWaitOff] = (int32_t)(rows_b + codes_b);
-        const int64_t mb = align16(rows_b + codes_b + wait_b);
+        hd[kHdrPartOff] = (int32_t)(rows_b + codes_b);
+        const int64_t mb = align16(rows_b + codes_b + tab_b);
         const size_t m0 = ts.meta.size();
         ts.meta.resize(m0 + mb, 0);
         unsigned char *blob = ts.meta.data() + m0;
         std::memcpy(blob, o.rows.data(), rows_b);
         std::memcpy(blob + rows_b, o.codes.data(), codes_b);
-        std::memcpy(blob + rows_b + codes_b, waits[t].data(), wait_b);
+        std::memcpy(blob + rows_b + codes_b, tab.data(), tab_b);
         ts.meta_off[t + 1] = (int64_t)ts.meta.size();
         ts.max_meta = std::max(ts.max_meta, mb);
         ts.max_nf = std::max<int64_t>(ts.max_nf, nf);
         ts.max_nvc = std::max(ts.max_nvc, o.nvc);
         ts.max_npc = std::max(ts.max_npc, o.npc);
-        ts.max_wait = std::max<int64_t>(ts.max_wait, (int64_t)waits[t].size());
+        ts.max_part = std::max<int64_t>(ts.max_part, (int64_t)tab.size());
         // unit data
         ts.foot.insert(ts.foot.end(), o.foot.begin(), o.foot.end());
         ts.unit.insert(ts.unit.end(), o.unit.begin(), o.unit.end());

@@ -3,10 +3,10 @@ without a GPU (libadm_host.so is the same mesh.cpp/tiles.cpp code compiled
 with the C++ compiler alone).  For every mesh and tile size: every chunk of a
 tile is written by exactly one unit role and summed by the segments of its
 outputs; every block of the pattern is produced by one tile (a plain store)
-or is "shared": the lowest of its tiles stores it, every other one adds to
-it after waiting for that tile (in a wait list of lower tiles only, so the
-waits cannot form a cycle); and every triangle and hinge belongs to exactly
-one tile."""
+or is "shared": the lowest of its tiles stores it, every other one writes a
+partial slot of its own (the slots of one output contiguous, in tile order,
+listed by the output's fix-up entry, every slot used exactly once); and every
+triangle and hinge belongs to exactly one tile."""
 import ctypes as C
 
 import numpy as np
@@ -61,7 +61,7 @@ def test_every_block_written_once_or_shared(H, name, tile, hinges):
     shared = bw == -2
     assert (ba[shared] >= 2).all()                # a shared block has two or more adders
     assert (ba[~shared] == 0).all()               # a plain block has exactly one writer
-    assert (int(st[1]) > 0) == bool(shared.any()) # lower-tile waits exist exactly when outputs are shared
+    assert (int(st[1]) > 0) == bool(shared.any()) # partial slots exist exactly when outputs are shared
     assert st[3] <= 227 * 1024                    # every tile fits FP64 shared memory
 
 
