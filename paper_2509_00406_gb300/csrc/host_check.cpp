@@ -145,7 +145,7 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             use[tab[idx]]++;
             return 0;
         };
-        // rows and codes: segments tile the chunk arrays; blocks produced
+        // rows and pair codes: segments tile the chunk arrays; blocks produced
         int64_t vcov = 0;
         std::vector<int> pcov(npc, 0);
         for (int32_t r = 0; r < nf; ++r) {
@@ -154,44 +154,67 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             const int32_t v = ts.foot[fb + r];
             const int32_t rs = w[0] & 0x7fffffff;
             if (rs != P.row_ptr[v]) return -106;
-            const int c0 = w[1] & 0xffff, nc = (w[1] >> 16) & 0xff, nv = (int)((uint32_t)w[1] >> 24);
+            const int nv = (int)((uint32_t)w[1] >> 24);
             const int vs0 = w[2] & 0xffff;
             if (vs0 != vcov) return -113;  // vertex segments in footprint order, back to back
             vcov += nv;
             const int32_t bd = rs + (w[3] & 0x7fff);
             if (P.col[bd] != v) return -114;
-            {
-                auto it = fixv.find(v);
-                const int rc = check_slot((w[3] >> 15) & 1, w[3] >> 16, it == fixv.end() ? -1 : it->second, ts.fix_v,
-                                          vprod[v], vslot_use);
-                if (rc) return rc;
-                vprod[v]++;
-                who[bd].push_back(t);
+            auto it = fixv.find(v);
+            const int rc = check_slot((w[3] >> 15) & 1, w[3] >> 16, it == fixv.end() ? -1 : it->second, ts.fix_v,
+                                      vprod[v], vslot_use);
+            if (rc) return rc;
+            vprod[v]++;
+            who[bd].push_back(t);
+        }
+        // a pair code's block: (row, position) or, if partial, the output
+        // whose slot run holds the table entry's slot
+        auto block_of = [&](bool part, uint32_t d, int32_t row_v) -> int32_t {
+            if (!part) {
+                const int32_t r = (int32_t)(d >> 9);
+                if (r >= nf) return -1;
+                int32_t w0;
+                std::memcpy(&w0, blob + 4 * kRowWords * r, 4);
+                const int32_t b = w0 + (int32_t)(d & 511u);
+                return (ts.foot[fb + r] == row_v && b < P.row_ptr[row_v + 1]) ? b : -1;
             }
-            for (int c = c0; c < c0 + nc; ++c) {
-                uint32_t code;
-                std::memcpy(&code, blob + hd[kHdrCodeOff] + 4 * c, 4);
-                const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 15u);
-                const int tr = (int)((code >> 19) & 1u), part = (int)((code >> 20) & 1u);
-                // a partial block's position comes from its fix-up entry
-                int32_t b = -1;
-                if (!part) {
-                    b = rs + (int32_t)(code >> 21);
-                } else {
-                    const int idx = (int)(code >> 21);
-                    if (idx >= npart) return -115;
-                    if (tab[idx] < 0 || tab[idx] >= ts.n_ppart) return -121;
-                    b = pslot_block[tab[idx]];  // the entry whose slot run holds this slot
-                    if (b < 0) return -121;
-                }
-                if (b >= P.row_ptr[v + 1] || b < rs || P.col[b] == v) return -116;
-                const int32_t lc = (int32_t)(std::lower_bound(ts.foot.begin() + fb, ts.foot.begin() + fb + nf, P.col[b]) -
-                                             (ts.foot.begin() + fb));
-                if (lc >= nf || ts.foot[fb + lc] != P.col[b] || tr != (r > lc ? 1 : 0)) return -117;
-                if (cnt == 0 || start + cnt > npc) return -118;
-                for (int q = start; q < start + cnt; ++q) pcov[q]++;
+            if ((int)d >= npart || tab[d] < 0 || tab[d] >= ts.n_ppart) return -1;
+            const int32_t b = pslot_block[tab[d]];
+            return (b >= P.row_ptr[row_v] && b < P.row_ptr[row_v + 1]) ? b : -1;
+        };
+        for (int j = 0; j < hd[kHdrNCode]; ++j) {
+            uint32_t c[2];
+            std::memcpy(c, blob + hd[kHdrCodeOff] + 8 * j, 8);
+            const int start = (int)(c[0] & 0x1fffu), cnt = (int)((c[0] >> 13) & 15u);
+            const bool pa = (c[0] >> 17) & 1u, pb = (c[0] >> 18) & 1u;
+            const uint32_t da = ((c[0] >> 19) & 511u) << 9 | (c[1] & 511u);
+            const uint32_t db = ((c[1] >> 9) & 511u) << 9 | ((c[1] >> 18) & 511u);
+            if (pa != pb) return -115;  // both blocks of a pair have the same producers
+            if (cnt == 0 || start + cnt > npc) return -118;
+            for (int q = start; q < start + cnt; ++q) pcov[q]++;
+            // the pair (va, vb), va < vb: rows of blocks A and B
+            int32_t va, vb;
+            if (!pa) {
+                const int32_t lo = (int32_t)(da >> 9), hi = (int32_t)(db >> 9);
+                if (lo >= nf || hi >= nf || lo >= hi) return -117;
+                va = ts.foot[fb + lo];
+                vb = ts.foot[fb + hi];
+            } else {
+                if ((int)da >= npart || (int)db >= npart || tab[da] < 0 || tab[da] >= ts.n_ppart || tab[db] < 0 ||
+                    tab[db] >= ts.n_ppart)
+                    return -121;
+                const int32_t b1 = pslot_block[tab[da]], b2 = pslot_block[tab[db]];
+                if (b1 < 0 || b2 < 0) return -121;
+                vb = P.col[b1];
+                va = P.col[b2];
+                if (va >= vb) return -117;
+            }
+            const int32_t ba = block_of(pa, da, va), bb = block_of(pb, db, vb);
+            if (ba < 0 || bb < 0 || P.col[ba] != vb || P.col[bb] != va) return -116;
+            for (const auto &blk : {std::make_pair(ba, da), std::make_pair(bb, db)}) {
+                const int32_t b = blk.first;
                 auto it = fixp.find(b);
-                const int rc = check_slot(part, (int)(code >> 21), it == fixp.end() ? -1 : it->second, ts.fix_p,
+                const int rc = check_slot(pa, (int)blk.second, it == fixp.end() ? -1 : it->second, ts.fix_p,
                                           producers[b], pslot_use);
                 if (rc) return rc;
                 producers[b]++;
@@ -199,8 +222,8 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
             }
         }
         if (vcov != nvc) return -113;
-        for (int c : pcov)  // every pair chunk is summed by its two blocks, (a, b) and (b, a)
-            if (c != 2) return -119;
+        for (int c : pcov)  // every pair chunk is summed by exactly one pair code
+            if (c != 1) return -119;
         for (int c : tab_use)
             if (c != 1) return -122;
     }

@@ -174,13 +174,15 @@ enum TileHdr {
 // An output several tiles produce is stored by the lowest-index one; each
 // other one writes its part to a partial slot (through the tile's table of
 // slots) that the fix-up pass adds in tile order.
-// footprint row words: [0] BSR start of the row, [1] first code (within the
-// tile) | number of codes << 16 | number of vertex chunks << 24, [2] first
-// vertex chunk, [3] position of the diagonal block in the BSR row (15 bits)
-// | partial << 15 | table index << 16 (partial rows).
-// code (one per pair block the tile produces): pair-chunk segment start
-// (15 bits) | its chunk count << 15 (4 bits) | transposed << 19 | partial
-// << 20 | position in the BSR row, or table index if partial, << 21 (11 bits)
+// footprint row words: [0] BSR start of the row, [1] number of vertex
+// chunks << 24, [2] first vertex chunk, [3] position of the diagonal block in
+// the BSR row (15 bits) | partial << 15 | table index << 16 (partial rows).
+// pair code (one per pair segment of the tile, 2 words): x = chunk start (13
+// bits) | chunk count << 13 (4 bits) | partial A << 17 | partial B << 18 |
+// row A << 19 (9 bits); y = position A (9 bits) | row B << 9 | position B
+// << 18.  Block A is (lo, hi) in footprint row lo, block B the transpose
+// (hi, lo) in row hi; for a partial block, row << 9 | position is its index
+// in the tile's slot table.
 constexpr int kRowWords = 4;
 
 // vertex-pair interaction terms and the block pattern they extend (dyn.cu;

@@ -513,42 +513,35 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                 }
             }
             if constexpr (MODE == MODE_HESS) {
-                // pair pass: a half-warp per footprint row, one lane per pair
-                // block of the row; the lane sums the block's segment in chunk
-                // order and transposes once if the row is the higher index
+                // pair pass: one lane per pair segment; the lane sums the
+                // segment in chunk order once, then writes block A = (lo, hi)
+                // and its transpose, block B = (hi, lo), each to the BSR or to
+                // its partial slot
                 constexpr int NB = VD * VD;
-                const int lane = tid & 31, half = lane >> 4, hl16 = lane & 15;
-                const int n_rows_pass = (nf + 1) / 2;
-                for (int rr = tid >> 5; rr < n_rows_pass; rr += THREADS / 32) {
-                    const int r = 2 * rr + half;
-                    int4 rw = make_int4(0, 0, 0, 0);
-                    if (r < nf) rw = *reinterpret_cast<const int4 *>(rows + kRowWords * r);
-                    const int c0 = rw.y & 0xffff, nc = r < nf ? (rw.y >> 16) & 0xff : 0;
-                    const int64_t rs = rw.x;
-                    for (int j = hl16; j < nc; j += 16) {
-                        const uint32_t code = codes[c0 + j];
-                        const int start = (int)(code & 0x7fffu), cnt = (int)((code >> 15) & 15u);
-                        T acc[NB];
+                const int npair = hd[kHdrNCode];
+                const uint2 *pc = reinterpret_cast<const uint2 *>(codes);
+                for (int j = tid; j < npair; j += THREADS) {
+                    const uint2 c = pc[j];
+                    const int start = (int)(c.x & 0x1fffu), cnt = (int)((c.x >> 13) & 15u);
+                    T acc[NB];
 #pragma unroll
-                        for (int k = 0; k < NB; ++k) acc[k] = -T(0);
-                        const T *src = sp + CP * start;
-                        for (int q = 0; q < cnt; ++q)
+                    for (int k = 0; k < NB; ++k) acc[k] = -T(0);
+                    const T *src = sp + CP * start;
+                    for (int q = 0; q < cnt; ++q)
 #pragma unroll
-                            for (int k = 0; k < NB; ++k) acc[k] += src[CP * q + k];
-                        if ((code >> 19) & 1u)
+                        for (int k = 0; k < NB; ++k) acc[k] += src[CP * q + k];
+                    const uint32_t da = ((c.x >> 19) & 511u) << 9 | (c.y & 511u);
+                    const uint32_t db = ((c.y >> 9) & 511u) << 9 | ((c.y >> 18) & 511u);
+                    T *oa = (c.x >> 17) & 1u ? A.ppart + (int64_t)ptab[da] * NB
+                                             : A.bsr + ((int64_t)rows[kRowWords * (da >> 9)] + (da & 511u)) * NB;
+                    T *ob = (c.x >> 18) & 1u ? A.ppart + (int64_t)ptab[db] * NB
+                                             : A.bsr + ((int64_t)rows[kRowWords * (db >> 9)] + (db & 511u)) * NB;
 #pragma unroll
-                            for (int i = 0; i < VD; ++i)
+                    for (int k = 0; k < NB; ++k) oa[k] = acc[k];
 #pragma unroll
-                                for (int k = i + 1; k < VD; ++k) {
-                                    const T tmp = acc[i * VD + k];
-                                    acc[i * VD + k] = acc[k * VD + i];
-                                    acc[k * VD + i] = tmp;
-                                }
-                        T *out = (code >> 20) & 1u ? A.ppart + (int64_t)ptab[code >> 21] * NB
-                                                   : A.bsr + (rs + (int64_t)(code >> 21)) * NB;
+                    for (int i = 0; i < VD; ++i)
 #pragma unroll
-                        for (int k = 0; k < NB; ++k) out[k] = acc[k];
-                    }
+                        for (int k = 0; k < VD; ++k) ob[i * VD + k] = acc[k * VD + i];
                 }
             }
         }

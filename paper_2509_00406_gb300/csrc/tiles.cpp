@@ -120,10 +120,10 @@ struct TileCount {
 
 int64_t hess_bytes(const TileCount &c, int elem_bytes)
 {
-    // x, staging (vertex and pair chunks of 9), metadata bound (rows, codes,
-    // and at most one shared output and one group per row and code)
+    // x, staging (vertex and pair chunks of 9), metadata bound (rows, code
+    // words, and at most one slot-table entry per row and per pair block)
     return align16(c.nf * 3 * elem_bytes) + align16((c.nvc + c.npc) * 9 * elem_bytes) +
-           align16(16 * c.nf + 4 * c.ncodes + 4 * (c.nf + c.ncodes) + 4 * (c.nf + c.ncodes));
+           align16(16 * c.nf + 4 * c.ncodes + 4 * (c.nf + c.ncodes));
 }
 
 }  // namespace
@@ -287,8 +287,8 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
             auto [s0, s1] = stack.back();
             stack.pop_back();
             const TileCount c = count_range(scr[th], s0, s1);
-            const bool fits = hess_bytes(c, 4) <= kBudget32 && hess_bytes(c, 8) <= kBudget64 && c.nf < 65536 &&
-                              c.npc < 32768 && c.nvc < 65536 && c.ncodes < 65536;
+            const bool fits = hess_bytes(c, 4) <= kBudget32 && hess_bytes(c, 8) <= kBudget64 && c.nf <= 512 &&
+                              c.npc < 8192 && c.nvc < 65536 && c.ncodes < 65536;
             if (!fits) {
                 if (s1 - s0 <= 1) {
                     fail = ADM_ERR_UNSUPPORTED;
@@ -331,6 +331,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
     };
     std::vector<TileOut> T(n_tiles);
     const int64_t maxrow = 512;
+    std::atomic<int> fail_big(0);  // a tile too large for the code fields: smaller tiles
     parallel_for(n_tiles, nthr, [&](int64_t t, unsigned th) {
         TileOut &o = T[t];
         Scratch &w = scr[th];
@@ -426,47 +427,46 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
                 o.slot_v[slot_first[i] + s] = {u.t[k], u.t[(k + 1) % 3]};
             }
         }
-        // rows and codes: walk every footprint row's BSR row
-        auto find_pseg = [&](int32_t a, int32_t b) -> const std::array<int32_t, 4> * {
-            const int32_t lo = std::min(a, b), hi = std::max(a, b);
-            auto it = std::lower_bound(pseg.begin(), pseg.end(), std::array<int32_t, 4>{lo, hi, 0, 0},
-                                       [](const std::array<int32_t, 4> &x, const std::array<int32_t, 4> &y) {
-                                           return x[0] != y[0] ? x[0] < y[0] : x[1] < y[1];
-                                       });
-            return (it != pseg.end() && (*it)[0] == lo && (*it)[1] == hi) ? &*it : nullptr;
-        };
+        // rows: BSR row start, vertex segment, diagonal block; pair codes,
+        // one per pair segment (2 words): chunk start (13 bits) | count << 13
+        // (4 bits) | partial A << 17 | partial B << 18 | row A << 19 (9 bits);
+        // position A (9 bits) | row B << 9 | position B << 18.  Block A is
+        // (lo, hi) in row lo, block B its transpose (hi, lo) in row hi; a
+        // partial block's (row << 9 | position) is its slot-table index.
         const int32_t nf = (int32_t)o.foot.size();
+        if (nf > 512 || o.npc > 8191) fail_big = 1;
+        auto pos_in_row = [&](int32_t v, int32_t c) -> int32_t {
+            const int32_t *b0 = P.col.data() + P.row_ptr[v], *b1 = P.col.data() + P.row_ptr[v + 1];
+            const int32_t *it = std::lower_bound(b0, b1, c);
+            return (it != b1 && *it == c) ? (int32_t)(it - b0) : -1;
+        };
         o.rows.assign((size_t)kRowWords * nf, 0);
         for (int32_t r = 0; r < nf; ++r) {
             const int32_t v = o.foot[r];
             const int32_t b0 = P.row_ptr[v], b1 = P.row_ptr[v + 1];
             if (b1 - b0 > maxrow) fail = ADM_ERR_UNSUPPORTED;
-            const uint32_t code0 = (uint32_t)o.codes.size();
-            int32_t diag = -1;
-            for (int32_t b = b0; b < b1; ++b) {
-                const int32_t c = P.col[b];
-                if (c == v) {
-                    diag = b - b0;
-                    continue;
-                }
-                const int32_t lc = (c >= 0 && c < nV) ? w.mark[c] : -1;
-                if (lc < 0) continue;
-                const auto *ps = find_pseg(r, lc);
-                if (!ps) continue;
-                if ((*ps)[2] >= 32768 || (*ps)[3] >= 16) fail = ADM_ERR_UNSUPPORTED;
-                o.codes.push_back((uint32_t)(*ps)[2] | (uint32_t)(*ps)[3] << 15 | (uint32_t)(r > lc) << 19 |
-                                  (uint32_t)(b - b0) << 21);
-            }
-            const uint32_t ncode = (uint32_t)o.codes.size() - code0;
-            if (diag < 0 || ncode > 255 || vseg_n[r] > 255 || vseg_n[r] == 0) fail = ADM_ERR_MESH;
+            const int32_t diag = pos_in_row(v, v);
+            if (diag < 0 || vseg_n[r] > 255 || vseg_n[r] == 0) fail = ADM_ERR_MESH;
             int32_t *row = &o.rows[(size_t)kRowWords * r];
             row[0] = b0;
-            row[1] = (int32_t)(code0 | ncode << 16 | (uint32_t)vseg_n[r] << 24);
+            row[1] = (int32_t)((uint32_t)vseg_n[r] << 24);
             row[2] = vseg_start[r];
             row[3] = diag;
         }
+        for (auto &ps : pseg) {
+            const int32_t lo = ps[0], hi = ps[1];
+            const int32_t pa = pos_in_row(o.foot[lo], o.foot[hi]), pb = pos_in_row(o.foot[hi], o.foot[lo]);
+            if (pa < 0 || pb < 0) fail = ADM_ERR_MESH;
+            if (ps[3] >= 16) fail = ADM_ERR_UNSUPPORTED;
+            o.codes.push_back((uint32_t)ps[2] | (uint32_t)ps[3] << 13 | (uint32_t)lo << 19);
+            o.codes.push_back((uint32_t)pa | (uint32_t)hi << 9 | (uint32_t)pb << 18);
+        }
         for (int32_t v : o.foot) w.mark[v] = -1;
     });
+    if (fail_big && !fail) {
+        if (tile_units <= 16) return ADM_ERR_UNSUPPORTED;
+        return tiles_build(m, P, with_hinges, tile_units / 2, ts);
+    }
     if (fail) return (adm_status)fail.load();
 
     // ---- outputs several tiles produce: rows (a vertex in several
@@ -564,17 +564,23 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
                     row[3] = (row[3] & 0x7fff) | 1 << 15 | (int32_t)(tab.size() << 16);
                     tab.push_back((*it)[3] + qv - 1);
                 }
-                const uint32_t c0 = (uint32_t)row[1] & 0xffffu, nc = ((uint32_t)row[1] >> 16) & 0xffu;
-                for (uint32_t c = c0; c < c0 + nc; ++c) {
-                    const int32_t col = P.col[P.row_ptr[v] + (o.codes[c] >> 21)];
-                    const int64_t qp = rank_of(prank, (int64_t)pkey(v, col, nV), t);
-                    if (qp == 0) continue;
-                    const size_t oi = (size_t)(std::lower_bound(pcols.begin(), pcols.end(), std::array<int32_t, 2>{v, col}) -
+            }
+            for (size_t j = 0; 2 * j < o.codes.size(); ++j) {
+                uint32_t &x = o.codes[2 * j], &y = o.codes[2 * j + 1];
+                const int32_t va = o.foot[(x >> 19) & 511], vb = o.foot[(y >> 9) & 511];
+                const int64_t qp = rank_of(prank, (int64_t)pkey(va, vb, nV), t);
+                if (qp == 0) continue;
+                auto run = [&](int32_t r, int32_t c) {
+                    const size_t oi = (size_t)(std::lower_bound(pcols.begin(), pcols.end(), std::array<int32_t, 2>{r, c}) -
                                                pcols.begin());
-                    if (tab.size() >= 2048) fail_part = 1;
-                    o.codes[c] = (o.codes[c] & 0xfffffu) | 1u << 20 | (uint32_t)tab.size() << 21;
-                    tab.push_back((mf.fp[oi][3] + qp - 1) | (int64_t)1 << 62);
-                }
+                    return mf.fp[oi][3] + qp - 1;
+                };
+                if (tab.size() + 2 > (1u << 18)) fail_part = 1;
+                const uint32_t ia = (uint32_t)tab.size(), ib = ia + 1;
+                tab.push_back(run(va, vb) | (int64_t)1 << 62);
+                tab.push_back(run(vb, va) | (int64_t)1 << 62);
+                x = (x & 0x1ffffu) | 1u << 17 | 1u << 18 | (ia >> 9) << 19;
+                y = (ia & 511u) | (ib >> 9) << 9 | (ib & 511u) << 18;
             }
         }
     });
@@ -621,7 +627,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         hd[kHdrNF] = nf;
         hd[kHdrNVC] = (int32_t)o.nvc;
         hd[kHdrNPC] = (int32_t)o.npc;
-        hd[kHdrNCode] = (int32_t)o.codes.size();
+        hd[kHdrNCode] = (int32_t)(o.codes.size() / 2);  // pair codes of 2 words
         // the tile's partial slots, global: vertex slots offset by the
         // mesh's first vertex slot, pair slots by its first pair slot
         const int32_t km = tile_mesh[t];
