@@ -168,7 +168,8 @@ void free_tiles(adm_ctx *h, TileSet &ts)
 {
     void *ptrs[] = {ts.d_hdr, ts.d_foot, ts.d_tri_perm, ts.d_tri_verts, ts.d_unit, ts.d_unit_dst, ts.d_slot_dst,
                     ts.d_meta, ts.d_meta_off, ts.d_zero_verts, ts.d_zero_blocks,
-                    ts.d_mesh_tile_off, ts.d_sync, ts.d_fix_v, ts.d_fix_p, ts.d_vpart, ts.d_ppart, ts.d_tri_rest[0],
+                    ts.d_mesh_tile_off, ts.d_sync, ts.d_fix_v, ts.d_fix_p, ts.d_vpart, ts.d_ppart, ts.d_slot_verts,
+                    ts.d_loc_tri, ts.d_loc_slot, ts.d_tri_rest[0],
                     ts.d_tri_rest[1], ts.d_slot_rest[0], ts.d_slot_rest[1], ts.d_vterm_rest[0], ts.d_vterm_rest[1]};
     for (void *p : ptrs) dev_free(h, p);
     ts = TileSet();
@@ -197,6 +198,7 @@ adm_status ensure_tiles(adm_ctx *h, int kind)
     if ((s = up(&ts.d_foot, ts.foot)) != ADM_OK) return s;
     if ((s = up(&ts.d_tri_perm, ts.tri_perm)) != ADM_OK) return s;
     if ((s = up(&ts.d_tri_verts, ts.tri_verts)) != ADM_OK) return s;
+    if ((s = up(&ts.d_slot_verts, ts.slot_verts)) != ADM_OK) return s;
     if ((s = up(&ts.d_unit, ts.unit)) != ADM_OK) return s;
     if ((s = up(&ts.d_unit_dst, ts.unit_dst)) != ADM_OK) return s;
     if ((s = up(&ts.d_slot_dst, ts.slot_dst)) != ADM_OK) return s;

@@ -133,6 +133,8 @@ struct TileSet {
     std::vector<int32_t> tri_verts;      // unit -> its vertices (global ids), 3 per unit
     std::vector<double> tri_rest;        // 5 per unit (Dm^-1 row-major, area)
     std::vector<int32_t> slot_edge;      // slot -> (hinge index) or -1; per slot
+    std::vector<int32_t> slot_verts;     // 4 per slot, global ids in evaluation order: t_k, t_k+1, t_k+2,
+                                         // the hinge's extra vertex (-1: none)
     std::vector<double> slot_rest;       // 2 per slot: hinge (thetabar, abar/3) or spring (l^2, 0)
     std::vector<double> vterm_rest;      // per cloth vertex term: a third of the rest area around it
     std::vector<int32_t> foot;           // footprint vertices (global ids), sorted, per tile
@@ -156,6 +158,11 @@ struct TileSet {
     void *d_vpart = nullptr, *d_ppart = nullptr;  // partial slots, sized for FP64
     int64_t smem_cache[4][2][2] = {};    // tile_smem_bytes by (mode, VD == 3, FP64), 0: not yet computed
     int32_t *d_hdr = nullptr, *d_foot = nullptr, *d_tri_perm = nullptr, *d_tri_verts = nullptr;
+    int32_t *d_slot_verts = nullptr;
+    // filtered passes: each term's filtered edge-coordinate result (energy,
+    // gradient, packed Hessian), structure of arrays over units and slots,
+    // sized for FP64 on first use
+    void *d_loc_tri = nullptr, *d_loc_slot = nullptr;
     uint16_t *d_unit = nullptr, *d_unit_dst = nullptr, *d_slot_dst = nullptr;
     unsigned char *d_meta = nullptr;
     int64_t *d_meta_off = nullptr;

@@ -9,11 +9,14 @@
 // G = (L (x) I)^T He (L (x) I): the nonzero spectrum of H is that of G, and
 // the rest of H's spectrum is the translations' exact zeros, which clamping
 // leaves alone.  An eigenvalue counts as negative below -tau max |lambda|
-// (tau 1e-10 in double, 1e-5 in float).  So the filter runs on G (n = NE VD: 9 for a hinge, 6 for a
-// 3D triangle, 4 for a 2D one): cyclic Jacobi in registers, then
+// (tau 1e-10 in double, 1e-5 in float).  So the filter runs on G (n = NE VD:
+// 9 for a hinge, 6 for a 3D triangle, 4 for a 2D one): round-robin Jacobi in
+// registers, then
 //   He += sum over lambda_i < 0 of (eps - lambda_i) w_i w_i^T,
 //   w_i = (L^-1 (x) I)^T v_i,
-// which is U^T (clamped G) U pulled back to the edge vectors.
+// which is U^T (clamped G) U pulled back to the edge vectors.  A term with
+// no eigenvalue below -tau max |G_ii| / 2 (a shifted Cholesky test; max
+// |G_ii| <= max |lambda|) is left as it is without the eigensolve.
 #pragma once
 
 #include "ad.cuh"
@@ -84,13 +87,52 @@ ADM_HD void edge_metric_factor(T (&L)[E::NE][E::NE], T (&Li)[E::NE][E::NE])
     }
 }
 
-// Symmetric eigen-decomposition A = V diag(A_ii) V^T by cyclic Jacobi
-// rotations (A packed upper, overwritten by its diagonalised form; V n x n,
-// columns the eigenvectors).  Stops when the off-diagonal mass is below
-// machine precision relative to the whole matrix, or after kMaxSweeps.
+// Round-robin pairing of n indices (n padded to even m): round r pairs
+// (i, j) with i + j = 2r mod (m - 1) for i, j < m - 1, and the index i with
+// 2i = 2r mod (m - 1) with m - 1.  Pairs of one round are disjoint, so their
+// rotations commute; pairs with an index >= n (the pad) are skipped.
+ADM_HD constexpr int rr_partner(int m, int r, int i)
+{
+    if (i == m - 1) {
+        for (int k = 0; k < m - 1; ++k)
+            if ((2 * k) % (m - 1) == (2 * r) % (m - 1)) return k;
+        return -1;
+    }
+    if ((2 * i) % (m - 1) == (2 * r) % (m - 1)) return m - 1;
+    return ((2 * r - i) % (m - 1) + (m - 1)) % (m - 1);
+}
+// the pairs (p < q) of every round, as a table built at compile time
+template <int M>
+struct RoundRobin {
+    int p[M - 1][M / 2] = {}, q[M - 1][M / 2] = {};
+    ADM_HD constexpr RoundRobin()
+    {
+        for (int r = 0; r < M - 1; ++r) {
+            int cnt = 0;
+            for (int i = 0; i < M; ++i) {
+                const int j = rr_partner(M, r, i);
+                if (i < j) {
+                    p[r][cnt] = i;
+                    q[r][cnt] = j;
+                    ++cnt;
+                }
+            }
+        }
+    }
+};
+
+// Symmetric eigen-decomposition A = V diag(A_ii) V^T by Jacobi rotations in
+// round-robin order (A packed upper, overwritten by its diagonalised form;
+// V n x n, columns the eigenvectors).  Every round first takes the rotation
+// angles of its disjoint pairs from the current A, then applies them, so
+// the angle computations of a round are independent of one another.  Stops
+// when the off-diagonal mass is below machine precision relative to the
+// whole matrix, or after kMaxSweeps.
 template <int N, typename T>
 ADM_HD void jacobi_eig(T (&A)[N * (N + 1) / 2], T (&V)[N][N])
 {
+    constexpr int M = N + (N & 1), R = M - 1, P = M / 2;
+    constexpr RoundRobin<M> rr;
 #pragma unroll
     for (int i = 0; i < N; ++i)
 #pragma unroll
@@ -109,35 +151,83 @@ ADM_HD void jacobi_eig(T (&A)[N * (N + 1) / 2], T (&V)[N][N])
         const T e = SpdFn<T>::eps();
         if (!(off > e * e * all)) break;
 #pragma unroll
-        for (int p = 0; p < N - 1; ++p)
+        for (int r = 0; r < R; ++r) {
+            T cs[P], sn[P], tn[P], ap[P];
+            // angles of the round's pairs, from the current A
 #pragma unroll
-            for (int q = p + 1; q < N; ++q) {
+            for (int k = 0; k < P; ++k) {
+                const int p = rr.p[r][k], q = rr.q[r][k];
+                cs[k] = T(1);
+                sn[k] = T(0);
+                tn[k] = T(0);
+                ap[k] = T(0);
+                if (q >= N) continue;
                 const T apq = A[hix(p, q)];
+                ap[k] = apq;
                 if (apq == T(0)) continue;
                 const T theta = (A[hix(q, q)] - A[hix(p, p)]) / (T(2) * apq);
                 const T at = theta < T(0) ? -theta : theta;
                 T t = T(1) / (at + SpdFn<T>::sqrt_(theta * theta + T(1)));
                 if (theta < T(0)) t = -t;
                 const T c = T(1) / SpdFn<T>::sqrt_(t * t + T(1));
-                const T s = t * c;
+                cs[k] = c;
+                sn[k] = t * c;
+                tn[k] = t;
+            }
+            // the rotations, one pair after another
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int p = rr.p[r][k], q = rr.q[r][k];
+                if (q >= N) continue;
+                const T c = cs[k], s = sn[k], t = tn[k], apq = ap[k];
                 A[hix(p, p)] -= t * apq;
                 A[hix(q, q)] += t * apq;
                 A[hix(p, q)] = T(0);
 #pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    if (k == p || k == q) continue;
-                    const T akp = A[sym_ix(k, p)], akq = A[sym_ix(k, q)];
-                    A[sym_ix(k, p)] = c * akp - s * akq;
-                    A[sym_ix(k, q)] = s * akp + c * akq;
+                for (int kk = 0; kk < N; ++kk) {
+                    if (kk == p || kk == q) continue;
+                    const T akp = A[sym_ix(kk, p)], akq = A[sym_ix(kk, q)];
+                    A[sym_ix(kk, p)] = c * akp - s * akq;
+                    A[sym_ix(kk, q)] = s * akp + c * akq;
                 }
 #pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    const T vkp = V[k][p], vkq = V[k][q];
-                    V[k][p] = c * vkp - s * vkq;
-                    V[k][q] = s * vkp + c * vkq;
+                for (int kk = 0; kk < N; ++kk) {
+                    const T vkp = V[kk][p], vkq = V[kk][q];
+                    V[kk][p] = c * vkp - s * vkq;
+                    V[kk][q] = s * vkp + c * vkq;
                 }
             }
+        }
     }
+}
+
+// Whether a symmetric A (packed upper) has no eigenvalue below -s: a
+// Cholesky factorisation of A + s I that meets no non-positive pivot.
+template <int N, typename T>
+ADM_HD bool shifted_cholesky_ok(const T (&A)[N * (N + 1) / 2], T s)
+{
+    T Lf[N][N];      // lower factor
+    bool ok = true;  // no early exit, so that the loops unroll completely
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        T d = A[hix(j, j)] + s;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (k < j) d -= Lf[j][k] * Lf[j][k];
+        ok = ok && d > T(0);
+        const T ljj = SpdFn<T>::sqrt_(d > T(0) ? d : T(1)), inv = T(1) / ljj;
+        Lf[j][j] = ljj;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            if (i <= j) continue;
+            T m = A[hix(j, i)];
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                if (k < j) m -= Lf[i][k] * Lf[j][k];
+            Lf[i][j] = m * inv;
+        }
+    }
+    return ok;
 }
 
 // Filter the edge-vector Hessian He (packed upper, n = NE VD) in place.
@@ -161,6 +251,14 @@ ADM_HD void project_edges(T (&He)[E::NE * VD * (E::NE * VD + 1) / 2], T eps)
                 for (int qq = q; qq < NE; ++qq) acc += L[pp][p] * L[qq][q] * He[sym_ix(pp * VD + r, qq * VD + s)];
             G[hix(i, j)] = acc;
         }
+    // nothing to clamp if no eigenvalue lies below -s, s = tau max |G_ii| / 2
+    // (max |G_ii| <= max |lambda|): then the filter leaves He as it is
+    {
+        T dmax = T(0);
+#pragma unroll
+        for (int m = 0; m < N; ++m) dmax = fmax(dmax, fabs(G[hix(m, m)]));
+        if (shifted_cholesky_ok<N>(G, T(0.5) * SpdFn<T>::tau() * dmax)) return;
+    }
     T Vv[N][N];
     jacobi_eig<N>(G, Vv);
     // negative means below -tau max |lambda|: a term's structural zeros

@@ -39,6 +39,7 @@ struct TiledArgs {
     TermConsts<T> c;
     const float *mlp_table;           // learned membrane: 10 per unit
     const T *xhat;                    // cloth inertial target
+    const T *loc_tri, *loc_slot;      // filtered passes: the terms' filtered results (SoA)
 };
 
 // floats of a vertex and of a pair chunk
@@ -205,12 +206,108 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
+// ------------------------------------------------------ filtered terms --
+// Filtered passes: each term's filtered edge-coordinate result (energy,
+// gradient, packed Hessian), one thread per term, into structure-of-arrays
+// buffers that k_tiled then reads in place of evaluating the terms.  The
+// filter's eigensolve is the expensive part; here it runs one term per
+// thread with no shared memory and no barriers.  A term outside the
+// energy's domain stores a NaN energy, which k_tiled reports.
+template <typename T>
+struct LocalArgs {
+    int64_t nU, nS;
+    const int32_t *tri_verts;         // 3 per unit
+    const int4 *slot_verts;           // per slot: t_k, t_k+1, t_k+2, extra (-1: none)
+    const T *tri_rest, *slot_rest;    // SoA, as k_tiled reads them
+    const T *x;
+    const float *mlp_table;           // learned membrane: 10 per unit
+    T *loc_tri, *loc_slot;
+    TermConsts<T> c;
+};
+
+// store / load one Local of K edge coordinates at index i of a
+// structure-of-arrays buffer of n entries
+template <int K, typename T>
+__device__ __forceinline__ void store_local_soa(const Local<T, K> &e, T *buf, int64_t i, int64_t n, bool ok)
+{
+    buf[i] = ok ? e.f : T(NAN);
+#pragma unroll
+    for (int k = 0; k < K; ++k) buf[(1 + k) * n + i] = e.g[k];
+#pragma unroll
+    for (int k = 0; k < K * (K + 1) / 2; ++k) buf[(1 + K + k) * n + i] = e.H[k];
+}
+template <int K, typename T>
+__device__ __forceinline__ void load_local_soa(Local<T, K> &e, const T *buf, int64_t i, int64_t n)
+{
+    e.f = buf[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) e.g[k] = buf[(1 + k) * n + i];
+#pragma unroll
+    for (int k = 0; k < K * (K + 1) / 2; ++k) e.H[k] = buf[(1 + K + k) * n + i];
+}
+
+template <typename T, int ENERGY>
+__global__ void __launch_bounds__(128) k_filtered_tris(LocalArgs<T> A)
+{
+    constexpr int VD = TriTraits<ENERGY>::VD;
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= A.nU) return;
+    T x[3 * VD];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int64_t v = A.tri_verts[3 * u + q];
+#pragma unroll
+        for (int d = 0; d < VD; ++d) x[q * VD + d] = A.x[v * VD + d];
+    }
+    T D[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nU + u];
+    const T area = A.tri_rest[4 * A.nU + u];
+    EdgeLocal<TriEdges, VD, T> L;
+    const bool ok = tri_term<T, ENERGY, true>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * u : nullptr);
+    store_local_soa(L.e, A.loc_tri, u, A.nU, ok);
+}
+
+// slots: hinges (ENERGY != ADM_MASS_SPRING) or springs
+template <typename T, int ENERGY>
+__global__ void __launch_bounds__(128) k_filtered_slots(LocalArgs<T> A)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= A.nS) return;
+    const int4 v = A.slot_verts[s];
+    const int32_t vv[4] = {v.x, v.y, v.z, v.w};
+    if constexpr (ENERGY == ADM_MASS_SPRING) {
+        T x[6];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) x[q * 3 + d] = A.x[(int64_t)vv[q] * 3 + d];
+        EdgeLocal<SpringEdges, 3, T> L;
+        spring_local<T, true>(x, A.slot_rest[s], A.c.kh2, L, A.c.eps);
+        store_local_soa(L.e, A.loc_slot, s, A.nS, isfinite(local_f(L)));
+    } else {
+        if (v.w < 0) return;  // no hinge on this slot's edge
+        T x[12];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) x[q * 3 + d] = A.x[(int64_t)vv[q] * 3 + d];
+        const T thetabar = A.slot_rest[s];
+        const T w = A.c.kbh2 * A.slot_rest[A.nS + s];
+        EdgeLocal<HingeEdges, 3, T> L;
+        const bool ok = hinge_local<T, true>(x, thetabar, w, L, A.c.eps) && isfinite(local_f(L));
+        store_local_soa(L.e, A.loc_slot, s, A.nS, ok);
+    }
+}
+
 // ------------------------------------------------------------- kernel --
 // resident blocks per SM the register budget is sized for: FP32 tiles run
 // 512 threads per SM at 128 registers (two blocks of 256 or four of 128);
-// FP64 and filtered tiles one block of 256 with the full register file
+// FP64 tiles one block of 256 with the full register file.  Filtered tiles
+// read their terms' filtered results (k_filtered_tris, k_filtered_slots), so
+// they have the budget of plain ones.
 template <typename T, bool PROJ, int THREADS>
-constexpr int tile_min_blocks() { return (sizeof(T) == 4 && !PROJ) ? 512 / THREADS : 1; }
+constexpr int tile_min_blocks() { return sizeof(T) == 4 ? 512 / THREADS : 1; }
 
 template <typename T, int ENERGY, bool TRIS, bool HINGES, int MODE, int THREADS, bool PROJ>
 __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())) k_tiled(TiledArgs<T> A)
@@ -289,7 +386,14 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                 for (int k = 0; k < 4; ++k) D[k] = A.tri_rest[k * A.nU + u];
                 const T area = A.tri_rest[4 * A.nU + u];
                 EdgeLocal<TriEdges, VD, T> L;
-                if (tri_term<T, ENERGY, PROJ>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * u : nullptr)) {
+                bool ok;
+                if constexpr (PROJ) {  // the filtered result of k_filtered_tris
+                    load_local_soa(L.e, A.loc_tri, u, A.nU);
+                    ok = isfinite(L.e.f);
+                } else {
+                    ok = tri_term<T, ENERGY, false>(x, D, area, A.c, L, A.mlp_table ? A.mlp_table + 10 * u : nullptr);
+                }
+                if (ok) {
                     fe += (double)local_f(L);
                     if constexpr (MODE >= MODE_GRAD) {
                         if constexpr (MODE == MODE_HVP) {
@@ -343,7 +447,14 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                     const T thetabar = A.slot_rest[sg];
                     const T w = A.c.kbh2 * A.slot_rest[A.nS + sg];
                     EdgeLocal<HingeEdges, 3, T> L;
-                    if (!(hinge_local<T, PROJ>(x, thetabar, w, L, A.c.eps) && isfinite(local_f(L)))) {
+                    bool ok;
+                    if constexpr (PROJ) {  // the filtered result of k_filtered_slots
+                        load_local_soa(L.e, A.loc_slot, sg, A.nS);
+                        ok = isfinite(L.e.f);
+                    } else {
+                        ok = hinge_local<T, false>(x, thetabar, w, L, A.c.eps) && isfinite(local_f(L));
+                    }
+                    if (!ok) {
                         atomicOr(A.status, ST_DOMAIN);
                         if constexpr (MODE >= MODE_GRAD) {  // its own chunks still need values
                             const uint16_t *sd = A.slot_dst + 4 * sg;
@@ -403,7 +514,8 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                         for (int d = 0; d < 3; ++d) x[q * 3 + d] = xs[sl[q] * 3 + d];
                     const int64_t sg = (int64_t)slot0 + ufirst + s;
                     EdgeLocal<SpringEdges, 3, T> L;
-                    spring_local<T, PROJ>(x, A.slot_rest[sg], A.c.kh2, L, A.c.eps);
+                    if constexpr (PROJ) load_local_soa(L.e, A.loc_slot, sg, A.nS);
+                    else spring_local<T, false>(x, A.slot_rest[sg], A.c.kh2, L, A.c.eps);
                     if (!isfinite(local_f(L))) {
                         atomicOr(A.status, ST_DOMAIN);
                         continue;
@@ -651,12 +763,12 @@ void launch_tiled_threads(int energy, int n_sm, size_t smem, cudaStream_t s, con
 // Launch of one (precision, mode, filtering) variant for any energy.  Each
 // variant is instantiated in its own translation unit (tiled_inst.cu) so
 // that they compile in parallel.  Grid: the resident blocks of the whole GPU
-// (persistent), at most one per tile.  FP32 without filtering also has a
-// 128-thread variant (ADM_OPT_TILE_THREADS, the autotuner's second axis).
+// (persistent), at most one per tile.  FP32 also has a 128-thread variant
+// (ADM_OPT_TILE_THREADS, the autotuner's second axis).
 template <typename T, int MODE, bool PROJ>
 void launch_tiled_mode(int energy, int threads, int n_sm, size_t smem, cudaStream_t s, const TiledArgs<T> &A)
 {
-    if constexpr (sizeof(T) == 4 && !PROJ) {
+    if constexpr (sizeof(T) == 4) {
         if (threads == 128) {
             launch_tiled_threads<T, MODE, PROJ, 128>(energy, n_sm, smem, s, A);
             return;
@@ -683,6 +795,25 @@ static void launch_tiled(int energy, int mode, bool proj, int threads, int n_sm,
     else if (mode == MODE_HESS) launch_tiled_mode<T, MODE_HESS, true>(energy, threads, n_sm, smem, s, A);
     else if (!proj) launch_tiled_mode<T, MODE_HVP, false>(energy, threads, n_sm, smem, s, A);
     else launch_tiled_mode<T, MODE_HVP, true>(energy, threads, n_sm, smem, s, A);
+}
+
+// buffers of the terms' filtered results, sized for FP64 (the largest
+// Local: 55 reals per hinge, 28 per triangle), allocated on first use
+inline adm_status ensure_filtered_locals(adm_ctx *h, TileSet &ts)
+{
+    if (ts.d_loc_tri && ts.d_loc_slot) return ADM_OK;
+    const size_t nu = (size_t)std::max<int64_t>(h->m.nT, 1), ns = (size_t)std::max<int64_t>(ts.n_slots, 1);
+    if (cudaMalloc(&ts.d_loc_tri, nu * 28 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ts.d_loc_slot, ns * 55 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ts.d_loc_tri);
+        cudaFree(ts.d_loc_slot);
+        ts.d_loc_tri = ts.d_loc_slot = nullptr;
+        return ADM_ERR_OOM;
+    }
+    h->owned.push_back(ts.d_loc_tri);
+    h->owned.push_back(ts.d_loc_slot);
+    return ADM_OK;
 }
 
 template <typename T>
@@ -746,7 +877,8 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     }
-    const bool split = a.n_split > 0 && a.split_mesh && a.split_ready && !pairs && a.energy != ADM_MLP_MEMBRANE &&
+    const bool filt = h->proj != 0 && (mode == MODE_HESS || mode == MODE_HVP);
+    const bool split = a.n_split > 0 && a.split_mesh && a.split_ready && !pairs && a.energy != ADM_MLP_MEMBRANE && !filt &&
                        h->split_stream[0] && h->split_stream[1] && h->split_start &&
                        (int)h->split_done.size() >= a.n_split && a.n_split <= 8;
     if (a.n_split > 0 && !split)  // x arriving in ranges, consumed whole here: wait for all of them
@@ -765,6 +897,45 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
         tm.end(ADM_STAGE_ZERO);
     }
     tm.begin(ADM_STAGE_TILED);
+    A.loc_tri = A.loc_slot = nullptr;
+    if (filt) {
+        // every term's filtered result first, one thread per term
+        adm_status st = ensure_filtered_locals(h, ts);
+        if (st != ADM_OK) return st;
+        LocalArgs<T> F;
+        F.nU = m.nT;
+        F.nS = ts.n_slots;
+        F.tri_verts = ts.d_tri_verts;
+        F.slot_verts = reinterpret_cast<const int4 *>(ts.d_slot_verts);
+        F.tri_rest = A.tri_rest;
+        F.slot_rest = A.slot_rest;
+        F.x = A.x;
+        F.mlp_table = A.mlp_table;
+        F.loc_tri = (T *)ts.d_loc_tri;
+        F.loc_slot = (T *)ts.d_loc_slot;
+        F.c = A.c;
+        const int bt = (int)((F.nU + 127) / 128), bs = (int)((F.nS + 127) / 128);
+        const bool tris = a.energy != ADM_HINGE_BENDING && a.energy != ADM_MASS_SPRING;
+        if (tris && F.nU > 0) {
+            switch (a.energy) {
+            case ADM_SYMDIR2D: k_filtered_tris<T, ADM_SYMDIR2D><<<bt, 128, 0, s>>>(F); break;
+            case ADM_STVK_MEMBRANE: k_filtered_tris<T, ADM_STVK_MEMBRANE><<<bt, 128, 0, s>>>(F); break;
+            case ADM_NH_MEMBRANE: k_filtered_tris<T, ADM_NH_MEMBRANE><<<bt, 128, 0, s>>>(F); break;
+            case ADM_AREA: k_filtered_tris<T, ADM_AREA><<<bt, 128, 0, s>>>(F); break;
+            case ADM_MLP_MEMBRANE:
+                if constexpr (sizeof(T) == 4) k_filtered_tris<T, ADM_MLP_MEMBRANE><<<bt, 128, 0, s>>>(F);
+                break;
+            case ADM_SHELL: k_filtered_tris<T, ADM_SHELL><<<bt, 128, 0, s>>>(F); break;
+            default: break;
+            }
+        }
+        if (F.nS > 0) {
+            if (hin) k_filtered_slots<T, ADM_SHELL><<<bs, 128, 0, s>>>(F);
+            else if (a.energy == ADM_MASS_SPRING) k_filtered_slots<T, ADM_MASS_SPRING><<<bs, 128, 0, s>>>(F);
+        }
+        A.loc_tri = F.loc_tri;
+        A.loc_slot = F.loc_slot;
+    }
     if (!split) {
         A.next = ts.d_sync;
         A.tile_begin = 0;

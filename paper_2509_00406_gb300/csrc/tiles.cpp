@@ -323,7 +323,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         std::vector<int32_t> foot;
         std::vector<uint16_t> unit, unit_dst, slot_dst;
         std::vector<int32_t> slot_hinge;            // per slot
-        std::vector<std::array<int32_t, 2>> slot_v; // per slot: its edge (for spring data)
+        std::vector<std::array<int32_t, 4>> slot_v; // per slot: t_k, t_k+1, t_k+2, extra (-1: none)
         std::vector<int32_t> rows;                  // kRowWords per footprint row (shared fields later)
         std::vector<uint32_t> codes;
         std::vector<uint64_t> pair_keys;            // produced unordered pairs (global key)
@@ -391,7 +391,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         o.unit_dst.assign(6 * un.size(), 0xffff);
         o.slot_dst.assign(4 * (size_t)slot, 0xffff);
         o.slot_hinge.assign(slot, -1);
-        o.slot_v.assign(slot, {-1, -1});
+        o.slot_v.assign(slot, {-1, -1, -1, -1});
         std::vector<int32_t> vseg_start(o.foot.size(), 0), vseg_n(o.foot.size(), 0);
         for (size_t c = 0; c < vr.size(); ++c) {
             const VRec &r = vr[c];
@@ -424,7 +424,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
             for (int s = 0; s < u.nslot; ++s) {
                 const int k = (u.rot + s) % 3;
                 o.slot_hinge[slot_first[i] + s] = u.hinge[s];
-                o.slot_v[slot_first[i] + s] = {u.t[k], u.t[(k + 1) % 3]};
+                o.slot_v[slot_first[i] + s] = {u.t[k], u.t[(k + 1) % 3], u.t[(k + 2) % 3], u.extra[s]};
             }
         }
         // rows: BSR row start, vertex segment, diagonal block; pair codes,
@@ -662,6 +662,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
         ts.slot_dst.insert(ts.slot_dst.end(), o.slot_dst.begin(), o.slot_dst.end());
         for (size_t s = 0; s < o.slot_hinge.size(); ++s) {
             ts.slot_edge.push_back(o.slot_hinge[s]);
+            ts.slot_verts.insert(ts.slot_verts.end(), o.slot_v[s].begin(), o.slot_v[s].end());
             const int32_t h = o.slot_hinge[s];
             if (h >= 0) {
                 ts.slot_rest.push_back(m.h_thetabar[h]);
