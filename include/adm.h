@@ -98,7 +98,7 @@ typedef enum {
                                  Sec. 5.5 scheme, kept as a reference path)    */
     ADM_OPT_TILE_TRIS = 2,    /* units (triangles with their attached hinges or
                                  springs) per tile of the tiled assembler,
-                                 1..4096; 0 (default): 224, lowered for small
+                                 1..4096; 0 (default): 192, lowered for small
                                  meshes to about nT / 304 (two tiles per SM),
                                  never below 32; tiles are split further until
                                  their shared memory fits */

@@ -323,6 +323,36 @@ class MLP:
                                   float(beta2), float(eps), _stream(stream)), "adm_mlp_adam")
 
     @staticmethod
+    def train(theta, norm, I, psi, dpsi, steps=20000, batch=8192, beta=4.0, lr0=3e-3, lr_end=3e-5, seed=0,
+              stream=None):
+        """Adam on the Sobolev loss (energy + beta * gradient) over the
+        samples (I, psi, dpsi), theta updated in place: `steps` batches of
+        `batch` samples drawn without replacement, reshuffled every epoch
+        (seeded), learning rate decaying geometrically from lr0 to lr_end.
+        Every step runs the library's kernels (adm_mlp_loss_grad,
+        adm_mlp_adam); returns the first and the last batch loss."""
+        import torch
+        n = I.shape[0]
+        m, v, grad = torch.zeros_like(theta), torch.zeros_like(theta), torch.zeros_like(theta)
+        ws = torch.zeros(MLP.workspace_size() // 4 + 1, dtype=torch.float32, device=theta.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=theta.device)
+        gen = torch.Generator(device=theta.device).manual_seed(seed)
+        perm = torch.randperm(n, device=theta.device, generator=gen)
+        first = None
+        for step in range(1, steps + 1):
+            o = (step - 1) * batch % n
+            if o + batch > n:  # a new epoch
+                perm = torch.randperm(n, device=theta.device, generator=gen)
+                o = 0
+            idx = perm[o:o + batch]
+            MLP.loss_grad(theta, norm, I[idx].contiguous(), psi[idx].contiguous(), dpsi[idx].contiguous(), beta,
+                          loss, grad, ws, stream)
+            MLP.adam(theta, m, v, grad, step, lr0 * (lr_end / lr0) ** (step / steps), stream=stream)
+            if step == 1:
+                first = loss.item()
+        return first, loss.item()
+
+    @staticmethod
     def nh_targets(F, E, nu, I, psi, dpsi, stream=None):
         _check(lib().adm_mlp_nh_targets(F.shape[0], _ptr(F), float(E), float(nu), _ptr(I), _ptr(psi), _ptr(dpsi),
                                         _stream(stream)), "adm_mlp_nh_targets")

@@ -152,7 +152,7 @@ adm_status ensure_shell(adm_ctx *h)
     return build_pattern(h, PAT_SHELL);
 }
 
-// units (triangles) per tile: the option, else 224 (two blocks per SM in
+// units (triangles) per tile: the option, else 192 (two blocks per SM in
 // FP32, one in FP64) shrunk for small meshes so that there are about two
 // tiles per SM of the 152, never below 32; the builder splits tiles further
 // until they fit shared memory
@@ -160,7 +160,7 @@ int tile_tris_for(const adm_ctx *h)
 {
     if (h->tile_tris > 0) return h->tile_tris;
     const int64_t per = h->m.nT / (2 * 152);
-    return (int)std::min<int64_t>(224, std::max<int64_t>(32, per));
+    return (int)std::min<int64_t>(192, std::max<int64_t>(32, per));
 }
 
 // device arrays of a tile set (freed before a rebuild)
