@@ -268,9 +268,13 @@ __global__ void __launch_bounds__(128) k_filtered_tris(LocalArgs<T> A)
     store_local_soa(L.e, A.loc_tri, u, A.nU, ok);
 }
 
-// slots: hinges (ENERGY != ADM_MASS_SPRING) or springs
+// slots: hinges (ENERGY != ADM_MASS_SPRING) or springs.  Blocks of 256,
+// two per SM: the 9x9 eigensolve then runs at 128 registers with part of
+// its eigenvectors spilled to L1-resident local memory, 16 warps per SM;
+// unbounded it takes 240 registers and runs 8 warps, 17 % slower on the
+// shell batch
 template <typename T, int ENERGY>
-__global__ void __launch_bounds__(128) k_filtered_slots(LocalArgs<T> A)
+__global__ void __launch_bounds__(256, 2) k_filtered_slots(LocalArgs<T> A)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= A.nS) return;
@@ -914,7 +918,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
         F.loc_tri = (T *)ts.d_loc_tri;
         F.loc_slot = (T *)ts.d_loc_slot;
         F.c = A.c;
-        const int bt = (int)((F.nU + 127) / 128), bs = (int)((F.nS + 127) / 128);
+        const int bt = (int)((F.nU + 127) / 128);
         const bool tris = a.energy != ADM_HINGE_BENDING && a.energy != ADM_MASS_SPRING;
         if (tris && F.nU > 0) {
             switch (a.energy) {
@@ -930,8 +934,9 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
             }
         }
         if (F.nS > 0) {
-            if (hin) k_filtered_slots<T, ADM_SHELL><<<bs, 128, 0, s>>>(F);
-            else if (a.energy == ADM_MASS_SPRING) k_filtered_slots<T, ADM_MASS_SPRING><<<bs, 128, 0, s>>>(F);
+            if (hin) k_filtered_slots<T, ADM_SHELL><<<(int)((F.nS + 255) / 256), 256, 0, s>>>(F);
+            else if (a.energy == ADM_MASS_SPRING)
+                k_filtered_slots<T, ADM_MASS_SPRING><<<(int)((F.nS + 255) / 256), 256, 0, s>>>(F);
         }
         A.loc_tri = F.loc_tri;
         A.loc_slot = F.loc_slot;
