@@ -8,10 +8,11 @@
 //   u = (I - m_I) / s_I,  z1 = W1 u + b1,  a1 = silu(z1),
 //   z2 = W2 a1 + b2,      a2 = silu(z2),   y = w3 . a2 + b3,
 //   psi = s_psi y + m_psi;  W1 64x3, W2 64x64, silu(z) = z sigma(z).
-// Forward mode carries 10 channels per sample through the network: the value,
-// the 3 tangents along u and the 6 second-order terms.  The 64x64 contraction
-// of every channel runs on the tensor cores (mma.sync m16n8k16, BF16 inputs,
-// FP32 accumulation), one warp per 16 samples; everything elementwise is FP32.
+// Each sample's value, 3 tangents along u and 6 second-order terms come from
+// forward mode for the value and the tangents and one reverse contraction for
+// the second-order part (forward over reverse, warp_forward8).  The 64x64
+// contractions run on the tensor cores (mma.sync m16n8k16, BF16 inputs, FP32
+// accumulation), one warp per 8 samples; everything elementwise is FP32.
 //
 // Training minimises the Sobolev loss on standardised quantities
 //   L = mean (y - ty)^2 + beta mean sum_k (dy/du_k - tg_k)^2
@@ -135,29 +136,40 @@ __device__ __forceinline__ float quad_sum(float v)
     return v;
 }
 
-// Forward mode through the network for 8 samples per warp, all in registers.
-// The hidden layer runs transposed, z2^T = W2 a1^T: W2 (64 x 64, row = output
-// unit) is the A operand, read from shared memory, and the 10 channels of the
-// activations a1^T (64 units x 8 samples) are B operands built by the lanes
-// themselves.  Lane (g, t) takes sample g: it evaluates layer 1 for units
-// 16 kt + 2 t + {0, 1, 8, 9}, exactly the rows of its B fragments, and after
-// the contraction holds every channel of z2 for units 16 mt + g + {0, 8} and
-// samples 2 t + {0, 1}, so the second-order chain rule through the second
-// SiLU stays in the lane.  Output sums over units close with shuffles.
+// Forward mode through the network for 8 samples per warp.  The value and
+// the 3 tangents along u are carried forward: the hidden layer runs
+// transposed, z2^T = W2 a1^T, with W2 (64 x 64, row = output unit) the A
+// operand from shared memory and the 4 channels of a1^T (64 units x 8
+// samples) B operands built by the lanes themselves.  Lane (g, t) takes
+// sample g: it evaluates layer 1 for units 16 kt + 2 t + {0, 1, 8, 9},
+// exactly the rows of its B fragments, and after the contraction holds every
+// channel of z2 for units 16 mt + g + {0, 8} and samples 2 t + {0, 1}.
+// The 6 second-order terms split as
+//   d2y/du_k du_l = sum_m w3_m [silu''(z2_m) dz2_m/du_k dz2_m/du_l
+//                               + silu'(z2_m) d2z2_m/du_k du_l],
+// and the second part is sum_n r_n silu''(z1_n) W1_nk W1_nl with
+// r = W2^T rho, rho_m = w3_m silu'(z2_m): one reverse contraction (W2^T is
+// the A operand, rho the B operand) instead of carrying 6 second-order
+// channels through W2.  rho and silu''(z1) pass between lanes through the
+// warp's slab ws (2 x 64 x 8 floats, [unit][sample]).  Output sums over
+// units close with shuffles.
 // u: standardised input of sample g = lane / 4.  y[n][c]: channel c of sample
 // 2 t + n (value, dy/du_k, upper Hessian uu00, uu01, uu11, uu02, uu12, uu22),
 // identical in the 8 lanes of a column t.
-__device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)[3], float (&y)[2][10])
+__device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)[3], float (&y)[2][10], float *ws)
 {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     constexpr int K2[6] = {0, 0, 1, 0, 1, 2}, L2[6] = {0, 1, 1, 2, 2, 2};
-    // layer 1 -> B fragments: b[kt][c][0] = units 16kt + 2t, +1; [1] = +8, +9
-    uint32_t b[4][10][2];
+    float *s2v = ws, *rho = ws + H * 8;  // [unit][sample]
+    __syncwarp();                         // the previous samples' reads of the slab are done
+    // layer 1 -> B fragments of the value and the tangents: b[kt][c][0] =
+    // units 16kt + 2t, +1; [1] = +8, +9; silu''(z1) of each unit to the slab
+    uint32_t b[4][4][2];
 #pragma unroll
     for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            float v[2][10];
+            float v[2][4];
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
                 const int i = 16 * kt + 2 * t + 8 * h + o;
@@ -165,15 +177,14 @@ __device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)
                 const float z = S.b1[i] + w0 * u[0] + w1 * u[1] + w2 * u[2];
                 float sg, s0, s1, s2;
                 silu_all(z, sg, s0, s1, s2);
-                const float wk[3] = {w0, w1, w2};
                 v[o][0] = s0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) v[o][1 + k] = s1 * wk[k];
-#pragma unroll
-                for (int m = 0; m < 6; ++m) v[o][4 + m] = s2 * wk[K2[m]] * wk[L2[m]];
+                v[o][1] = s1 * w0;
+                v[o][2] = s1 * w1;
+                v[o][3] = s1 * w2;
+                s2v[i * 8 + g] = s2;
             }
 #pragma unroll
-            for (int c = 0; c < 10; ++c) b[kt][c][h] = pack_bf16(v[0][c], v[1][c]);
+            for (int c = 0; c < 4; ++c) b[kt][c][h] = pack_bf16(v[0][c], v[1][c]);
         }
 #pragma unroll
     for (int n = 0; n < 2; ++n)
@@ -181,9 +192,9 @@ __device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)
         for (int c = 0; c < 10; ++c) y[n][c] = 0.0f;
 #pragma unroll 1
     for (int mt = 0; mt < 4; ++mt) {
-        float acc[10][4];
+        float acc[4][4];
 #pragma unroll
-        for (int c = 0; c < 10; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[c][q] = 0.0f;
 #pragma unroll
@@ -194,7 +205,7 @@ __device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)
             const uint32_t a2 = *reinterpret_cast<const uint32_t *>(w + 8);
             const uint32_t a3 = *reinterpret_cast<const uint32_t *>(w + 8 * LDW + 8);
 #pragma unroll
-            for (int c = 0; c < 10; ++c)
+            for (int c = 0; c < 4; ++c)
                 asm volatile(
                     "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                     "{%0,%1,%2,%3};\n"
@@ -202,7 +213,8 @@ __device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)
                     : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b[kt][c][0]), "r"(b[kt][c][1]));
         }
         // layer 2 and the output layer for units j = 16 mt + g + 8 (q >> 1),
-        // samples 2 t + (q & 1)
+        // samples 2 t + (q & 1): value, tangents, the first second-order
+        // part; rho of the unit to the slab
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = 16 * mt + g + 8 * (q >> 1), n = q & 1;
@@ -214,7 +226,40 @@ __device__ __forceinline__ void warp_forward8(const MlpSmem &S, const float (&u)
 #pragma unroll
             for (int k = 0; k < 3; ++k) y[n][1 + k] += w * s1 * d[k];
 #pragma unroll
-            for (int m = 0; m < 6; ++m) y[n][4 + m] += w * (s2 * d[K2[m]] * d[L2[m]] + s1 * acc[4 + m][q]);
+            for (int m = 0; m < 6; ++m) y[n][4 + m] += w * s2 * d[K2[m]] * d[L2[m]];
+            rho[j * 8 + 2 * t + n] = w * s1;
+        }
+    }
+    __syncwarp();  // rho and silu''(z1) of all units and samples are in the slab
+    // reverse contraction r = W2^T rho (rows: layer-1 units n = 16 nt + g +
+    // 8 (q >> 1); columns: samples 2 t + (q & 1)), then the second part of
+    // the second-order terms
+#pragma unroll 1
+    for (int nt = 0; nt < 4; ++nt) {
+        float r[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            const __nv_bfloat16 *w = S.W2T + (16 * nt + g) * LDW + 16 * kt + 2 * t;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(w);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(w + 8 * LDW);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(w + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(w + 8 * LDW + 8);
+            const int m0 = 16 * kt + 2 * t;
+            const uint32_t b0 = pack_bf16(rho[m0 * 8 + g], rho[(m0 + 1) * 8 + g]);
+            const uint32_t b1 = pack_bf16(rho[(m0 + 8) * 8 + g], rho[(m0 + 9) * 8 + g]);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(r[0]), "+f"(r[1]), "+f"(r[2]), "+f"(r[3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = 16 * nt + g + 8 * (q >> 1), n = q & 1;
+            const float p = r[q] * s2v[i * 8 + 2 * t + n];
+            const float wk[3] = {S.W1[3 * i], S.W1[3 * i + 1], S.W1[3 * i + 2]};
+#pragma unroll
+            for (int m = 0; m < 6; ++m) y[n][4 + m] += p * wk[K2[m]] * wk[L2[m]];
         }
     }
     // sum over the 8 lanes g of each column t
@@ -265,6 +310,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_mlp_eval(const float *th, con
                                                           const float *I, float *out)
 {
     __shared__ MlpSmem S;
+    __shared__ float slab[WARPS][2 * H * 8];
     load_params(S, th, norm);
     __syncthreads();
     const int w = threadIdx.x >> 5, g = (threadIdx.x & 31) >> 2;
@@ -274,7 +320,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_mlp_eval(const float *th, con
 #pragma unroll
         for (int k = 0; k < 3; ++k) u[k] = s < n ? (I[3 * s + k] - S.norm[k]) / S.norm[3 + k] : 0.0f;
         float y[2][10];
-        warp_forward8(S, u, y);
+        warp_forward8(S, u, y, slab[w]);
         store_unstandardised(S, y, base, n, out);
     }
 }
@@ -623,25 +669,42 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_mlp_tri(const float *th, cons
                                                          float *table)
 {
     __shared__ MlpSmem S;
+    __shared__ float slab[WARPS][2 * H * 8];
     load_params(S, th, norm);
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2;
-    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 8; base < nT; base += (int64_t)gridDim.x * WARPS * 8) {
+    const int64_t stride = (int64_t)gridDim.x * WARPS * 8;
+    // lanes 0..7 load the positions and rest data of triangle base + lane;
+    // the next iteration's are loaded while the network runs
+    auto load = [&](int64_t bb, float (&xv)[9], float (&D)[4]) {
+        const int64_t p = bb + (lane & 7);
+        if (lane < 8 && p < nT) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t v = verts[3 * p + c];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * v + d];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) D[k] = rest[k * nT + p];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) xv[k] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) D[k] = 0.0f;
+        }
+    };
+    float xv[9], D[4];
+    load(((int64_t)blockIdx.x * WARPS + w) * 8, xv, D);
+    for (int64_t base = ((int64_t)blockIdx.x * WARPS + w) * 8; base < nT; base += stride) {
         // lanes 0..7 form the invariants of triangles base + lane
         float uu[3] = {0.0f, 0.0f, 0.0f};
-        const int64_t p = base + (lane & 7);
-        if (lane < 8 && p < nT) {
-            float xv[9];
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * (int64_t)verts[3 * p + c] + d];
-            const float D0 = rest[p], D1 = rest[nT + p], D2 = rest[2 * nT + p], D3 = rest[3 * nT + p];
+        if (lane < 8 && base + lane < nT) {
             float c11 = 0.0f, c22 = 0.0f, c12 = 0.0f;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const float u1 = xv[3 + d] - xv[d], w1 = xv[6 + d] - xv[d];
-                const float f1 = u1 * D0 + w1 * D2, f2 = u1 * D1 + w1 * D3;
+                const float f1 = u1 * D[0] + w1 * D[2], f2 = u1 * D[1] + w1 * D[3];
                 c11 += f1 * f1;
                 c22 += f2 * f2;
                 c12 += f1 * f2;
@@ -651,11 +714,12 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_mlp_tri(const float *th, cons
 #pragma unroll
             for (int k = 0; k < 3; ++k) uu[k] = (I3[k] - S.norm[k]) / S.norm[3 + k];
         }
+        load(base + stride, xv, D);
         float u[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) u[k] = __shfl_sync(0xffffffffu, uu[k], g);
         float y[2][10];
-        warp_forward8(S, u, y);
+        warp_forward8(S, u, y, slab[w]);
         store_unstandardised(S, y, base, nT, table);
     }
 }
