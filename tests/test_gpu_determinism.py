@@ -79,3 +79,58 @@ def test_hvp_and_gradient_modes_bit_identical():
     # the gradient-only pass and the H v pass sum the same segments
     assert np.array_equal(res[0][1], res[0][3])
     m.close()
+
+
+def test_filtered_passes_bit_identical():
+    """With per-term filtering the terms' filtered results pass through HBM
+    to the tiled kernel; two passes still agree bit for bit."""
+    b = _batch()
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    m.set_projection(True, 0.0)
+    _, nV, nnzb, _, _ = m.pattern(adm.SHELL)
+    x = torch.from_numpy(b.x.astype(np.float32)).cuda()
+    outs = []
+    for rep in range(2):
+        e = torch.zeros(m.n_mesh, dtype=torch.float64, device="cuda")
+        g = torch.full((nV * 3,), float("nan"), device="cuda")
+        H = torch.full((nnzb * 9,), float("nan"), device="cuda")
+        m.eval_batch(adm.SHELL, adm.FP32, x, e, None, g, H)
+        torch.cuda.synchronize()
+        assert m.status() == 0
+        outs.append([t.cpu().numpy() for t in (e, g, H)])
+    for a, c in zip(*outs):
+        assert not np.isnan(a).any()
+        assert np.array_equal(a.view(np.uint8), c.view(np.uint8))
+    m.close()
+
+
+def test_host_buffer_path_matches_device_path():
+    """The host-buffer entry point feeds the batch in mesh ranges on two
+    streams, one tiled launch per range, then the fix-up; every output is the
+    same fixed-order sum as in the single device-resident launch, so the
+    gradient, the BSR Hessian, the per-mesh energies and the norms agree
+    bit for bit."""
+    b = _batch()
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.SHELL, SHELL_P)
+    _, nV, nnzb, _, _ = m.pattern(adm.SHELL)
+    x32 = b.x.astype(np.float32)
+    e = torch.zeros(m.n_mesh, dtype=torch.float64, device="cuda")
+    gn = torch.zeros_like(e)
+    g = torch.zeros(nV * 3, device="cuda")
+    H = torch.zeros(nnzb * 9, device="cuda")
+    m.eval_batch(adm.SHELL, adm.FP32, torch.from_numpy(x32).cuda(), e, gn, g, H)
+    torch.cuda.synchronize()
+    xh = torch.from_numpy(x32.reshape(-1).copy()).pin_memory()
+    eh = torch.zeros(m.n_mesh, dtype=torch.float64).pin_memory()
+    gnh = torch.zeros_like(eh).pin_memory()
+    gh = torch.full((nV * 3,), float("nan")).pin_memory()
+    Hh = torch.full((nnzb * 9,), float("nan")).pin_memory()
+    m.eval_batch_host(adm.SHELL, adm.FP32, xh.numpy(), eh.numpy(), gnh.numpy(), gh.numpy(), Hh.numpy())
+    assert m.status() == 0
+    for dev, host in ((e, eh), (gn, gnh), (g, gh), (H, Hh)):
+        a, c = dev.cpu().numpy(), host.numpy()
+        assert not np.isnan(c).any()
+        assert np.array_equal(a.view(np.uint8), c.view(np.uint8))
+    m.close()
