@@ -93,9 +93,14 @@ typedef enum { ADM_FP64 = 0, ADM_FP32 = 1 } adm_precision;
 
 /* Options for adm_set_option(). */
 typedef enum {
-    ADM_OPT_ASSEMBLER = 1,    /* 0 = tiled (shared-memory patches, default),
+    ADM_OPT_ASSEMBLER = 1,    /* 0 = tiled (default): shared-memory tiles,
+                                 every contribution staged and each output
+                                 summed in a fixed order, no float atomics,
+                                 so two passes on the same input give
+                                 bit-identical gradients, Hessians and H v;
                                  1 = per-element atomic scatter (the paper's
-                                 Sec. 5.5 scheme, kept as a reference path)    */
+                                 Sec. 5.5 scheme, kept as a reference path;
+                                 its sums depend on thread timing)           */
     ADM_OPT_TILE_TRIS = 2,    /* units (triangles with their attached hinges or
                                  springs) per tile of the tiled assembler,
                                  1..4096; 0 (default): 192, lowered for small
@@ -256,7 +261,10 @@ adm_status adm_eval(adm_handle h, adm_energy energy, adm_precision prec, const v
  * run on the tiled kernel whatever ADM_OPT_ASSEMBLER says.  Clamping acts on
  * the spectrum of the term as a function of its vertex positions; the three
  * translations, exact zeros of every term here, are left alone.  Errors:
- * ADM_ERR_ARG.  Drops captured graphs when the setting changes. */
+ * ADM_ERR_ARG.  Drops captured graphs when the setting changes.  The first
+ * filtered Hessian or H v pass allocates, per tile set, a buffer of every
+ * term's filtered result (28 doubles per triangle, 55 per attached edge;
+ * 3.8 GB for 4.3M triangles): ADM_ERR_OOM if that fails. */
 adm_status adm_set_projection(adm_handle h, int32_t enable, double eps);
 
 /* Matrix-free Hessian-vector product (the paper's matrix-free mode,
