@@ -792,7 +792,10 @@ def run_ours(args, rank: int, world: int, local: int):
     kern = {k: v for k, v in prof.items() if k != "zero" and v[1] > 0}
     dom = max(kern, key=lambda k: kern[k][0] * kern[k][1])
     dom_ms = kern[dom][0]
-    launches_per_step = sum(v[1] for v in kern.values()) / args.steps
+    # kernels per stage entry: the tiled stage launches k_tiled and, when the
+    # batch has outputs several tiles share (it does), k_tile_fixup
+    per_stage = {"tiled": 2}
+    launches_per_step = sum(v[1] * per_stage.get(k, 1) for k, v in kern.items()) / args.steps
     if args.assembler == 1:
         launches_per_step += prof["zero"][1] / args.steps   # the atomic scatter's zero fill
     peak, peak_src = measured_peaks()
