@@ -191,6 +191,8 @@ enum TileHdr {
 // (hi, lo) in row hi; for a partial block, row << 9 | position is its index
 // in the tile's slot table.
 constexpr int kRowWords = 4;
+// footprint rows of one tile at most (the row fields of the pair codes are 9 bits)
+constexpr int kMaxFootRows = 512;
 
 // vertex-pair interaction terms and the block pattern they extend (dyn.cu;
 // Sec. 4.3, Sec. 6.3, Alg. 1)
@@ -349,15 +351,18 @@ ADM_TILE_HD constexpr int chunk_floats(int mode, int vd, bool pair)
                                : 0;
 }
 // one tile's dynamic shared memory (byte offsets): x of the footprint, v
-// (matrix-free mode), vertex chunks, pair chunks, the metadata blob
+// (matrix-free mode), vertex chunks, pair chunks, the metadata blob.  The x
+// and v regions are sized by nf_cap, the largest footprint of the tile set,
+// so that every tile places its chunks after them: the kernel stages the
+// next tile's x while the current tile's chunks are still being summed.
 struct TileLayout {
     int32_t off_vs, off_sv, off_sp, off_blob, total;
 };
-ADM_TILE_HD TileLayout tile_layout(int nf, int nvc, int npc, int meta_bytes, int mode, int vd, int eb)
+ADM_TILE_HD TileLayout tile_layout(int nf_cap, int nvc, int npc, int meta_bytes, int mode, int vd, int eb)
 {
     auto a16 = [](int b) { return (b + 15) & ~15; };
     TileLayout L;
-    const int xs = nf * vd * eb;
+    const int xs = nf_cap * vd * eb;
     L.off_vs = a16(xs);
     L.off_sv = a16(L.off_vs + (mode == MODE_HVP ? xs : 0));
     L.off_sp = a16(L.off_sv + nvc * chunk_floats(mode, vd, false) * eb);

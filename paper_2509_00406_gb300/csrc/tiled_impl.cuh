@@ -10,6 +10,9 @@
 // input give bit-identical results.
 #pragma once
 
+#include <climits>
+#include <type_traits>
+
 #include "device_common.cuh"
 
 namespace adm {
@@ -34,6 +37,7 @@ struct TiledArgs {
     int32_t *next;                    // work queue position of this launch
     T *vpart, *ppart;                 // partial slots of shared outputs: Chunk<MODE_HESS, VD>::V, VD^2 each
     int32_t tile_begin, tile_end;     // this launch's tiles
+    int32_t nf_cap;                   // largest footprint of the tile set (rows of the x region)
     double *epart;                    // per tile
     int *status;
     TermConsts<T> c;
@@ -164,6 +168,60 @@ __device__ __forceinline__ void put_vertices(const LT &L, T *const (&vch)[NV], c
         else put_vertex<MODE, VD, A, ADD>(L, vch[A]);
     });
 }
+
+// ------------------------------------------------------- row stores --
+// store N consecutive reals from registers to global memory whose start is
+// aligned to one real: in aligned pairs where the run allows (a 3x3 FP32
+// block at 36 b bytes takes one single and four pair stores instead of
+// nine single ones, whichever parity b has)
+template <int N, typename T>
+__device__ __forceinline__ void store_run(T *dst, const T *v)
+{
+    using V2 = std::conditional_t<sizeof(T) == 4, float2, double2>;
+    if constexpr (N == 1) {
+        dst[0] = v[0];
+    } else if constexpr (N > 1) {
+        const bool odd = ((reinterpret_cast<uintptr_t>(dst) / sizeof(T)) & 1u) != 0;
+        if constexpr (N % 2 == 1) {
+            // odd start: the first real alone, then pairs; even start: pairs,
+            // then the last real alone
+            dst[odd ? 0 : N - 1] = odd ? v[0] : v[N - 1];
+            V2 *p = reinterpret_cast<V2 *>(dst + (odd ? 1 : 0));
+#pragma unroll
+            for (int j = 0; j < (N - 1) / 2; ++j) {
+                V2 w;
+                w.x = odd ? v[2 * j + 1] : v[2 * j];
+                w.y = odd ? v[2 * j + 2] : v[2 * j + 1];
+                p[j] = w;
+            }
+        } else if (!odd) {
+            V2 *p = reinterpret_cast<V2 *>(dst);
+#pragma unroll
+            for (int j = 0; j < N / 2; ++j) {
+                V2 w;
+                w.x = v[2 * j];
+                w.y = v[2 * j + 1];
+                p[j] = w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) dst[j] = v[j];
+        }
+    }
+}
+
+// one real global -> shared without passing through registers (cp.async);
+// the copies of a thread are complete after cp_async_wait_all
+template <typename T>
+__device__ __forceinline__ void cp_async_real(T *dst, const T *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ------------------------------------------------------------ waits --
 __device__ __forceinline__ void bar_init(uint64_t *bar)
@@ -319,43 +377,75 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
     constexpr int VD = TriTraits<ENERGY>::VD;
     constexpr int CV = Chunk<MODE, VD>::V, CP = Chunk<MODE, VD>::P;
     constexpr bool CLOTH = ENERGY == ADM_MASS_SPRING;
+    constexpr int NW = THREADS / 32;
+    constexpr int KR = (kMaxFootRows + THREADS - 1) / THREADS;  // footprint rows a thread stages
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t meta_bar;
-    __shared__ int s_tile;
+    __shared__ int s_next;
+    __shared__ double s_red[NW];
     const int tid = threadIdx.x;
+    // x (and v) of the footprint sit in a region of fixed size, below every
+    // tile's chunks, so the next tile's rows land there while the current
+    // tile's chunks are summed
     T *xs = reinterpret_cast<T *>(smem_raw);
+    T *vsm = reinterpret_cast<T *>(smem_raw + tile_layout(A.nf_cap, 0, 0, 0, MODE, VD, (int)sizeof(T)).off_vs);
+    // x (and v) rows of tile t into the fixed region: cp.async, no registers;
+    // completed by cp_async_wait_all before the barrier that opens the tile
+    auto stage_rows = [&](int t, const int32_t (&fv)[KR]) {
+        const int nf = A.hdr[kHdr * (int64_t)t + kHdrNF];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int i = tid + k * THREADS;
+            if (i >= nf) break;
+            const int64_t v = fv[k];
+#pragma unroll
+            for (int d = 0; d < VD; ++d) cp_async_real(xs + VD * i + d, A.x + v * VD + d);
+            if constexpr (MODE == MODE_HVP)
+#pragma unroll
+                for (int d = 0; d < VD; ++d) cp_async_real(vsm + VD * i + d, A.v + v * VD + d);
+        }
+    };
+    auto foot_rows = [&](int t, int32_t (&fv)[KR]) {
+        const int32_t *hd = A.hdr + kHdr * (int64_t)t;
+        const int fb = hd[kHdrFoot], nf = hd[kHdrNF];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int i = tid + k * THREADS;
+            fv[k] = i < nf ? A.foot[fb + i] : 0;
+        }
+    };
     if (MODE >= MODE_GRAD && tid == 0) bar_init(&meta_bar);
+    if (tid == 0) s_next = A.tile_begin + atomicAdd(A.next, 1);
     __syncthreads();
     uint32_t phase = 0;
-    const int32_t cap = A.tile_end - A.tile_begin + 1;  // every iteration takes one queue position
-    int32_t iter = 0;
-    for (; iter < cap; ++iter) {
-        if (tid == 0) s_tile = A.tile_begin + atomicAdd(A.next, 1);
+    // every queue position taken is bounded by the tile count + 1; a block
+    // that takes that many without the queue running dry reports a timeout
+    const int32_t cap = A.tile_end - A.tile_begin + 1;
+    int32_t taken = 1;
+    int t = s_next;
+    if (t < A.tile_end) {
+        int32_t fv[KR];
+        foot_rows(t, fv);
+        stage_rows(t, fv);
+        cp_async_wait_all();
+    }
+    while (t < A.tile_end) {
+        // x of tile t is staged; the previous tile's chunks, blob and
+        // partial energies are no longer read
         __syncthreads();
-        const int t = s_tile;
-        if (t >= A.tile_end) break;
         const int32_t *hd = A.hdr + kHdr * (int64_t)t;
         const int32_t u0 = hd[kHdrUnit], nu = hd[kHdrNUnit], slot0 = hd[kHdrSlot];
         const int32_t fb = hd[kHdrFoot], nf = hd[kHdrNF];
         const int64_t m0 = A.meta_off[t];
         const int32_t meta_bytes = (int32_t)(A.meta_off[t + 1] - m0);
-        const TileLayout lay = tile_layout(nf, hd[kHdrNVC], hd[kHdrNPC], meta_bytes, MODE, VD, (int)sizeof(T));
-        T *vsm = reinterpret_cast<T *>(smem_raw + lay.off_vs);
+        const TileLayout lay = tile_layout(A.nf_cap, hd[kHdrNVC], hd[kHdrNPC], meta_bytes, MODE, VD, (int)sizeof(T));
         T *sv = reinterpret_cast<T *>(smem_raw + lay.off_sv);
         T *sp = reinterpret_cast<T *>(smem_raw + lay.off_sp);
         unsigned char *blob = smem_raw + lay.off_blob;
-        if (MODE >= MODE_GRAD && tid == 0) {
-            bulk_copy_start(&meta_bar, blob, A.meta + m0, (uint32_t)meta_bytes);
+        if (tid == 0) {
+            if (MODE >= MODE_GRAD) bulk_copy_start(&meta_bar, blob, A.meta + m0, (uint32_t)meta_bytes);
+            s_next = taken < cap ? A.tile_begin + atomicAdd(A.next, 1) : INT_MAX;
         }
-        for (int i = tid; i < nf; i += THREADS) {
-            const int64_t v = A.foot[fb + i];
-#pragma unroll
-            for (int d = 0; d < VD; ++d) xs[VD * i + d] = A.x[v * VD + d];
-            if (MODE == MODE_HVP)
-#pragma unroll
-                for (int d = 0; d < VD; ++d) vsm[VD * i + d] = A.v[v * VD + d];
-        }
-        __syncthreads();
 
         // ---- units: evaluate, stage contributions in their chunks
         double fe = 0.0;
@@ -572,7 +662,16 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                 }
             }
         }
+        // per-warp energy partials, summed in warp order after the barrier
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fe += __shfl_down_sync(0xffffffffu, fe, o);
+        if ((tid & 31) == 0) s_red[tid >> 5] = fe;
+        // chunks complete, the next tile known, x of this tile no longer read
         __syncthreads();
+        const int tn = s_next;
+        ++taken;
+        int32_t fvn[KR];
+        if (tn < A.tile_end) foot_rows(tn, fvn);  // the loads land while the vertex pass runs
 
         // ---- gather: every output entry is the sum of its segment
         bool meta_ok = true;
@@ -604,117 +703,178 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
 #pragma unroll
                     for (int e = 0; e < CV; ++e) acc[e] += src[CV * q + e];
                 if ((rw.w >> 15) & 1) {  // a later producer of a shared row
-                    T *p = A.vpart + (int64_t)ptab[rw.w >> 16] * CVH;
-#pragma unroll
-                    for (int e = 0; e < CV; ++e) p[e] = acc[e];
+                    store_run<CV>(A.vpart + (int64_t)ptab[rw.w >> 16] * CVH, acc);
                     continue;
                 }
                 const int64_t vg = A.foot[fb + r];
-                if (A.grad) {
-                    T *g = A.grad + vg * VD;
-#pragma unroll
-                    for (int d = 0; d < VD; ++d) g[d] = acc[d];
-                }
-                if constexpr (MODE == MODE_HVP) {
-                    T *y = A.hv + vg * VD;
-#pragma unroll
-                    for (int d = 0; d < VD; ++d) y[d] = acc[VD + d];
-                }
+                if (A.grad) store_run<VD>(A.grad + vg * VD, acc);
+                if constexpr (MODE == MODE_HVP) store_run<VD>(A.hv + vg * VD, acc + VD);
                 if constexpr (MODE == MODE_HESS) {
-                    T *out = A.bsr + ((int64_t)rw.x + (rw.w & 0x7fff)) * (VD * VD);
+                    T blk[VD * VD];
 #pragma unroll
                     for (int i = 0; i < VD; ++i)
 #pragma unroll
-                        for (int j = 0; j < VD; ++j) out[i * VD + j] = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
-                }
-            }
-            if constexpr (MODE == MODE_HESS) {
-                // pair pass: one lane per pair segment; the lane sums the
-                // segment in chunk order once, then writes block A = (lo, hi)
-                // and its transpose, block B = (hi, lo), each to the BSR or to
-                // its partial slot
-                constexpr int NB = VD * VD;
-                const int npair = hd[kHdrNCode];
-                const uint2 *pc = reinterpret_cast<const uint2 *>(codes);
-                for (int j = tid; j < npair; j += THREADS) {
-                    const uint2 c = pc[j];
-                    const int start = (int)(c.x & 0x1fffu), cnt = (int)((c.x >> 13) & 15u);
-                    T acc[NB];
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) acc[k] = -T(0);
-                    const T *src = sp + CP * start;
-                    for (int q = 0; q < cnt; ++q)
-#pragma unroll
-                        for (int k = 0; k < NB; ++k) acc[k] += src[CP * q + k];
-                    const uint32_t da = ((c.x >> 19) & 511u) << 9 | (c.y & 511u);
-                    const uint32_t db = ((c.y >> 9) & 511u) << 9 | ((c.y >> 18) & 511u);
-                    T *oa = (c.x >> 17) & 1u ? A.ppart + (int64_t)ptab[da] * NB
-                                             : A.bsr + ((int64_t)rows[kRowWords * (da >> 9)] + (da & 511u)) * NB;
-                    T *ob = (c.x >> 18) & 1u ? A.ppart + (int64_t)ptab[db] * NB
-                                             : A.bsr + ((int64_t)rows[kRowWords * (db >> 9)] + (db & 511u)) * NB;
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) oa[k] = acc[k];
-#pragma unroll
-                    for (int i = 0; i < VD; ++i)
-#pragma unroll
-                        for (int k = 0; k < VD; ++k) ob[i * VD + k] = acc[k * VD + i];
+                        for (int j = 0; j < VD; ++j) blk[i * VD + j] = acc[VD + (i <= j ? hix(i, j) : hix(j, i))];
+                    store_run<VD * VD>(A.bsr + ((int64_t)rw.x + (rw.w & 0x7fff)) * (VD * VD), blk);
                 }
             }
         }
-        const double sum = block_sum<THREADS>(fe);
-        if (tid == 0) A.epart[t] = sum;
-        __syncthreads();
+        // x (and v) of the next tile into the fixed region; eval of this tile
+        // is over, and the region lies below this tile's chunks and blob
+        if (tn < A.tile_end) stage_rows(tn, fvn);
+        if (MODE == MODE_HESS && meta_ok) {
+            // pair pass: one lane per pair segment; the lane sums the
+            // segment in chunk order once, then writes block A = (lo, hi)
+            // and its transpose, block B = (hi, lo), each to the BSR or to
+            // its partial slot
+            constexpr int NB = VD * VD;
+            const int npair = hd[kHdrNCode];
+            const uint2 *pc = reinterpret_cast<const uint2 *>(codes);
+            for (int j = tid; j < npair; j += THREADS) {
+                const uint2 c = pc[j];
+                const int start = (int)(c.x & 0x1fffu), cnt = (int)((c.x >> 13) & 15u);
+                T acc[NB];
+#pragma unroll
+                for (int k = 0; k < NB; ++k) acc[k] = -T(0);
+                const T *src = sp + CP * start;
+                for (int q = 0; q < cnt; ++q)
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) acc[k] += src[CP * q + k];
+                const uint32_t da = ((c.x >> 19) & 511u) << 9 | (c.y & 511u);
+                const uint32_t db = ((c.y >> 9) & 511u) << 9 | ((c.y >> 18) & 511u);
+                T *oa = (c.x >> 17) & 1u ? A.ppart + (int64_t)ptab[da] * NB
+                                         : A.bsr + ((int64_t)rows[kRowWords * (da >> 9)] + (da & 511u)) * NB;
+                T *ob = (c.x >> 18) & 1u ? A.ppart + (int64_t)ptab[db] * NB
+                                         : A.bsr + ((int64_t)rows[kRowWords * (db >> 9)] + (db & 511u)) * NB;
+                T tr[NB];
+#pragma unroll
+                for (int i = 0; i < VD; ++i)
+#pragma unroll
+                    for (int k = 0; k < VD; ++k) tr[i * VD + k] = acc[k * VD + i];
+                store_run<NB>(oa, acc);
+                store_run<NB>(ob, tr);
+            }
+        }
+        if (tid == 0) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) sum += s_red[w];
+            A.epart[t] = sum;
+        }
+        cp_async_wait_all();
+        t = tn;
     }
-    if (iter == cap) atomicOr(A.status, ST_TIMEOUT);  // the queue never ran dry within its bound
+    if (t == INT_MAX && tid == 0) atomicOr(A.status, ST_TIMEOUT);  // the queue never ran dry within its bound
 }
 
-// Fix-up of the outputs several tiles produce: one thread per output float
-// adds the output's partial slots, in tile order, to what the lowest tile
-// stored.  Entries: row vertex, position of the block in its BSR row (row
-// start from the active pattern's row pointer), number of slots, first
-// slot; vertex outputs (gradient row, H v row or diagonal block: W floats
-// each) take threads [0, n_v W), pair blocks the next n_p VD^2.  Entries and
-// slots are in output order, so consecutive threads touch consecutive floats.
+// N consecutive reals from global memory into registers, in aligned pairs
+// where the run allows (the loads of store_run)
+template <int N, typename T>
+__device__ __forceinline__ void load_run(const T *src, T *v)
+{
+    using V2 = std::conditional_t<sizeof(T) == 4, float2, double2>;
+    if constexpr (N == 1) {
+        v[0] = src[0];
+    } else if constexpr (N > 1) {
+        const bool odd = ((reinterpret_cast<uintptr_t>(src) / sizeof(T)) & 1u) != 0;
+        if constexpr (N % 2 == 1) {
+            const T one = src[odd ? 0 : N - 1];
+            const V2 *p = reinterpret_cast<const V2 *>(src + (odd ? 1 : 0));
+            T w[N - 1];
+#pragma unroll
+            for (int j = 0; j < (N - 1) / 2; ++j) {
+                const V2 q = p[j];
+                w[2 * j] = q.x;
+                w[2 * j + 1] = q.y;
+            }
+            // odd start: one, w[0..N-2]; even start: w[0..N-2], one
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                if (j == 0) v[0] = odd ? one : w[0];
+                else if (j == N - 1) v[N - 1] = odd ? w[N - 2] : one;
+                else v[j] = odd ? w[j - 1] : w[j];
+            }
+        } else if (!odd) {
+            const V2 *p = reinterpret_cast<const V2 *>(src);
+#pragma unroll
+            for (int j = 0; j < N / 2; ++j) {
+                const V2 q = p[j];
+                v[2 * j] = q.x;
+                v[2 * j + 1] = q.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = src[j];
+        }
+    }
+}
+
+// Fix-up of the outputs several tiles produce: one thread per output (a
+// gradient or H v row with its diagonal block, or a pair block) adds the
+// output's partial slots, in tile order, to what the lowest tile stored;
+// each float is the stored value plus its slots in slot order.  Entries:
+// row vertex, position of the block in its BSR row (row start from the
+// active pattern's row pointer), number of slots, first slot; vertex
+// entries take threads [0, n_v), pair entries the next n_p.  Entries and
+// slots are in output order, so neighbouring threads read neighbouring
+// slots.
 template <typename T, int VD, int MODE>
-__global__ void k_tile_fixup(const int4 *__restrict__ fix_v, int64_t n_v, const int4 *__restrict__ fix_p, int64_t n_p,
-                             const T *__restrict__ vpart, const T *__restrict__ ppart,
-                             const int32_t *__restrict__ row_ptr, T *grad, T *bsr, T *hv)
+__global__ void __launch_bounds__(256) k_tile_fixup(const int4 *__restrict__ fix_v, int64_t n_v,
+                                                    const int4 *__restrict__ fix_p, int64_t n_p,
+                                                    const T *__restrict__ vpart, const T *__restrict__ ppart,
+                                                    const int32_t *__restrict__ row_ptr, T *grad, T *bsr, T *hv)
 {
     constexpr int CVH = Chunk<MODE_HESS, VD>::V, NB = VD * VD;
-    constexpr int W = MODE == MODE_HESS ? VD + NB : (MODE == MODE_HVP ? 2 * VD : VD);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_v * W) {
-        const int64_t ei = i / W;
-        const int k = (int)(i - ei * W);
-        const int4 e = __ldg(fix_v + ei);
-        T *out;
-        int src;  // float of the vertex chunk this output float sums
-        if (k < VD) {
-            if (!grad) return;
-            out = grad + (int64_t)e.x * VD + k;
-            src = k;
-        } else if (MODE == MODE_HVP) {
-            out = hv + (int64_t)e.x * VD + (k - VD);
-            src = k;
-        } else {
-            const int r = (k - VD) / VD, c = (k - VD) % VD;
-            out = bsr + ((int64_t)__ldg(row_ptr + e.x) + e.y) * NB + (k - VD);
-            src = VD + (r <= c ? hix(r, c) : hix(c, r));
+    if (i < n_v) {
+        const int4 e = __ldg(fix_v + i);
+        const T *p = vpart + (int64_t)e.w * CVH;
+        if (grad) {
+            T *out = grad + (int64_t)e.x * VD;
+            T a[VD];
+            load_run<VD>(out, a);
+            for (int q = 0; q < e.z; ++q)
+#pragma unroll
+                for (int d = 0; d < VD; ++d) a[d] += p[(int64_t)q * CVH + d];
+            store_run<VD>(out, a);
         }
-        const T *p = vpart + (int64_t)e.w * CVH + src;
-        T a = *out;
-        for (int q = 0; q < e.z; ++q) a += p[(int64_t)q * CVH];
-        *out = a;
-    } else if (MODE == MODE_HESS && i < n_v * W + n_p * NB) {
-        const int64_t j = i - n_v * W;
-        const int64_t ei = j / NB;
-        const int k = (int)(j - ei * NB);
-        const int4 e = __ldg(fix_p + ei);
-        T *out = bsr + ((int64_t)__ldg(row_ptr + e.x) + e.y) * NB + k;
-        const T *p = ppart + (int64_t)e.w * NB + k;
-        T a = *out;
-        for (int q = 0; q < e.z; ++q) a += p[(int64_t)q * NB];
-        *out = a;
+        if constexpr (MODE == MODE_HVP) {
+            T *out = hv + (int64_t)e.x * VD;
+            T a[VD];
+            load_run<VD>(out, a);
+            for (int q = 0; q < e.z; ++q)
+#pragma unroll
+                for (int d = 0; d < VD; ++d) a[d] += p[(int64_t)q * CVH + VD + d];
+            store_run<VD>(out, a);
+        }
+        if constexpr (MODE == MODE_HESS) {
+            T *out = bsr + ((int64_t)__ldg(row_ptr + e.x) + e.y) * NB;
+            T a[NB];
+            load_run<NB>(out, a);
+            for (int q = 0; q < e.z; ++q) {
+                T u[VD * (VD + 1) / 2];
+#pragma unroll
+                for (int k = 0; k < VD * (VD + 1) / 2; ++k) u[k] = p[(int64_t)q * CVH + VD + k];
+#pragma unroll
+                for (int r = 0; r < VD; ++r)
+#pragma unroll
+                    for (int c = 0; c < VD; ++c) a[r * VD + c] += u[r <= c ? hix(r, c) : hix(c, r)];
+            }
+            store_run<NB>(out, a);
+        }
+    } else if (MODE == MODE_HESS && i < n_v + n_p) {
+        const int4 e = __ldg(fix_p + (i - n_v));
+        T *out = bsr + ((int64_t)__ldg(row_ptr + e.x) + e.y) * NB;
+        const T *p = ppart + (int64_t)e.w * NB;
+        T a[NB];
+        load_run<NB>(out, a);
+        for (int q = 0; q < e.z; ++q) {
+            T u[NB];
+            load_run<NB>(p + (int64_t)q * NB, u);
+#pragma unroll
+            for (int k = 0; k < NB; ++k) a[k] += u[k];
+        }
+        store_run<NB>(out, a);
     }
 }
 
@@ -863,6 +1023,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     A.ppart = (T *)ts.d_ppart;
     A.epart = h->d_epart;
     A.status = h->d_status;
+    A.nf_cap = (int32_t)std::max<int64_t>(ts.max_nf, 1);
     A.c = consts<T>(h, a.energy);
     A.mlp_table = nullptr;
     A.xhat = (const T *)h->d_xhat[a.prec];
@@ -974,8 +1135,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
     const int64_t n_fp = mode == MODE_HESS ? (int64_t)ts.fix_p.size() / 4 : 0;
     if (n_fv + n_fp > 0) {
         const int32_t *rp = active_row_ptr(h, kind);
-        const int wv = mode == MODE_HESS ? vd + vd * vd : (mode == MODE_HVP ? 2 * vd : vd);
-        const int blocks = (int)((n_fv * wv + n_fp * vd * vd + 255) / 256);
+        const int blocks = (int)((n_fv + n_fp + 255) / 256);
         const int4 *fv = reinterpret_cast<const int4 *>(ts.d_fix_v), *fp = reinterpret_cast<const int4 *>(ts.d_fix_p);
         const T *vp = (const T *)ts.d_vpart, *pp = (const T *)ts.d_ppart;
         auto go = [&](auto kern) { kern<<<blocks, 256, 0, s>>>(fv, n_fv, fp, n_fp, vp, pp, rp, (T *)a.grad, (T *)a.bsr, (T *)a.hv); };

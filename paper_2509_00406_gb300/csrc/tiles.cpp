@@ -104,7 +104,7 @@ int64_t tile_smem_bytes(const TileSet &ts, int mode, int vd, int elem_bytes)
     int64_t best = 0;
     for (int32_t t = 0; t < ts.n_tiles; ++t) {
         const int32_t *hd = &ts.hdr[(size_t)kHdr * t];
-        const TileLayout L = tile_layout(hd[kHdrNF], hd[kHdrNVC], hd[kHdrNPC],
+        const TileLayout L = tile_layout((int)ts.max_nf, hd[kHdrNVC], hd[kHdrNPC],
                                          (int)(ts.meta_off[t + 1] - ts.meta_off[t]), mode, vd, elem_bytes);
         best = std::max<int64_t>(best, L.total);
     }
@@ -128,8 +128,12 @@ int64_t hess_bytes(const TileCount &c, int elem_bytes)
 
 }  // namespace
 
-// FP32 tiles run two blocks per SM (about 112 KB each), FP64 tiles one
-constexpr int64_t kBudget32 = 110 * 1024, kBudget64 = 220 * 1024;
+// FP32 tiles run two blocks per SM (at most about 112 KB each), FP64 tiles
+// one.  A tile's own count takes its x at its own footprint; the kernel
+// sizes that region for the set's largest footprint (kMaxFootRows rows at
+// most, 6 KB in FP32 and 12 KB in FP64 above the tile's own), so the budgets
+// leave that much room
+constexpr int64_t kBudget32 = 104 * 1024, kBudget64 = 208 * 1024;
 
 adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, int tile_units, TileSet &ts)
 {
@@ -287,7 +291,7 @@ adm_status tiles_build(const HostMesh &m, const Pattern &P, bool with_hinges, in
             auto [s0, s1] = stack.back();
             stack.pop_back();
             const TileCount c = count_range(scr[th], s0, s1);
-            const bool fits = hess_bytes(c, 4) <= kBudget32 && hess_bytes(c, 8) <= kBudget64 && c.nf <= 512 &&
+            const bool fits = hess_bytes(c, 4) <= kBudget32 && hess_bytes(c, 8) <= kBudget64 && c.nf <= kMaxFootRows &&
                               c.npc < 8192 && c.nvc < 65536 && c.ncodes < 65536;
             if (!fits) {
                 if (s1 - s0 <= 1) {
