@@ -223,6 +223,17 @@ __device__ __forceinline__ void cp_async_real(T *dst, const T *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// L2 prefetch (bulk, one thread) of the 16-byte aligned part of
+// [p, p + bytes): the start is rounded up and the end down, so nothing
+// outside the range is touched
+__device__ __forceinline__ void l2_prefetch(const void *p, int64_t bytes)
+{
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + (uintptr_t)bytes) & ~uintptr_t(15);
+    if (bytes > 0 && e > a)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((uint32_t)(e - a)) : "memory");
+}
+
 // ------------------------------------------------------------ waits --
 __device__ __forceinline__ void bar_init(uint64_t *bar)
 {
@@ -383,16 +394,23 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
     __shared__ __align__(8) uint64_t meta_bar;
     __shared__ int s_next;
     __shared__ double s_red[NW];
+    // header and metadata span of the current tile and of the next one
+    // (double buffered by tile parity), written by the control thread
+    __shared__ int32_t s_hdr[2][kHdr];
+    __shared__ int64_t s_moff[2][2];
     const int tid = threadIdx.x;
+    // the control thread: the block's last thread, whose warp has no unit
+    // to evaluate unless the tile fills the block
+    constexpr int CTL = THREADS - 1;
     // x (and v) of the footprint sit in a region of fixed size, below every
     // tile's chunks, so the next tile's rows land there while the current
     // tile's chunks are summed
     T *xs = reinterpret_cast<T *>(smem_raw);
     T *vsm = reinterpret_cast<T *>(smem_raw + tile_layout(A.nf_cap, 0, 0, 0, MODE, VD, (int)sizeof(T)).off_vs);
-    // x (and v) rows of tile t into the fixed region: cp.async, no registers;
+    // x (and v) rows of a tile into the fixed region: cp.async, no registers;
     // completed by cp_async_wait_all before the barrier that opens the tile
-    auto stage_rows = [&](int t, const int32_t (&fv)[KR]) {
-        const int nf = A.hdr[kHdr * (int64_t)t + kHdrNF];
+    auto stage_rows = [&](const int32_t *hd, const int32_t (&fv)[KR]) {
+        const int nf = hd[kHdrNF];
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
             const int i = tid + k * THREADS;
@@ -405,8 +423,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
                 for (int d = 0; d < VD; ++d) cp_async_real(vsm + VD * i + d, A.v + v * VD + d);
         }
     };
-    auto foot_rows = [&](int t, int32_t (&fv)[KR]) {
-        const int32_t *hd = A.hdr + kHdr * (int64_t)t;
+    auto foot_rows = [&](const int32_t *hd, int32_t (&fv)[KR]) {
         const int fb = hd[kHdrFoot], nf = hd[kHdrNF];
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
@@ -414,10 +431,42 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
             fv[k] = i < nf ? A.foot[fb + i] : 0;
         }
     };
-    if (MODE >= MODE_GRAD && tid == 0) bar_init(&meta_bar);
-    if (tid == 0) s_next = A.tile_begin + atomicAdd(A.next, 1);
+    // control thread: the header and metadata span of tile t into buffer b,
+    // and an L2 prefetch of what the tile's evaluation and staging read
+    auto fetch_tile = [&](int t, int b) {
+        const int32_t *g = A.hdr + kHdr * (int64_t)t;
+#pragma unroll
+        for (int k = 0; k < kHdr; ++k) s_hdr[b][k] = g[k];
+        const int64_t m0 = A.meta_off[t], m1 = A.meta_off[t + 1];
+        s_moff[b][0] = m0;
+        s_moff[b][1] = m1;
+        const int64_t u0 = g[kHdrUnit], nu = g[kHdrNUnit], sl0 = g[kHdrSlot], ns = g[kHdrNSlot];
+        l2_prefetch(A.unit + 8 * u0, nu * 16);
+        l2_prefetch(A.unit_dst + 6 * u0, nu * 12);
+        if constexpr (TRIS && !PROJ) {
+            if (A.mlp_table) l2_prefetch(A.mlp_table + 10 * u0, nu * 40);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) l2_prefetch(A.tri_rest + k * A.nU + u0, nu * (int64_t)sizeof(T));
+        }
+        if constexpr (HINGES || CLOTH) {
+            l2_prefetch(A.slot_dst + 4 * sl0, ns * 8);
+            if constexpr (!PROJ) {
+                l2_prefetch(A.slot_rest + sl0, ns * (int64_t)sizeof(T));
+                if constexpr (HINGES) l2_prefetch(A.slot_rest + A.nS + sl0, ns * (int64_t)sizeof(T));
+            }
+        }
+        l2_prefetch(A.foot + g[kHdrFoot], (int64_t)g[kHdrNF] * 4);
+        if constexpr (MODE >= MODE_GRAD) l2_prefetch(A.meta + m0, m1 - m0);
+    };
+    if (tid == CTL) {
+        if (MODE >= MODE_GRAD) bar_init(&meta_bar);
+        const int t0 = A.tile_begin + atomicAdd(A.next, 1);
+        s_next = t0;
+        if (t0 < A.tile_end) fetch_tile(t0, 0);
+    }
     __syncthreads();
     uint32_t phase = 0;
+    int p = 0;  // header buffer of the current tile
     // every queue position taken is bounded by the tile count + 1; a block
     // that takes that many without the queue running dry reports a timeout
     const int32_t cap = A.tile_end - A.tile_begin + 1;
@@ -425,26 +474,28 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
     int t = s_next;
     if (t < A.tile_end) {
         int32_t fv[KR];
-        foot_rows(t, fv);
-        stage_rows(t, fv);
+        foot_rows(s_hdr[0], fv);
+        stage_rows(s_hdr[0], fv);
         cp_async_wait_all();
     }
     while (t < A.tile_end) {
         // x of tile t is staged; the previous tile's chunks, blob and
         // partial energies are no longer read
         __syncthreads();
-        const int32_t *hd = A.hdr + kHdr * (int64_t)t;
+        const int32_t *hd = s_hdr[p];
         const int32_t u0 = hd[kHdrUnit], nu = hd[kHdrNUnit], slot0 = hd[kHdrSlot];
         const int32_t fb = hd[kHdrFoot], nf = hd[kHdrNF];
-        const int64_t m0 = A.meta_off[t];
-        const int32_t meta_bytes = (int32_t)(A.meta_off[t + 1] - m0);
+        const int64_t m0 = s_moff[p][0];
+        const int32_t meta_bytes = (int32_t)(s_moff[p][1] - m0);
         const TileLayout lay = tile_layout(A.nf_cap, hd[kHdrNVC], hd[kHdrNPC], meta_bytes, MODE, VD, (int)sizeof(T));
         T *sv = reinterpret_cast<T *>(smem_raw + lay.off_sv);
         T *sp = reinterpret_cast<T *>(smem_raw + lay.off_sp);
         unsigned char *blob = smem_raw + lay.off_blob;
-        if (tid == 0) {
+        if (tid == CTL) {
             if (MODE >= MODE_GRAD) bulk_copy_start(&meta_bar, blob, A.meta + m0, (uint32_t)meta_bytes);
-            s_next = taken < cap ? A.tile_begin + atomicAdd(A.next, 1) : INT_MAX;
+            const int tn = taken < cap ? A.tile_begin + atomicAdd(A.next, 1) : INT_MAX;
+            s_next = tn;
+            if (tn < A.tile_end) fetch_tile(tn, p ^ 1);
         }
 
         // ---- units: evaluate, stage contributions in their chunks
@@ -671,7 +722,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
         const int tn = s_next;
         ++taken;
         int32_t fvn[KR];
-        if (tn < A.tile_end) foot_rows(tn, fvn);  // the loads land while the vertex pass runs
+        if (tn < A.tile_end) foot_rows(s_hdr[p ^ 1], fvn);  // the loads land while the vertex pass runs
 
         // ---- gather: every output entry is the sum of its segment
         bool meta_ok = true;
@@ -721,7 +772,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
         }
         // x (and v) of the next tile into the fixed region; eval of this tile
         // is over, and the region lies below this tile's chunks and blob
-        if (tn < A.tile_end) stage_rows(tn, fvn);
+        if (tn < A.tile_end) stage_rows(s_hdr[p ^ 1], fvn);
         if (MODE == MODE_HESS && meta_ok) {
             // pair pass: one lane per pair segment; the lane sums the
             // segment in chunk order once, then writes block A = (lo, hi)
@@ -763,6 +814,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
         }
         cp_async_wait_all();
         t = tn;
+        p ^= 1;
     }
     if (t == INT_MAX && tid == 0) atomicOr(A.status, ST_TIMEOUT);  // the queue never ran dry within its bound
 }
