@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip graph/MLP/secondary measurements")
+    ap.add_argument("--mlp-net", type=int, default=1, choices=[0, 1],
+                    help="learned-membrane network kernel of --profile-case mlp: 0 mma.sync, 1 tcgen05")
     ap.add_argument("--profile-case", choices=["mlp", "filtered", "hvp"], default=None,
                     help="run a few passes of one secondary case on the first --meshes meshes and exit "
                          "(a small workload for ncu)")
@@ -497,6 +499,19 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
     H1 = torch.zeros(nnzb_t * 9, dtype=torch.float32, device="cuda")
     e2, g2, H2 = torch.zeros_like(e1), torch.zeros_like(g1), torch.zeros_like(H1)
     m.set_option(adm.OPT_PROFILE, steps)
+    # both network kernels: warp-level mma.sync and tcgen05 (TMEM accumulators)
+    nets = {}
+    for net_id, net_name in ((0, "mma_sync"), (1, "tcgen05")):
+        m.set_option(adm.OPT_MLP_NET, net_id)
+        m.set_option(adm.OPT_PROFILE, steps)
+        ms_net = _time_steps(torch, lambda: m.eval_batch(adm.MLP_MEMBRANE, adm.FP32, x, e1, None, g1, H1,
+                                                         stream=stream), steps, stream)
+        prof_net = m.profile_read()
+        assert m.status() == 0
+        nets[net_name] = {"ms_per_step": ms_net, "triangles_per_s": mesh.nT / (ms_net * 1e-3),
+                          "stages_ms": {k: round(v[0], 4) for k, v in prof_net.items() if v[1] > 0}}
+    m.set_option(adm.OPT_MLP_NET, 1)  # the library default
+    m.set_option(adm.OPT_PROFILE, steps)
     ms_mlp = _time_steps(torch, lambda: m.eval_batch(adm.MLP_MEMBRANE, adm.FP32, x, e1, None, g1, H1, stream=stream),
                          steps, stream)
     prof = m.profile_read()
@@ -528,9 +543,10 @@ def measure_extras(args, m, mesh, x, e, gn, g, H, n_el, stream):
                 "batch": "synth.stretched_batch: per mesh x = c + R diag(s) R^T (X - c), s_k ~ U[0.7, 1.4]"}
     nT = mesh.nT
     out["mlp_membrane"] = {
-        "workload": "learned Neo-Hookean membrane (MLP 3-64-64-1, BF16 tensor cores) on the shell batch triangles",
+        "workload": "learned Neo-Hookean membrane (MLP 3-64-64-1, BF16 tensor cores: tcgen05, TMEM accumulators) on the shell batch triangles",
         "value": nT / (ms_mlp * 1e-3), "unit": "triangles/s", "ms_per_step": ms_mlp,
         "stages_ms": {k: round(v[0], 4) for k, v in prof.items() if v[1] > 0},
+        "network_kernels": nets,
         "analytic_nh_ms_per_step": ms_nh, "analytic_nh_triangles_per_s": nT / (ms_nh * 1e-3),
         "rel_err_vs_analytic_nh": {"hessian_fro": relH, "gradient": relg, "energy": relE,
                                    "energy_abs_over_s_psi_area": absE,
@@ -696,6 +712,7 @@ def run_profile_case(args):
         th[4416:4480] = rng.normal(scale=1 / 8, size=64)
         norm = np.array([3.0, 3.0, 1.0, 0.3, 0.5, 0.3, 1e3, 1e3], dtype=np.float32)
         m.mlp_attach(torch.from_numpy(th).cuda(), torch.from_numpy(norm).cuda())
+        m.set_option(adm.OPT_MLP_NET, args.mlp_net)
     else:
         energy = adm.SHELL
         if args.profile_case == "filtered":

@@ -116,7 +116,7 @@ typedef enum {
     ADM_OPT_TILE_THREADS = 6, /* threads per block of the tiled kernel in FP32
                                  without filtering: 128 or 256 (0, default:
                                  256); FP64 and filtered passes use 256 */
-    ADM_OPT_GRAPH = 5         /* 1: adm_eval / adm_eval_batch capture their
+    ADM_OPT_GRAPH = 5,        /* 1: adm_eval / adm_eval_batch capture their
                                  whole pass (zero-fill, element kernel,
                                  reductions) into a CUDA graph on the first call
                                  with a given (energy, precision, buffers) tuple
@@ -126,6 +126,16 @@ typedef enum {
                                  library stream, the replay on the caller's
                                  stream.  Changing parameters or options drops
                                  the captured graphs. */
+    ADM_OPT_MLP_NET = 7       /* network kernel of the learned membrane
+                                 (ADM_MLP_MEMBRANE passes): 1 (default) =
+                                 fifth-generation tensor cores (tcgen05.mma,
+                                 FP32 accumulators in tensor memory), 128
+                                 triangles per MMA tile; 0 = warp-level BF16
+                                 tensor-core MMA (mma.sync), one warp per 8
+                                 triangles.
+                                 Both round weights and activations to BF16
+                                 and accumulate in FP32; their outputs differ
+                                 by the summation order only. */
 } adm_option;
 
 /* Kernel stages reported by adm_profile_read(). */

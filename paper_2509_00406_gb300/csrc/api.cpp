@@ -503,6 +503,11 @@ adm_status adm_set_option(adm_handle h, adm_option option, int64_t value)
         if ((value == 0 ? 256 : (int)value) != h->tile_threads) drop_graphs(h);
         h->tile_threads = value == 0 ? 256 : (int)value;
         return ADM_OK;
+    case ADM_OPT_MLP_NET:  // 0 mma.sync, 1 tcgen05 (the default)
+        if (value != 0 && value != 1) return ADM_ERR_ARG;
+        if ((int)value != h->mlp_net) drop_graphs(h);
+        h->mlp_net = (int)value;
+        return ADM_OK;
     case ADM_OPT_TILE_TRIS:
         if (value != 0 && (value < 1 || value > 4096)) return ADM_ERR_ARG;
         if (value != h->tile_tris)

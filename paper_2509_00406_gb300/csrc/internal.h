@@ -277,6 +277,7 @@ struct adm_ctx {
     int proj = 0;            // per-term Hessian filtering on (adm_set_projection)
     double proj_eps = 0.0;   // value negative local eigenvalues are raised to
     int tile_tris = 0;  // 0: automatic (tile_tris_for)
+    int mlp_net = 1;         // network kernel of the learned membrane: 0 mma.sync, 1 tcgen05 (default)
     int tile_threads = 256;  // threads per block of the FP32 tiled kernel (128 or 256)
     int block_threads = 128;
     // host-buffer path
@@ -433,7 +434,8 @@ adm_status mlp_nh_targets(int64_t n, const float *F, double mu, double lam, floa
 // per-triangle table of the learned membrane in unit order: verts = the
 // units' rotated vertices (3 per unit), rest_tiled = their rest data (SoA)
 adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *verts,
-                              const float *rest_tiled, const float *x, float *table, cudaStream_t s);
+                              const float *rest_tiled, const float *x, float *table, int tc_net, int *status,
+                              cudaStream_t s);
 
 adm_status launch_jacobian(adm_ctx *h, int prec, const void *x, void *r, void *jv, void *jtj,
                            cudaStream_t stream);

@@ -10,9 +10,13 @@
 //   psi = s_psi y + m_psi;  W1 64x3, W2 64x64, silu(z) = z sigma(z).
 // Each sample's value, 3 tangents along u and 6 second-order terms come from
 // forward mode for the value and the tangents and one reverse contraction for
-// the second-order part (forward over reverse, warp_forward8).  The 64x64
-// contractions run on the tensor cores (mma.sync m16n8k16, BF16 inputs, FP32
-// accumulation), one warp per 8 samples; everything elementwise is FP32.
+// the second-order part (forward over reverse).  The 64x64 contractions run
+// on the tensor cores with BF16 inputs and FP32 accumulation, in two forms:
+// k_mlp_tri_tc (the default for the per-triangle table) issues tcgen05.mma
+// on 128-triangle tiles with the accumulators in tensor memory;
+// warp_forward8 (sample evaluation, training, and the table when the
+// mma.sync form is chosen) runs mma.sync m16n8k16, one warp per 8 samples.
+// Everything elementwise is FP32.
 //
 // Training minimises the Sobolev loss on standardised quantities
 //   L = mean (y - ty)^2 + beta mean sum_k (dy/du_k - tg_k)^2
@@ -724,6 +728,300 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_mlp_tri(const float *th, cons
     }
 }
 
+// ---------------------------------------------- tcgen05 network variant --
+// The per-triangle network of k_mlp_tri on the fifth-generation tensor
+// cores: the contractions are tcgen05.mma (kind::f16, BF16 operands from
+// shared memory, FP32 accumulators in tensor memory), issued by one thread
+// and completed on an mbarrier; the elementwise work stays on the FP32 pipes.
+// A tile is 128 triangles (the MMA's M), one TMEM lane per triangle:
+//   1. layer 1 in FP32, its value and 3 tangents written as four BF16 A
+//      operands (128 x 64 each) in the K-major canonical layout;
+//   2. z2 of the 4 channels, D_c = A_c W2^T, into TMEM columns 64 c .. 64 c + 63
+//      (16 MMAs of 128 x 64 x 16);
+//   3. from TMEM: silu of z2 and its derivatives, the value, gradient and
+//      first second-order part, and rho = w3 silu'(z2) written as a BF16 A
+//      operand over channel 0's;
+//   4. r = rho W2 (4 MMAs) into columns 0 .. 63, then the second part
+//      sum_n r_n silu''(z1_n) W1_nk W1_nl.
+// Two threads per triangle: warps w and w + 4 read the same TMEM lanes
+// (a warp reaches lanes 32 (w mod 4) ..); the first takes units 0-31, the
+// second 32-63, and their partial outputs meet in shared memory.
+// Canonical K-major layout without swizzle: element (row, k) at byte
+// (row / 8) 128 + (k / 8) LBO + (row % 8) 16 + (k % 8) 2, i.e. 8 x 16-byte
+// core matrices, row groups 128 bytes apart (the descriptor's SBO), K chunks
+// LBO apart.
+namespace tc {
+constexpr int TILE = 128, THREADS = 256, HALF = H / 2;
+constexpr uint32_t A_LBO = (TILE / 8) * 128, B_LBO = (H / 8) * 128;
+constexpr uint32_t A_BYTES = TILE * H * 2, B_BYTES = H * H * 2;
+constexpr uint32_t SMEM = 4 * A_BYTES + 2 * B_BYTES;  // 80 KB: two blocks per SM, 256 TMEM columns each
+constexpr uint32_t TMEM_COLS = 256;
+// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, N, M
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) | ((uint32_t)(TILE >> 4) << 24);
+
+__device__ __forceinline__ uint32_t canon(int row, int k, uint32_t lbo)
+{
+    return (uint32_t)(row >> 3) * 128u + (uint32_t)(k >> 3) * lbo + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+// shared-memory matrix descriptor: start, LBO, SBO = 128 (bytes >> 4), the
+// descriptor version bit, no swizzle
+__device__ __forceinline__ uint64_t sdesc(const void *p, uint32_t lbo)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | (uint64_t)((lbo >> 4) & 0x3FFFu) << 16 | (uint64_t)(128u >> 4) << 32 |
+           (uint64_t)1 << 46;
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, bool acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                 "l"(a), "l"(b), "r"(IDESC), "r"((uint32_t)acc)
+                 : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t *bar)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b) : "memory");
+}
+// wait for the given phase parity; gives up after about a second
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(b), "r"(parity), "r"(1000u)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+// 8 BF16 values into one 16-byte row piece of a canonical operand
+__device__ __forceinline__ void st8(unsigned char *dst, const float (&v)[8])
+{
+    uint4 w;
+    w.x = pack_bf16(v[0], v[1]);
+    w.y = pack_bf16(v[2], v[3]);
+    w.z = pack_bf16(v[4], v[5]);
+    w.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(dst) = w;
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, const float *norm, int64_t nT,
+                                                                const int32_t *verts, const float *rest,
+                                                                const float *x, float *table, int *status)
+{
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    __shared__ float W1s[H * 3], b1s[H], b2s[H], w3s[H], b3s, norms[8];
+    __shared__ float part[TILE][10];  // the second half's partial outputs
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t taddr_s;
+    unsigned char *Ac = smem_tc;                      // 4 operands: a1, da1/du_0..2 (rho over a1's)
+    unsigned char *Bz = smem_tc + 4 * A_BYTES;        // W2 (rows: layer-2 units, K: layer-1 units)
+    unsigned char *Br = Bz + B_BYTES;                 // W2^T (rows: layer-1 units, K: layer-2 units)
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int row = 32 * (w & 3) + lane;  // this thread's triangle within the tile, its TMEM lane
+    const int u0 = (w >> 2) * HALF;       // first unit of this thread's half
+    // parameters, BF16-rounded as the other kernels use them
+    {
+        const float *W1 = th, *b1 = W1 + H * 3, *W2 = b1 + H, *b2 = W2 + H * H, *w3 = b2 + H, *b3 = w3 + H;
+        for (int k = tid; k < H * H; k += THREADS) {
+            const int i = k / H, j = k % H;
+            const __nv_bfloat16 v = __float2bfloat16(W2[k]);
+            *reinterpret_cast<__nv_bfloat16 *>(Bz + canon(i, j, B_LBO)) = v;
+            *reinterpret_cast<__nv_bfloat16 *>(Br + canon(j, i, B_LBO)) = v;
+        }
+        for (int k = tid; k < H * 3; k += THREADS) W1s[k] = bf16r(W1[k]);
+        for (int k = tid; k < H; k += THREADS) {
+            b1s[k] = bf16r(b1[k]);
+            b2s[k] = bf16r(b2[k]);
+            w3s[k] = bf16r(w3[k]);
+        }
+        if (tid == 0) b3s = bf16r(b3[0]);
+        if (tid < 8) norms[tid] = norm[tid];
+    }
+    if (w == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&taddr_s);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tbase = taddr_s, tlane = tbase + ((uint32_t)(32 * (w & 3)) << 16);
+    constexpr int K2[6] = {0, 0, 1, 0, 1, 2}, L2[6] = {0, 1, 1, 2, 2, 2};
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t t0 = (int64_t)blockIdx.x * TILE; t0 < nT && ok; t0 += (int64_t)gridDim.x * TILE) {
+        const int64_t p = t0 + row;
+        // invariants of triangle p, standardised (zero past the end)
+        float u[3] = {0.0f, 0.0f, 0.0f};
+        if (p < nT) {
+            float xv[9], D[4];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t v = verts[3 * p + c];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) xv[3 * c + d] = x[3 * v + d];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) D[k] = rest[k * nT + p];
+            float c11 = 0.0f, c22 = 0.0f, c12 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float e1 = xv[3 + d] - xv[d], e2 = xv[6 + d] - xv[d];
+                const float f1 = e1 * D[0] + e2 * D[2], f2 = e1 * D[1] + e2 * D[3];
+                c11 += f1 * f1;
+                c22 += f2 * f2;
+                c12 += f1 * f2;
+            }
+            const float i3 = c11 * c22 - c12 * c12;
+            const float I3[3] = {c11 + c22 + 1.0f, i3 + c11 + c22, i3};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) u[k] = (I3[k] - norms[k]) / norms[3 + k];
+        }
+        // 1. layer 1 of this half's units: value and tangents as BF16 operands
+#pragma unroll 1
+        for (int kb = 0; kb < HALF / 8; ++kb) {
+            float v[4][8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int i = u0 + 8 * kb + o;
+                const float wa = W1s[3 * i], wb = W1s[3 * i + 1], wc = W1s[3 * i + 2];
+                float sg, s0, s1, s2;
+                silu_all(b1s[i] + wa * u[0] + wb * u[1] + wc * u[2], sg, s0, s1, s2);
+                v[0][o] = s0;
+                v[1][o] = s1 * wa;
+                v[2][o] = s1 * wb;
+                v[3][o] = s1 * wc;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) st8(Ac + c * A_BYTES + canon(row, u0 + 8 * kb, A_LBO), v[c]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        __syncthreads();
+        // 2. z2 of the four channels
+        if (tid == 0) {
+            fence_after();
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int j = 0; j < H / 16; ++j)
+                    mma(tbase + 64 * c, sdesc(Ac + c * A_BYTES + 2 * j * A_LBO, A_LBO), sdesc(Bz + 2 * j * B_LBO, B_LBO),
+                        j > 0);
+            commit(&bar);
+        }
+        ok = __syncthreads_and(wait(&bar, phase & 1u));
+        ++phase;
+        fence_after();
+        if (!ok) break;
+        // 3. layer 2 and the output layer for this half's units; rho as an operand
+        float y[10];
+#pragma unroll
+        for (int c = 0; c < 10; ++c) y[c] = 0.0f;
+#pragma unroll 1
+        for (int kb = 0; kb < HALF / 8; ++kb) {
+            const int j0 = u0 + 8 * kb;
+            float z[4][8];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ld8(tlane + (uint32_t)(64 * c + j0), z[c]);
+            float rho[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int j = j0 + o;
+                float sg, s0, s1, s2;
+                silu_all(z[0][o] + b2s[j], sg, s0, s1, s2);
+                const float wj = w3s[j], d[3] = {z[1][o], z[2][o], z[3][o]};
+                y[0] += wj * s0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) y[1 + k] += wj * s1 * d[k];
+#pragma unroll
+                for (int m = 0; m < 6; ++m) y[4 + m] += wj * s2 * d[K2[m]] * d[L2[m]];
+                rho[o] = wj * s1;
+            }
+            st8(Ac + canon(row, j0, A_LBO), rho);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_before();
+        __syncthreads();
+        // 4. r = rho W2 (row = triangle, column = layer-1 unit n)
+        if (tid == 0) {
+            fence_after();
+#pragma unroll
+            for (int j = 0; j < H / 16; ++j)
+                mma(tbase, sdesc(Ac + 2 * j * A_LBO, A_LBO), sdesc(Br + 2 * j * B_LBO, B_LBO), j > 0);
+            commit(&bar);
+        }
+        ok = __syncthreads_and(wait(&bar, phase & 1u));
+        ++phase;
+        fence_after();
+        if (!ok) break;
+#pragma unroll 1
+        for (int kb = 0; kb < HALF / 8; ++kb) {
+            const int n0 = u0 + 8 * kb;
+            float r[8];
+            ld8(tlane + (uint32_t)n0, r);
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int n = n0 + o;
+                const float wa = W1s[3 * n], wb = W1s[3 * n + 1], wc = W1s[3 * n + 2];
+                float sg, s0, s1, s2;
+                silu_all(b1s[n] + wa * u[0] + wb * u[1] + wc * u[2], sg, s0, s1, s2);
+                const float q = r[o] * s2, wk[3] = {wa, wb, wc};
+#pragma unroll
+                for (int m = 0; m < 6; ++m) y[4 + m] += q * wk[K2[m]] * wk[L2[m]];
+            }
+        }
+        // the two halves of each triangle meet; the first half stores
+        if (w >= 4)
+#pragma unroll
+            for (int c = 0; c < 10; ++c) part[row][c] = y[c];
+        fence_before();
+        __syncthreads();
+        if (w < 4 && p < nT) {
+            const float sp = norms[7];
+#pragma unroll
+            for (int c = 0; c < 10; ++c) {
+                const float v = y[c] + part[row][c] + (c == 0 ? b3s : 0.0f);
+                float o;
+                if (c == 0) o = sp * v + norms[6];
+                else if (c < 4) o = sp * v / norms[3 + c - 1];
+                else o = sp * v / (norms[3 + K2[c - 4]] * norms[3 + L2[c - 4]]);
+                table[10 * p + c] = o;
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
+    fence_before();
+    __syncthreads();
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
 }  // namespace
 
 // launchers used by api.cpp
@@ -771,8 +1069,21 @@ adm_status mlp_nh_targets(int64_t n, const float *F, double mu, double lam, floa
 }
 
 adm_status mlp_triangle_table(const float *th, const float *norm, int64_t nT, const int32_t *verts,
-                              const float *rest_tiled, const float *x, float *table, cudaStream_t s)
+                              const float *rest_tiled, const float *x, float *table, int tc_net, int *status,
+                              cudaStream_t s)
 {
+    if (tc_net) {
+        // persistent: two blocks per SM (shared memory allows no third, so
+        // the 256 TMEM columns of each always fit)
+        int dev = 0, n_sm = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t blocks = std::min<int64_t>((nT + tc::TILE - 1) / tc::TILE, 2 * (int64_t)n_sm);
+        cudaFuncSetAttribute(k_mlp_tri_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM);
+        if (blocks > 0)
+            k_mlp_tri_tc<<<(unsigned)blocks, tc::THREADS, tc::SMEM, s>>>(th, norm, nT, verts, rest_tiled, x, table,
+                                                                         status);
+        return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;
+    }
     const int64_t blocks = std::min<int64_t>((nT + WARPS * 8 - 1) / (WARPS * 8), 152 * 8);
     if (blocks > 0) k_mlp_tri<<<(unsigned)blocks, WARPS * 32, 0, s>>>(th, norm, nT, verts, rest_tiled, x, table);
     return cudaGetLastError() == cudaSuccess ? ADM_OK : ADM_ERR_CUDA;

@@ -1084,7 +1084,7 @@ adm_status eval_tiled(adm_ctx *h, const EvalArgs &a)
         tm.begin(ADM_STAGE_MLP);
         adm_status st = mlp_triangle_table(h->d_mlp_theta, h->d_mlp_norm, m.nT, ts.d_tri_verts,
                                            (const float *)ts.d_tri_rest[ADM_FP32], (const float *)a.x,
-                                           h->d_mlp_table, s);
+                                           h->d_mlp_table, h->mlp_net, h->d_status, s);
         tm.end(ADM_STAGE_MLP);
         if (st != ADM_OK) return st;
         A.mlp_table = h->d_mlp_table;

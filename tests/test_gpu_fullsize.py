@@ -356,4 +356,13 @@ def test_learned_membrane_batch_700_trained_sampled_meshes(deform):
     bl = np.concatenate([np.arange(P.row_ptr[r], P.row_ptr[r + 1]) for r in rows])
     Hm = H[rp[v0]:rp[v1]]
     assert rel(Hm[bl], ref["vals"][bl]) <= 3e-2
+    # the other network kernel on the whole batch: the same BF16 network,
+    # FP32 contractions summed in another order (mma.sync against tcgen05)
+    m.set_option(adm.OPT_MLP_NET, 1)
+    _, _, e2, _, g2, H2 = batch_eval(m, adm.MLP_MEMBRANE, x32)
+    m.set_option(adm.OPT_MLP_NET, 0)
+    _, _, e0, _, g0, H0 = batch_eval(m, adm.MLP_MEMBRANE, x32)
+    assert rel(e2, e0) <= 2e-3 and rel(H2, H0) <= 2e-3
+    if deform == "in_range":
+        assert rel(g2, g0) <= 2e-3
     m.close()

@@ -180,3 +180,54 @@ def test_mlp_membrane_mesh_matches_oracle():
     assert abs(e.item() - ref["energy"]) <= 3e-2 * abs(ref["energy"])
     assert rel(gd.cpu().numpy().reshape(-1, 3), ref["grad"]) < 3e-2
     assert rel(Hd.cpu().numpy().reshape(-1, 3, 3), ref["vals"]) < 3e-2
+
+
+@pytest.mark.parametrize("net", [0, 1])
+def test_mlp_membrane_batch_both_networks_match_oracle(net):
+    """Both network kernels (0: warp-level mma.sync, 1: tcgen05 with TMEM
+    accumulators, 128 triangles per MMA tile) on a batch whose 1,680
+    triangles span 13 MMA tiles with a ragged last one: each against the
+    oracle's network on the same BF16 weights (3e-2), and the tcgen05 one
+    against the mma.sync one.  The two round the same FP32 activations to
+    BF16 and differ only in the FP32 summation order of the contractions,
+    which can move a BF16 rounding of rho by one unit, so they agree to
+    about 1e-4; the bound is 2e-3."""
+    rng = np.random.default_rng(6)
+    b = synth.shell_batch([1, 2, 3], sigma=2e-2, seed=9)
+    x = b.x.astype(np.float32)
+    _, I, psi, _ = samples(2000, 15)
+    th = init_theta(rng)
+    norm = norm_of(I, psi)
+    m = adm.Mesh(b.rest, b.faces, 3, v_off=b.v_off, f_off=b.f_off)
+    m.set_params(adm.MLP_MEMBRANE, [E, NU, 1e-3])
+    m.mlp_attach(cuda32(th), cuda32(norm))
+    _, nV, nnzb, rp, col = m.pattern(adm.MLP_MEMBRANE)
+    rp = rp.cpu().numpy()
+
+    def run(option):
+        m.set_option(adm.OPT_MLP_NET, option)
+        e = torch.zeros(b.n_mesh, dtype=torch.float64, device="cuda")
+        gd = torch.full((nV * 3,), float("nan"), device="cuda")
+        Hd = torch.full((nnzb * 9,), float("nan"), device="cuda")
+        m.eval_batch(adm.MLP_MEMBRANE, adm.FP32, cuda32(x), e, None, gd, Hd)
+        torch.cuda.synchronize()
+        assert m.status() == 0
+        return e.cpu().numpy(), gd.cpu().numpy().reshape(-1, 3), Hd.cpu().numpy().reshape(-1, 3, 3)
+
+    e, g, H = run(net)
+    assert np.isfinite(H).all() and np.isfinite(g).all()
+    oracle.mlp_set(bf16(th), norm)
+    for k in range(b.n_mesh):
+        v0, v1, f0, f1 = b.v_off[k], b.v_off[k + 1], b.f_off[k], b.f_off[k + 1]
+        P = oracle.Problem(b.rest[v0:v1], b.faces[f0:f1] - v0, oracle.MLP, 3, params=[E, NU, 1e-3])
+        ref = P.assemble(x[v0:v1].astype(np.float64))
+        assert abs(e[k] - ref["energy"]) <= 3e-2 * abs(ref["energy"]), (k, e[k], ref["energy"])
+        assert rel(g[v0:v1], ref["grad"]) < 3e-2
+        assert rel(H[rp[v0]:rp[v1]], ref["vals"]) < 3e-2
+    if net == 1:
+        e0, g0, H0 = run(0)
+        assert rel(e, e0) < 2e-3 and rel(g, g0) < 2e-3 and rel(H, H0) < 2e-3
+        # the same network kernel twice: bit-identical
+        e1, g1, H1 = run(1)
+        assert np.array_equal(e1, e) and np.array_equal(g1, g) and np.array_equal(H1, H)
+    m.close()

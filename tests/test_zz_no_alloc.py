@@ -48,13 +48,19 @@ def test_noalloc_norm_matches_batched_gradient_norm(prec):
     assert ref > 0
     L = adm.lib()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for _ in range(2):   # two calls in a row share the static scratch
-        out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    outs = [torch.full((1,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free = []
+    for out in outs:   # two calls in a row share the static scratch
         s = L.adm_grad_norm_noalloc(C.c_void_p(g.data_ptr()), g.numel(), prec, C.c_void_p(out.data_ptr()),
                                     stream)
         assert s == 0, adm.strerror(s)
         torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
         assert abs(out.item() - ref) <= TOL[prec] * ref
+    # the second call finds its scratch set up by the first and takes no
+    # device memory (the first may load the library's module on this device)
+    assert free[1] == free[0]
     # the norm itself, checked on the host
     assert abs(ref - np.linalg.norm(g.cpu().double().numpy())) <= TOL[prec] * ref
     m.close()
