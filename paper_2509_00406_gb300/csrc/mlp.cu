@@ -800,17 +800,52 @@ __device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity)
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// 8 consecutive FP32 columns of this thread's TMEM lane
+// 8 consecutive FP32 columns of this thread's TMEM lane; the load and its
+// wait in one statement, so that no use of the registers precedes the wait
 __device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8])
 {
     uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr)
                  : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+// 8 columns at each of 4 column offsets (the four channels), one wait
+__device__ __forceinline__ void ld8x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, float (&v)[4][8])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
+        : "memory");
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[c][q] = __uint_as_float(r[8 * c + q]);
+}
+// silu and its first derivative (layer 1 needs no more); its second
+// derivative alone (the reverse part); the formulas of silu_all
+__device__ __forceinline__ void silu01(float z, float &s, float &s1)
+{
+    const float sg = __frcp_rn(1.0f + __expf(-z));
+    s = z * sg;
+    s1 = sg * (1.0f + z * (1.0f - sg));
+}
+__device__ __forceinline__ float silu2(float z)
+{
+    const float sg = __frcp_rn(1.0f + __expf(-z));
+    return sg * (1.0f - sg) * (2.0f + z * (1.0f - 2.0f * sg));
 }
 // 8 BF16 values into one 16-byte row piece of a canonical operand
 __device__ __forceinline__ void st8(unsigned char *dst, const float (&v)[8])
@@ -912,8 +947,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
             for (int o = 0; o < 8; ++o) {
                 const int i = u0 + 8 * kb + o;
                 const float wa = W1s[3 * i], wb = W1s[3 * i + 1], wc = W1s[3 * i + 2];
-                float sg, s0, s1, s2;
-                silu_all(b1s[i] + wa * u[0] + wb * u[1] + wc * u[2], sg, s0, s1, s2);
+                float s0, s1;
+                silu01(b1s[i] + wa * u[0] + wb * u[1] + wc * u[2], s0, s1);
                 v[0][o] = s0;
                 v[1][o] = s1 * wa;
                 v[2][o] = s1 * wb;
@@ -948,8 +983,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
         for (int kb = 0; kb < HALF / 8; ++kb) {
             const int j0 = u0 + 8 * kb;
             float z[4][8];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) ld8(tlane + (uint32_t)(64 * c + j0), z[c]);
+            ld8x4(tlane + (uint32_t)j0, tlane + (uint32_t)(64 + j0), tlane + (uint32_t)(128 + j0),
+                  tlane + (uint32_t)(192 + j0), z);
             float rho[8];
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
@@ -957,12 +992,14 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
                 float sg, s0, s1, s2;
                 silu_all(z[0][o] + b2s[j], sg, s0, s1, s2);
                 const float wj = w3s[j], d[3] = {z[1][o], z[2][o], z[3][o]};
+                const float g1 = wj * s1, g2 = wj * s2;
+                const float e[3] = {g2 * d[0], g2 * d[1], g2 * d[2]};
                 y[0] += wj * s0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) y[1 + k] += wj * s1 * d[k];
+                for (int k = 0; k < 3; ++k) y[1 + k] += g1 * d[k];
 #pragma unroll
-                for (int m = 0; m < 6; ++m) y[4 + m] += wj * s2 * d[K2[m]] * d[L2[m]];
-                rho[o] = wj * s1;
+                for (int m = 0; m < 6; ++m) y[4 + m] += e[K2[m]] * d[L2[m]];
+                rho[o] = g1;
             }
             st8(Ac + canon(row, j0, A_LBO), rho);
         }
@@ -990,11 +1027,10 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
             for (int o = 0; o < 8; ++o) {
                 const int n = n0 + o;
                 const float wa = W1s[3 * n], wb = W1s[3 * n + 1], wc = W1s[3 * n + 2];
-                float sg, s0, s1, s2;
-                silu_all(b1s[n] + wa * u[0] + wb * u[1] + wc * u[2], sg, s0, s1, s2);
-                const float q = r[o] * s2, wk[3] = {wa, wb, wc};
+                const float q = r[o] * silu2(b1s[n] + wa * u[0] + wb * u[1] + wc * u[2]);
+                const float wk[3] = {wa, wb, wc}, qk[3] = {q * wa, q * wb, q * wc};
 #pragma unroll
-                for (int m = 0; m < 6; ++m) y[4 + m] += q * wk[K2[m]] * wk[L2[m]];
+                for (int m = 0; m < 6; ++m) y[4 + m] += qk[K2[m]] * wk[L2[m]];
             }
         }
         // the two halves of each triangle meet; the first half stores
