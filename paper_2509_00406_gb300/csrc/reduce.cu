@@ -18,11 +18,15 @@ __global__ void __launch_bounds__(THREADS) k_sumsq(const T *g, const int32_t *cb
         // The FP64 pipe of this GPU runs at a small fraction of the FP32
         // rate; it now does one add per four entries instead of a convert
         // and a fused multiply-add per entry.
+        // unrolled so that several rounds of loads are in flight; the
+        // summation order (one running sum per thread) is unchanged
+#pragma unroll 4
         for (; i + 3 * THREADS < e; i += 4 * THREADS) {
             const float v0 = g[i], v1 = g[i + THREADS], v2 = g[i + 2 * THREADS], v3 = g[i + 3 * THREADS];
             s += (double)((v0 * v0 + v1 * v1) + (v2 * v2 + v3 * v3));
         }
     }
+#pragma unroll 4
     for (; i < e; i += THREADS) {
         const double v = (double)g[i];
         s += v * v;
