@@ -108,11 +108,12 @@ __device__ __forceinline__ int elem_col(int e) { return 8 * (e >> 2) + 2 * (thre
 
 // SiLU and its first two derivatives: sg = sigma(z), s = z sg,
 // s1 = sg (1 + z (1 - sg)), s2 = sg (1 - sg) (2 + z (1 - 2 sg)).  The fast
-// exponential and reciprocal intrinsics suffice: the network's activations
-// are rounded to BF16 before every contraction.
+// exponential and divide intrinsics suffice (about 2 ulp): the network's
+// activations are rounded to BF16 before every contraction.  The correctly
+// rounded reciprocal cost the per-triangle network a quarter of its time.
 __device__ __forceinline__ void silu_all(float z, float &sg, float &s, float &s1, float &s2)
 {
-    sg = __frcp_rn(1.0f + __expf(-z));
+    sg = __fdividef(1.0f, 1.0f + __expf(-z));
     s = z * sg;
     s1 = sg * (1.0f + z * (1.0f - sg));
     s2 = sg * (1.0f - sg) * (2.0f + z * (1.0f - 2.0f * sg));
@@ -834,19 +835,17 @@ __device__ __forceinline__ void ld8x4(uint32_t t0, uint32_t t1, uint32_t t2, uin
 #pragma unroll
         for (int q = 0; q < 8; ++q) v[c][q] = __uint_as_float(r[8 * c + q]);
 }
-// silu and its first derivative (layer 1 needs no more); its second
-// derivative alone (the reverse part); the formulas of silu_all
-__device__ __forceinline__ void silu01(float z, float &s, float &s1)
+// the logistic function with the fast divide intrinsic (about 2 ulp; the
+// activations are rounded to BF16 before every contraction), and the SiLU
+// formulas of silu_all on it: value and first derivative (layer 1), all
+// three (layer 2), the second derivative from a kept sigma (reverse part)
+__device__ __forceinline__ float sigm(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+__device__ __forceinline__ void silu01(float z, float sg, float &s, float &s1)
 {
-    const float sg = __frcp_rn(1.0f + __expf(-z));
     s = z * sg;
     s1 = sg * (1.0f + z * (1.0f - sg));
 }
-__device__ __forceinline__ float silu2(float z)
-{
-    const float sg = __frcp_rn(1.0f + __expf(-z));
-    return sg * (1.0f - sg) * (2.0f + z * (1.0f - 2.0f * sg));
-}
+__device__ __forceinline__ float silu2(float z, float sg) { return sg * (1.0f - sg) * (2.0f + z * (1.0f - 2.0f * sg)); }
 // 8 BF16 values into one 16-byte row piece of a canonical operand
 __device__ __forceinline__ void st8(unsigned char *dst, const float (&v)[8])
 {
@@ -939,16 +938,20 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
 #pragma unroll
             for (int k = 0; k < 3; ++k) u[k] = (I3[k] - norms[k]) / norms[3 + k];
         }
-        // 1. layer 1 of this half's units: value and tangents as BF16 operands
-#pragma unroll 1
+        // 1. layer 1 of this half's units: value and tangents as BF16
+        // operands; sigma(z1) kept in registers for the reverse part
+        float sg1[HALF];
+#pragma unroll
         for (int kb = 0; kb < HALF / 8; ++kb) {
             float v[4][8];
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
                 const int i = u0 + 8 * kb + o;
                 const float wa = W1s[3 * i], wb = W1s[3 * i + 1], wc = W1s[3 * i + 2];
+                const float z1 = b1s[i] + wa * u[0] + wb * u[1] + wc * u[2];
+                sg1[8 * kb + o] = sigm(z1);
                 float s0, s1;
-                silu01(b1s[i] + wa * u[0] + wb * u[1] + wc * u[2], s0, s1);
+                silu01(z1, sg1[8 * kb + o], s0, s1);
                 v[0][o] = s0;
                 v[1][o] = s1 * wa;
                 v[2][o] = s1 * wb;
@@ -989,8 +992,10 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
 #pragma unroll
             for (int o = 0; o < 8; ++o) {
                 const int j = j0 + o;
-                float sg, s0, s1, s2;
-                silu_all(z[0][o] + b2s[j], sg, s0, s1, s2);
+                const float z2 = z[0][o] + b2s[j], sg = sigm(z2);
+                float s0, s1;
+                silu01(z2, sg, s0, s1);
+                const float s2 = silu2(z2, sg);
                 const float wj = w3s[j], d[3] = {z[1][o], z[2][o], z[3][o]};
                 const float g1 = wj * s1, g2 = wj * s2;
                 const float e[3] = {g2 * d[0], g2 * d[1], g2 * d[2]};
@@ -1018,7 +1023,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
         ++phase;
         fence_after();
         if (!ok) break;
-#pragma unroll 1
+#pragma unroll
         for (int kb = 0; kb < HALF / 8; ++kb) {
             const int n0 = u0 + 8 * kb;
             float r[8];
@@ -1027,7 +1032,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
             for (int o = 0; o < 8; ++o) {
                 const int n = n0 + o;
                 const float wa = W1s[3 * n], wb = W1s[3 * n + 1], wc = W1s[3 * n + 2];
-                const float q = r[o] * silu2(b1s[n] + wa * u[0] + wb * u[1] + wc * u[2]);
+                const float q = r[o] * silu2(b1s[n] + wa * u[0] + wb * u[1] + wc * u[2], sg1[8 * kb + o]);
                 const float wk[3] = {wa, wb, wc}, qk[3] = {q * wa, q * wb, q * wc};
 #pragma unroll
                 for (int m = 0; m < 6; ++m) y[4 + m] += qk[K2[m]] * wk[L2[m]];
