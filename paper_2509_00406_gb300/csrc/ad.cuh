@@ -336,11 +336,20 @@ template <class A>
 concept Active = requires { typename A::scalar; };
 
 template <typename T> struct Fn;
+// FP32 on the device: reciprocal by the fast divide intrinsic and square
+// root as x rsqrt(x) (about 2 ulp each, against the correctly rounded forms'
+// multi-instruction sequences); arguments are positive and normal where the
+// terms call them (squared lengths, r^2 of atan2)
 template <> struct Fn<float> {
+#ifdef __CUDA_ARCH__
+    ADM_HD static float sqrt_(float x) { return x * rsqrtf(x); }
+    ADM_HD static float rcp_(float x) { return __fdividef(1.0f, x); }
+#else
     ADM_HD static float sqrt_(float x) { return ::sqrtf(x); }
+    ADM_HD static float rcp_(float x) { return 1.0f / x; }
+#endif
     ADM_HD static float log_(float x) { return ::logf(x); }
     ADM_HD static float atan2_(float y, float x) { return ::atan2f(y, x); }
-    ADM_HD static float rcp_(float x) { return 1.0f / x; }
 };
 template <> struct Fn<double> {
     ADM_HD static double sqrt_(double x) { return ::sqrt(x); }
