@@ -29,7 +29,7 @@ UMBRELLA = 9
 # adm_precision
 FP64, FP32 = 0, 1
 # adm_option
-OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE, OPT_GRAPH, OPT_TILE_THREADS = 1, 2, 3, 4, 5, 6
+OPT_ASSEMBLER, OPT_TILE_TRIS, OPT_BLOCK_THREADS, OPT_PROFILE, OPT_GRAPH, OPT_TILE_THREADS, OPT_MLP_NET = 1, 2, 3, 4, 5, 6, 7
 # adm_stage
 STAGES = ["zero", "triangles", "hinges", "gnorm", "finalize", "tiled", "graph", "mlp", "pairs"]
 MLP_NPARAM = 4481
