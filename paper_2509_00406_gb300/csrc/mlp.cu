@@ -975,6 +975,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
             commit(&bar);
         }
         ok = __syncthreads_and(wait(&bar, phase & 1u));
+        if (!ok) wait(&bar, phase & 1u);  // bounded again: the MMAs in flight land before the TMEM is freed
         ++phase;
         fence_after();
         if (!ok) break;
@@ -1020,6 +1021,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_mlp_tri_tc(const float *th, 
             commit(&bar);
         }
         ok = __syncthreads_and(wait(&bar, phase & 1u));
+        if (!ok) wait(&bar, phase & 1u);  // as above
         ++phase;
         fence_after();
         if (!ok) break;

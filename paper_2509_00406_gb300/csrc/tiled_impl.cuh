@@ -750,6 +750,9 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
 #pragma unroll
                 for (int e = 0; e < CV; ++e) acc[e] = -T(0);
                 const T *src = sv + CV * vs0;
+                // two chunks per iteration: their loads are in flight together
+                // (the sums keep the chunk order)
+#pragma unroll 2
                 for (int q = 0; q < nv; ++q)
 #pragma unroll
                     for (int e = 0; e < CV; ++e) acc[e] += src[CV * q + e];
@@ -788,6 +791,7 @@ __global__ void __launch_bounds__(THREADS, (tile_min_blocks<T, PROJ, THREADS>())
 #pragma unroll
                 for (int k = 0; k < NB; ++k) acc[k] = -T(0);
                 const T *src = sp + CP * start;
+#pragma unroll 2
                 for (int q = 0; q < cnt; ++q)
 #pragma unroll
                     for (int k = 0; k < NB; ++k) acc[k] += src[CP * q + k];
