@@ -40,7 +40,8 @@ extern "C" {
 //   block_adds[b] = number of tiles producing a shared block (0 otherwise).
 // stats: {n_tiles, partial slots (vertex + pair), n_zero_verts, FP64
 // Hessian-mode shared-memory bytes (VD = 3), nnzb, nH, build_ms, largest
-// slot table of a tile}.  Returns 0 or an adm_status, or a negative code
+// slot table of a tile, FP32 Hessian-mode shared-memory bytes (VD = 3)}
+// (9 entries).  Returns 0 or an adm_status, or a negative code
 // < -99 naming the check that failed.
 int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t nT, const int64_t *v_off,
                         const int64_t *f_off, int32_t n_mesh, int32_t with_hinges, int32_t tile_tris,
@@ -264,6 +265,7 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
     stats[5] = (double)m.nH();
     stats[6] = std::chrono::duration<double, std::milli>(t1 - t0).count();
     stats[7] = (double)ts.max_part;
+    stats[8] = (double)tile_smem_bytes(ts, MODE_HESS, 3, 4);
     // every triangle is exactly one unit
     std::vector<char> seen_t(nT, 0);
     for (int32_t e : ts.tri_perm)

@@ -29,7 +29,7 @@ def run(L, mesh, with_hinges, tile):
     cap = 64 * mesh.nV + 100
     bw = np.zeros(cap, dtype=np.int32)
     ba = np.zeros(cap, dtype=np.int32)
-    st = np.zeros(8)
+    st = np.zeros(9)
     p = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
     rc = L.adm_host_tile_check(p(V), C.c_int64(mesh.nV), p(F), C.c_int64(mesh.nT), p(vo), p(fo),
                                C.c_int32(mesh.n_mesh), C.c_int32(with_hinges), C.c_int32(tile), p(bw), p(ba),
@@ -82,3 +82,17 @@ def test_unused_vertex_is_zeroed(H):
     assert rc == 0, rc
     assert (bw != -1).all()
     assert int(st[2]) >= 1                          # the unused vertex is in the zero list
+
+
+@pytest.mark.parametrize("tile", [96, 192, 224])
+def test_tiles_keep_two_fp32_blocks_per_sm(H, tile):
+    """Every tile's shared memory, with its x region sized for the set's
+    largest footprint (the next tile's x is staged there while the current
+    tile's chunks are summed), stays within what two FP32 blocks per SM
+    allow (228 KB per SM, 1 KB reserved per block), and FP64 within one
+    block's 227 KB, on the shell batch's mesh levels."""
+    mesh = synth.shell_batch([4, 5, 6, 4], seed=3)
+    rc, bw, ba, st = run(H, mesh, 1, tile)
+    assert rc == 0, rc
+    assert st[8] <= (228 * 1024) // 2 - 1024, st[8]
+    assert st[3] <= 227 * 1024, st[3]
