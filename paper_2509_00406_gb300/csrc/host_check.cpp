@@ -281,4 +281,29 @@ int adm_host_tile_check(const double *V, int64_t nV, const int32_t *F, int64_t n
     return 0;
 }
 
+// tcgen05 operand layout and instruction descriptor (internal.h): every
+// element of a rows x k BF16 operand (rows and k multiples of 8) maps to its
+// own 2-byte slot inside rows * k * 2 bytes, every 8-element row piece starts
+// on a 16-byte boundary, and the descriptor of a 128 x 64 tile carries the
+// formats, majorness, N and M where the kernel's MMAs read them.  Returns 0,
+// or the number of the check that failed.
+int adm_host_umma_check(int32_t rows, int32_t k)
+{
+    if (rows <= 0 || k <= 0 || rows % 8 || k % 8) return 9;
+    const uint32_t lbo = (uint32_t)(rows / 8) * 128u, bytes = (uint32_t)rows * (uint32_t)k * 2u;
+    std::vector<char> seen(bytes, 0);
+    for (int r = 0; r < rows; ++r)
+        for (int kk = 0; kk < k; ++kk) {
+            const uint32_t o = umma_canon(r, kk, lbo);
+            if (o % 2 || o + 2 > bytes) return 1;
+            if (seen[o]++) return 2;
+            if (kk % 8 == 0 && o % 16) return 3;
+        }
+    const uint32_t d = umma_idesc_bf16(128, 64);
+    if (((d >> 4) & 3u) != 1 || ((d >> 7) & 7u) != 1 || ((d >> 10) & 7u) != 1 || ((d >> 13) & 15u) != 0 ||
+        ((d >> 17) & 63u) != 64 / 8 || ((d >> 24) & 31u) != 128 / 16)
+        return 4;
+    return 0;
+}
+
 }  // extern "C"

@@ -371,6 +371,22 @@ ADM_TILE_HD TileLayout tile_layout(int nf_cap, int nvc, int npc, int meta_bytes,
     L.total = L.off_blob + (mode >= MODE_GRAD ? meta_bytes : 0);
     return L;
 }
+// tcgen05 operands of the learned membrane's network: the byte offset of
+// element (row, k) of a K-major BF16 operand in the canonical layout without
+// swizzle (8-row x 16-byte core matrices, row groups 128 bytes apart -- the
+// shared-memory descriptor's stride byte offset -- and 8-element K chunks
+// lbo bytes apart, its leading byte offset), and the instruction descriptor
+// of tcgen05.mma kind::f16 for BF16 A and B, FP32 D, both K-major, an M x N
+// tile: D format bits 4-5, A and B formats bits 7-9 and 10-12, N / 8 from
+// bit 17, M / 16 from bit 24
+ADM_TILE_HD constexpr uint32_t umma_canon(int row, int k, uint32_t lbo)
+{
+    return (uint32_t)(row >> 3) * 128u + (uint32_t)(k >> 3) * lbo + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+ADM_TILE_HD constexpr uint32_t umma_idesc_bf16(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
 // dynamic shared memory of the tiled kernel for a tile set, mode and
 // precision: the largest tile's layout
 int64_t tile_smem_bytes(const TileSet &ts, int mode, int vd, int elem_bytes);

@@ -758,12 +758,9 @@ constexpr uint32_t A_BYTES = TILE * H * 2, B_BYTES = H * H * 2;
 constexpr uint32_t SMEM = 4 * A_BYTES + 2 * B_BYTES;  // 80 KB: two blocks per SM, 256 TMEM columns each
 constexpr uint32_t TMEM_COLS = 256;
 // instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, N, M
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) | ((uint32_t)(TILE >> 4) << 24);
+constexpr uint32_t IDESC = umma_idesc_bf16(TILE, H);
 
-__device__ __forceinline__ uint32_t canon(int row, int k, uint32_t lbo)
-{
-    return (uint32_t)(row >> 3) * 128u + (uint32_t)(k >> 3) * lbo + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
-}
+__device__ __forceinline__ uint32_t canon(int row, int k, uint32_t lbo) { return umma_canon(row, k, lbo); }
 // shared-memory matrix descriptor: start, LBO, SBO = 128 (bytes >> 4), the
 // descriptor version bit, no swizzle
 __device__ __forceinline__ uint64_t sdesc(const void *p, uint32_t lbo)

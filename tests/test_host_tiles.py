@@ -96,3 +96,13 @@ def test_tiles_keep_two_fp32_blocks_per_sm(H, tile):
     assert rc == 0, rc
     assert st[8] <= (228 * 1024) // 2 - 1024, st[8]
     assert st[3] <= 227 * 1024, st[3]
+
+
+@pytest.mark.parametrize("rows,k", [(128, 64), (64, 64), (8, 8)])
+def test_tcgen05_operand_layout_and_descriptor(H, rows, k):
+    """The learned membrane's tcgen05 operands: the canonical K-major layout
+    without swizzle places each BF16 element of a rows x k operand in its
+    own slot of the buffer, with 16-byte aligned row pieces (one store of 8
+    elements each), and the instruction descriptor encodes BF16 inputs, FP32
+    accumulation, K-major operands, N = 64 and M = 128."""
+    assert H.adm_host_umma_check(rows, k) == 0
