@@ -8,6 +8,11 @@
 #include <unordered_map>
 
 #include "internal.h"
+// the device path's per-term filtering, compiled for the host as well (the
+// math declarations come first: nvcc provides them implicitly)
+#include <cmath>
+#include "spd.cuh"
+#include "terms.cuh"
 
 using namespace adm;
 
@@ -303,6 +308,31 @@ int adm_host_umma_check(int32_t rows, int32_t k)
     if (((d >> 4) & 3u) != 1 || ((d >> 7) & 7u) != 1 || ((d >> 10) & 7u) != 1 || ((d >> 13) & 15u) != 0 ||
         ((d >> 17) & 63u) != 64 / 8 || ((d >> 24) & 31u) != 128 / 16)
         return 4;
+    return 0;
+}
+
+// Per-term Hessian filtering of the filtered passes (spd.cuh: edge metric,
+// shifted-Cholesky test, round-robin Jacobi, clamp), run on the host on one
+// term's Hessian in its edge vectors He (packed upper: 45 reals for a hinge,
+// 21 for a triangle in 3D), in place, in FP64 (prec 0) or in FP32 (prec 1,
+// He rounded to float first).  kind 0: hinge, 1: triangle in 3D.  Returns 0,
+// or 9 for a bad kind or precision.
+int adm_host_project_edges(int32_t kind, int32_t prec, double *He, double eps)
+{
+    auto run = [&](auto real, auto edges) {
+        using T = decltype(real);
+        using E = decltype(edges);
+        constexpr int N = E::NE * 3, NP = N * (N + 1) / 2;
+        T h[NP];
+        for (int k = 0; k < NP; ++k) h[k] = (T)He[k];
+        project_edges<E, 3>(h, (T)eps);
+        for (int k = 0; k < NP; ++k) He[k] = (double)h[k];
+    };
+    if (kind == 0 && prec == 0) run(double{}, HingeEdges{});
+    else if (kind == 0 && prec == 1) run(float{}, HingeEdges{});
+    else if (kind == 1 && prec == 0) run(double{}, TriEdges{});
+    else if (kind == 1 && prec == 1) run(float{}, TriEdges{});
+    else return 9;
     return 0;
 }
 
