@@ -336,4 +336,53 @@ int adm_host_project_edges(int32_t kind, int32_t prec, double *He, double eps)
     return 0;
 }
 
+// The device's per-element forward mode (terms.cuh), compiled for the host:
+// one StVK membrane triangle (x: 9 reals, Dinv: the rest edges' inverse,
+// 2x2 row-major, area, E, nu, thickness) or one dihedral hinge (x: 12
+// reals, rest angle, weight w of w (theta - thetabar)^2), evaluated in its
+// edge vectors in FP64 (prec 0) or FP32 (prec 1), then expanded to vertex
+// coordinates by the accessors the kernels write their chunks with: energy,
+// gradient (k) and Hessian (k x k, row-major).  Returns 0, 1 outside the
+// term's domain, 9 for a bad precision.
+int adm_host_stvk_local(int32_t prec, const double *x9, const double *Dinv, double area, double E, double nu,
+                        double thick, double *f, double *g, double *H)
+{
+    auto run = [&](auto real) {
+        using T = decltype(real);
+        T x[9], D[4];
+        for (int k = 0; k < 9; ++k) x[k] = (T)x9[k];
+        for (int k = 0; k < 4; ++k) D[k] = (T)Dinv[k];
+        const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / (1.0 - nu * nu);
+        EdgeLocal<TriEdges, 3, T> L;
+        membrane_local<T, PsiStVK<T>, false>(x, D, PsiStVK<T>{(T)mu, (T)lam, (T)(thick * area)}, L);
+        *f = (double)local_f(L);
+        for (int i = 0; i < 9; ++i) g[i] = (double)local_g(L, i);
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) H[9 * i + j] = (double)local_H(L, i, j);
+        return std::isfinite(*f);
+    };
+    if (prec != 0 && prec != 1) return 9;
+    const bool ok = prec == 0 ? run(double{}) : run(float{});
+    return ok ? 0 : 1;
+}
+
+int adm_host_hinge_local(int32_t prec, const double *x12, double thetabar, double w, double *f, double *g, double *H)
+{
+    auto run = [&](auto real) {
+        using T = decltype(real);
+        T x[12];
+        for (int k = 0; k < 12; ++k) x[k] = (T)x12[k];
+        EdgeLocal<HingeEdges, 3, T> L;
+        const bool ok = hinge_local<T, false>(x, (T)thetabar, (T)w, L, T(0));
+        *f = (double)local_f(L);
+        for (int i = 0; i < 12; ++i) g[i] = (double)local_g(L, i);
+        for (int i = 0; i < 12; ++i)
+            for (int j = 0; j < 12; ++j) H[12 * i + j] = (double)local_H(L, i, j);
+        return ok && std::isfinite(*f);
+    };
+    if (prec != 0 && prec != 1) return 9;
+    const bool ok = prec == 0 ? run(double{}) : run(float{});
+    return ok ? 0 : 1;
+}
+
 }  // extern "C"
