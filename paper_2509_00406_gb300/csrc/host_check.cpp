@@ -337,31 +337,46 @@ int adm_host_project_edges(int32_t kind, int32_t prec, double *He, double eps)
 }
 
 // The device's per-element forward mode (terms.cuh), compiled for the host:
-// one StVK membrane triangle (x: 9 reals, Dinv: the rest edges' inverse,
-// 2x2 row-major, area, E, nu, thickness) or one dihedral hinge (x: 12
-// reals, rest angle, weight w of w (theta - thetabar)^2), evaluated in its
-// edge vectors in FP64 (prec 0) or FP32 (prec 1), then expanded to vertex
-// coordinates by the accessors the kernels write their chunks with: energy,
-// gradient (k) and Hessian (k x k, row-major).  Returns 0, 1 outside the
-// term's domain, 9 for a bad precision.
-int adm_host_stvk_local(int32_t prec, const double *x9, const double *Dinv, double area, double E, double nu,
-                        double thick, double *f, double *g, double *H)
+// one triangle term -- kind 0 StVK membrane, 1 Neo-Hookean membrane (x: 9
+// reals), 2 symmetric Dirichlet in 2D (x: 6 reals) -- with Dinv the rest
+// edges' inverse (2x2 row-major), the rest area and E, nu, thickness (the
+// membranes), or one dihedral hinge (x: 12 reals, rest angle, weight w of
+// w (theta - thetabar)^2); evaluated in its edge vectors in FP64 (prec 0) or
+// FP32 (prec 1), then expanded to vertex coordinates by the accessors the
+// kernels write their chunks with: energy, gradient (k) and Hessian (k x k,
+// row-major).  Returns 0, 1 outside the term's domain, 9 for a bad kind or
+// precision.
+int adm_host_tri_local(int32_t kind, int32_t prec, const double *xin, const double *Dinv, double area, double E,
+                       double nu, double thick, double *f, double *g, double *H)
 {
+    const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / (1.0 - nu * nu);
+    auto out = [&](const auto &L, int k) {
+        *f = (double)local_f(L);
+        for (int i = 0; i < k; ++i) g[i] = (double)local_g(L, i);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) H[k * i + j] = (double)local_H(L, i, j);
+    };
     auto run = [&](auto real) {
         using T = decltype(real);
-        T x[9], D[4];
-        for (int k = 0; k < 9; ++k) x[k] = (T)x9[k];
-        for (int k = 0; k < 4; ++k) D[k] = (T)Dinv[k];
-        const double mu = E / (2.0 * (1.0 + nu)), lam = E * nu / (1.0 - nu * nu);
+        T D[4];
+        for (int q = 0; q < 4; ++q) D[q] = (T)Dinv[q];
+        if (kind == 2) {
+            T x[6];
+            for (int q = 0; q < 6; ++q) x[q] = (T)xin[q];
+            EdgeLocal<TriEdges, 2, T> L;
+            const T det = uv_local<T, PsiSymDir<T>, false>(x, D, PsiSymDir<T>{(T)area}, L);
+            out(L, 6);
+            return det > T(0) && std::isfinite(*f);
+        }
+        T x[9];
+        for (int q = 0; q < 9; ++q) x[q] = (T)xin[q];
         EdgeLocal<TriEdges, 3, T> L;
-        membrane_local<T, PsiStVK<T>, false>(x, D, PsiStVK<T>{(T)mu, (T)lam, (T)(thick * area)}, L);
-        *f = (double)local_f(L);
-        for (int i = 0; i < 9; ++i) g[i] = (double)local_g(L, i);
-        for (int i = 0; i < 9; ++i)
-            for (int j = 0; j < 9; ++j) H[9 * i + j] = (double)local_H(L, i, j);
-        return std::isfinite(*f);
+        if (kind == 0) membrane_local<T, PsiStVK<T>, false>(x, D, PsiStVK<T>{(T)mu, (T)lam, (T)(thick * area)}, L);
+        else membrane_local<T, PsiNH<T>, false>(x, D, PsiNH<T>{(T)mu, (T)lam, (T)(thick * area)}, L);
+        out(L, 9);
+        return (bool)std::isfinite(*f);
     };
-    if (prec != 0 && prec != 1) return 9;
+    if ((prec != 0 && prec != 1) || kind < 0 || kind > 2) return 9;
     const bool ok = prec == 0 ? run(double{}) : run(float{});
     return ok ? 0 : 1;
 }
